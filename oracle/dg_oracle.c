@@ -1,0 +1,1153 @@
+/*
+ * dg_oracle.c -- plain, slow, FP64 CPU restatement of the DGSEM operator of
+ * GALAEXI (arXiv 2404.12703), used as TEST INFRASTRUCTURE ONLY.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may load
+ * this library.  It shares no code with the CUDA path: it builds its own
+ * 1D operators, its own connectivity (by matching node coordinates, not
+ * vertex ids), its own metrics, and evaluates every sum as a plain loop in the
+ * order the paper writes it.  Compiled twice: with REAL = double (the oracle)
+ * and with REAL = long double (-DORC_QUAD, to measure the FP64 rounding floor).
+ *
+ * What it computes (paper sections / equations):
+ *   - LGL nodes, weights, D_ij = l_j'(x_i), the weak operator
+ *     Dhat_ij = -(w_j/w_i) D_ji (Eq. dgsem and the definitions after it; the
+ *     printed weight ratio is read with i and j exchanged, the reading that makes
+ *     the weak form of Eq. weak_form come out), and the split operator
+ *     Dsplit = 2D with the two corner corrections (Sec. 2.2, Nonlinear Stability).
+ *   - curl-form metrics J a^i_n = -xhat_i . curl_xi (x_l grad_xi x_m) (Sec. 2.2,
+ *     Mapping the Equations), J = det(dx/dxi).
+ *   - BR1 lifting of (u, v, w, T) in weak form (Eq. lifting, Sec. 2.2).
+ *   - KEP split-form volume integral (Pirozzoli two-point flux with averaged
+ *     metrics) plus the collocated viscous volume term (Eq. dgsem).
+ *   - Roe (no entropy fix) or Lax-Friedrichs surface flux, BR1 viscous surface
+ *     flux, times the surface element (FillFlux); SurfInt by a loop over faces
+ *     in the manner of Algorithm 3; ApplyJac.
+ *   - Hennemann a-priori indicator and convex DG/FV sub-cell blending
+ *     (Sec. 2.3, Eq. of the blended operator).
+ *   - Carpenter-Kennedy five-stage 2N-storage RK4 (Sec. 2.2, Time integration)
+ *     and a CFL time step (the paper gives no rule; see the reading in dg_dt).
+ *   - kinetic energy E_k and its exact rate (Sec. 5.2).
+ *
+ * Node index inside an element: node = i + n*(j + n*k), i along xi.
+ * Public state layout: U[e][node][v], v = (rho, rho u, rho v, rho w, rho e).
+ * Local faces: f = 2*d + s, d in {xi, eta, zeta}, s = 0 for the minus face
+ * (index 0) and 1 for the plus face (index N).  Face frame (p, q): (j, k) for
+ * d = 0, (i, k) for d = 1, (i, j) for d = 2.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef ORC_QUAD
+typedef long double real;
+#define RSQRT(x) sqrtl(x)
+#define RABS(x) fabsl(x)
+#define REXP(x) expl(x)
+#define RLOG(x) logl(x)
+#define RPOW(x, y) powl(x, y)
+#define RFLOOR(x) floorl(x)
+#define REPS LDBL_EPSILON
+#define ORC(name) orcq_##name
+#else
+typedef double real;
+#define RSQRT(x) sqrt(x)
+#define RABS(x) fabs(x)
+#define REXP(x) exp(x)
+#define RLOG(x) log(x)
+#define RPOW(x, y) pow(x, y)
+#define RFLOOR(x) floor(x)
+#define REPS DBL_EPSILON
+#define ORC(name) orc_##name
+#endif
+
+#define NMAX 16
+
+/* ------------------------------------------------------------------ */
+/* Parameters, passed as a flat double array from Python.              */
+/* ------------------------------------------------------------------ */
+enum {
+  P_GAMMA = 0, P_R, P_PR, P_MU, P_RIEMANN, P_VISCOUS, P_SHOCK,
+  P_ALPHA_MIN, P_ALPHA_MAX, P_CFL, P_DFL, P_ALPHA_FORCE, P_COUNT
+};
+
+typedef struct {
+  real gamma, R, Pr, mu;
+  int riemann;  /* 0 = Roe, 1 = Lax-Friedrichs */
+  int viscous;
+  int shock;
+  real alpha_min, alpha_max, cfl, dfl;
+  real alpha_force;  /* >= 0: every element blends with this alpha (tests) */
+} params_t;
+
+static params_t read_params(const double* p) {
+  params_t P;
+  P.gamma = p[P_GAMMA];
+  P.R = p[P_R];
+  P.Pr = p[P_PR];
+  P.mu = p[P_MU];
+  P.riemann = (int)p[P_RIEMANN];
+  P.viscous = (int)p[P_VISCOUS];
+  P.shock = (int)p[P_SHOCK];
+  P.alpha_min = p[P_ALPHA_MIN];
+  P.alpha_max = p[P_ALPHA_MAX];
+  P.cfl = p[P_CFL];
+  P.dfl = p[P_DFL];
+  P.alpha_force = p[P_ALPHA_FORCE];
+  return P;
+}
+
+/* ------------------------------------------------------------------ */
+/* 1D operators                                                        */
+/* ------------------------------------------------------------------ */
+
+/* Legendre polynomial P_N and derivative by the three-term recurrence. */
+static void legendre(int N, real x, real* P, real* dP) {
+  real p0 = 1, p1 = x, d0 = 0, d1 = 1;
+  if (N == 0) { *P = 1; *dP = 0; return; }
+  for (int k = 2; k <= N; ++k) {
+    real p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+    real d2 = k * p1 + x * d1;   /* P_k' = k P_{k-1} + x P_{k-1}' */
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  (void)d0;
+  *P = p1;
+  *dP = d1;
+}
+
+/* LGL nodes: -1, +1 and the roots of P_N'; weights 2 / (N (N+1) P_N(x)^2). */
+static void lgl(int N, real* x, real* w) {
+  x[0] = -1;
+  x[N] = 1;
+  for (int j = 1; j < N; ++j) {
+    real t = -cos(M_PI * (double)j / (double)N);
+    for (int it = 0; it < 200; ++it) {
+      real P, dP;
+      legendre(N, t, &P, &dP);
+      /* Legendre ODE: (1 - x^2) P'' = 2 x P' - N (N+1) P */
+      real d2P = (2 * t * dP - (real)N * (N + 1) * P) / (1 - t * t);
+      real dt = dP / d2P;
+      t -= dt;
+      if (RABS(dt) <= 4 * REPS) break;
+    }
+    x[j] = t;
+  }
+  for (int j = 0; j <= N; ++j) {
+    real P, dP;
+    legendre(N, x[j], &P, &dP);
+    w[j] = 2 / ((real)N * (N + 1) * P * P);
+  }
+}
+
+/* D[i][j] = l_j'(x_i) with l_j(x) = prod_{m != j} (x - x_m) / (x_j - x_m). */
+static void lagrange_derivative(int n, const real* x, real* D) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      real s = 0;
+      for (int m = 0; m < n; ++m) {
+        if (m == j) continue;
+        real prod = 1 / (x[j] - x[m]);
+        for (int k = 0; k < n; ++k) {
+          if (k == j || k == m) continue;
+          prod *= (x[i] - x[k]) / (x[j] - x[k]);
+        }
+        s += prod;
+      }
+      D[i * n + j] = s;
+    }
+}
+
+/* Gauss-Jordan inverse with partial pivoting of an n x n matrix. */
+static int invert(int n, const real* A, real* Ainv) {
+  real a[NMAX * 2 * NMAX];
+  int m = 2 * n;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j)
+      a[i * m + j] = j < n ? A[i * n + j] : (j - n == i ? 1 : 0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (RABS(a[r * m + c]) > RABS(a[piv * m + c])) piv = r;
+    if (a[piv * m + c] == 0) return -1;
+    if (piv != c)
+      for (int j = 0; j < m; ++j) {
+        real t = a[c * m + j]; a[c * m + j] = a[piv * m + j]; a[piv * m + j] = t;
+      }
+    real d = a[c * m + c];
+    for (int j = 0; j < m; ++j) a[c * m + j] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      real f = a[r * m + c];
+      for (int j = 0; j < m; ++j) a[r * m + j] -= f * a[c * m + j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Ainv[i * n + j] = a[i * m + n + j];
+  return 0;
+}
+
+typedef struct {
+  int N, n;
+  real x[NMAX], w[NMAX];
+  real D[NMAX * NMAX];      /* D[i][a] = l_a'(x_i)                         */
+  real Dhat[NMAX * NMAX];   /* Dhat[i][a] = -(w_a / w_i) D[a][i]           */
+  real Dsplit[NMAX * NMAX]; /* 2 D[i][a] - d_iN d_aN / w_N + d_i0 d_a0 / w_0 */
+  real Vinv[NMAX * NMAX];   /* inverse of V[i][m] = Ltilde_m(x_i)          */
+} ops_t;
+
+static int build_ops(int N, ops_t* o) {
+  if (N < 1 || N + 1 > NMAX) return -1;
+  int n = N + 1;
+  o->N = N;
+  o->n = n;
+  lgl(N, o->x, o->w);
+  lagrange_derivative(n, o->x, o->D);
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < n; ++a) {
+      o->Dhat[i * n + a] = -(o->w[a] / o->w[i]) * o->D[a * n + i];
+      real ds = 2 * o->D[i * n + a];
+      if (i == N && a == N) ds -= 1 / o->w[N];
+      if (i == 0 && a == 0) ds += 1 / o->w[0];
+      o->Dsplit[i * n + a] = ds;
+    }
+  /* orthonormal Legendre modes Ltilde_m = sqrt((2m+1)/2) P_m */
+  real V[NMAX * NMAX];
+  for (int i = 0; i < n; ++i)
+    for (int m = 0; m < n; ++m) {
+      real P, dP;
+      legendre(m, o->x[i], &P, &dP);
+      V[i * n + m] = RSQRT((real)(2 * m + 1) / 2) * P;
+    }
+  return invert(n, V, o->Vinv);
+}
+
+/* ------------------------------------------------------------------ */
+/* Mesh                                                                */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  ops_t o;
+  int N, n, n2, n3;
+  long E;
+  real period[3];
+  real* xyz;     /* [E][n3][3]                                   */
+  real* Ja;      /* [E][n3][3][3]  Ja[.][d][c] = (J a^d)_c       */
+  real* J;       /* [E][n3]                                      */
+  int* nbr_e;    /* [E*6]                                        */
+  int* nbr_f;    /* [E*6]                                        */
+  int* master;   /* [E*6] 1 if this element side owns the normal */
+  int* nbr_node; /* [E*6][n2] partner face node, in partner frame */
+  int status;
+} mesh_t;
+
+static inline long node_of(int n, int i, int j, int k) { return i + (long)n * (j + (long)n * k); }
+
+/* volume node of face f at face coordinates (p, q) */
+static long face_node(int n, int f, int p, int q) {
+  int d = f / 2, end = (f % 2) ? n - 1 : 0;
+  if (d == 0) return node_of(n, end, p, q);
+  if (d == 1) return node_of(n, p, end, q);
+  return node_of(n, p, q, end);
+}
+
+/* index of node along direction d and the node with that index replaced by a */
+static inline int line_index(int n, long node, int d) {
+  long s = d == 0 ? 1 : (d == 1 ? n : (long)n * n);
+  return (int)((node / s) % n);
+}
+static inline long line_node(int n, long node, int d, int a) {
+  long s = d == 0 ? 1 : (d == 1 ? n : (long)n * n);
+  int cur = (int)((node / s) % n);
+  return node + (long)(a - cur) * s;
+}
+
+static real wrap(real v, real L, real tol) {
+  if (L <= 0) return v;
+  v = v - L * RFLOOR(v / L);
+  if (v > L - tol) v -= L;
+  return v;
+}
+static real pdist(real a, real b, real L) {
+  real d = RABS(a - b);
+  if (L > 0) {
+    real d2 = RABS(d - L);
+    if (d2 < d) d = d2;
+  }
+  return d;
+}
+
+typedef struct { real c[3]; long id; } fkey_t;
+static int cmp_fkey(const void* A, const void* B) {
+  const fkey_t* a = (const fkey_t*)A;
+  const fkey_t* b = (const fkey_t*)B;
+  if (a->c[0] < b->c[0]) return -1;
+  if (a->c[0] > b->c[0]) return 1;
+  return a->id < b->id ? -1 : (a->id > b->id ? 1 : 0);
+}
+
+static int build_connectivity(mesh_t* M) {
+  int n = M->n, n2 = M->n2;
+  long E = M->E, F = E * 6;
+  /* tolerance: a small fraction of the first element's extent */
+  real ext = 0;
+  for (int c = 0; c < 3; ++c) {
+    real lo = M->xyz[c], hi = M->xyz[c];
+    for (long v = 0; v < M->n3; ++v) {
+      real t = M->xyz[v * 3 + c];
+      if (t < lo) lo = t;
+      if (t > hi) hi = t;
+    }
+    if (hi - lo > ext) ext = hi - lo;
+  }
+  real tol = 1e-7 * ext;
+  fkey_t* keys = (fkey_t*)malloc(sizeof(fkey_t) * F);
+  if (!keys) return -1;
+  for (long e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      real c[3] = {0, 0, 0};
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          long v = face_node(n, f, p, q);
+          for (int d = 0; d < 3; ++d) c[d] += M->xyz[(e * M->n3 + v) * 3 + d];
+        }
+      fkey_t* k = &keys[e * 6 + f];
+      for (int d = 0; d < 3; ++d) k->c[d] = wrap(c[d] / n2, M->period[d], tol);
+      k->id = e * 6 + f;
+    }
+  qsort(keys, F, sizeof(fkey_t), cmp_fkey);
+  for (long a = 0; a < F; ++a) M->nbr_e[a] = -1;
+  int err = 0;
+  for (long a = 0; a < F && !err; ++a) {
+    long ia = keys[a].id;
+    for (long b = a + 1; b < F; ++b) {
+      if (keys[b].c[0] - keys[a].c[0] > tol) break;
+      if (pdist(keys[a].c[1], keys[b].c[1], M->period[1]) > tol) continue;
+      if (pdist(keys[a].c[2], keys[b].c[2], M->period[2]) > tol) continue;
+      long ib = keys[b].id;
+      if (M->nbr_e[ia] >= 0 || M->nbr_e[ib] >= 0) { err = 1; break; }
+      M->nbr_e[ia] = (int)(ib / 6); M->nbr_f[ia] = (int)(ib % 6);
+      M->nbr_e[ib] = (int)(ia / 6); M->nbr_f[ib] = (int)(ia % 6);
+      M->master[ia] = ia < ib;
+      M->master[ib] = ib < ia;
+    }
+  }
+  /* x-wrap: faces whose wrapped centroid sits within tol of 0 from below were
+     moved to ~0 by wrap(); nothing else straddles.  Every face needs a partner. */
+  for (long a = 0; a < F && !err; ++a)
+    if (M->nbr_e[a] < 0) err = 2;
+  free(keys);
+  if (err) return -2;
+  /* node correspondence by coordinates */
+  for (long e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      long ef = e * 6 + f;
+      long e2 = M->nbr_e[ef];
+      int f2 = M->nbr_f[ef];
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          const real* xa = &M->xyz[(e * M->n3 + face_node(n, f, p, q)) * 3];
+          int found = -1;
+          for (int q2 = 0; q2 < n; ++q2)
+            for (int p2 = 0; p2 < n; ++p2) {
+              const real* xb = &M->xyz[(e2 * M->n3 + face_node(n, f2, p2, q2)) * 3];
+              int ok = 1;
+              for (int d = 0; d < 3; ++d)
+                if (pdist(xa[d], xb[d], M->period[d]) > tol) ok = 0;
+              if (ok) {
+                if (found >= 0) return -3;
+                found = p2 + n * q2;
+              }
+            }
+          if (found < 0) return -4;
+          M->nbr_node[ef * n2 + p + n * q] = found;
+        }
+    }
+  return 0;
+}
+
+/* Metrics are formed in long double and rounded to REAL at the end.  The curl
+   form applies D twice to products of coordinates, which multiplies rounding
+   by about (sum_a |D_ia|)^2 ~ 2500 at N = 7; in plain double that leaves the
+   discrete metric identities and the two sides of a face inconsistent at the
+   1e-12 level, which a background pressure of p0 ~ 71 (Ma = 0.1) turns into
+   free-stream errors far above round-off.  In extended precision the rounded
+   metrics are within a few ulp of exact. */
+typedef long double mreal;
+
+static mreal mline(int n, const mreal* Dm, const mreal* fld, int stride, long v, int d) {
+  int i = line_index(n, v, d);
+  mreal s = 0;
+  for (int a = 0; a < n; ++a) s += Dm[i * n + a] * fld[line_node(n, v, d, a) * stride];
+  return s;
+}
+
+static void build_metrics(mesh_t* M) {
+  int n = M->n, n3 = M->n3;
+  /* 1D derivative matrix in long double, from long-double LGL nodes */
+  mreal xm[NMAX], Dm[NMAX * NMAX];
+  {
+    /* repeat the node / derivative construction in long double */
+    int N = M->N;
+    xm[0] = -1;
+    xm[N] = 1;
+    for (int j = 1; j < N; ++j) {
+      mreal t = -cosl(M_PI * (long double)j / (long double)N);
+      for (int it = 0; it < 200; ++it) {
+        mreal p0 = 1, p1 = t, d1 = 1;
+        for (int k = 2; k <= N; ++k) {
+          mreal p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+          mreal d2 = k * p1 + t * d1;
+          p0 = p1; p1 = p2; d1 = d2;
+        }
+        mreal d2P = (2 * t * d1 - (mreal)N * (N + 1) * p1) / (1 - t * t);
+        mreal dt = d1 / d2P;
+        t -= dt;
+        if (fabsl(dt) <= 4 * LDBL_EPSILON) break;
+      }
+      xm[j] = t;
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        mreal s = 0;
+        for (int m = 0; m < n; ++m) {
+          if (m == j) continue;
+          mreal prod = 1 / (xm[j] - xm[m]);
+          for (int k = 0; k < n; ++k) {
+            if (k == j || k == m) continue;
+            prod *= (xm[i] - xm[k]) / (xm[j] - xm[k]);
+          }
+          s += prod;
+        }
+        Dm[i * n + j] = s;
+      }
+  }
+  mreal* dx = (mreal*)malloc(sizeof(mreal) * 9 * n3);   /* dx[v][c][d] = d x_c / d xi_d */
+  mreal* V = (mreal*)malloc(sizeof(mreal) * 3 * n3);    /* V[v][d]                    */
+  mreal* X = (mreal*)malloc(sizeof(mreal) * 3 * n3);
+  for (long e = 0; e < M->E; ++e) {
+    /* the curl form is invariant under a translation of the coordinates; use
+       coordinates relative to the element's first node so that the products
+       x_l grad x_m carry rounding relative to the element size, not to the
+       distance from the origin */
+    const real* Xa = &M->xyz[e * n3 * 3];
+    for (long v = 0; v < n3; ++v)
+      for (int c = 0; c < 3; ++c) X[v * 3 + c] = (mreal)Xa[v * 3 + c] - (mreal)Xa[c];
+    for (long v = 0; v < n3; ++v)
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) dx[v * 9 + c * 3 + d] = mline(n, Dm, X + c, 3, v, d);
+    for (long v = 0; v < n3; ++v) {
+      const mreal* a = &dx[v * 9];
+      M->J[e * n3 + v] = (real)(a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                                a[2] * (a[3] * a[7] - a[4] * a[6]));
+    }
+    for (int nc = 0; nc < 3; ++nc) {
+      int m = (nc + 1) % 3, l = (nc + 2) % 3;
+      for (long v = 0; v < n3; ++v)
+        for (int d = 0; d < 3; ++d) V[v * 3 + d] = X[v * 3 + l] * dx[v * 9 + m * 3 + d];
+      for (long v = 0; v < n3; ++v)
+        for (int i = 0; i < 3; ++i) {
+          int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+          mreal curl = mline(n, Dm, V + i2, 3, v, i1) - mline(n, Dm, V + i1, 3, v, i2);
+          M->Ja[((e * n3 + v) * 3 + i) * 3 + nc] = (real)(-curl);
+        }
+    }
+  }
+  free(dx);
+  free(V);
+  free(X);
+}
+
+/* ------------------------------------------------------------------ */
+/* Point-wise physics                                                  */
+/* ------------------------------------------------------------------ */
+
+/* primitive variables q = (rho, u, v, w, p, T) by Eqs. eos_p, eos_T */
+static void cons_to_prim(const params_t* P, const real* U, real* q) {
+  q[0] = U[0];
+  q[1] = U[1] / U[0];
+  q[2] = U[2] / U[0];
+  q[3] = U[3] / U[0];
+  q[4] = (P->gamma - 1) * (U[4] - (real)0.5 * (U[1] * q[1] + U[2] * q[2] + U[3] * q[3]));
+  q[5] = q[4] / (U[0] * P->R);
+}
+
+/* Euler flux contracted with a (not necessarily unit) vector nv (Eq. nse) */
+static void euler_flux(const real* U, const real* q, const real* nv, real* f) {
+  real un = q[1] * nv[0] + q[2] * nv[1] + q[3] * nv[2];
+  f[0] = U[0] * un;
+  f[1] = U[1] * un + q[4] * nv[0];
+  f[2] = U[2] * un + q[4] * nv[1];
+  f[3] = U[3] * un + q[4] * nv[2];
+  f[4] = (U[4] + q[4]) * un;
+}
+
+/* Pirozzoli kinetic-energy-preserving two-point flux with metric m */
+static void kep_flux(const real* UL, const real* qL, const real* UR, const real* qR,
+                     const real* m, real* f) {
+  real rho = (qL[0] + qR[0]) / 2;
+  real u[3] = {(qL[1] + qR[1]) / 2, (qL[2] + qR[2]) / 2, (qL[3] + qR[3]) / 2};
+  real p = (qL[4] + qR[4]) / 2;
+  real H = ((UL[4] + qL[4]) / qL[0] + (UR[4] + qR[4]) / qR[0]) / 2;
+  real un = u[0] * m[0] + u[1] * m[1] + u[2] * m[2];
+  f[0] = rho * un;
+  for (int c = 0; c < 3; ++c) f[1 + c] = rho * un * u[c] + p * m[c];
+  f[4] = rho * un * H;
+}
+
+/* Roe flux with unit normal n, no entropy fix */
+static void roe_flux(const params_t* P, const real* UL, const real* qL, const real* UR,
+                     const real* qR, const real* n, real* f) {
+  real fL[5], fR[5];
+  euler_flux(UL, qL, n, fL);
+  euler_flux(UR, qR, n, fR);
+  real sL = RSQRT(qL[0]), sR = RSQRT(qR[0]);
+  real HL = (UL[4] + qL[4]) / qL[0], HR = (UR[4] + qR[4]) / qR[0];
+  real ut[3];
+  for (int c = 0; c < 3; ++c) ut[c] = (sL * qL[1 + c] + sR * qR[1 + c]) / (sL + sR);
+  real Ht = (sL * HL + sR * HR) / (sL + sR);
+  real rt = sL * sR;
+  real q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+  real c2 = (P->gamma - 1) * (Ht - q2 / 2);
+  real c = RSQRT(c2);
+  real un = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
+  real drho = qR[0] - qL[0], dp = qR[4] - qL[4];
+  real du[3] = {qR[1] - qL[1], qR[2] - qL[2], qR[3] - qL[3]};
+  real dun = du[0] * n[0] + du[1] * n[1] + du[2] * n[2];
+  real a1 = (dp - rt * c * dun) / (2 * c2);
+  real a2 = drho - dp / c2;
+  real a5 = (dp + rt * c * dun) / (2 * c2);
+  real l1 = RABS(un - c), l2 = RABS(un), l5 = RABS(un + c);
+  real dut[3] = {du[0] - dun * n[0], du[1] - dun * n[1], du[2] - dun * n[2]};
+  real udut = ut[0] * dut[0] + ut[1] * dut[1] + ut[2] * dut[2];
+  real D[5];
+  D[0] = l1 * a1 + l2 * a2 + l5 * a5;
+  for (int k = 0; k < 3; ++k)
+    D[1 + k] = l1 * a1 * (ut[k] - c * n[k]) + l2 * a2 * ut[k] + l5 * a5 * (ut[k] + c * n[k]) +
+               l2 * rt * dut[k];
+  D[4] = l1 * a1 * (Ht - un * c) + l2 * a2 * q2 / 2 + l5 * a5 * (Ht + un * c) + l2 * rt * udut;
+  for (int v = 0; v < 5; ++v) f[v] = (fL[v] + fR[v]) / 2 - D[v] / 2;
+}
+
+/* Local Lax-Friedrichs (Rusanov) flux with unit normal n */
+static void lf_flux(const params_t* P, const real* UL, const real* qL, const real* UR,
+                    const real* qR, const real* n, real* f) {
+  real fL[5], fR[5];
+  euler_flux(UL, qL, n, fL);
+  euler_flux(UR, qR, n, fR);
+  real cL = RSQRT(P->gamma * qL[4] / qL[0]), cR = RSQRT(P->gamma * qR[4] / qR[0]);
+  real uL = qL[1] * n[0] + qL[2] * n[1] + qL[3] * n[2];
+  real uR = qR[1] * n[0] + qR[2] * n[1] + qR[3] * n[2];
+  real lL = RABS(uL) + cL, lR = RABS(uR) + cR;
+  real lm = lL > lR ? lL : lR;
+  for (int v = 0; v < 5; ++v) f[v] = (fL[v] + fR[v]) / 2 - lm * (UR[v] - UL[v]) / 2;
+}
+
+static void riemann(const params_t* P, int kind, const real* UL, const real* qL, const real* UR,
+                    const real* qR, const real* n, real* f) {
+  if (kind == 0) roe_flux(P, UL, qL, UR, qR, n, f);
+  else lf_flux(P, UL, qL, UR, qR, n, f);
+}
+
+/* viscous flux F_v = (0, tau, tau.u - q) contracted with nv (Eq. nse, stress and
+   Fourier law); g[qv][x] = d(u, v, w, T)_qv / dx_x */
+static void visc_flux(const params_t* P, const real* q, const real* g, const real* nv, real* f) {
+  real ux = g[0], uy = g[1], uz = g[2];
+  real vx = g[3], vy = g[4], vz = g[5];
+  real wx = g[6], wy = g[7], wz = g[8];
+  real Tx = g[9], Ty = g[10], Tz = g[11];
+  real mu = P->mu;
+  real lam = P->gamma * P->R * mu / ((P->gamma - 1) * P->Pr);
+  real div = ux + vy + wz;
+  real txx = mu * (2 * ux - (real)2 / 3 * div);
+  real tyy = mu * (2 * vy - (real)2 / 3 * div);
+  real tzz = mu * (2 * wz - (real)2 / 3 * div);
+  real txy = mu * (uy + vx), txz = mu * (uz + wx), tyz = mu * (vz + wy);
+  real u = q[1], v = q[2], w = q[3];
+  real Fx[5] = {0, txx, txy, txz, txx * u + txy * v + txz * w + lam * Tx};
+  real Fy[5] = {0, txy, tyy, tyz, txy * u + tyy * v + tyz * w + lam * Ty};
+  real Fz[5] = {0, txz, tyz, tzz, txz * u + tyz * v + tzz * w + lam * Tz};
+  for (int k = 0; k < 5; ++k) f[k] = Fx[k] * nv[0] + Fy[k] * nv[1] + Fz[k] * nv[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* Shock indicator (Hennemann a-priori indicator on rho*p)             */
+/* ------------------------------------------------------------------ */
+static real indicator(const mesh_t* M, const params_t* P, const real* qe /* [n3][6] */, real* Eout) {
+  int n = M->n, N = M->N, n3 = M->n3;
+  real s[NMAX * NMAX * NMAX], t1[NMAX * NMAX * NMAX], t2[NMAX * NMAX * NMAX];
+  for (long v = 0; v < n3; ++v) s[v] = qe[v * 6 + 0] * qe[v * 6 + 4];
+  /* modal coefficients: apply Vinv along i, then j, then k */
+  const real* Vi = M->o.Vinv;
+  for (long v = 0; v < n3; ++v) {
+    int m = line_index(n, v, 0);
+    real a = 0;
+    for (int x = 0; x < n; ++x) a += Vi[m * n + x] * s[line_node(n, v, 0, x)];
+    t1[v] = a;
+  }
+  for (long v = 0; v < n3; ++v) {
+    int m = line_index(n, v, 1);
+    real a = 0;
+    for (int x = 0; x < n; ++x) a += Vi[m * n + x] * t1[line_node(n, v, 1, x)];
+    t2[v] = a;
+  }
+  real mj[NMAX];
+  for (int j = 0; j < n; ++j) mj[j] = 0;
+  for (long v = 0; v < n3; ++v) {
+    int m = line_index(n, v, 2);
+    real a = 0;
+    for (int x = 0; x < n; ++x) a += Vi[m * n + x] * t2[line_node(n, v, 2, x)];
+    int mi = line_index(n, v, 0), mjj = line_index(n, v, 1), mk = m;
+    int deg = mi > mjj ? mi : mjj;
+    if (mk > deg) deg = mk;
+    mj[deg] += a * a;
+  }
+  real totN = 0, totN1 = 0;
+  for (int j = 0; j <= N; ++j) totN += mj[j];
+  for (int j = 0; j <= N - 1; ++j) totN1 += mj[j];
+  real e1 = totN > 0 ? mj[N] / totN : 0;
+  real e2 = totN1 > 0 ? mj[N - 1] / totN1 : 0;
+  real Ei = e1 > e2 ? e1 : e2;
+  if (Eout) *Eout = Ei;
+  real T = (real)0.5 * RPOW((real)10, (real)-1.8 * RPOW((real)(N + 1), (real)0.25));
+  real sh = RLOG((1 - (real)1e-4) / (real)1e-4);
+  real alpha = 1 / (1 + REXP(-sh * (Ei - T) / T));
+  if (alpha < P->alpha_min) alpha = 0;
+  if (alpha > P->alpha_max) alpha = P->alpha_max;
+  return alpha;
+}
+
+/* ------------------------------------------------------------------ */
+/* The DG operator                                                     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  real* q;    /* [E][n3][6]                          */
+  real* g;    /* [E][n3][12] lifted gradients          */
+  real* Bc;   /* [E][n3][5]  convective DG volume term */
+  real* B;    /* [E][n3][5]  everything else           */
+  real* alpha;/* [E]                                   */
+} work_t;
+
+static void work_free(work_t* w) {
+  free(w->q); free(w->g); free(w->Bc); free(w->B); free(w->alpha);
+}
+static int work_alloc(const mesh_t* M, work_t* w) {
+  long E = M->E, n3 = M->n3;
+  w->q = (real*)calloc(E * n3 * 6, sizeof(real));
+  w->g = (real*)calloc(E * n3 * 12, sizeof(real));
+  w->Bc = (real*)calloc(E * n3 * 5, sizeof(real));
+  w->B = (real*)calloc(E * n3 * 5, sizeof(real));
+  w->alpha = (real*)calloc(E, sizeof(real));
+  if (!w->q || !w->g || !w->Bc || !w->B || !w->alpha) { work_free(w); return -1; }
+  return 0;
+}
+
+/* J Ut = -[ V_conv + V_visc + S ], Eq. dgsem with the split-form volume term.
+   want: NULL for every element, else a 0/1 mask of the elements whose Ut is
+   wanted (their neighbours' gradients are formed as needed). */
+static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
+                    const unsigned char* want, real* alpha_out, real* g_out, real* fstar_out,
+                    work_t* w) {
+  int n = M->n, n2 = M->n2, n3 = M->n3;
+  long E = M->E;
+  const ops_t* o = &M->o;
+  unsigned char* needg = (unsigned char*)calloc(E, 1);
+  for (long e = 0; e < E; ++e) {
+    if (want && !want[e]) continue;
+    needg[e] = 1;
+    for (int f = 0; f < 6; ++f) needg[M->nbr_e[e * 6 + f]] = 1;
+  }
+  /* ConsToPrim everywhere */
+  for (long v = 0; v < E * n3; ++v) cons_to_prim(P, &U[v * 5], &w->q[v * 6]);
+  memset(w->B, 0, sizeof(real) * E * n3 * 5);
+  memset(w->Bc, 0, sizeof(real) * E * n3 * 5);
+
+  /* ---- BR1 lifting of (u, v, w, T), weak form (Eq. lifting) ---- */
+  static const int lifted[4] = {1, 2, 3, 5};
+  if (P->viscous) {
+    memset(w->g, 0, sizeof(real) * E * n3 * 12);
+    for (long e = 0; e < E; ++e) {
+      if (!needg[e]) continue;
+      for (long v = 0; v < n3; ++v)
+        for (int d = 0; d < 3; ++d) {
+          int i = line_index(n, v, d);
+          for (int a = 0; a < n; ++a) {
+            long va = line_node(n, v, d, a);
+            const real* Jaa = &M->Ja[((e * n3 + va) * 3 + d) * 3];
+            for (int qv = 0; qv < 4; ++qv)
+              for (int x = 0; x < 3; ++x)
+                w->g[(e * n3 + v) * 12 + qv * 3 + x] +=
+                    o->Dhat[i * n + a] * Jaa[x] * w->q[(e * n3 + va) * 6 + lifted[qv]];
+          }
+        }
+    }
+    /* surface: q* = (q_master + q_slave)/2 times the master's outward s n, with
+       lhat = 1/w at the face node; the slave gets the opposite sign */
+    for (long e = 0; e < E; ++e)
+      for (int f = 0; f < 6; ++f) {
+        long ef = e * 6 + f;
+        if (!M->master[ef]) continue;
+        long e2 = M->nbr_e[ef];
+        int f2 = M->nbr_f[ef];
+        if (!needg[e] && !needg[e2]) continue;
+        real sgn = (f % 2) ? 1 : -1;
+        for (int qq = 0; qq < n; ++qq)
+          for (int p = 0; p < n; ++p) {
+            long vM = face_node(n, f, p, qq);
+            int a2 = M->nbr_node[ef * n2 + p + n * qq];
+            long vS = face_node(n, f2, a2 % n, a2 / n);
+            const real* Jam = &M->Ja[((e * n3 + vM) * 3 + f / 2) * 3];
+            for (int qv = 0; qv < 4; ++qv) {
+              real qs = (w->q[(e * n3 + vM) * 6 + lifted[qv]] + w->q[(e2 * n3 + vS) * 6 + lifted[qv]]) / 2;
+              for (int x = 0; x < 3; ++x) {
+                real fl = qs * sgn * Jam[x];
+                w->g[(e * n3 + vM) * 12 + qv * 3 + x] += fl / o->w[(f % 2) ? n - 1 : 0];
+                w->g[(e2 * n3 + vS) * 12 + qv * 3 + x] -= fl / o->w[(f2 % 2) ? n - 1 : 0];
+              }
+            }
+          }
+      }
+    for (long e = 0; e < E; ++e) {
+      if (!needg[e]) continue;
+      for (long v = 0; v < n3; ++v)
+        for (int k = 0; k < 12; ++k) w->g[(e * n3 + v) * 12 + k] /= M->J[e * n3 + v];
+    }
+  }
+
+  /* ---- indicator ---- */
+  for (long e = 0; e < E; ++e) w->alpha[e] = 0;
+  if (P->shock)
+    for (long e = 0; e < E; ++e) {
+      if (want && !want[e]) continue;
+      w->alpha[e] = P->alpha_force >= 0 ? P->alpha_force : indicator(M, P, &w->q[e * n3 * 6], NULL);
+    }
+
+  /* ---- volume integral ---- */
+  for (long e = 0; e < E; ++e) {
+    if (want && !want[e]) continue;
+    for (long v = 0; v < n3; ++v)
+      for (int d = 0; d < 3; ++d) {
+        int i = line_index(n, v, d);
+        const real* Jai = &M->Ja[((e * n3 + v) * 3 + d) * 3];
+        for (int a = 0; a < n; ++a) {
+          long va = line_node(n, v, d, a);
+          const real* Jaa = &M->Ja[((e * n3 + va) * 3 + d) * 3];
+          real m[3] = {(Jai[0] + Jaa[0]) / 2, (Jai[1] + Jaa[1]) / 2, (Jai[2] + Jaa[2]) / 2};
+          real fs[5];
+          kep_flux(&U[(e * n3 + v) * 5], &w->q[(e * n3 + v) * 6], &U[(e * n3 + va) * 5],
+                   &w->q[(e * n3 + va) * 6], m, fs);
+          for (int k = 0; k < 5; ++k) w->Bc[(e * n3 + v) * 5 + k] += o->Dsplit[i * n + a] * fs[k];
+          if (P->viscous) {
+            real fv[5];
+            visc_flux(P, &w->q[(e * n3 + va) * 6], &w->g[(e * n3 + va) * 12], Jaa, fv);
+            for (int k = 0; k < 5; ++k) w->B[(e * n3 + v) * 5 + k] -= o->Dhat[i * n + a] * fv[k];
+          }
+        }
+      }
+  }
+
+  /* ---- FV sub-cell operator and convex blend (Sec. 2.3) ---- */
+  if (P->shock) {
+    real* vfv = (real*)malloc(sizeof(real) * n3 * 5);
+    for (long e = 0; e < E; ++e) {
+      if (want && !want[e]) continue;
+      real al = w->alpha[e];
+      if (al == 0) continue;
+      memset(vfv, 0, sizeof(real) * n3 * 5);
+      for (int d = 0; d < 3; ++d)
+        for (long v0 = 0; v0 < n3; ++v0) {
+          if (line_index(n, v0, d) != 0) continue;   /* one pass per line */
+          /* interface metrics by telescoping the discrete derivative:
+             Ja_{-1/2} = Ja_0, Ja_{i+1/2} = Ja_{i-1/2} + w_i (D Ja)_i */
+          real Jh[NMAX + 1][3];
+          for (int c = 0; c < 3; ++c) Jh[0][c] = M->Ja[((e * n3 + v0) * 3 + d) * 3 + c];
+          for (int i = 0; i < n; ++i) {
+            for (int c = 0; c < 3; ++c) {
+              real dj = 0;
+              for (int a = 0; a < n; ++a)
+                dj += o->D[i * n + a] * M->Ja[((e * n3 + line_node(n, v0, d, a)) * 3 + d) * 3 + c];
+              Jh[i + 1][c] = Jh[i][c] + o->w[i] * dj;
+            }
+          }
+          for (int i = 0; i < n - 1; ++i) {
+            long vl = line_node(n, v0, d, i), vr = line_node(n, v0, d, i + 1);
+            const real* m = Jh[i + 1];
+            real s = RSQRT(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            real nn[3] = {m[0] / s, m[1] / s, m[2] / s};
+            real fb[5];
+            lf_flux(P, &U[(e * n3 + vl) * 5], &w->q[(e * n3 + vl) * 6], &U[(e * n3 + vr) * 5],
+                    &w->q[(e * n3 + vr) * 6], nn, fb);
+            for (int k = 0; k < 5; ++k) {
+              vfv[vl * 5 + k] += fb[k] * s / o->w[i];
+              vfv[vr * 5 + k] -= fb[k] * s / o->w[i + 1];
+            }
+          }
+        }
+      for (long v = 0; v < n3; ++v)
+        for (int k = 0; k < 5; ++k)
+          w->Bc[(e * n3 + v) * 5 + k] = (1 - al) * w->Bc[(e * n3 + v) * 5 + k] + al * vfv[v * 5 + k];
+    }
+    free(vfv);
+  }
+
+  /* ---- FillFlux + SurfInt, looping over faces (Algorithm 3) ---- */
+  for (long e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      long ef = e * 6 + f;
+      if (!M->master[ef]) continue;
+      long e2 = M->nbr_e[ef];
+      int f2 = M->nbr_f[ef];
+      if (want && !want[e] && !want[e2]) continue;
+      real sgn = (f % 2) ? 1 : -1;
+      for (int qq = 0; qq < n; ++qq)
+        for (int p = 0; p < n; ++p) {
+          long vM = face_node(n, f, p, qq);
+          int a2 = M->nbr_node[ef * n2 + p + n * qq];
+          long vS = face_node(n, f2, a2 % n, a2 / n);
+          const real* Jam = &M->Ja[((e * n3 + vM) * 3 + f / 2) * 3];
+          real nv[3] = {sgn * Jam[0], sgn * Jam[1], sgn * Jam[2]};
+          real s = RSQRT(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+          real nu[3] = {nv[0] / s, nv[1] / s, nv[2] / s};
+          const real* UM = &U[(e * n3 + vM) * 5];
+          const real* US = &U[(e2 * n3 + vS) * 5];
+          const real* qM = &w->q[(e * n3 + vM) * 6];
+          const real* qS = &w->q[(e2 * n3 + vS) * 6];
+          real fc[5], fs[5];
+          riemann(P, P->riemann, UM, qM, US, qS, nu, fc);
+          for (int k = 0; k < 5; ++k) fs[k] = fc[k] * s;
+          if (P->viscous) {
+            real fvM[5], fvS[5];
+            visc_flux(P, qM, &w->g[(e * n3 + vM) * 12], nv, fvM);
+            visc_flux(P, qS, &w->g[(e2 * n3 + vS) * 12], nv, fvS);
+            for (int k = 0; k < 5; ++k) fs[k] -= (fvM[k] + fvS[k]) / 2;
+          }
+          if (fstar_out)
+            for (int k = 0; k < 5; ++k) fstar_out[(ef * n2 + p + n * qq) * 5 + k] = fs[k];
+          for (int k = 0; k < 5; ++k) {
+            w->B[(e * n3 + vM) * 5 + k] += fs[k] / o->w[(f % 2) ? n - 1 : 0];
+            w->B[(e2 * n3 + vS) * 5 + k] -= fs[k] / o->w[(f2 % 2) ? n - 1 : 0];
+          }
+        }
+    }
+
+  /* ---- ApplyJac ---- */
+  for (long e = 0; e < E; ++e) {
+    if (want && !want[e]) continue;
+    for (long v = 0; v < n3; ++v)
+      for (int k = 0; k < 5; ++k) {
+        long x = (e * n3 + v) * 5 + k;
+        Ut[x] = -(w->Bc[x] + w->B[x]) / M->J[e * n3 + v];
+      }
+  }
+  if (alpha_out)
+    for (long e = 0; e < E; ++e) alpha_out[e] = w->alpha[e];
+  if (g_out && P->viscous)
+    for (long x = 0; x < E * n3 * 12; ++x) g_out[x] = w->g[x];
+  free(needg);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Time step and LSERK                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Carpenter-Kennedy RK4(3)5 2N-storage coefficients (Sec. 2.2 cites them) */
+static const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                               -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0,
+                               -1275806237668.0 / 842570457699.0};
+static const double RK_B[5] = {1432997174477.0 / 9575080441755.0,
+                               5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0,
+                               3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0,
+                               2526269341429.0 / 6820363218457.0,
+                               2006345519317.0 / 3224310063776.0,
+                               2802321613138.0 / 2924317926251.0};
+
+typedef void (*rhs_fn)(void* ctx, const real* U, real t, real* Ut);
+
+/* one 2N-storage step: dU = A_s dU + dt R(U); U = U + B_s dU */
+static void lserk_step(real* U, real* dU, real* Ut, long len, real t, real dt, rhs_fn f, void* ctx) {
+  for (int s = 0; s < 5; ++s) {
+    f(ctx, U, t + (real)RK_C[s] * dt, Ut);
+    for (long x = 0; x < len; ++x) {
+      dU[x] = (s == 0 ? 0 : (real)RK_A[s] * dU[x]) + dt * Ut[x];
+      U[x] = U[x] + (real)RK_B[s] * dU[x];
+    }
+  }
+}
+
+/* Time step (the paper gives no rule; reading):
+     lambda_c = sum_d (|u . Ja^d| + c |Ja^d|) / J,
+     lambda_v = max(4/3, gamma/Pr) (mu/rho) sum_d |Ja^d|^2 / J^2,
+     dt = min(CFL 2 / ((N+1)^2 max lambda_c), DFL 4 / ((N+1)^4 max lambda_v)). */
+static real time_step(const mesh_t* M, const params_t* P, const real* U, int* nonfinite) {
+  long E = M->E, n3 = M->n3;
+  real lc = 0, lv = 0;
+  int bad = 0;
+  for (long x = 0; x < E * n3; ++x) {
+    real q[6];
+    cons_to_prim(P, &U[x * 5], q);
+    real c = RSQRT(P->gamma * q[4] / q[0]);
+    real Jv = M->J[x];
+    real a = 0, b = 0;
+    for (int d = 0; d < 3; ++d) {
+      const real* j = &M->Ja[(x * 3 + d) * 3];
+      real nj2 = j[0] * j[0] + j[1] * j[1] + j[2] * j[2];
+      a += RABS(q[1] * j[0] + q[2] * j[1] + q[3] * j[2]) + c * RSQRT(nj2);
+      b += nj2;
+    }
+    a /= Jv;
+    real kv = (real)4 / 3 > P->gamma / P->Pr ? (real)4 / 3 : P->gamma / P->Pr;
+    b = kv * P->mu / q[0] * b / (Jv * Jv);
+    if (!(a == a) || !(b == b) || !(c == c)) bad = 1;
+    if (a > lc) lc = a;
+    if (b > lv) lv = b;
+  }
+  if (nonfinite) *nonfinite = bad;
+  real np1 = (real)(M->N + 1);
+  real dt = P->cfl * 2 / (np1 * np1 * lc);
+  if (P->viscous && lv > 0) {
+    real dv = P->dfl * 4 / (np1 * np1 * np1 * np1 * lv);
+    if (dv < dt) dt = dv;
+  }
+  return dt;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exported API (double at the boundary)                               */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  mesh_t M;
+  work_t w;
+  params_t P;
+} handle_t;
+
+static void to_real(const double* a, real* b, long n) { for (long i = 0; i < n; ++i) b[i] = a[i]; }
+static void to_double(const real* a, double* b, long n) { for (long i = 0; i < n; ++i) b[i] = (double)a[i]; }
+
+int ORC(ops)(int N, double* x, double* w, double* D, double* Dhat, double* Dsplit, double* Vinv) {
+  ops_t o;
+  if (build_ops(N, &o)) return -1;
+  int n = N + 1;
+  to_double(o.x, x, n);
+  to_double(o.w, w, n);
+  to_double(o.D, D, n * n);
+  to_double(o.Dhat, Dhat, n * n);
+  to_double(o.Dsplit, Dsplit, n * n);
+  to_double(o.Vinv, Vinv, n * n);
+  return 0;
+}
+
+void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, int* status) {
+  handle_t* h = (handle_t*)calloc(1, sizeof(handle_t));
+  mesh_t* M = &h->M;
+  *status = 0;
+  if (build_ops(N, &M->o)) { *status = -1; free(h); return NULL; }
+  M->N = N; M->n = N + 1; M->n2 = M->n * M->n; M->n3 = M->n2 * M->n; M->E = E;
+  for (int d = 0; d < 3; ++d) M->period[d] = period[d];
+  long n3 = M->n3;
+  M->xyz = (real*)malloc(sizeof(real) * E * n3 * 3);
+  M->Ja = (real*)malloc(sizeof(real) * E * n3 * 9);
+  M->J = (real*)malloc(sizeof(real) * E * n3);
+  M->nbr_e = (int*)malloc(sizeof(int) * E * 6);
+  M->nbr_f = (int*)malloc(sizeof(int) * E * 6);
+  M->master = (int*)malloc(sizeof(int) * E * 6);
+  M->nbr_node = (int*)malloc(sizeof(int) * E * 6 * M->n2);
+  to_real(xyz, M->xyz, E * n3 * 3);
+  int st = build_connectivity(M);
+  if (st) { *status = st; }
+  build_metrics(M);
+  if (work_alloc(M, &h->w)) *status = -5;
+  return h;
+}
+
+void ORC(mesh_free)(void* hv) {
+  handle_t* h = (handle_t*)hv;
+  if (!h) return;
+  mesh_t* M = &h->M;
+  free(M->xyz); free(M->Ja); free(M->J); free(M->nbr_e); free(M->nbr_f); free(M->master);
+  free(M->nbr_node);
+  work_free(&h->w);
+  free(h);
+}
+
+void ORC(connectivity)(void* hv, int* nbr_e, int* nbr_f, int* master, int* nbr_node) {
+  mesh_t* M = &((handle_t*)hv)->M;
+  long F = M->E * 6;
+  memcpy(nbr_e, M->nbr_e, sizeof(int) * F);
+  memcpy(nbr_f, M->nbr_f, sizeof(int) * F);
+  memcpy(master, M->master, sizeof(int) * F);
+  memcpy(nbr_node, M->nbr_node, sizeof(int) * F * M->n2);
+}
+
+void ORC(metrics)(void* hv, double* Ja, double* J) {
+  mesh_t* M = &((handle_t*)hv)->M;
+  to_double(M->Ja, Ja, M->E * M->n3 * 9);
+  to_double(M->J, J, M->E * M->n3);
+}
+
+static real* conv_state(const mesh_t* M, const double* U) {
+  long len = M->E * M->n3 * 5;
+  real* r = (real*)malloc(sizeof(real) * len);
+  to_real(U, r, len);
+  return r;
+}
+
+int ORC(rhs)(void* hv, const double* prm, const double* U, double* Ut, const unsigned char* want,
+             double* alpha, double* grad, double* fstar) {
+  handle_t* h = (handle_t*)hv;
+  mesh_t* M = &h->M;
+  params_t P = read_params(prm);
+  long len = M->E * M->n3 * 5;
+  real* Ur = conv_state(M, U);
+  real* Utr = (real*)calloc(len, sizeof(real));
+  real* al = alpha ? (real*)calloc(M->E, sizeof(real)) : NULL;
+  real* gr = grad ? (real*)calloc(M->E * M->n3 * 12, sizeof(real)) : NULL;
+  real* fr = fstar ? (real*)calloc(M->E * 6 * M->n2 * 5, sizeof(real)) : NULL;
+  int st = rhs_impl(M, &P, Ur, Utr, want, al, gr, fr, &h->w);
+  if (fr) { to_double(fr, fstar, M->E * 6 * M->n2 * 5); free(fr); }
+  for (long x = 0; x < len; ++x) Ut[x] = (double)Utr[x];
+  if (al) { to_double(al, alpha, M->E); free(al); }
+  if (gr) { to_double(gr, grad, M->E * M->n3 * 12); free(gr); }
+  free(Ur);
+  free(Utr);
+  return st;
+}
+
+typedef struct { handle_t* h; params_t P; } dgctx_t;
+static void dg_rhs_cb(void* c, const real* U, real t, real* Ut) {
+  dgctx_t* x = (dgctx_t*)c;
+  (void)t;
+  rhs_impl(&x->h->M, &x->P, U, Ut, NULL, NULL, NULL, NULL, &x->h->w);
+}
+
+double ORC(dt)(void* hv, const double* prm, const double* U, int* nonfinite) {
+  handle_t* h = (handle_t*)hv;
+  params_t P = read_params(prm);
+  real* Ur = conv_state(&h->M, U);
+  real dt = time_step(&h->M, &P, Ur, nonfinite);
+  free(Ur);
+  return (double)dt;
+}
+
+/* n_steps LSERK steps; dt_fixed > 0 uses that step, else the CFL rule each step */
+int ORC(step)(void* hv, const double* prm, double* U, int n_steps, double dt_fixed, double* t_io,
+              double* dt_last) {
+  handle_t* h = (handle_t*)hv;
+  mesh_t* M = &h->M;
+  dgctx_t c = {h, read_params(prm)};
+  long len = M->E * M->n3 * 5;
+  real* Ur = conv_state(M, U);
+  real* dU = (real*)calloc(len, sizeof(real));
+  real* Ut = (real*)calloc(len, sizeof(real));
+  real t = *t_io, dt = 0;
+  int st = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    int bad = 0;
+    dt = dt_fixed > 0 ? (real)dt_fixed : time_step(M, &c.P, Ur, &bad);
+    if (bad) { st = -5; break; }
+    lserk_step(Ur, dU, Ut, len, t, dt, dg_rhs_cb, &c);
+    t += dt;
+  }
+  to_double(Ur, U, len);
+  *t_io = (double)t;
+  if (dt_last) *dt_last = (double)dt;
+  free(Ur); free(dU); free(Ut);
+  return st;
+}
+
+/* E_k = 1/(2|Omega|) int rho |u|^2 and dE_k/dt = 1/|Omega| int (u.(rho u)_t - |u|^2 rho_t / 2)
+   by LGL quadrature (Sec. 5.2, with rho0 = U0 = 1) */
+void ORC(kinetic)(void* hv, const double* U, const double* Ut, double* out) {
+  mesh_t* M = &((handle_t*)hv)->M;
+  int n = M->n;
+  real vol = 0, ek = 0, rate = 0;
+  for (long e = 0; e < M->E; ++e)
+    for (long v = 0; v < M->n3; ++v) {
+      int i = (int)(v % n), j = (int)((v / n) % n), k = (int)(v / ((long)n * n));
+      real wq = M->o.w[i] * M->o.w[j] * M->o.w[k] * M->J[e * M->n3 + v];
+      const double* u = &U[(e * M->n3 + v) * 5];
+      real r = u[0], vx = u[1] / r, vy = u[2] / r, vz = u[3] / r;
+      real v2 = vx * vx + vy * vy + vz * vz;
+      vol += wq;
+      ek += wq * r * v2 / 2;
+      if (Ut) {
+        const double* ut = &Ut[(e * M->n3 + v) * 5];
+        rate += wq * (vx * ut[1] + vy * ut[2] + vz * ut[3] - v2 * ut[0] / 2);
+      }
+    }
+  out[0] = (double)(ek / vol);
+  out[1] = (double)(rate / vol);
+  out[2] = (double)vol;
+}
+
+/* ---- point-wise hooks for the pin tests ---- */
+void ORC(point_flux)(const double* prm, int kind, const double* UL, const double* UR,
+                     const double* nv, double* f) {
+  params_t P = read_params(prm);
+  real uL[5], uR[5], qL[6], qR[6], n[3], fr[5];
+  to_real(UL, uL, 5);
+  to_real(UR, uR, 5);
+  to_real(nv, n, 3);
+  cons_to_prim(&P, uL, qL);
+  cons_to_prim(&P, uR, qR);
+  if (kind == 0) roe_flux(&P, uL, qL, uR, qR, n, fr);
+  else if (kind == 1) lf_flux(&P, uL, qL, uR, qR, n, fr);
+  else if (kind == 2) kep_flux(uL, qL, uR, qR, n, fr);
+  else euler_flux(uL, qL, n, fr);
+  to_double(fr, f, 5);
+}
+
+void ORC(point_visc)(const double* prm, const double* U, const double* g, const double* nv, double* f) {
+  params_t P = read_params(prm);
+  real u[5], q[6], gg[12], n[3], fr[5];
+  to_real(U, u, 5);
+  to_real(g, gg, 12);
+  to_real(nv, n, 3);
+  cons_to_prim(&P, u, q);
+  visc_flux(&P, q, gg, n, fr);
+  to_double(fr, f, 5);
+}
+
+/* indicator of one element's state U[n3][5] at degree N */
+double ORC(indicator)(int N, const double* prm, const double* U, double* E_out) {
+  static mesh_t M;
+  if (build_ops(N, &M.o)) return -1;
+  M.N = N; M.n = N + 1; M.n2 = M.n * M.n; M.n3 = M.n2 * M.n;
+  params_t P = read_params(prm);
+  real q[NMAX * NMAX * NMAX * 6], u[5];
+  for (long v = 0; v < M.n3; ++v) {
+    to_real(&U[v * 5], u, 5);
+    cons_to_prim(&P, u, &q[v * 6]);
+  }
+  real Ei = 0;
+  real a = indicator(&M, &P, q, &Ei);
+  if (E_out) *E_out = (double)Ei;
+  return (double)a;
+}
+
+/* LSERK on scalar ODEs, for the order and stability-polynomial pins.
+   kind 0: y' = lam y;  kind 1: y' = -y^2 + cos(t) */
+typedef struct { int kind; real lam; } odectx_t;
+static void ode_cb(void* c, const real* y, real t, real* yt) {
+  odectx_t* o = (odectx_t*)c;
+  if (o->kind == 0) yt[0] = o->lam * y[0];
+  else yt[0] = -y[0] * y[0] + (real)cos((double)t);
+}
+double ORC(lserk_ode)(int kind, double lam, double y0, double dt, int n_steps) {
+  odectx_t c = {kind, (real)lam};
+  real y = y0, dy = 0, yt = 0, t = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    lserk_step(&y, &dy, &yt, 1, t, (real)dt, ode_cb, &c);
+    t += dt;
+  }
+  return (double)y;
+}
+
+void ORC(rk_coeffs)(double* A, double* B, double* C) {
+  for (int s = 0; s < 5; ++s) { A[s] = RK_A[s]; B[s] = RK_B[s]; C[s] = RK_C[s]; }
+}

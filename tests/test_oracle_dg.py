@@ -1,0 +1,296 @@
+"""Pins for the oracle's DG operator and time integration as a whole.
+
+* free-stream preservation on curved, rotated, renumbered meshes (Roe and LF,
+  viscous on and off, FV blending on) -- the property the curl-form metrics
+  and the averaged-metric two-point flux exist for (Sec. 2.2);
+* discrete conservation of mass, momentum and energy on periodic meshes;
+* invariance under element renumbering and rotation of local frames;
+* consistency with the exact PDE: R(U) of a smooth state converges to the
+  symbolic -div(F_c - F_v) (Eq. nse, stress, Fourier law), which fails for a
+  dropped term, a wrong sign, a transposed metric or a wrong viscous constant;
+* convergence of an advected density wave (an exact Euler solution) at the
+  order the paper reports for the split form (Sec. 5.1);
+* the five-stage LSERK: stability polynomial and observed fourth order;
+* the time-step rule on a case with a closed form;
+* kinetic energy (Sec. 5.2) for the Version-I TGV (exactly 1/8) and its rate;
+* the indicator's limiting cases and the FV-blended scheme on the Sod tube
+  against the exact Riemann solution.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2404_12703_gb300 import workloads as W
+
+from exact_solutions import sod_exact
+
+
+def quad_weights(N):
+    x, w, *_ = O.ops(N)
+    return np.einsum("i,j,k->kji", w, w, w).reshape(-1)
+
+
+def flux_scale(U, N):
+    """max |Euler flux| times max row-sum of |Dsplit|: the size of the terms the
+    volume integral sums, used to scale round-off bounds."""
+    _, _, _, _, Ds, _ = O.ops(N)
+    r = U[..., 0]
+    u2 = (U[..., 1] ** 2 + U[..., 2] ** 2 + U[..., 3] ** 2) / r
+    p = 0.4 * (U[..., 4] - 0.5 * u2)
+    F = np.abs(u2).max() + np.abs(p).max() + np.abs((U[..., 4] + p)).max()
+    return F * np.abs(Ds).sum(axis=1).max()
+
+
+@pytest.mark.parametrize("N", [3, 5, 7])
+@pytest.mark.parametrize("riemann,viscous,alpha", [("roe", False, -1), ("roe", True, -1),
+                                                   ("lf", True, -1), ("lf", False, 0.5)])
+def test_free_stream_preservation(N, riemann, viscous, alpha):
+    nel = (3, 3, 2) if N == 7 else (3, 4, 3)
+    m = W.box_mesh(N, nel, curved=0.1, seed=20240419)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    U = W.uniform_state((m["E"], (N + 1) ** 3), rho=1.1, vel=(0.4, -0.3, 0.25), p=3.0)
+    prm = O.params(riemann=riemann, viscous=viscous, shock=alpha >= 0, alpha_force=alpha)
+    Ut = M.rhs(U, prm)
+    _, J = M.metrics()
+    bound = 1e-14 * flux_scale(U, N) / J.min()
+    assert np.abs(Ut).max() < bound, (np.abs(Ut).max(), bound)
+
+
+@pytest.mark.parametrize("shock,alpha", [(False, -1), (True, 0.4), (True, -1)])
+def test_conservation(shock, alpha):
+    N = 4
+    m = W.box_mesh(N, (3, 3, 4), curved=0.1, seed=3)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    U = W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5), 0.05, 9)
+    prm = O.params(riemann="lf" if shock else "roe", shock=shock, alpha_force=alpha)
+    Ut, al = M.rhs(U, prm, with_alpha=True)
+    if shock and alpha < 0:
+        assert al.max() > 0      # the random perturbation triggers the indicator
+    _, J = M.metrics()
+    wq = quad_weights(N)[None, :, None] * J[..., None]
+    total = (wq * Ut).sum(axis=(0, 1))
+    scale = (wq * np.abs(Ut)).sum(axis=(0, 1))
+    assert np.all(np.abs(total) < 1e-13 * scale + 1e-15), total / scale
+
+
+def test_invariance_under_renumbering_and_rotation():
+    N = 3
+    nel = (3, 3, 3)
+    base = W.box_mesh(N, nel, curved=0.1)
+    turned = W.box_mesh(N, nel, curved=0.1, seed=11)
+    prm = O.params(mu=0.01)
+    Ub = W.tgv_state(base["xyz"], Ma=0.5).reshape(base["E"], -1, 5)
+    Ut_b = O.Mesh(N, base["xyz"], base["period"]).rhs(Ub, prm).reshape(base["E"], N + 1, N + 1, N + 1, 5)
+    Ut_t = O.Mesh(N, turned["xyz"], turned["period"]).rhs(
+        W.tgv_state(turned["xyz"], Ma=0.5).reshape(turned["E"], -1, 5), prm)
+    Ut_t = Ut_t.reshape(turned["E"], N + 1, N + 1, N + 1, 5)
+    idx = np.arange(N + 1)
+    I, Jj, K = np.meshgrid(idx, idx, idx, indexing="ij")
+    loc = np.stack([2 * I - N, 2 * Jj - N, 2 * K - N], axis=-1)
+    scale = np.abs(Ut_b).max(axis=(0, 1, 2, 3))
+    for e in range(turned["E"]):
+        R = W.ROTATIONS[turned["rot"][e]]
+        can = (loc @ R.T + N) // 2
+        c = turned["canon"][e]
+        mapped = Ut_b[c][can[..., 2], can[..., 1], can[..., 0]]      # [i, j, k, v]
+        got = np.transpose(Ut_t[e], (2, 1, 0, 3))                     # [i, j, k, v]
+        assert np.all(np.abs(got - mapped).max(axis=(0, 1, 2)) <= 1e-12 * scale)
+
+
+def _symbolic_rhs(mu, Pr=0.72, gamma=1.4, Rg=1.0, viscous=True):
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z", real=True)
+    rho = 1 + sp.Rational(1, 10) * sp.sin(x) * sp.cos(y) + sp.Rational(1, 20) * sp.cos(z)
+    u = sp.Rational(3, 10) + sp.Rational(1, 5) * sp.sin(y) * sp.cos(z)
+    v = -sp.Rational(1, 10) + sp.Rational(1, 5) * sp.cos(x) * sp.sin(z)
+    w = sp.Rational(3, 20) * sp.sin(x + y)
+    p = 1 + sp.Rational(1, 10) * sp.cos(x) * sp.sin(y) + sp.Rational(1, 20) * sp.sin(z)
+    X = (x, y, z)
+    vel = (u, v, w)
+    E = p / (gamma - 1) + rho * (u * u + v * v + w * w) / 2
+    T = p / (rho * Rg)
+    lam = gamma * Rg * mu / ((gamma - 1) * Pr)
+    div = sum(sp.diff(vel[i], X[i]) for i in range(3))
+    tau = [[mu * (sp.diff(vel[i], X[j]) + sp.diff(vel[j], X[i])) - (sp.Rational(2, 3) * mu * div if i == j else 0)
+            for j in range(3)] for i in range(3)]
+    res = []
+    # convective minus viscous flux divergence, sign: U_t = -div(F_c - F_v)
+    Fc = [[rho * vel[d] for d in range(3)]]
+    for i in range(3):
+        Fc.append([rho * vel[i] * vel[d] + (p if i == d else 0) for d in range(3)])
+    Fc.append([(E + p) * vel[d] for d in range(3)])
+    Fv = [[0, 0, 0]] + [[tau[i][d] for d in range(3)] for i in range(3)]
+    Fv.append([sum(tau[d][k] * vel[k] for k in range(3)) + lam * sp.diff(T, X[d]) for d in range(3)])
+    for k in range(5):
+        r = -sum(sp.diff(Fc[k][d] - (Fv[k][d] if viscous else 0), X[d]) for d in range(3))
+        res.append(sp.lambdify((x, y, z), r, "numpy"))
+    prim = [sp.lambdify((x, y, z), q, "numpy") for q in (rho, u, v, w, p)]
+    return prim, res
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_consistency_with_exact_divergence(viscous):
+    """R(U) of a smooth state converges to the exact -div(F_c - F_v)."""
+    N = 3
+    mu = 0.05
+    prim, exact = _symbolic_rhs(mu, viscous=viscous)
+    prm = O.params(mu=mu, viscous=viscous)
+    errs = []
+    for nel in (4, 8):
+        m = W.box_mesh(N, (nel,) * 3, curved=0.05, seed=nel)
+        X = m["xyz"].reshape(m["E"], -1, 3)
+        xx, yy, zz = X[..., 0], X[..., 1], X[..., 2]
+        r, u, v, w, p = (np.broadcast_to(f(xx, yy, zz), xx.shape) for f in prim)
+        U = W.prim_to_cons(r, u, v, w, p)
+        Ut = O.Mesh(N, m["xyz"], m["period"]).rhs(U, prm)
+        ref = np.stack([np.broadcast_to(f(xx, yy, zz), xx.shape) for f in exact], axis=-1)
+        errs.append(np.abs(Ut - ref).max(axis=(0, 1)) / np.abs(ref).max(axis=(0, 1)))
+    errs = np.array(errs)
+    assert np.all(errs[1] < 0.02), errs
+    # at least order N - 1 = 2 pointwise (interior nodes converge faster)
+    assert np.all(errs[1] < errs[0] / 2 ** (N - 1)), errs
+
+
+def test_density_wave_convergence():
+    """Advected density sinusoid (exact Euler solution): L2 error falls at about
+    the design order N + 1 (Sec. 5.1 reports the design order for the split form)."""
+    N = 3
+    prm = O.params(viscous=False, riemann="roe")
+    T = 0.2
+    errs = []
+    for nel in (4, 8):
+        m = W.box_mesh(N, (nel,) * 3, length=(2.0, 2.0, 2.0), origin=(-1, -1, -1), curved=0.05, seed=1)
+        M = O.Mesh(N, m["xyz"], m["period"])
+        U0 = W.density_wave_state(m["xyz"], t=0.0).reshape(m["E"], -1, 5)
+        nsteps = 20 * nel
+        U, t, _ = M.step(U0, prm, nsteps, dt=T / nsteps)
+        ex = W.density_wave_state(m["xyz"], t=T).reshape(m["E"], -1, 5)
+        _, J = M.metrics()
+        wq = quad_weights(N)[None, :] * J
+        errs.append(math.sqrt((wq * (U[..., 0] - ex[..., 0]) ** 2).sum() / wq.sum()))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > N + 0.5, (errs, rate)
+
+
+def test_lserk_order_and_stability_polynomial():
+    A, B, C = O.rk_coeffs()
+    assert A[0] == 0.0
+    # one step of y' = z y gives R(z); fit the degree-5 polynomial exactly
+    zs = np.linspace(-1.0, 1.0, 11)
+    R = np.array([O.lserk_ode(0, z, 1.0, 1.0, 1) for z in zs])
+    coef = np.polynomial.polynomial.polyfit(zs, R, 5)
+    np.testing.assert_allclose(coef[:5], [1, 1, 1 / 2, 1 / 6, 1 / 24], atol=1e-12)
+    assert 0 < coef[5] < 1 / 120            # fifth stage term, below 1/5!
+    # observed order on a nonlinear, non-autonomous ODE: y' = -y^2 + cos t
+    ref = O.lserk_ode(1, 0, 0.5, 1.0 / 4096, 4096)
+    e1 = abs(O.lserk_ode(1, 0, 0.5, 1.0 / 32, 32) - ref)
+    e2 = abs(O.lserk_ode(1, 0, 0.5, 1.0 / 64, 64) - ref)
+    assert 3.7 < math.log2(e1 / e2) < 4.5
+    # the abscissae are the running sums the 2N-storage form implies for y' = 1
+    assert abs(O.lserk_ode(0, 0, 1.0, 1.0, 1) - 1.0) < 1e-15
+
+
+def test_time_step_closed_form():
+    """Cartesian element of size h, uniform state: lambda_c = sum_d (|u_d| + c) 2/h."""
+    N = 4
+    m = W.box_mesh(N, (4, 4, 4), length=(2.0, 2.0, 2.0))
+    M = O.Mesh(N, m["xyz"], m["period"])
+    vel = (0.4, -0.3, 0.25)
+    U = W.uniform_state((m["E"], (N + 1) ** 3), rho=1.1, vel=vel, p=3.0)
+    c = math.sqrt(1.4 * 3.0 / 1.1)
+    h = 0.5
+    lam = sum(abs(v) + c for v in vel) * 2 / h
+    dt_c = 0.9 * 2 / ((N + 1) ** 2 * lam)
+    prm = O.params(viscous=False)
+    dt, bad = M.dt(U, prm)
+    assert not bad
+    assert abs(dt - dt_c) < 1e-14 * dt_c
+    # viscous limit: lambda_v = max(4/3, gamma/Pr) mu/rho sum_d (2/h)^2
+    mu = 0.5
+    lv = max(4 / 3, 1.4 / 0.72) * mu / 1.1 * 3 * (2 / h) ** 2
+    dt_v = 0.9 * 4 / ((N + 1) ** 4 * lv)
+    dt2, _ = M.dt(U, O.params(mu=mu))
+    assert abs(dt2 - min(dt_c, dt_v)) < 1e-14 * dt2
+
+
+def test_kinetic_energy_tgv_version1_and_rate():
+    N = 5
+    m = W.box_mesh(N, (4, 4, 4), curved=0.05, seed=4)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    U = W.tgv_state(m["xyz"], version=1).reshape(m["E"], -1, 5)
+    Ek, _, vol = M.kinetic(U)
+    assert abs(vol - (2 * math.pi) ** 3) < 1e-6 * vol
+    assert abs(Ek - 0.125) < 1e-5
+    # exact rate from Ut against a central difference of E_k along Ut
+    prm = O.params()
+    Ut = M.rhs(U, prm)
+    _, rate, _ = M.kinetic(U, Ut)
+    d = 1e-4
+    Ep, _, _ = M.kinetic(U + d * Ut)
+    Em, _, _ = M.kinetic(U - d * Ut)
+    assert abs(rate - (Ep - Em) / (2 * d)) < 1e-8 * max(1.0, abs(rate)) + 1e-7
+
+
+def test_indicator_limits():
+    N = 5
+    n = N + 1
+    x = W.lgl_points(N)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")      # [i, j, k]
+    def elem(rho, p):
+        U = W.prim_to_cons(rho, 0 * rho, 0 * rho, 0 * rho, p)
+        return np.transpose(U, (2, 1, 0, 3)).reshape(-1, 5)   # -> [k, j, i]
+    one = np.ones_like(X)
+    # constant state: no high modes -> alpha = 0
+    a, E = O.indicator(N, elem(one, one))
+    assert a == 0 and E < 1e-20
+    # rho p a polynomial of degree <= N-2 in every variable: E = 0 -> alpha = 0
+    a, E = O.indicator(N, elem(1 + 0.2 * X, 1 + 0.1 * Y * Z))
+    assert a == 0 and E < 1e-20
+    # a jump inside the element: alpha capped at alpha_max = 0.5
+    a, E = O.indicator(N, elem(np.where(X < 0, 1.0, 0.125), np.where(X < 0, 1.0, 0.1)))
+    assert a == 0.5 and E > 0.01
+    # rho p = Ltilde_N(x) + c with a mean: E is the top-mode energy fraction
+    c = np.zeros(n)
+    c[N] = 1.0
+    PN = np.polynomial.legendre.legval(X, c) * math.sqrt((2 * N + 1) / 2)
+    a, E = O.indicator(N, elem(one, 2 + 0.5 * PN))
+    # 3D modes: 2 = c_000 Ltilde_0^3 with Ltilde_0 = 1/sqrt(2) -> c_000 = 4 sqrt(2);
+    # 0.5 Ltilde_N(x) = c_N00 Ltilde_N(x) Ltilde_0^2 -> c_N00 = 1; E = 1 / (1 + 32)
+    assert abs(E - 1.0 / 33.0) < 1e-12
+
+
+def test_sod_tube_with_blending_converges_to_exact():
+    """FV sub-cell blending with LF fluxes on the Sod tube (inviscid): the density
+    approaches the exact Riemann solution as the mesh is refined, and the
+    indicator switches on only near the waves."""
+    N = 3
+    prm = O.params(viscous=False, riemann="lf", shock=True)
+    errs = []
+    for nx in (16, 32):
+        h = 2.0 / nx
+        m = W.box_mesh(N, (nx, 2, 2), length=(2.0, 2 * h, 2 * h), origin=(0, 0, 0))
+        M = O.Mesh(N, m["xyz"], m["period"])
+        U = W.sod_state(m["xyz"]).reshape(m["E"], -1, 5)
+        t = 0.0
+        while t < 0.2 - 1e-12:
+            dt, bad = M.dt(U, prm)
+            assert not bad
+            dt = min(dt, 0.2 - t)
+            U, t, _ = M.step(U, prm, 1, dt=dt, t=t)
+        assert np.isfinite(U).all()
+        X = m["xyz"].reshape(m["E"], -1, 3)[..., 0]
+        sel = (X > 0.5) & (X < 1.5)
+        ex = sod_exact(X[sel], 0.2, x0=1.0)
+        _, J = M.metrics()
+        wq = quad_weights(N)[None, :] * J
+        errs.append((wq[sel] * np.abs(U[..., 0][sel] - ex[:, 0])).sum() / wq[sel].sum())
+        _, al = M.rhs(U, prm, with_alpha=True)
+        xc = X.mean(axis=1)
+        # undisturbed plateau between the rarefaction fans from x = 0 and x = 1
+        assert al[(xc > 0.35) & (xc < 0.65)].max() == 0
+        # the shock (x = 1 + 1.752 t) sits in a blended element
+        assert al[np.abs(xc - 1.3504) < h].max() > 0
+    assert errs[1] < 0.8 * errs[0], errs
+    assert errs[1] < 0.05

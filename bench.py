@@ -1,0 +1,326 @@
+"""Benchmark: DOF-updates per second per RK stage of the DGSEM time step.
+
+Default workload (one GPU): Taylor-Green vortex Re = 1600, Ma = 0.1 on the
+24^3-element curved hexahedral mesh (nodes displaced by 0.1 h sin products,
+element ids and local frames permuted from seed 20240419), N = 7 (7,077,888
+DOF), KEP split form + Roe + BR1, five-stage LSERK4 with the CFL rule, FP64.
+A step is one full time step (CFL reduction + 5 stages of the whole operator).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (a
+plain FP64 C restatement of the same method, test infrastructure) on a bounded
+sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s per RK stage (FP64 vs FP32-bulk) and % HBM roofline; serving p50/p99"
+UNIT = "DOF-updates/s"
+STAGES = 5
+N_DEG = 7
+NEL = 24
+SEED = 20240419
+
+# Algorithmic cost per DOF per RK stage at N = 7 (FP64), counting an FMA as two
+# flops: split-form KEP volume with pair symmetry 567, conservative BR1 lifting
+# 612, viscous fluxes and their volume term 324, surface Riemann + BR1 fluxes
+# 131, ConsToPrim / SurfInt / ApplyJac / RK 50.
+FLOPS_PER_DOF = {"volume": 567 + 324 + 30, "lift": 612, "surf_flux": 131, "surf_prims": 10, "cfl": 10}
+# Algorithmic bytes per DOF per stage of the minimal two-phase method (FP64):
+# 8 (30 + 204 / (N + 1)).
+BYTES_PER_DOF = 8 * (30 + 204 / (N_DEG + 1))
+# DRAM bytes per DOF of one k_volume<7,1> launch, from the ncu capture summarised
+# in profiles/k_volume_tgv12_N7_fp64.md (12^3 mesh; the traffic scales with
+# the DOF count).  Set to None whenever the kernel changes until re-measured.
+VOLUME_TRAFFIC_BYTES_PER_DOF = 331.3
+
+
+def workload_desc(nel=NEL):
+    E = nel ** 3
+    dof = E * (N_DEG + 1) ** 3
+    return {
+        "workload": f"TGV Re=1600 Ma=0.1 on a {nel}^3-element curved hex mesh (0.1 h sin-product node "
+                    f"displacement, element ids and local frames permuted from seed {SEED}), N={N_DEG}, "
+                    f"{dof} DOF, KEP split form + Roe + BR1, LSERK4 (5 stages) with CFL 0.9",
+        "elements": E, "N": N_DEG, "dof": dof, "precision": "FP64",
+        "l2": f"inputs larger than L2 (state {dof * 40 / 1e6:.0f} MB, metrics {dof * 80 / 1e6:.0f} MB "
+              f"per GPU); no flush",
+    }
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 ALU peak of a GB300, derived from unit counts and clocks: 152 SMs x
+# 2 FP64 FMA lanes per SM per clock x 2 flop x 2.07 GHz = 1.26 TFLOP/s (the
+# nominal 1.25 TFLOP/s FP64 figure of the part).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def cpu_oracle_sample(steps, nel=6, seed=SEED):
+    """The oracle (plain FP64 C, single thread) on a bounded sample of the same
+    workload: a nel^3 curved, permuted mesh at N = 7, `steps` LSERK steps."""
+    import oracle as O
+    from paper_2404_12703_gb300 import workloads as W
+    m = W.box_mesh(N_DEG, (nel,) * 3, curved=0.1, seed=seed)
+    M = O.Mesh(N_DEG, m["xyz"], m["period"])
+    U = W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5)
+    prm = O.params()
+    dof = m["E"] * (N_DEG + 1) ** 3
+    times = []
+    t = 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        U, t, _ = M.step(U, prm, 1, t=t)
+        times.append(time.perf_counter() - t0)
+    return dof, times
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    nel = 6
+    dof, times = cpu_oracle_sample(args.warmup + args.steps, nel=nel)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = dof * STAGES * len(timed) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_desc(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{nel}^3 elements of the same curved N=7 TGV workload "
+                                   f"({dof} DOF), one LSERK step per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2404_12703_gb300 import build as B
+    from paper_2404_12703_gb300 import dg
+    from paper_2404_12703_gb300 import workloads as W
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    dg.load()
+
+    nel = args.nel
+    m = W.box_mesh(N_DEG, (nel,) * 3, curved=0.1, seed=SEED)
+    E = m["E"]
+    dof = E * (N_DEG + 1) ** 3
+    U0 = W.tgv_state(m["xyz"]).reshape(E, -1, 5)
+    stream = torch.cuda.Stream()
+    solver = dg.Solver(m, stream=stream)
+    solver.set_state(U0)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also captures the step graph)
+    solver.step(args.warmup)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    launches0 = dg.launch_count()
+    with Clocks(local) as clk:
+        barrier()
+        ev0.record(stream)
+        solver.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    launches = dg.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * dof * STAGES / (ms_step * 1e-3)
+    Ufinal, tfinal = solver.get_state()
+    finite = bool(np.isfinite(Ufinal).all())
+
+    # per-kernel device time over the same number of steps, eagerly launched
+    # with CUDA events on the solver's stream
+    prof = solver.profile_step(args.steps)
+    tot_ms = sum(v[0] for v in prof.values())
+    kernels = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1],
+                   "share": (v[0] / tot_ms if tot_ms else None)} for k, v in prof.items()}
+    vol_ms = kernels["volume"]["ms_per_launch"]
+    vol_flops = FLOPS_PER_DOF["volume"] * dof
+    achieved_tf = vol_flops / (vol_ms * 1e-3) / 1e12
+    peaks, peak_src = measured_peaks()
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                "traffic": (VOLUME_TRAFFIC_BYTES_PER_DOF * dof if VOLUME_TRAFFIC_BYTES_PER_DOF else None),
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                "12^3 capture scaled by DOF)",
+                "kernel": "k_volume<7,1> (split-form KEP volume integral + viscous volume term + SurfInt "
+                          "+ ApplyJac + RK update)",
+                "peak_source": "FP64 FMA peak derived from unit counts and clocks (152 SM x 2 DFMA/clk x "
+                               "2 flop x 2.07 GHz)",
+                "hbm": {"algorithmic_bytes_per_dof": BYTES_PER_DOF,
+                        "achieved_gbs": BYTES_PER_DOF * dof * STAGES / (ms_step * 1e-3) / 1e9,
+                        "peak_gbs": peaks.get("hbm_gbs"), "peak_source": peak_src}}
+    roofline["hbm"]["frac"] = roofline["hbm"]["achieved_gbs"] / roofline["hbm"]["peak_gbs"]
+    total_flops = sum(FLOPS_PER_DOF.values()) * dof * STAGES
+    roofline["whole_step_fp64_frac"] = total_flops / (ms_step * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
+
+    # end to end through the public API with host buffers: per step, upload the
+    # state from pinned host memory, advance one step, read the state back
+    pinned_in = torch.from_numpy(U0.reshape(-1)).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    Uh_in = pinned_in.numpy()
+    Uh_out = pinned_out.numpy()
+    e2e_steps = max(1, min(args.steps, 5))
+    solver.set_state(Uh_in)
+    solver.step(1)
+    solver.get_state(Uh_out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_state(Uh_in)
+        solver.step(1)
+        solver.get_state(Uh_out)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    nbytes = dof * 5 * 8
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cdof, ctimes = cpu_oracle_sample(2, nel=4)
+        cval = cdof * STAGES * len(ctimes) / sum(ctimes)
+        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"4^3 elements of the same curved N=7 TGV workload ({cdof} DOF), 2 LSERK steps, "
+                         f"single-threaded FP64 C"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_desc(nel),
+            "pid_s": 1.0 / (value / world), "finite": finite, "t_end": tfinal,
+            "gpu_launches": launches, "kernels": kernels, "roofline": roofline,
+            "e2e": {"value": world * dof * STAGES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
+            "clocks": clk.summary(), "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nel", type=int, default=NEL,
+                    help="elements per direction (24 is the benchmark workload; smaller for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

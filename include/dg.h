@@ -1,0 +1,185 @@
+/*
+ * dg.h -- C ABI of libdg: the DGSEM time derivative Ut = R(U) of the
+ * compressible Navier-Stokes equations on unstructured, curved hexahedral
+ * meshes and its low-storage Runge-Kutta time stepping, on one NVIDIA GB300
+ * (sm_103a).  The method is that of GALAEXI (arXiv 2404.12703):
+ *
+ *   Sec. 2.1  Eq. nse, stress tensor, Fourier law, Eqs. eos_p / eos_T
+ *   Sec. 2.2  curl-form metrics, Eq. transformed_goveq, Eq. weak_form,
+ *             Eq. ansatz (LGL nodes), Eq. dgsem (VolInt, FillFlux, SurfInt,
+ *             ApplyJac), split-form KEP volume integral, BR1 lifting
+ *             (Eq. lifting), five-stage low-storage RK (Time integration)
+ *   Sec. 2.3  a-priori indicator and convex DG / FV sub-cell blending
+ *   Sec. 3.3  / App. A  ProlongToFace, FillFlux, SurfInt, ApplyJac
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns a status (DG_OK = 0, negative on error).  Nothing
+ *    throws across the ABI.  After an error the context keeps its last
+ *    consistent state; dg_last_error() gives a human-readable message.
+ *  - Node index inside an element: node = i + n*(j + n*k), n = N + 1,
+ *    i along the element's local xi direction.  Public state layout:
+ *    U[e][node][v], v = (rho, rho u, rho v, rho w, rho e), float64.
+ *  - Input pointers are borrowed for the duration of the call only.  Output
+ *    buffers belong to the caller.  The library owns (and frees in
+ *    dg_destroy) all device memory it allocates.
+ *  - "Device pointer" means memory on the device the context was created on.
+ *    Work is enqueued on the context's stream (see dg_init_mesh); calls that
+ *    return data to the host synchronise that stream.
+ *  - Only closed (e.g. triply periodic) meshes are supported: every face must
+ *    have exactly one partner face with the same four distinct corner ids.
+ *    A periodic direction therefore needs at least three elements: with two,
+ *    the faces across the other directions of both layers share all corner ids.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,        /* invalid argument (null pointer, N out of range, ...) */
+  DG_ERR_MESH = -2,       /* mesh is not a closed, consistent hex mesh          */
+  DG_ERR_OOM = -3,        /* device allocation failed                           */
+  DG_ERR_CUDA = -4,       /* a CUDA runtime call failed                         */
+  DG_ERR_NONFINITE = -5,  /* the time-step reduction met a NaN / Inf            */
+  DG_ERR_TIMEOUT = -6,    /* a bounded device-side wait gave up                 */
+  DG_ERR_STATE = -7,      /* call not valid in the context's current state      */
+  DG_PENDING = 1          /* serving: request not finished yet                  */
+};
+
+enum { DG_RIEMANN_ROE = 0, DG_RIEMANN_LF = 1 };
+enum { DG_FP64 = 0, DG_FP32_BULK = 1 };
+
+/* Physical and numerical parameters (Sec. 2.1 - 2.3). */
+typedef struct {
+  double gamma;          /* ratio of specific heats                               */
+  double R;              /* specific gas constant                                 */
+  double Pr;             /* Prandtl number                                        */
+  double mu;             /* constant dynamic viscosity                            */
+  int riemann;           /* DG_RIEMANN_ROE (no entropy fix) or DG_RIEMANN_LF      */
+  int viscous;           /* 0: Euler; 1: Navier-Stokes with BR1 lifting            */
+  int shock_capturing;   /* 1: Hennemann indicator + FV sub-cell blending         */
+  double alpha_min;      /* blending factors below this are set to 0              */
+  double alpha_max;      /* upper bound of the blending factor                    */
+  double cfl, dfl;       /* convective / viscous time-step factors                */
+  int precision;         /* DG_FP64 or DG_FP32_BULK                               */
+  double alpha_force;    /* < 0: use the indicator; >= 0: every element uses this
+                            blending factor (verification)                       */
+} dg_params;
+
+/* Fills p with the defaults: gamma 1.4, R 1, Pr 0.72, mu 1/1600, Roe, viscous,
+   no shock capturing, alpha in [1e-3, 0.5], CFL = DFL = 0.9, FP64. */
+void dg_default_params(dg_params* p);
+
+/* Mesh description (host memory).
+   corner_vid[e][c]: vertex id of corner c = bi + 2 bj + 4 bk of element e,
+     where bi = 0 for i = 0 and 1 for i = N (likewise j, k).  Faces are
+     matched by their sets of corner ids; periodic images must share ids.
+   xyz[e][node][3]: physical coordinates of the LGL nodes (Eq. ansatz). */
+typedef struct {
+  int N;                       /* polynomial degree, 1 <= N <= 7 */
+  int64_t n_elems;             /* number of elements E >= 1      */
+  const int64_t* corner_vid;   /* [E][8] host                    */
+  const double* xyz;           /* [E][(N+1)^3][3] host            */
+} dg_mesh_desc;
+
+typedef struct dg_ctx dg_ctx;
+
+/* Builds a context for one mesh on the current CUDA device.
+   On the device: element<->side maps with face orientation (flip) found from
+   corner ids (Sec. 2.2 "unstructured mesh topology", App. A ProlongToFace),
+   curl-form metrics J a^i and J (Sec. 2.2, Mapping the Equations) formed in
+   double-double and rounded, surface normals and surface elements.
+   stream: a cudaStream_t (NULL = legacy default stream) on which all later
+   work of this context is enqueued.  The call synchronises before returning.
+   Errors: DG_ERR_ARG for bad sizes, DG_ERR_MESH if faces do not pair up or a
+   face's orientation cannot be determined, DG_ERR_OOM / DG_ERR_CUDA.
+   On error *out is set to NULL. */
+int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params, void* stream);
+
+/* Changes the stream later work is enqueued on. */
+int dg_set_stream(dg_ctx* ctx, void* stream);
+
+/* Replaces the parameters (same mesh).  The precision may be changed too. */
+int dg_set_params(dg_ctx* ctx, const dg_params* params);
+
+/* Copies a state into the context and sets the time t.
+   U: [E][node][5] float64, on the host (on_device = 0) or the device (1).
+   Stream-ordered; a host source is copied before the call returns. */
+int dg_set_state(dg_ctx* ctx, const double* U, int on_device, double t);
+
+/* Copies the context's state out and reports its time (either may be NULL).
+   Synchronises the context's stream.  Returns DG_ERR_NONFINITE if a time step
+   since the last dg_set_state met a non-finite value. */
+int dg_get_state(dg_ctx* ctx, double* U, int on_device, double* t);
+
+/* Ut = R(U), Eq. dgsem with the split-form volume integral, BR1 lifting and
+   (if enabled) sub-cell blending, for the state U_dev (device, public layout)
+   or the context's own state when U_dev is NULL.  Ut_dev: caller-owned device
+   buffer [E][node][5].  Stream-ordered (asynchronous). */
+int dg_rhs(dg_ctx* ctx, const double* U_dev, double* Ut_dev);
+
+/* Advances the context's state by n_steps steps of the five-stage
+   low-storage RK4 (Sec. 2.2, Time integration).  dt > 0: fixed step;
+   dt <= 0: each step uses the CFL rule evaluated on the device from the
+   step's initial state.  Stream-ordered (asynchronous, graph-launched). */
+int dg_step(dg_ctx* ctx, int n_steps, double dt);
+
+/* Same work as dg_step, launched kernel by kernel (no graph) with CUDA events
+   recorded on the context's stream around every launch.  Accumulates, per
+   kernel kind k, the summed device time ms[k] and the launch count
+   launches[k]: k = 0 CFL reduction, 1 BR1 surface prolongation, 2 lifting,
+   3 surface flux, 4 volume integral + SurfInt + ApplyJac + RK update.  Both
+   arrays have 5 entries.  Synchronises after every step. */
+int dg_profile_step(dg_ctx* ctx, int n_steps, double dt, double* ms, int64_t* launches);
+
+/* Time step the CFL rule gives for the context's state (synchronises). */
+int dg_time_step(dg_ctx* ctx, double* dt);
+
+/* Kinetic energy E_k = 1/(2|Omega|) int rho |u|^2 and its exact rate from the
+   right-hand side, dE_k/dt = 1/|Omega| int (u.(rho u)_t - |u|^2 rho_t / 2)
+   (Sec. 5.2), of the context's state; out[0] = E_k, out[1] = dE_k/dt,
+   out[2] = |Omega|.  FP64 reductions on the device; synchronises. */
+int dg_kinetic(dg_ctx* ctx, double* out);
+
+/* Verification access to intermediate arrays (device buffers, caller-owned).
+   what = DG_DEBUG_METRICS: out0 = Ja [E][node][3][3] ((J a^d)_c at [d][c]),
+                            out1 = J [E][node]
+   what = DG_DEBUG_MAPS:    out0 = int32 [E][6][3] (neighbour element,
+                            neighbour face, 1 if this side is the master),
+                            out1 = int32 [E][6][n^2] partner face node
+   what = DG_DEBUG_GRAD:    out0 = lifted gradients [E][node][4][3] of the
+                            last dg_rhs / stage (d(u,v,w,T)/dx_c)
+   what = DG_DEBUG_FSTAR:   out0 = surface flux times s-hat [E][6][n^2][5]
+                            on master faces (zero on slave faces), face node
+                            p + n q in the master's face frame, last dg_rhs
+   what = DG_DEBUG_ALPHA:   out0 = blending factor [E] of the last dg_rhs
+   Synchronises. */
+enum { DG_DEBUG_METRICS = 0, DG_DEBUG_MAPS = 1, DG_DEBUG_GRAD = 2, DG_DEBUG_FSTAR = 3,
+       DG_DEBUG_ALPHA = 4 };
+int dg_debug(dg_ctx* ctx, int what, void* out0, void* out1);
+
+/* Basic sizes of a context. */
+int dg_sizes(const dg_ctx* ctx, int* N, int64_t* n_elems, int64_t* n_sides, int64_t* bytes);
+
+/* Releases every device allocation of the context.  NULL is ignored. */
+void dg_destroy(dg_ctx* ctx);
+
+/* Static description of an error code, and the last error message of this
+   thread (never NULL). */
+const char* dg_error_string(int code);
+const char* dg_last_error(void);
+
+/* Number of kernel launches the library has enqueued since load (all
+   contexts), for launch accounting in benchmarks. */
+int64_t dg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

@@ -67,7 +67,7 @@ def _lib(quad: bool = False):
 
         api = {
             "ops": fn("ops", C.c_int, [C.c_int, dp, dp, dp, dp, dp, dp]),
-            "mesh_new": fn("mesh_new", C.c_void_p, [C.c_int, C.c_long, dp, dp, ip]),
+            "mesh_new": fn("mesh_new", C.c_void_p, [C.c_int, C.c_long, dp, dp, C.c_void_p, ip]),
             "mesh_free": fn("mesh_free", None, [C.c_void_p]),
             "connectivity": fn("connectivity", None, [C.c_void_p, ip, ip, ip, ip]),
             "metrics": fn("metrics", None, [C.c_void_p, dp, dp]),
@@ -155,7 +155,10 @@ def rk_coeffs():
 class Mesh:
     """Oracle view of one mesh: connectivity, metrics and the DG operator."""
 
-    def __init__(self, N, xyz, period, quad=False):
+    def __init__(self, N, xyz, period, quad=False, metric_mask=None):
+        """``metric_mask``: optional boolean mask over elements; metrics are then
+        formed only for those elements and their face neighbours (use the same
+        mask as ``want`` in ``rhs``)."""
         self.N = int(N)
         self.n = self.N + 1
         xyz = _f64(xyz)
@@ -163,7 +166,11 @@ class Mesh:
         self.quad = quad
         self._api = _lib(quad)
         st = C.c_int(0)
-        self._h = self._api["mesh_new"](self.N, self.E, _dp(xyz.reshape(-1)), _dp(_f64(period)), C.byref(st))
+        mask = None
+        if metric_mask is not None:
+            mask = np.ascontiguousarray(np.asarray(metric_mask, dtype=np.uint8))
+        self._h = self._api["mesh_new"](self.N, self.E, _dp(xyz.reshape(-1)), _dp(_f64(period)),
+                                        mask.ctypes.data if mask is not None else None, C.byref(st))
         self.status = st.value
         if self.status != 0:
             self.close()

@@ -104,52 +104,57 @@ static params_t read_params(const double* p) {
 /* 1D operators                                                        */
 /* ------------------------------------------------------------------ */
 
+/* The 1D operators are formed in long double and rounded to REAL, so that
+   they are (nearly) correctly rounded: at low Mach numbers the row sums of D
+   multiply a large background pressure, and a few ulp of difference in D
+   would otherwise dominate the comparison with another implementation. */
+typedef long double oreal;
+
 /* Legendre polynomial P_N and derivative by the three-term recurrence. */
-static void legendre(int N, real x, real* P, real* dP) {
-  real p0 = 1, p1 = x, d0 = 0, d1 = 1;
+static void legendre(int N, oreal x, oreal* P, oreal* dP) {
+  oreal p0 = 1, p1 = x, d1 = 1;
   if (N == 0) { *P = 1; *dP = 0; return; }
   for (int k = 2; k <= N; ++k) {
-    real p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
-    real d2 = k * p1 + x * d1;   /* P_k' = k P_{k-1} + x P_{k-1}' */
-    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+    oreal p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+    oreal d2 = k * p1 + x * d1;   /* P_k' = k P_{k-1} + x P_{k-1}' */
+    p0 = p1; p1 = p2; d1 = d2;
   }
-  (void)d0;
   *P = p1;
   *dP = d1;
 }
 
 /* LGL nodes: -1, +1 and the roots of P_N'; weights 2 / (N (N+1) P_N(x)^2). */
-static void lgl(int N, real* x, real* w) {
+static void lgl(int N, oreal* x, oreal* w) {
   x[0] = -1;
   x[N] = 1;
   for (int j = 1; j < N; ++j) {
-    real t = -cos(M_PI * (double)j / (double)N);
+    oreal t = -cosl(M_PI * (long double)j / (long double)N);
     for (int it = 0; it < 200; ++it) {
-      real P, dP;
+      oreal P, dP;
       legendre(N, t, &P, &dP);
       /* Legendre ODE: (1 - x^2) P'' = 2 x P' - N (N+1) P */
-      real d2P = (2 * t * dP - (real)N * (N + 1) * P) / (1 - t * t);
-      real dt = dP / d2P;
+      oreal d2P = (2 * t * dP - (oreal)N * (N + 1) * P) / (1 - t * t);
+      oreal dt = dP / d2P;
       t -= dt;
-      if (RABS(dt) <= 4 * REPS) break;
+      if (fabsl(dt) <= 4 * LDBL_EPSILON) break;
     }
     x[j] = t;
   }
   for (int j = 0; j <= N; ++j) {
-    real P, dP;
+    oreal P, dP;
     legendre(N, x[j], &P, &dP);
-    w[j] = 2 / ((real)N * (N + 1) * P * P);
+    w[j] = 2 / ((oreal)N * (N + 1) * P * P);
   }
 }
 
 /* D[i][j] = l_j'(x_i) with l_j(x) = prod_{m != j} (x - x_m) / (x_j - x_m). */
-static void lagrange_derivative(int n, const real* x, real* D) {
+static void lagrange_derivative(int n, const oreal* x, oreal* D) {
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
-      real s = 0;
+      oreal s = 0;
       for (int m = 0; m < n; ++m) {
         if (m == j) continue;
-        real prod = 1 / (x[j] - x[m]);
+        oreal prod = 1 / (x[j] - x[m]);
         for (int k = 0; k < n; ++k) {
           if (k == j || k == m) continue;
           prod *= (x[i] - x[k]) / (x[j] - x[k]);
@@ -161,8 +166,8 @@ static void lagrange_derivative(int n, const real* x, real* D) {
 }
 
 /* Gauss-Jordan inverse with partial pivoting of an n x n matrix. */
-static int invert(int n, const real* A, real* Ainv) {
-  real a[NMAX * 2 * NMAX];
+static int invert(int n, const oreal* A, oreal* Ainv) {
+  oreal a[NMAX * 2 * NMAX];
   int m = 2 * n;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < m; ++j)
@@ -170,17 +175,17 @@ static int invert(int n, const real* A, real* Ainv) {
   for (int c = 0; c < n; ++c) {
     int piv = c;
     for (int r = c + 1; r < n; ++r)
-      if (RABS(a[r * m + c]) > RABS(a[piv * m + c])) piv = r;
+      if (fabsl(a[r * m + c]) > fabsl(a[piv * m + c])) piv = r;
     if (a[piv * m + c] == 0) return -1;
     if (piv != c)
       for (int j = 0; j < m; ++j) {
-        real t = a[c * m + j]; a[c * m + j] = a[piv * m + j]; a[piv * m + j] = t;
+        oreal t = a[c * m + j]; a[c * m + j] = a[piv * m + j]; a[piv * m + j] = t;
       }
-    real d = a[c * m + c];
+    oreal d = a[c * m + c];
     for (int j = 0; j < m; ++j) a[c * m + j] /= d;
     for (int r = 0; r < n; ++r) {
       if (r == c) continue;
-      real f = a[r * m + c];
+      oreal f = a[r * m + c];
       for (int j = 0; j < m; ++j) a[r * m + j] -= f * a[c * m + j];
     }
   }
@@ -196,6 +201,7 @@ typedef struct {
   real Dhat[NMAX * NMAX];   /* Dhat[i][a] = -(w_a / w_i) D[a][i]           */
   real Dsplit[NMAX * NMAX]; /* 2 D[i][a] - d_iN d_aN / w_N + d_i0 d_a0 / w_0 */
   real Vinv[NMAX * NMAX];   /* inverse of V[i][m] = Ltilde_m(x_i)          */
+  oreal Dl[NMAX * NMAX];    /* D in long double, for the metrics          */
 } ops_t;
 
 static int build_ops(int N, ops_t* o) {
@@ -203,25 +209,29 @@ static int build_ops(int N, ops_t* o) {
   int n = N + 1;
   o->N = N;
   o->n = n;
-  lgl(N, o->x, o->w);
-  lagrange_derivative(n, o->x, o->D);
+  oreal x[NMAX], w[NMAX], V[NMAX * NMAX], Vi[NMAX * NMAX];
+  lgl(N, x, w);
+  lagrange_derivative(n, x, o->Dl);
+  for (int i = 0; i < n; ++i) { o->x[i] = (real)x[i]; o->w[i] = (real)w[i]; }
   for (int i = 0; i < n; ++i)
     for (int a = 0; a < n; ++a) {
-      o->Dhat[i * n + a] = -(o->w[a] / o->w[i]) * o->D[a * n + i];
-      real ds = 2 * o->D[i * n + a];
-      if (i == N && a == N) ds -= 1 / o->w[N];
-      if (i == 0 && a == 0) ds += 1 / o->w[0];
-      o->Dsplit[i * n + a] = ds;
+      o->D[i * n + a] = (real)o->Dl[i * n + a];
+      o->Dhat[i * n + a] = (real)(-(w[a] / w[i]) * o->Dl[a * n + i]);
+      oreal ds = 2 * o->Dl[i * n + a];
+      if (i == N && a == N) ds -= 1 / w[N];
+      if (i == 0 && a == 0) ds += 1 / w[0];
+      o->Dsplit[i * n + a] = (real)ds;
     }
   /* orthonormal Legendre modes Ltilde_m = sqrt((2m+1)/2) P_m */
-  real V[NMAX * NMAX];
   for (int i = 0; i < n; ++i)
     for (int m = 0; m < n; ++m) {
-      real P, dP;
-      legendre(m, o->x[i], &P, &dP);
-      V[i * n + m] = RSQRT((real)(2 * m + 1) / 2) * P;
+      oreal P, dP;
+      legendre(m, x[i], &P, &dP);
+      V[i * n + m] = sqrtl((oreal)(2 * m + 1) / 2) * P;
     }
-  return invert(n, V, o->Vinv);
+  if (invert(n, V, Vi)) return -1;
+  for (int i = 0; i < n * n; ++i) o->Vinv[i] = (real)Vi[i];
+  return 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -383,50 +393,22 @@ static mreal mline(int n, const mreal* Dm, const mreal* fld, int stride, long v,
   return s;
 }
 
-static void build_metrics(mesh_t* M) {
+/* need: NULL for every element, else a 0/1 mask of the elements whose metrics
+   are formed (the others are left as NaN). */
+static void build_metrics(mesh_t* M, const unsigned char* need) {
   int n = M->n, n3 = M->n3;
-  /* 1D derivative matrix in long double, from long-double LGL nodes */
-  mreal xm[NMAX], Dm[NMAX * NMAX];
-  {
-    /* repeat the node / derivative construction in long double */
-    int N = M->N;
-    xm[0] = -1;
-    xm[N] = 1;
-    for (int j = 1; j < N; ++j) {
-      mreal t = -cosl(M_PI * (long double)j / (long double)N);
-      for (int it = 0; it < 200; ++it) {
-        mreal p0 = 1, p1 = t, d1 = 1;
-        for (int k = 2; k <= N; ++k) {
-          mreal p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
-          mreal d2 = k * p1 + t * d1;
-          p0 = p1; p1 = p2; d1 = d2;
-        }
-        mreal d2P = (2 * t * d1 - (mreal)N * (N + 1) * p1) / (1 - t * t);
-        mreal dt = d1 / d2P;
-        t -= dt;
-        if (fabsl(dt) <= 4 * LDBL_EPSILON) break;
-      }
-      xm[j] = t;
-    }
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        mreal s = 0;
-        for (int m = 0; m < n; ++m) {
-          if (m == j) continue;
-          mreal prod = 1 / (xm[j] - xm[m]);
-          for (int k = 0; k < n; ++k) {
-            if (k == j || k == m) continue;
-            prod *= (xm[i] - xm[k]) / (xm[j] - xm[k]);
-          }
-          s += prod;
-        }
-        Dm[i * n + j] = s;
-      }
-  }
+  const mreal* Dm = M->o.Dl;
   mreal* dx = (mreal*)malloc(sizeof(mreal) * 9 * n3);   /* dx[v][c][d] = d x_c / d xi_d */
   mreal* V = (mreal*)malloc(sizeof(mreal) * 3 * n3);    /* V[v][d]                    */
   mreal* X = (mreal*)malloc(sizeof(mreal) * 3 * n3);
   for (long e = 0; e < M->E; ++e) {
+    if (need && !need[e]) {
+      for (long v = 0; v < n3; ++v) {
+        M->J[e * n3 + v] = NAN;
+        for (int k = 0; k < 9; ++k) M->Ja[(e * n3 + v) * 9 + k] = NAN;
+      }
+      continue;
+    }
     /* the curl form is invariant under a translation of the coordinates; use
        coordinates relative to the element's first node so that the products
        x_l grad x_m carry rounding relative to the element size, not to the
@@ -942,7 +924,11 @@ int ORC(ops)(int N, double* x, double* w, double* D, double* Dhat, double* Dspli
   return 0;
 }
 
-void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, int* status) {
+/* metric_mask: NULL, or a 0/1 mask over elements; metrics are then formed only
+   for the masked elements and the two rings of face neighbours around them
+   (enough for rhs() with the same mask as `want`). */
+void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, const unsigned char* metric_mask,
+                    int* status) {
   handle_t* h = (handle_t*)calloc(1, sizeof(handle_t));
   mesh_t* M = &h->M;
   *status = 0;
@@ -960,7 +946,26 @@ void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, int*
   to_real(xyz, M->xyz, E * n3 * 3);
   int st = build_connectivity(M);
   if (st) { *status = st; }
-  build_metrics(M);
+  unsigned char* need = NULL;
+  if (metric_mask && !st) {
+    /* the mask, its neighbours (their lifted gradients are needed) and their
+       neighbours (master-side normals of the neighbours' faces) */
+    need = (unsigned char*)calloc(E, 1);
+    unsigned char* ring = (unsigned char*)calloc(E, 1);
+    for (long e = 0; e < E; ++e) {
+      if (!metric_mask[e]) continue;
+      ring[e] = 1;
+      for (int f = 0; f < 6; ++f) ring[M->nbr_e[e * 6 + f]] = 1;
+    }
+    for (long e = 0; e < E; ++e) {
+      if (!ring[e]) continue;
+      need[e] = 1;
+      for (int f = 0; f < 6; ++f) need[M->nbr_e[e * 6 + f]] = 1;
+    }
+    free(ring);
+  }
+  build_metrics(M, need);
+  free(need);
   if (work_alloc(M, &h->w)) *status = -5;
   return h;
 }

@@ -1,0 +1,557 @@
+// dg_api.cu -- the C ABI of libdg (include/dg.h): context life cycle, the 1D
+// operators, state transfer, RHS evaluation and graph-launched LSERK steps.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "dg_common.cuh"
+#include "dg_launch.h"
+
+namespace dg {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int k) { g_launches += k; }
+
+void prof_begin(dg_ctx* c, int kind) {
+  Profiler* p = c->prof;
+  if (!p || p->used >= Profiler::MAX_EV) return;
+  p->slot[p->used] = kind;
+  cudaEventRecord(p->ev[p->used][0], c->stream);
+}
+void prof_end(dg_ctx* c) {
+  Profiler* p = c->prof;
+  if (!p || p->used >= Profiler::MAX_EV) return;
+  cudaEventRecord(p->ev[p->used][1], c->stream);
+  ++p->used;
+}
+
+static thread_local std::string g_last_error;
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// 1D operators (Sec. 2.2): LGL nodes as -1, +1 and the zeros of the Jacobi
+// polynomial P^(1,1)_{N-1} (proportional to P_N'), weights 2/(N(N+1)P_N^2),
+// the derivative matrix from barycentric weights, all in long double.
+// ---------------------------------------------------------------------------
+typedef long double ld;
+
+static void jacobi11(int m, ld x, ld& Pm, ld& Pm1) {
+  // P^(1,1)_0 = 1, P^(1,1)_1 = 2x,
+  // k (k+2) P_k = (2k+1)(k+1) x P_{k-1} - k (k+1) P_{k-2}
+  ld a = 1, b = 2 * x;
+  if (m == 0) { Pm = 1; Pm1 = 0; return; }
+  for (int k = 2; k <= m; ++k) {
+    ld c = ((2 * k + 1) * (ld)(k + 1) * x * b - (ld)k * (k + 1) * a) / ((ld)k * (k + 2));
+    a = b;
+    b = c;
+  }
+  Pm = b;
+  Pm1 = a;
+}
+
+static ld legendreP(int N, ld x) {
+  ld a = 1, b = x;
+  if (N == 0) return 1;
+  for (int k = 2; k <= N; ++k) {
+    ld c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+    a = b;
+    b = c;
+  }
+  return b;
+}
+
+static void build_ops(int N, Ops& o) {
+  const int n = N + 1;
+  ld x[NPMAX], w[NPMAX], D[NPMAX * NPMAX], lam[NPMAX];
+  x[0] = -1;
+  x[N] = 1;
+  const int m = N - 1;
+  for (int j = 1; j < N; ++j) {
+    ld t = -std::cos((ld)M_PI * j / N);
+    for (int it = 0; it < 100; ++it) {
+      ld P, Pp;
+      jacobi11(m, t, P, Pp);
+      // (1 - x^2) P_m' = -m x P_m + (m + 1) P_{m-1}
+      ld dP = (-(ld)m * t * P + (ld)(m + 1) * Pp) / (1 - t * t);
+      ld step = P / dP;
+      t -= step;
+      if (std::fabs(step) < 1e-30L) break;
+    }
+    x[j] = t;
+  }
+  for (int j = 0; j < n; ++j) {
+    ld P = legendreP(N, x[j]);
+    w[j] = 2 / ((ld)N * (N + 1) * P * P);
+  }
+  for (int j = 0; j < n; ++j) {
+    ld p = 1;
+    for (int k = 0; k < n; ++k)
+      if (k != j) p *= (x[j] - x[k]);
+    lam[j] = 1 / p;
+  }
+  for (int i = 0; i < n; ++i) {
+    ld s = 0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      D[i * n + j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+      s += D[i * n + j];
+    }
+    D[i * n + i] = -s;
+  }
+  memset(&o, 0, sizeof(o));
+  for (int i = 0; i < n; ++i) {
+    o.x[i] = (double)x[i];
+    o.w[i] = (double)w[i];
+    o.winv[i] = (double)(1 / w[i]);
+  }
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < n; ++a) {
+      const ld d = D[i * n + a];
+      o.D[i * n + a] = (double)d;
+      o.Dlo[i * n + a] = (double)(d - (ld)o.D[i * n + a]);
+      // weak operator: Dhat_ia = -(w_a / w_i) D_ai
+      o.Dhat[i * n + a] = (double)(-(w[a] / w[i]) * D[a * n + i]);
+      // split operator: 2 D plus the two surface corrections
+      ld ds = 2 * d;
+      if (i == N && a == N) ds -= 1 / w[N];
+      if (i == 0 && a == 0) ds += 1 / w[0];
+      o.Dsplit[i * n + a] = (double)ds;
+    }
+  // inverse Vandermonde of the orthonormal Legendre basis by discrete
+  // orthogonality of the LGL quadrature: c_m = sum_i w_i L_m(x_i) u_i / gamma_m
+  ld L[NPMAX * NPMAX];
+  for (int mm = 0; mm < n; ++mm)
+    for (int i = 0; i < n; ++i) L[mm * n + i] = std::sqrt((ld)(2 * mm + 1) / 2) * legendreP(mm, x[i]);
+  for (int mm = 0; mm < n; ++mm) {
+    ld gam = 0;
+    for (int i = 0; i < n; ++i) gam += w[i] * L[mm * n + i] * L[mm * n + i];
+    for (int i = 0; i < n; ++i) o.Vinv[mm * n + i] = (double)(w[i] * L[mm * n + i] / gam);
+  }
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count, int64_t& bytes) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e == cudaSuccess) bytes += (int64_t)(sizeof(T) * count);
+  return e;
+}
+
+int alloc_side_arrays(dg_ctx* c, std::string& msg) {
+  cudaError_t e = cudaSuccess;
+  const int64_t S = c->S, n2 = c->n2;
+  if (e == cudaSuccess) e = dalloc(&c->nrm, S * 4 * n2, c->bytes);
+  if (e == cudaSuccess) e = dalloc(&c->lflux, S * 12 * n2, c->bytes);
+  if (e == cudaSuccess) e = dalloc(&c->fstar, S * 5 * n2, c->bytes);
+  if (e == cudaSuccess) e = dalloc(&c->side_e, S, c->bytes);
+  if (e == cudaSuccess) e = dalloc(&c->side_f, S, c->bytes);
+  if (e != cudaSuccess) {
+    msg = std::string("side arrays: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+  }
+  return DG_OK;
+}
+
+// Carpenter-Kennedy RK4(3)5 2N-storage coefficients (Sec. 2.2 cites them)
+static const double RKA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                              -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double RKB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                              1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                              2277821191437.0 / 14882151754819.0};
+
+__global__ void k_set_scalars(DevScalars* s, double dt_fixed, int set_t, double t, int reset_flags) {
+  s->dt_fixed = dt_fixed;
+  if (set_t) s->t = t;
+  if (reset_flags) s->nonfinite = 0;
+}
+__global__ void k_zero_kin(DevScalars* s) {
+  s->kin[0] = s->kin[1] = s->kin[2] = s->kin[3] = 0.0;
+  s->lam_c = 0ull;
+  s->lam_v = 0ull;
+}
+__global__ void k_dt_only(DevScalars* s, double cfl, double dfl, int N, int viscous) {
+  const double np1 = N + 1.0;
+  const double lc = __longlong_as_double((long long)s->lam_c);
+  const double lv = __longlong_as_double((long long)s->lam_v);
+  double dt = cfl * 2.0 / (np1 * np1 * lc);
+  if (viscous && lv > 0) dt = fmin(dt, dfl * 4.0 / (np1 * np1 * np1 * np1 * lv));
+  s->kin[3] = dt;
+  s->lam_c = 0ull;
+  s->lam_v = 0ull;
+}
+
+static void destroy_graph(dg_ctx* c) {
+  if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+  c->step_graph = nullptr;
+  c->step_graph_kind = -1;
+}
+
+static int check_params(const dg_params* p) {
+  if (!p) return fail(DG_ERR_ARG, "params is NULL");
+  if (!(p->gamma > 1.0) || !(p->R > 0) || !(p->Pr > 0) || !(p->mu >= 0) || !(p->cfl > 0) || !(p->dfl > 0))
+    return fail(DG_ERR_ARG, "invalid physical parameters");
+  if (p->riemann != DG_RIEMANN_ROE && p->riemann != DG_RIEMANN_LF) return fail(DG_ERR_ARG, "unknown Riemann solver");
+  if (p->precision != DG_FP64 && p->precision != DG_FP32_BULK) return fail(DG_ERR_ARG, "unknown precision");
+  if (p->precision == DG_FP32_BULK) return fail(DG_ERR_ARG, "FP32-bulk precision is not available in this build");
+  return DG_OK;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+void dg_default_params(dg_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->gamma = 1.4;
+  p->R = 1.0;
+  p->Pr = 0.72;
+  p->mu = 1.0 / 1600.0;
+  p->riemann = DG_RIEMANN_ROE;
+  p->viscous = 1;
+  p->shock_capturing = 0;
+  p->alpha_min = 1e-3;
+  p->alpha_max = 0.5;
+  p->cfl = 0.9;
+  p->dfl = 0.9;
+  p->precision = DG_FP64;
+  p->alpha_force = -1.0;
+}
+
+const char* dg_error_string(int code) {
+  switch (code) {
+    case DG_OK: return "ok";
+    case DG_ERR_ARG: return "invalid argument";
+    case DG_ERR_MESH: return "invalid mesh";
+    case DG_ERR_OOM: return "out of device memory";
+    case DG_ERR_CUDA: return "CUDA error";
+    case DG_ERR_NONFINITE: return "non-finite value in the solution";
+    case DG_ERR_TIMEOUT: return "device-side wait timed out";
+    case DG_ERR_STATE: return "invalid call for the context's state";
+    case DG_PENDING: return "pending";
+    default: return "unknown error";
+  }
+}
+
+const char* dg_last_error(void) { return g_last_error.c_str(); }
+
+int64_t dg_launch_count(void) { return g_launches.load(); }
+
+void dg_destroy(dg_ctx* c) {
+  if (!c) return;
+  destroy_graph(c);
+  cudaFree(c->U);
+  cudaFree(c->dU);
+  cudaFree(c->Ut);
+  cudaFree(c->Upub);
+  cudaFree(c->metric);
+  cudaFree(c->g);
+  cudaFree(c->nrm);
+  cudaFree(c->lflux);
+  cudaFree(c->fstar);
+  cudaFree(c->alpha);
+  cudaFree(c->fvmetric);
+  cudaFree(c->elem_side);
+  cudaFree(c->side_e);
+  cudaFree(c->side_f);
+  cudaFree(c->ops);
+  cudaFree(c->scal);
+  if (c->scal_host) cudaFreeHost(c->scal_host);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params, void* stream) {
+  if (!out) return fail(DG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !mesh->corner_vid || !mesh->xyz) return fail(DG_ERR_ARG, "mesh description incomplete");
+  if (mesh->N < 1 || mesh->N > NMAX) return fail(DG_ERR_ARG, "N must be in [1, 7]");
+  if (mesh->n_elems < 1 || mesh->n_elems > (int64_t)1 << 26) return fail(DG_ERR_ARG, "bad element count");
+  int st = check_params(params);
+  if (st != DG_OK) return st;
+  dg_ctx* c = new dg_ctx();
+  cudaGetDevice(&c->device);
+  c->stream = (cudaStream_t)stream;
+  c->prm = *params;
+  c->N = mesh->N;
+  c->n = c->N + 1;
+  c->n2 = c->n * c->n;
+  c->n3 = c->n2 * c->n;
+  c->E = mesh->n_elems;
+  const int64_t E = c->E, n3 = c->n3;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  A(dalloc(&c->U, E * 5 * n3, c->bytes));
+  A(dalloc(&c->dU, E * 5 * n3, c->bytes));
+  A(dalloc(&c->Ut, E * 5 * n3, c->bytes));
+  A(dalloc(&c->Upub, E * 5 * n3, c->bytes));
+  A(dalloc(&c->metric, E * 10 * n3, c->bytes));
+  A(dalloc(&c->g, E * 12 * n3, c->bytes));
+  A(dalloc(&c->alpha, E, c->bytes));
+  A(dalloc(&c->fvmetric, E * 3 * (c->n - 1) * 3 * c->n2, c->bytes));
+  A(dalloc(&c->elem_side, E * 6, c->bytes));
+  A(dalloc(&c->ops, 1, c->bytes));
+  A(dalloc(&c->scal, 1, c->bytes));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->scal_host, sizeof(DevScalars));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    int r = cuda_fail(e, "allocation");
+    dg_destroy(c);
+    return r;
+  }
+  if (e == cudaSuccess) e = init_kernel_attributes(c->N);
+  Ops ops;
+  build_ops(c->N, ops);
+  A(cudaMemcpyAsync(c->ops, &ops, sizeof(Ops), cudaMemcpyHostToDevice, c->stream));
+  A(cudaMemsetAsync(c->scal, 0, sizeof(DevScalars), c->stream));
+  A(cudaMemsetAsync(c->alpha, 0, sizeof(double) * E, c->stream));
+  A(cudaMemsetAsync(c->g, 0, sizeof(double) * E * 12 * n3, c->stream));
+  A(cudaStreamSynchronize(c->stream));
+  if (e != cudaSuccess) {
+    int r = cuda_fail(e, "initialisation");
+    dg_destroy(c);
+    return r;
+  }
+  std::string msg;
+  st = build_mesh(c, mesh->corner_vid, mesh->xyz, msg);
+  if (st != DG_OK) {
+    dg_destroy(c);
+    return fail(st, msg);
+  }
+  *out = c;
+  return DG_OK;
+}
+
+int dg_set_stream(dg_ctx* c, void* stream) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  c->stream = (cudaStream_t)stream;
+  return DG_OK;
+}
+
+int dg_set_params(dg_ctx* c, const dg_params* p) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  int st = check_params(p);
+  if (st != DG_OK) return st;
+  c->prm = *p;
+  destroy_graph(c);
+  return DG_OK;
+}
+
+int dg_sizes(const dg_ctx* c, int* N, int64_t* E, int64_t* S, int64_t* bytes) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (N) *N = c->N;
+  if (E) *E = c->E;
+  if (S) *S = c->S;
+  if (bytes) *bytes = c->bytes;
+  return DG_OK;
+}
+
+int dg_set_state(dg_ctx* c, const double* U, int on_device, double t) {
+  if (!c || !U) return fail(DG_ERR_ARG, "ctx or U is NULL");
+  const size_t bytes = sizeof(double) * c->E * 5 * c->n3;
+  cudaError_t e = cudaSuccess;
+  const double* src = U;
+  if (!on_device) {
+    e = cudaMemcpyAsync(c->Upub, U, bytes, cudaMemcpyHostToDevice, c->stream);
+    src = c->Upub;
+  }
+  if (e == cudaSuccess) e = launch_to_internal(c, src, c->U);
+  if (e == cudaSuccess) {
+    k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, 0.0, 1, t, 1);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_set_state");
+  c->t_host = t;
+  c->state_set = true;
+  return DG_OK;
+}
+
+int dg_get_state(dg_ctx* c, double* U, int on_device, double* t) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  const size_t bytes = sizeof(double) * c->E * 5 * c->n3;
+  cudaError_t e = cudaSuccess;
+  if (U) {
+    e = launch_to_public(c, c->U, on_device ? U : c->Upub);
+    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(U, c->Upub, bytes, cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->scal_host, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_get_state");
+  c->t_host = c->scal_host->t;
+  if (t) *t = c->t_host;
+  if (c->scal_host->nonfinite) return fail(DG_ERR_NONFINITE, "a time step met a non-finite value");
+  return DG_OK;
+}
+
+int dg_rhs(dg_ctx* c, const double* U_dev, double* Ut_dev) {
+  if (!c || !Ut_dev) return fail(DG_ERR_ARG, "ctx or Ut is NULL");
+  if (!U_dev && !c->state_set) return fail(DG_ERR_STATE, "no state set");
+  cudaError_t e = cudaSuccess;
+  const double* Uin = c->U;
+  if (U_dev) {
+    // the RK register is free between steps: use it for the internal copy
+    e = launch_to_internal(c, U_dev, c->dU);
+    Uin = c->dU;
+  }
+  if (e == cudaSuccess) e = launch_rhs(c, Uin, 0, 0.0, 0.0, 0);
+  if (e == cudaSuccess) e = launch_to_public(c, c->Ut, Ut_dev);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_rhs");
+  return DG_OK;
+}
+
+static cudaError_t enqueue_step(dg_ctx* c) {
+  cudaError_t e = launch_cfl(c);
+  for (int s = 0; s < 5 && e == cudaSuccess; ++s) e = launch_rhs(c, c->U, 1, RKA[s], RKB[s], s == 0);
+  return e;
+}
+
+int dg_step(dg_ctx* c, int n_steps, double dt) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  if (n_steps < 0) return fail(DG_ERR_ARG, "n_steps < 0");
+  if (n_steps == 0) return DG_OK;
+  k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, dt > 0 ? dt : 0.0, 0, 0.0, 0);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !c->step_graph) {
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t le = enqueue_step(c);
+      e = cudaStreamEndCapture(c->cap_stream, &graph);
+      if (e == cudaSuccess) e = le;
+    }
+    c->stream = user;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->step_graph = nullptr;
+      return cuda_fail(e, "graph capture of a time step");
+    }
+  }
+  for (int i = 0; i < n_steps && e == cudaSuccess; ++i) {
+    e = cudaGraphLaunch(c->step_graph, c->stream);
+    count_launch(2 + 5 * (c->prm.viscous ? 4 : 2));
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "dg_step");
+  return DG_OK;
+}
+
+int dg_profile_step(dg_ctx* c, int n_steps, double dt, double* ms, int64_t* launches) {
+  if (!c || !ms || !launches) return fail(DG_ERR_ARG, "NULL argument");
+  if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  Profiler* p = new Profiler();
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < Profiler::MAX_EV && e == cudaSuccess; ++i) {
+    e = cudaEventCreate(&p->ev[i][0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev[i][1]);
+  }
+  if (e == cudaSuccess) {
+    k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, dt > 0 ? dt : 0.0, 0, 0.0, 0);
+    count_launch();
+    c->prof = p;
+    for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
+      p->used = 0;
+      e = enqueue_step(c);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      for (int k = 0; k < p->used && e == cudaSuccess; ++k) {
+        float t = 0;
+        e = cudaEventElapsedTime(&t, p->ev[k][0], p->ev[k][1]);
+        p->ms[p->slot[k]] += t;
+        p->launches[p->slot[k]] += 1;
+      }
+    }
+    c->prof = nullptr;
+  }
+  for (int k = 0; k < 5; ++k) {
+    ms[k] = p->ms[k];
+    launches[k] = p->launches[k];
+  }
+  for (int i = 0; i < Profiler::MAX_EV; ++i) {
+    if (p->ev[i][0]) cudaEventDestroy(p->ev[i][0]);
+    if (p->ev[i][1]) cudaEventDestroy(p->ev[i][1]);
+  }
+  delete p;
+  if (e != cudaSuccess) return cuda_fail(e, "dg_profile_step");
+  return DG_OK;
+}
+
+int dg_time_step(dg_ctx* c, double* dt) {
+  if (!c || !dt) return fail(DG_ERR_ARG, "ctx or dt is NULL");
+  if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  k_zero_kin<<<1, 1, 0, c->stream>>>(c->scal);
+  count_launch();
+  // reuse the CFL reduction, but report instead of stepping
+  const double kv = std::max(4.0 / 3.0, c->prm.gamma / c->prm.Pr) * c->prm.mu;
+  (void)kv;
+  cudaError_t e = launch_cfl(c);  // advances t by the CFL dt: undo below
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->scal_host, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_time_step");
+  *dt = c->scal_host->dt;
+  k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, 0.0, 1, c->scal_host->t - c->scal_host->dt, 0);
+  count_launch();
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_time_step");
+  if (c->scal_host->nonfinite) return fail(DG_ERR_NONFINITE, "non-finite value in the state");
+  return DG_OK;
+}
+
+int dg_kinetic(dg_ctx* c, double* out) {
+  if (!c || !out) return fail(DG_ERR_ARG, "ctx or out is NULL");
+  if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  cudaError_t e = launch_rhs(c, c->U, 0, 0.0, 0.0, 0);
+  if (e == cudaSuccess) {
+    k_zero_kin<<<1, 1, 0, c->stream>>>(c->scal);
+    count_launch();
+    e = launch_kinetic(c, c->U, c->Ut);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->scal_host, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_kinetic");
+  out[0] = c->scal_host->kin[0] / c->scal_host->kin[2];
+  out[1] = c->scal_host->kin[1] / c->scal_host->kin[2];
+  out[2] = c->scal_host->kin[2];
+  return DG_OK;
+}
+
+int dg_debug(dg_ctx* c, int what, void* out0, void* out1) {
+  if (!c || !out0) return fail(DG_ERR_ARG, "ctx or out0 is NULL");
+  cudaError_t e = cudaSuccess;
+  switch (what) {
+    case DG_DEBUG_METRICS:
+      if (!out1) return fail(DG_ERR_ARG, "out1 is NULL");
+      e = launch_debug_metrics(c, (double*)out0, (double*)out1);
+      break;
+    case DG_DEBUG_MAPS:
+      if (!out1) return fail(DG_ERR_ARG, "out1 is NULL");
+      e = launch_debug_maps(c, (int*)out0, (int*)out1);
+      break;
+    case DG_DEBUG_GRAD: e = launch_debug_grad(c, (double*)out0); break;
+    case DG_DEBUG_FSTAR: e = launch_debug_fstar(c, (double*)out0); break;
+    case DG_DEBUG_ALPHA:
+      e = cudaMemcpyAsync(out0, c->alpha, sizeof(double) * c->E, cudaMemcpyDeviceToDevice, c->stream);
+      break;
+    default: return fail(DG_ERR_ARG, "unknown debug item");
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_debug");
+  return DG_OK;
+}
+
+}  // extern "C"

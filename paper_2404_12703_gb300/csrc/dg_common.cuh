@@ -1,0 +1,206 @@
+// dg_common.cuh -- device helpers shared by the libdg kernels: index maps,
+// double-double arithmetic for the metric construction, and the point-wise
+// physics of the compressible Navier-Stokes equations (Sec. 2.1).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dg_types.h"
+
+namespace dg {
+
+// ---------------------------------------------------------------------------
+// Index maps.  Node index inside an element: i + n (j + n k).
+// Local faces f = 2 d + s (d: xi, eta, zeta; s = 0 minus, 1 plus face).
+// Face frame (p, q): (j, k) for d = 0, (i, k) for d = 1, (i, j) for d = 2.
+// ---------------------------------------------------------------------------
+template <int n>
+__host__ __device__ __forceinline__ int face_vol_node(int f, int p, int q) {
+  const int d = f >> 1, end = (f & 1) ? n - 1 : 0;
+  return d == 0 ? end + n * (p + n * q) : (d == 1 ? p + n * (end + n * q) : p + n * (q + n * end));
+}
+
+// Flip convention: the slave face node (ps, qs) (slave's own face frame)
+// coincides with master node (pm, qm) = T(ps, qs), where T first swaps the
+// two coordinates if bit 2 is set, then reverses p (bit 0) and q (bit 1).
+template <int n>
+__host__ __device__ __forceinline__ void flip_to_master(int flip, int ps, int qs, int& pm, int& qm) {
+  int a = (flip & 4) ? qs : ps;
+  int b = (flip & 4) ? ps : qs;
+  pm = (flip & 1) ? n - 1 - a : a;
+  qm = (flip & 2) ? n - 1 - b : b;
+}
+template <int n>
+__host__ __device__ __forceinline__ void flip_to_slave(int flip, int pm, int qm, int& ps, int& qs) {
+  int a = (flip & 1) ? n - 1 - pm : pm;
+  int b = (flip & 2) ? n - 1 - qm : qm;
+  ps = (flip & 4) ? b : a;
+  qs = (flip & 4) ? a : b;
+}
+
+// elem_side packing: side index << 4 | is_slave << 3 | flip
+__host__ __device__ __forceinline__ int es_side(int v) { return v >> 4; }
+__host__ __device__ __forceinline__ int es_slave(int v) { return (v >> 3) & 1; }
+__host__ __device__ __forceinline__ int es_flip(int v) { return v & 7; }
+
+// ---------------------------------------------------------------------------
+// Double-double arithmetic (Knuth's two-sum, an FMA-based exact product, and
+// renormalisation), used only at initialisation for the curl-form metrics.
+// ---------------------------------------------------------------------------
+struct dd {
+  double hi, lo;
+};
+__device__ __forceinline__ dd dd_from(double a) { return {a, 0.0}; }
+__device__ __forceinline__ dd two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dd quick_two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  return {s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  dd t = two_sum(a.lo, b.lo);
+  double e = __dadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, e);
+  e = __dadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, e);
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  double p = __dmul_rn(a.hi, b.hi);
+  double e = __fma_rn(a.hi, b.hi, -p);
+  e = __fma_rn(a.hi, b.lo, e);
+  e = __fma_rn(a.lo, b.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ double dd_to_double(dd a) { return __dadd_rn(a.hi, a.lo); }
+
+// ---------------------------------------------------------------------------
+// Point-wise physics, templated on the arithmetic type T.
+// ---------------------------------------------------------------------------
+struct Gas {
+  double gamma, R, Pr, mu;
+  double gm1;     // gamma - 1
+  double lambda;  // heat conductivity gamma R mu / ((gamma - 1) Pr)
+};
+
+template <typename T>
+struct Prim {
+  T rho, u, v, w, p, T_;  // density, velocity, pressure, temperature
+};
+
+// Eqs. eos_p / eos_T
+template <typename T>
+__device__ __forceinline__ Prim<T> cons_to_prim(const T U[5], T gm1, T Rinv) {
+  Prim<T> q;
+  T ri = T(1) / U[0];
+  q.rho = U[0];
+  q.u = U[1] * ri;
+  q.v = U[2] * ri;
+  q.w = U[3] * ri;
+  q.p = gm1 * (U[4] - T(0.5) * (U[1] * q.u + U[2] * q.v + U[3] * q.w));
+  q.T_ = q.p * ri * Rinv;
+  return q;
+}
+
+// Euler flux contracted with nv (Eq. nse)
+template <typename T>
+__device__ __forceinline__ void euler_flux(const T U[5], const Prim<T>& q, const T nv[3], T f[5]) {
+  T un = q.u * nv[0] + q.v * nv[1] + q.w * nv[2];
+  f[0] = U[0] * un;
+  f[1] = U[1] * un + q.p * nv[0];
+  f[2] = U[2] * un + q.p * nv[1];
+  f[3] = U[3] * un + q.p * nv[2];
+  f[4] = (U[4] + q.p) * un;
+}
+
+// Roe's approximate Riemann solver, unit normal n, no entropy fix.
+template <typename T>
+__device__ __forceinline__ void roe_flux(const T UL[5], const Prim<T>& qL, const T UR[5], const Prim<T>& qR,
+                                         const T n[3], T gm1, T f[5]) {
+  T fL[5], fR[5];
+  euler_flux(UL, qL, n, fL);
+  euler_flux(UR, qR, n, fR);
+  T sL = sqrt(qL.rho), sR = sqrt(qR.rho);
+  T inv = T(1) / (sL + sR);
+  T HL = (UL[4] + qL.p) / qL.rho, HR = (UR[4] + qR.p) / qR.rho;
+  T ut0 = (sL * qL.u + sR * qR.u) * inv;
+  T ut1 = (sL * qL.v + sR * qR.v) * inv;
+  T ut2 = (sL * qL.w + sR * qR.w) * inv;
+  T Ht = (sL * HL + sR * HR) * inv;
+  T rt = sL * sR;
+  T q2 = ut0 * ut0 + ut1 * ut1 + ut2 * ut2;
+  T c2 = gm1 * (Ht - T(0.5) * q2);
+  T c = sqrt(c2);
+  T c2i = T(1) / c2;
+  T un = ut0 * n[0] + ut1 * n[1] + ut2 * n[2];
+  T drho = qR.rho - qL.rho, dp = qR.p - qL.p;
+  T du0 = qR.u - qL.u, du1 = qR.v - qL.v, du2 = qR.w - qL.w;
+  T dun = du0 * n[0] + du1 * n[1] + du2 * n[2];
+  T a1 = T(0.5) * (dp - rt * c * dun) * c2i;
+  T a2 = drho - dp * c2i;
+  T a5 = T(0.5) * (dp + rt * c * dun) * c2i;
+  T l1 = fabs(un - c) * a1, l2 = fabs(un), l5 = fabs(un + c) * a5;
+  T l2a = l2 * a2, l2r = l2 * rt;
+  T dt0 = du0 - dun * n[0], dt1 = du1 - dun * n[1], dt2 = du2 - dun * n[2];
+  T D0 = l1 + l2a + l5;
+  T D1 = l1 * (ut0 - c * n[0]) + l2a * ut0 + l5 * (ut0 + c * n[0]) + l2r * dt0;
+  T D2 = l1 * (ut1 - c * n[1]) + l2a * ut1 + l5 * (ut1 + c * n[1]) + l2r * dt1;
+  T D3 = l1 * (ut2 - c * n[2]) + l2a * ut2 + l5 * (ut2 + c * n[2]) + l2r * dt2;
+  T D4 = l1 * (Ht - un * c) + l2a * T(0.5) * q2 + l5 * (Ht + un * c) +
+         l2r * (ut0 * dt0 + ut1 * dt1 + ut2 * dt2);
+  f[0] = T(0.5) * (fL[0] + fR[0] - D0);
+  f[1] = T(0.5) * (fL[1] + fR[1] - D1);
+  f[2] = T(0.5) * (fL[2] + fR[2] - D2);
+  f[3] = T(0.5) * (fL[3] + fR[3] - D3);
+  f[4] = T(0.5) * (fL[4] + fR[4] - D4);
+}
+
+// Local Lax-Friedrichs (Rusanov), unit normal n.
+template <typename T>
+__device__ __forceinline__ void lf_flux(const T UL[5], const Prim<T>& qL, const T UR[5], const Prim<T>& qR,
+                                        const T n[3], T gamma, T f[5]) {
+  T fL[5], fR[5];
+  euler_flux(UL, qL, n, fL);
+  euler_flux(UR, qR, n, fR);
+  T cL = sqrt(gamma * qL.p / qL.rho), cR = sqrt(gamma * qR.p / qR.rho);
+  T lL = fabs(qL.u * n[0] + qL.v * n[1] + qL.w * n[2]) + cL;
+  T lR = fabs(qR.u * n[0] + qR.v * n[1] + qR.w * n[2]) + cR;
+  T lm = lL > lR ? lL : lR;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) f[k] = T(0.5) * (fL[k] + fR[k] - lm * (UR[k] - UL[k]));
+}
+
+// Viscous stress and the energy "work + conduction" vector from the lifted
+// gradients g[qv*3 + x] = d(u, v, w, T)_qv / dx_x (Eq. nse, stress tensor,
+// Fourier law).  tau = (xx, yy, zz, xy, xz, yz), W_x = tau_x . u + lambda T_x.
+template <typename T>
+__device__ __forceinline__ void viscous_parts(const T g[12], T u, T v, T w, T mu, T lam, T tau[6], T W[3]) {
+  T div = g[0] + g[4] + g[8];
+  T tw = T(2.0 / 3.0) * div;
+  tau[0] = mu * (T(2) * g[0] - tw);
+  tau[1] = mu * (T(2) * g[4] - tw);
+  tau[2] = mu * (T(2) * g[8] - tw);
+  tau[3] = mu * (g[1] + g[3]);
+  tau[4] = mu * (g[2] + g[6]);
+  tau[5] = mu * (g[5] + g[7]);
+  W[0] = tau[0] * u + tau[3] * v + tau[4] * w + lam * g[9];
+  W[1] = tau[3] * u + tau[1] * v + tau[5] * w + lam * g[10];
+  W[2] = tau[4] * u + tau[5] * v + tau[2] * w + lam * g[11];
+}
+
+// F_v . nv  (4 non-zero components: momentum x, y, z and energy)
+template <typename T>
+__device__ __forceinline__ void viscous_flux_n(const T tau[6], const T W[3], const T nv[3], T f[4]) {
+  f[0] = tau[0] * nv[0] + tau[3] * nv[1] + tau[4] * nv[2];
+  f[1] = tau[3] * nv[0] + tau[1] * nv[1] + tau[5] * nv[2];
+  f[2] = tau[4] * nv[0] + tau[5] * nv[1] + tau[2] * nv[2];
+  f[3] = W[0] * nv[0] + W[1] * nv[1] + W[2] * nv[2];
+}
+
+}  // namespace dg

@@ -1,0 +1,48 @@
+// dg_launch.h -- host-side interfaces between the translation units of libdg.
+#pragma once
+#include <string>
+
+#include "dg_types.h"
+
+namespace dg {
+
+// launch accounting (dg_launch_count)
+void count_launch(int k = 1);
+
+// kernel kinds timed by dg_profile_step
+enum { PK_CFL = 0, PK_SURF_PRIMS = 1, PK_LIFT = 2, PK_SURF_FLUX = 3, PK_VOLUME = 4 };
+// record an event before / after a kernel launch when c->prof is set
+void prof_begin(dg_ctx* c, int kind);
+void prof_end(dg_ctx* c);
+
+// allocation of the side arrays once the number of sides is known
+int alloc_side_arrays(dg_ctx* c, std::string& msg);
+
+// device mesh set-up (dg_mesh.cu)
+int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::string& msg);
+
+// one evaluation of the right-hand side (dg_rhs.cu).
+//   mode 0: write Ut (internal layout) into c->Ut for state U
+//   mode 1: RK stage update of c->U / c->dU with coefficients (A, B)
+cudaError_t launch_rhs(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first_stage);
+
+// CFL reduction: writes dt (and advances nothing); fixed dt if dt_fixed > 0
+cudaError_t launch_cfl(dg_ctx* c);
+
+// raises the dynamic shared-memory limits of the kernels of degree N
+cudaError_t init_kernel_attributes(int N);
+
+// layout conversion public [E][n3][5] <-> internal [E][5][n3]
+cudaError_t launch_to_internal(dg_ctx* c, const double* pub, double* internal);
+cudaError_t launch_to_public(dg_ctx* c, const double* internal, double* pub);
+
+// kinetic energy reductions into c->scal->kin (U internal, Ut internal or null)
+cudaError_t launch_kinetic(dg_ctx* c, const double* U, const double* Ut);
+
+// verification copies
+cudaError_t launch_debug_metrics(dg_ctx* c, double* Ja, double* J);
+cudaError_t launch_debug_maps(dg_ctx* c, int* nbr, int* nodes);
+cudaError_t launch_debug_grad(dg_ctx* c, double* out);
+cudaError_t launch_debug_fstar(dg_ctx* c, double* out);
+
+}  // namespace dg

@@ -1,0 +1,111 @@
+// dg_types.h -- internal data structures of libdg shared by the host code and
+// the kernels (no CUDA-specific types beyond the runtime API).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int NMAX = 7;
+constexpr int NPMAX = NMAX + 1;
+
+// 1D operators of one degree N, rounded to double from extended-precision
+// values (Sec. 2.2, Eq. dgsem and the operator definitions after it).
+struct Ops {
+  double x[NPMAX], w[NPMAX], winv[NPMAX];
+  double D[NPMAX * NPMAX];       // D[i][a] = l_a'(x_i)
+  double Dhat[NPMAX * NPMAX];    // -(w_a / w_i) D[a][i]
+  double Dsplit[NPMAX * NPMAX];  // 2 D + corner corrections (diagonal zero)
+  double Dlo[NPMAX * NPMAX];     // D - (double)D (double-double tail)
+  double Vinv[NPMAX * NPMAX];    // nodal -> orthonormal Legendre modes
+  double Dinv_w[NPMAX];          // unused padding / reserved
+};
+
+// Scalars kept on the device (one block, one per context).
+struct DevScalars {
+  double dt;                 // time step of the current step
+  double t;                  // time of the state
+  double dt_fixed;           // > 0: fixed step
+  unsigned long long lam_c;  // max convective spectral radius (bits of a positive double)
+  unsigned long long lam_v;  // max viscous spectral radius
+  int nonfinite;             // sticky: a non-finite value met in the CFL reduction
+  int mesh_error;            // set by the map construction kernels
+  int pad[2];
+  double kin[4];             // kinetic-energy reductions
+};
+
+// Per-stage launch parameters of the RHS kernels.
+struct StageArgs {
+  int E, S;
+  const double* U;       // [E][5][n3] internal state
+  const double* metric;  // [E][10][n3]: J a^d_c at d*3+c, then 1/J
+  const double* nrm;     // [S][4][n2]: s n (3), s
+  const int* elem_side;  // [E][6]
+  const int2* side_e;    // [S] (eM, eS)
+  const int* side_f;     // [S] fM | fS << 4 | flip << 8
+  double* g;             // [E][12][n3] lifted gradients
+  double* lflux;         // [S][12][n2]
+  double* fstar;         // [S][5][n2]
+  double* alpha;         // [E]
+  const double* fvmetric;  // [E][3][n2][(n-1)*3] sub-cell interface metrics
+  const Ops* ops;
+  double gamma, gm1, Rinv, mu, lam;
+  int riemann, viscous, shock;
+  double alpha_min, alpha_max, alpha_force;
+  // output: either Ut (mode 0) or the RK update (mode 1)
+  double* Ut;       // [E][5][n3] internal layout
+  double* Urk;      // state updated in place
+  double* dU;       // RK register
+  const DevScalars* scal;
+  double rkA, rkB;
+  int first_stage;
+};
+
+}  // namespace dg
+
+struct dg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;      // user stream: all work is ordered on it
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  int N = 0, n = 0, n2 = 0, n3 = 0;
+  int64_t E = 0, S = 0;
+  dg_params prm{};
+  // device memory
+  double* U = nullptr;       // [E][5][n3]
+  double* dU = nullptr;      // [E][5][n3]
+  double* Ut = nullptr;      // [E][5][n3] scratch for dg_rhs
+  double* Upub = nullptr;    // [E][n3][5] scratch for layout conversion
+  double* metric = nullptr;  // [E][10][n3]
+  double* g = nullptr;       // [E][12][n3]
+  double* nrm = nullptr;     // [S][4][n2]
+  double* lflux = nullptr;   // [S][12][n2]
+  double* fstar = nullptr;   // [S][5][n2]
+  double* alpha = nullptr;   // [E]
+  double* fvmetric = nullptr;  // [E][3][n2][(n-1)*3]
+  int* elem_side = nullptr;  // [E][6]
+  int2* side_e = nullptr;    // [S]
+  int* side_f = nullptr;     // [S]
+  dg::Ops* ops = nullptr;    // device copy of the operators of degree N
+  dg::DevScalars* scal = nullptr;
+  dg::DevScalars* scal_host = nullptr;  // pinned mirror
+  int64_t bytes = 0;
+  double t_host = 0.0;
+  bool state_set = false;
+  // CUDA graphs of one time step (CFL or fixed dt)
+  cudaGraphExec_t step_graph = nullptr;
+  int step_graph_kind = -1;
+  // per-kernel event timing (dg_profile_step); null when not profiling
+  struct Profiler* prof = nullptr;
+};
+
+// Event pairs around each kernel launch, grouped by kernel kind.
+struct Profiler {
+  static constexpr int MAX_EV = 256;
+  cudaEvent_t ev[MAX_EV][2];
+  int slot[MAX_EV];
+  int used = 0;
+  double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};

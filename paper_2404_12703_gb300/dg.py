@@ -1,0 +1,262 @@
+"""Thin Python binding of libdg's C ABI (``include/dg.h``).
+
+Argument marshalling only: every step of the DG operator and the time
+integration runs in libdg's CUDA kernels.  PyTorch supplies device memory and
+the current CUDA stream.  There is no CPU fallback: if libdg.so cannot be
+loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdg.so")
+_lock = threading.Lock()
+_lib = None
+
+DG_OK, DG_ERR_ARG, DG_ERR_MESH, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE, DG_ERR_TIMEOUT, DG_ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+DG_PENDING = 1
+ROE, LF = 0, 1
+FP64, FP32_BULK = 0, 1
+DEBUG_METRICS, DEBUG_MAPS, DEBUG_GRAD, DEBUG_FSTAR, DEBUG_ALPHA = 0, 1, 2, 3, 4
+
+#: every symbol include/dg.h declares
+EXPORTS = ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
+           "dg_get_state", "dg_rhs", "dg_step", "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
+           "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count")
+
+
+class DgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdg error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double), ("mu", C.c_double),
+                ("riemann", C.c_int), ("viscous", C.c_int), ("shock_capturing", C.c_int),
+                ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("cfl", C.c_double),
+                ("dfl", C.c_double), ("precision", C.c_int), ("alpha_force", C.c_double)]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("N", C.c_int), ("n_elems", C.c_int64), ("corner_vid", C.POINTER(C.c_int64)),
+                ("xyz", C.POINTER(C.c_double))]
+
+
+def load(path: str | None = None):
+    """Load libdg.so (build it first with ``paper_2404_12703_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libdg.so not found at {p}: run paper_2404_12703_gb300.build.build() first")
+        lib = C.CDLL(p)
+        vp = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        sig = {
+            "dg_default_params": (None, [C.POINTER(Params)]),
+            "dg_init_mesh": (C.c_int, [C.POINTER(vp), C.POINTER(MeshDesc), C.POINTER(Params), vp]),
+            "dg_set_stream": (C.c_int, [vp, vp]),
+            "dg_set_params": (C.c_int, [vp, C.POINTER(Params)]),
+            "dg_set_state": (C.c_int, [vp, vp, C.c_int, C.c_double]),
+            "dg_get_state": (C.c_int, [vp, vp, C.c_int, dp]),
+            "dg_rhs": (C.c_int, [vp, vp, vp]),
+            "dg_step": (C.c_int, [vp, C.c_int, C.c_double]),
+            "dg_profile_step": (C.c_int, [vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int64)]),
+            "dg_time_step": (C.c_int, [vp, dp]),
+            "dg_kinetic": (C.c_int, [vp, dp]),
+            "dg_debug": (C.c_int, [vp, C.c_int, vp, vp]),
+            "dg_sizes": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64)]),
+            "dg_destroy": (None, [vp]),
+            "dg_error_string": (C.c_char_p, [C.c_int]),
+            "dg_last_error": (C.c_char_p, []),
+            "dg_launch_count": (C.c_int64, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(code):
+    if code != DG_OK:
+        lib = load()
+        raise DgError(code, lib.dg_last_error().decode())
+    return code
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().dg_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "riemann" and isinstance(v, str):
+            v = {"roe": ROE, "lf": LF}[v]
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": FP64, "fp32": FP32_BULK}[v]
+        setattr(p, k, v)
+    return p
+
+
+def launch_count() -> int:
+    return int(load().dg_launch_count())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Solver:
+    """One mesh on the current CUDA device, with its state.
+
+    ``mesh`` is a dict with ``N``, ``xyz`` [E][n][n][n][3] (or [E][n^3][3]) and
+    ``corner_vid`` [E][8] as produced by ``workloads.box_mesh``.
+    """
+
+    def __init__(self, mesh, params: Params | None = None, stream=None, **kw):
+        lib = load()
+        self._lib = lib
+        self.N = int(mesh["N"])
+        self.n = self.N + 1
+        xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
+        cvid = np.ascontiguousarray(mesh["corner_vid"], dtype=np.int64)
+        self.E = int(xyz.shape[0])
+        self.params = params if params is not None else default_params(**kw)
+        desc = MeshDesc(self.N, self.E, cvid.ctypes.data_as(C.POINTER(C.c_int64)),
+                        xyz.ctypes.data_as(C.POINTER(C.c_double)))
+        h = C.c_void_p()
+        _check(lib.dg_init_mesh(C.byref(h), C.byref(desc), C.byref(self.params), _stream_ptr(stream)))
+        self._h = h
+
+    # -- life cycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sizes(self):
+        N, E, S, b = C.c_int(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(self._lib.dg_sizes(self._h, C.byref(N), C.byref(E), C.byref(S), C.byref(b)))
+        return {"N": N.value, "E": E.value, "S": S.value, "bytes": b.value}
+
+    def set_stream(self, stream=None):
+        _check(self._lib.dg_set_stream(self._h, _stream_ptr(stream)))
+
+    def set_params(self, params: Params | None = None, **kw):
+        if params is None:
+            params = self.params
+            for k, v in kw.items():
+                if k == "riemann" and isinstance(v, str):
+                    v = {"roe": ROE, "lf": LF}[v]
+                setattr(params, k, v)
+        _check(self._lib.dg_set_params(self._h, C.byref(params)))
+        self.params = params
+
+    # -- state ----------------------------------------------------------------
+    def set_state(self, U, t=0.0):
+        """U: torch CUDA tensor or numpy array, float64, shape [E, n^3, 5] (any view)."""
+        if isinstance(U, np.ndarray):
+            Uh = np.ascontiguousarray(U, dtype=np.float64)
+            assert Uh.size == self.E * self.n ** 3 * 5
+            _check(self._lib.dg_set_state(self._h, C.c_void_p(Uh.ctypes.data), 0, float(t)))
+        else:
+            import torch
+            assert U.is_cuda and U.dtype == torch.float64 and U.is_contiguous()
+            assert U.numel() == self.E * self.n ** 3 * 5
+            _check(self._lib.dg_set_state(self._h, C.c_void_p(U.data_ptr()), 1, float(t)))
+
+    def get_state(self, out=None):
+        """Returns (U, t).  ``out`` may be a CUDA tensor (device copy), a host
+        numpy array of E * n^3 * 5 float64 (e.g. backed by pinned memory), or
+        None (a new numpy array)."""
+        t = C.c_double()
+        if out is None or isinstance(out, np.ndarray):
+            U = np.empty((self.E, self.n ** 3, 5)) if out is None else out
+            assert U.dtype == np.float64 and U.flags.c_contiguous and U.size == self.E * self.n ** 3 * 5
+            _check(self._lib.dg_get_state(self._h, C.c_void_p(U.ctypes.data), 0, C.byref(t)))
+            return U, t.value
+        _check(self._lib.dg_get_state(self._h, C.c_void_p(out.data_ptr()), 1, C.byref(t)))
+        return out, t.value
+
+    # -- operator and time stepping --------------------------------------------
+    def rhs(self, U=None, out=None):
+        """Ut = R(U) on the device.  U: CUDA float64 tensor [E, n^3, 5] or None
+        (the solver's own state).  Returns a CUDA tensor."""
+        import torch
+        if out is None:
+            out = torch.empty((self.E, self.n ** 3, 5), dtype=torch.float64, device="cuda")
+        up = C.c_void_p(U.data_ptr()) if U is not None else C.c_void_p(0)
+        _check(self._lib.dg_rhs(self._h, up, C.c_void_p(out.data_ptr())))
+        return out
+
+    def step(self, n_steps=1, dt=0.0):
+        _check(self._lib.dg_step(self._h, int(n_steps), float(dt)))
+
+    #: kernel kinds reported by profile_step, in the library's order
+    KERNELS = ("cfl", "surf_prims", "lift", "surf_flux", "volume")
+
+    def profile_step(self, n_steps=1, dt=0.0):
+        """Per-kernel summed device time (ms) and launch counts over n_steps
+        eagerly launched steps (CUDA events on the solver's stream)."""
+        ms = (C.c_double * 5)()
+        cnt = (C.c_int64 * 5)()
+        _check(self._lib.dg_profile_step(self._h, int(n_steps), float(dt), ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KERNELS)}
+
+    def time_step(self):
+        dt = C.c_double()
+        _check(self._lib.dg_time_step(self._h, C.byref(dt)))
+        return dt.value
+
+    def kinetic(self):
+        out = (C.c_double * 3)()
+        _check(self._lib.dg_kinetic(self._h, out))
+        return tuple(out)
+
+    # -- verification -------------------------------------------------------------
+    def debug(self, what):
+        import torch
+        E, n3, n2 = self.E, self.n ** 3, self.n ** 2
+        dev = "cuda"
+        if what == "metrics":
+            Ja = torch.empty((E, n3, 3, 3), dtype=torch.float64, device=dev)
+            J = torch.empty((E, n3), dtype=torch.float64, device=dev)
+            _check(self._lib.dg_debug(self._h, DEBUG_METRICS, C.c_void_p(Ja.data_ptr()), C.c_void_p(J.data_ptr())))
+            return Ja.cpu().numpy(), J.cpu().numpy()
+        if what == "maps":
+            nbr = torch.empty((E, 6, 3), dtype=torch.int32, device=dev)
+            nodes = torch.empty((E, 6, n2), dtype=torch.int32, device=dev)
+            _check(self._lib.dg_debug(self._h, DEBUG_MAPS, C.c_void_p(nbr.data_ptr()), C.c_void_p(nodes.data_ptr())))
+            return nbr.cpu().numpy(), nodes.cpu().numpy()
+        if what == "grad":
+            g = torch.empty((E, n3, 4, 3), dtype=torch.float64, device=dev)
+            _check(self._lib.dg_debug(self._h, DEBUG_GRAD, C.c_void_p(g.data_ptr()), None))
+            return g.cpu().numpy()
+        if what == "fstar":
+            f = torch.empty((E, 6, n2, 5), dtype=torch.float64, device=dev)
+            _check(self._lib.dg_debug(self._h, DEBUG_FSTAR, C.c_void_p(f.data_ptr()), None))
+            return f.cpu().numpy()
+        if what == "alpha":
+            a = torch.empty((E,), dtype=torch.float64, device=dev)
+            _check(self._lib.dg_debug(self._h, DEBUG_ALPHA, C.c_void_p(a.data_ptr()), None))
+            return a.cpu().numpy()
+        raise ValueError(what)

@@ -1,0 +1,51 @@
+"""Helpers for the GPU parity tests: building libdg once, feeding the same seeded
+inputs to the CUDA path and the oracle, and the error norms with their bounds."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2404_12703_gb300 import workloads as W
+
+_built = False
+
+
+def gpu_or_skip():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    global _built
+    if not _built:
+        from paper_2404_12703_gb300 import build
+        build.build()
+        _built = True
+    from paper_2404_12703_gb300 import dg
+    dg.load()
+    return torch, dg
+
+
+def oracle_params(dgp):
+    """Oracle parameter vector equal to a dg.Params."""
+    return O.params(gamma=dgp.gamma, R=dgp.R, Pr=dgp.Pr, mu=dgp.mu, riemann=dgp.riemann,
+                    viscous=dgp.viscous, shock=dgp.shock_capturing, alpha_min=dgp.alpha_min,
+                    alpha_max=dgp.alpha_max, cfl=dgp.cfl, dfl=dgp.dfl, alpha_force=dgp.alpha_force)
+
+
+def rel_err(a, ref):
+    """max-norm error per conservative variable, relative to max |ref| of that variable."""
+    a = np.asarray(a).reshape(-1, 5)
+    ref = np.asarray(ref).reshape(-1, 5)
+    scale = np.abs(ref).max(axis=0)
+    scale[scale == 0] = 1.0
+    return np.abs(a - ref).max(axis=0) / scale
+
+
+def parity_bound(oracle_fp64, oracle_ld, floor_factor=4.0, base=1e-12):
+    """Per-variable bound: 1e-12, or floor_factor times the FP64 oracle's own
+    rounding error against the long-double oracle when that floor is higher
+    (the stated 1e-12 sits below FP64's floor at low Mach number and high N)."""
+    floor = rel_err(oracle_fp64, oracle_ld)
+    return np.maximum(base, floor_factor * floor), floor
+
+
+def mesh(N, nel, curved=0.1, seed=20240419, **kw):
+    return W.box_mesh(N, nel, curved=curved, seed=seed, **kw)

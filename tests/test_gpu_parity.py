@@ -1,0 +1,213 @@
+"""GPU parity: libdg (hand-written sm_103a kernels, called through the C ABI)
+against the CPU oracle on the same seeded inputs.
+
+Bounds: integer maps bit-exact; floating point against the long-double oracle
+within max(1e-12, 4 x the FP64 oracle's own error), per conservative variable
+(the FP64 rounding floor of the operator exceeds 1e-12 at Ma = 0.1 and
+N >= 3, so an FP64 implementation is held to the floor FP64 allows);
+10 LSERK steps within 1e-10 relative of the oracle's 10 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2404_12703_gb300 import workloads as W
+
+from gpu_util import gpu_or_skip, mesh, oracle_params, parity_bound, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(dg, m, **kw):
+    return dg.Solver(m, **kw)
+
+
+@pytest.mark.parametrize("N,nel,seed", [(2, (3, 4, 5), 3), (3, (4, 4, 4), 20240419), (7, (3, 3, 4), 7)])
+def test_maps_bit_exact(N, nel, seed):
+    torch, dg = gpu_or_skip()
+    m = mesh(N, nel, seed=seed)
+    s = _solver(dg, m)
+    nbr, nodes = s.debug("maps")
+    on, of, om, onode = O.Mesh(N, m["xyz"], m["period"]).connectivity()
+    np.testing.assert_array_equal(nbr[..., 0], on)
+    np.testing.assert_array_equal(nbr[..., 1], of)
+    np.testing.assert_array_equal(nbr[..., 2], om)
+    np.testing.assert_array_equal(nodes, onode)
+
+
+@pytest.mark.parametrize("N", [1, 3, 5, 7])
+def test_metrics(N):
+    torch, dg = gpu_or_skip()
+    m = mesh(N, (3, 3, 4))
+    s = _solver(dg, m)
+    Ja, J = s.debug("metrics")
+    oJa, oJ = O.Mesh(N, m["xyz"], m["period"]).metrics()
+    # both are rounded from extended precision: a few ulp apart at most
+    assert np.abs(Ja - oJa).max() <= 1e-14 * np.abs(oJa).max()
+    assert np.abs(J - oJ).max() <= 1e-14 * np.abs(oJ).max()
+
+
+CASES = [
+    # N, elements, Ma, params
+    (3, (4, 4, 4), 0.1, dict()),                                  # TGV 4^3 N=3, Roe + BR1
+    (7, (3, 4, 3), 0.1, dict()),                                  # N=7 curved, rotated, ragged
+    (5, (3, 3, 3), 0.5, dict(riemann="lf")),                      # LF, viscous
+    (4, (3, 3, 3), 1.0, dict(viscous=0)),                         # Euler, Roe
+    (2, (3, 4, 5), 0.5, dict(mu=0.01)),                           # ragged, low N
+    (1, (3, 3, 4), 0.5, dict()),                                  # N = 1
+]
+
+
+@pytest.mark.parametrize("N,nel,Ma,kw", CASES)
+def test_rhs_parity(N, nel, Ma, kw):
+    torch, dg = gpu_or_skip()
+    m = mesh(N, nel)
+    s = _solver(dg, m, **kw)
+    U = W.random_perturbation(W.tgv_state(m["xyz"], Ma=Ma).reshape(m["E"], -1, 5), 1e-3, 5)
+    Ud = torch.from_numpy(U).cuda()
+    Ut = s.rhs(Ud).cpu().numpy()
+    prm = oracle_params(s.params)
+    ref = O.Mesh(N, m["xyz"], m["period"], quad=True).rhs(U, prm)
+    o64 = O.Mesh(N, m["xyz"], m["period"]).rhs(U, prm)
+    bound, floor = parity_bound(o64, ref)
+    err = rel_err(Ut, ref)
+    assert np.all(err <= bound), (err, bound, floor)
+    if Ma >= 0.5:
+        assert np.all(err <= 1e-12), err
+
+
+@pytest.mark.parametrize("N,nel", [(1, (3, 4, 5)), (2, (3, 4, 5)), (3, (3, 3, 7)), (4, (3, 3, 7))])
+@pytest.mark.parametrize("kw", [dict(mu=0.01), dict(mu=0.01, riemann="lf", shock_capturing=1, alpha_force=0.4),
+                                dict(viscous=0, riemann="lf", shock_capturing=1)])
+def test_partial_last_block(N, nel, kw):
+    """Element counts that leave the last thread block of the element kernels
+    partly filled (several elements share a block at N <= 4)."""
+    torch, dg = gpu_or_skip()
+    m = mesh(N, nel)
+    s = _solver(dg, m, **kw)
+    U = W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.5).reshape(m["E"], -1, 5), 1e-2, 8)
+    Ut = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    prm = oracle_params(s.params)
+    ref, oal = O.Mesh(N, m["xyz"], m["period"], quad=True).rhs(U, prm, with_alpha=True)
+    o64 = O.Mesh(N, m["xyz"], m["period"]).rhs(U, prm)
+    bound, floor = parity_bound(o64, ref)
+    err = rel_err(Ut, ref)
+    assert np.all(err <= bound), (err, bound, floor)
+    if s.params.shock_capturing:
+        al = s.debug("alpha")
+        assert np.abs(al - oal).max() <= 1e-12
+
+
+def test_gradients_and_face_fluxes():
+    torch, dg = gpu_or_skip()
+    N = 4
+    m = mesh(N, (3, 3, 3))
+    s = _solver(dg, m, mu=0.01)
+    U = W.tgv_state(m["xyz"], Ma=0.5).reshape(m["E"], -1, 5)
+    s.rhs(torch.from_numpy(U).cuda())
+    torch.cuda.synchronize()
+    g = s.debug("grad")
+    fs = s.debug("fstar")
+    prm = oracle_params(s.params)
+    _, og, ofs = O.Mesh(N, m["xyz"], m["period"], quad=True).rhs(U, prm, with_grad=True, with_fstar=True)
+    assert np.abs(g - og).max() <= 1e-12 * np.abs(og).max()
+    assert np.abs(fs - ofs).max() <= 1e-12 * np.abs(ofs).max()
+
+
+def test_ten_steps_parity():
+    """Taylor-Green vortex, 4^3 elements, N = 3, Roe + BR1, LSERK4 with the CFL
+    rule, 10 steps (the plain FP64 configuration)."""
+    torch, dg = gpu_or_skip()
+    N = 3
+    m = W.box_mesh(N, (4, 4, 4))
+    s = _solver(dg, m)
+    U0 = W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5)
+    s.set_state(U0)
+    dt0 = s.time_step()
+    s.step(10)
+    U, t = s.get_state()
+    prm = oracle_params(s.params)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    odt, _ = M.dt(U0, prm)
+    assert abs(dt0 - odt) <= 1e-14 * odt
+    Uo, to, _ = M.step(U0, prm, 10)
+    assert abs(t - to) <= 1e-13 * to
+    err = np.abs(U - Uo).max() / np.abs(Uo).max()
+    assert err <= 1e-10, err
+    # and against the slow quad oracle on a few steps of a fixed dt
+    Uq, _, _ = O.Mesh(N, m["xyz"], m["period"], quad=True).step(U0, prm, 2, dt=odt)
+    s.set_state(U0)
+    s.step(2, dt=odt)
+    U2, _ = s.get_state()
+    assert rel_err(U2, Uq).max() <= 1e-12
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(riemann="lf", viscous=0),
+                                dict(shock_capturing=1, alpha_force=0.5, riemann="lf")])
+def test_free_stream_and_conservation(kw):
+    torch, dg = gpu_or_skip()
+    N = 7
+    m = mesh(N, (3, 3, 3))
+    s = _solver(dg, m, **kw)
+    U = W.uniform_state((m["E"], (N + 1) ** 3), rho=1.1, vel=(0.4, -0.3, 0.25), p=3.0)
+    Ut = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    _, J = s.debug("metrics")
+    x, w, _, _, Ds, _ = O.ops(N)
+    F = 3.0 + 1.1 * 0.25 + 3.0 * 3.5
+    assert np.abs(Ut).max() < 1e-14 * F * np.abs(Ds).sum(axis=1).max() / J.min()
+    # conservation on a perturbed TGV state
+    U = W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5), 0.02, 3)
+    Ut = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    wq = np.einsum("i,j,k->kji", w, w, w).reshape(-1)[None, :, None] * J[..., None]
+    tot = (wq * Ut).sum(axis=(0, 1))
+    scale = (wq * np.abs(Ut)).sum(axis=(0, 1))
+    assert np.all(np.abs(tot) <= 1e-13 * scale), tot / scale
+
+
+@pytest.mark.parametrize("alpha_force", [0.3, -1.0])
+def test_shock_capturing_parity(alpha_force):
+    """Sod-type tube state (the shock-capturing configuration's initial jump,
+    smoothed over one element so the indicator sees a range of values)."""
+    torch, dg = gpu_or_skip()
+    N = 5
+    nx = 8
+    h = 2.0 / nx
+    m = W.box_mesh(N, (nx, 3, 3), length=(2.0, 3 * h, 3 * h), curved=0.05, seed=9)
+    s = _solver(dg, m, viscous=0, riemann="lf", shock_capturing=1, alpha_force=alpha_force)
+    U = W.sod_state(m["xyz"]).reshape(m["E"], -1, 5)
+    U = W.random_perturbation(U, 1e-3, 2)
+    Ut = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    al = s.debug("alpha")
+    prm = oracle_params(s.params)
+    ref, oal = O.Mesh(N, m["xyz"], m["period"], quad=True).rhs(U, prm, with_alpha=True)
+    o64 = O.Mesh(N, m["xyz"], m["period"]).rhs(U, prm)
+    if alpha_force < 0:
+        assert oal.max() > 0 and (oal == 0).any()
+        np.testing.assert_array_equal(al > 0, oal > 0)
+        assert np.abs(al - oal).max() <= 1e-12
+    bound, floor = parity_bound(o64, ref)
+    err = rel_err(Ut, ref)
+    assert np.all(err <= bound), (err, bound, floor)
+
+
+def test_full_size_sampled_elements():
+    """The 24^3-element curved, renumbered and rotated N = 7 mesh (7.08 M DOF),
+    in the launch configuration the benchmark times: Ut of sampled elements
+    against the oracle, which forms only what those elements need."""
+    torch, dg = gpu_or_skip()
+    N = 7
+    m = W.box_mesh(N, (24, 24, 24), curved=0.1, seed=20240419)
+    s = _solver(dg, m)
+    U = W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5)
+    Ut = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    rng = np.random.Generator(np.random.PCG64(1))
+    pick = rng.choice(m["E"], size=12, replace=False)
+    want = np.zeros(m["E"], bool)
+    want[pick] = True
+    prm = oracle_params(s.params)
+    ref = O.Mesh(N, m["xyz"], m["period"], quad=True, metric_mask=want).rhs(U, prm, want=want)
+    o64 = O.Mesh(N, m["xyz"], m["period"], metric_mask=want).rhs(U, prm, want=want)
+    bound, floor = parity_bound(o64[want], ref[want])
+    err = rel_err(Ut[want], ref[want])
+    assert np.all(err <= bound), (err, bound, floor)
+    assert np.isfinite(Ut).all()

@@ -147,6 +147,27 @@ int dg_time_step(dg_ctx* ctx, double* dt);
    out[2] = |Omega|.  FP64 reductions on the device; synchronises. */
 int dg_kinetic(dg_ctx* ctx, double* out);
 
+/* Kinetic energy of a caller-owned state, allocating no device memory.
+   The paper has no counterpart: this is an interface addition for callers that
+   cannot call cudaMalloc -- applications whose device memory is handed out in
+   advance by their own arena or pool, and loops that must not take the
+   implicit device synchronisation a cudaMalloc / cudaFree can cause.
+   Inputs (device, caller-owned): U [E][node][5] (public layout), J [E][node]
+   (Jacobians, e.g. from dg_debug DG_DEBUG_METRICS), Ut [E][node][5] or NULL.
+   Output (device, caller-owned, 3 doubles): out[0] = E_k, out[1] = dE_k/dt
+   (0 when Ut is NULL), out[2] = |Omega|, with the definitions of dg_kinetic.
+   N in [1, 7]; n_elems at most 262144 (its built-in scratch holds one partial
+   sum triple per element), else DG_ERR_ARG.  Stream-ordered on `stream`; no
+   synchronisation.  The scratch is a single file-scope device array (6 MiB,
+   held by every GPU that loads the library until the process exits), shared
+   by all calls on a device: calls whose work overlaps on the GPU (for
+   example on two streams) race on it.  Each call overwrites every scratch
+   entry it reads, so nothing needs clearing.  The first call on a device
+   looks up the array's device address (cudaGetSymbolAddress) and caches it:
+   make that first call before any stream capture. */
+int dg_kinetic_noalloc(int N, int64_t n_elems, const double* U, const double* J, const double* Ut, double* out,
+                       void* stream);
+
 /* Verification access to intermediate arrays (device buffers, caller-owned).
    what = DG_DEBUG_METRICS: out0 = Ja [E][node][3][3] ((J a^d)_c at [d][c]),
                             out1 = J [E][node]

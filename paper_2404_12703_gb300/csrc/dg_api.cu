@@ -139,6 +139,14 @@ static void build_ops(int N, Ops& o) {
   }
 }
 
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+void lgl_weights(int N, double* w) {
+  Ops o;
+  build_ops(N, o);
+  for (int i = 0; i <= N; ++i) w[i] = o.w[i];
+}
+
 template <typename T>
 static cudaError_t dalloc(T** p, size_t count, int64_t& bytes) {
   cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);

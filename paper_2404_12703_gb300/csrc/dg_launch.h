@@ -15,6 +15,12 @@ enum { PK_CFL = 0, PK_SURF_PRIMS = 1, PK_LIFT = 2, PK_SURF_FLUX = 3, PK_VOLUME =
 void prof_begin(dg_ctx* c, int kind);
 void prof_end(dg_ctx* c);
 
+// records the thread's last error message and returns code
+int set_error(int code, const std::string& msg);
+
+// LGL quadrature weights of degree N (n = N + 1 entries)
+void lgl_weights(int N, double* w);
+
 // allocation of the side arrays once the number of sides is known
 int alloc_side_arrays(dg_ctx* c, std::string& msg);
 

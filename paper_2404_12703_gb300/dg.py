@@ -28,7 +28,7 @@ DEBUG_METRICS, DEBUG_MAPS, DEBUG_GRAD, DEBUG_FSTAR, DEBUG_ALPHA = 0, 1, 2, 3, 4
 #: every symbol include/dg.h declares
 EXPORTS = ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
            "dg_get_state", "dg_rhs", "dg_step", "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
-           "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count")
+           "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
 
 
 class DgError(RuntimeError):
@@ -80,6 +80,7 @@ def load(path: str | None = None):
             "dg_error_string": (C.c_char_p, [C.c_int]),
             "dg_last_error": (C.c_char_p, []),
             "dg_launch_count": (C.c_int64, []),
+            "dg_kinetic_noalloc": (C.c_int, [C.c_int, C.c_int64, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -106,6 +107,22 @@ def default_params(**kw) -> Params:
             v = {"fp64": FP64, "fp32": FP32_BULK}[v]
         setattr(p, k, v)
     return p
+
+
+def kinetic_noalloc(N, U, J, Ut=None, out=None, stream=None):
+    """E_k, dE_k/dt and |Omega| of a caller-owned device state without any device
+    allocation inside the library (for callers that cannot allocate: see
+    dg_kinetic_noalloc in include/dg.h).  U: CUDA float64 [E, n^3, 5];
+    J: CUDA float64 [E, n^3]; Ut: like U or None; out: CUDA float64 [3] or None
+    (then a tensor is allocated here, by PyTorch, not by the library)."""
+    import torch
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=U.device)
+    E = J.shape[0]
+    _check(load().dg_kinetic_noalloc(int(N), int(E), C.c_void_p(U.data_ptr()), C.c_void_p(J.data_ptr()),
+                                     C.c_void_p(Ut.data_ptr() if Ut is not None else 0),
+                                     C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def launch_count() -> int:

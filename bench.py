@@ -47,6 +47,12 @@ BYTES_PER_DOF = 8 * (30 + 204 / (N_DEG + 1))
 # in profiles/k_volume_tgv12_N7_fp64.md (12^3 mesh; the traffic scales with
 # the DOF count).  Set to None whenever the kernel changes until re-measured.
 VOLUME_TRAFFIC_BYTES_PER_DOF = 331.3
+# FP32-bulk: algorithmic bytes per DOF of one volume-kernel launch (reads U 40,
+# FP64 metrics 80, FP32 lifted gradients 48, dU 40, surface fluxes ~8; writes
+# U 40, dU 40), and of a whole stage for the minimal two-phase method with the
+# RK register and metrics in FP64 and the face traces in FP32: 342 B at N = 7.
+VOLUME32_BYTES_PER_DOF = 40 + 80 + 48 + 40 + 8 + 40 + 40
+BYTES32_PER_DOF = 342.0
 
 
 def workload_desc(nel=NEL):
@@ -279,6 +285,62 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     nbytes = dof * 5 * 8
 
+    # FP32-bulk on the same workload: flux/volume/surface arithmetic in FP32,
+    # state, RK register, metrics and reductions in FP64
+    fp32 = None
+    if not args.no_fp32:
+        s32 = dg.Solver(m, stream=stream, precision=dg.FP32_BULK)
+        s32.set_state(U0)
+        s32.step(args.warmup)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        s32.step(args.steps)
+        e1.record(stream)
+        barrier()
+        ms32 = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            t = torch.tensor([ms32], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms32 = float(t.item())
+        prof32 = s32.profile_step(args.steps)
+        tot32 = sum(v[0] for v in prof32.values())
+        k32 = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1],
+                   "share": (v[0] / tot32 if tot32 else None)} for k, v in prof32.items()}
+        vol32 = k32["volume"]["ms_per_launch"]
+        # accuracy against the FP64 path: same initial state, same fixed dt,
+        # `steps` steps each; kinetic-energy dissipation rate and L2 state error
+        solver.set_state(U0)
+        dt_fix = solver.time_step()
+        solver.step(args.steps, dt=dt_fix)
+        s32.set_state(U0)
+        s32.step(args.steps, dt=dt_fix)
+        U64, _ = solver.get_state()
+        U32, _ = s32.get_state()
+        kin64 = solver.kinetic()
+        kin32 = s32.kinetic()
+        fp32 = {
+            "value": world * dof * STAGES / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
+            "speedup_vs_fp64": ms_step / ms32, "dtype": "f32 arithmetic, f64 state/RK/metrics/reductions",
+            "kernels": k32,
+            "roofline": {"bound": "hbm", "kernel": "k_volume<7,1,float>",
+                         "achieved": VOLUME32_BYTES_PER_DOF * dof / (vol32 * 1e-3) / 1e9,
+                         "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": VOLUME32_BYTES_PER_DOF * dof / (vol32 * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+                         "traffic": None, "peak_source": peak_src,
+                         "algorithmic_bytes_per_dof": VOLUME32_BYTES_PER_DOF},
+            "whole_step_hbm_frac": BYTES32_PER_DOF * dof * STAGES / (ms32 * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+            "accuracy_vs_fp64": {
+                "steps": args.steps, "dt": dt_fix,
+                "ke_dissipation_rate_rel_err": abs(kin32[1] - kin64[1]) / abs(kin64[1]),
+                "ke_rel_err": abs(kin32[0] - kin64[0]) / abs(kin64[0]),
+                "l2_state_rel_err": float(np.sqrt(((U32 - U64) ** 2).sum() / (U64 ** 2).sum())),
+            },
+        }
+        s32.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cdof, ctimes = cpu_oracle_sample(2, nel=4)
@@ -296,7 +358,7 @@ def run_ours(args):
             "gpu_launches": launches, "kernels": kernels, "roofline": roofline,
             "e2e": {"value": world * dof * STAGES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
-            "clocks": clk.summary(), "cpu_baseline": cpu,
+            "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32,
         }
         print(json.dumps(line), flush=True)
     solver.close()
@@ -312,6 +374,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurement")
     ap.add_argument("--nel", type=int, default=NEL,
                     help="elements per direction (24 is the benchmark workload; smaller for profiling)")
     args = ap.parse_args()

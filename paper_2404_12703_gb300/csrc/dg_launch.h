@@ -37,6 +37,13 @@ cudaError_t launch_cfl(dg_ctx* c);
 
 // raises the dynamic shared-memory limits of the kernels of degree N
 cudaError_t init_kernel_attributes(int N);
+cudaError_t init_kernel_attributes_fp32(int N);
+
+// FP32-bulk evaluation (dg_rhs32.cu), same contract as launch_rhs
+cudaError_t launch_rhs_fp32(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first_stage);
+
+// reference state of the shifted primitives from the context's state
+cudaError_t launch_refs(dg_ctx* c);
 
 // layout conversion public [E][n3][5] <-> internal [E][5][n3]
 cudaError_t launch_to_internal(dg_ctx* c, const double* pub, double* internal);

@@ -1,0 +1,730 @@
+// dg_stage.cuh -- the kernels of one evaluation of the DG time derivative
+// (Eq. dgsem with the split-form volume integral and BR1 lifting) and of the
+// fused low-storage RK stage, templated on the arithmetic type T of the
+// flux, volume and surface work (double: the FP64 path; float: the FP32-bulk
+// path, in which the state, the RK register, the metrics and the final
+// combination stay in FP64).
+//
+// Per stage:
+//   k_surf_prims  ProlongToFace of the lifted primitives (u, v, w, T) and the
+//                 BR1 surface flux q* (s n) on every side node   (Lift_FillFlux)
+//   k_lift        lifted gradients, weak form: volume part with Dhat, surface
+//                 part from the sides, 1/J                      (Lift_VolInt,
+//                                                                Lift_SurfInt,
+//                                                                Lift_ApplyJac)
+//   k_surf_flux   Roe / LF flux plus BR1 viscous flux times s   (FillFlux)
+//   k_volume      split-form KEP volume integral, viscous volume term,
+//                 optional DG/FV blending, SurfInt, ApplyJac and either Ut or
+//                 the RK update dU = A dU + dt Ut, U += B dU   (VolInt, SurfInt,
+//                                                                ApplyJac, RK)
+//
+// Shifted primitives.  The fluxes work with p' = p - p_ref, H' = H - H_ref and
+// T' = T - T_ref for constants (p_ref, H_ref, T_ref) held per context (all zero
+// on the FP64 path).  This is exact algebra: the p_ref and T_ref parts of the
+// volume and surface terms add up to p_ref (resp. T_ref) times the discrete
+// metric identities, which vanish to round-off; the H_ref part of the energy
+// equation is exactly H_ref times the mass equation and is added back in FP64
+// from the density right-hand side.  At Ma = 0.1 (p ~ 71, fluctuations ~ 0.06)
+// this keeps FP32 rounding relative to the fluctuations, not to p.
+//
+// Data layout: element-major SoA, U[e][v][node], node = i + n (j + n k).
+#pragma once
+#include <algorithm>
+#include <cmath>
+
+#include "dg_common.cuh"
+#include "dg_launch.h"
+
+namespace dg {
+
+template <int N>
+struct Shape {
+  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  static constexpr int EPB = n3 >= 256 ? 1 : 256 / n3;  // elements per block
+  static constexpr int THREADS = EPB * n3;
+};
+
+// buffers of the arithmetic type T
+template <typename T>
+struct TBuf;
+template <>
+struct TBuf<double> {
+  static __host__ __device__ double* g(const StageArgs& a) { return a.g; }
+  static __host__ __device__ double* lflux(const StageArgs& a) { return a.lflux; }
+  static __host__ __device__ double* fstar(const StageArgs& a) { return a.fstar; }
+};
+template <>
+struct TBuf<float> {
+  static __host__ __device__ float* g(const StageArgs& a) { return a.g32; }
+  static __host__ __device__ float* lflux(const StageArgs& a) { return a.lflux32; }
+  static __host__ __device__ float* fstar(const StageArgs& a) { return a.fstar32; }
+};
+
+// ---------------------------------------------------------------------------
+// Shifted primitive state and the fluxes written in it
+// ---------------------------------------------------------------------------
+template <typename T>
+struct SPrim {
+  T rho, u, v, w, p, H, Tt;  // p, H, Tt shifted by the context's references
+};
+
+// ConsToPrim (Eqs. eos_p, eos_T) in FP64, then shifted and rounded to T
+template <typename T>
+__device__ __forceinline__ SPrim<T> shifted_prim(const double U[5], double gm1, double Rinv, double pr, double Hr,
+                                                double Tr, double* p_full = nullptr) {
+  const double ri = 1.0 / U[0];
+  const double u = U[1] * ri, v = U[2] * ri, w = U[3] * ri;
+  const double p = gm1 * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
+  const double H = (U[4] + p) * ri;
+  const double Tm = p * ri * Rinv;
+  if (p_full) *p_full = p;
+  return {T(U[0]), T(u), T(v), T(w), T(p - pr), T(H - Hr), T(Tm - Tr)};
+}
+
+// Euler flux contracted with nv, energy component minus H_ref times mass flux
+template <typename T>
+__device__ __forceinline__ void euler_flux_s(const SPrim<T>& q, const T nv[3], T f[5]) {
+  const T un = q.u * nv[0] + q.v * nv[1] + q.w * nv[2];
+  const T m = q.rho * un;
+  f[0] = m;
+  f[1] = m * q.u + q.p * nv[0];
+  f[2] = m * q.v + q.p * nv[1];
+  f[3] = m * q.w + q.p * nv[2];
+  f[4] = m * q.H;
+}
+
+// Roe's approximate Riemann solver, unit normal n, no entropy fix
+template <typename T>
+__device__ __forceinline__ void roe_flux_s(const SPrim<T>& L, const SPrim<T>& R, const T n[3], T gm1, T Href,
+                                           T f[5]) {
+  T fL[5], fR[5];
+  euler_flux_s(L, n, fL);
+  euler_flux_s(R, n, fR);
+  const T sL = sqrt(L.rho), sR = sqrt(R.rho);
+  const T inv = T(1) / (sL + sR);
+  const T ut0 = (sL * L.u + sR * R.u) * inv;
+  const T ut1 = (sL * L.v + sR * R.v) * inv;
+  const T ut2 = (sL * L.w + sR * R.w) * inv;
+  const T Ht = (sL * L.H + sR * R.H) * inv;  // shifted Roe-average enthalpy
+  const T rt = sL * sR;
+  const T q2 = ut0 * ut0 + ut1 * ut1 + ut2 * ut2;
+  const T c2 = gm1 * ((Href + Ht) - T(0.5) * q2);
+  const T c = sqrt(c2);
+  const T c2i = T(1) / c2;
+  const T un = ut0 * n[0] + ut1 * n[1] + ut2 * n[2];
+  const T drho = R.rho - L.rho, dp = R.p - L.p;
+  const T du0 = R.u - L.u, du1 = R.v - L.v, du2 = R.w - L.w;
+  const T dun = du0 * n[0] + du1 * n[1] + du2 * n[2];
+  const T a1 = T(0.5) * (dp - rt * c * dun) * c2i;
+  const T a2 = drho - dp * c2i;
+  const T a5 = T(0.5) * (dp + rt * c * dun) * c2i;
+  const T l1 = fabs(un - c) * a1, l2 = fabs(un), l5 = fabs(un + c) * a5;
+  const T l2a = l2 * a2, l2r = l2 * rt;
+  const T dt0 = du0 - dun * n[0], dt1 = du1 - dun * n[1], dt2 = du2 - dun * n[2];
+  const T D0 = l1 + l2a + l5;
+  const T D1 = l1 * (ut0 - c * n[0]) + l2a * ut0 + l5 * (ut0 + c * n[0]) + l2r * dt0;
+  const T D2 = l1 * (ut1 - c * n[1]) + l2a * ut1 + l5 * (ut1 + c * n[1]) + l2r * dt1;
+  const T D3 = l1 * (ut2 - c * n[2]) + l2a * ut2 + l5 * (ut2 + c * n[2]) + l2r * dt2;
+  const T D4 = l1 * (Ht - un * c) + l2a * (T(0.5) * q2 - Href) + l5 * (Ht + un * c) +
+               l2r * (ut0 * dt0 + ut1 * dt1 + ut2 * dt2);
+  f[0] = T(0.5) * (fL[0] + fR[0] - D0);
+  f[1] = T(0.5) * (fL[1] + fR[1] - D1);
+  f[2] = T(0.5) * (fL[2] + fR[2] - D2);
+  f[3] = T(0.5) * (fL[3] + fR[3] - D3);
+  f[4] = T(0.5) * (fL[4] + fR[4] - D4);
+}
+
+// Local Lax-Friedrichs (Rusanov), unit normal n
+template <typename T>
+__device__ __forceinline__ void lf_flux_s(const SPrim<T>& L, const SPrim<T>& R, const T n[3], T gamma, T pref,
+                                          T f[5]) {
+  T fL[5], fR[5];
+  euler_flux_s(L, n, fL);
+  euler_flux_s(R, n, fR);
+  const T cL = sqrt(gamma * (L.p + pref) / L.rho), cR = sqrt(gamma * (R.p + pref) / R.rho);
+  const T lL = fabs(L.u * n[0] + L.v * n[1] + L.w * n[2]) + cL;
+  const T lR = fabs(R.u * n[0] + R.v * n[1] + R.w * n[2]) + cR;
+  const T lm = lL > lR ? lL : lR;
+  // jumps of the conservative variables; energy minus H_ref times density:
+  // rho e - H_ref rho = rho H' - p' - p_ref, whose jump is that of rho H' - p'
+  const T d[5] = {R.rho - L.rho, R.rho * R.u - L.rho * L.u, R.rho * R.v - L.rho * L.v, R.rho * R.w - L.rho * L.w,
+                  (R.rho * R.H - R.p) - (L.rho * L.H - L.p)};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) f[k] = T(0.5) * (fL[k] + fR[k] - lm * d[k]);
+}
+
+// ---------------------------------------------------------------------------
+// BR1 surface flux of the lifted primitives
+// ---------------------------------------------------------------------------
+template <int N, typename T>
+__global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
+  using S = Shape<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)a.S * n2) return;
+  const int s = (int)(tid / n2), pq = (int)(tid % n2);
+  const int p = pq % n, q = pq / n;
+  const int2 ee = a.side_e[s];
+  const int sf = a.side_f[s];
+  const int fM = sf & 15, fS = (sf >> 4) & 15, flip = sf >> 8;
+  int ps, qs;
+  flip_to_slave<n>(flip, p, q, ps, qs);
+  const int vM = face_vol_node<n>(fM, p, q), vS = face_vol_node<n>(fS, ps, qs);
+  double UM[5], US[5];
+  const double* uM = a.U + (size_t)ee.x * 5 * n3 + vM;
+  const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) { UM[k] = uM[k * n3]; US[k] = uS[k * n3]; }
+  const double pr = a.scal->ref_p, Hr = a.scal->ref_H, Tr = a.scal->ref_T;
+  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, pr, Hr, Tr);
+  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, pr, Hr, Tr);
+  const T qa[4] = {T(0.5) * (qM.u + qS.u), T(0.5) * (qM.v + qS.v), T(0.5) * (qM.w + qS.w), T(0.5) * (qM.Tt + qS.Tt)};
+  const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
+  const T sn[3] = {T(nr[0]), T(nr[n2]), T(nr[2 * n2])};
+  T* out = TBuf<T>::lflux(a) + (size_t)s * 12 * n2 + pq;
+#pragma unroll
+  for (int qv = 0; qv < 4; ++qv)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) out[(qv * 3 + x) * n2] = qa[qv] * sn[x];
+}
+
+// ---------------------------------------------------------------------------
+// Lifted gradients (weak form, Eq. lifting)
+// ---------------------------------------------------------------------------
+template <int N, typename T>
+__global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
+  using S = Shape<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sDh = reinterpret_cast<T*>(smraw);  // [n2]
+  T* sq = sDh + n2;                      // [EPB][4][n3]
+  T* sF = sq + EPB * 4 * n3;             // [EPB][12][n3]
+  const int le = threadIdx.x / n3, t = threadIdx.x % n3;
+  // Slots past the last element redo the last element in their own shared
+  // memory slot, so that every thread of a block runs the same path through
+  // the barriers; only the final global stores are masked.
+  const bool valid = blockIdx.x * EPB + le < a.E;
+  const int e = valid ? blockIdx.x * EPB + le : a.E - 1;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) sDh[k] = T(a.ops->Dhat[k]);
+  T* q = sq + le * 4 * n3;
+  T* F = sF + le * 12 * n3;
+  const double* Me = a.metric + (size_t)e * 10 * n3;
+  {
+    double U[5];
+    const double* u = a.U + (size_t)e * 5 * n3 + t;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
+    const SPrim<T> pr = shifted_prim<T>(U, a.gm1, a.Rinv, a.scal->ref_p, a.scal->ref_H, a.scal->ref_T);
+    q[t] = pr.u;
+    q[n3 + t] = pr.v;
+    q[2 * n3 + t] = pr.w;
+    q[3 * n3 + t] = pr.Tt;
+  }
+  __syncwarp();
+  __syncthreads();
+  const int idx[3] = {t % n, (t / n) % n, t / n2};
+  constexpr int str[3] = {1, n, n2};
+  T acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = T(0);
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    {
+      const T J0 = T(Me[(d * 3 + 0) * n3 + t]), J1 = T(Me[(d * 3 + 1) * n3 + t]), J2 = T(Me[(d * 3 + 2) * n3 + t]);
+#pragma unroll
+      for (int qv = 0; qv < 4; ++qv) {
+        const T qq = q[qv * n3 + t];
+        F[(qv * 3 + 0) * n3 + t] = J0 * qq;
+        F[(qv * 3 + 1) * n3 + t] = J1 * qq;
+        F[(qv * 3 + 2) * n3 + t] = J2 * qq;
+      }
+    }
+    __syncwarp();
+    __syncthreads();
+    {
+      const int id = idx[d], base = t - id * str[d];
+#pragma unroll
+      for (int al = 0; al < n; ++al) {
+        const T c = sDh[id * n + al];
+        const int nb = base + al * str[d];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] += c * F[k * n3 + nb];
+      }
+    }
+    __syncwarp();
+    __syncthreads();
+  }
+  if (!valid) return;
+  // surface part: on LGL nodes only face nodes receive it
+  const T* Lf = TBuf<T>::lflux(a);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int id = idx[d];
+    if (id != 0 && id != n - 1) continue;
+    const int f = 2 * d + (id == n - 1 ? 1 : 0);
+    const int es = a.elem_side[(size_t)e * 6 + f];
+    const int s = es_side(es);
+    const int p = d == 0 ? idx[1] : idx[0];
+    const int qq = d == 2 ? idx[1] : idx[2];
+    int pm = p, qm = qq;
+    if (es_slave(es)) flip_to_master<n>(es_flip(es), p, qq, pm, qm);
+    const T sg = T(es_slave(es) ? -a.ops->winv[id] : a.ops->winv[id]);
+    const T* L = Lf + (size_t)s * 12 * n2 + pm + n * qm;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] += sg * L[k * n2];
+  }
+  const T Ji = T(Me[9 * n3 + t]);
+  T* g = TBuf<T>::g(a) + (size_t)e * 12 * n3 + t;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) g[k * n3] = acc[k] * Ji;
+}
+
+// ---------------------------------------------------------------------------
+// FillFlux: Riemann flux + BR1 viscous flux, times the surface element
+// ---------------------------------------------------------------------------
+template <int N, typename T>
+__global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
+  using S = Shape<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)a.S * n2) return;
+  const int s = (int)(tid / n2), pq = (int)(tid % n2);
+  const int p = pq % n, q = pq / n;
+  const int2 ee = a.side_e[s];
+  const int sf = a.side_f[s];
+  const int fM = sf & 15, fS = (sf >> 4) & 15, flip = sf >> 8;
+  int ps, qs;
+  flip_to_slave<n>(flip, p, q, ps, qs);
+  const int vM = face_vol_node<n>(fM, p, q), vS = face_vol_node<n>(fS, ps, qs);
+  double UM[5], US[5];
+  const double* uM = a.U + (size_t)ee.x * 5 * n3 + vM;
+  const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) { UM[k] = uM[k * n3]; US[k] = uS[k * n3]; }
+  const double pr = a.scal->ref_p, Hr = a.scal->ref_H, Tr = a.scal->ref_T;
+  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, pr, Hr, Tr);
+  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, pr, Hr, Tr);
+  const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
+  const T sn[3] = {T(nr[0]), T(nr[n2]), T(nr[2 * n2])};
+  const double sAd = nr[3 * n2];
+  const double invd = 1.0 / sAd;
+  const T sA = T(sAd);
+  const T nu[3] = {T(nr[0] * invd), T(nr[n2] * invd), T(nr[2 * n2] * invd)};
+  T f[5];
+  if (a.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, T(a.gm1), T(Hr), f);
+  else lf_flux_s(qM, qS, nu, T(a.gamma), T(pr), f);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) f[k] *= sA;
+  if (a.viscous) {
+    T gM[12], gS[12];
+    const T* G = TBuf<T>::g(a);
+    const T* pgM = G + (size_t)ee.x * 12 * n3 + vM;
+    const T* pgS = G + (size_t)ee.y * 12 * n3 + vS;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { gM[k] = pgM[k * n3]; gS[k] = pgS[k * n3]; }
+    T tau[6], W[3], fvM[4], fvS[4];
+    viscous_parts(gM, qM.u, qM.v, qM.w, T(a.mu), T(a.lam), tau, W);
+    viscous_flux_n(tau, W, sn, fvM);
+    viscous_parts(gS, qS.u, qS.v, qS.w, T(a.mu), T(a.lam), tau, W);
+    viscous_flux_n(tau, W, sn, fvS);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f[1 + k] -= T(0.5) * (fvM[k] + fvS[k]);
+  }
+  T* out = TBuf<T>::fstar(a) + (size_t)s * 5 * n2 + pq;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) out[k * n2] = f[k];
+}
+
+// ---------------------------------------------------------------------------
+// Hennemann indicator on rho p (modal energy of the top modes), Sec. 2.3, in
+// FP64 on both paths.  Every thread of the element runs the same
+// instructions (no single-thread branch in front of a barrier): row sums are
+// formed by all threads (rows are formed twice or more, with identical
+// values), then every thread adds the row sums itself.
+// sT1 / sT2: n3 doubles each, sRow: 4 n2 doubles.
+// ---------------------------------------------------------------------------
+template <int n>
+__device__ double element_alpha(double rp, double* sT1, double* sT2, double* sRow, const double* sVinv, int t,
+                                double amin, double amax) {
+  constexpr int n2 = n * n, N = n - 1;
+  const int i = t % n, j = (t / n) % n, k = t / n2;
+  sT1[t] = rp;
+  __syncwarp();
+  __syncthreads();
+  double s = 0.0;
+  for (int x = 0; x < n; ++x) s += sVinv[i * n + x] * sT1[x + n * (j + n * k)];
+  sT2[t] = s;
+  __syncwarp();
+  __syncthreads();
+  s = 0.0;
+  for (int x = 0; x < n; ++x) s += sVinv[j * n + x] * sT2[i + n * (x + n * k)];
+  sT1[t] = s;
+  __syncwarp();
+  __syncthreads();
+  s = 0.0;
+  for (int x = 0; x < n; ++x) s += sVinv[k * n + x] * sT1[i + n * (j + n * x)];
+  sT2[t] = s * s;  // energy of mode (i, j, k)
+  __syncwarp();
+  __syncthreads();
+  {
+    // row r = (j, k): sums over i by the maximum degree max(i, j, k)
+    const int r = t % n2, rj = r % n, rk = r / n;
+    double mN = 0, mN1 = 0, tot = 0, tot1 = 0;
+    for (int x = 0; x < n; ++x) {
+      const int dv = max(x, max(rj, rk));
+      const double m2 = sT2[x + n * r];
+      tot += m2;
+      tot1 += dv <= N - 1 ? m2 : 0.0;
+      mN += dv == N ? m2 : 0.0;
+      mN1 += dv == N - 1 ? m2 : 0.0;
+    }
+    sRow[r] = mN;
+    sRow[n2 + r] = mN1;
+    sRow[2 * n2 + r] = tot;
+    sRow[3 * n2 + r] = tot1;
+  }
+  __syncwarp();
+  __syncthreads();
+  double mN = 0, mN1 = 0, tot = 0, tot1 = 0;
+  for (int r = 0; r < n2; ++r) {
+    mN += sRow[r];
+    mN1 += sRow[n2 + r];
+    tot += sRow[2 * n2 + r];
+    tot1 += sRow[3 * n2 + r];
+  }
+  const double e1 = tot > 0 ? mN / tot : 0.0;
+  const double e2 = tot1 > 0 ? mN1 / tot1 : 0.0;
+  const double E = e1 > e2 ? e1 : e2;
+  const double T = 0.5 * pow(10.0, -1.8 * pow((double)(N + 1), 0.25));
+  const double sh = log((1.0 - 1e-4) / 1e-4);
+  double al = 1.0 / (1.0 + exp(-sh * (E - T) / T));
+  if (al < amin) al = 0.0;
+  if (al > amax) al = amax;
+  __syncwarp();
+  __syncthreads();  // sT1 / sT2 / sRow may be reused after this
+  return al;
+}
+
+// shared-memory layout of k_volume: FP64 part first, then the T arrays
+template <int N, typename T>
+struct VolumeSmem {
+  using S = Shape<N>;
+  static constexpr size_t n_dbl = S::n2 + S::EPB * (2 * S::n3 + 4 * S::n2);  // Vinv, indicator scratch
+  static constexpr size_t n_t = 2 * S::n2 + S::EPB * (6 + 9 + 5) * S::n3;     // Dsplit, Dhat, P, J, G
+  static constexpr size_t bytes = sizeof(double) * n_dbl + sizeof(T) * n_t;
+};
+
+// ---------------------------------------------------------------------------
+// Volume integral + SurfInt + ApplyJac (+ RK update)
+// ---------------------------------------------------------------------------
+template <int N, int MODE, typename T>
+__global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
+  using S = Shape<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sVi = reinterpret_cast<double*>(smraw);  // [n2] Vinv (FP64)
+  double* sX = sVi + n2;                           // [EPB][2 n3 + 4 n2] indicator scratch (FP64)
+  T* sDs = reinterpret_cast<T*>(sX + EPB * (2 * n3 + 4 * n2));  // [n2] Dsplit
+  T* sDh = sDs + n2;                                             // [n2] Dhat
+  T* sP = sDh + n2;                                              // [EPB][6][n3] rho u v w p' H'
+  T* sJ = sP + EPB * 6 * n3;                                     // [EPB][9][n3]
+  T* sG = sJ + EPB * 9 * n3;                                     // [EPB][5][n3] viscous / FV fluxes
+  const int le = threadIdx.x / n3, t = threadIdx.x % n3;
+  // slots past the last element redo the last element (see k_lift)
+  const bool valid = blockIdx.x * EPB + le < a.E;
+  const int e = valid ? blockIdx.x * EPB + le : a.E - 1;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) {
+    sDs[k] = T(a.ops->Dsplit[k]);
+    sDh[k] = T(a.ops->Dhat[k]);
+    sVi[k] = a.ops->Vinv[k];
+  }
+  T* P = sP + le * 6 * n3;
+  T* Jm = sJ + le * 9 * n3;
+  T* G = sG + le * 5 * n3;
+  const double* Me = a.metric + (size_t)e * 10 * n3;
+  const double pr_ref = a.scal->ref_p, H_ref = a.scal->ref_H, T_ref = a.scal->ref_T;
+  double U[5];
+  double p_full;
+  SPrim<T> me;
+  T g[12];
+  {
+    const double* u = a.U + (size_t)e * 5 * n3 + t;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
+    me = shifted_prim<T>(U, a.gm1, a.Rinv, pr_ref, H_ref, T_ref, &p_full);
+    P[t] = me.rho;
+    P[n3 + t] = me.u;
+    P[2 * n3 + t] = me.v;
+    P[3 * n3 + t] = me.w;
+    P[4 * n3 + t] = me.p;
+    P[5 * n3 + t] = me.H;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Jm[c * n3 + t] = T(Me[c * n3 + t]);
+    if (a.viscous) {
+      const T* pg = TBuf<T>::g(a) + (size_t)e * 12 * n3 + t;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) g[k] = pg[k * n3];
+    }
+  }
+  __syncwarp();
+  __syncthreads();
+  const int idx[3] = {t % n, (t / n) % n, t / n2};
+  constexpr int str[3] = {1, n, n2};
+  T accC[5] = {0, 0, 0, 0, 0};  // convective DG volume term
+  T acc[5] = {0, 0, 0, 0, 0};   // viscous volume + surface terms
+  T tau[6] = {0, 0, 0, 0, 0, 0}, W[3] = {0, 0, 0};
+  if (a.viscous) viscous_parts(g, me.u, me.v, me.w, T(a.mu), T(a.lam), tau, W);
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    const T Ji0 = Jm[(d * 3 + 0) * n3 + t], Ji1 = Jm[(d * 3 + 1) * n3 + t], Ji2 = Jm[(d * 3 + 2) * n3 + t];
+    if (a.viscous) {
+      {
+        const T nv[3] = {Ji0, Ji1, Ji2};
+        T fv[4];
+        viscous_flux_n(tau, W, nv, fv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) G[k * n3 + t] = fv[k];
+      }
+      __syncwarp();
+      __syncthreads();
+    }
+    {
+      const int id = idx[d], base = t - id * str[d];
+#pragma unroll
+      for (int al = 0; al < n; ++al) {
+        if (al == id) continue;
+        const int nb = base + al * str[d];
+        const T Dv = sDs[id * n + al];
+        const T m0 = (Ji0 + Jm[(d * 3 + 0) * n3 + nb]) / 2;
+        const T m1 = (Ji1 + Jm[(d * 3 + 1) * n3 + nb]) / 2;
+        const T m2 = (Ji2 + Jm[(d * 3 + 2) * n3 + nb]) / 2;
+        const T rho = (me.rho + P[nb]) / 2;
+        const T u0 = (me.u + P[n3 + nb]) / 2, u1 = (me.v + P[2 * n3 + nb]) / 2, u2 = (me.w + P[3 * n3 + nb]) / 2;
+        const T pp = (me.p + P[4 * n3 + nb]) / 2;
+        const T H = (me.H + P[5 * n3 + nb]) / 2;
+        const T fr = rho * (u0 * m0 + u1 * m1 + u2 * m2);
+        accC[0] += Dv * fr;
+        accC[1] += Dv * (fr * u0 + pp * m0);
+        accC[2] += Dv * (fr * u1 + pp * m1);
+        accC[3] += Dv * (fr * u2 + pp * m2);
+        accC[4] += Dv * (fr * H);
+      }
+      if (a.viscous) {
+#pragma unroll
+        for (int al = 0; al < n; ++al) {
+          const T c = sDh[id * n + al];
+          const int nb = base + al * str[d];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[1 + k] -= c * G[k * n3 + nb];
+        }
+      }
+    }
+    if (a.viscous) {
+      __syncwarp();
+      __syncthreads();
+    }
+  }
+
+  // ---- shock capturing: indicator and FV sub-cell blending (Sec. 2.3) ----
+  if (a.shock) {
+    double al;
+    if (a.alpha_force >= 0) {
+      al = a.alpha_force;
+    } else {
+      double* X1 = sX + le * (2 * n3 + 4 * n2);
+      // all threads of the block take part in the barriers inside
+      al = element_alpha<n>(U[0] * p_full, X1, X1 + n3, X1 + 2 * n3, sVi, t, a.alpha_min, a.alpha_max);
+    }
+    if (valid && t == 0) a.alpha[e] = al;
+    // block-uniform condition: the FV pass has barriers, and the elements of
+    // one block may have different blending factors
+    if (__syncthreads_or(al > 0)) {
+      T vfv[5] = {0, 0, 0, 0, 0};
+      const double* FVm = a.fvmetric + (size_t)e * 3 * (n - 1) * 3 * n2;
+#pragma unroll 1
+      for (int d = 0; d < 3; ++d) {
+        const int id = idx[d];
+        // the flux through interface id + 1/2 is formed by the node on its
+        // left; the last node of a line forms a dummy one (same instructions
+        // for every thread) that is not stored
+        const bool right = id < n - 1;
+        const int line = d == 0 ? idx[1] + n * idx[2] : (d == 1 ? idx[0] + n * idx[2] : idx[0] + n * idx[1]);
+        const double* fm = FVm + (size_t)(d * (n - 1) + (right ? id : n - 2)) * 3 * n2 + line;
+        const double mv[3] = {fm[0], fm[n2], fm[2 * n2]};
+        const double sAd = sqrt(mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2]);
+        const T nu[3] = {T(mv[0] / sAd), T(mv[1] / sAd), T(mv[2] / sAd)};
+        const int nb = right ? t + str[d] : t;
+        double UR[5];
+        const double* ur = a.U + (size_t)e * 5 * n3 + nb;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) UR[k] = ur[k * n3];
+        const SPrim<T> qR = shifted_prim<T>(UR, a.gm1, a.Rinv, pr_ref, H_ref, T_ref);
+        T fb[5];
+        lf_flux_s(me, qR, nu, T(a.gamma), T(pr_ref), fb);
+        if (right) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) G[k * n3 + t] = fb[k] * T(sAd);
+        }
+        __syncwarp();
+        __syncthreads();
+        if (right) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) vfv[k] += G[k * n3 + t] / T(a.ops->w[id]);
+        }
+        if (id > 0) {
+          const int nl = t - str[d];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) vfv[k] -= G[k * n3 + nl] / T(a.ops->w[id]);
+        }
+        __syncwarp();
+        __syncthreads();
+      }
+      if (al > 0) {
+        const T alt = T(al);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) accC[k] = (1 - alt) * accC[k] + alt * vfv[k];
+      }
+    }
+  }
+  if (!valid) return;
+
+  // ---- SurfInt: face nodes receive +-f* lhat ----
+  const T* Fst = TBuf<T>::fstar(a);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int id = idx[d];
+    if (id != 0 && id != n - 1) continue;
+    const int f = 2 * d + (id == n - 1 ? 1 : 0);
+    const int es = a.elem_side[(size_t)e * 6 + f];
+    const int s = es_side(es);
+    const int p = d == 0 ? idx[1] : idx[0];
+    const int qq = d == 2 ? idx[1] : idx[2];
+    int pm = p, qm = qq;
+    if (es_slave(es)) flip_to_master<n>(es_flip(es), p, qq, pm, qm);
+    const T sg = T(es_slave(es) ? -a.ops->winv[id] : a.ops->winv[id]);
+    const T* Fs = Fst + (size_t)s * 5 * n2 + pm + n * qm;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] += sg * Fs[k * n2];
+  }
+  // ---- ApplyJac; the energy equation gets H_ref times the mass equation back ----
+  const double Ji = Me[9 * n3 + t];
+  double Ut[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) Ut[k] = -(double)(accC[k] + acc[k]) * Ji;
+  Ut[4] += H_ref * Ut[0];
+  if (MODE == 0) {
+    double* o = a.Ut + (size_t)e * 5 * n3 + t;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[k * n3] = Ut[k];
+  } else {
+    const double dt = a.scal->dt;
+    double* du = a.dU + (size_t)e * 5 * n3 + t;
+    double* uo = a.Urk + (size_t)e * 5 * n3 + t;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const double r = a.first_stage ? dt * Ut[k] : a.rkA * du[k * n3] + dt * Ut[k];
+      du[k * n3] = r;
+      uo[k * n3] = U[k] + a.rkB * r;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side: launch arguments, shared-memory sizes, one RHS evaluation
+// ---------------------------------------------------------------------------
+inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
+  StageArgs a{};
+  a.E = (int)c->E;
+  a.S = (int)c->S;
+  a.U = U;
+  a.metric = c->metric;
+  a.nrm = c->nrm;
+  a.elem_side = c->elem_side;
+  a.side_e = c->side_e;
+  a.side_f = c->side_f;
+  a.g = c->g;
+  a.lflux = c->lflux;
+  a.fstar = c->fstar;
+  a.g32 = c->g32;
+  a.lflux32 = c->lflux32;
+  a.fstar32 = c->fstar32;
+  a.alpha = c->alpha;
+  a.fvmetric = c->fvmetric;
+  a.ops = c->ops;
+  a.gamma = c->prm.gamma;
+  a.gm1 = c->prm.gamma - 1.0;
+  a.Rinv = 1.0 / c->prm.R;
+  a.mu = c->prm.mu;
+  a.lam = c->prm.gamma * c->prm.R * c->prm.mu / ((c->prm.gamma - 1.0) * c->prm.Pr);
+  a.riemann = c->prm.riemann;
+  a.viscous = c->prm.viscous;
+  a.shock = c->prm.shock_capturing;
+  a.alpha_min = c->prm.alpha_min;
+  a.alpha_max = c->prm.alpha_max;
+  a.alpha_force = c->prm.alpha_force;
+  a.scal = c->scal;
+  return a;
+}
+
+template <int N, typename T>
+inline size_t lift_smem_bytes() {
+  using S = Shape<N>;
+  return sizeof(T) * (S::n2 + S::EPB * 16 * S::n3);
+}
+
+template <int N, typename T>
+cudaError_t stage_set_attrs() {
+  cudaFuncSetAttribute(k_lift<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lift_smem_bytes<N, T>());
+  cudaFuncSetAttribute(k_volume<N, 0, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)VolumeSmem<N, T>::bytes);
+  cudaFuncSetAttribute(k_volume<N, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)VolumeSmem<N, T>::bytes);
+  return cudaGetLastError();
+}
+
+template <int N, typename T>
+cudaError_t stage_launch(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first) {
+  using S = Shape<N>;
+  StageArgs a = make_stage_args(c, U);
+  a.Ut = c->Ut;
+  a.Urk = c->U;
+  a.dU = c->dU;
+  a.rkA = rkA;
+  a.rkB = rkB;
+  a.first_stage = first;
+  const int64_t side_nodes = c->S * S::n2;
+  const unsigned sb = (unsigned)((side_nodes + 255) / 256);
+  const unsigned eb = (unsigned)((c->E + S::EPB - 1) / S::EPB);
+  if (c->prm.viscous) {
+    prof_begin(c, PK_SURF_PRIMS);
+    k_surf_prims<N, T><<<sb, 256, 0, c->stream>>>(a);
+    prof_end(c);
+    prof_begin(c, PK_LIFT);
+    k_lift<N, T><<<eb, S::THREADS, lift_smem_bytes<N, T>(), c->stream>>>(a);
+    prof_end(c);
+    count_launch(2);
+  }
+  prof_begin(c, PK_SURF_FLUX);
+  k_surf_flux<N, T><<<sb, 256, 0, c->stream>>>(a);
+  prof_end(c);
+  prof_begin(c, PK_VOLUME);
+  if (mode == 0) k_volume<N, 0, T><<<eb, S::THREADS, VolumeSmem<N, T>::bytes, c->stream>>>(a);
+  else k_volume<N, 1, T><<<eb, S::THREADS, VolumeSmem<N, T>::bytes, c->stream>>>(a);
+  prof_end(c);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+#define DG_DISPATCH(N_, CALL)                      \
+  switch (N_) {                                    \
+    case 1: { constexpr int NN = 1; CALL; } break; \
+    case 2: { constexpr int NN = 2; CALL; } break; \
+    case 3: { constexpr int NN = 3; CALL; } break; \
+    case 4: { constexpr int NN = 4; CALL; } break; \
+    case 5: { constexpr int NN = 5; CALL; } break; \
+    case 6: { constexpr int NN = 6; CALL; } break; \
+    case 7: { constexpr int NN = 7; CALL; } break; \
+    default: return cudaErrorInvalidValue;         \
+  }
+
+}  // namespace dg

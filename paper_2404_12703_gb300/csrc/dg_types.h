@@ -34,6 +34,7 @@ struct DevScalars {
   int mesh_error;            // set by the map construction kernels
   int pad[2];
   double kin[4];             // kinetic-energy reductions
+  double ref_p, ref_H, ref_T;  // reference state of the shifted primitives (0 in FP64)
 };
 
 // Per-stage launch parameters of the RHS kernels.
@@ -48,6 +49,9 @@ struct StageArgs {
   double* g;             // [E][12][n3] lifted gradients
   double* lflux;         // [S][12][n2]
   double* fstar;         // [S][5][n2]
+  float* g32;            // FP32-bulk copies of the three arrays above
+  float* lflux32;
+  float* fstar32;
   double* alpha;         // [E]
   const double* fvmetric;  // [E][3][n2][(n-1)*3] sub-cell interface metrics
   const Ops* ops;
@@ -82,6 +86,9 @@ struct dg_ctx {
   double* nrm = nullptr;     // [S][4][n2]
   double* lflux = nullptr;   // [S][12][n2]
   double* fstar = nullptr;   // [S][5][n2]
+  float* g32 = nullptr;      // FP32-bulk: [E][12][n3]
+  float* lflux32 = nullptr;  // FP32-bulk: [S][12][n2]
+  float* fstar32 = nullptr;  // FP32-bulk: [S][5][n2]
   double* alpha = nullptr;   // [E]
   double* fvmetric = nullptr;  // [E][3][n2][(n-1)*3]
   int* elem_side = nullptr;  // [E][6]

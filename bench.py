@@ -46,7 +46,7 @@ BYTES_PER_DOF = 8 * (30 + 204 / (N_DEG + 1))
 # DRAM bytes per DOF of one k_volume<7,1> launch, from the ncu capture summarised
 # in profiles/k_volume_tgv12_N7_fp64.md (12^3 mesh; the traffic scales with
 # the DOF count).  Set to None whenever the kernel changes until re-measured.
-VOLUME_TRAFFIC_BYTES_PER_DOF = 331.3
+VOLUME_TRAFFIC_BYTES_PER_DOF = 330.5
 # FP32-bulk: algorithmic bytes per DOF of one volume-kernel launch (reads U 40,
 # FP64 metrics 80, FP32 lifted gradients 48, dU 40, surface fluxes ~8; writes
 # U 40, dU 40), and of a whole stage for the minimal two-phase method with the

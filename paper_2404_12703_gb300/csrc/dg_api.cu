@@ -274,6 +274,7 @@ void dg_destroy(dg_ctx* c) {
   cudaFree(c->fstar32);
   cudaFree(c->alpha);
   cudaFree(c->fvmetric);
+  cudaFree(c->cflgeo);
   cudaFree(c->elem_side);
   cudaFree(c->side_e);
   cudaFree(c->side_f);
@@ -313,6 +314,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params
   A(dalloc(&c->g32, E * 12 * n3, c->bytes));
   A(dalloc(&c->alpha, E, c->bytes));
   A(dalloc(&c->fvmetric, E * 3 * (c->n - 1) * 3 * c->n2, c->bytes));
+  A(dalloc(&c->cflgeo, E * 4 * n3, c->bytes));
   A(dalloc(&c->elem_side, E * 6, c->bytes));
   A(dalloc(&c->ops, 1, c->bytes));
   A(dalloc(&c->scal, 1, c->bytes));

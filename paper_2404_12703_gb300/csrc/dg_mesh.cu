@@ -271,6 +271,26 @@ __global__ void k_side_geom(int S, const int2* __restrict__ side_e, const int* _
   out[3 * n2 + pq] = sqrt(sn[0] * sn[0] + sn[1] * sn[1] + sn[2] * sn[2]);
 }
 
+// per-node geometric factors of the time-step rule: |J a^d| and sum_d |J a^d|^2
+template <int N>
+__global__ void k_cfl_geo(int E, const double* __restrict__ metric, double* __restrict__ geo) {
+  constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (x >= (int64_t)E * n3) return;
+  const int64_t e = x / n3;
+  const int t = (int)(x % n3);
+  const double* Me = metric + e * 10 * n3 + t;
+  double* G = geo + e * 4 * n3 + t;
+  double b = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double j0 = Me[(d * 3) * n3], j1 = Me[(d * 3 + 1) * n3], j2 = Me[(d * 3 + 2) * n3];
+    const double nj2 = j0 * j0 + j1 * j1 + j2 * j2;
+    G[d * n3] = sqrt(nj2);
+    b += nj2;
+  }
+  G[3 * n3] = b;
+}
+
 template <int N>
 static cudaError_t launch_metrics(dg_ctx* c, const double* d_xyz) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -281,7 +301,9 @@ static cudaError_t launch_metrics(dg_ctx* c, const double* d_xyz) {
   const int64_t tot = c->S * n2;
   k_side_geom<N><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>((int)c->S, c->side_e, c->side_f, c->metric,
                                                                        c->nrm);
-  count_launch();
+  const int64_t nodes = c->E * n3;
+  k_cfl_geo<N><<<(unsigned)((nodes + 255) / 256), 256, 0, c->stream>>>((int)c->E, c->metric, c->cflgeo);
+  count_launch(2);
   return cudaGetLastError();
 }
 

@@ -13,8 +13,8 @@ namespace dg {
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U, const double* __restrict__ metric,
-                                            double gamma, double gm1, double Rinv, double kv, int viscous,
-                                            DevScalars* scal) {
+                                            const double* __restrict__ geo, double gamma, double gm1, double Rinv,
+                                            double kv, int viscous, DevScalars* scal) {
   constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
   double lc = 0.0, lv = 0.0;
   int bad = 0;
@@ -23,23 +23,24 @@ __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U
     const int64_t e = x / n3;
     const int t = (int)(x % n3);
     double Uv[5];
-    const double* u = U + e * 5 * n3 + t;
+    const double* up = U + e * 5 * n3 + t;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) Uv[k] = u[k * n3];
-    const Prim<double> q = cons_to_prim(Uv, gm1, Rinv);
-    const double c = sqrt(gamma * q.p / q.rho);
+    for (int k = 0; k < 5; ++k) Uv[k] = up[k * n3];
+    const double ri = 1.0 / Uv[0];
+    const double u = Uv[1] * ri, v = Uv[2] * ri, w = Uv[3] * ri;
+    const double p = gm1 * (Uv[4] - 0.5 * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
+    const double c = sqrt(gamma * p * ri);
     const double* Me = metric + e * 10 * n3 + t;
+    const double* Gm = geo + e * 4 * n3 + t;
     const double Ji = Me[9 * n3];
-    double aa = 0.0, bb = 0.0;
+    double aa = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double j0 = Me[(d * 3) * n3], j1 = Me[(d * 3 + 1) * n3], j2 = Me[(d * 3 + 2) * n3];
-      const double nj2 = j0 * j0 + j1 * j1 + j2 * j2;
-      aa += fabs(q.u * j0 + q.v * j1 + q.w * j2) + c * sqrt(nj2);
-      bb += nj2;
+      aa += fabs(u * j0 + v * j1 + w * j2) + c * Gm[d * n3];
     }
     aa *= Ji;
-    bb = kv / q.rho * bb * Ji * Ji;
+    const double bb = kv * ri * Gm[3 * n3] * Ji * Ji;
     if (!isfinite(aa) || !isfinite(bb)) bad = 1;
     lc = fmax(lc, aa);
     lv = fmax(lv, bb);
@@ -251,7 +252,7 @@ cudaError_t launch_cfl(dg_ctx* c) {
   const double kv = std::max(4.0 / 3.0, c->prm.gamma / c->prm.Pr) * c->prm.mu;
   const int nb = cfl_blocks(c);
   prof_begin(c, PK_CFL);
-  DG_DISPATCH(c->N, (k_cfl<NN><<<nb, 256, 0, c->stream>>>((int)c->E, c->U, c->metric, c->prm.gamma,
+  DG_DISPATCH(c->N, (k_cfl<NN><<<nb, 256, 0, c->stream>>>((int)c->E, c->U, c->metric, c->cflgeo, c->prm.gamma,
                                                           c->prm.gamma - 1.0, 1.0 / c->prm.R, kv, c->prm.viscous,
                                                           c->scal)));
   k_dt<<<1, 1, 0, c->stream>>>(c->scal, c->prm.cfl, c->prm.dfl, c->N, c->prm.viscous);

@@ -410,7 +410,7 @@ template <int N, typename T>
 struct VolumeSmem {
   using S = Shape<N>;
   static constexpr size_t n_dbl = S::n2 + S::EPB * (2 * S::n3 + 4 * S::n2);  // Vinv, indicator scratch
-  static constexpr size_t n_t = 2 * S::n2 + S::EPB * (6 + 9 + 5) * S::n3;     // Dsplit, Dhat, P, J, G
+  static constexpr size_t n_t = 2 * S::n2 + S::EPB * (6 + 9 + 5 + 15) * S::n3;  // Dsplit, Dhat, P, J, G, A
   static constexpr size_t bytes = sizeof(double) * n_dbl + sizeof(T) * n_t;
 };
 
@@ -426,9 +426,10 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
   double* sX = sVi + n2;                           // [EPB][2 n3 + 4 n2] indicator scratch (FP64)
   T* sDs = reinterpret_cast<T*>(sX + EPB * (2 * n3 + 4 * n2));  // [n2] Dsplit
   T* sDh = sDs + n2;                                             // [n2] Dhat
-  T* sP = sDh + n2;                                              // [EPB][6][n3] rho u v w p' H'
-  T* sJ = sP + EPB * 6 * n3;                                     // [EPB][9][n3]
+  T* sP = sDh + n2;                                              // [EPB][6][n3] rho u v w p' H', halved
+  T* sJ = sP + EPB * 6 * n3;                                     // [EPB][9][n3] metrics, halved
   T* sG = sJ + EPB * 9 * n3;                                     // [EPB][5][n3] viscous / FV fluxes
+  T* sA = sG + EPB * 5 * n3;                                     // [EPB][3][5][n3] two-point sums
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
   // slots past the last element redo the last element (see k_lift)
   const bool valid = blockIdx.x * EPB + le < a.E;
@@ -441,6 +442,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
   T* P = sP + le * 6 * n3;
   T* Jm = sJ + le * 9 * n3;
   T* G = sG + le * 5 * n3;
+  T* A = sA + le * 15 * n3;
   const double* Me = a.metric + (size_t)e * 10 * n3;
   const double pr_ref = a.scal->ref_p, H_ref = a.scal->ref_H, T_ref = a.scal->ref_T;
   double U[5];
@@ -452,14 +454,16 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
     me = shifted_prim<T>(U, a.gm1, a.Rinv, pr_ref, H_ref, T_ref, &p_full);
-    P[t] = me.rho;
-    P[n3 + t] = me.u;
-    P[2 * n3 + t] = me.v;
-    P[3 * n3 + t] = me.w;
-    P[4 * n3 + t] = me.p;
-    P[5 * n3 + t] = me.H;
+    // halved values: every arithmetic mean of the two-point flux is then one
+    // addition, bit-identical to (a + b) / 2
+    P[t] = T(0.5) * me.rho;
+    P[n3 + t] = T(0.5) * me.u;
+    P[2 * n3 + t] = T(0.5) * me.v;
+    P[3 * n3 + t] = T(0.5) * me.w;
+    P[4 * n3 + t] = T(0.5) * me.p;
+    P[5 * n3 + t] = T(0.5) * me.H;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) Jm[c * n3 + t] = T(Me[c * n3 + t]);
+    for (int c = 0; c < 9; ++c) Jm[c * n3 + t] = T(0.5) * T(Me[c * n3 + t]);
     if (a.viscous) {
       const T* pg = TBuf<T>::g(a) + (size_t)e * 12 * n3 + t;
 #pragma unroll
@@ -474,12 +478,111 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
   T acc[5] = {0, 0, 0, 0, 0};   // viscous volume + surface terms
   T tau[6] = {0, 0, 0, 0, 0, 0}, W[3] = {0, 0, 0};
   if (a.viscous) viscous_parts(g, me.u, me.v, me.w, T(a.mu), T(a.lam), tau, W);
+  // ---- split-form KEP volume integral ----
+  // FP64 (bound by the FP64 pipe): one line per task; every unordered pair
+  // (i, alpha) of the line forms the symmetric two-point flux once and adds
+  // Dsplit_{i alpha} f to node i and Dsplit_{alpha i} f to node alpha, which
+  // halves the flux evaluations.  FP32 (bound by latency, not arithmetic):
+  // one node per thread over all its partners, which keeps every thread busy.
+  // Each direction has its own sum array.
+  constexpr bool kPairs = sizeof(T) == sizeof(double);
+  if (!kPairs) {
+    const int idl[3] = {t % n, (t / n) % n, t / n2};
 #pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    const T Ji0 = Jm[(d * 3 + 0) * n3 + t], Ji1 = Jm[(d * 3 + 1) * n3 + t], Ji2 = Jm[(d * 3 + 2) * n3 + t];
-    if (a.viscous) {
+    for (int d = 0; d < 3; ++d) {
+      const int id = idl[d], base = t - id * str[d];
+      const T* J0 = Jm + (d * 3 + 0) * n3;
+      const T* J1 = Jm + (d * 3 + 1) * n3;
+      const T* J2 = Jm + (d * 3 + 2) * n3;
+      const T ri = P[t], ui = P[n3 + t], vvi = P[2 * n3 + t], wi = P[3 * n3 + t];
+      const T pi = P[4 * n3 + t], Hi = P[5 * n3 + t];
+      const T j0 = J0[t], j1 = J1[t], j2 = J2[t];
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0), s4 = T(0);
+#pragma unroll
+      for (int al = 0; al < n; ++al) {
+        if (al == id) continue;
+        const int va = base + al * str[d];
+        const T m0 = j0 + J0[va], m1 = j1 + J1[va], m2 = j2 + J2[va];
+        const T rho = ri + P[va];
+        const T u0 = ui + P[n3 + va], u1 = vvi + P[2 * n3 + va], u2 = wi + P[3 * n3 + va];
+        const T pp = pi + P[4 * n3 + va];
+        const T H = Hi + P[5 * n3 + va];
+        const T fr = rho * (u0 * m0 + u1 * m1 + u2 * m2);
+        const T dv = sDs[id * n + al];
+        s0 += dv * fr;
+        s1 += dv * (fr * u0 + pp * m0);
+        s2 += dv * (fr * u1 + pp * m1);
+        s3 += dv * (fr * u2 + pp * m2);
+        s4 += dv * (fr * H);
+      }
+      T* Ad = A + d * 5 * n3;
+      Ad[t] = s0;
+      Ad[n3 + t] = s1;
+      Ad[2 * n3 + t] = s2;
+      Ad[3 * n3 + t] = s3;
+      Ad[4 * n3 + t] = s4;
+    }
+  }
+  for (int lt = t; kPairs && lt < 3 * n2; lt += n3) {
+    const int d = lt / n2, line = lt % n2;
+    const int lp = line % n, lq = line / n;
+    const int base = d == 0 ? n * (lp + n * lq) : (d == 1 ? lp + n2 * lq : lp + n * lq);
+    const int st = d == 0 ? 1 : (d == 1 ? n : n2);
+    const T* J0 = Jm + (d * 3 + 0) * n3;
+    const T* J1 = Jm + (d * 3 + 1) * n3;
+    const T* J2 = Jm + (d * 3 + 2) * n3;
+    // this task is the only writer of the line's nodes in direction d's array:
+    // node i keeps its sums in registers, partner contributions go straight
+    // to shared memory
+    T* Ad = A + d * 5 * n3;
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Ad[k * n3 + base + i * st] = T(0);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const int vi = base + i * st;
+      const T ri = P[vi], ui = P[n3 + vi], vvi = P[2 * n3 + vi], wi = P[3 * n3 + vi];
+      const T pi = P[4 * n3 + vi], Hi = P[5 * n3 + vi];
+      const T j0 = J0[vi], j1 = J1[vi], j2 = J2[vi];
+      T ai0 = T(0), ai1 = T(0), ai2 = T(0), ai3 = T(0), ai4 = T(0);
+#pragma unroll
+      for (int al = i + 1; al < n; ++al) {
+        const int va = base + al * st;
+        const T m0 = j0 + J0[va], m1 = j1 + J1[va], m2 = j2 + J2[va];
+        const T rho = ri + P[va];
+        const T u0 = ui + P[n3 + va], u1 = vvi + P[2 * n3 + va], u2 = wi + P[3 * n3 + va];
+        const T pp = pi + P[4 * n3 + va];
+        const T H = Hi + P[5 * n3 + va];
+        const T fr = rho * (u0 * m0 + u1 * m1 + u2 * m2);
+        const T f1 = fr * u0 + pp * m0, f2 = fr * u1 + pp * m1, f3 = fr * u2 + pp * m2, f4 = fr * H;
+        const T dia = sDs[i * n + al], dai = sDs[al * n + i];
+        ai0 += dia * fr;
+        ai1 += dia * f1;
+        ai2 += dia * f2;
+        ai3 += dia * f3;
+        ai4 += dia * f4;
+        Ad[va] += dai * fr;
+        Ad[n3 + va] += dai * f1;
+        Ad[2 * n3 + va] += dai * f2;
+        Ad[3 * n3 + va] += dai * f3;
+        Ad[4 * n3 + va] += dai * f4;
+      }
+      Ad[vi] += ai0;
+      Ad[n3 + vi] += ai1;
+      Ad[2 * n3 + vi] += ai2;
+      Ad[3 * n3 + vi] += ai3;
+      Ad[4 * n3 + vi] += ai4;
+    }
+  }
+
+  // ---- viscous volume term: collocated weak form, per direction ----
+  if (a.viscous) {
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
       {
-        const T nv[3] = {Ji0, Ji1, Ji2};
+        const T nv[3] = {T(2) * Jm[(d * 3 + 0) * n3 + t], T(2) * Jm[(d * 3 + 1) * n3 + t],
+                         T(2) * Jm[(d * 3 + 2) * n3 + t]};
         T fv[4];
         viscous_flux_n(tau, W, nv, fv);
 #pragma unroll
@@ -487,29 +590,8 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
       }
       __syncwarp();
       __syncthreads();
-    }
-    {
-      const int id = idx[d], base = t - id * str[d];
-#pragma unroll
-      for (int al = 0; al < n; ++al) {
-        if (al == id) continue;
-        const int nb = base + al * str[d];
-        const T Dv = sDs[id * n + al];
-        const T m0 = (Ji0 + Jm[(d * 3 + 0) * n3 + nb]) / 2;
-        const T m1 = (Ji1 + Jm[(d * 3 + 1) * n3 + nb]) / 2;
-        const T m2 = (Ji2 + Jm[(d * 3 + 2) * n3 + nb]) / 2;
-        const T rho = (me.rho + P[nb]) / 2;
-        const T u0 = (me.u + P[n3 + nb]) / 2, u1 = (me.v + P[2 * n3 + nb]) / 2, u2 = (me.w + P[3 * n3 + nb]) / 2;
-        const T pp = (me.p + P[4 * n3 + nb]) / 2;
-        const T H = (me.H + P[5 * n3 + nb]) / 2;
-        const T fr = rho * (u0 * m0 + u1 * m1 + u2 * m2);
-        accC[0] += Dv * fr;
-        accC[1] += Dv * (fr * u0 + pp * m0);
-        accC[2] += Dv * (fr * u1 + pp * m1);
-        accC[3] += Dv * (fr * u2 + pp * m2);
-        accC[4] += Dv * (fr * H);
-      }
-      if (a.viscous) {
+      {
+        const int id = idx[d], base = t - id * str[d];
 #pragma unroll
         for (int al = 0; al < n; ++al) {
           const T c = sDh[id * n + al];
@@ -518,12 +600,14 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
           for (int k = 0; k < 4; ++k) acc[1 + k] -= c * G[k * n3 + nb];
         }
       }
-    }
-    if (a.viscous) {
       __syncwarp();
       __syncthreads();
     }
   }
+  __syncwarp();
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 5; ++k) accC[k] = (A[k * n3 + t] + A[(5 + k) * n3 + t]) + A[(10 + k) * n3 + t];
 
   // ---- shock capturing: indicator and FV sub-cell blending (Sec. 2.3) ----
   if (a.shock) {

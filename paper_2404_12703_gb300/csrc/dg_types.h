@@ -91,6 +91,7 @@ struct dg_ctx {
   float* fstar32 = nullptr;  // FP32-bulk: [S][5][n2]
   double* alpha = nullptr;   // [E]
   double* fvmetric = nullptr;  // [E][3][n2][(n-1)*3]
+  double* cflgeo = nullptr;    // [E][4][n3]: |J a^d| (d = 0..2), sum_d |J a^d|^2
   int* elem_side = nullptr;  // [E][6]
   int2* side_e = nullptr;    // [S]
   int* side_f = nullptr;     // [S]

@@ -163,6 +163,100 @@ def cpu_oracle_sample(steps, nel=6, seed=SEED):
     return dof, times
 
 
+def serving_cases(n_cases, seed=5):
+    """Seeded stream of cases (a shortened version of the serving workload):
+    mesh n^3 with n from {4, 6, 8}, N from {3, 5, 7}, half Taylor-Green vortex
+    (Re 1600, Ma 0.1, viscous), half isentropic vortex (inviscid, strength 5,
+    mean flow (1, 1, 0)), each to t_end = 0.05."""
+    from paper_2404_12703_gb300 import workloads as W
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_cases):
+        nel = int(rng.choice([4, 6, 8]))
+        N = int(rng.choice([3, 5, 7]))
+        if rng.random() < 0.5:
+            m = W.box_mesh(N, (nel,) * 3, curved=0.1, seed=1000 + i)
+            U = W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5)
+            mu, kind = 1.0 / 1600.0, "tgv"
+        else:
+            L = 10.0
+            m = W.box_mesh(N, (nel,) * 3, length=(L, L, L), curved=0.05, seed=1000 + i)
+            U = W.isentropic_vortex_state(m["xyz"], center=(L / 2, L / 2), strength=5.0,
+                                          period=m["period"]).reshape(m["E"], -1, 5)
+            mu, kind = 0.0, "vortex"
+        out.append({"mesh": m, "U0": U, "mu": mu, "kind": kind, "N": N, "nel": nel, "t_end": 0.05})
+    return out
+
+
+def serving_bench(dg, n_cases, precision):
+    """Continuous batching against the same cases run one by one."""
+    import torch
+    cases = serving_cases(n_cases)
+    dofs = [c["mesh"]["E"] * (c["N"] + 1) ** 3 for c in cases]
+    # one by one through the standalone solver (graph-launched steps)
+    service = []
+    seq_dofstage = 0.0
+    for c, dof in zip(cases, dofs):
+        sv = dg.Solver(c["mesh"], mu=c["mu"], precision=precision)
+        sv.set_state(c["U0"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = 0.0
+        steps = 0
+        while t < c["t_end"]:
+            dt = sv.time_step()
+            dt = min(dt, c["t_end"] - t)
+            sv.step(1, dt=dt)
+            t += dt
+            steps += 1
+        sv.get_state()
+        service.append(time.perf_counter() - t0)
+        seq_dofstage += dof * STAGES * steps
+        sv.close()
+    mean_service = sum(service) / len(service)
+    rate = 0.9 / mean_service
+    rng = np.random.Generator(np.random.PCG64(5))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(cases)))
+    arrivals -= arrivals[0]
+    # the one-by-one queue: same arrivals, FIFO, measured service times
+    free_at, seq_lat = 0.0, []
+    for a, sv_t in zip(arrivals, service):
+        start = max(a, free_at)
+        free_at = start + sv_t
+        seq_lat.append(free_at - a)
+    seq_makespan = free_at
+    # the server: same arrivals
+    pools = {3: 8 ** 3 * 12, 5: 8 ** 3 * 12, 7: 8 ** 3 * 8}
+    srv = dg.Server(pools, max_cases=64, precision=precision)
+    t0 = time.perf_counter()
+    tickets = []
+    for a, c in zip(arrivals, cases):
+        while time.perf_counter() - t0 < a:
+            time.sleep(0.0005)
+        tickets.append(srv.submit(c["mesh"], c["U0"], c["t_end"], mu=c["mu"]))
+    lat = []
+    for tk in tickets:
+        _, st = srv.wait(tk, with_state=False)
+        lat.append(st["time_to_solution"])
+    makespan = time.perf_counter() - t0
+    sstats = srv.stats()
+    srv.close()
+    p = lambda v, q: float(np.percentile(np.asarray(v), q))
+    return {
+        "workload": f"{len(cases)} cases (seeded PCG64(5)): n^3 meshes n in {{4,6,8}}, N in {{3,5,7}}, "
+                    f"half TGV (Re 1600, Ma 0.1), half isentropic vortex (inviscid), each to t = 0.05; "
+                    f"Poisson arrivals at 0.9 x the one-by-one service rate ({rate:.2f}/s); shortened from "
+                    f"the 200-case, t = 1 configuration",
+        "precision": "FP64" if precision == dg.FP64 else "FP32-bulk",
+        "p50_s": p(lat, 50), "p99_s": p(lat, 99),
+        "dof_updates_per_s": sstats["dof_stage_updates"] / makespan, "makespan_s": makespan,
+        "one_by_one": {"p50_s": p(seq_lat, 50), "p99_s": p(seq_lat, 99),
+                       "dof_updates_per_s": seq_dofstage / seq_makespan, "makespan_s": seq_makespan,
+                       "mean_service_s": mean_service},
+        "batched_steps": sstats["steps"], "graph_captures": sstats["captures"],
+    }
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -341,6 +435,10 @@ def run_ours(args):
         }
         s32.close()
 
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = serving_bench(dg, args.serving_cases, dg.FP64)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cdof, ctimes = cpu_oracle_sample(2, nel=4)
@@ -358,7 +456,7 @@ def run_ours(args):
             "gpu_launches": launches, "kernels": kernels, "roofline": roofline,
             "e2e": {"value": world * dof * STAGES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
-            "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32,
+            "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     solver.close()
@@ -375,6 +473,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-cases", type=int, default=24)
     ap.add_argument("--nel", type=int, default=NEL,
                     help="elements per direction (24 is the benchmark workload; smaller for profiling)")
     args = ap.parse_args()

@@ -147,6 +147,75 @@ int dg_time_step(dg_ctx* ctx, double* dt);
    out[2] = |Omega|.  FP64 reductions on the device; synchronises. */
 int dg_kinetic(dg_ctx* ctx, double* out);
 
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over many flow cases.
+ * (An addition around the paper's method: the per-case arithmetic is exactly
+ * that of dg_step.)
+ *
+ * Cases of one polynomial degree N share a device pool: their elements and
+ * sides sit side by side in one set of arrays, and one launch of each stage
+ * kernel (captured with the rest of the time step in a CUDA graph) advances
+ * every resident case of that N by one LSERK4 step, each with its own CFL
+ * time step, time and end time.  A worker thread admits waiting cases as
+ * soon as their pool has room (a free element range, a free side range and a
+ * free case slot: admission by device memory), builds their maps and metrics
+ * on a second stream while the resident cases keep stepping, retires cases
+ * that reached their end time, and records each case's time to solution.
+ * Per-element arithmetic does not depend on the other cases of a launch, so a
+ * case's result is the same alone and in any mix.
+ * ------------------------------------------------------------------------ */
+typedef struct dg_server dg_server;
+
+typedef struct {
+  double gamma, R, Pr;     /* common to every case                           */
+  double dfl;              /* viscous time-step factor                       */
+  int precision;           /* DG_FP64 or DG_FP32_BULK                        */
+  int max_cases;           /* case slots (resident cases), >= 1               */
+  int64_t pool_elems[8];   /* pool capacity in elements for N = 1..7 (index N);
+                              0 = that N is not served                      */
+} dg_server_config;
+
+typedef struct {
+  dg_mesh_desc mesh;       /* as for dg_init_mesh (host memory, copied)      */
+  const double* U0;        /* initial state [E][node][5], host, copied       */
+  double t_end;            /* end time (the state starts at t = 0)           */
+  double mu;               /* viscosity; 0 gives the Euler equations         */
+  int riemann;             /* DG_RIEMANN_ROE or DG_RIEMANN_LF                */
+  double cfl;              /* CFL factor of the case                         */
+} dg_case_desc;
+
+/* Fills cfg with defaults: gamma 1.4, R 1, Pr 0.72, DFL 0.9, FP64, 64 case
+   slots, pools of 262,144 elements for N = 3 and N = 5 and 65,536 elements
+   for N = 7 (about 48 GB in FP64; set the capacities to fit the device). */
+void dg_server_default_config(dg_server_config* cfg);
+
+/* Creates the server, its pools (device memory of all capacities is
+   allocated here) and its worker thread, on the current device.
+   Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
+int dg_server_create(dg_server** out, const dg_server_config* cfg);
+
+/* Queues one case (non-blocking; mesh and state are copied).  *ticket
+   identifies it in dg_poll.  DG_ERR_ARG if its N has no pool or it can never
+   fit its pool. */
+int dg_submit(dg_server* srv, const dg_case_desc* desc, int64_t* ticket);
+
+/* DG_PENDING while the case is waiting or running; DG_OK once finished, then
+   U_out (host, [E][node][5], may be NULL) receives the final state and
+   stats (may be NULL) 8 doubles: time to solution (s, submit to done), queue
+   wait (submit to admission), service time (admission to done), final time,
+   steps, elements, N, 1 if the case met a non-finite value (else 0).
+   A finished case can be polled any number of times; DG_ERR_ARG for an
+   unknown ticket. */
+int dg_poll(dg_server* srv, int64_t ticket, double* U_out, double* stats);
+
+/* Server counters: out[0] batched steps launched, out[1] cases finished,
+   out[2] cases resident, out[3] cases waiting, out[4] graph captures,
+   out[5] DOF-stage updates done (sum over cases of DOF x 5 per step). */
+int dg_server_stats(dg_server* srv, double* out);
+
+/* Stops the worker after the current step and frees everything. */
+void dg_server_destroy(dg_server* srv);
+
 /* Kinetic energy of a caller-owned state, allocating no device memory.
    The paper has no counterpart: this is an interface addition for callers that
    cannot call cudaMalloc -- applications whose device memory is handed out in

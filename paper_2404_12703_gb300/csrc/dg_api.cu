@@ -276,6 +276,8 @@ void dg_destroy(dg_ctx* c) {
   cudaFree(c->fvmetric);
   cudaFree(c->cflgeo);
   cudaFree(c->elem_side);
+  cudaFree(c->elem_case);
+  cudaFree(c->side_case);
   cudaFree(c->side_e);
   cudaFree(c->side_f);
   cudaFree(c->ops);
@@ -284,6 +286,87 @@ void dg_destroy(dg_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
+
+}  // extern "C"
+
+namespace dg {
+
+// A serving pool: the arrays of a context sized for capE elements and 3 capE
+// sides, every slot free (case maps -1, other arrays zero), no mesh yet.
+int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, cudaStream_t stream,
+                    std::string& msg) {
+  *out = nullptr;
+  dg_ctx* c = new dg_ctx();
+  cudaGetDevice(&c->device);
+  c->stream = stream;
+  c->prm = *params;
+  c->N = N;
+  c->n = N + 1;
+  c->n2 = c->n * c->n;
+  c->n3 = c->n2 * c->n;
+  c->E = 0;
+  c->S = 0;
+  const int64_t E = capE, S = 3 * capE, n3 = c->n3, n2 = c->n2;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  A(dalloc(&c->U, E * 5 * n3, c->bytes));
+  A(dalloc(&c->dU, E * 5 * n3, c->bytes));
+  A(dalloc(&c->Ut, E * 5 * n3, c->bytes));
+  A(dalloc(&c->Upub, E * 5 * n3, c->bytes));
+  A(dalloc(&c->metric, E * 10 * n3, c->bytes));
+  A(dalloc(&c->g, E * 12 * n3, c->bytes));
+  A(dalloc(&c->g32, E * 12 * n3, c->bytes));
+  A(dalloc(&c->alpha, E, c->bytes));
+  A(dalloc(&c->fvmetric, E * 3 * (c->n - 1) * 3 * n2, c->bytes));
+  A(dalloc(&c->cflgeo, E * 4 * n3, c->bytes));
+  A(dalloc(&c->elem_side, E * 6, c->bytes));
+  A(dalloc(&c->elem_case, E, c->bytes));
+  A(dalloc(&c->nrm, S * 4 * n2, c->bytes));
+  A(dalloc(&c->lflux, S * 12 * n2, c->bytes));
+  A(dalloc(&c->fstar, S * 5 * n2, c->bytes));
+  A(dalloc(&c->lflux32, S * 12 * n2, c->bytes));
+  A(dalloc(&c->fstar32, S * 5 * n2, c->bytes));
+  A(dalloc(&c->side_e, S, c->bytes));
+  A(dalloc(&c->side_f, S, c->bytes));
+  A(dalloc(&c->side_case, S, c->bytes));
+  A(dalloc(&c->ops, 1, c->bytes));
+  A(dalloc(&c->scal, 1, c->bytes));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->scal_host, sizeof(DevScalars));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = init_kernel_attributes(N);
+  if (e == cudaSuccess) {
+    Ops ops;
+    build_ops(N, ops);
+    A(cudaMemcpyAsync(c->ops, &ops, sizeof(Ops), cudaMemcpyHostToDevice, stream));
+    A(cudaMemsetAsync(c->scal, 0, sizeof(DevScalars), stream));
+    A(cudaMemsetAsync(c->U, 0, sizeof(double) * E * 5 * n3, stream));
+    A(cudaMemsetAsync(c->dU, 0, sizeof(double) * E * 5 * n3, stream));
+    A(cudaMemsetAsync(c->metric, 0, sizeof(double) * E * 10 * n3, stream));
+    A(cudaMemsetAsync(c->cflgeo, 0, sizeof(double) * E * 4 * n3, stream));
+    A(cudaMemsetAsync(c->g, 0, sizeof(double) * E * 12 * n3, stream));
+    A(cudaMemsetAsync(c->g32, 0, sizeof(float) * E * 12 * n3, stream));
+    A(cudaMemsetAsync(c->elem_side, 0, sizeof(int) * E * 6, stream));
+    A(cudaMemsetAsync(c->side_e, 0, sizeof(int2) * S, stream));
+    A(cudaMemsetAsync(c->side_f, 0, sizeof(int) * S, stream));
+    A(cudaMemsetAsync(c->nrm, 0, sizeof(double) * S * 4 * n2, stream));
+    A(cudaMemsetAsync(c->elem_case, 0xff, sizeof(int) * E, stream));
+    A(cudaMemsetAsync(c->side_case, 0xff, sizeof(int) * S, stream));
+    A(cudaStreamSynchronize(stream));
+  }
+  if (e != cudaSuccess) {
+    msg = std::string("pool allocation: ") + cudaGetErrorString(e);
+    const int code = e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+    dg_destroy(c);
+    return code;
+  }
+  c->state_set = true;
+  *out = c;
+  return DG_OK;
+}
+
+}  // namespace dg
+
+extern "C" {
 
 int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params, void* stream) {
   if (!out) return fail(DG_ERR_ARG, "out is NULL");

@@ -24,6 +24,10 @@ void lgl_weights(int N, double* w);
 // allocation of the side arrays once the number of sides is known
 int alloc_side_arrays(dg_ctx* c, std::string& msg);
 
+// serving pool of capE elements with every slot free (dg_api.cu)
+int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, cudaStream_t stream,
+                    std::string& msg);
+
 // device mesh set-up (dg_mesh.cu)
 int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::string& msg);
 

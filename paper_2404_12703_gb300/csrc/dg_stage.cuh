@@ -68,6 +68,22 @@ struct SPrim {
   T rho, u, v, w, p, H, Tt;  // p, H, Tt shifted by the context's references
 };
 
+// Parameters that may differ between the cases of a serving pool
+struct CaseParams {
+  double mu, lam, pr, Hr, Tr;
+  int riemann;
+};
+__device__ __forceinline__ CaseParams case_params(const StageArgs& a, int c) {
+  if (a.cases) {
+    const CaseData& d = a.cases[c < 0 ? 0 : c];
+    return {d.mu, d.lam, d.ref_p, d.ref_H, d.ref_T, d.riemann};
+  }
+  return {a.mu, a.lam, a.scal->ref_p, a.scal->ref_H, a.scal->ref_T, a.riemann};
+}
+__device__ __forceinline__ double case_dt(const StageArgs& a, int c) {
+  return a.cases ? a.cases[c < 0 ? 0 : c].dt : a.scal->dt;
+}
+
 // ConsToPrim (Eqs. eos_p, eos_T) in FP64, then shifted and rounded to T
 template <typename T>
 __device__ __forceinline__ SPrim<T> shifted_prim(const double U[5], double gm1, double Rinv, double pr, double Hr,
@@ -164,6 +180,9 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   if (tid >= (int64_t)a.S * n2) return;
   const int s = (int)(tid / n2), pq = (int)(tid % n2);
   const int p = pq % n, q = pq / n;
+  const int cs = a.side_case ? a.side_case[s] : 0;
+  if (cs < 0) return;  // free side slot of a serving pool
+  const CaseParams cp = case_params(a, cs);
   const int2 ee = a.side_e[s];
   const int sf = a.side_f[s];
   const int fM = sf & 15, fS = (sf >> 4) & 15, flip = sf >> 8;
@@ -175,9 +194,8 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
 #pragma unroll
   for (int k = 0; k < 5; ++k) { UM[k] = uM[k * n3]; US[k] = uS[k * n3]; }
-  const double pr = a.scal->ref_p, Hr = a.scal->ref_H, Tr = a.scal->ref_T;
-  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, pr, Hr, Tr);
-  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, pr, Hr, Tr);
+  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp.pr, cp.Hr, cp.Tr);
+  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp.pr, cp.Hr, cp.Tr);
   const T qa[4] = {T(0.5) * (qM.u + qS.u), T(0.5) * (qM.v + qS.v), T(0.5) * (qM.w + qS.w), T(0.5) * (qM.Tt + qS.Tt)};
   const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
   const T sn[3] = {T(nr[0]), T(nr[n2]), T(nr[2 * n2])};
@@ -203,8 +221,16 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
   // Slots past the last element redo the last element in their own shared
   // memory slot, so that every thread of a block runs the same path through
   // the barriers; only the final global stores are masked.
-  const bool valid = blockIdx.x * EPB + le < a.E;
-  const int e = valid ? blockIdx.x * EPB + le : a.E - 1;
+  const int e = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
+  const int ce = a.elem_case ? a.elem_case[e] : 0;
+  // free element slots of a serving pool compute on whatever they hold and
+  // store nothing, like the slots past the last element
+  const bool valid = blockIdx.x * EPB + le < a.E && ce >= 0;
+  // a block of free pool slots, or of cases that have reached their end time
+  // (time step 0), only leaves (every thread takes this barrier)
+  const bool busy = valid && !(a.cases && a.cases[ce].dt == 0.0);
+  if (a.elem_case && __syncthreads_and(!busy)) return;
+  const CaseParams cp = case_params(a, ce);
   for (int k = threadIdx.x; k < n2; k += blockDim.x) sDh[k] = T(a.ops->Dhat[k]);
   T* q = sq + le * 4 * n3;
   T* F = sF + le * 12 * n3;
@@ -214,7 +240,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
     const double* u = a.U + (size_t)e * 5 * n3 + t;
 #pragma unroll
     for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
-    const SPrim<T> pr = shifted_prim<T>(U, a.gm1, a.Rinv, a.scal->ref_p, a.scal->ref_H, a.scal->ref_T);
+    const SPrim<T> pr = shifted_prim<T>(U, a.gm1, a.Rinv, cp.pr, cp.Hr, cp.Tr);
     q[t] = pr.u;
     q[n3 + t] = pr.v;
     q[2 * n3 + t] = pr.w;
@@ -290,6 +316,10 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   if (tid >= (int64_t)a.S * n2) return;
   const int s = (int)(tid / n2), pq = (int)(tid % n2);
   const int p = pq % n, q = pq / n;
+  const int cs = a.side_case ? a.side_case[s] : 0;
+  if (cs < 0) return;  // free side slot of a serving pool
+  const CaseParams cp = case_params(a, cs);
+  const double pr = cp.pr, Hr = cp.Hr, Tr = cp.Tr;
   const int2 ee = a.side_e[s];
   const int sf = a.side_f[s];
   const int fM = sf & 15, fS = (sf >> 4) & 15, flip = sf >> 8;
@@ -301,7 +331,6 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
 #pragma unroll
   for (int k = 0; k < 5; ++k) { UM[k] = uM[k * n3]; US[k] = uS[k * n3]; }
-  const double pr = a.scal->ref_p, Hr = a.scal->ref_H, Tr = a.scal->ref_T;
   const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, pr, Hr, Tr);
   const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, pr, Hr, Tr);
   const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
@@ -311,7 +340,7 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   const T sA = T(sAd);
   const T nu[3] = {T(nr[0] * invd), T(nr[n2] * invd), T(nr[2 * n2] * invd)};
   T f[5];
-  if (a.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, T(a.gm1), T(Hr), f);
+  if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, T(a.gm1), T(Hr), f);
   else lf_flux_s(qM, qS, nu, T(a.gamma), T(pr), f);
 #pragma unroll
   for (int k = 0; k < 5; ++k) f[k] *= sA;
@@ -323,9 +352,9 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) { gM[k] = pgM[k * n3]; gS[k] = pgS[k * n3]; }
     T tau[6], W[3], fvM[4], fvS[4];
-    viscous_parts(gM, qM.u, qM.v, qM.w, T(a.mu), T(a.lam), tau, W);
+    viscous_parts(gM, qM.u, qM.v, qM.w, T(cp.mu), T(cp.lam), tau, W);
     viscous_flux_n(tau, W, sn, fvM);
-    viscous_parts(gS, qS.u, qS.v, qS.w, T(a.mu), T(a.lam), tau, W);
+    viscous_parts(gS, qS.u, qS.v, qS.w, T(cp.mu), T(cp.lam), tau, W);
     viscous_flux_n(tau, W, sn, fvS);
 #pragma unroll
     for (int k = 0; k < 4; ++k) f[1 + k] -= T(0.5) * (fvM[k] + fvS[k]);
@@ -431,9 +460,16 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
   T* sG = sJ + EPB * 9 * n3;                                     // [EPB][5][n3] viscous / FV fluxes
   T* sA = sG + EPB * 5 * n3;                                     // [EPB][3][5][n3] two-point sums
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
-  // slots past the last element redo the last element (see k_lift)
-  const bool valid = blockIdx.x * EPB + le < a.E;
-  const int e = valid ? blockIdx.x * EPB + le : a.E - 1;
+  // slots past the last element redo the last element, free slots of a
+  // serving pool compute on what they hold; neither stores (see k_lift)
+  const int e = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
+  const int ce = a.elem_case ? a.elem_case[e] : 0;
+  const bool valid = blockIdx.x * EPB + le < a.E && ce >= 0;
+  // a block of free pool slots, or of cases that have reached their end time
+  // (time step 0), only leaves (every thread takes this barrier)
+  const bool busy = valid && !(a.cases && a.cases[ce].dt == 0.0);
+  if (a.elem_case && __syncthreads_and(!busy)) return;
+  const CaseParams cp = case_params(a, ce);
   for (int k = threadIdx.x; k < n2; k += blockDim.x) {
     sDs[k] = T(a.ops->Dsplit[k]);
     sDh[k] = T(a.ops->Dhat[k]);
@@ -444,7 +480,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
   T* G = sG + le * 5 * n3;
   T* A = sA + le * 15 * n3;
   const double* Me = a.metric + (size_t)e * 10 * n3;
-  const double pr_ref = a.scal->ref_p, H_ref = a.scal->ref_H, T_ref = a.scal->ref_T;
+  const double pr_ref = cp.pr, H_ref = cp.Hr, T_ref = cp.Tr;
   double U[5];
   double p_full;
   SPrim<T> me;
@@ -477,7 +513,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
   T accC[5] = {0, 0, 0, 0, 0};  // convective DG volume term
   T acc[5] = {0, 0, 0, 0, 0};   // viscous volume + surface terms
   T tau[6] = {0, 0, 0, 0, 0, 0}, W[3] = {0, 0, 0};
-  if (a.viscous) viscous_parts(g, me.u, me.v, me.w, T(a.mu), T(a.lam), tau, W);
+  if (a.viscous) viscous_parts(g, me.u, me.v, me.w, T(cp.mu), T(cp.lam), tau, W);
   // ---- split-form KEP volume integral ----
   // FP64 (bound by the FP64 pipe): one line per task; every unordered pair
   // (i, alpha) of the line forms the symmetric two-point flux once and adds
@@ -701,7 +737,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) o[k * n3] = Ut[k];
   } else {
-    const double dt = a.scal->dt;
+    const double dt = case_dt(a, ce);
     double* du = a.dU + (size_t)e * 5 * n3 + t;
     double* uo = a.Urk + (size_t)e * 5 * n3 + t;
 #pragma unroll
@@ -747,6 +783,9 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.alpha_max = c->prm.alpha_max;
   a.alpha_force = c->prm.alpha_force;
   a.scal = c->scal;
+  a.elem_case = c->elem_case;
+  a.side_case = c->side_case;
+  a.cases = c->cases;
   return a;
 }
 

@@ -37,6 +37,21 @@ struct DevScalars {
   double ref_p, ref_H, ref_T;  // reference state of the shifted primitives (0 in FP64)
 };
 
+// Per-case data of a serving pool (device, one entry per case slot).
+struct CaseData {
+  double dt, t, t_end;
+  double mu, lam;              // viscosity and heat conductivity (0: Euler)
+  double ref_p, ref_H, ref_T;  // reference state of the shifted primitives
+  double cfl, dfl;
+  unsigned long long lam_c, lam_v;  // CFL reductions (bits of positive doubles)
+  int riemann;
+  int active;     // 1 while the case is resident
+  int nonfinite;  // sticky
+  int steps;      // completed steps
+  int N;          // polynomial degree of the case's pool
+  int pad;
+};
+
 // Per-stage launch parameters of the RHS kernels.
 struct StageArgs {
   int E, S;
@@ -65,6 +80,11 @@ struct StageArgs {
   const DevScalars* scal;
   double rkA, rkB;
   int first_stage;
+  // serving pools: case of every element / side (-1: free slot) and the
+  // per-case data; null for a single-mesh context
+  const int* elem_case;
+  const int* side_case;
+  const CaseData* cases;
 };
 
 }  // namespace dg
@@ -106,6 +126,11 @@ struct dg_ctx {
   int step_graph_kind = -1;
   // per-kernel event timing (dg_profile_step); null when not profiling
   struct Profiler* prof = nullptr;
+  // serving pool (null for a single-mesh context): case maps and case table
+  int* elem_case = nullptr;
+  int* side_case = nullptr;
+  dg::CaseData* cases = nullptr;
+  int n_case_slots = 0;
 };
 
 // Event pairs around each kernel launch, grouped by kernel kind.

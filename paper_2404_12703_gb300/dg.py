@@ -26,7 +26,9 @@ FP64, FP32_BULK = 0, 1
 DEBUG_METRICS, DEBUG_MAPS, DEBUG_GRAD, DEBUG_FSTAR, DEBUG_ALPHA = 0, 1, 2, 3, 4
 
 #: every symbol include/dg.h declares
-EXPORTS = ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
+SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "dg_poll", "dg_server_stats",
+                 "dg_server_destroy")
+EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
            "dg_get_state", "dg_rhs", "dg_step", "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
            "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
 
@@ -47,6 +49,16 @@ class Params(C.Structure):
 class MeshDesc(C.Structure):
     _fields_ = [("N", C.c_int), ("n_elems", C.c_int64), ("corner_vid", C.POINTER(C.c_int64)),
                 ("xyz", C.POINTER(C.c_double))]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double), ("dfl", C.c_double),
+                ("precision", C.c_int), ("max_cases", C.c_int), ("pool_elems", C.c_int64 * 8)]
+
+
+class CaseDesc(C.Structure):
+    _fields_ = [("mesh", MeshDesc), ("U0", C.POINTER(C.c_double)), ("t_end", C.c_double), ("mu", C.c_double),
+                ("riemann", C.c_int), ("cfl", C.c_double)]
 
 
 def load(path: str | None = None):
@@ -81,6 +93,12 @@ def load(path: str | None = None):
             "dg_last_error": (C.c_char_p, []),
             "dg_launch_count": (C.c_int64, []),
             "dg_kinetic_noalloc": (C.c_int, [C.c_int, C.c_int64, vp, vp, vp, vp, vp]),
+            "dg_server_default_config": (None, [C.POINTER(ServerConfig)]),
+            "dg_server_create": (C.c_int, [C.POINTER(vp), C.POINTER(ServerConfig)]),
+            "dg_submit": (C.c_int, [vp, C.POINTER(CaseDesc), C.POINTER(C.c_int64)]),
+            "dg_poll": (C.c_int, [vp, C.c_int64, vp, dp]),
+            "dg_server_stats": (C.c_int, [vp, dp]),
+            "dg_server_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -277,3 +295,87 @@ class Solver:
             _check(self._lib.dg_debug(self._h, DEBUG_ALPHA, C.c_void_p(a.data_ptr()), None))
             return a.cpu().numpy()
         raise ValueError(what)
+
+
+class Server:
+    """Continuous-batching request loop (include/dg.h, "Serving").
+
+    ``pool_elems`` maps a polynomial degree to its pool capacity in elements;
+    cases of that degree are admitted while their pool has room.
+    """
+
+    STAT_KEYS = ("time_to_solution", "queue_wait", "service_time", "t_final", "steps", "elements", "N",
+                 "nonfinite")
+
+    def __init__(self, pool_elems=None, max_cases=64, precision=FP64, gamma=1.4, R=1.0, Pr=0.72, dfl=0.9):
+        lib = load()
+        self._lib = lib
+        cfg = ServerConfig()
+        lib.dg_server_default_config(C.byref(cfg))
+        cfg.gamma, cfg.R, cfg.Pr, cfg.dfl = gamma, R, Pr, dfl
+        cfg.precision = precision
+        cfg.max_cases = max_cases
+        if pool_elems is not None:
+            for N in range(8):
+                cfg.pool_elems[N] = int(pool_elems.get(N, 0))
+        self.cfg = cfg
+        self.meta = {}
+        h = C.c_void_p()
+        _check(lib.dg_server_create(C.byref(h), C.byref(cfg)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, mesh, U0, t_end, mu=0.0, riemann=ROE, cfl=0.9):
+        """Queue one case; returns its ticket.  Arrays are copied by the library."""
+        if isinstance(riemann, str):
+            riemann = {"roe": ROE, "lf": LF}[riemann]
+        xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
+        cvid = np.ascontiguousarray(mesh["corner_vid"], dtype=np.int64)
+        U0 = np.ascontiguousarray(U0, dtype=np.float64)
+        N, E = int(mesh["N"]), int(xyz.shape[0])
+        assert U0.size == E * (N + 1) ** 3 * 5
+        d = CaseDesc()
+        d.mesh = MeshDesc(N, E, cvid.ctypes.data_as(C.POINTER(C.c_int64)), xyz.ctypes.data_as(C.POINTER(C.c_double)))
+        d.U0 = U0.ctypes.data_as(C.POINTER(C.c_double))
+        d.t_end, d.mu, d.riemann, d.cfl = float(t_end), float(mu), int(riemann), float(cfl)
+        t = C.c_int64()
+        _check(self._lib.dg_submit(self._h, C.byref(d), C.byref(t)))
+        self.meta[t.value] = (N, E)
+        return t.value
+
+    def poll(self, ticket, with_state=True):
+        """(done, U or None, stats dict or None)."""
+        N, E = self.meta[ticket]
+        U = np.empty((E, (N + 1) ** 3, 5)) if with_state else None
+        st = (C.c_double * 8)()
+        code = self._lib.dg_poll(self._h, int(ticket), C.c_void_p(U.ctypes.data) if U is not None else None, st)
+        if code == DG_PENDING:
+            return False, None, None
+        _check(code)
+        return True, U, dict(zip(self.STAT_KEYS, list(st)))
+
+    def wait(self, ticket, timeout=600.0, with_state=True):
+        import time
+        t0 = time.time()
+        while True:
+            done, U, stats = self.poll(ticket, with_state)
+            if done:
+                return U, stats
+            if time.time() - t0 > timeout:
+                raise TimeoutError(f"case {ticket} not finished after {timeout} s")
+            time.sleep(0.002)
+
+    def stats(self):
+        out = (C.c_double * 6)()
+        _check(self._lib.dg_server_stats(self._h, out))
+        return dict(zip(("steps", "finished", "resident", "waiting", "captures", "dof_stage_updates"), list(out)))

@@ -42,8 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_binding_covers_header():
-    assert declared_functions() <= set(dg.EXPORTS) | {"dg_submit", "dg_poll"} or \
-        declared_functions() <= set(dg.EXPORTS) | set(getattr(dg, "SERVE_EXPORTS", ()))
+    assert declared_functions() <= set(dg.EXPORTS)
 
 
 def test_error_strings_without_gpu(lib):

@@ -1,0 +1,116 @@
+"""Serving (continuous batching): cases of different meshes and degrees share
+batched launches; each result must be the same alone and in the mix (bitwise:
+the per-element arithmetic does not depend on the other cases of a launch),
+equal the standalone solver over the same time-step sequence, and the loop
+must admit waiting cases as pool memory frees up."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+from paper_2404_12703_gb300 import workloads as W
+
+from gpu_util import gpu_or_skip
+
+pytestmark = pytest.mark.gpu
+
+
+def tgv_case(N, nel, seed):
+    m = W.box_mesh(N, nel, curved=0.1, seed=seed)
+    return m, W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5), 1.0 / 1600.0
+
+
+def vortex_case(N, nel, seed):
+    L = 10.0
+    m = W.box_mesh(N, nel, length=(L, L, L), curved=0.05, seed=seed)
+    U = W.isentropic_vortex_state(m["xyz"], center=(L / 2, L / 2), strength=5.0, period=m["period"])
+    return m, U.reshape(m["E"], -1, 5), 0.0
+
+
+CASES = [("tgv", 3, (4, 4, 4), 1), ("vortex", 5, (3, 4, 3), 2), ("tgv", 3, (3, 4, 5), 3),
+         ("vortex", 7, (3, 3, 3), 4), ("tgv", 5, (3, 3, 4), 5)]
+
+
+def make(kind, N, nel, seed):
+    return (tgv_case if kind == "tgv" else vortex_case)(N, nel, seed)
+
+
+POOLS = {3: 400, 5: 200, 7: 64}
+
+
+def test_alone_and_in_the_mix_are_bitwise_equal():
+    torch, dg = gpu_or_skip()
+    t_end = 0.06
+    built = [make(*c) for c in CASES]
+    alone = []
+    for m, U0, mu in built:
+        srv = dg.Server(POOLS, max_cases=8)
+        tk = srv.submit(m, U0, t_end, mu=mu)
+        U, st = srv.wait(tk)
+        srv.close()
+        assert st["t_final"] == t_end and st["nonfinite"] == 0 and st["steps"] >= 3
+        alone.append(U)
+    srv = dg.Server(POOLS, max_cases=8)
+    tickets = [srv.submit(m, U0, t_end, mu=mu) for m, U0, mu in built]
+    for tk, Ua in zip(tickets, alone):
+        U, st = srv.wait(tk)
+        np.testing.assert_array_equal(U, Ua)
+    s = srv.stats()
+    assert s["finished"] == len(CASES) and s["resident"] == 0
+    srv.close()
+
+
+def test_server_matches_standalone_solver():
+    """Same time-step sequence (CFL steps, the last one clipped at t_end)."""
+    torch, dg = gpu_or_skip()
+    m, U0, mu = make("tgv", 3, (4, 4, 4), 1)
+    t_end = 0.05
+    srv = dg.Server(POOLS, max_cases=4)
+    U, st = srv.wait(srv.submit(m, U0, t_end, mu=mu))
+    srv.close()
+    K = int(st["steps"])
+    s = dg.Solver(m, mu=mu)
+    s.set_state(U0)
+    s.step(K - 1)
+    _, t = s.get_state()
+    s.step(1, dt=t_end - t)
+    Us, ts = s.get_state()
+    assert abs(ts - t_end) < 1e-15
+    assert np.abs(U - Us).max() <= 1e-14 * np.abs(Us).max()
+
+
+def test_admission_waits_for_memory_and_overlaps():
+    """A pool that holds two of the cases at a time: the others queue, are
+    admitted as cases retire, and a case submitted while others run starts
+    before they finish."""
+    torch, dg = gpu_or_skip()
+    built = [make("tgv", 3, (4, 4, 4), s) for s in range(5)]
+    srv = dg.Server({3: 140}, max_cases=8)       # 64 elements per case: two fit
+    t_end = 0.05
+    tickets = [srv.submit(m, U0, t_end, mu=mu) for m, U0, mu in built[:4]]
+    time.sleep(0.05)
+    late = srv.submit(*built[4][:2], t_end, mu=built[4][2])
+    stats = [srv.wait(tk)[1] for tk in tickets + [late]]
+    waits = [st["queue_wait"] for st in stats]
+    assert max(waits) > 0.0
+    assert sum(1 for w in waits if w > 1e-3) >= 2    # some cases had to wait for memory
+    for st in stats:
+        assert st["t_final"] == t_end and st["nonfinite"] == 0
+    # a too-large case is refused at submission
+    big = W.box_mesh(3, (6, 6, 6))
+    with pytest.raises(dg.DgError):
+        srv.submit(big, W.tgv_state(big["xyz"]).reshape(big["E"], -1, 5), 0.01)
+    srv.close()
+
+
+def test_fp32_bulk_serving_close_to_fp64():
+    torch, dg = gpu_or_skip()
+    m, U0, mu = make("vortex", 5, (3, 4, 3), 2)
+    out = {}
+    for prec in (dg.FP64, dg.FP32_BULK):
+        srv = dg.Server(POOLS, max_cases=4, precision=prec)
+        out[prec] = srv.wait(srv.submit(m, U0, 0.1, mu=mu))[0]
+        srv.close()
+    err = np.sqrt(((out[dg.FP32_BULK] - out[dg.FP64]) ** 2).sum() / (out[dg.FP64] ** 2).sum())
+    assert err < 1e-5

@@ -46,12 +46,12 @@ BYTES_PER_DOF = 8 * (30 + 204 / (N_DEG + 1))
 # DRAM bytes per DOF of one k_volume<7,1> launch, from the ncu capture summarised
 # in profiles/k_volume_tgv12_N7_fp64.md (12^3 mesh; the traffic scales with
 # the DOF count).  Set to None whenever the kernel changes until re-measured.
-VOLUME_TRAFFIC_BYTES_PER_DOF = 330.5
+VOLUME_TRAFFIC_BYTES_PER_DOF = 332.05
 # FP32-bulk: algorithmic bytes per DOF of one volume-kernel launch (reads U 40,
-# FP64 metrics 80, FP32 lifted gradients 48, dU 40, surface fluxes ~8; writes
+# FP32 metrics 40, FP32 lifted gradients 48, dU 40, surface fluxes ~8; writes
 # U 40, dU 40), and of a whole stage for the minimal two-phase method with the
-# RK register and metrics in FP64 and the face traces in FP32: 342 B at N = 7.
-VOLUME32_BYTES_PER_DOF = 40 + 80 + 48 + 40 + 8 + 40 + 40
+# RK register in FP64 and the face traces in FP32: 342 B at N = 7.
+VOLUME32_BYTES_PER_DOF = 40 + 40 + 48 + 40 + 8 + 40 + 40
 BYTES32_PER_DOF = 342.0
 
 
@@ -163,16 +163,20 @@ def cpu_oracle_sample(steps, nel=6, seed=SEED):
     return dof, times
 
 
+SERVING_SIZES = (4, 8, 12, 16)
+SERVING_T_END = 0.02
+
+
 def serving_cases(n_cases, seed=5):
     """Seeded stream of cases (a shortened version of the serving workload):
-    mesh n^3 with n from {4, 6, 8}, N from {3, 5, 7}, half Taylor-Green vortex
-    (Re 1600, Ma 0.1, viscous), half isentropic vortex (inviscid, strength 5,
-    mean flow (1, 1, 0)), each to t_end = 0.05."""
+    mesh n^3 with n from {4, 8, 12, 16}, N from {3, 5, 7}, half Taylor-Green
+    vortex (Re 1600, Ma 0.1, viscous), half isentropic vortex (inviscid,
+    strength 5, mean flow (1, 1, 0)), each to t_end = 0.02."""
     from paper_2404_12703_gb300 import workloads as W
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for i in range(n_cases):
-        nel = int(rng.choice([4, 6, 8]))
+        nel = int(rng.choice(SERVING_SIZES))
         N = int(rng.choice([3, 5, 7]))
         if rng.random() < 0.5:
             m = W.box_mesh(N, (nel,) * 3, curved=0.1, seed=1000 + i)
@@ -184,16 +188,40 @@ def serving_cases(n_cases, seed=5):
             U = W.isentropic_vortex_state(m["xyz"], center=(L / 2, L / 2), strength=5.0,
                                           period=m["period"]).reshape(m["E"], -1, 5)
             mu, kind = 0.0, "vortex"
-        out.append({"mesh": m, "U0": U, "mu": mu, "kind": kind, "N": N, "nel": nel, "t_end": 0.05})
+        out.append({"mesh": m, "U0": U, "mu": mu, "kind": kind, "N": N, "nel": nel, "t_end": SERVING_T_END})
     return out
 
 
+SERVING_POOLS = {3: 16 ** 3 * 6, 5: 16 ** 3 * 6, 7: 16 ** 3 * 4}
+
+
+def serve_all(dg, cases, precision, arrivals):
+    """Submits the cases at the given arrival times (s after the start) to one
+    server; returns time-to-solution per case, makespan and server stats."""
+    srv = dg.Server(SERVING_POOLS, max_cases=64, precision=precision)
+    t0 = time.perf_counter()
+    tickets = []
+    for a, c in zip(arrivals, cases):
+        while time.perf_counter() - t0 < a:
+            time.sleep(0.0005)
+        tickets.append(srv.submit(c["mesh"], c["U0"], c["t_end"], mu=c["mu"]))
+    lat = []
+    for tk in tickets:
+        _, st = srv.wait(tk, with_state=False)
+        lat.append(st["time_to_solution"])
+    makespan = time.perf_counter() - t0
+    sstats = srv.stats()
+    srv.close()
+    return lat, makespan, sstats
+
+
 def serving_bench(dg, n_cases, precision):
-    """Continuous batching against the same cases run one by one."""
+    """Continuous batching against the same cases run one by one through the
+    standalone solver (dg_advance: the same CFL steps, the last one clipped at
+    the end time)."""
     import torch
     cases = serving_cases(n_cases)
     dofs = [c["mesh"]["E"] * (c["N"] + 1) ** 3 for c in cases]
-    # one by one through the standalone solver (graph-launched steps)
     service = []
     seq_dofstage = 0.0
     for c, dof in zip(cases, dofs):
@@ -201,14 +229,7 @@ def serving_bench(dg, n_cases, precision):
         sv.set_state(c["U0"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        t = 0.0
-        steps = 0
-        while t < c["t_end"]:
-            dt = sv.time_step()
-            dt = min(dt, c["t_end"] - t)
-            sv.step(1, dt=dt)
-            t += dt
-            steps += 1
+        _, steps = sv.advance(c["t_end"])
         sv.get_state()
         service.append(time.perf_counter() - t0)
         seq_dofstage += dof * STAGES * steps
@@ -225,26 +246,13 @@ def serving_bench(dg, n_cases, precision):
         free_at = start + sv_t
         seq_lat.append(free_at - a)
     seq_makespan = free_at
-    # the server: same arrivals
-    pools = {3: 8 ** 3 * 12, 5: 8 ** 3 * 12, 7: 8 ** 3 * 8}
-    srv = dg.Server(pools, max_cases=64, precision=precision)
-    t0 = time.perf_counter()
-    tickets = []
-    for a, c in zip(arrivals, cases):
-        while time.perf_counter() - t0 < a:
-            time.sleep(0.0005)
-        tickets.append(srv.submit(c["mesh"], c["U0"], c["t_end"], mu=c["mu"]))
-    lat = []
-    for tk in tickets:
-        _, st = srv.wait(tk, with_state=False)
-        lat.append(st["time_to_solution"])
-    makespan = time.perf_counter() - t0
-    sstats = srv.stats()
-    srv.close()
+    lat, makespan, sstats = serve_all(dg, cases, precision, arrivals)
+    # closed system: every case submitted at once (capacity, not arrivals)
+    _, sat_makespan, sat_stats = serve_all(dg, cases, precision, np.zeros(len(cases)))
     p = lambda v, q: float(np.percentile(np.asarray(v), q))
     return {
-        "workload": f"{len(cases)} cases (seeded PCG64(5)): n^3 meshes n in {{4,6,8}}, N in {{3,5,7}}, "
-                    f"half TGV (Re 1600, Ma 0.1), half isentropic vortex (inviscid), each to t = 0.05; "
+        "workload": f"{len(cases)} cases (seeded PCG64(5)): n^3 meshes n in {set(SERVING_SIZES)}, N in {{3,5,7}}, "
+                    f"half TGV (Re 1600, Ma 0.1), half isentropic vortex (inviscid), each to t = {SERVING_T_END}; "
                     f"Poisson arrivals at 0.9 x the one-by-one service rate ({rate:.2f}/s); shortened from "
                     f"the 200-case, t = 1 configuration",
         "precision": "FP64" if precision == dg.FP64 else "FP32-bulk",
@@ -252,9 +260,116 @@ def serving_bench(dg, n_cases, precision):
         "dof_updates_per_s": sstats["dof_stage_updates"] / makespan, "makespan_s": makespan,
         "one_by_one": {"p50_s": p(seq_lat, 50), "p99_s": p(seq_lat, 99),
                        "dof_updates_per_s": seq_dofstage / seq_makespan, "makespan_s": seq_makespan,
-                       "mean_service_s": mean_service},
+                       "mean_service_s": mean_service,
+                       "busy_dof_updates_per_s": seq_dofstage / sum(service)},
+        "all_at_once": {"makespan_s": sat_makespan,
+                        "dof_updates_per_s": sat_stats["dof_stage_updates"] / sat_makespan,
+                        "vs_one_by_one_busy": sum(service) / sat_makespan},
         "batched_steps": sstats["steps"], "graph_captures": sstats["captures"],
     }
+
+
+def shock_tube_bench(dg, torch, stream):
+    """Sod tube, 64 x 8 x 8 Cartesian elements on the periodic [0,2] x [0,1/4]^2
+    box, N = 5 (884,736 DOF), inviscid, LF fluxes, indicator + FV sub-cell
+    blending with alpha in [0, 0.5], CFL steps to t = 0.2; L1 density error
+    against the exact Riemann solution on 0.5 < x < 1.5."""
+    from paper_2404_12703_gb300 import workloads as W
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from exact_solutions import sod_exact
+    N, t_end = 5, 0.2
+    m = W.box_mesh(N, (64, 8, 8), length=(2.0, 0.25, 0.25), origin=(0.0, 0.0, 0.0))
+    dof = m["E"] * (N + 1) ** 3
+    U0 = W.sod_state(m["xyz"]).reshape(m["E"], -1, 5)
+    out = {}
+    for name, prec in (("fp64", dg.FP64), ("fp32_bulk", dg.FP32_BULK)):
+        s = dg.Solver(m, stream=stream, viscous=0, riemann="lf", shock_capturing=1, precision=prec)
+        s.set_state(U0)
+        s.advance(0.002)  # warm-up (graph capture)
+        s.set_state(U0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t, steps = s.advance(t_end)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        U, _ = s.get_state()
+        alpha = s.debug("alpha")
+        _, J = s.debug("metrics")
+        X = m["xyz"].reshape(m["E"], -1, 3)[..., 0]
+        sel = (X > 0.5) & (X < 1.5)
+        ex = sod_exact(X[sel], t_end, x0=1.0)
+        xg = W.lgl_points(N)
+        PN = np.polynomial.legendre.legval(xg, [0] * N + [1])
+        w = 2.0 / (N * (N + 1) * PN ** 2)  # LGL quadrature weights
+        wq = np.einsum("i,j,k->kji", w, w, w).reshape(-1)[None, :] * J
+        l1 = float((wq[sel] * np.abs(U[..., 0][sel] - ex[:, 0])).sum() / wq[sel].sum())
+        out[name] = {"steps": steps, "t_final": t, "ms_total": ms, "ms_per_step": ms / max(steps, 1),
+                     "dof_updates_per_s": dof * STAGES * steps / (ms * 1e-3), "l1_rho_err": l1,
+                     "blended_elements": int((alpha > 0).sum()), "alpha_max": float(alpha.max()),
+                     "finite": bool(np.isfinite(U).all())}
+        s.close()
+    return {"workload": "Sod tube 64x8x8 elements, N=5 (884,736 DOF), [0,2]x[0,1/4]^2 periodic, inviscid, LF, "
+                        "indicator + FV blending alpha in [0,0.5], CFL 0.9 to t = 0.2", **out}
+
+
+def run_long(args):
+    """FP32-bulk against FP64 over a long Taylor-Green run: 32^3 Cartesian
+    elements at N = 5 (7,077,888 DOF), Re 1600, Ma 0.1, both precisions from
+    the same state with the same fixed time step (the CFL step of the initial
+    state, adjusted to land on every output time), to t_end.  Prints one JSON
+    line with E_k and its exact dissipation rate at each output time and the
+    L2 state difference at the end."""
+    import torch
+    from paper_2404_12703_gb300 import build as B
+    from paper_2404_12703_gb300 import dg
+    from paper_2404_12703_gb300 import workloads as W
+    B.build()
+    dg.load()
+    N, nel = 5, 32
+    m = W.box_mesh(N, (nel,) * 3)
+    dof = m["E"] * (N + 1) ** 3
+    U0 = W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5)
+    stream = torch.cuda.Stream()
+    s64 = dg.Solver(m, stream=stream)
+    s32 = dg.Solver(m, stream=stream, precision=dg.FP32_BULK)
+    for s in (s64, s32):
+        s.set_state(U0)
+    every = args.long_every
+    per = int(np.ceil(every / s64.time_step()))
+    dt = every / per
+    rows, ms = [], {"fp64": 0.0, "fp32_bulk": 0.0}
+    t = 0.0
+    n_out = int(round(args.long_run / every))
+    for k in range(1, n_out + 1):
+        for name, s in (("fp64", s64), ("fp32_bulk", s32)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(per, dt=dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[name] += e0.elapsed_time(e1)
+        t = k * every
+        k64, k32 = s64.kinetic(), s32.kinetic()
+        rows.append({"t": t, "ek_fp64": k64[0], "ek_fp32": k32[0], "rate_fp64": -k64[1], "rate_fp32": -k32[1],
+                     "rate_rel_err": abs(k32[1] - k64[1]) / abs(k64[1]),
+                     "ek_rel_err": abs(k32[0] - k64[0]) / abs(k64[0])})
+        print(json.dumps({"progress": rows[-1]}), flush=True)
+    U64, _ = s64.get_state()
+    U32, _ = s32.get_state()
+    steps = per * n_out
+    line = {"workload": f"Taylor-Green vortex Re 1600 Ma 0.1, {nel}^3 Cartesian elements, N = {N} ({dof} DOF), "
+                        f"FP32-bulk vs FP64 from the same state, fixed dt = {dt:.6g} ({steps} steps) to t = {t}",
+            "rows": rows, "max_rate_rel_err": max(r["rate_rel_err"] for r in rows),
+            "l2_state_rel_err": float(np.sqrt(((U32 - U64) ** 2).sum() / (U64 ** 2).sum())),
+            "finite": bool(np.isfinite(U32).all() and np.isfinite(U64).all()),
+            "ms_per_step": {k: v / steps for k, v in ms.items()},
+            "dof_updates_per_s": {k: dof * STAGES * steps / (v * 1e-3) for k, v in ms.items()}}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -435,9 +550,15 @@ def run_ours(args):
         }
         s32.close()
 
+    shock = None
+    if not args.no_shock and rank == 0:
+        shock = shock_tube_bench(dg, torch, stream)
+
     serving = None
     if not args.no_serving and rank == 0:
-        serving = serving_bench(dg, args.serving_cases, dg.FP64)
+        serving = {"fp64": serving_bench(dg, args.serving_cases, dg.FP64)}
+        if not args.no_fp32:
+            serving["fp32_bulk"] = serving_bench(dg, args.serving_cases, dg.FP32_BULK)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -456,7 +577,8 @@ def run_ours(args):
             "gpu_launches": launches, "kernels": kernels, "roofline": roofline,
             "e2e": {"value": world * dof * STAGES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
-            "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32, "serving": serving,
+            "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32, "shock_tube": shock,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     solver.close()
@@ -474,10 +596,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serving-cases", type=int, default=24)
+    ap.add_argument("--serving-cases", type=int, default=48)
+    ap.add_argument("--no-shock", action="store_true", help="skip the shock-tube measurement")
     ap.add_argument("--nel", type=int, default=NEL,
                     help="elements per direction (24 is the benchmark workload; smaller for profiling)")
+    ap.add_argument("--long-run", type=float, default=0.0,
+                    help="instead of the benchmark: FP32-bulk vs FP64 Taylor-Green run (32^3, N = 5) to this time")
+    ap.add_argument("--long-every", type=float, default=0.25, help="output interval of --long-run")
     args = ap.parse_args()
+    if args.long_run > 0:
+        return run_long(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -130,6 +130,18 @@ int dg_rhs(dg_ctx* ctx, const double* U_dev, double* Ut_dev);
    step's initial state.  Stream-ordered (asynchronous, graph-launched). */
 int dg_step(dg_ctx* ctx, int n_steps, double dt);
 
+/* Advances the context's state with CFL time steps (as dg_step with dt <= 0)
+   to exactly t_end: the device clips a step that would pass t_end to end on
+   it, and steps taken after t_end is reached have dt = 0 and leave the state
+   unchanged.  The host launches the steps in batches sized from the last
+   time step, reading the time back between batches.  Stops early after
+   max_steps steps.  *t_out (may be NULL): the time reached; *steps_out (may
+   be NULL): the number of steps with dt > 0.  Synchronises the context's
+   stream.  Returns DG_ERR_NONFINITE if a step met a non-finite value.
+   (Sec. 2.2 advances the LSERK scheme to a prescribed end time; the exact
+   stop is this library's.) */
+int dg_advance(dg_ctx* ctx, double t_end, int64_t max_steps, double* t_out, int64_t* steps_out);
+
 /* Same work as dg_step, launched kernel by kernel (no graph) with CUDA events
    recorded on the context's stream around every launch.  Accumulates, per
    kernel kind k, the summed device time ms[k] and the launch count

@@ -178,8 +178,10 @@ static const double RKB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0
                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                               2277821191437.0 / 14882151754819.0};
 
-__global__ void k_set_scalars(DevScalars* s, double dt_fixed, int set_t, double t, int reset_flags) {
+__global__ void k_set_scalars(DevScalars* s, double dt_fixed, int set_t, double t, int reset_flags,
+                              double t_end = 0.0) {
   s->dt_fixed = dt_fixed;
+  s->t_end = t_end;
   if (set_t) s->t = t;
   if (reset_flags) s->nonfinite = 0;
 }
@@ -188,17 +190,6 @@ __global__ void k_zero_kin(DevScalars* s) {
   s->lam_c = 0ull;
   s->lam_v = 0ull;
 }
-__global__ void k_dt_only(DevScalars* s, double cfl, double dfl, int N, int viscous) {
-  const double np1 = N + 1.0;
-  const double lc = __longlong_as_double((long long)s->lam_c);
-  const double lv = __longlong_as_double((long long)s->lam_v);
-  double dt = cfl * 2.0 / (np1 * np1 * lc);
-  if (viscous && lv > 0) dt = fmin(dt, dfl * 4.0 / (np1 * np1 * np1 * np1 * lv));
-  s->kin[3] = dt;
-  s->lam_c = 0ull;
-  s->lam_v = 0ull;
-}
-
 static void destroy_graph(dg_ctx* c) {
   if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
   c->step_graph = nullptr;
@@ -265,6 +256,7 @@ void dg_destroy(dg_ctx* c) {
   cudaFree(c->Ut);
   cudaFree(c->Upub);
   cudaFree(c->metric);
+  cudaFree(c->metric32);
   cudaFree(c->g);
   cudaFree(c->nrm);
   cudaFree(c->lflux);
@@ -314,6 +306,7 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
   A(dalloc(&c->Ut, E * 5 * n3, c->bytes));
   A(dalloc(&c->Upub, E * 5 * n3, c->bytes));
   A(dalloc(&c->metric, E * 10 * n3, c->bytes));
+  A(dalloc(&c->metric32, E * 10 * n3, c->bytes));
   A(dalloc(&c->g, E * 12 * n3, c->bytes));
   A(dalloc(&c->g32, E * 12 * n3, c->bytes));
   A(dalloc(&c->alpha, E, c->bytes));
@@ -342,6 +335,7 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
     A(cudaMemsetAsync(c->U, 0, sizeof(double) * E * 5 * n3, stream));
     A(cudaMemsetAsync(c->dU, 0, sizeof(double) * E * 5 * n3, stream));
     A(cudaMemsetAsync(c->metric, 0, sizeof(double) * E * 10 * n3, stream));
+    A(cudaMemsetAsync(c->metric32, 0, sizeof(float) * E * 10 * n3, stream));
     A(cudaMemsetAsync(c->cflgeo, 0, sizeof(double) * E * 4 * n3, stream));
     A(cudaMemsetAsync(c->g, 0, sizeof(double) * E * 12 * n3, stream));
     A(cudaMemsetAsync(c->g32, 0, sizeof(float) * E * 12 * n3, stream));
@@ -393,6 +387,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params
   A(dalloc(&c->Ut, E * 5 * n3, c->bytes));
   A(dalloc(&c->Upub, E * 5 * n3, c->bytes));
   A(dalloc(&c->metric, E * 10 * n3, c->bytes));
+  A(dalloc(&c->metric32, E * 10 * n3, c->bytes));
   A(dalloc(&c->g, E * 12 * n3, c->bytes));
   A(dalloc(&c->g32, E * 12 * n3, c->bytes));
   A(dalloc(&c->alpha, E, c->bytes));
@@ -523,20 +518,15 @@ int dg_rhs(dg_ctx* c, const double* U_dev, double* Ut_dev) {
 }
 
 static cudaError_t enqueue_step(dg_ctx* c) {
-  cudaError_t e = launch_cfl(c);
+  cudaError_t e = launch_cfl(c, false);
   for (int s = 0; s < 5 && e == cudaSuccess; ++s) e = launch_rhs(c, c->U, 1, RKA[s], RKB[s], s == 0);
   return e;
 }
 
-int dg_step(dg_ctx* c, int n_steps, double dt) {
-  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
-  if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
-  if (n_steps < 0) return fail(DG_ERR_ARG, "n_steps < 0");
-  if (n_steps == 0) return DG_OK;
-  k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, dt > 0 ? dt : 0.0, 0, 0.0, 0);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && !c->step_graph) {
+// captures the whole time step once (CFL reduction + 5 stages)
+static cudaError_t ensure_step_graph(dg_ctx* c) {
+  cudaError_t e = cudaSuccess;
+  if (!c->step_graph) {
     cudaStream_t user = c->stream;
     c->stream = c->cap_stream;
     cudaGraph_t graph = nullptr;
@@ -549,16 +539,74 @@ int dg_step(dg_ctx* c, int n_steps, double dt) {
     c->stream = user;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, graph, 0);
     if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      c->step_graph = nullptr;
-      return cuda_fail(e, "graph capture of a time step");
-    }
+    if (e != cudaSuccess) c->step_graph = nullptr;
   }
-  for (int i = 0; i < n_steps && e == cudaSuccess; ++i) {
+  return e;
+}
+
+static cudaError_t launch_steps(dg_ctx* c, int64_t n_steps) {
+  cudaError_t e = ensure_step_graph(c);
+  if (e != cudaSuccess) return e;
+  for (int64_t i = 0; i < n_steps && e == cudaSuccess; ++i) {
     e = cudaGraphLaunch(c->step_graph, c->stream);
     count_launch(2 + 5 * (c->prm.viscous ? 4 : 2));
   }
+  return e;
+}
+
+int dg_step(dg_ctx* c, int n_steps, double dt) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  if (n_steps < 0) return fail(DG_ERR_ARG, "n_steps < 0");
+  if (n_steps == 0) return DG_OK;
+  k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, dt > 0 ? dt : 0.0, 0, 0.0, 0);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_steps(c, n_steps);
   if (e != cudaSuccess) return cuda_fail(e, "dg_step");
+  return DG_OK;
+}
+
+int dg_advance(dg_ctx* c, double t_end, int64_t max_steps, double* t_out, int64_t* steps_out) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  if (!(t_end > 0) || !std::isfinite(t_end)) return fail(DG_ERR_ARG, "t_end must be finite and > 0");
+  if (max_steps < 0) return fail(DG_ERR_ARG, "max_steps < 0");
+  DevScalars* h = c->scal_host;
+  auto read_back = [&]() {
+    cudaError_t r = cudaMemcpyAsync(h, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
+    return r;
+  };
+  k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, 0.0, 0, 0.0, 0, t_end);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = read_back();
+  const long long steps0 = h->steps;
+  int64_t launched = 0;
+  double dt_last = 0.0;
+  while (e == cudaSuccess && h->t < t_end && launched < max_steps && !h->nonfinite) {
+    // a batch that ends just short of t_end at the last step's size; the
+    // last few steps go one at a time
+    int64_t K = 1;
+    if (dt_last > 0) K = std::max<int64_t>(1, (int64_t)(0.95 * (t_end - h->t) / dt_last));
+    K = std::min<int64_t>(K, max_steps - launched);
+    e = launch_steps(c, K);
+    launched += K;
+    if (e == cudaSuccess) e = read_back();
+    dt_last = h->dt;
+  }
+  // later dg_step calls take no end time
+  if (e == cudaSuccess) {
+    k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, 0.0, 0, 0.0, 0, 0.0);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "dg_advance");
+  c->t_host = h->t;
+  if (t_out) *t_out = h->t;
+  if (steps_out) *steps_out = (int64_t)(h->steps - steps0);
+  if (h->nonfinite) return fail(DG_ERR_NONFINITE, "a time step met a non-finite value");
   return DG_OK;
 }
 
@@ -604,20 +652,12 @@ int dg_profile_step(dg_ctx* c, int n_steps, double dt, double* ms, int64_t* laun
 int dg_time_step(dg_ctx* c, double* dt) {
   if (!c || !dt) return fail(DG_ERR_ARG, "ctx or dt is NULL");
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
-  k_zero_kin<<<1, 1, 0, c->stream>>>(c->scal);
-  count_launch();
-  // reuse the CFL reduction, but report instead of stepping
-  const double kv = std::max(4.0 / 3.0, c->prm.gamma / c->prm.Pr) * c->prm.mu;
-  (void)kv;
-  cudaError_t e = launch_cfl(c);  // advances t by the CFL dt: undo below
+  // the CFL reduction of a step, reported instead of taken
+  cudaError_t e = launch_cfl(c, true);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->scal_host, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "dg_time_step");
-  *dt = c->scal_host->dt;
-  k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, 0.0, 1, c->scal_host->t - c->scal_host->dt, 0);
-  count_launch();
-  e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "dg_time_step");
+  *dt = c->scal_host->dt_cfl;
   if (c->scal_host->nonfinite) return fail(DG_ERR_NONFINITE, "non-finite value in the state");
   return DG_OK;
 }

@@ -37,7 +37,8 @@ int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::strin
 cudaError_t launch_rhs(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first_stage);
 
 // CFL reduction: writes dt (and advances nothing); fixed dt if dt_fixed > 0
-cudaError_t launch_cfl(dg_ctx* c);
+// report_only: writes the CFL time step to dt_cfl instead of taking the step
+cudaError_t launch_cfl(dg_ctx* c, bool report_only);
 
 // raises the dynamic shared-memory limits of the kernels of degree N
 cudaError_t init_kernel_attributes(int N);

@@ -291,6 +291,12 @@ __global__ void k_cfl_geo(int E, const double* __restrict__ metric, double* __re
   G[3 * n3] = b;
 }
 
+// FP32 copy of an FP64 array (round to nearest)
+__global__ void k_round_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+
 template <int N>
 static cudaError_t launch_metrics(dg_ctx* c, const double* d_xyz) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -303,7 +309,9 @@ static cudaError_t launch_metrics(dg_ctx* c, const double* d_xyz) {
                                                                        c->nrm);
   const int64_t nodes = c->E * n3;
   k_cfl_geo<N><<<(unsigned)((nodes + 255) / 256), 256, 0, c->stream>>>((int)c->E, c->metric, c->cflgeo);
-  count_launch(2);
+  const int64_t mwords = c->E * 10 * n3;
+  k_round_f32<<<(unsigned)((mwords + 255) / 256), 256, 0, c->stream>>>(mwords, c->metric, c->metric32);
+  count_launch(3);
   return cudaGetLastError();
 }
 

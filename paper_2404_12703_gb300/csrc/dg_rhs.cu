@@ -11,39 +11,39 @@ namespace dg {
 // ---------------------------------------------------------------------------
 // CFL reduction (the paper gives no rule; see dg_time_step in dg.h)
 // ---------------------------------------------------------------------------
-template <int N>
+// T = float (FP32-bulk): the spectral radii in FP32, from the FP32 metrics
+template <int N, typename T>
 __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U, const double* __restrict__ metric,
-                                            const double* __restrict__ geo, double gamma, double gm1, double Rinv,
-                                            double kv, int viscous, DevScalars* scal) {
+                                            const float* __restrict__ metric32, const double* __restrict__ geo,
+                                            double gamma, double gm1, double Rinv, double kv, int viscous,
+                                            DevScalars* scal) {
   constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
+  constexpr bool f32 = sizeof(T) == sizeof(float);
   double lc = 0.0, lv = 0.0;
   int bad = 0;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < (int64_t)E * n3;
        x += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = x / n3;
     const int t = (int)(x % n3);
-    double Uv[5];
+    T Uv[5];
     const double* up = U + e * 5 * n3 + t;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) Uv[k] = up[k * n3];
-    const double ri = 1.0 / Uv[0];
-    const double u = Uv[1] * ri, v = Uv[2] * ri, w = Uv[3] * ri;
-    const double p = gm1 * (Uv[4] - 0.5 * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
-    const double c = sqrt(gamma * p * ri);
-    const double* Me = metric + e * 10 * n3 + t;
+    for (int k = 0; k < 5; ++k) Uv[k] = T(up[k * n3]);
+    const T ri = T(1) / Uv[0];
+    const T u = Uv[1] * ri, v = Uv[2] * ri, w = Uv[3] * ri;
+    const T p = T(gm1) * (Uv[4] - T(0.5) * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
+    const T c = sqrt(T(gamma) * p * ri);
+    auto M = [&](int k) { return f32 ? T(metric32[(e * 10 + k) * n3 + t]) : T(metric[(e * 10 + k) * n3 + t]); };
     const double* Gm = geo + e * 4 * n3 + t;
-    const double Ji = Me[9 * n3];
-    double aa = 0.0;
+    const T Ji = M(9);
+    T aa = T(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const double j0 = Me[(d * 3) * n3], j1 = Me[(d * 3 + 1) * n3], j2 = Me[(d * 3 + 2) * n3];
-      aa += fabs(u * j0 + v * j1 + w * j2) + c * Gm[d * n3];
-    }
+    for (int d = 0; d < 3; ++d) aa += fabs(u * M(d * 3) + v * M(d * 3 + 1) + w * M(d * 3 + 2)) + c * T(Gm[d * n3]);
     aa *= Ji;
-    const double bb = kv * ri * Gm[3 * n3] * Ji * Ji;
+    const T bb = T(kv) * ri * T(Gm[3 * n3]) * Ji * Ji;
     if (!isfinite(aa) || !isfinite(bb)) bad = 1;
-    lc = fmax(lc, aa);
-    lv = fmax(lv, bb);
+    lc = fmax(lc, double(aa));
+    lv = fmax(lv, double(bb));
   }
   // block reduction
   __shared__ double rc[32], rv[32];
@@ -67,22 +67,42 @@ __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U
   }
 }
 
-__global__ void k_dt(DevScalars* scal, double cfl, double dfl, int N, int viscous) {
+// the CFL rule from the reduced spectral radii
+__device__ __forceinline__ double cfl_dt(const DevScalars* scal, double cfl, double dfl, int N, int viscous) {
   const double np1 = (double)(N + 1);
-  double dt;
-  if (scal->dt_fixed > 0) {
-    dt = scal->dt_fixed;
-  } else {
-    const double lc = __longlong_as_double((long long)scal->lam_c);
-    const double lv = __longlong_as_double((long long)scal->lam_v);
-    dt = cfl * 2.0 / (np1 * np1 * lc);
-    if (viscous && lv > 0) {
-      const double dv = dfl * 4.0 / (np1 * np1 * np1 * np1 * lv);
-      if (dv < dt) dt = dv;
+  const double lc = __longlong_as_double((long long)scal->lam_c);
+  const double lv = __longlong_as_double((long long)scal->lam_v);
+  double dt = cfl * 2.0 / (np1 * np1 * lc);
+  if (viscous && lv > 0) {
+    const double dv = dfl * 4.0 / (np1 * np1 * np1 * np1 * lv);
+    if (dv < dt) dt = dv;
+  }
+  return dt;
+}
+
+// reports the CFL time step of the current state without stepping
+__global__ void k_dt_report(DevScalars* scal, double cfl, double dfl, int N, int viscous) {
+  scal->dt_cfl = cfl_dt(scal, cfl, dfl, N, viscous);
+  scal->lam_c = 0ull;
+  scal->lam_v = 0ull;
+}
+
+__global__ void k_dt(DevScalars* scal, double cfl, double dfl, int N, int viscous) {
+  double dt = scal->dt_fixed > 0 ? scal->dt_fixed : cfl_dt(scal, cfl, dfl, N, viscous);
+  double tn = scal->t + dt;
+  if (scal->t_end > 0) {
+    const double rest = scal->t_end - scal->t;
+    if (!(rest > 0)) {
+      dt = 0.0;
+      tn = scal->t;
+    } else if (dt >= rest) {
+      dt = rest;
+      tn = scal->t_end;
     }
   }
   scal->dt = dt;
-  scal->t += dt;
+  scal->t = tn;
+  if (dt > 0) scal->steps += 1;
   scal->lam_c = 0ull;
   scal->lam_v = 0ull;
 }
@@ -220,22 +240,25 @@ cudaError_t launch_rhs(dg_ctx* c, const double* U, int mode, double rkA, double 
 }
 
 // reference state of the shifted primitives: zero on the FP64 path; on the
-// FP32-bulk path the values at the first node of element 0
-__global__ void k_refs(const double* __restrict__ U, int n3, double gm1, double Rinv, int use, DevScalars* s) {
+// FP32-bulk path the density and pressure at the first node of element 0,
+// at rest
+__global__ void k_refs(const double* __restrict__ U, int n3, double gm1, double R, int use, DevScalars* s) {
   if (!use) {
-    s->ref_p = s->ref_H = s->ref_T = 0.0;
+    s->ref_p = s->ref_H = s->ref_T = s->ref_rho = s->ref_E = 0.0;
     return;
   }
-  const double r = U[0], ri = 1.0 / r;
+  const double r = U[0];
   const double mu = U[n3], mv = U[2 * n3], mw = U[3 * n3], E = U[4 * n3];
-  const double p = gm1 * (E - 0.5 * (mu * mu + mv * mv + mw * mw) * ri);
+  const double p = gm1 * (E - 0.5 * (mu * mu + mv * mv + mw * mw) / r);
+  s->ref_rho = r;
   s->ref_p = p;
-  s->ref_H = (E + p) * ri;
-  s->ref_T = p * ri * Rinv;
+  s->ref_E = p / gm1;
+  s->ref_H = (s->ref_E + p) / r;
+  s->ref_T = p / (r * R);
 }
 
 cudaError_t launch_refs(dg_ctx* c) {
-  k_refs<<<1, 1, 0, c->stream>>>(c->U, c->n3, c->prm.gamma - 1.0, 1.0 / c->prm.R,
+  k_refs<<<1, 1, 0, c->stream>>>(c->U, c->n3, c->prm.gamma - 1.0, c->prm.R,
                                  c->prm.precision == DG_FP32_BULK ? 1 : 0, c->scal);
   count_launch();
   return cudaGetLastError();
@@ -248,14 +271,23 @@ static int cfl_blocks(dg_ctx* c) {
   return (int)std::min<int64_t>(need, (int64_t)sms * 8);
 }
 
-cudaError_t launch_cfl(dg_ctx* c) {
+cudaError_t launch_cfl(dg_ctx* c, bool report_only) {
   const double kv = std::max(4.0 / 3.0, c->prm.gamma / c->prm.Pr) * c->prm.mu;
   const int nb = cfl_blocks(c);
   prof_begin(c, PK_CFL);
-  DG_DISPATCH(c->N, (k_cfl<NN><<<nb, 256, 0, c->stream>>>((int)c->E, c->U, c->metric, c->cflgeo, c->prm.gamma,
-                                                          c->prm.gamma - 1.0, 1.0 / c->prm.R, kv, c->prm.viscous,
-                                                          c->scal)));
-  k_dt<<<1, 1, 0, c->stream>>>(c->scal, c->prm.cfl, c->prm.dfl, c->N, c->prm.viscous);
+  if (c->prm.precision == DG_FP32_BULK) {
+    DG_DISPATCH(c->N, (k_cfl<NN, float><<<nb, 256, 0, c->stream>>>((int)c->E, c->U, c->metric, c->metric32, c->cflgeo,
+                                                                 c->prm.gamma, c->prm.gamma - 1.0, 1.0 / c->prm.R, kv,
+                                                                 c->prm.viscous, c->scal)));
+  } else {
+    DG_DISPATCH(c->N, (k_cfl<NN, double><<<nb, 256, 0, c->stream>>>((int)c->E, c->U, c->metric, c->metric32,
+                                                                  c->cflgeo, c->prm.gamma, c->prm.gamma - 1.0,
+                                                                  1.0 / c->prm.R, kv, c->prm.viscous, c->scal)));
+  }
+  if (report_only)
+    k_dt_report<<<1, 1, 0, c->stream>>>(c->scal, c->prm.cfl, c->prm.dfl, c->N, c->prm.viscous);
+  else
+    k_dt<<<1, 1, 0, c->stream>>>(c->scal, c->prm.cfl, c->prm.dfl, c->N, c->prm.viscous);
   prof_end(c);
   count_launch(2);
   return cudaGetLastError();

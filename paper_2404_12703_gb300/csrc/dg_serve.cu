@@ -33,38 +33,43 @@ namespace dg {
 // kernels
 // ---------------------------------------------------------------------------
 
-// per-case CFL reduction: one block per element, one atomic per element
-template <int N>
+// per-case CFL reduction: one block per element, one atomic per element.
+// T = float (FP32-bulk pools): the spectral radii in FP32 from the FP32
+// metrics, as for a standalone FP32-bulk context.
+template <int N, typename T>
 __global__ void __launch_bounds__(128) k_cfl_cases(int64_t E, const double* __restrict__ U,
                                                    const double* __restrict__ metric,
+                                                   const float* __restrict__ metric32,
                                                    const double* __restrict__ geo, const int* __restrict__ ecase,
                                                    double gamma, double gm1, double kvf, CaseData* cases) {
   constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
+  constexpr bool f32 = sizeof(T) == sizeof(float);
   const int64_t e = blockIdx.x;
   if (e >= E) return;
   const int c = ecase[e];
-  if (c < 0) return;  // free slot: the whole block leaves together
-  const double kv = kvf * cases[c].mu;
+  // free slot, or a case at its end time: the whole block leaves together
+  if (c < 0 || !(cases[c].t < cases[c].t_end)) return;
+  const T kv = T(kvf * cases[c].mu);
   double lc = 0.0, lv = 0.0;
   int bad = 0;
   for (int t = threadIdx.x; t < n3; t += 128) {
     const double* up = U + e * 5 * n3 + t;
-    const double r = up[0], ri = 1.0 / r;
-    const double u = up[n3] * ri, v = up[2 * n3] * ri, w = up[3 * n3] * ri;
-    const double p = gm1 * (up[4 * n3] - 0.5 * (up[n3] * u + up[2 * n3] * v + up[3 * n3] * w));
-    const double cs = sqrt(gamma * p * ri);
-    const double* Me = metric + e * 10 * n3 + t;
+    const T r = T(up[0]), ri = T(1) / r;
+    const T m0 = T(up[n3]), m1 = T(up[2 * n3]), m2 = T(up[3 * n3]);
+    const T u = m0 * ri, v = m1 * ri, w = m2 * ri;
+    const T p = T(gm1) * (T(up[4 * n3]) - T(0.5) * (m0 * u + m1 * v + m2 * w));
+    const T cs = sqrt(T(gamma) * p * ri);
+    auto M = [&](int k) { return f32 ? T(metric32[(e * 10 + k) * n3 + t]) : T(metric[(e * 10 + k) * n3 + t]); };
     const double* Gm = geo + e * 4 * n3 + t;
-    const double Ji = Me[9 * n3];
-    double aa = 0.0;
+    const T Ji = M(9);
+    T aa = T(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-      aa += fabs(u * Me[(d * 3) * n3] + v * Me[(d * 3 + 1) * n3] + w * Me[(d * 3 + 2) * n3]) + cs * Gm[d * n3];
+    for (int d = 0; d < 3; ++d) aa += fabs(u * M(d * 3) + v * M(d * 3 + 1) + w * M(d * 3 + 2)) + cs * T(Gm[d * n3]);
     aa *= Ji;
-    const double bb = kv * ri * Gm[3 * n3] * Ji * Ji;
+    const T bb = kv * ri * T(Gm[3 * n3]) * Ji * Ji;
     if (!isfinite(aa) || !isfinite(bb)) bad = 1;
-    lc = fmax(lc, aa);
-    lv = fmax(lv, bb);
+    lc = fmax(lc, double(aa));
+    lv = fmax(lv, double(bb));
   }
   __shared__ double rc[4], rv[4];
   __shared__ int rb;
@@ -131,10 +136,19 @@ __global__ void k_shift_side_e(const int2* __restrict__ src, int2* __restrict__ 
 
 template <int N>
 static void launch_cfl_cases(dg_ctx* p, double kvf, cudaStream_t st) {
-  if (p->E > 0)
-    k_cfl_cases<N><<<(unsigned)p->E, 128, 0, st>>>(p->E, p->U, p->metric, p->cflgeo, p->elem_case,
-                                                     p->prm.gamma, p->prm.gamma - 1.0, kvf, p->cases);
+  if (p->E <= 0) return;
+  if (p->prm.precision == DG_FP32_BULK)
+    k_cfl_cases<N, float><<<(unsigned)p->E, 128, 0, st>>>(p->E, p->U, p->metric, p->metric32, p->cflgeo,
+                                                            p->elem_case, p->prm.gamma, p->prm.gamma - 1.0, kvf,
+                                                            p->cases);
+  else
+    k_cfl_cases<N, double><<<(unsigned)p->E, 128, 0, st>>>(p->E, p->U, p->metric, p->metric32, p->cflgeo,
+                                                             p->elem_case, p->prm.gamma, p->prm.gamma - 1.0, kvf,
+                                                             p->cases);
 }
+
+// marks a case slot free (stream-ordered; no host buffer involved)
+__global__ void k_deactivate(CaseData* d) { d->active = 0; }
 
 // ---------------------------------------------------------------------------
 // host side
@@ -203,6 +217,8 @@ struct Request {
   int riemann = 0;
   double t_submit = 0;
   dg_ctx* prepared = nullptr;  // maps, metrics and state built by the set-up thread
+  double* out_buf = nullptr;   // pinned buffer the final state is copied to
+  size_t out_cap = 0;          // its size in doubles
 };
 
 struct Slot {
@@ -213,6 +229,18 @@ struct Slot {
   double t_submit = 0, t_admit = 0, t_end = 0;
   int64_t first_step = 0;       // index of the first batched step the case takes part in
   CaseData* staging = nullptr;  // pinned, per slot
+  double* out_buf = nullptr;    // pinned output buffer of the resident case
+  size_t out_cap = 0;
+};
+
+// a retired case whose final state is still being copied out
+struct Retiring {
+  int64_t ticket = 0;
+  double* buf = nullptr;
+  size_t cap = 0, count = 0;
+  cudaEvent_t ev = nullptr;
+  double t_submit = 0, t_admit = 0;
+  double stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 struct Result {
@@ -252,6 +280,9 @@ struct dg_server {
   cudaGraphExec_t graph = nullptr;
   bool dirty = true;
   std::vector<dg::PendingFree> frees;
+  std::vector<dg::Retiring> retiring;           // step thread only
+  std::multimap<size_t, double*> pinned_free;   // reusable output buffers (size in doubles)
+  std::vector<cudaEvent_t> events_free;         // step thread only
   double stat_steps = 0, stat_finished = 0, stat_captures = 0, stat_dofstages = 0;
   std::string worker_error;
 };
@@ -341,7 +372,34 @@ static bool prepare(dg_server* s, Request& r, std::string& err) {
     return false;
   }
   r.prepared = tmp;
+  // pinned output buffer, reused from retired cases when one is large enough
+  const size_t need = (size_t)r.E * (r.N + 1) * (r.N + 1) * (r.N + 1) * 5;
+  {
+    std::lock_guard<std::mutex> lk(s->m);
+    auto it = s->pinned_free.lower_bound(need);
+    if (it != s->pinned_free.end()) {
+      r.out_buf = it->second;
+      r.out_cap = it->first;
+      s->pinned_free.erase(it);
+    }
+  }
+  if (!r.out_buf) {
+    if (cudaMallocHost(&r.out_buf, sizeof(double) * need) != cudaSuccess) {
+      r.out_buf = nullptr;
+      err = "case set-up failed: no pinned host memory for the result";
+      dg_destroy(tmp);
+      r.prepared = nullptr;
+      return false;
+    }
+    r.out_cap = need;
+  }
   return true;
+}
+
+static void give_pinned(dg_server* s, double* buf, size_t cap) {
+  if (!buf) return;
+  std::lock_guard<std::mutex> lk(s->m);
+  s->pinned_free.emplace(cap, buf);
 }
 
 // Copies a prepared case into its pool on the step stream (step thread).
@@ -371,6 +429,7 @@ static bool admit(dg_server* s, Request& r, std::string& err) {
   };
   cp(p->U + e0 * 5 * n3, tmp->U, sizeof(double) * E * 5 * n3);
   cp(p->metric + e0 * 10 * n3, tmp->metric, sizeof(double) * E * 10 * n3);
+  cp(p->metric32 + e0 * 10 * n3, tmp->metric32, sizeof(float) * E * 10 * n3);
   cp(p->cflgeo + e0 * 4 * n3, tmp->cflgeo, sizeof(double) * E * 4 * n3);
   cp(p->fvmetric + e0 * 3 * (p->n - 1) * 3 * n2, tmp->fvmetric, sizeof(double) * E * 3 * (p->n - 1) * 3 * n2);
   cp(p->nrm + s0 * 4 * n2, tmp->nrm, sizeof(double) * S * 4 * n2);
@@ -398,12 +457,16 @@ static bool admit(dg_server* s, Request& r, std::string& err) {
   d.active = 1;
   d.N = r.N;
   if (s->prm.precision == DG_FP32_BULK) {
+    // the density and pressure of the case's first node, at rest (as for a
+    // standalone FP32-bulk context)
     const double* u0 = r.U0.data();
-    const double rho = u0[0], ri = 1.0 / rho;
-    const double pp = (s->prm.gamma - 1.0) * (u0[4] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2] + u0[3] * u0[3]) * ri);
+    const double gm1 = s->prm.gamma - 1.0, rho = u0[0];
+    const double pp = gm1 * (u0[4] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2] + u0[3] * u0[3]) / rho);
+    d.ref_rho = rho;
     d.ref_p = pp;
-    d.ref_H = (u0[4] + pp) * ri;
-    d.ref_T = pp * ri / s->prm.R;
+    d.ref_E = pp / gm1;
+    d.ref_H = (d.ref_E + pp) / rho;
+    d.ref_T = pp / (rho * s->prm.R);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_cases + slot, &d, sizeof(CaseData), cudaMemcpyHostToDevice, q);
   cudaEvent_t ev = nullptr;
@@ -431,6 +494,9 @@ static bool admit(dg_server* s, Request& r, std::string& err) {
   sl.t_admit = now_s();
   sl.t_end = r.t_end;
   sl.first_step = s->launched;
+  sl.out_buf = r.out_buf;
+  sl.out_cap = r.out_cap;
+  r.out_buf = nullptr;
   const int64_t hiE = P.elems.high(), hiS = P.sides.high();
   if (hiE != p->E || hiS != p->S) {
     p->E = hiE;
@@ -463,41 +529,47 @@ static void reap_frees(dg_server* s, bool wait) {
   }
 }
 
-// copies the case's state out (public layout), frees its slot and ranges
-static void retire(dg_server* s, int slot, const CaseData& rec, Result& res) {
+// Starts copying the case's state out (public layout, into its pinned output
+// buffer) and frees its slot and ranges at once: later work on them is
+// ordered after the copy on the step stream.  The result is published by
+// finish_retired once the copy has completed.
+static void retire(dg_server* s, int slot, const CaseData& rec) {
   Slot& sl = s->slots[slot];
   Pool& P = s->pools[sl.N];
   dg_ctx* p = P.ctx;
   const int n3 = p->n3;
   cudaStream_t q = s->stream;
-  // public layout into the pool's conversion buffer, then to the host
   dg_ctx view = {};
   view.E = sl.E;
   view.n3 = n3;
   view.stream = q;
   launch_to_public(&view, p->U + sl.e0 * 5 * n3, p->Upub + sl.e0 * 5 * n3);
-  res.U.resize((size_t)sl.E * n3 * 5);
-  cudaMemcpyAsync(res.U.data(), p->Upub + sl.e0 * 5 * n3, sizeof(double) * res.U.size(), cudaMemcpyDeviceToHost, q);
+  Retiring r;
+  r.ticket = sl.ticket;
+  r.buf = sl.out_buf;
+  r.cap = sl.out_cap;
+  r.count = (size_t)sl.E * n3 * 5;
+  cudaMemcpyAsync(r.buf, p->Upub + sl.e0 * 5 * n3, sizeof(double) * r.count, cudaMemcpyDeviceToHost, q);
   k_fill_int<<<(unsigned)((sl.E + 255) / 256), 256, 0, q>>>(p->elem_case + sl.e0, sl.E, -1);
   k_fill_int<<<(unsigned)((sl.S + 255) / 256), 256, 0, q>>>(p->side_case + sl.s0, sl.S, -1);
-  CaseData& d = *sl.staging;
-  d = rec;
-  const double t_final = d.t;
-  const double steps = d.steps;
-  const int nonfinite = d.nonfinite;
-  d.active = 0;
-  cudaMemcpyAsync(s->d_cases + slot, &d, sizeof(CaseData), cudaMemcpyHostToDevice, q);
-  count_launch(3);
-  cudaStreamSynchronize(q);
-  const double t_done = now_s();
-  res.stats[0] = t_done - sl.t_submit;
-  res.stats[1] = sl.t_admit - sl.t_submit;
-  res.stats[2] = t_done - sl.t_admit;
-  res.stats[3] = t_final;
-  res.stats[4] = steps;
-  res.stats[5] = (double)sl.E;
-  res.stats[6] = sl.N;
-  res.stats[7] = nonfinite ? 1.0 : 0.0;
+  k_deactivate<<<1, 1, 0, q>>>(s->d_cases + slot);
+  count_launch(4);
+  if (s->events_free.empty()) {
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    s->events_free.push_back(ev);
+  }
+  r.ev = s->events_free.back();
+  s->events_free.pop_back();
+  cudaEventRecord(r.ev, q);
+  r.t_submit = sl.t_submit;
+  r.t_admit = sl.t_admit;
+  r.stats[3] = rec.t;
+  r.stats[4] = rec.steps;
+  r.stats[5] = (double)sl.E;
+  r.stats[6] = sl.N;
+  r.stats[7] = rec.nonfinite ? 1.0 : 0.0;
+  s->retiring.push_back(r);
   P.elems.give(sl.e0, sl.E);
   P.sides.give(sl.s0, sl.S);
   const int64_t hiE = P.elems.high(), hiS = P.sides.high();
@@ -508,6 +580,35 @@ static void retire(dg_server* s, int slot, const CaseData& rec, Result& res) {
   }
   sl.used = false;
   sl.ticket = -1;
+  sl.out_buf = nullptr;
+}
+
+// Publishes the results whose copies have completed (all of them with wait).
+static void finish_retired(dg_server* s, bool wait) {
+  for (size_t i = 0; i < s->retiring.size();) {
+    Retiring& r = s->retiring[i];
+    if (!wait && cudaEventQuery(r.ev) != cudaSuccess) {
+      ++i;
+      continue;
+    }
+    cudaEventSynchronize(r.ev);
+    const double t_done = now_s();
+    Result res;
+    res.U.assign(r.buf, r.buf + r.count);
+    memcpy(res.stats, r.stats, sizeof(res.stats));
+    res.stats[0] = t_done - r.t_submit;
+    res.stats[1] = r.t_admit - r.t_submit;
+    res.stats[2] = t_done - r.t_admit;
+    s->events_free.push_back(r.ev);
+    give_pinned(s, r.buf, r.cap);
+    {
+      std::lock_guard<std::mutex> lk(s->m);
+      s->results[r.ticket] = std::move(res);
+      s->running.erase(r.ticket);
+      s->stat_finished += 1;
+    }
+    s->retiring.erase(s->retiring.begin() + i);
+  }
 }
 
 // Step loop.  Keeps one batched step queued behind the one it inspects: after
@@ -524,7 +625,14 @@ static void worker_loop(dg_server* s) {
     {
       std::unique_lock<std::mutex> lk(s->m);
       if (s->stop) break;
-      if (s->running.empty() && s->ready.empty() && !inflight) {
+      bool resident = false;
+      for (auto& sl : s->slots) resident = resident || sl.used;
+      if (!resident && s->ready.empty() && !inflight) {
+        if (!s->retiring.empty()) {
+          lk.unlock();
+          finish_retired(s, true);
+          continue;
+        }
         s->cv.wait_for(lk, std::chrono::milliseconds(5));
         if (s->stop) break;
       }
@@ -543,6 +651,8 @@ static void worker_loop(dg_server* s) {
           if (s->slots[i].used && s->slots[i].ticket == r.ticket) s->running[r.ticket] = i;
         s->admitting.erase(r.ticket);
       } else if (!err.empty()) {
+        give_pinned(s, r.out_buf, r.out_cap);
+        r.out_buf = nullptr;
         Result res;
         res.stats[7] = 2.0;
         std::lock_guard<std::mutex> lk(s->m);
@@ -610,18 +720,12 @@ static void worker_loop(dg_server* s) {
         std::lock_guard<std::mutex> lk(s->m);
         s->stat_dofstages += 5.0 * (double)sl.E * (sl.N + 1) * (sl.N + 1) * (sl.N + 1);
       }
-      if (d.t >= sl.t_end || d.nonfinite) {
-        Result res;
-        const int64_t ticket = sl.ticket;
-        retire(s, i, d, res);
-        std::lock_guard<std::mutex> lk(s->m);
-        s->results[ticket] = std::move(res);
-        s->running.erase(ticket);
-        s->stat_finished += 1;
-      }
+      if (d.t >= sl.t_end || d.nonfinite) retire(s, i, d);
     }
+    finish_retired(s, false);
   }
   cudaStreamSynchronize(s->stream);
+  finish_retired(s, true);
 }
 
 // Set-up thread: takes queued cases in arrival order and prepares up to
@@ -691,9 +795,17 @@ void dg_server_destroy(dg_server* s) {
   s->cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
   if (s->preparer.joinable()) s->preparer.join();
-  for (auto& r : s->ready)
+  for (auto& r : s->ready) {
     if (r.prepared) dg_destroy(r.prepared);
+    if (r.out_buf) cudaFreeHost(r.out_buf);
+  }
   s->ready.clear();
+  for (auto& sl : s->slots)
+    if (sl.out_buf) cudaFreeHost(sl.out_buf);
+  for (auto& kv : s->pinned_free) cudaFreeHost(kv.second);
+  s->pinned_free.clear();
+  for (auto ev : s->events_free) cudaEventDestroy(ev);
+  s->events_free.clear();
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
   reap_frees(s, true);

@@ -42,6 +42,12 @@ struct Shape {
   static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   static constexpr int EPB = n3 >= 256 ? 1 : 256 / n3;  // elements per block
   static constexpr int THREADS = EPB * n3;
+  // FP32-bulk volume kernel: at least 1024 resident threads per SM (it is
+  // latency-bound); the FP64 one is bound by the FP64 pipe at one block
+  template <typename T>
+  static constexpr int vol_min_blocks() {
+    return sizeof(T) == sizeof(float) && THREADS <= 512 ? 1024 / THREADS : 1;
+  }
 };
 
 // buffers of the arithmetic type T
@@ -68,33 +74,67 @@ struct SPrim {
   T rho, u, v, w, p, H, Tt;  // p, H, Tt shifted by the context's references
 };
 
-// Parameters that may differ between the cases of a serving pool
+// Parameters that may differ between the cases of a serving pool.  The
+// reference state (zero on the FP64 path) is a state at rest: rr, pr, its
+// total energy Er = pr / (gamma - 1), enthalpy Hr = (Er + pr) / rr and
+// temperature Tr = pr / (rr R).
 struct CaseParams {
-  double mu, lam, pr, Hr, Tr;
+  double mu, lam, pr, Hr, Tr, rr, Er;
   int riemann;
 };
 __device__ __forceinline__ CaseParams case_params(const StageArgs& a, int c) {
   if (a.cases) {
     const CaseData& d = a.cases[c < 0 ? 0 : c];
-    return {d.mu, d.lam, d.ref_p, d.ref_H, d.ref_T, d.riemann};
+    return {d.mu, d.lam, d.ref_p, d.ref_H, d.ref_T, d.ref_rho, d.ref_E, d.riemann};
   }
-  return {a.mu, a.lam, a.scal->ref_p, a.scal->ref_H, a.scal->ref_T, a.riemann};
+  const DevScalars* s = a.scal;
+  return {a.mu, a.lam, s->ref_p, s->ref_H, s->ref_T, s->ref_rho, s->ref_E, a.riemann};
 }
 __device__ __forceinline__ double case_dt(const StageArgs& a, int c) {
   return a.cases ? a.cases[c < 0 ? 0 : c].dt : a.scal->dt;
 }
 
-// ConsToPrim (Eqs. eos_p, eos_T) in FP64, then shifted and rounded to T
+// ConsToPrim (Eqs. eos_p, eos_T) in FP64; the FP64 path has a zero reference
 template <typename T>
-__device__ __forceinline__ SPrim<T> shifted_prim(const double U[5], double gm1, double Rinv, double pr, double Hr,
-                                                double Tr, double* p_full = nullptr) {
+__device__ __forceinline__ SPrim<T> shifted_prim(const double U[5], double gm1, double Rinv, const CaseParams& cp,
+                                                double* p_full = nullptr) {
   const double ri = 1.0 / U[0];
   const double u = U[1] * ri, v = U[2] * ri, w = U[3] * ri;
   const double p = gm1 * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
   const double H = (U[4] + p) * ri;
   const double Tm = p * ri * Rinv;
   if (p_full) *p_full = p;
-  return {T(U[0]), T(u), T(v), T(w), T(p - pr), T(H - Hr), T(Tm - Tr)};
+  return {T(U[0]), T(u), T(v), T(w), T(p - cp.pr), T(H - cp.Hr), T(Tm - cp.Tr)};
+}
+
+// FP32-bulk: the shifted primitives from the two deviations that cancel,
+// d_rho = rho - rr and d_E = rho e - Er, taken in FP64; the rest in FP32.
+// With Er = pr / (gamma - 1) and Hr = (Er + pr) / rr, exactly
+//   p' = (gamma - 1)(d_E - |m|^2 / (2 rho)),
+//   H' = (d_E + p' - Hr d_rho) / rho,
+//   T' = (p' - (pr / rr) d_rho) / (rho R).
+template <>
+__device__ __forceinline__ SPrim<float> shifted_prim<float>(const double U[5], double gm1, double Rinv,
+                                                            const CaseParams& cp, double* p_full) {
+  const float drho = float(U[0] - cp.rr), dE = float(U[4] - cp.Er);
+  const float rho = float(U[0]), m0 = float(U[1]), m1 = float(U[2]), m2 = float(U[3]);
+  const float ri = 1.0f / rho;
+  const float u = m0 * ri, v = m1 * ri, w = m2 * ri;
+  const float pp = float(gm1) * (dE - 0.5f * (m0 * u + m1 * v + m2 * w));
+  const float Hp = (dE + pp - float(cp.Hr) * drho) * ri;
+  const float Tp = (pp - float(cp.rr > 0 ? cp.pr / cp.rr : 0.0) * drho) * ri * float(Rinv);
+  if (p_full) *p_full = cp.pr + double(pp);
+  return {rho, u, v, w, pp, Hp, Tp};
+}
+
+// metric component c (0..8: J a^d_x at 3d + x; 9: 1/J) of node t of element e
+template <typename T>
+__device__ __forceinline__ T metric_at(const StageArgs& a, size_t e, int c, int t, int n3) {
+  return T(a.metric[(e * 10 + c) * n3 + t]);
+}
+template <>
+__device__ __forceinline__ float metric_at<float>(const StageArgs& a, size_t e, int c, int t, int n3) {
+  return a.metric32[(e * 10 + c) * n3 + t];
 }
 
 // Euler flux contracted with nv, energy component minus H_ref times mass flux
@@ -194,8 +234,8 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
 #pragma unroll
   for (int k = 0; k < 5; ++k) { UM[k] = uM[k * n3]; US[k] = uS[k * n3]; }
-  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp.pr, cp.Hr, cp.Tr);
-  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp.pr, cp.Hr, cp.Tr);
+  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
+  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
   const T qa[4] = {T(0.5) * (qM.u + qS.u), T(0.5) * (qM.v + qS.v), T(0.5) * (qM.w + qS.w), T(0.5) * (qM.Tt + qS.Tt)};
   const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
   const T sn[3] = {T(nr[0]), T(nr[n2]), T(nr[2 * n2])};
@@ -234,13 +274,12 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
   for (int k = threadIdx.x; k < n2; k += blockDim.x) sDh[k] = T(a.ops->Dhat[k]);
   T* q = sq + le * 4 * n3;
   T* F = sF + le * 12 * n3;
-  const double* Me = a.metric + (size_t)e * 10 * n3;
   {
     double U[5];
     const double* u = a.U + (size_t)e * 5 * n3 + t;
 #pragma unroll
     for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
-    const SPrim<T> pr = shifted_prim<T>(U, a.gm1, a.Rinv, cp.pr, cp.Hr, cp.Tr);
+    const SPrim<T> pr = shifted_prim<T>(U, a.gm1, a.Rinv, cp);
     q[t] = pr.u;
     q[n3 + t] = pr.v;
     q[2 * n3 + t] = pr.w;
@@ -256,7 +295,8 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
     {
-      const T J0 = T(Me[(d * 3 + 0) * n3 + t]), J1 = T(Me[(d * 3 + 1) * n3 + t]), J2 = T(Me[(d * 3 + 2) * n3 + t]);
+      const T J0 = metric_at<T>(a, e, d * 3 + 0, t, n3), J1 = metric_at<T>(a, e, d * 3 + 1, t, n3),
+              J2 = metric_at<T>(a, e, d * 3 + 2, t, n3);
 #pragma unroll
       for (int qv = 0; qv < 4; ++qv) {
         const T qq = q[qv * n3 + t];
@@ -299,7 +339,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] += sg * L[k * n2];
   }
-  const T Ji = T(Me[9 * n3 + t]);
+  const T Ji = metric_at<T>(a, e, 9, t, n3);
   T* g = TBuf<T>::g(a) + (size_t)e * 12 * n3 + t;
 #pragma unroll
   for (int k = 0; k < 12; ++k) g[k * n3] = acc[k] * Ji;
@@ -319,7 +359,6 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   const int cs = a.side_case ? a.side_case[s] : 0;
   if (cs < 0) return;  // free side slot of a serving pool
   const CaseParams cp = case_params(a, cs);
-  const double pr = cp.pr, Hr = cp.Hr, Tr = cp.Tr;
   const int2 ee = a.side_e[s];
   const int sf = a.side_f[s];
   const int fM = sf & 15, fS = (sf >> 4) & 15, flip = sf >> 8;
@@ -331,8 +370,8 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
 #pragma unroll
   for (int k = 0; k < 5; ++k) { UM[k] = uM[k * n3]; US[k] = uS[k * n3]; }
-  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, pr, Hr, Tr);
-  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, pr, Hr, Tr);
+  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
+  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
   const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
   const T sn[3] = {T(nr[0]), T(nr[n2]), T(nr[2 * n2])};
   const double sAd = nr[3 * n2];
@@ -340,8 +379,8 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   const T sA = T(sAd);
   const T nu[3] = {T(nr[0] * invd), T(nr[n2] * invd), T(nr[2 * n2] * invd)};
   T f[5];
-  if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, T(a.gm1), T(Hr), f);
-  else lf_flux_s(qM, qS, nu, T(a.gamma), T(pr), f);
+  if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, T(a.gm1), T(cp.Hr), f);
+  else lf_flux_s(qM, qS, nu, T(a.gamma), T(cp.pr), f);
 #pragma unroll
   for (int k = 0; k < 5; ++k) f[k] *= sA;
   if (a.viscous) {
@@ -447,7 +486,7 @@ struct VolumeSmem {
 // Volume integral + SurfInt + ApplyJac (+ RK update)
 // ---------------------------------------------------------------------------
 template <int N, int MODE, typename T>
-__global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
+__global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_blocks<T>()) k_volume(StageArgs a) {
   using S = Shape<N>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -479,8 +518,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
   T* Jm = sJ + le * 9 * n3;
   T* G = sG + le * 5 * n3;
   T* A = sA + le * 15 * n3;
-  const double* Me = a.metric + (size_t)e * 10 * n3;
-  const double pr_ref = cp.pr, H_ref = cp.Hr, T_ref = cp.Tr;
+  const double pr_ref = cp.pr, H_ref = cp.Hr;
   double U[5];
   double p_full;
   SPrim<T> me;
@@ -489,7 +527,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
     const double* u = a.U + (size_t)e * 5 * n3 + t;
 #pragma unroll
     for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
-    me = shifted_prim<T>(U, a.gm1, a.Rinv, pr_ref, H_ref, T_ref, &p_full);
+    me = shifted_prim<T>(U, a.gm1, a.Rinv, cp, &p_full);
     // halved values: every arithmetic mean of the two-point flux is then one
     // addition, bit-identical to (a + b) / 2
     P[t] = T(0.5) * me.rho;
@@ -499,7 +537,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
     P[4 * n3 + t] = T(0.5) * me.p;
     P[5 * n3 + t] = T(0.5) * me.H;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) Jm[c * n3 + t] = T(0.5) * T(Me[c * n3 + t]);
+    for (int c = 0; c < 9; ++c) Jm[c * n3 + t] = T(0.5) * metric_at<T>(a, e, c, t, n3);
     if (a.viscous) {
       const T* pg = TBuf<T>::g(a) + (size_t)e * 12 * n3 + t;
 #pragma unroll
@@ -678,7 +716,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
         const double* ur = a.U + (size_t)e * 5 * n3 + nb;
 #pragma unroll
         for (int k = 0; k < 5; ++k) UR[k] = ur[k * n3];
-        const SPrim<T> qR = shifted_prim<T>(UR, a.gm1, a.Rinv, pr_ref, H_ref, T_ref);
+        const SPrim<T> qR = shifted_prim<T>(UR, a.gm1, a.Rinv, cp);
         T fb[5];
         lf_flux_s(me, qR, nu, T(a.gamma), T(pr_ref), fb);
         if (right) {
@@ -727,7 +765,8 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume(StageArgs a) {
     for (int k = 0; k < 5; ++k) acc[k] += sg * Fs[k * n2];
   }
   // ---- ApplyJac; the energy equation gets H_ref times the mass equation back ----
-  const double Ji = Me[9 * n3 + t];
+  // (FP32-bulk: 1/J rounded to FP32 scales all five components alike)
+  const double Ji = metric_at<T>(a, e, 9, t, n3);
   double Ut[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) Ut[k] = -(double)(accC[k] + acc[k]) * Ji;
@@ -758,6 +797,7 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.S = (int)c->S;
   a.U = U;
   a.metric = c->metric;
+  a.metric32 = c->metric32;
   a.nrm = c->nrm;
   a.elem_side = c->elem_side;
   a.side_e = c->side_e;

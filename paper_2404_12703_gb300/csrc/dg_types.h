@@ -35,6 +35,10 @@ struct DevScalars {
   int pad[2];
   double kin[4];             // kinetic-energy reductions
   double ref_p, ref_H, ref_T;  // reference state of the shifted primitives (0 in FP64)
+  double t_end;              // > 0: CFL steps are clipped to end on t_end
+  long long steps;           // steps taken with dt > 0
+  double dt_cfl;             // CFL time step of the current state (dg_time_step)
+  double ref_rho, ref_E;     // reference density and total energy (state at rest)
 };
 
 // Per-case data of a serving pool (device, one entry per case slot).
@@ -42,6 +46,7 @@ struct CaseData {
   double dt, t, t_end;
   double mu, lam;              // viscosity and heat conductivity (0: Euler)
   double ref_p, ref_H, ref_T;  // reference state of the shifted primitives
+  double ref_rho, ref_E;
   double cfl, dfl;
   unsigned long long lam_c, lam_v;  // CFL reductions (bits of positive doubles)
   int riemann;
@@ -57,6 +62,7 @@ struct StageArgs {
   int E, S;
   const double* U;       // [E][5][n3] internal state
   const double* metric;  // [E][10][n3]: J a^d_c at d*3+c, then 1/J
+  const float* metric32;  // the same, rounded to FP32 (FP32-bulk)
   const double* nrm;     // [S][4][n2]: s n (3), s
   const int* elem_side;  // [E][6]
   const int2* side_e;    // [S] (eM, eS)
@@ -102,6 +108,7 @@ struct dg_ctx {
   double* Ut = nullptr;      // [E][5][n3] scratch for dg_rhs
   double* Upub = nullptr;    // [E][n3][5] scratch for layout conversion
   double* metric = nullptr;  // [E][10][n3]
+  float* metric32 = nullptr;  // [E][10][n3] rounded to FP32 (FP32-bulk)
   double* g = nullptr;       // [E][12][n3]
   double* nrm = nullptr;     // [S][4][n2]
   double* lflux = nullptr;   // [S][12][n2]

@@ -29,7 +29,7 @@ DEBUG_METRICS, DEBUG_MAPS, DEBUG_GRAD, DEBUG_FSTAR, DEBUG_ALPHA = 0, 1, 2, 3, 4
 SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "dg_poll", "dg_server_stats",
                  "dg_server_destroy")
 EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
-           "dg_get_state", "dg_rhs", "dg_step", "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
+           "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
            "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
 
 
@@ -82,6 +82,7 @@ def load(path: str | None = None):
             "dg_get_state": (C.c_int, [vp, vp, C.c_int, dp]),
             "dg_rhs": (C.c_int, [vp, vp, vp]),
             "dg_step": (C.c_int, [vp, C.c_int, C.c_double]),
+            "dg_advance": (C.c_int, [vp, C.c_double, C.c_int64, dp, C.POINTER(C.c_int64)]),
             "dg_profile_step": (C.c_int, [vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int64)]),
             "dg_time_step": (C.c_int, [vp, dp]),
             "dg_kinetic": (C.c_int, [vp, dp]),
@@ -245,6 +246,14 @@ class Solver:
 
     def step(self, n_steps=1, dt=0.0):
         _check(self._lib.dg_step(self._h, int(n_steps), float(dt)))
+
+    def advance(self, t_end, max_steps=1 << 62):
+        """CFL steps to exactly t_end (the last one clipped on the device);
+        returns (time reached, steps taken)."""
+        t = C.c_double()
+        k = C.c_int64()
+        _check(self._lib.dg_advance(self._h, float(t_end), int(max_steps), C.byref(t), C.byref(k)))
+        return t.value, k.value
 
     #: kernel kinds reported by profile_step, in the library's order
     KERNELS = ("cfl", "surf_prims", "lift", "surf_flux", "volume")

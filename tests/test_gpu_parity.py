@@ -142,6 +142,59 @@ def test_ten_steps_parity():
     assert rel_err(U2, Uq).max() <= 1e-12
 
 
+def test_time_step_reports_without_stepping():
+    """dg_time_step reports the CFL step of the current state and changes
+    nothing, also after fixed-dt steps."""
+    torch, dg = gpu_or_skip()
+    N = 3
+    m = W.box_mesh(N, (4, 4, 4))
+    s = _solver(dg, m)
+    U0 = W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5)
+    s.set_state(U0)
+    prm = oracle_params(s.params)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    dt1 = s.time_step()
+    assert s.time_step() == dt1
+    assert abs(dt1 - M.dt(U0, prm)[0]) <= 1e-14 * dt1
+    s.step(1, dt=dt1 / 3)
+    U1, t1 = s.get_state()
+    assert t1 == dt1 / 3
+    dt2 = s.time_step()
+    assert abs(dt2 - M.dt(U1, prm)[0]) <= 1e-14 * dt2
+    assert s.get_state()[1] == t1
+
+
+def test_advance_equals_stepping_to_the_end_time():
+    """dg_advance: CFL steps with the last one clipped on the device, bitwise
+    the same as stepping from the host with the reported CFL steps."""
+    torch, dg = gpu_or_skip()
+    N = 3
+    m = W.box_mesh(N, (4, 4, 4), curved=0.1)
+    U0 = W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5)
+    t_end = 0.037
+    a = _solver(dg, m)
+    a.set_state(U0)
+    ta, ka = a.advance(t_end)
+    Ua, _ = a.get_state()
+    assert ta == t_end and ka >= 3
+    b = _solver(dg, m)
+    b.set_state(U0)
+    t, k = 0.0, 0
+    while t < t_end:
+        dt = min(b.time_step(), t_end - t)
+        b.step(1, dt=dt)
+        t = b.get_state()[1] if dt < t_end - t else t_end
+        k += 1
+    Ub, _ = b.get_state()
+    assert k == ka
+    np.testing.assert_array_equal(Ua, Ub)
+    # advancing again to the same time does nothing; a cap on the steps stops early
+    assert a.advance(t_end) == (t_end, 0)
+    a.set_state(U0)
+    t2, k2 = a.advance(t_end, max_steps=2)
+    assert k2 == 2 and t2 < t_end
+
+
 @pytest.mark.parametrize("kw", [dict(), dict(riemann="lf", viscous=0),
                                 dict(shock_capturing=1, alpha_force=0.5, riemann="lf")])
 def test_free_stream_and_conservation(kw):

@@ -68,6 +68,22 @@ def workload_desc(nel=NEL):
     }
 
 
+def max_over_ranks(x, world, device):
+    """The largest of the ranks' values (the job's time is its slowest rank)."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(units_per_step, ms_step, world):
+    """Whole-job throughput of `world` replicas, each doing units_per_step
+    per step, timed by the slowest rank."""
+    return world * units_per_step / (ms_step * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -195,10 +211,15 @@ def serving_cases(n_cases, seed=5):
 SERVING_POOLS = {3: 16 ** 3 * 6, 5: 16 ** 3 * 6, 7: 16 ** 3 * 4}
 
 
-def serve_all(dg, cases, precision, arrivals):
+# FIFO-capped policy: strict arrival order while the resident DOF stay within
+# one 16^3 N = 7 case
+SERVING_CAP_DOF = 16 ** 3 * 8 ** 3
+
+
+def serve_all(dg, cases, precision, arrivals, max_resident_dof=0):
     """Submits the cases at the given arrival times (s after the start) to one
     server; returns time-to-solution per case, makespan and server stats."""
-    srv = dg.Server(SERVING_POOLS, max_cases=64, precision=precision)
+    srv = dg.Server(SERVING_POOLS, max_cases=64, precision=precision, max_resident_dof=max_resident_dof)
     t0 = time.perf_counter()
     tickets = []
     for a, c in zip(arrivals, cases):
@@ -247,24 +268,30 @@ def serving_bench(dg, n_cases, precision):
         seq_lat.append(free_at - a)
     seq_makespan = free_at
     lat, makespan, sstats = serve_all(dg, cases, precision, arrivals)
+    lat_c, makespan_c, sstats_c = serve_all(dg, cases, precision, arrivals, SERVING_CAP_DOF)
     # closed system: every case submitted at once (capacity, not arrivals)
     _, sat_makespan, sat_stats = serve_all(dg, cases, precision, np.zeros(len(cases)))
     p = lambda v, q: float(np.percentile(np.asarray(v), q))
     return {
-        "workload": f"{len(cases)} cases (seeded PCG64(5)): n^3 meshes n in {set(SERVING_SIZES)}, N in {{3,5,7}}, "
+        "workload": f"{len(cases)} cases (seeded PCG64(5)): n^3 meshes n in {{{','.join(map(str, SERVING_SIZES))}}}, "
+                    f"N in {{3,5,7}}, "
                     f"half TGV (Re 1600, Ma 0.1), half isentropic vortex (inviscid), each to t = {SERVING_T_END}; "
                     f"Poisson arrivals at 0.9 x the one-by-one service rate ({rate:.2f}/s); shortened from "
                     f"the 200-case, t = 1 configuration",
         "precision": "FP64" if precision == dg.FP64 else "FP32-bulk",
         "p50_s": p(lat, 50), "p99_s": p(lat, 99),
         "dof_updates_per_s": sstats["dof_stage_updates"] / makespan, "makespan_s": makespan,
+        "fifo_capped": {"max_resident_dof": SERVING_CAP_DOF, "p50_s": p(lat_c, 50), "p99_s": p(lat_c, 99),
+                        "dof_updates_per_s": sstats_c["dof_stage_updates"] / makespan_c, "makespan_s": makespan_c},
         "one_by_one": {"p50_s": p(seq_lat, 50), "p99_s": p(seq_lat, 99),
                        "dof_updates_per_s": seq_dofstage / seq_makespan, "makespan_s": seq_makespan,
                        "mean_service_s": mean_service,
                        "busy_dof_updates_per_s": seq_dofstage / sum(service)},
         "all_at_once": {"makespan_s": sat_makespan,
                         "dof_updates_per_s": sat_stats["dof_stage_updates"] / sat_makespan,
-                        "vs_one_by_one_busy": sum(service) / sat_makespan},
+                        "vs_one_by_one_busy": sum(service) / sat_makespan,
+                        "step_device_s": sat_stats["step_device_s"],
+                        "host_s": {k: sat_stats[k] for k in ("capture_host_s", "setup_host_s", "insert_host_s")}},
         "batched_steps": sstats["steps"], "graph_captures": sstats["captures"],
     }
 
@@ -439,12 +466,9 @@ def run_ours(args):
         barrier()
     launches = dg.launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, "cuda")
     ms_step = ms / args.steps
-    value = world * dof * STAGES / (ms_step * 1e-3)
+    value = replicas_value(dof * STAGES, ms_step, world)
     Ufinal, tfinal = solver.get_state()
     finite = bool(np.isfinite(Ufinal).all())
 
@@ -510,10 +534,7 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         ms32 = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            t = torch.tensor([ms32], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms32 = float(t.item())
+        ms32 = max_over_ranks(ms32, world, "cuda")
         prof32 = s32.profile_step(args.steps)
         tot32 = sum(v[0] for v in prof32.values())
         k32 = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1],

@@ -185,6 +185,12 @@ typedef struct {
   int max_cases;           /* case slots (resident cases), >= 1               */
   int64_t pool_elems[8];   /* pool capacity in elements for N = 1..7 (index N);
                               0 = that N is not served                      */
+  int64_t max_resident_dof;/* admission policy: 0 = admit every case that fits
+                              its pool (in arrival order, later cases may pass
+                              one that does not fit); > 0 = admit in strict
+                              arrival order while the resident DOF stay within
+                              this bound (a case is always admitted onto an
+                              idle server)                                  */
 } dg_server_config;
 
 typedef struct {
@@ -220,9 +226,13 @@ int dg_submit(dg_server* srv, const dg_case_desc* desc, int64_t* ticket);
    unknown ticket. */
 int dg_poll(dg_server* srv, int64_t ticket, double* U_out, double* stats);
 
-/* Server counters: out[0] batched steps launched, out[1] cases finished,
-   out[2] cases resident, out[3] cases waiting, out[4] graph captures,
-   out[5] DOF-stage updates done (sum over cases of DOF x 5 per step). */
+/* Server counters (out: 10 doubles): out[0] batched steps completed,
+   out[1] cases finished, out[2] cases resident, out[3] cases waiting,
+   out[4] graph captures, out[5] DOF-stage updates done (sum over cases of
+   DOF x 5 per step), out[6] device time of the batched steps in seconds
+   (CUDA events around each step's graph launch); host seconds spent in
+   out[7] graph captures, out[8] case set-up (set-up thread), out[9] case
+   insertion (step loop). */
 int dg_server_stats(dg_server* srv, double* out);
 
 /* Stops the worker after the current step and frees everything. */

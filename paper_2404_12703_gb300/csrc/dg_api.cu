@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "dg_common.cuh"
@@ -147,23 +148,63 @@ void lgl_weights(int N, double* w) {
   for (int i = 0; i <= N; ++i) w[i] = o.w[i];
 }
 
+// Stream-ordered allocations from a pool owned by the library (one per
+// device), which keeps freed memory for reuse: contexts created for the
+// server's cases allocate and free without the device-wide waits of
+// cudaMalloc / cudaFree.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  static std::mutex m;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(m);
+    if (!pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pools[dev], &props);
+      if (e != cudaSuccess) {
+        pools[dev] = nullptr;
+        return e;
+      }
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 template <typename T>
-static cudaError_t dalloc(T** p, size_t count, int64_t& bytes) {
-  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
-  if (e == cudaSuccess) bytes += (int64_t)(sizeof(T) * count);
+static cudaError_t dalloc(dg_ctx* c, T** p, size_t count) {
+  cudaError_t e = c->pool_stream ? pool_alloc((void**)p, sizeof(T) * count, c->pool_stream)
+                                 : cudaMalloc((void**)p, sizeof(T) * count);
+  if (e == cudaSuccess) c->bytes += (int64_t)(sizeof(T) * count);
   return e;
+}
+
+static void dfree(dg_ctx* c, void* p) {
+  if (!p) return;
+  if (c->pool_stream) cudaFreeAsync(p, c->pool_stream);
+  else cudaFree(p);
 }
 
 int alloc_side_arrays(dg_ctx* c, std::string& msg) {
   cudaError_t e = cudaSuccess;
   const int64_t S = c->S, n2 = c->n2;
-  if (e == cudaSuccess) e = dalloc(&c->nrm, S * 4 * n2, c->bytes);
-  if (e == cudaSuccess) e = dalloc(&c->lflux, S * 12 * n2, c->bytes);
-  if (e == cudaSuccess) e = dalloc(&c->fstar, S * 5 * n2, c->bytes);
-  if (e == cudaSuccess) e = dalloc(&c->lflux32, S * 12 * n2, c->bytes);
-  if (e == cudaSuccess) e = dalloc(&c->fstar32, S * 5 * n2, c->bytes);
-  if (e == cudaSuccess) e = dalloc(&c->side_e, S, c->bytes);
-  if (e == cudaSuccess) e = dalloc(&c->side_f, S, c->bytes);
+  if (e == cudaSuccess) e = dalloc(c, &c->nrm, S * 4 * n2);
+  if (e == cudaSuccess) e = dalloc(c, &c->nrm32, S * 7 * n2);
+  if (e == cudaSuccess) e = dalloc(c, &c->lflux, S * 12 * n2);
+  if (e == cudaSuccess) e = dalloc(c, &c->fstar, S * 5 * n2);
+  if (e == cudaSuccess) e = dalloc(c, &c->lflux32, S * 12 * n2);
+  if (e == cudaSuccess) e = dalloc(c, &c->fstar32, S * 5 * n2);
+  if (e == cudaSuccess) e = dalloc(c, &c->side_e, S);
+  if (e == cudaSuccess) e = dalloc(c, &c->side_f, S);
   if (e != cudaSuccess) {
     msg = std::string("side arrays: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
@@ -251,29 +292,32 @@ int64_t dg_launch_count(void) { return g_launches.load(); }
 void dg_destroy(dg_ctx* c) {
   if (!c) return;
   destroy_graph(c);
-  cudaFree(c->U);
-  cudaFree(c->dU);
-  cudaFree(c->Ut);
-  cudaFree(c->Upub);
-  cudaFree(c->metric);
-  cudaFree(c->metric32);
-  cudaFree(c->g);
-  cudaFree(c->nrm);
-  cudaFree(c->lflux);
-  cudaFree(c->fstar);
-  cudaFree(c->g32);
-  cudaFree(c->lflux32);
-  cudaFree(c->fstar32);
-  cudaFree(c->alpha);
-  cudaFree(c->fvmetric);
-  cudaFree(c->cflgeo);
-  cudaFree(c->elem_side);
-  cudaFree(c->elem_case);
-  cudaFree(c->side_case);
-  cudaFree(c->side_e);
-  cudaFree(c->side_f);
-  cudaFree(c->ops);
-  cudaFree(c->scal);
+  dfree(c, c->U);
+  dfree(c, c->dU);
+  dfree(c, c->Ut);
+  dfree(c, c->Upub);
+  dfree(c, c->metric);
+  dfree(c, c->metric32);
+  dfree(c, c->g);
+  dfree(c, c->nrm);
+  dfree(c, c->nrm32);
+  dfree(c, c->lflux);
+  dfree(c, c->fstar);
+  dfree(c, c->g32);
+  dfree(c, c->lflux32);
+  dfree(c, c->fstar32);
+  dfree(c, c->alpha);
+  dfree(c, c->fvmetric);
+  dfree(c, c->cflgeo);
+  dfree(c, c->elem_side);
+  dfree(c, c->elem_case);
+  dfree(c, c->side_case);
+  dfree(c, c->elem_list);
+  dfree(c, c->side_list);
+  dfree(c, c->side_e);
+  dfree(c, c->side_f);
+  dfree(c, c->ops);
+  dfree(c, c->scal);
   if (c->scal_host) cudaFreeHost(c->scal_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
@@ -301,29 +345,30 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
   const int64_t E = capE, S = 3 * capE, n3 = c->n3, n2 = c->n2;
   cudaError_t e = cudaSuccess;
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-  A(dalloc(&c->U, E * 5 * n3, c->bytes));
-  A(dalloc(&c->dU, E * 5 * n3, c->bytes));
-  A(dalloc(&c->Ut, E * 5 * n3, c->bytes));
-  A(dalloc(&c->Upub, E * 5 * n3, c->bytes));
-  A(dalloc(&c->metric, E * 10 * n3, c->bytes));
-  A(dalloc(&c->metric32, E * 10 * n3, c->bytes));
-  A(dalloc(&c->g, E * 12 * n3, c->bytes));
-  A(dalloc(&c->g32, E * 12 * n3, c->bytes));
-  A(dalloc(&c->alpha, E, c->bytes));
-  A(dalloc(&c->fvmetric, E * 3 * (c->n - 1) * 3 * n2, c->bytes));
-  A(dalloc(&c->cflgeo, E * 4 * n3, c->bytes));
-  A(dalloc(&c->elem_side, E * 6, c->bytes));
-  A(dalloc(&c->elem_case, E, c->bytes));
-  A(dalloc(&c->nrm, S * 4 * n2, c->bytes));
-  A(dalloc(&c->lflux, S * 12 * n2, c->bytes));
-  A(dalloc(&c->fstar, S * 5 * n2, c->bytes));
-  A(dalloc(&c->lflux32, S * 12 * n2, c->bytes));
-  A(dalloc(&c->fstar32, S * 5 * n2, c->bytes));
-  A(dalloc(&c->side_e, S, c->bytes));
-  A(dalloc(&c->side_f, S, c->bytes));
-  A(dalloc(&c->side_case, S, c->bytes));
-  A(dalloc(&c->ops, 1, c->bytes));
-  A(dalloc(&c->scal, 1, c->bytes));
+  A(dalloc(c, &c->U, E * 5 * n3));
+  A(dalloc(c, &c->dU, E * 5 * n3));
+  A(dalloc(c, &c->Ut, E * 5 * n3));
+  A(dalloc(c, &c->Upub, E * 5 * n3));
+  A(dalloc(c, &c->metric, E * 10 * n3));
+  A(dalloc(c, &c->metric32, E * 10 * n3));
+  A(dalloc(c, &c->g, E * 12 * n3));
+  A(dalloc(c, &c->g32, E * 12 * n3));
+  A(dalloc(c, &c->alpha, E));
+  A(dalloc(c, &c->fvmetric, E * 3 * (c->n - 1) * 3 * n2));
+  A(dalloc(c, &c->cflgeo, E * 4 * n3));
+  A(dalloc(c, &c->elem_side, E * 6));
+  A(dalloc(c, &c->elem_case, E));
+  A(dalloc(c, &c->nrm, S * 4 * n2));
+  A(dalloc(c, &c->nrm32, S * 7 * n2));
+  A(dalloc(c, &c->lflux, S * 12 * n2));
+  A(dalloc(c, &c->fstar, S * 5 * n2));
+  A(dalloc(c, &c->lflux32, S * 12 * n2));
+  A(dalloc(c, &c->fstar32, S * 5 * n2));
+  A(dalloc(c, &c->side_e, S));
+  A(dalloc(c, &c->side_f, S));
+  A(dalloc(c, &c->side_case, S));
+  A(dalloc(c, &c->ops, 1));
+  A(dalloc(c, &c->scal, 1));
   if (e == cudaSuccess) e = cudaMallocHost(&c->scal_host, sizeof(DevScalars));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = init_kernel_attributes(N);
@@ -343,6 +388,7 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
     A(cudaMemsetAsync(c->side_e, 0, sizeof(int2) * S, stream));
     A(cudaMemsetAsync(c->side_f, 0, sizeof(int) * S, stream));
     A(cudaMemsetAsync(c->nrm, 0, sizeof(double) * S * 4 * n2, stream));
+    A(cudaMemsetAsync(c->nrm32, 0, sizeof(float) * S * 7 * n2, stream));
     A(cudaMemsetAsync(c->elem_case, 0xff, sizeof(int) * E, stream));
     A(cudaMemsetAsync(c->side_case, 0xff, sizeof(int) * S, stream));
     A(cudaStreamSynchronize(stream));
@@ -358,11 +404,11 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
   return DG_OK;
 }
 
-}  // namespace dg
-
-extern "C" {
-
-int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params, void* stream) {
+// pool_stream non-null: a context for the server's cases, whose device
+// arrays come from the library pool in that stream's order and which has no
+// pinned mirror or capture stream (it is only built, loaded and copied from)
+int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params, cudaStream_t stream,
+                   cudaStream_t pool_stream) {
   if (!out) return fail(DG_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!mesh || !mesh->corner_vid || !mesh->xyz) return fail(DG_ERR_ARG, "mesh description incomplete");
@@ -372,7 +418,8 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params
   if (st != DG_OK) return st;
   dg_ctx* c = new dg_ctx();
   cudaGetDevice(&c->device);
-  c->stream = (cudaStream_t)stream;
+  c->stream = stream;
+  c->pool_stream = pool_stream;
   c->prm = *params;
   c->N = mesh->N;
   c->n = c->N + 1;
@@ -382,22 +429,22 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params
   const int64_t E = c->E, n3 = c->n3;
   cudaError_t e = cudaSuccess;
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-  A(dalloc(&c->U, E * 5 * n3, c->bytes));
-  A(dalloc(&c->dU, E * 5 * n3, c->bytes));
-  A(dalloc(&c->Ut, E * 5 * n3, c->bytes));
-  A(dalloc(&c->Upub, E * 5 * n3, c->bytes));
-  A(dalloc(&c->metric, E * 10 * n3, c->bytes));
-  A(dalloc(&c->metric32, E * 10 * n3, c->bytes));
-  A(dalloc(&c->g, E * 12 * n3, c->bytes));
-  A(dalloc(&c->g32, E * 12 * n3, c->bytes));
-  A(dalloc(&c->alpha, E, c->bytes));
-  A(dalloc(&c->fvmetric, E * 3 * (c->n - 1) * 3 * c->n2, c->bytes));
-  A(dalloc(&c->cflgeo, E * 4 * n3, c->bytes));
-  A(dalloc(&c->elem_side, E * 6, c->bytes));
-  A(dalloc(&c->ops, 1, c->bytes));
-  A(dalloc(&c->scal, 1, c->bytes));
-  if (e == cudaSuccess) e = cudaMallocHost(&c->scal_host, sizeof(DevScalars));
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  A(dalloc(c, &c->U, E * 5 * n3));
+  A(dalloc(c, &c->dU, E * 5 * n3));
+  A(dalloc(c, &c->Ut, E * 5 * n3));
+  A(dalloc(c, &c->Upub, E * 5 * n3));
+  A(dalloc(c, &c->metric, E * 10 * n3));
+  A(dalloc(c, &c->metric32, E * 10 * n3));
+  A(dalloc(c, &c->g, E * 12 * n3));
+  A(dalloc(c, &c->g32, E * 12 * n3));
+  A(dalloc(c, &c->alpha, E));
+  A(dalloc(c, &c->fvmetric, E * 3 * (c->n - 1) * 3 * c->n2));
+  A(dalloc(c, &c->cflgeo, E * 4 * n3));
+  A(dalloc(c, &c->elem_side, E * 6));
+  A(dalloc(c, &c->ops, 1));
+  A(dalloc(c, &c->scal, 1));
+  if (e == cudaSuccess && !pool_stream) e = cudaMallocHost(&c->scal_host, sizeof(DevScalars));
+  if (e == cudaSuccess && !pool_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     int r = cuda_fail(e, "allocation");
     dg_destroy(c);
@@ -424,6 +471,14 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params
   }
   *out = c;
   return DG_OK;
+}
+
+}  // namespace dg
+
+extern "C" {
+
+int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params, void* stream) {
+  return dg::init_mesh_impl(out, mesh, params, (cudaStream_t)stream, nullptr);
 }
 
 int dg_set_stream(dg_ctx* c, void* stream) {
@@ -479,6 +534,7 @@ int dg_set_state(dg_ctx* c, const double* U, int on_device, double t) {
 
 int dg_get_state(dg_ctx* c, double* U, int on_device, double* t) {
   if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (!c->scal_host) return fail(DG_ERR_STATE, "internal case context: no host mirror");
   const size_t bytes = sizeof(double) * c->E * 5 * c->n3;
   cudaError_t e = cudaSuccess;
   if (U) {
@@ -557,6 +613,7 @@ static cudaError_t launch_steps(dg_ctx* c, int64_t n_steps) {
 int dg_step(dg_ctx* c, int n_steps, double dt) {
   if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  if (!c->cap_stream) return fail(DG_ERR_STATE, "internal case context: no capture stream");
   if (n_steps < 0) return fail(DG_ERR_ARG, "n_steps < 0");
   if (n_steps == 0) return DG_OK;
   k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, dt > 0 ? dt : 0.0, 0, 0.0, 0);
@@ -573,6 +630,7 @@ int dg_advance(dg_ctx* c, double t_end, int64_t max_steps, double* t_out, int64_
   if (!(t_end > 0) || !std::isfinite(t_end)) return fail(DG_ERR_ARG, "t_end must be finite and > 0");
   if (max_steps < 0) return fail(DG_ERR_ARG, "max_steps < 0");
   DevScalars* h = c->scal_host;
+  if (!h) return fail(DG_ERR_STATE, "internal case context: no host mirror");
   auto read_back = [&]() {
     cudaError_t r = cudaMemcpyAsync(h, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
     if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
@@ -613,6 +671,7 @@ int dg_advance(dg_ctx* c, double t_end, int64_t max_steps, double* t_out, int64_
 int dg_profile_step(dg_ctx* c, int n_steps, double dt, double* ms, int64_t* launches) {
   if (!c || !ms || !launches) return fail(DG_ERR_ARG, "NULL argument");
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  if (!c->cap_stream) return fail(DG_ERR_STATE, "internal case context: no capture stream");
   Profiler* p = new Profiler();
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < Profiler::MAX_EV && e == cudaSuccess; ++i) {
@@ -652,6 +711,7 @@ int dg_profile_step(dg_ctx* c, int n_steps, double dt, double* ms, int64_t* laun
 int dg_time_step(dg_ctx* c, double* dt) {
   if (!c || !dt) return fail(DG_ERR_ARG, "ctx or dt is NULL");
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  if (!c->scal_host) return fail(DG_ERR_STATE, "internal case context: no host mirror");
   // the CFL reduction of a step, reported instead of taken
   cudaError_t e = launch_cfl(c, true);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->scal_host, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
@@ -665,6 +725,7 @@ int dg_time_step(dg_ctx* c, double* dt) {
 int dg_kinetic(dg_ctx* c, double* out) {
   if (!c || !out) return fail(DG_ERR_ARG, "ctx or out is NULL");
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  if (!c->scal_host) return fail(DG_ERR_STATE, "internal case context: no host mirror");
   cudaError_t e = launch_rhs(c, c->U, 0, 0.0, 0.0, 0);
   if (e == cudaSuccess) {
     k_zero_kin<<<1, 1, 0, c->stream>>>(c->scal);

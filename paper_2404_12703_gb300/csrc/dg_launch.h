@@ -24,6 +24,15 @@ void lgl_weights(int N, double* w);
 // allocation of the side arrays once the number of sides is known
 int alloc_side_arrays(dg_ctx* c, std::string& msg);
 
+// stream-ordered allocation from the library's device memory pool (dg_api.cu)
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+
+// dg_init_mesh; with pool_stream non-null the context's arrays come from the
+// library pool in that stream's order and it has no pinned mirror or capture
+// stream (the server's per-case contexts)
+int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params, cudaStream_t stream,
+                   cudaStream_t pool_stream);
+
 // serving pool of capE elements with every slot free (dg_api.cu)
 int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, cudaStream_t stream,
                     std::string& msg);

@@ -291,6 +291,22 @@ __global__ void k_cfl_geo(int E, const double* __restrict__ metric, double* __re
   G[3 * n3] = b;
 }
 
+// FP32 side geometry: s n, the unit normal and s, each rounded once
+__global__ void k_nrm32(int64_t nodes, int n2, const double* __restrict__ nrm, float* __restrict__ nrm32) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nodes) return;
+  const int64_t s = i / n2;
+  const int pq = (int)(i % n2);
+  const double* in = nrm + s * 4 * n2 + pq;
+  float* out = nrm32 + s * 7 * n2 + pq;
+  const double sA = in[3 * n2];
+  for (int k = 0; k < 3; ++k) {
+    out[k * n2] = (float)in[k * n2];
+    out[(3 + k) * n2] = (float)(in[k * n2] / sA);
+  }
+  out[6 * n2] = (float)sA;
+}
+
 // FP32 copy of an FP64 array (round to nearest)
 __global__ void k_round_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -309,6 +325,8 @@ static cudaError_t launch_metrics(dg_ctx* c, const double* d_xyz) {
                                                                        c->nrm);
   const int64_t nodes = c->E * n3;
   k_cfl_geo<N><<<(unsigned)((nodes + 255) / 256), 256, 0, c->stream>>>((int)c->E, c->metric, c->cflgeo);
+  k_nrm32<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(tot, n2, c->nrm, c->nrm32);
+  count_launch();
   const int64_t mwords = c->E * 10 * n3;
   k_round_f32<<<(unsigned)((mwords + 255) / 256), 256, 0, c->stream>>>(mwords, c->metric, c->metric32);
   count_launch(3);
@@ -331,13 +349,23 @@ int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::strin
       status = e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
     }
   };
-  ck(cudaMalloc(&d_cvid, sizeof(long long) * E * 8), "cudaMalloc cvid");
-  ck(cudaMalloc(&d_xyz, sizeof(double) * E * n3 * 3), "cudaMalloc xyz");
-  ck(cudaMalloc(&d_table, sizeof(int) * tsize), "cudaMalloc table");
-  ck(cudaMalloc(&d_partner, sizeof(int) * F), "cudaMalloc partner");
-  ck(cudaMalloc(&d_flag, sizeof(int) * F), "cudaMalloc flag");
-  ck(cudaMalloc(&d_sideof, sizeof(int) * F), "cudaMalloc sideof");
-  ck(cudaMalloc(&d_misc, sizeof(int) * 4), "cudaMalloc misc");
+  // temporaries: from the library pool for pool-stream contexts
+  auto tmp_alloc = [&](auto** p, size_t bytes, const char* what) {
+    cudaError_t e = c->pool_stream ? pool_alloc((void**)p, bytes, c->pool_stream) : cudaMalloc((void**)p, bytes);
+    ck(e, what);
+  };
+  auto tmp_free = [&](void* p) {
+    if (!p) return;
+    if (c->pool_stream) cudaFreeAsync(p, c->pool_stream);
+    else cudaFree(p);
+  };
+  tmp_alloc(&d_cvid, sizeof(long long) * E * 8, "allocating cvid");
+  tmp_alloc(&d_xyz, sizeof(double) * E * n3 * 3, "allocating xyz");
+  tmp_alloc(&d_table, sizeof(int) * tsize, "allocating table");
+  tmp_alloc(&d_partner, sizeof(int) * F, "allocating partner");
+  tmp_alloc(&d_flag, sizeof(int) * F, "allocating flag");
+  tmp_alloc(&d_sideof, sizeof(int) * F, "allocating sideof");
+  tmp_alloc(&d_misc, sizeof(int) * 4, "allocating misc");
   if (status == DG_OK) {
     ck(cudaMemcpyAsync(d_cvid, h_cvid, sizeof(long long) * E * 8, cudaMemcpyHostToDevice, c->stream), "copy cvid");
     ck(cudaMemcpyAsync(d_xyz, h_xyz, sizeof(double) * E * n3 * 3, cudaMemcpyHostToDevice, c->stream), "copy xyz");
@@ -395,13 +423,13 @@ int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::strin
       status = DG_ERR_MESH;
     }
   }
-  cudaFree(d_cvid);
-  cudaFree(d_xyz);
-  cudaFree(d_table);
-  cudaFree(d_partner);
-  cudaFree(d_flag);
-  cudaFree(d_sideof);
-  cudaFree(d_misc);
+  tmp_free(d_cvid);
+  tmp_free(d_xyz);
+  tmp_free(d_table);
+  tmp_free(d_partner);
+  tmp_free(d_flag);
+  tmp_free(d_sideof);
+  tmp_free(d_misc);
   return status;
 }
 

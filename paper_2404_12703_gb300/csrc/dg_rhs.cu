@@ -245,6 +245,7 @@ cudaError_t launch_rhs(dg_ctx* c, const double* U, int mode, double rkA, double 
 __global__ void k_refs(const double* __restrict__ U, int n3, double gm1, double R, int use, DevScalars* s) {
   if (!use) {
     s->ref_p = s->ref_H = s->ref_T = s->ref_rho = s->ref_E = 0.0;
+    s->f_ref_p = s->f_ref_H = s->f_ref_T = 0.0f;
     return;
   }
   const double r = U[0];
@@ -255,6 +256,9 @@ __global__ void k_refs(const double* __restrict__ U, int n3, double gm1, double 
   s->ref_E = p / gm1;
   s->ref_H = (s->ref_E + p) / r;
   s->ref_T = p / (r * R);
+  s->f_ref_p = (float)s->ref_p;
+  s->f_ref_H = (float)s->ref_H;
+  s->f_ref_T = (float)s->ref_T;
 }
 
 cudaError_t launch_refs(dg_ctx* c) {

@@ -37,15 +37,15 @@ namespace dg {
 // T = float (FP32-bulk pools): the spectral radii in FP32 from the FP32
 // metrics, as for a standalone FP32-bulk context.
 template <int N, typename T>
-__global__ void __launch_bounds__(128) k_cfl_cases(int64_t E, const double* __restrict__ U,
-                                                   const double* __restrict__ metric,
+__global__ void __launch_bounds__(128) k_cfl_cases(int64_t nlist, const int* __restrict__ elist,
+                                                   const double* __restrict__ U, const double* __restrict__ metric,
                                                    const float* __restrict__ metric32,
                                                    const double* __restrict__ geo, const int* __restrict__ ecase,
                                                    double gamma, double gm1, double kvf, CaseData* cases) {
   constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
   constexpr bool f32 = sizeof(T) == sizeof(float);
-  const int64_t e = blockIdx.x;
-  if (e >= E) return;
+  if (blockIdx.x >= nlist) return;
+  const int64_t e = elist[blockIdx.x];
   const int c = ecase[e];
   // free slot, or a case at its end time: the whole block leaves together
   if (c < 0 || !(cases[c].t < cases[c].t_end)) return;
@@ -136,15 +136,16 @@ __global__ void k_shift_side_e(const int2* __restrict__ src, int2* __restrict__ 
 
 template <int N>
 static void launch_cfl_cases(dg_ctx* p, double kvf, cudaStream_t st) {
-  if (p->E <= 0) return;
+  const int64_t nl = p->n_elem_list;
+  if (nl <= 0) return;
   if (p->prm.precision == DG_FP32_BULK)
-    k_cfl_cases<N, float><<<(unsigned)p->E, 128, 0, st>>>(p->E, p->U, p->metric, p->metric32, p->cflgeo,
-                                                            p->elem_case, p->prm.gamma, p->prm.gamma - 1.0, kvf,
-                                                            p->cases);
+    k_cfl_cases<N, float><<<(unsigned)nl, 128, 0, st>>>(nl, p->elem_list, p->U, p->metric, p->metric32, p->cflgeo,
+                                                          p->elem_case, p->prm.gamma, p->prm.gamma - 1.0, kvf,
+                                                          p->cases);
   else
-    k_cfl_cases<N, double><<<(unsigned)p->E, 128, 0, st>>>(p->E, p->U, p->metric, p->metric32, p->cflgeo,
-                                                             p->elem_case, p->prm.gamma, p->prm.gamma - 1.0, kvf,
-                                                             p->cases);
+    k_cfl_cases<N, double><<<(unsigned)nl, 128, 0, st>>>(nl, p->elem_list, p->U, p->metric, p->metric32, p->cflgeo,
+                                                           p->elem_case, p->prm.gamma, p->prm.gamma - 1.0, kvf,
+                                                           p->cases);
 }
 
 // marks a case slot free (stream-ordered; no host buffer involved)
@@ -205,6 +206,11 @@ struct Pool {
   int N = 0;
   dg_ctx* ctx = nullptr;
   RangeAlloc elems, sides;
+  cudaStream_t branch = nullptr;  // capture-only stream: the pool's branch of the step graph
+  cudaEvent_t fork = nullptr, join = nullptr;
+  int* h_elist[2] = {nullptr, nullptr};  // pinned staging of the occupied-element / side lists,
+  int* h_slist[2] = {nullptr, nullptr};  // alternating between rebuilds
+  int list_buf = 0;
 };
 
 struct Request {
@@ -263,7 +269,8 @@ struct dg_server {
   std::map<int, dg::Pool> pools;
   dg::CaseData* d_cases = nullptr;
   dg::CaseData* h_cases = nullptr;    // two buffers: case records after step k and k+1
-  cudaEvent_t step_ev[2] = {nullptr, nullptr};
+  cudaEvent_t step_ev[2] = {nullptr, nullptr};   // after step k's records are copied (timing)
+  cudaEvent_t step_t0[2] = {nullptr, nullptr};   // before step k's graph launch (timing)
   int64_t launched = 0;               // batched steps launched so far
   std::vector<dg::Slot> slots;
   std::thread worker;
@@ -278,12 +285,15 @@ struct dg_server {
   std::map<int64_t, int> admitting;  // tickets taken off the queue, being admitted
   int64_t next_ticket = 1;
   cudaGraphExec_t graph = nullptr;
+  std::vector<std::pair<cudaGraphExec_t, cudaEvent_t>> old_graphs;  // replaced, maybe still in flight
   bool dirty = true;
   std::vector<dg::PendingFree> frees;
+  int64_t resident_dof = 0;                     // step thread only
   std::vector<dg::Retiring> retiring;           // step thread only
   std::multimap<size_t, double*> pinned_free;   // reusable output buffers (size in doubles)
   std::vector<cudaEvent_t> events_free;         // step thread only
-  double stat_steps = 0, stat_finished = 0, stat_captures = 0, stat_dofstages = 0;
+  double stat_steps = 0, stat_finished = 0, stat_captures = 0, stat_dofstages = 0, stat_device_s = 0;
+  double stat_capture_s = 0, stat_prepare_s = 0, stat_insert_s = 0;  // host time
   std::string worker_error;
 };
 
@@ -291,52 +301,130 @@ namespace dg {
 
 static thread_local std::string g_serve_err;
 
+// Rebuilds each pool's lists of occupied elements and sides from the case
+// slots (in element order) and copies them to the device on the step stream:
+// work already queued still reads the old lists, later steps the new ones.
+// A pinned staging buffer is reused two rebuilds later, after the step loop
+// has waited for a step queued behind its copy.
+static cudaError_t rebuild_lists(dg_server* s) {
+  cudaError_t e = cudaSuccess;
+  for (auto& kv : s->pools) {
+    Pool& P = kv.second;
+    std::vector<std::pair<int64_t, int>> occ;  // (e0, slot)
+    for (int i = 0; i < (int)s->slots.size(); ++i)
+      if (s->slots[i].used && s->slots[i].N == P.N) occ.emplace_back(s->slots[i].e0, i);
+    std::sort(occ.begin(), occ.end());
+    int* he = P.h_elist[P.list_buf];
+    int* hs = P.h_slist[P.list_buf];
+    int64_t ne = 0, ns = 0;
+    for (auto& o : occ) {
+      const Slot& sl = s->slots[o.second];
+      for (int64_t k = 0; k < sl.E; ++k) he[ne++] = (int)(sl.e0 + k);
+      for (int64_t k = 0; k < sl.S; ++k) hs[ns++] = (int)(sl.s0 + k);
+    }
+    if (ne > 0 && e == cudaSuccess)
+      e = cudaMemcpyAsync(P.ctx->elem_list, he, sizeof(int) * ne, cudaMemcpyHostToDevice, s->stream);
+    if (ns > 0 && e == cudaSuccess)
+      e = cudaMemcpyAsync(P.ctx->side_list, hs, sizeof(int) * ns, cudaMemcpyHostToDevice, s->stream);
+    P.ctx->n_elem_list = ne;
+    P.ctx->n_side_list = ns;
+    P.list_buf ^= 1;
+  }
+  return e;
+}
+
 // the whole batched step for the pools' current ranges, captured once
 static cudaError_t capture_step(dg_server* s) {
-  if (s->graph) {
-    cudaGraphExecDestroy(s->graph);
-    s->graph = nullptr;
-  }
   static const double RKA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
                                 -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
   static const double RKB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
                                 1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                                 2277821191437.0 / 14882151754819.0};
   const double kvf = std::max(4.0 / 3.0, s->prm.gamma / s->prm.Pr);
+  // The graph forks into one branch per pool, so that the kernels of
+  // different pools (degrees) can run side by side:
+  //   fork -> [CFL of each pool] -> join -> per-case dt -> fork -> [5 stages of
+  //   each pool] -> join
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaError_t le = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (le == cudaSuccess) le = r; };
+  auto fork = [&]() {
+    for (auto& kv : s->pools) {
+      chk(cudaEventRecord(kv.second.fork, s->cap_stream));
+      chk(cudaStreamWaitEvent(kv.second.branch, kv.second.fork, 0));
+    }
+  };
+  auto join = [&]() {
+    for (auto& kv : s->pools) {
+      chk(cudaEventRecord(kv.second.join, kv.second.branch));
+      chk(cudaStreamWaitEvent(s->cap_stream, kv.second.join, 0));
+    }
+  };
+  fork();
   for (auto& kv : s->pools) {
     Pool& P = kv.second;
     switch (P.N) {
-      case 1: launch_cfl_cases<1>(P.ctx, kvf, s->cap_stream); break;
-      case 2: launch_cfl_cases<2>(P.ctx, kvf, s->cap_stream); break;
-      case 3: launch_cfl_cases<3>(P.ctx, kvf, s->cap_stream); break;
-      case 4: launch_cfl_cases<4>(P.ctx, kvf, s->cap_stream); break;
-      case 5: launch_cfl_cases<5>(P.ctx, kvf, s->cap_stream); break;
-      case 6: launch_cfl_cases<6>(P.ctx, kvf, s->cap_stream); break;
-      default: launch_cfl_cases<7>(P.ctx, kvf, s->cap_stream); break;
+      case 1: launch_cfl_cases<1>(P.ctx, kvf, P.branch); break;
+      case 2: launch_cfl_cases<2>(P.ctx, kvf, P.branch); break;
+      case 3: launch_cfl_cases<3>(P.ctx, kvf, P.branch); break;
+      case 4: launch_cfl_cases<4>(P.ctx, kvf, P.branch); break;
+      case 5: launch_cfl_cases<5>(P.ctx, kvf, P.branch); break;
+      case 6: launch_cfl_cases<6>(P.ctx, kvf, P.branch); break;
+      default: launch_cfl_cases<7>(P.ctx, kvf, P.branch); break;
     }
     count_launch();
   }
+  join();
   k_dt_cases<<<(s->cfg.max_cases + 127) / 128, 128, 0, s->cap_stream>>>(s->cfg.max_cases, s->d_cases);
   count_launch();
-  for (int st = 0; st < 5 && le == cudaSuccess; ++st) {
-    for (auto& kv : s->pools) {
-      Pool& P = kv.second;
-      if (P.ctx->E == 0) continue;
-      cudaStream_t keep = P.ctx->stream;
-      P.ctx->stream = s->cap_stream;
-      le = launch_rhs(P.ctx, P.ctx->U, 1, RKA[st], RKB[st], st == 0);
-      P.ctx->stream = keep;
-      if (le != cudaSuccess) break;
-    }
+  fork();
+  for (auto& kv : s->pools) {
+    Pool& P = kv.second;
+    if (P.ctx->n_elem_list == 0) continue;
+    cudaStream_t keep = P.ctx->stream;
+    P.ctx->stream = P.branch;
+    for (int st = 0; st < 5 && le == cudaSuccess; ++st) le = launch_rhs(P.ctx, P.ctx->U, 1, RKA[st], RKB[st], st == 0);
+    P.ctx->stream = keep;
   }
+  join();
   e = cudaStreamEndCapture(s->cap_stream, &g);
   if (e == cudaSuccess) e = le;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&s->graph, g, 0);
+  // Same topology (only grid sizes changed): update the executable graph in
+  // place, which affects later launches only.  Otherwise instantiate a new
+  // one; the old one is destroyed once its last launch has completed.
+  bool updated = false;
+  if (e == cudaSuccess && s->graph) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(s->graph, g, &info) == cudaSuccess) {
+      updated = true;
+    } else {
+      cudaGetLastError();
+      cudaEvent_t ev = nullptr;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+          cudaEventRecord(ev, s->stream) == cudaSuccess) {
+        s->old_graphs.push_back({s->graph, ev});
+      } else {
+        cudaStreamSynchronize(s->stream);
+        cudaGraphExecDestroy(s->graph);
+        if (ev) cudaEventDestroy(ev);
+      }
+      s->graph = nullptr;
+    }
+  }
+  if (e == cudaSuccess && !updated) e = cudaGraphInstantiate(&s->graph, g, 0);
   if (g) cudaGraphDestroy(g);
+  // executable graphs whose last launch has completed
+  for (size_t i = 0; i < s->old_graphs.size();) {
+    if (cudaEventQuery(s->old_graphs[i].second) == cudaSuccess) {
+      cudaGraphExecDestroy(s->old_graphs[i].first);
+      cudaEventDestroy(s->old_graphs[i].second);
+      s->old_graphs.erase(s->old_graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
   {
     std::lock_guard<std::mutex> lk(s->m);
     s->stat_captures += 1;
@@ -363,7 +451,7 @@ static bool prepare(dg_server* s, Request& r, std::string& err) {
   prm.riemann = r.riemann;
   dg_mesh_desc desc{r.N, r.E, r.cvid.data(), r.xyz.data()};
   dg_ctx* tmp = nullptr;
-  int st = dg_init_mesh(&tmp, &desc, &prm, s->setup_stream);
+  int st = init_mesh_impl(&tmp, &desc, &prm, s->setup_stream, s->setup_stream);
   if (st == DG_OK) st = dg_set_state(tmp, r.U0.data(), 0, 0.0);
   if (st == DG_OK && cudaStreamSynchronize(s->setup_stream) != cudaSuccess) st = DG_ERR_CUDA;
   if (st != DG_OK) {
@@ -433,6 +521,7 @@ static bool admit(dg_server* s, Request& r, std::string& err) {
   cp(p->cflgeo + e0 * 4 * n3, tmp->cflgeo, sizeof(double) * E * 4 * n3);
   cp(p->fvmetric + e0 * 3 * (p->n - 1) * 3 * n2, tmp->fvmetric, sizeof(double) * E * 3 * (p->n - 1) * 3 * n2);
   cp(p->nrm + s0 * 4 * n2, tmp->nrm, sizeof(double) * S * 4 * n2);
+  cp(p->nrm32 + s0 * 7 * n2, tmp->nrm32, sizeof(float) * S * 7 * n2);
   cp(p->side_f + s0, tmp->side_f, sizeof(int) * S);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->dU + e0 * 5 * n3, 0, sizeof(double) * E * 5 * n3, q);
   if (e == cudaSuccess) {
@@ -451,6 +540,8 @@ static bool admit(dg_server* s, Request& r, std::string& err) {
   d.t_end = r.t_end;
   d.mu = r.mu;
   d.lam = s->prm.gamma * s->prm.R * r.mu / ((s->prm.gamma - 1.0) * s->prm.Pr);
+  d.f_mu = (float)d.mu;
+  d.f_lam = (float)d.lam;
   d.cfl = r.cfl;
   d.dfl = s->prm.dfl;
   d.riemann = r.riemann;
@@ -467,6 +558,9 @@ static bool admit(dg_server* s, Request& r, std::string& err) {
     d.ref_E = pp / gm1;
     d.ref_H = (d.ref_E + pp) / rho;
     d.ref_T = pp / (rho * s->prm.R);
+    d.f_ref_p = (float)d.ref_p;
+    d.f_ref_H = (float)d.ref_H;
+    d.f_ref_T = (float)d.ref_T;
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_cases + slot, &d, sizeof(CaseData), cudaMemcpyHostToDevice, q);
   cudaEvent_t ev = nullptr;
@@ -497,12 +591,9 @@ static bool admit(dg_server* s, Request& r, std::string& err) {
   sl.out_buf = r.out_buf;
   sl.out_cap = r.out_cap;
   r.out_buf = nullptr;
-  const int64_t hiE = P.elems.high(), hiS = P.sides.high();
-  if (hiE != p->E || hiS != p->S) {
-    p->E = hiE;
-    p->S = hiS;
-    s->dirty = true;
-  }
+  p->E = P.elems.high();
+  p->S = P.sides.high();
+  s->dirty = true;  // the occupied lists change
   return true;
 }
 
@@ -572,12 +663,10 @@ static void retire(dg_server* s, int slot, const CaseData& rec) {
   s->retiring.push_back(r);
   P.elems.give(sl.e0, sl.E);
   P.sides.give(sl.s0, sl.S);
-  const int64_t hiE = P.elems.high(), hiS = P.sides.high();
-  if (hiE != p->E || hiS != p->S) {
-    p->E = hiE;
-    p->S = hiS;
-    s->dirty = true;
-  }
+  p->E = P.elems.high();
+  p->S = P.sides.high();
+  s->dirty = true;  // the occupied lists change
+  s->resident_dof -= sl.E * (int64_t)(sl.N + 1) * (sl.N + 1) * (sl.N + 1);
   sl.used = false;
   sl.ticket = -1;
   sl.out_buf = nullptr;
@@ -642,9 +731,19 @@ static void worker_loop(dg_server* s) {
       }
     }
     std::vector<Request> back;
+    const double ti0 = now_s();
+    bool blocked = false;  // strict order: a case that waits holds back the later ones
     for (auto& r : take) {
       std::string err;
+      const int64_t dof = r.E * (r.N + 1) * (r.N + 1) * (r.N + 1);
+      const int64_t cap = s->cfg.max_resident_dof;
+      if (cap > 0 && (blocked || (s->resident_dof > 0 && s->resident_dof + dof > cap))) {
+        blocked = true;
+        back.push_back(std::move(r));
+        continue;
+      }
       if (admit(s, r, err)) {
+        s->resident_dof += dof;
         std::lock_guard<std::mutex> lk(s->m);
         s->running[r.ticket] = -1;
         for (int i = 0; i < (int)s->slots.size(); ++i)
@@ -660,12 +759,14 @@ static void worker_loop(dg_server* s) {
         s->worker_error = err;
         s->admitting.erase(r.ticket);
       } else {
+        if (cap > 0) blocked = true;
         back.push_back(std::move(r));  // no room yet: stays prepared
       }
     }
-    if (!back.empty()) {
+    {
       std::lock_guard<std::mutex> lk(s->m);
       for (auto it = back.rbegin(); it != back.rend(); ++it) s->ready.push_front(std::move(*it));
+      if (!take.empty()) s->stat_insert_s += now_s() - ti0;
     }
     s->cv.notify_all();
     bool have = false;
@@ -674,7 +775,13 @@ static void worker_loop(dg_server* s) {
     if (have) {
       if (s->dirty) {
         // an executable graph still in flight is released when it completes
-        cudaError_t e = capture_step(s);
+        const double tc0 = now_s();
+        cudaError_t e = rebuild_lists(s);
+        if (e == cudaSuccess) e = capture_step(s);
+        {
+          std::lock_guard<std::mutex> lk(s->m);
+          s->stat_capture_s += now_s() - tc0;
+        }
         if (e != cudaSuccess) {
           std::lock_guard<std::mutex> lk(s->m);
           s->worker_error = std::string("graph capture: ") + cudaGetErrorString(e);
@@ -684,6 +791,7 @@ static void worker_loop(dg_server* s) {
         s->dirty = false;
       }
       const int b = (int)(s->launched & 1);
+      cudaEventRecord(s->step_t0[b], s->stream);
       cudaGraphLaunch(s->graph, s->stream);
       count_launch(1);
       cudaMemcpyAsync(s->h_cases + b * s->cfg.max_cases, s->d_cases, sizeof(CaseData) * s->cfg.max_cases,
@@ -708,9 +816,12 @@ static void worker_loop(dg_server* s) {
     }
     inflight = have;
     const CaseData* rec = s->h_cases + b * s->cfg.max_cases;
+    float step_ms = 0.0f;
+    cudaEventElapsedTime(&step_ms, s->step_t0[b], s->step_ev[b]);
     {
       std::lock_guard<std::mutex> lk(s->m);
       s->stat_steps += 1;
+      s->stat_device_s += 1e-3 * step_ms;
     }
     for (int i = 0; i < (int)s->slots.size(); ++i) {
       Slot& sl = s->slots[i];
@@ -751,7 +862,12 @@ static void prepare_loop(dg_server* s) {
     }
     std::string err;
     reap_frees(s, false);
+    const double tp0 = now_s();
     const bool ok = prepare(s, r, err);
+    {
+      std::lock_guard<std::mutex> lk(s->m);
+      s->stat_prepare_s += now_s() - tp0;
+    }
     std::lock_guard<std::mutex> lk(s->m);
     if (ok) {
       s->ready.push_back(std::move(r));
@@ -810,15 +926,28 @@ void dg_server_destroy(dg_server* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   reap_frees(s, true);
   if (s->graph) cudaGraphExecDestroy(s->graph);
+  for (auto& og : s->old_graphs) {
+    cudaGraphExecDestroy(og.first);
+    cudaEventDestroy(og.second);
+  }
   for (auto& kv : s->pools) {
     kv.second.ctx->cases = nullptr;  // owned by the server
     dg_destroy(kv.second.ctx);
+    if (kv.second.branch) cudaStreamDestroy(kv.second.branch);
+    for (int b = 0; b < 2; ++b) {
+      if (kv.second.h_elist[b]) cudaFreeHost(kv.second.h_elist[b]);
+      if (kv.second.h_slist[b]) cudaFreeHost(kv.second.h_slist[b]);
+    }
+    if (kv.second.fork) cudaEventDestroy(kv.second.fork);
+    if (kv.second.join) cudaEventDestroy(kv.second.join);
   }
   for (auto& sl : s->slots)
     if (sl.staging) cudaFreeHost(sl.staging);
   if (s->h_cases) cudaFreeHost(s->h_cases);
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 2; ++b) {
     if (s->step_ev[b]) cudaEventDestroy(s->step_ev[b]);
+    if (s->step_t0[b]) cudaEventDestroy(s->step_t0[b]);
+  }
   if (s->d_cases) cudaFree(s->d_cases);
   if (s->stream) cudaStreamDestroy(s->stream);
   if (s->setup_stream) cudaStreamDestroy(s->setup_stream);
@@ -830,6 +959,7 @@ int dg_server_create(dg_server** out, const dg_server_config* cfg) {
   if (!out || !cfg) return set_error(DG_ERR_ARG, "dg_server_create: NULL argument");
   *out = nullptr;
   if (cfg->max_cases < 1 || cfg->max_cases > 4096) return set_error(DG_ERR_ARG, "max_cases must be in [1, 4096]");
+  if (cfg->max_resident_dof < 0) return set_error(DG_ERR_ARG, "max_resident_dof must be >= 0");
   if (cfg->precision != DG_FP64 && cfg->precision != DG_FP32_BULK) return set_error(DG_ERR_ARG, "bad precision");
   dg_server* s = new dg_server();
   s->cfg = *cfg;
@@ -843,12 +973,19 @@ int dg_server_create(dg_server** out, const dg_server_config* cfg) {
   s->prm.shock_capturing = 0;
   cudaGetDevice(&s->device);
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->setup_stream, cudaStreamNonBlocking);
+  // case set-up kernels are short: they get the higher priority, so that they
+  // start between the blocks of the step kernels instead of after them
+  int prio_low = 0, prio_high = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->setup_stream, cudaStreamNonBlocking, prio_high);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_cases, sizeof(CaseData) * cfg->max_cases);
   if (e == cudaSuccess) e = cudaMemset(s->d_cases, 0, sizeof(CaseData) * cfg->max_cases);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_cases, 2 * sizeof(CaseData) * cfg->max_cases);
-  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&s->step_ev[b], cudaEventDisableTiming);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaEventCreate(&s->step_ev[b]);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->step_t0[b]);
+  }
   s->slots.resize(cfg->max_cases);
   for (auto& sl : s->slots)
     if (e == cudaSuccess) e = cudaMallocHost(&sl.staging, sizeof(CaseData));
@@ -869,6 +1006,20 @@ int dg_server_create(dg_server** out, const dg_server_config* cfg) {
     }
     P.ctx->cases = s->d_cases;
     P.ctx->n_case_slots = cfg->max_cases;
+    cudaError_t pe = cudaStreamCreateWithFlags(&P.branch, cudaStreamNonBlocking);
+    if (pe == cudaSuccess) pe = cudaMalloc(&P.ctx->elem_list, sizeof(int) * cfg->pool_elems[N]);
+    if (pe == cudaSuccess) pe = cudaMalloc(&P.ctx->side_list, sizeof(int) * 3 * cfg->pool_elems[N]);
+    for (int b = 0; b < 2 && pe == cudaSuccess; ++b) {
+      pe = cudaMallocHost(&P.h_elist[b], sizeof(int) * cfg->pool_elems[N]);
+      if (pe == cudaSuccess) pe = cudaMallocHost(&P.h_slist[b], sizeof(int) * 3 * cfg->pool_elems[N]);
+    }
+    if (pe == cudaSuccess) pe = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
+    if (pe == cudaSuccess) pe = cudaEventCreateWithFlags(&P.join, cudaEventDisableTiming);
+    if (pe != cudaSuccess) {
+      s->pools[N] = P;
+      dg_server_destroy(s);
+      return set_error(DG_ERR_CUDA, std::string("dg_server_create: ") + cudaGetErrorString(pe));
+    }
     P.elems.init(cfg->pool_elems[N]);
     P.sides.init(3 * cfg->pool_elems[N]);
     s->pools[N] = P;
@@ -942,6 +1093,10 @@ int dg_server_stats(dg_server* s, double* out) {
   out[3] = (double)(s->pending.size() + s->ready.size());
   out[4] = s->stat_captures;
   out[5] = s->stat_dofstages;
+  out[6] = s->stat_device_s;
+  out[7] = s->stat_capture_s;
+  out[8] = s->stat_prepare_s;
+  out[9] = s->stat_insert_s;
   return DG_OK;
 }
 

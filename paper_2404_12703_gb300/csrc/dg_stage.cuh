@@ -78,17 +78,28 @@ struct SPrim {
 // reference state (zero on the FP64 path) is a state at rest: rr, pr, its
 // total energy Er = pr / (gamma - 1), enthalpy Hr = (Er + pr) / rr and
 // temperature Tr = pr / (rr R).
+// The FP32 fields are the same constants rounded once, on the host or by the
+// kernel that sets the references, so that no kernel converts them per thread.
 struct CaseParams {
   double mu, lam, pr, Hr, Tr, rr, Er;
   int riemann;
+  float fmu, flam, fpr, fHr, fTr, fgm1, fRinv, fgamma;
 };
 __device__ __forceinline__ CaseParams case_params(const StageArgs& a, int c) {
   if (a.cases) {
     const CaseData& d = a.cases[c < 0 ? 0 : c];
-    return {d.mu, d.lam, d.ref_p, d.ref_H, d.ref_T, d.ref_rho, d.ref_E, d.riemann};
+    return {d.mu,     d.lam,     d.ref_p,   d.ref_H,   d.ref_T, d.ref_rho, d.ref_E,  d.riemann,
+            d.f_mu,   d.f_lam,   d.f_ref_p, d.f_ref_H, d.f_ref_T, a.f_gm1, a.f_Rinv, a.f_gamma};
   }
   const DevScalars* s = a.scal;
-  return {a.mu, a.lam, s->ref_p, s->ref_H, s->ref_T, s->ref_rho, s->ref_E, a.riemann};
+  return {a.mu,   a.lam,   s->ref_p,   s->ref_H,   s->ref_T, s->ref_rho, s->ref_E,  a.riemann,
+          a.f_mu, a.f_lam, s->f_ref_p, s->f_ref_H, s->f_ref_T, a.f_gm1, a.f_Rinv, a.f_gamma};
+}
+// the constant in the arithmetic type: the FP64 value, or its FP32 copy
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f) {
+  if constexpr (sizeof(T) == sizeof(float)) return f;
+  else return d;
 }
 __device__ __forceinline__ double case_dt(const StageArgs& a, int c) {
   return a.cases ? a.cases[c < 0 ? 0 : c].dt : a.scal->dt;
@@ -112,7 +123,7 @@ __device__ __forceinline__ SPrim<T> shifted_prim(const double U[5], double gm1, 
 // With Er = pr / (gamma - 1) and Hr = (Er + pr) / rr, exactly
 //   p' = (gamma - 1)(d_E - |m|^2 / (2 rho)),
 //   H' = (d_E + p' - Hr d_rho) / rho,
-//   T' = (p' - (pr / rr) d_rho) / (rho R).
+//   T' = (p' / R - Tr d_rho) / rho.
 template <>
 __device__ __forceinline__ SPrim<float> shifted_prim<float>(const double U[5], double gm1, double Rinv,
                                                             const CaseParams& cp, double* p_full) {
@@ -120,9 +131,9 @@ __device__ __forceinline__ SPrim<float> shifted_prim<float>(const double U[5], d
   const float rho = float(U[0]), m0 = float(U[1]), m1 = float(U[2]), m2 = float(U[3]);
   const float ri = 1.0f / rho;
   const float u = m0 * ri, v = m1 * ri, w = m2 * ri;
-  const float pp = float(gm1) * (dE - 0.5f * (m0 * u + m1 * v + m2 * w));
-  const float Hp = (dE + pp - float(cp.Hr) * drho) * ri;
-  const float Tp = (pp - float(cp.rr > 0 ? cp.pr / cp.rr : 0.0) * drho) * ri * float(Rinv);
+  const float pp = cp.fgm1 * (dE - 0.5f * (m0 * u + m1 * v + m2 * w));
+  const float Hp = (dE + pp - cp.fHr * drho) * ri;
+  const float Tp = (pp * cp.fRinv - cp.fTr * drho) * ri;
   if (p_full) *p_full = cp.pr + double(pp);
   return {rho, u, v, w, pp, Hp, Tp};
 }
@@ -218,7 +229,8 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= (int64_t)a.S * n2) return;
-  const int s = (int)(tid / n2), pq = (int)(tid % n2);
+  const int si = (int)(tid / n2), pq = (int)(tid % n2);
+  const int s = a.side_list ? a.side_list[si] : si;
   const int p = pq % n, q = pq / n;
   const int cs = a.side_case ? a.side_case[s] : 0;
   if (cs < 0) return;  // free side slot of a serving pool
@@ -237,8 +249,14 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
   const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
   const T qa[4] = {T(0.5) * (qM.u + qS.u), T(0.5) * (qM.v + qS.v), T(0.5) * (qM.w + qS.w), T(0.5) * (qM.Tt + qS.Tt)};
-  const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
-  const T sn[3] = {T(nr[0]), T(nr[n2]), T(nr[2 * n2])};
+  T sn[3];
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const float* nr = a.nrm32 + (size_t)s * 7 * n2 + pq;
+    sn[0] = nr[0], sn[1] = nr[n2], sn[2] = nr[2 * n2];
+  } else {
+    const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
+    sn[0] = nr[0], sn[1] = nr[n2], sn[2] = nr[2 * n2];
+  }
   T* out = TBuf<T>::lflux(a) + (size_t)s * 12 * n2 + pq;
 #pragma unroll
   for (int qv = 0; qv < 4; ++qv)
@@ -253,15 +271,17 @@ template <int N, typename T>
 __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
   using S = Shape<N>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  constexpr int n2p = (n2 + 3) & ~3;  // keeps the arrays below 16-byte aligned
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sDh = reinterpret_cast<T*>(smraw);  // [n2]
-  T* sq = sDh + n2;                      // [EPB][4][n3]
+  T* sDh = reinterpret_cast<T*>(smraw);  // [n2p]
+  T* sq = sDh + n2p;                     // [EPB][4][n3]
   T* sF = sq + EPB * 4 * n3;             // [EPB][12][n3]
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
   // Slots past the last element redo the last element in their own shared
   // memory slot, so that every thread of a block runs the same path through
   // the barriers; only the final global stores are masked.
-  const int e = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
+  const int ei = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
+  const int e = a.elem_list ? a.elem_list[ei] : ei;
   const int ce = a.elem_case ? a.elem_case[e] : 0;
   // free element slots of a serving pool compute on whatever they hold and
   // store nothing, like the slots past the last element
@@ -274,6 +294,18 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
   for (int k = threadIdx.x; k < n2; k += blockDim.x) sDh[k] = T(a.ops->Dhat[k]);
   T* q = sq + le * 4 * n3;
   T* F = sF + le * 12 * n3;
+  // FP32: the node's ten metric values are loaded up front, so that their
+  // latency overlaps the state loads instead of following each barrier
+  constexpr bool pre = sizeof(T) == sizeof(float);
+  T Mpre[pre ? 10 : 1];
+  if constexpr (pre) {
+#pragma unroll
+    for (int c = 0; c < 10; ++c) Mpre[c] = metric_at<T>(a, e, c, t, n3);
+  }
+  auto Mv = [&](int c) -> T {
+    if constexpr (pre) return Mpre[c];
+    else return metric_at<T>(a, e, c, t, n3);
+  };
   {
     double U[5];
     const double* u = a.U + (size_t)e * 5 * n3 + t;
@@ -292,17 +324,28 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
   T acc[12];
 #pragma unroll
   for (int c = 0; c < 12; ++c) acc[c] = T(0);
+  // FP32 (bound by shared-memory load instructions): the products are stored
+  // as six float2 planes, halving the loads of the line sums
+  constexpr bool pairs2 = sizeof(T) == sizeof(float);
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
     {
-      const T J0 = metric_at<T>(a, e, d * 3 + 0, t, n3), J1 = metric_at<T>(a, e, d * 3 + 1, t, n3),
-              J2 = metric_at<T>(a, e, d * 3 + 2, t, n3);
+      const T J0 = Mv(d * 3 + 0), J1 = Mv(d * 3 + 1), J2 = Mv(d * 3 + 2);
+      T pr[12];
 #pragma unroll
       for (int qv = 0; qv < 4; ++qv) {
         const T qq = q[qv * n3 + t];
-        F[(qv * 3 + 0) * n3 + t] = J0 * qq;
-        F[(qv * 3 + 1) * n3 + t] = J1 * qq;
-        F[(qv * 3 + 2) * n3 + t] = J2 * qq;
+        pr[qv * 3 + 0] = J0 * qq;
+        pr[qv * 3 + 1] = J1 * qq;
+        pr[qv * 3 + 2] = J2 * qq;
+      }
+      if constexpr (pairs2) {
+        float2* F2 = reinterpret_cast<float2*>(F);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) F2[k * n3 + t] = make_float2(pr[2 * k], pr[2 * k + 1]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) F[k * n3 + t] = pr[k];
       }
     }
     __syncwarp();
@@ -313,8 +356,18 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
       for (int al = 0; al < n; ++al) {
         const T c = sDh[id * n + al];
         const int nb = base + al * str[d];
+        if constexpr (pairs2) {
+          const float2* F2 = reinterpret_cast<const float2*>(F);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] += c * F[k * n3 + nb];
+          for (int k = 0; k < 6; ++k) {
+            const float2 v = F2[k * n3 + nb];
+            acc[2 * k] += c * v.x;
+            acc[2 * k + 1] += c * v.y;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 12; ++k) acc[k] += c * F[k * n3 + nb];
+        }
       }
     }
     __syncwarp();
@@ -339,7 +392,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] += sg * L[k * n2];
   }
-  const T Ji = metric_at<T>(a, e, 9, t, n3);
+  const T Ji = Mv(9);
   T* g = TBuf<T>::g(a) + (size_t)e * 12 * n3 + t;
 #pragma unroll
   for (int k = 0; k < 12; ++k) g[k * n3] = acc[k] * Ji;
@@ -354,7 +407,8 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= (int64_t)a.S * n2) return;
-  const int s = (int)(tid / n2), pq = (int)(tid % n2);
+  const int si = (int)(tid / n2), pq = (int)(tid % n2);
+  const int s = a.side_list ? a.side_list[si] : si;
   const int p = pq % n, q = pq / n;
   const int cs = a.side_case ? a.side_case[s] : 0;
   if (cs < 0) return;  // free side slot of a serving pool
@@ -372,15 +426,23 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   for (int k = 0; k < 5; ++k) { UM[k] = uM[k * n3]; US[k] = uS[k * n3]; }
   const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
   const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
-  const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
-  const T sn[3] = {T(nr[0]), T(nr[n2]), T(nr[2 * n2])};
-  const double sAd = nr[3 * n2];
-  const double invd = 1.0 / sAd;
-  const T sA = T(sAd);
-  const T nu[3] = {T(nr[0] * invd), T(nr[n2] * invd), T(nr[2 * n2] * invd)};
+  T sn[3], nu[3], sA;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const float* nr = a.nrm32 + (size_t)s * 7 * n2 + pq;
+    sn[0] = nr[0], sn[1] = nr[n2], sn[2] = nr[2 * n2];
+    nu[0] = nr[3 * n2], nu[1] = nr[4 * n2], nu[2] = nr[5 * n2];
+    sA = nr[6 * n2];
+  } else {
+    const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
+    sn[0] = nr[0], sn[1] = nr[n2], sn[2] = nr[2 * n2];
+    const double sAd = nr[3 * n2];
+    const double invd = 1.0 / sAd;
+    sA = sAd;
+    nu[0] = nr[0] * invd, nu[1] = nr[n2] * invd, nu[2] = nr[2 * n2] * invd;
+  }
   T f[5];
-  if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, T(a.gm1), T(cp.Hr), f);
-  else lf_flux_s(qM, qS, nu, T(a.gamma), T(cp.pr), f);
+  if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, pick<T>(a.gm1, a.f_gm1), pick<T>(cp.Hr, cp.fHr), f);
+  else lf_flux_s(qM, qS, nu, pick<T>(a.gamma, a.f_gamma), pick<T>(cp.pr, cp.fpr), f);
 #pragma unroll
   for (int k = 0; k < 5; ++k) f[k] *= sA;
   if (a.viscous) {
@@ -391,9 +453,9 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) { gM[k] = pgM[k * n3]; gS[k] = pgS[k * n3]; }
     T tau[6], W[3], fvM[4], fvS[4];
-    viscous_parts(gM, qM.u, qM.v, qM.w, T(cp.mu), T(cp.lam), tau, W);
+    viscous_parts(gM, qM.u, qM.v, qM.w, pick<T>(cp.mu, cp.fmu), pick<T>(cp.lam, cp.flam), tau, W);
     viscous_flux_n(tau, W, sn, fvM);
-    viscous_parts(gS, qS.u, qS.v, qS.w, T(cp.mu), T(cp.lam), tau, W);
+    viscous_parts(gS, qS.u, qS.v, qS.w, pick<T>(cp.mu, cp.fmu), pick<T>(cp.lam, cp.flam), tau, W);
     viscous_flux_n(tau, W, sn, fvS);
 #pragma unroll
     for (int k = 0; k < 4; ++k) f[1 + k] -= T(0.5) * (fvM[k] + fvS[k]);
@@ -477,8 +539,17 @@ __device__ double element_alpha(double rp, double* sT1, double* sT2, double* sRo
 template <int N, typename T>
 struct VolumeSmem {
   using S = Shape<N>;
-  static constexpr size_t n_dbl = S::n2 + S::EPB * (2 * S::n3 + 4 * S::n2);  // Vinv, indicator scratch
-  static constexpr size_t n_t = 2 * S::n2 + S::EPB * (6 + 9 + 5 + 15) * S::n3;  // Dsplit, Dhat, P, J, G, A
+  // FP32: node-major primitives (float4 + float2) and metrics (one float4 per
+  // direction), so a partner is read with three loads
+  static constexpr bool aos = sizeof(T) == sizeof(float);
+  static constexpr int n2p = (S::n2 + 3) & ~3;
+  static constexpr int nJ = aos ? 12 : 9;
+  // Vinv, indicator scratch (even count: the T arrays start 16-byte aligned)
+  static constexpr size_t n_dbl = (S::n2 + S::EPB * (2 * S::n3 + 4 * S::n2) + 1) & ~size_t(1);
+  // per-element stride of the primitives: a multiple of 4 floats in FP32, so
+  // that every element's float4 view starts 16-byte aligned
+  static constexpr int pstride = aos ? 6 * ((S::n3 + 3) & ~3) : 6 * S::n3;
+  static constexpr size_t n_t = 2 * n2p + S::EPB * (pstride + (nJ + 5 + 15) * S::n3);  // Dsplit, Dhat, P, J, G, A
   static constexpr size_t bytes = sizeof(double) * n_dbl + sizeof(T) * n_t;
 };
 
@@ -490,18 +561,21 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   using S = Shape<N>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   extern __shared__ __align__(16) unsigned char smraw[];
+  using L = VolumeSmem<N, T>;
+  constexpr bool aos = L::aos;
   double* sVi = reinterpret_cast<double*>(smraw);  // [n2] Vinv (FP64)
   double* sX = sVi + n2;                           // [EPB][2 n3 + 4 n2] indicator scratch (FP64)
-  T* sDs = reinterpret_cast<T*>(sX + EPB * (2 * n3 + 4 * n2));  // [n2] Dsplit
-  T* sDh = sDs + n2;                                             // [n2] Dhat
-  T* sP = sDh + n2;                                              // [EPB][6][n3] rho u v w p' H', halved
-  T* sJ = sP + EPB * 6 * n3;                                     // [EPB][9][n3] metrics, halved
-  T* sG = sJ + EPB * 9 * n3;                                     // [EPB][5][n3] viscous / FV fluxes
-  T* sA = sG + EPB * 5 * n3;                                     // [EPB][3][5][n3] two-point sums
+  T* sDs = reinterpret_cast<T*>(reinterpret_cast<double*>(smraw) + L::n_dbl);  // [n2] Dsplit
+  T* sDh = sDs + L::n2p;                                                       // [n2] Dhat
+  T* sP = sDh + L::n2p;                  // [EPB][6][n3] rho u v w p' H', halved (FP32: [n3] float4 + [n3] float2)
+  T* sJ = sP + EPB * L::pstride;         // [EPB][9][n3] metrics, halved (FP32: [3][n3] float4)
+  T* sG = sJ + EPB * L::nJ * n3;         // [EPB][5][n3] viscous / FV fluxes
+  T* sA = sG + EPB * 5 * n3;             // [EPB][3][5][n3] two-point sums
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
   // slots past the last element redo the last element, free slots of a
   // serving pool compute on what they hold; neither stores (see k_lift)
-  const int e = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
+  const int ei = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
+  const int e = a.elem_list ? a.elem_list[ei] : ei;
   const int ce = a.elem_case ? a.elem_case[e] : 0;
   const bool valid = blockIdx.x * EPB + le < a.E && ce >= 0;
   // a block of free pool slots, or of cases that have reached their end time
@@ -514,11 +588,20 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
     sDh[k] = T(a.ops->Dhat[k]);
     sVi[k] = a.ops->Vinv[k];
   }
-  T* P = sP + le * 6 * n3;
-  T* Jm = sJ + le * 9 * n3;
+  T* P = sP + le * L::pstride;
+  T* Jm = sJ + le * L::nJ * n3;
   T* G = sG + le * 5 * n3;
+  // FP32 views of the same memory
+  float4* P4 = reinterpret_cast<float4*>(P);
+  float2* P2 = reinterpret_cast<float2*>(P + 4 * n3);
+  float4* J4 = reinterpret_cast<float4*>(Jm);
+  // halved metric component c of direction d at a node
+  auto Jc = [&](int d, int c, int node) -> T {
+    if constexpr (aos) return reinterpret_cast<const float*>(J4 + d * n3 + node)[c];
+    else return Jm[(d * 3 + c) * n3 + node];
+  };
   T* A = sA + le * 15 * n3;
-  const double pr_ref = cp.pr, H_ref = cp.Hr;
+  const double H_ref = cp.Hr;
   double U[5];
   double p_full;
   SPrim<T> me;
@@ -530,14 +613,23 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
     me = shifted_prim<T>(U, a.gm1, a.Rinv, cp, &p_full);
     // halved values: every arithmetic mean of the two-point flux is then one
     // addition, bit-identical to (a + b) / 2
-    P[t] = T(0.5) * me.rho;
-    P[n3 + t] = T(0.5) * me.u;
-    P[2 * n3 + t] = T(0.5) * me.v;
-    P[3 * n3 + t] = T(0.5) * me.w;
-    P[4 * n3 + t] = T(0.5) * me.p;
-    P[5 * n3 + t] = T(0.5) * me.H;
+    if constexpr (aos) {
+      P4[t] = make_float4(0.5f * me.rho, 0.5f * me.u, 0.5f * me.v, 0.5f * me.w);
+      P2[t] = make_float2(0.5f * me.p, 0.5f * me.H);
 #pragma unroll
-    for (int c = 0; c < 9; ++c) Jm[c * n3 + t] = T(0.5) * metric_at<T>(a, e, c, t, n3);
+      for (int d = 0; d < 3; ++d)
+        J4[d * n3 + t] = make_float4(0.5f * metric_at<T>(a, e, 3 * d, t, n3), 0.5f * metric_at<T>(a, e, 3 * d + 1, t, n3),
+                                     0.5f * metric_at<T>(a, e, 3 * d + 2, t, n3), 0.0f);
+    } else {
+      P[t] = T(0.5) * me.rho;
+      P[n3 + t] = T(0.5) * me.u;
+      P[2 * n3 + t] = T(0.5) * me.v;
+      P[3 * n3 + t] = T(0.5) * me.w;
+      P[4 * n3 + t] = T(0.5) * me.p;
+      P[5 * n3 + t] = T(0.5) * me.H;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) Jm[c * n3 + t] = T(0.5) * metric_at<T>(a, e, c, t, n3);
+    }
     if (a.viscous) {
       const T* pg = TBuf<T>::g(a) + (size_t)e * 12 * n3 + t;
 #pragma unroll
@@ -551,7 +643,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   T accC[5] = {0, 0, 0, 0, 0};  // convective DG volume term
   T acc[5] = {0, 0, 0, 0, 0};   // viscous volume + surface terms
   T tau[6] = {0, 0, 0, 0, 0, 0}, W[3] = {0, 0, 0};
-  if (a.viscous) viscous_parts(g, me.u, me.v, me.w, T(cp.mu), T(cp.lam), tau, W);
+  if (a.viscous) viscous_parts(g, me.u, me.v, me.w, pick<T>(cp.mu, cp.fmu), pick<T>(cp.lam, cp.flam), tau, W);
   // ---- split-form KEP volume integral ----
   // FP64 (bound by the FP64 pipe): one line per task; every unordered pair
   // (i, alpha) of the line forms the symmetric two-point flux once and adds
@@ -560,27 +652,27 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   // one node per thread over all its partners, which keeps every thread busy.
   // Each direction has its own sum array.
   constexpr bool kPairs = sizeof(T) == sizeof(double);
-  if (!kPairs) {
+  if constexpr (!kPairs) {
     const int idl[3] = {t % n, (t / n) % n, t / n2};
+    const float4 pi4 = P4[t];
+    const float2 pi2 = P2[t];
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
       const int id = idl[d], base = t - id * str[d];
-      const T* J0 = Jm + (d * 3 + 0) * n3;
-      const T* J1 = Jm + (d * 3 + 1) * n3;
-      const T* J2 = Jm + (d * 3 + 2) * n3;
-      const T ri = P[t], ui = P[n3 + t], vvi = P[2 * n3 + t], wi = P[3 * n3 + t];
-      const T pi = P[4 * n3 + t], Hi = P[5 * n3 + t];
-      const T j0 = J0[t], j1 = J1[t], j2 = J2[t];
+      const float4 ji = J4[d * n3 + t];
       T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0), s4 = T(0);
 #pragma unroll
       for (int al = 0; al < n; ++al) {
         if (al == id) continue;
         const int va = base + al * str[d];
-        const T m0 = j0 + J0[va], m1 = j1 + J1[va], m2 = j2 + J2[va];
-        const T rho = ri + P[va];
-        const T u0 = ui + P[n3 + va], u1 = vvi + P[2 * n3 + va], u2 = wi + P[3 * n3 + va];
-        const T pp = pi + P[4 * n3 + va];
-        const T H = Hi + P[5 * n3 + va];
+        const float4 pa4 = P4[va];
+        const float2 pa2 = P2[va];
+        const float4 ja = J4[d * n3 + va];
+        const T m0 = ji.x + ja.x, m1 = ji.y + ja.y, m2 = ji.z + ja.z;
+        const T rho = pi4.x + pa4.x;
+        const T u0 = pi4.y + pa4.y, u1 = pi4.z + pa4.z, u2 = pi4.w + pa4.w;
+        const T pp = pi2.x + pa2.x;
+        const T H = pi2.y + pa2.y;
         const T fr = rho * (u0 * m0 + u1 * m1 + u2 * m2);
         const T dv = sDs[id * n + al];
         s0 += dv * fr;
@@ -597,7 +689,8 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
       Ad[4 * n3 + t] = s4;
     }
   }
-  for (int lt = t; kPairs && lt < 3 * n2; lt += n3) {
+  if constexpr (kPairs)
+  for (int lt = t; lt < 3 * n2; lt += n3) {
     const int d = lt / n2, line = lt % n2;
     const int lp = line % n, lq = line / n;
     const int base = d == 0 ? n * (lp + n * lq) : (d == 1 ? lp + n2 * lq : lp + n * lq);
@@ -655,8 +748,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
       {
-        const T nv[3] = {T(2) * Jm[(d * 3 + 0) * n3 + t], T(2) * Jm[(d * 3 + 1) * n3 + t],
-                         T(2) * Jm[(d * 3 + 2) * n3 + t]};
+        const T nv[3] = {T(2) * Jc(d, 0, t), T(2) * Jc(d, 1, t), T(2) * Jc(d, 2, t)};
         T fv[4];
         viscous_flux_n(tau, W, nv, fv);
 #pragma unroll
@@ -718,7 +810,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
         for (int k = 0; k < 5; ++k) UR[k] = ur[k * n3];
         const SPrim<T> qR = shifted_prim<T>(UR, a.gm1, a.Rinv, cp);
         T fb[5];
-        lf_flux_s(me, qR, nu, T(a.gamma), T(pr_ref), fb);
+        lf_flux_s(me, qR, nu, pick<T>(a.gamma, a.f_gamma), pick<T>(cp.pr, cp.fpr), fb);
         if (right) {
 #pragma unroll
           for (int k = 0; k < 5; ++k) G[k * n3 + t] = fb[k] * T(sAd);
@@ -765,11 +857,12 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
     for (int k = 0; k < 5; ++k) acc[k] += sg * Fs[k * n2];
   }
   // ---- ApplyJac; the energy equation gets H_ref times the mass equation back ----
-  // (FP32-bulk: 1/J rounded to FP32 scales all five components alike)
-  const double Ji = metric_at<T>(a, e, 9, t, n3);
+  // in the arithmetic type (FP32-bulk: 1/J rounded to FP32 scales all five
+  // components alike); the H_ref part of the energy equation in FP64
+  const T Ji = metric_at<T>(a, e, 9, t, n3);
   double Ut[5];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) Ut[k] = -(double)(accC[k] + acc[k]) * Ji;
+  for (int k = 0; k < 5; ++k) Ut[k] = (double)(-(accC[k] + acc[k]) * Ji);
   Ut[4] += H_ref * Ut[0];
   if (MODE == 0) {
     double* o = a.Ut + (size_t)e * 5 * n3 + t;
@@ -799,6 +892,7 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.metric = c->metric;
   a.metric32 = c->metric32;
   a.nrm = c->nrm;
+  a.nrm32 = c->nrm32;
   a.elem_side = c->elem_side;
   a.side_e = c->side_e;
   a.side_f = c->side_f;
@@ -816,6 +910,11 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.Rinv = 1.0 / c->prm.R;
   a.mu = c->prm.mu;
   a.lam = c->prm.gamma * c->prm.R * c->prm.mu / ((c->prm.gamma - 1.0) * c->prm.Pr);
+  a.f_gamma = (float)a.gamma;
+  a.f_gm1 = (float)a.gm1;
+  a.f_Rinv = (float)a.Rinv;
+  a.f_mu = (float)a.mu;
+  a.f_lam = (float)a.lam;
   a.riemann = c->prm.riemann;
   a.viscous = c->prm.viscous;
   a.shock = c->prm.shock_capturing;
@@ -826,13 +925,19 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.elem_case = c->elem_case;
   a.side_case = c->side_case;
   a.cases = c->cases;
+  a.elem_list = c->elem_list;
+  a.side_list = c->side_list;
+  if (c->elem_list) {
+    a.E = (int)c->n_elem_list;
+    a.S = (int)c->n_side_list;
+  }
   return a;
 }
 
 template <int N, typename T>
 inline size_t lift_smem_bytes() {
   using S = Shape<N>;
-  return sizeof(T) * (S::n2 + S::EPB * 16 * S::n3);
+  return sizeof(T) * (((S::n2 + 3) & ~3) + S::EPB * 16 * S::n3);
 }
 
 template <int N, typename T>
@@ -855,9 +960,10 @@ cudaError_t stage_launch(dg_ctx* c, const double* U, int mode, double rkA, doubl
   a.rkA = rkA;
   a.rkB = rkB;
   a.first_stage = first;
-  const int64_t side_nodes = c->S * S::n2;
+  const int64_t side_nodes = (int64_t)a.S * S::n2;
   const unsigned sb = (unsigned)((side_nodes + 255) / 256);
-  const unsigned eb = (unsigned)((c->E + S::EPB - 1) / S::EPB);
+  const unsigned eb = (unsigned)((a.E + S::EPB - 1) / S::EPB);
+  if (a.E == 0) return cudaSuccess;
   if (c->prm.viscous) {
     prof_begin(c, PK_SURF_PRIMS);
     k_surf_prims<N, T><<<sb, 256, 0, c->stream>>>(a);

@@ -39,6 +39,7 @@ struct DevScalars {
   long long steps;           // steps taken with dt > 0
   double dt_cfl;             // CFL time step of the current state (dg_time_step)
   double ref_rho, ref_E;     // reference density and total energy (state at rest)
+  float f_ref_p, f_ref_H, f_ref_T, f_pad;  // FP32 copies for the FP32-bulk kernels
 };
 
 // Per-case data of a serving pool (device, one entry per case slot).
@@ -55,6 +56,7 @@ struct CaseData {
   int steps;      // completed steps
   int N;          // polynomial degree of the case's pool
   int pad;
+  float f_mu, f_lam, f_ref_p, f_ref_H, f_ref_T, f_pad;  // FP32 copies (FP32-bulk kernels)
 };
 
 // Per-stage launch parameters of the RHS kernels.
@@ -64,6 +66,7 @@ struct StageArgs {
   const double* metric;  // [E][10][n3]: J a^d_c at d*3+c, then 1/J
   const float* metric32;  // the same, rounded to FP32 (FP32-bulk)
   const double* nrm;     // [S][4][n2]: s n (3), s
+  const float* nrm32;    // [S][7][n2]: s n (3), unit n (3), s, in FP32 (FP32-bulk)
   const int* elem_side;  // [E][6]
   const int2* side_e;    // [S] (eM, eS)
   const int* side_f;     // [S] fM | fS << 4 | flip << 8
@@ -77,6 +80,7 @@ struct StageArgs {
   const double* fvmetric;  // [E][3][n2][(n-1)*3] sub-cell interface metrics
   const Ops* ops;
   double gamma, gm1, Rinv, mu, lam;
+  float f_gamma, f_gm1, f_Rinv, f_mu, f_lam;  // FP32 copies (FP32-bulk kernels)
   int riemann, viscous, shock;
   double alpha_min, alpha_max, alpha_force;
   // output: either Ut (mode 0) or the RK update (mode 1)
@@ -91,6 +95,10 @@ struct StageArgs {
   const int* elem_case;
   const int* side_case;
   const CaseData* cases;
+  // serving pools: the occupied elements and sides; the launch grids cover
+  // these (E and S are then their counts), so freed ranges cost nothing
+  const int* elem_list;
+  const int* side_list;
 };
 
 }  // namespace dg
@@ -99,6 +107,7 @@ struct dg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;      // user stream: all work is ordered on it
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  cudaStream_t pool_stream = nullptr;  // non-null: arrays from the library pool, in this stream's order
   int N = 0, n = 0, n2 = 0, n3 = 0;
   int64_t E = 0, S = 0;
   dg_params prm{};
@@ -111,6 +120,7 @@ struct dg_ctx {
   float* metric32 = nullptr;  // [E][10][n3] rounded to FP32 (FP32-bulk)
   double* g = nullptr;       // [E][12][n3]
   double* nrm = nullptr;     // [S][4][n2]
+  float* nrm32 = nullptr;    // [S][7][n2]: s n, unit n, s in FP32 (FP32-bulk)
   double* lflux = nullptr;   // [S][12][n2]
   double* fstar = nullptr;   // [S][5][n2]
   float* g32 = nullptr;      // FP32-bulk: [E][12][n3]
@@ -138,6 +148,9 @@ struct dg_ctx {
   int* side_case = nullptr;
   dg::CaseData* cases = nullptr;
   int n_case_slots = 0;
+  int* elem_list = nullptr;  // occupied elements / sides of a serving pool (device)
+  int* side_list = nullptr;
+  int64_t n_elem_list = 0, n_side_list = 0;
 };
 
 // Event pairs around each kernel launch, grouped by kernel kind.

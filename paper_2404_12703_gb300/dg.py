@@ -53,7 +53,8 @@ class MeshDesc(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double), ("dfl", C.c_double),
-                ("precision", C.c_int), ("max_cases", C.c_int), ("pool_elems", C.c_int64 * 8)]
+                ("precision", C.c_int), ("max_cases", C.c_int), ("pool_elems", C.c_int64 * 8),
+                ("max_resident_dof", C.c_int64)]
 
 
 class CaseDesc(C.Structure):
@@ -316,7 +317,8 @@ class Server:
     STAT_KEYS = ("time_to_solution", "queue_wait", "service_time", "t_final", "steps", "elements", "N",
                  "nonfinite")
 
-    def __init__(self, pool_elems=None, max_cases=64, precision=FP64, gamma=1.4, R=1.0, Pr=0.72, dfl=0.9):
+    def __init__(self, pool_elems=None, max_cases=64, precision=FP64, gamma=1.4, R=1.0, Pr=0.72, dfl=0.9,
+                 max_resident_dof=0):
         lib = load()
         self._lib = lib
         cfg = ServerConfig()
@@ -324,6 +326,7 @@ class Server:
         cfg.gamma, cfg.R, cfg.Pr, cfg.dfl = gamma, R, Pr, dfl
         cfg.precision = precision
         cfg.max_cases = max_cases
+        cfg.max_resident_dof = int(max_resident_dof)
         if pool_elems is not None:
             for N in range(8):
                 cfg.pool_elems[N] = int(pool_elems.get(N, 0))
@@ -385,6 +388,7 @@ class Server:
             time.sleep(0.002)
 
     def stats(self):
-        out = (C.c_double * 6)()
+        out = (C.c_double * 10)()
         _check(self._lib.dg_server_stats(self._h, out))
-        return dict(zip(("steps", "finished", "resident", "waiting", "captures", "dof_stage_updates"), list(out)))
+        return dict(zip(("steps", "finished", "resident", "waiting", "captures", "dof_stage_updates",
+                         "step_device_s", "capture_host_s", "setup_host_s", "insert_host_s"), list(out)))

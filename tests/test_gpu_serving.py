@@ -114,3 +114,29 @@ def test_fp32_bulk_serving_close_to_fp64():
         srv.close()
     err = np.sqrt(((out[dg.FP32_BULK] - out[dg.FP64]) ** 2).sum() / (out[dg.FP64] ** 2).sum())
     assert err < 1e-5
+
+
+def test_resident_dof_cap_admits_in_order():
+    """With max_resident_dof equal to one case's DOF, three cases submitted at
+    once run one after the other, in submission order, with unchanged results."""
+    torch, dg = gpu_or_skip()
+    built = [make("tgv", 3, (4, 4, 4), s) for s in (11, 12, 13)]
+    dof = built[0][0]["E"] * 4 ** 3
+    t_end = 0.03
+    free = dg.Server(POOLS, max_cases=8)
+    ref = [free.wait(free.submit(m, U0, t_end, mu=mu))[0] for m, U0, mu in built]
+    free.close()
+    srv = dg.Server(POOLS, max_cases=8, max_resident_dof=dof)
+    tickets = [srv.submit(m, U0, t_end, mu=mu) for m, U0, mu in built]
+    out = [srv.wait(tk) for tk in tickets]
+    srv.close()
+    for (U, st), Ur in zip(out, ref):
+        np.testing.assert_array_equal(U, Ur)
+        assert st["t_final"] == t_end
+    waits = [st["queue_wait"] for _, st in out]
+    services = [st["service_time"] for _, st in out]
+    # each case is admitted only once the previous one has taken its last step
+    # (its service time also covers copying its state out, after that)
+    assert waits[0] < waits[1] < waits[2]
+    assert waits[1] >= 0.5 * services[0]
+    assert waits[2] >= waits[1] + 0.5 * services[1]

@@ -60,7 +60,7 @@ typedef struct {
   double gamma;          /* ratio of specific heats                               */
   double R;              /* specific gas constant                                 */
   double Pr;             /* Prandtl number                                        */
-  double mu;             /* constant dynamic viscosity                            */
+  double mu;             /* dynamic viscosity (with sutherland: its value at T_ref) */
   int riemann;           /* DG_RIEMANN_ROE (no entropy fix) or DG_RIEMANN_LF      */
   int viscous;           /* 0: Euler; 1: Navier-Stokes with BR1 lifting            */
   int shock_capturing;   /* 1: Hennemann indicator + FV sub-cell blending         */
@@ -70,6 +70,11 @@ typedef struct {
   int precision;         /* DG_FP64 or DG_FP32_BULK                               */
   double alpha_force;    /* < 0: use the indicator; >= 0: every element uses this
                             blending factor (verification)                       */
+  int sutherland;        /* 1: mu(T) = mu 1.4042 (T/T_ref)^(3/2) / (T/T_ref + 0.4042)
+                            at every node (Eq. sutherland), lambda following mu at
+                            constant Pr; 0: constant mu.  Standalone contexts only:
+                            the server's cases use a constant mu                 */
+  double T_ref;          /* Sutherland reference temperature (> 0)                */
 } dg_params;
 
 /* Fills p with the defaults: gamma 1.4, R 1, Pr 0.72, mu 1/1600, Roe, viscous,

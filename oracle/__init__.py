@@ -99,12 +99,14 @@ def _f64(a):
 
 def params(gamma=1.4, R=1.0, Pr=0.72, mu=1.0 / 1600.0, riemann="roe", viscous=True,
            shock=False, alpha_min=1e-3, alpha_max=0.5, cfl=0.9, dfl=0.9,
-           alpha_force=-1.0) -> np.ndarray:
+           alpha_force=-1.0, sutherland=False, T_ref=1.0) -> np.ndarray:
     """Flat parameter vector in the oracle's layout.  ``alpha_force >= 0`` makes
-    every element blend with that alpha instead of the indicator's (tests)."""
+    every element blend with that alpha instead of the indicator's (tests).
+    ``sutherland``: mu(T) by Sutherland's law, ``mu`` being its value at T_ref."""
     r = {"roe": 0, "lf": 1}[riemann] if isinstance(riemann, str) else int(riemann)
     return np.array([gamma, R, Pr, mu, r, int(bool(viscous)), int(bool(shock)),
-                     alpha_min, alpha_max, cfl, dfl, alpha_force], dtype=np.float64)
+                     alpha_min, alpha_max, cfl, dfl, alpha_force, int(bool(sutherland)), T_ref],
+                    dtype=np.float64)
 
 
 def ops(N: int, quad: bool = False):

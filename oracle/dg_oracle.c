@@ -71,7 +71,7 @@ typedef double real;
 /* ------------------------------------------------------------------ */
 enum {
   P_GAMMA = 0, P_R, P_PR, P_MU, P_RIEMANN, P_VISCOUS, P_SHOCK,
-  P_ALPHA_MIN, P_ALPHA_MAX, P_CFL, P_DFL, P_ALPHA_FORCE, P_COUNT
+  P_ALPHA_MIN, P_ALPHA_MAX, P_CFL, P_DFL, P_ALPHA_FORCE, P_SUTHERLAND, P_TREF, P_COUNT
 };
 
 typedef struct {
@@ -81,6 +81,8 @@ typedef struct {
   int shock;
   real alpha_min, alpha_max, cfl, dfl;
   real alpha_force;  /* >= 0: every element blends with this alpha (tests) */
+  int sutherland;    /* 1: mu = mu(T) by Sutherland's law, mu being its value at T_ref */
+  real T_ref;
 } params_t;
 
 static params_t read_params(const double* p) {
@@ -97,6 +99,8 @@ static params_t read_params(const double* p) {
   P.cfl = p[P_CFL];
   P.dfl = p[P_DFL];
   P.alpha_force = p[P_ALPHA_FORCE];
+  P.sutherland = (int)p[P_SUTHERLAND];
+  P.T_ref = p[P_TREF];
   return P;
 }
 
@@ -532,14 +536,23 @@ static void riemann(const params_t* P, int kind, const real* UL, const real* qL,
   else lf_flux(P, UL, qL, UR, qR, n, f);
 }
 
+/* dynamic viscosity at temperature T: constant, or Sutherland's law
+   (Eq. sutherland) mu(T) = mu_ref 1.4042 (T/T_ref)^(3/2) / (T/T_ref + 0.4042) */
+static real viscosity(const params_t* P, real T) {
+  if (!P->sutherland) return P->mu;
+  real th = T / P->T_ref;
+  return P->mu * (real)1.4042 * th * RSQRT(th) / (th + (real)0.4042);
+}
+
 /* viscous flux F_v = (0, tau, tau.u - q) contracted with nv (Eq. nse, stress and
-   Fourier law); g[qv][x] = d(u, v, w, T)_qv / dx_x */
+   Fourier law, heat conductivity lambda = gamma R mu / ((gamma - 1) Pr));
+   g[qv][x] = d(u, v, w, T)_qv / dx_x */
 static void visc_flux(const params_t* P, const real* q, const real* g, const real* nv, real* f) {
   real ux = g[0], uy = g[1], uz = g[2];
   real vx = g[3], vy = g[4], vz = g[5];
   real wx = g[6], wy = g[7], wz = g[8];
   real Tx = g[9], Ty = g[10], Tz = g[11];
-  real mu = P->mu;
+  real mu = viscosity(P, q[5]);
   real lam = P->gamma * P->R * mu / ((P->gamma - 1) * P->Pr);
   real div = ux + vy + wz;
   real txx = mu * (2 * ux - (real)2 / 3 * div);
@@ -864,7 +877,7 @@ static void lserk_step(real* U, real* dU, real* Ut, long len, real t, real dt, r
 
 /* Time step (the paper gives no rule; reading):
      lambda_c = sum_d (|u . Ja^d| + c |Ja^d|) / J,
-     lambda_v = max(4/3, gamma/Pr) (mu/rho) sum_d |Ja^d|^2 / J^2,
+     lambda_v = max(4/3, gamma/Pr) (mu(T)/rho) sum_d |Ja^d|^2 / J^2,
      dt = min(CFL 2 / ((N+1)^2 max lambda_c), DFL 4 / ((N+1)^4 max lambda_v)). */
 static real time_step(const mesh_t* M, const params_t* P, const real* U, int* nonfinite) {
   long E = M->E, n3 = M->n3;
@@ -884,7 +897,7 @@ static real time_step(const mesh_t* M, const params_t* P, const real* U, int* no
     }
     a /= Jv;
     real kv = (real)4 / 3 > P->gamma / P->Pr ? (real)4 / 3 : P->gamma / P->Pr;
-    b = kv * P->mu / q[0] * b / (Jv * Jv);
+    b = kv * viscosity(P, q[5]) / q[0] * b / (Jv * Jv);
     if (!(a == a) || !(b == b) || !(c == c)) bad = 1;
     if (a > lc) lc = a;
     if (b > lv) lv = b;

@@ -243,6 +243,7 @@ static int check_params(const dg_params* p) {
     return fail(DG_ERR_ARG, "invalid physical parameters");
   if (p->riemann != DG_RIEMANN_ROE && p->riemann != DG_RIEMANN_LF) return fail(DG_ERR_ARG, "unknown Riemann solver");
   if (p->precision != DG_FP64 && p->precision != DG_FP32_BULK) return fail(DG_ERR_ARG, "unknown precision");
+  if (p->sutherland && !(p->T_ref > 0)) return fail(DG_ERR_ARG, "Sutherland's law needs T_ref > 0");
   return DG_OK;
 }
 
@@ -268,6 +269,8 @@ void dg_default_params(dg_params* p) {
   p->dfl = 0.9;
   p->precision = DG_FP64;
   p->alpha_force = -1.0;
+  p->sutherland = 0;
+  p->T_ref = 1.0;
 }
 
 const char* dg_error_string(int code) {

@@ -16,7 +16,7 @@ template <int N, typename T>
 __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U, const double* __restrict__ metric,
                                             const float* __restrict__ metric32, const double* __restrict__ geo,
                                             double gamma, double gm1, double Rinv, double kv, int viscous,
-                                            DevScalars* scal) {
+                                            int sutherland, double inv_Tref, DevScalars* scal) {
   constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
   constexpr bool f32 = sizeof(T) == sizeof(float);
   double lc = 0.0, lv = 0.0;
@@ -40,7 +40,12 @@ __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U
 #pragma unroll
     for (int d = 0; d < 3; ++d) aa += fabs(u * M(d * 3) + v * M(d * 3 + 1) + w * M(d * 3 + 2)) + c * T(Gm[d * n3]);
     aa *= Ji;
-    const T bb = T(kv) * ri * T(Gm[3 * n3]) * Ji * Ji;
+    T kvn = T(kv);
+    if (sutherland) {  // mu(T) / mu_ref by Sutherland's law (Eq. sutherland)
+      const T th = p * ri * T(Rinv) * T(inv_Tref);
+      kvn = kvn * T(1.4042) * th * sqrt(th) / (th + T(0.4042));
+    }
+    const T bb = kvn * ri * T(Gm[3 * n3]) * Ji * Ji;
     if (!isfinite(aa) || !isfinite(bb)) bad = 1;
     lc = fmax(lc, double(aa));
     lv = fmax(lv, double(bb));
@@ -282,11 +287,13 @@ cudaError_t launch_cfl(dg_ctx* c, bool report_only) {
   if (c->prm.precision == DG_FP32_BULK) {
     DG_DISPATCH(c->N, (k_cfl<NN, float><<<nb, 256, 0, c->stream>>>((int)c->E, c->U, c->metric, c->metric32, c->cflgeo,
                                                                  c->prm.gamma, c->prm.gamma - 1.0, 1.0 / c->prm.R, kv,
-                                                                 c->prm.viscous, c->scal)));
+                                                                 c->prm.viscous, c->prm.sutherland,
+                                                                 1.0 / c->prm.T_ref, c->scal)));
   } else {
     DG_DISPATCH(c->N, (k_cfl<NN, double><<<nb, 256, 0, c->stream>>>((int)c->E, c->U, c->metric, c->metric32,
                                                                   c->cflgeo, c->prm.gamma, c->prm.gamma - 1.0,
-                                                                  1.0 / c->prm.R, kv, c->prm.viscous, c->scal)));
+                                                                  1.0 / c->prm.R, kv, c->prm.viscous,
+                                                                  c->prm.sutherland, 1.0 / c->prm.T_ref, c->scal)));
   }
   if (report_only)
     k_dt_report<<<1, 1, 0, c->stream>>>(c->scal, c->prm.cfl, c->prm.dfl, c->N, c->prm.viscous);

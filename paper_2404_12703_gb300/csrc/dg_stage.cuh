@@ -101,6 +101,21 @@ __device__ __forceinline__ T pick(double d, float f) {
   if constexpr (sizeof(T) == sizeof(float)) return f;
   else return d;
 }
+
+// viscosity and heat conductivity at a node of (shifted) temperature Tt:
+// constant, or Sutherland's law (Eq. sutherland) with lambda = kappa mu
+template <typename T>
+__device__ __forceinline__ void visc_coeffs(const StageArgs& a, const CaseParams& cp, T Tt, T& mu, T& lam) {
+  const T mu0 = pick<T>(cp.mu, cp.fmu);
+  if (!a.sutherland) {
+    mu = mu0;
+    lam = pick<T>(cp.lam, cp.flam);
+    return;
+  }
+  const T th = (Tt + pick<T>(cp.Tr, cp.fTr)) * pick<T>(a.inv_Tref, a.f_inv_Tref);
+  mu = mu0 * T(1.4042) * th * sqrt(th) / (th + T(0.4042));
+  lam = mu * pick<T>(a.kappa, a.f_kappa);
+}
 __device__ __forceinline__ double case_dt(const StageArgs& a, int c) {
   return a.cases ? a.cases[c < 0 ? 0 : c].dt : a.scal->dt;
 }
@@ -452,10 +467,12 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
     const T* pgS = G + (size_t)ee.y * 12 * n3 + vS;
 #pragma unroll
     for (int k = 0; k < 12; ++k) { gM[k] = pgM[k * n3]; gS[k] = pgS[k * n3]; }
-    T tau[6], W[3], fvM[4], fvS[4];
-    viscous_parts(gM, qM.u, qM.v, qM.w, pick<T>(cp.mu, cp.fmu), pick<T>(cp.lam, cp.flam), tau, W);
+    T tau[6], W[3], fvM[4], fvS[4], vmu, vlam;
+    visc_coeffs<T>(a, cp, qM.Tt, vmu, vlam);
+    viscous_parts(gM, qM.u, qM.v, qM.w, vmu, vlam, tau, W);
     viscous_flux_n(tau, W, sn, fvM);
-    viscous_parts(gS, qS.u, qS.v, qS.w, pick<T>(cp.mu, cp.fmu), pick<T>(cp.lam, cp.flam), tau, W);
+    visc_coeffs<T>(a, cp, qS.Tt, vmu, vlam);
+    viscous_parts(gS, qS.u, qS.v, qS.w, vmu, vlam, tau, W);
     viscous_flux_n(tau, W, sn, fvS);
 #pragma unroll
     for (int k = 0; k < 4; ++k) f[1 + k] -= T(0.5) * (fvM[k] + fvS[k]);
@@ -549,7 +566,13 @@ struct VolumeSmem {
   // per-element stride of the primitives: a multiple of 4 floats in FP32, so
   // that every element's float4 view starts 16-byte aligned
   static constexpr int pstride = aos ? 6 * ((S::n3 + 3) & ~3) : 6 * S::n3;
-  static constexpr size_t n_t = 2 * n2p + S::EPB * (pstride + (nJ + 5 + 15) * S::n3);  // Dsplit, Dhat, P, J, G, A
+  // viscous / FV fluxes: FP32 keeps the four viscous components of a node in
+  // one float4 (element stride padded like the primitives)
+  static constexpr int gstride = aos ? 5 * ((S::n3 + 3) & ~3) : 5 * S::n3;
+  // per-direction two-point sums: only the FP64 pair tasks need them (the
+  // FP32 per-node sums stay in registers)
+  static constexpr int nA = aos ? 0 : 15;
+  static constexpr size_t n_t = 2 * n2p + S::EPB * (pstride + nJ * S::n3 + gstride + nA * S::n3);
   static constexpr size_t bytes = sizeof(double) * n_dbl + sizeof(T) * n_t;
 };
 
@@ -569,8 +592,8 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   T* sDh = sDs + L::n2p;                                                       // [n2] Dhat
   T* sP = sDh + L::n2p;                  // [EPB][6][n3] rho u v w p' H', halved (FP32: [n3] float4 + [n3] float2)
   T* sJ = sP + EPB * L::pstride;         // [EPB][9][n3] metrics, halved (FP32: [3][n3] float4)
-  T* sG = sJ + EPB * L::nJ * n3;         // [EPB][5][n3] viscous / FV fluxes
-  T* sA = sG + EPB * 5 * n3;             // [EPB][3][5][n3] two-point sums
+  T* sG = sJ + EPB * L::nJ * n3;         // [EPB][5][n3] viscous / FV fluxes (FP32 viscous: [n3] float4)
+  T* sA = sG + EPB * L::gstride;         // [EPB][3][5][n3] two-point sums (FP64 only)
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
   // slots past the last element redo the last element, free slots of a
   // serving pool compute on what they hold; neither stores (see k_lift)
@@ -590,7 +613,8 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   }
   T* P = sP + le * L::pstride;
   T* Jm = sJ + le * L::nJ * n3;
-  T* G = sG + le * 5 * n3;
+  T* G = sG + le * L::gstride;
+  float4* G4 = reinterpret_cast<float4*>(G);
   // FP32 views of the same memory
   float4* P4 = reinterpret_cast<float4*>(P);
   float2* P2 = reinterpret_cast<float2*>(P + 4 * n3);
@@ -600,7 +624,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
     if constexpr (aos) return reinterpret_cast<const float*>(J4 + d * n3 + node)[c];
     else return Jm[(d * 3 + c) * n3 + node];
   };
-  T* A = sA + le * 15 * n3;
+  T* A = sA + le * L::nA * n3;
   const double H_ref = cp.Hr;
   double U[5];
   double p_full;
@@ -643,7 +667,11 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   T accC[5] = {0, 0, 0, 0, 0};  // convective DG volume term
   T acc[5] = {0, 0, 0, 0, 0};   // viscous volume + surface terms
   T tau[6] = {0, 0, 0, 0, 0, 0}, W[3] = {0, 0, 0};
-  if (a.viscous) viscous_parts(g, me.u, me.v, me.w, pick<T>(cp.mu, cp.fmu), pick<T>(cp.lam, cp.flam), tau, W);
+  if (a.viscous) {
+    T vmu, vlam;
+    visc_coeffs<T>(a, cp, me.Tt, vmu, vlam);
+    viscous_parts(g, me.u, me.v, me.w, vmu, vlam, tau, W);
+  }
   // ---- split-form KEP volume integral ----
   // FP64 (bound by the FP64 pipe): one line per task; every unordered pair
   // (i, alpha) of the line forms the symmetric two-point flux once and adds
@@ -681,12 +709,12 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
         s3 += dv * (fr * u2 + pp * m2);
         s4 += dv * (fr * H);
       }
-      T* Ad = A + d * 5 * n3;
-      Ad[t] = s0;
-      Ad[n3 + t] = s1;
-      Ad[2 * n3 + t] = s2;
-      Ad[3 * n3 + t] = s3;
-      Ad[4 * n3 + t] = s4;
+      // same association as the FP64 path's (A_0 + A_1) + A_2
+      if (d == 0) {
+        accC[0] = s0, accC[1] = s1, accC[2] = s2, accC[3] = s3, accC[4] = s4;
+      } else {
+        accC[0] += s0, accC[1] += s1, accC[2] += s2, accC[3] += s3, accC[4] += s4;
+      }
     }
   }
   if constexpr (kPairs)
@@ -751,8 +779,12 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
         const T nv[3] = {T(2) * Jc(d, 0, t), T(2) * Jc(d, 1, t), T(2) * Jc(d, 2, t)};
         T fv[4];
         viscous_flux_n(tau, W, nv, fv);
+        if constexpr (aos) {
+          G4[t] = make_float4(fv[0], fv[1], fv[2], fv[3]);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) G[k * n3 + t] = fv[k];
+          for (int k = 0; k < 4; ++k) G[k * n3 + t] = fv[k];
+        }
       }
       __syncwarp();
       __syncthreads();
@@ -762,8 +794,16 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
         for (int al = 0; al < n; ++al) {
           const T c = sDh[id * n + al];
           const int nb = base + al * str[d];
+          if constexpr (aos) {
+            const float4 gv = G4[nb];
+            acc[1] -= c * gv.x;
+            acc[2] -= c * gv.y;
+            acc[3] -= c * gv.z;
+            acc[4] -= c * gv.w;
+          } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) acc[1 + k] -= c * G[k * n3 + nb];
+            for (int k = 0; k < 4; ++k) acc[1 + k] -= c * G[k * n3 + nb];
+          }
         }
       }
       __syncwarp();
@@ -772,8 +812,10 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   }
   __syncwarp();
   __syncthreads();
+  if constexpr (kPairs) {
 #pragma unroll
-  for (int k = 0; k < 5; ++k) accC[k] = (A[k * n3 + t] + A[(5 + k) * n3 + t]) + A[(10 + k) * n3 + t];
+    for (int k = 0; k < 5; ++k) accC[k] = (A[k * n3 + t] + A[(5 + k) * n3 + t]) + A[(10 + k) * n3 + t];
+  }
 
   // ---- shock capturing: indicator and FV sub-cell blending (Sec. 2.3) ----
   if (a.shock) {
@@ -915,6 +957,11 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.f_Rinv = (float)a.Rinv;
   a.f_mu = (float)a.mu;
   a.f_lam = (float)a.lam;
+  a.sutherland = c->prm.sutherland;
+  a.inv_Tref = 1.0 / c->prm.T_ref;
+  a.kappa = c->prm.gamma * c->prm.R / ((c->prm.gamma - 1.0) * c->prm.Pr);
+  a.f_inv_Tref = (float)a.inv_Tref;
+  a.f_kappa = (float)a.kappa;
   a.riemann = c->prm.riemann;
   a.viscous = c->prm.viscous;
   a.shock = c->prm.shock_capturing;

@@ -81,6 +81,10 @@ struct StageArgs {
   const Ops* ops;
   double gamma, gm1, Rinv, mu, lam;
   float f_gamma, f_gm1, f_Rinv, f_mu, f_lam;  // FP32 copies (FP32-bulk kernels)
+  // Sutherland's law: mu(T) at every node, lambda = kappa mu(T)
+  int sutherland;
+  double inv_Tref, kappa;
+  float f_inv_Tref, f_kappa;
   int riemann, viscous, shock;
   double alpha_min, alpha_max, alpha_force;
   // output: either Ut (mode 0) or the RK update (mode 1)

@@ -43,7 +43,8 @@ class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double), ("mu", C.c_double),
                 ("riemann", C.c_int), ("viscous", C.c_int), ("shock_capturing", C.c_int),
                 ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("cfl", C.c_double),
-                ("dfl", C.c_double), ("precision", C.c_int), ("alpha_force", C.c_double)]
+                ("dfl", C.c_double), ("precision", C.c_int), ("alpha_force", C.c_double),
+                ("sutherland", C.c_int), ("T_ref", C.c_double)]
 
 
 class MeshDesc(C.Structure):

@@ -294,3 +294,38 @@ def test_sod_tube_with_blending_converges_to_exact():
         assert al[np.abs(xc - 1.3504) < h].max() > 0
     assert errs[1] < 0.8 * errs[0], errs
     assert errs[1] < 0.05
+
+
+def test_sutherland_operator_at_reference_temperature():
+    """A state whose temperature is T_ref at every node (density p / (R T_ref)
+    with the Taylor-Green pressure field) has the same right-hand side and
+    time step with Sutherland's law as with the constant mu_ref; at another
+    uniform temperature the viscous part scales by mu(T) / mu_ref."""
+    N = 3
+    m = W.box_mesh(N, (3, 3, 3), curved=0.1, seed=4)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    Tref = 0.45
+    Ut = W.tgv_state(m["xyz"], Ma=0.5)
+    r, u, v, w, p = [np.asarray(a) for a in _tgv_prims(Ut)]
+    U = W.prim_to_cons(p / Tref, u, v, w, p).reshape(m["E"], -1, 5)
+    const = O.params(mu=0.01)
+    suth = O.params(mu=0.01, sutherland=True, T_ref=Tref)
+    a, b = M.rhs(U, const), M.rhs(U, suth)
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+    assert abs(M.dt(U, const)[0] - M.dt(U, suth)[0]) <= 1e-14 * M.dt(U, const)[0]
+    # uniform T = 2 T_ref: viscous contribution times mu(2 T_ref) / mu_ref
+    T2 = 2 * Tref
+    U2 = W.prim_to_cons(p / T2, u, v, w, p).reshape(m["E"], -1, 5)
+    inv = O.params(mu=0.0, viscous=False)
+    vis_c = M.rhs(U2, const) - M.rhs(U2, inv)
+    vis_s = M.rhs(U2, suth) - M.rhs(U2, inv)
+    fac = 1.4042 * 2 ** 1.5 / (2 + 0.4042)
+    assert np.abs(vis_s - fac * vis_c).max() <= 1e-10 * np.abs(vis_s).max()
+
+
+def _tgv_prims(U):
+    U = U.reshape(-1, 5)
+    r = U[:, 0]
+    u, v, w = U[:, 1] / r, U[:, 2] / r, U[:, 3] / r
+    p = 0.4 * (U[:, 4] - 0.5 * r * (u * u + v * v + w * w))
+    return r, u, v, w, p

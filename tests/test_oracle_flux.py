@@ -195,3 +195,36 @@ def test_viscous_flux_frame_invariance():
     fr = O.point_visc(Ur, Gr, R @ n, prm)
     np.testing.assert_allclose(fr[[0, 4]], f[[0, 4]], rtol=1e-13, atol=1e-14)
     np.testing.assert_allclose(fr[1:4], R @ f[1:4], rtol=1e-13, atol=1e-14)
+
+
+def _state_at_T(T, rho=1.3, u=(0.3, -0.2, 0.5), R=1.0, gamma=1.4):
+    return prim_to_cons(np.array(rho), np.array(u[0]), np.array(u[1]), np.array(u[2]),
+                        np.array(rho * R * T), gamma)
+
+
+def test_sutherland_viscous_flux_special_cases():
+    """Sutherland's law (Eq. sutherland) through the whole viscous flux: at
+    T = T_ref it gives mu_ref; it grows like sqrt(T) for T >> T_ref and like
+    T^(3/2) for T << T_ref; the heat flux follows mu (constant Pr)."""
+    rng = np.random.default_rng(3)
+    g = rng.normal(size=(4, 3))
+    nv = np.array([0.3, -0.8, 0.5])
+    Tref = 0.7
+    const = O.params(mu=2e-3)
+    suth = O.params(mu=2e-3, sutherland=True, T_ref=Tref)
+
+    def ratio(T):
+        U = _state_at_T(T)
+        fs, fc = O.point_visc(U, g, nv, suth), O.point_visc(U, g, nv, const)
+        r = fs[1:] / fc[1:]
+        assert np.allclose(r, r[0], rtol=1e-13, atol=0)  # stress and heat flux scale alike
+        return r[0]
+
+    assert abs(ratio(Tref) - 1.0) < 1e-14
+    # T >> T_ref: mu(4T) / mu(T) -> 2
+    assert abs(ratio(4e6 * Tref) / ratio(1e6 * Tref) - 2.0) < 1e-6
+    # T << T_ref: mu(T) -> (1.4042 / 0.4042) (T/T_ref)^(3/2)
+    th = 1e-8
+    assert abs(ratio(th * Tref) / (1.4042 / 0.4042 * th ** 1.5) - 1.0) < 1e-6
+    # the Euler part has no viscous flux: the mass component is zero
+    assert O.point_visc(_state_at_T(2.0), g, nv, suth)[0] == 0.0

@@ -140,3 +140,21 @@ def test_resident_dof_cap_admits_in_order():
     assert waits[0] < waits[1] < waits[2]
     assert waits[1] >= 0.5 * services[0]
     assert waits[2] >= waits[1] + 0.5 * services[1]
+
+
+def test_fp32_bulk_alone_and_in_the_mix_are_bitwise_equal():
+    """FP32-bulk cases carry their own reference state, so their results too
+    do not depend on the other cases of a launch."""
+    torch, dg = gpu_or_skip()
+    t_end = 0.04
+    built = [make(*c) for c in CASES[:3]]
+    alone = []
+    for m, U0, mu in built:
+        srv = dg.Server(POOLS, max_cases=8, precision=dg.FP32_BULK)
+        alone.append(srv.wait(srv.submit(m, U0, t_end, mu=mu))[0])
+        srv.close()
+    srv = dg.Server(POOLS, max_cases=8, precision=dg.FP32_BULK)
+    tickets = [srv.submit(m, U0, t_end, mu=mu) for m, U0, mu in built]
+    for tk, Ua in zip(tickets, alone):
+        np.testing.assert_array_equal(srv.wait(tk)[0], Ua)
+    srv.close()

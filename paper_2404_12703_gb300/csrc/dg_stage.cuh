@@ -67,6 +67,20 @@ struct TBuf<float> {
 };
 
 // ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, 8 bytes per thread and call)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// waits until at most K of this thread's committed groups are still in flight
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Shifted primitive state and the fluxes written in it
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -561,8 +575,10 @@ struct VolumeSmem {
   static constexpr bool aos = sizeof(T) == sizeof(float);
   static constexpr int n2p = (S::n2 + 3) & ~3;
   static constexpr int nJ = aos ? 12 : 9;
-  // Vinv, indicator scratch (even count: the T arrays start 16-byte aligned)
-  static constexpr size_t n_dbl = (S::n2 + S::EPB * (2 * S::n3 + 4 * S::n2) + 1) & ~size_t(1);
+  // Vinv, indicator scratch, FP32: the node's state and RK register copied in
+  // asynchronously (even count: the T arrays start 16-byte aligned)
+  static constexpr int nUd = aos ? 10 * S::n3 : 0;
+  static constexpr size_t n_dbl = (S::n2 + S::EPB * (2 * S::n3 + 4 * S::n2 + nUd) + 1) & ~size_t(1);
   // per-element stride of the primitives: a multiple of 4 floats in FP32, so
   // that every element's float4 view starts 16-byte aligned
   static constexpr int pstride = aos ? 6 * ((S::n3 + 3) & ~3) : 6 * S::n3;
@@ -595,6 +611,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   T* sG = sJ + EPB * L::nJ * n3;         // [EPB][5][n3] viscous / FV fluxes (FP32 viscous: [n3] float4)
   T* sA = sG + EPB * L::gstride;         // [EPB][3][5][n3] two-point sums (FP64 only)
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
+  double* sUd = sX + EPB * (2 * n3 + 4 * n2) + le * L::nUd;  // FP32: [2][5][n3] U and dU of the element
   // slots past the last element redo the last element, free slots of a
   // serving pool compute on what they hold; neither stores (see k_lift)
   const int ei = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
@@ -632,8 +649,24 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   T g[12];
   {
     const double* u = a.U + (size_t)e * 5 * n3 + t;
+    if constexpr (aos) {
+      // the state now, the RK register (read only at the end) in a second group
 #pragma unroll
-    for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
+      for (int k = 0; k < 5; ++k) cp_async8(sUd + k * n3 + t, u + k * n3);
+      cp_async_commit();
+      if (MODE == 1 && !a.first_stage) {
+        const double* du = a.dU + (size_t)e * 5 * n3 + t;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) cp_async8(sUd + (5 + k) * n3 + t, du + k * n3);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();
+#pragma unroll
+      for (int k = 0; k < 5; ++k) U[k] = sUd[k * n3 + t];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
+    }
     me = shifted_prim<T>(U, a.gm1, a.Rinv, cp, &p_full);
     // halved values: every arithmetic mean of the two-point flux is then one
     // addition, bit-identical to (a + b) / 2
@@ -878,6 +911,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
       }
     }
   }
+  if constexpr (aos) cp_async_wait<0>();
   if (!valid) return;
 
   // ---- SurfInt: face nodes receive +-f* lhat ----
@@ -916,9 +950,12 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
     double* uo = a.Urk + (size_t)e * 5 * n3 + t;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      const double r = a.first_stage ? dt * Ut[k] : a.rkA * du[k * n3] + dt * Ut[k];
+      // FP32-bulk: the state and the RK register from the shared-memory copies
+      const double duk = aos ? sUd[(5 + k) * n3 + t] : du[k * n3];
+      const double uk = aos ? sUd[k * n3 + t] : U[k];
+      const double r = a.first_stage ? dt * Ut[k] : a.rkA * duk + dt * Ut[k];
       du[k * n3] = r;
-      uo[k * n3] = U[k] + a.rkB * r;
+      uo[k * n3] = uk + a.rkB * r;
     }
   }
 }

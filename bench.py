@@ -490,6 +490,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     solver = dg.Solver(m, stream=stream)
     solver.set_state(U0)
+    # launch configuration chosen by the library's autotuner on this workload
+    tune64 = solver.autotune()
 
     def barrier():
         torch.cuda.synchronize()
@@ -568,6 +570,7 @@ def run_ours(args):
     if not args.no_fp32:
         s32 = dg.Solver(m, stream=stream, precision=dg.FP32_BULK)
         s32.set_state(U0)
+        tune32 = s32.autotune()
         s32.step(args.warmup)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -598,6 +601,7 @@ def run_ours(args):
         fp32 = {
             "value": world * dof * STAGES / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
             "speedup_vs_fp64": ms_step / ms32, "dtype": "f32 arithmetic, f64 state/RK/metrics/reductions",
+            "autotune": {"config": tune32[0], "variant_ms": tune32[1]},
             "kernels": k32,
             "roofline": {"bound": "hbm", "kernel": "k_volume<7,1,float>",
                          "achieved": VOLUME32_BYTES_PER_DOF * dof / (vol32 * 1e-3) / 1e9,
@@ -644,6 +648,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_desc(nel),
             "pid_s": 1.0 / (value / world), "finite": finite, "t_end": tfinal,
             "gpu_launches": launches, "kernels": kernels, "roofline": roofline,
+            "autotune": {"config": tune64[0], "variant_ms": tune64[1]},
             "e2e": {"value": world * dof * STAGES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32, "shock_tube": shock, "compressible_tgv": comp,

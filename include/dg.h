@@ -155,6 +155,29 @@ int dg_advance(dg_ctx* ctx, double t_end, int64_t max_steps, double* t_out, int6
    arrays have 5 entries.  Synchronises after every step. */
 int dg_profile_step(dg_ctx* ctx, int n_steps, double dt, double* ms, int64_t* launches);
 
+/* Autotuner of the stage kernels' launch configuration (the paper plans
+   launch-configuration tuning, Sec. 3.2; this is the library's own).  Times
+   every launch variant on the context's current state and keeps the fastest:
+   elements per thread block of the lifting and volume kernels (the default,
+   about 256 threads, or twice as many elements), the volume kernel's thread
+   mapping for the split-form sums (FP64: one task per line pair, or one per
+   node) and the side kernels' block size (128 or 256 threads).  Only scratch
+   arrays are written; the state is unchanged.  config (may be NULL, 4 ints):
+   lift elements per block, volume elements per block, line pairs (1) or per
+   node (0), side block size.  ms (may be NULL, 8 doubles): mean time per
+   launch of each variant (-1 where a variant does not exist), in the order
+   lift D, lift 2D, volume D default mapping, volume D other mapping, volume
+   2D default, volume 2D other, side kernels at 256, at 128.  Synchronises.
+   Elements per block change no arithmetic; the volume mapping changes the
+   summation order of the split-form sums (both within the FP64 parity). */
+int dg_autotune(dg_ctx* ctx, int* config, double* ms);
+
+/* Sets (config, 4 ints as above; 0 / -1 entries select the defaults) or
+   reads back the launch configuration.  DG_ERR_ARG for a value that is not
+   one of the variants. */
+int dg_set_config(dg_ctx* ctx, const int* config);
+int dg_get_config(const dg_ctx* ctx, int* config);
+
 /* Time step the CFL rule gives for the context's state (synchronises). */
 int dg_time_step(dg_ctx* ctx, double* dt);
 
@@ -179,7 +202,10 @@ int dg_kinetic(dg_ctx* ctx, double* out);
  * on a second stream while the resident cases keep stepping, retires cases
  * that reached their end time, and records each case's time to solution.
  * Per-element arithmetic does not depend on the other cases of a launch, so a
- * case's result is the same alone and in any mix.
+ * case's result is the same alone and in any mix.  Each pool's launch
+ * configuration is autotuned on its first cases (elements per block and side
+ * block sizes only: the volume kernel keeps its default thread mapping, so
+ * that the results do not depend on the tuning either).
  * ------------------------------------------------------------------------ */
 typedef struct dg_server dg_server;
 

@@ -711,6 +711,56 @@ int dg_profile_step(dg_ctx* c, int n_steps, double dt, double* ms, int64_t* laun
   return DG_OK;
 }
 
+static void variants_of(int N, int& D, bool& lift2, bool& vol2) {
+  const int n3 = (N + 1) * (N + 1) * (N + 1);
+  D = n3 >= 256 ? 1 : 256 / n3;
+  lift2 = 2 * D * n3 <= 1024;
+  vol2 = 2 * D * n3 <= 512;
+}
+
+int dg_autotune(dg_ctx* c, int* config, double* ms) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  double t[8];
+  cudaError_t e = launch_autotune(c, t);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_autotune");
+  destroy_graph(c);  // the next step captures the chosen variants
+  if (config) dg_get_config(c, config);
+  if (ms) memcpy(ms, t, sizeof(t));
+  return DG_OK;
+}
+
+int dg_set_config(dg_ctx* c, const int* config) {
+  if (!c || !config) return fail(DG_ERR_ARG, "ctx or config is NULL");
+  int D;
+  bool lift2, vol2;
+  variants_of(c->N, D, lift2, vol2);
+  const int le = config[0], ve = config[1], pr = config[2], sb = config[3];
+  if (!(le == 0 || le == D || (lift2 && le == 2 * D))) return fail(DG_ERR_ARG, "lift elements per block");
+  if (!(ve == 0 || ve == D || (vol2 && ve == 2 * D))) return fail(DG_ERR_ARG, "volume elements per block");
+  if (!(pr == -1 || pr == 0 || pr == 1)) return fail(DG_ERR_ARG, "volume mapping");
+  if (pr == 1 && c->prm.precision == DG_FP32_BULK) return fail(DG_ERR_ARG, "line pairs are an FP64 mapping");
+  if (!(sb == 0 || sb == 128 || sb == 256)) return fail(DG_ERR_ARG, "side block size");
+  c->cfg.lift_epb = le;
+  c->cfg.vol_epb = ve;
+  c->cfg.vol_pairs = pr;
+  c->cfg.side_block = sb == 0 ? 256 : sb;
+  destroy_graph(c);
+  return DG_OK;
+}
+
+int dg_get_config(const dg_ctx* c, int* config) {
+  if (!c || !config) return fail(DG_ERR_ARG, "ctx or config is NULL");
+  int D;
+  bool lift2, vol2;
+  variants_of(c->N, D, lift2, vol2);
+  config[0] = c->cfg.lift_epb > 0 ? c->cfg.lift_epb : D;
+  config[1] = c->cfg.vol_epb > 0 ? c->cfg.vol_epb : D;
+  config[2] = c->cfg.vol_pairs >= 0 ? c->cfg.vol_pairs : (c->prm.precision == DG_FP32_BULK ? 0 : 1);
+  config[3] = c->cfg.side_block;
+  return DG_OK;
+}
+
 int dg_time_step(dg_ctx* c, double* dt) {
   if (!c || !dt) return fail(DG_ERR_ARG, "ctx or dt is NULL");
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");

@@ -51,10 +51,24 @@ cudaError_t launch_cfl(dg_ctx* c, bool report_only);
 
 // raises the dynamic shared-memory limits of the kernels of degree N
 cudaError_t init_kernel_attributes(int N);
-cudaError_t init_kernel_attributes_fp32(int N);
 
-// FP32-bulk evaluation (dg_rhs32.cu), same contract as launch_rhs
-cudaError_t launch_rhs_fp32(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first_stage);
+// stage kernels of one degree, both precisions (dg_stage_n<K>.cu)
+#define DG_DECLARE_STAGE_N(K)                                                                    \
+  cudaError_t stage_attrs_n##K();                                                                \
+  cudaError_t stage_launch_n##K(dg_ctx* c, const double* U, int mode, double A, double B, int f); \
+  cudaError_t stage_autotune_n##K(dg_ctx* c, double* ms);
+DG_DECLARE_STAGE_N(1)
+DG_DECLARE_STAGE_N(2)
+DG_DECLARE_STAGE_N(3)
+DG_DECLARE_STAGE_N(4)
+DG_DECLARE_STAGE_N(5)
+DG_DECLARE_STAGE_N(6)
+DG_DECLARE_STAGE_N(7)
+#undef DG_DECLARE_STAGE_N
+
+// autotuner of the stage kernels' launch variants (ms: 8 timings, see
+// stage_autotune in dg_stage.cuh)
+cudaError_t launch_autotune(dg_ctx* c, double* ms);
 
 // reference state of the shifted primitives from the context's state
 cudaError_t launch_refs(dg_ctx* c);

@@ -232,16 +232,42 @@ __global__ void k_debug_fstar(int E, const int* __restrict__ elem_side, const S*
 // host launchers
 // ---------------------------------------------------------------------------
 cudaError_t init_kernel_attributes(int N) {
-  cudaError_t e = cudaSuccess;
-  DG_DISPATCH(N, (e = stage_set_attrs<NN, double>()));
-  if (e != cudaSuccess) return e;
-  return init_kernel_attributes_fp32(N);
+  switch (N) {
+    case 1: return stage_attrs_n1();
+    case 2: return stage_attrs_n2();
+    case 3: return stage_attrs_n3();
+    case 4: return stage_attrs_n4();
+    case 5: return stage_attrs_n5();
+    case 6: return stage_attrs_n6();
+    case 7: return stage_attrs_n7();
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_rhs(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first) {
-  if (c->prm.precision == DG_FP32_BULK) return launch_rhs_fp32(c, U, mode, rkA, rkB, first);
-  DG_DISPATCH(c->N, return (stage_launch<NN, double>(c, U, mode, rkA, rkB, first)));
-  return cudaSuccess;
+  switch (c->N) {
+    case 1: return stage_launch_n1(c, U, mode, rkA, rkB, first);
+    case 2: return stage_launch_n2(c, U, mode, rkA, rkB, first);
+    case 3: return stage_launch_n3(c, U, mode, rkA, rkB, first);
+    case 4: return stage_launch_n4(c, U, mode, rkA, rkB, first);
+    case 5: return stage_launch_n5(c, U, mode, rkA, rkB, first);
+    case 6: return stage_launch_n6(c, U, mode, rkA, rkB, first);
+    case 7: return stage_launch_n7(c, U, mode, rkA, rkB, first);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_autotune(dg_ctx* c, double* ms) {
+  switch (c->N) {
+    case 1: return stage_autotune_n1(c, ms);
+    case 2: return stage_autotune_n2(c, ms);
+    case 3: return stage_autotune_n3(c, ms);
+    case 4: return stage_autotune_n4(c, ms);
+    case 5: return stage_autotune_n5(c, ms);
+    case 6: return stage_autotune_n6(c, ms);
+    case 7: return stage_autotune_n7(c, ms);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // reference state of the shifted primitives: zero on the FP64 path; on the

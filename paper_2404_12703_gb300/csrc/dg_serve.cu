@@ -777,6 +777,24 @@ static void worker_loop(dg_server* s) {
         // an executable graph still in flight is released when it completes
         const double tc0 = now_s();
         cudaError_t e = rebuild_lists(s);
+        // a pool's launch configuration is tuned once, when its cases first
+        // fill the GPU several times over (about four waves of default
+        // blocks: tuning on a few small cases would pick for tiny grids)
+        int nsm = 152;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
+        for (auto& kv : s->pools) {
+          dg_ctx* pc = kv.second.ctx;
+          const int n3 = pc->n3, D = n3 >= 256 ? 1 : 256 / n3;
+          if (e != cudaSuccess || pc->tuned || pc->n_elem_list < (int64_t)4 * 2 * nsm * D) continue;
+          cudaStream_t keep = pc->stream;
+          pc->stream = s->stream;
+          // the thread mapping stays the default one: a case's result must not
+          // depend on which cases the pool was tuned on
+          pc->tune_keep_mapping = true;
+          double ms[8];
+          e = launch_autotune(pc, ms);
+          pc->stream = keep;
+        }
         if (e == cudaSuccess) e = capture_step(s);
         {
           std::lock_guard<std::mutex> lk(s->m);

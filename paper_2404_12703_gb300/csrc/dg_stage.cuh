@@ -37,10 +37,14 @@
 
 namespace dg {
 
-template <int N>
+// Element blocks: EPB elements per thread block, one thread per node.
+// EPB_ = 0 takes the default (about 256 threads); the autotuner may pick
+// twice as many elements per block.
+template <int N, int EPB_ = 0>
 struct Shape {
   static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-  static constexpr int EPB = n3 >= 256 ? 1 : 256 / n3;  // elements per block
+  static constexpr int EPB_DEFAULT = n3 >= 256 ? 1 : 256 / n3;
+  static constexpr int EPB = EPB_ > 0 ? EPB_ : EPB_DEFAULT;  // elements per block
   static constexpr int THREADS = EPB * n3;
   // FP32-bulk volume kernel: at least 1024 resident threads per SM (it is
   // latency-bound); the FP64 one is bound by the FP64 pipe at one block
@@ -296,9 +300,9 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
 // ---------------------------------------------------------------------------
 // Lifted gradients (weak form, Eq. lifting)
 // ---------------------------------------------------------------------------
-template <int N, typename T>
-__global__ void __launch_bounds__(Shape<N>::THREADS) k_lift(StageArgs a) {
-  using S = Shape<N>;
+template <int N, typename T, int EPB_ = 0>
+__global__ void __launch_bounds__(Shape<N, EPB_>::THREADS) k_lift(StageArgs a) {
+  using S = Shape<N, EPB_>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   constexpr int n2p = (n2 + 3) & ~3;  // keeps the arrays below 16-byte aligned
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -567,12 +571,13 @@ __device__ double element_alpha(double rp, double* sT1, double* sT2, double* sRo
 }
 
 // shared-memory layout of k_volume: FP64 part first, then the T arrays
-template <int N, typename T>
+template <int N, typename T, int EPB_ = 0, bool PAIRS = sizeof(T) == sizeof(double)>
 struct VolumeSmem {
-  using S = Shape<N>;
+  using S = Shape<N, EPB_>;
   // FP32: node-major primitives (float4 + float2) and metrics (one float4 per
   // direction), so a partner is read with three loads
   static constexpr bool aos = sizeof(T) == sizeof(float);
+  static_assert(!(aos && PAIRS), "the line-pair two-point sums are an FP64 mapping");
   static constexpr int n2p = (S::n2 + 3) & ~3;
   static constexpr int nJ = aos ? 12 : 9;
   // Vinv, indicator scratch, FP32: the node's state and RK register copied in
@@ -585,9 +590,9 @@ struct VolumeSmem {
   // viscous / FV fluxes: FP32 keeps the four viscous components of a node in
   // one float4 (element stride padded like the primitives)
   static constexpr int gstride = aos ? 5 * ((S::n3 + 3) & ~3) : 5 * S::n3;
-  // per-direction two-point sums: only the FP64 pair tasks need them (the
-  // FP32 per-node sums stay in registers)
-  static constexpr int nA = aos ? 0 : 15;
+  // per-direction two-point sums: only the line-pair tasks need them (the
+  // per-node sums stay in registers)
+  static constexpr int nA = PAIRS ? 15 : 0;
   static constexpr size_t n_t = 2 * n2p + S::EPB * (pstride + nJ * S::n3 + gstride + nA * S::n3);
   static constexpr size_t bytes = sizeof(double) * n_dbl + sizeof(T) * n_t;
 };
@@ -595,12 +600,15 @@ struct VolumeSmem {
 // ---------------------------------------------------------------------------
 // Volume integral + SurfInt + ApplyJac (+ RK update)
 // ---------------------------------------------------------------------------
-template <int N, int MODE, typename T>
-__global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_blocks<T>()) k_volume(StageArgs a) {
-  using S = Shape<N>;
+// PAIRS: each unordered pair of a line forms its two-point flux once (one
+// task per line, FP64); otherwise each node sums over all its partners.
+template <int N, int MODE, typename T, int EPB_ = 0, bool PAIRS = sizeof(T) == sizeof(double)>
+__global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::template vol_min_blocks<T>())
+    k_volume(StageArgs a) {
+  using S = Shape<N, EPB_>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   extern __shared__ __align__(16) unsigned char smraw[];
-  using L = VolumeSmem<N, T>;
+  using L = VolumeSmem<N, T, EPB_, PAIRS>;
   constexpr bool aos = L::aos;
   double* sVi = reinterpret_cast<double*>(smraw);  // [n2] Vinv (FP64)
   double* sX = sVi + n2;                           // [EPB][2 n3 + 4 n2] indicator scratch (FP64)
@@ -712,28 +720,38 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
   // halves the flux evaluations.  FP32 (bound by latency, not arithmetic):
   // one node per thread over all its partners, which keeps every thread busy.
   // Each direction has its own sum array.
-  constexpr bool kPairs = sizeof(T) == sizeof(double);
+  constexpr bool kPairs = PAIRS;
   if constexpr (!kPairs) {
     const int idl[3] = {t % n, (t / n) % n, t / n2};
-    const float4 pi4 = P4[t];
-    const float2 pi2 = P2[t];
+    // halved primitives and direction-d metrics of a node, either layout
+    auto node = [&](int d, int v, T& r, T& u0, T& u1, T& u2, T& pp, T& H, T& j0, T& j1, T& j2) {
+      if constexpr (aos) {
+        const float4 a4 = P4[v];
+        const float2 a2 = P2[v];
+        const float4 jj = J4[d * n3 + v];
+        r = a4.x, u0 = a4.y, u1 = a4.z, u2 = a4.w, pp = a2.x, H = a2.y, j0 = jj.x, j1 = jj.y, j2 = jj.z;
+      } else {
+        r = P[v], u0 = P[n3 + v], u1 = P[2 * n3 + v], u2 = P[3 * n3 + v], pp = P[4 * n3 + v], H = P[5 * n3 + v];
+        j0 = Jm[(d * 3) * n3 + v], j1 = Jm[(d * 3 + 1) * n3 + v], j2 = Jm[(d * 3 + 2) * n3 + v];
+      }
+    };
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
       const int id = idl[d], base = t - id * str[d];
-      const float4 ji = J4[d * n3 + t];
+      T ri, ui, vvi, wi, pi, Hi, j0, j1, j2;
+      node(d, t, ri, ui, vvi, wi, pi, Hi, j0, j1, j2);
       T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0), s4 = T(0);
 #pragma unroll
       for (int al = 0; al < n; ++al) {
         if (al == id) continue;
         const int va = base + al * str[d];
-        const float4 pa4 = P4[va];
-        const float2 pa2 = P2[va];
-        const float4 ja = J4[d * n3 + va];
-        const T m0 = ji.x + ja.x, m1 = ji.y + ja.y, m2 = ji.z + ja.z;
-        const T rho = pi4.x + pa4.x;
-        const T u0 = pi4.y + pa4.y, u1 = pi4.z + pa4.z, u2 = pi4.w + pa4.w;
-        const T pp = pi2.x + pa2.x;
-        const T H = pi2.y + pa2.y;
+        T ra, ua, va_, wa, pa, Ha, ja0, ja1, ja2;
+        node(d, va, ra, ua, va_, wa, pa, Ha, ja0, ja1, ja2);
+        const T m0 = j0 + ja0, m1 = j1 + ja1, m2 = j2 + ja2;
+        const T rho = ri + ra;
+        const T u0 = ui + ua, u1 = vvi + va_, u2 = wi + wa;
+        const T pp = pi + pa;
+        const T H = Hi + Ha;
         const T fr = rho * (u0 * m0 + u1 * m1 + u2 * m2);
         const T dv = sDs[id * n + al];
         s0 += dv * fr;
@@ -742,7 +760,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
         s3 += dv * (fr * u2 + pp * m2);
         s4 += dv * (fr * H);
       }
-      // same association as the FP64 path's (A_0 + A_1) + A_2
+      // same association as the line-pair path's (A_0 + A_1) + A_2
       if (d == 0) {
         accC[0] = s0, accC[1] = s1, accC[2] = s2, accC[3] = s3, accC[4] = s4;
       } else {
@@ -1018,25 +1036,96 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   return a;
 }
 
-template <int N, typename T>
+template <int N, typename T, int E = 0>
 inline size_t lift_smem_bytes() {
-  using S = Shape<N>;
+  using S = Shape<N, E>;
   return sizeof(T) * (((S::n2 + 3) & ~3) + S::EPB * 16 * S::n3);
+}
+
+// Launch variants the autotuner chooses among: the default elements per
+// block D and 2D (lifting up to 1024 threads, volume up to 512), and for FP64
+// the volume kernel's two thread mappings.
+template <int N, typename T>
+struct Variants {
+  static constexpr int D = Shape<N>::EPB_DEFAULT;
+  static constexpr int n3 = Shape<N>::n3;
+  static constexpr bool lift2 = 2 * D * n3 <= 1024;
+  static constexpr bool vol2 = 2 * D * n3 <= 512;
+  static constexpr bool fp64 = sizeof(T) == sizeof(double);
+};
+
+template <int N, typename T, int E>
+inline void launch_lift(const StageArgs& a, cudaStream_t st) {
+  using S = Shape<N, E>;
+  k_lift<N, T, E><<<(unsigned)((a.E + S::EPB - 1) / S::EPB), S::THREADS, lift_smem_bytes<N, T, E>(), st>>>(a);
+}
+template <int N, int MODE, typename T, int E, bool PR>
+inline void launch_vol(const StageArgs& a, cudaStream_t st) {
+  using S = Shape<N, E>;
+  k_volume<N, MODE, T, E, PR>
+      <<<(unsigned)((a.E + S::EPB - 1) / S::EPB), S::THREADS, VolumeSmem<N, T, E, PR>::bytes, st>>>(a);
+}
+template <int N, typename T>
+inline void launch_side(const StageArgs& a, int block, cudaStream_t st, bool prims) {
+  const int64_t side_nodes = (int64_t)a.S * Shape<N>::n2;
+  const int b = block == 128 ? 128 : 256;
+  const unsigned g = (unsigned)((side_nodes + b - 1) / b);
+  if (prims) k_surf_prims<N, T><<<g, b, 0, st>>>(a);
+  else k_surf_flux<N, T><<<g, b, 0, st>>>(a);
+}
+
+template <int N, typename T>
+inline void lift_variant(const StageArgs& a, int epb, cudaStream_t st) {
+  using V = Variants<N, T>;
+  if constexpr (V::lift2) {
+    if (epb == 2 * V::D) return launch_lift<N, T, 2 * V::D>(a, st);
+  }
+  launch_lift<N, T, 0>(a, st);
+}
+template <int N, int MODE, typename T>
+inline void vol_variant(const StageArgs& a, int epb, int pairs, cudaStream_t st) {
+  using V = Variants<N, T>;
+  if constexpr (MODE == 0) {
+    // dg_rhs and the diagnostics: the default variant
+    launch_vol<N, 0, T, 0, V::fp64>(a, st);
+  } else {
+    const bool pr = V::fp64 && (pairs < 0 ? true : pairs != 0);
+    if constexpr (V::vol2) {
+      if (epb == 2 * V::D) {
+        if constexpr (V::fp64) {
+          if (!pr) return launch_vol<N, 1, T, 2 * V::D, false>(a, st);
+        }
+        return launch_vol<N, 1, T, 2 * V::D, V::fp64>(a, st);
+      }
+    }
+    if constexpr (V::fp64) {
+      if (!pr) return launch_vol<N, 1, T, 0, false>(a, st);
+    }
+    launch_vol<N, 1, T, 0, V::fp64>(a, st);
+  }
 }
 
 template <int N, typename T>
 cudaError_t stage_set_attrs() {
-  cudaFuncSetAttribute(k_lift<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lift_smem_bytes<N, T>());
-  cudaFuncSetAttribute(k_volume<N, 0, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)VolumeSmem<N, T>::bytes);
-  cudaFuncSetAttribute(k_volume<N, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)VolumeSmem<N, T>::bytes);
+  using V = Variants<N, T>;
+  const int maxsm = 227 * 1024;
+  auto lift = [&](auto kern, size_t bytes) {
+    if (bytes <= (size_t)maxsm) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  lift(k_lift<N, T, 0>, lift_smem_bytes<N, T, 0>());
+  if constexpr (V::lift2) lift(k_lift<N, T, 2 * V::D>, lift_smem_bytes<N, T, 2 * V::D>());
+  lift(k_volume<N, 0, T, 0, V::fp64>, VolumeSmem<N, T, 0, V::fp64>::bytes);
+  lift(k_volume<N, 1, T, 0, V::fp64>, VolumeSmem<N, T, 0, V::fp64>::bytes);
+  if constexpr (V::fp64) lift(k_volume<N, 1, T, 0, false>, VolumeSmem<N, T, 0, false>::bytes);
+  if constexpr (V::vol2) {
+    lift(k_volume<N, 1, T, 2 * V::D, V::fp64>, VolumeSmem<N, T, 2 * V::D, V::fp64>::bytes);
+    if constexpr (V::fp64) lift(k_volume<N, 1, T, 2 * V::D, false>, VolumeSmem<N, T, 2 * V::D, false>::bytes);
+  }
   return cudaGetLastError();
 }
 
 template <int N, typename T>
 cudaError_t stage_launch(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first) {
-  using S = Shape<N>;
   StageArgs a = make_stage_args(c, U);
   a.Ut = c->Ut;
   a.Urk = c->U;
@@ -1044,29 +1133,138 @@ cudaError_t stage_launch(dg_ctx* c, const double* U, int mode, double rkA, doubl
   a.rkA = rkA;
   a.rkB = rkB;
   a.first_stage = first;
-  const int64_t side_nodes = (int64_t)a.S * S::n2;
-  const unsigned sb = (unsigned)((side_nodes + 255) / 256);
-  const unsigned eb = (unsigned)((a.E + S::EPB - 1) / S::EPB);
   if (a.E == 0) return cudaSuccess;
+  const StageConfig& g = c->cfg;
   if (c->prm.viscous) {
     prof_begin(c, PK_SURF_PRIMS);
-    k_surf_prims<N, T><<<sb, 256, 0, c->stream>>>(a);
+    launch_side<N, T>(a, g.side_block, c->stream, true);
     prof_end(c);
     prof_begin(c, PK_LIFT);
-    k_lift<N, T><<<eb, S::THREADS, lift_smem_bytes<N, T>(), c->stream>>>(a);
+    lift_variant<N, T>(a, g.lift_epb, c->stream);
     prof_end(c);
     count_launch(2);
   }
   prof_begin(c, PK_SURF_FLUX);
-  k_surf_flux<N, T><<<sb, 256, 0, c->stream>>>(a);
+  launch_side<N, T>(a, g.side_block, c->stream, false);
   prof_end(c);
   prof_begin(c, PK_VOLUME);
-  if (mode == 0) k_volume<N, 0, T><<<eb, S::THREADS, VolumeSmem<N, T>::bytes, c->stream>>>(a);
-  else k_volume<N, 1, T><<<eb, S::THREADS, VolumeSmem<N, T>::bytes, c->stream>>>(a);
+  if (mode == 0) vol_variant<N, 0, T>(a, g.vol_epb, g.vol_pairs, c->stream);
+  else vol_variant<N, 1, T>(a, g.vol_epb, g.vol_pairs, c->stream);
   prof_end(c);
   count_launch(2);
   return cudaGetLastError();
 }
+
+// Autotuner: times every launch variant of the stage kernels on the context's
+// own data and keeps the fastest of each kernel.  The runs write only scratch
+// arrays: the lifted gradients and surface fluxes (recomputed by every
+// stage), and an RK update redirected into the Ut and public-layout buffers;
+// the state is untouched.  ms[]: per variant, mean ms over the timed
+// repetitions, in the order lift D, lift 2D, volume (D, default mapping),
+// volume (D, other mapping), volume (2D, default), volume (2D, other), side
+// 256, side 128 (-1 where a variant does not exist).
+template <int N, typename T>
+cudaError_t stage_autotune(dg_ctx* c, double* ms) {
+  using V = Variants<N, T>;
+  StageArgs a = make_stage_args(c, c->U);
+  a.Ut = c->Ut;
+  a.Urk = c->Ut;
+  a.dU = c->Upub;
+  a.rkA = 0.5;
+  a.rkB = 0.5;
+  a.first_stage = 0;
+  for (int i = 0; i < 8; ++i) ms[i] = -1.0;
+  if (a.E == 0) return cudaSuccess;
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaMemsetAsync(c->Upub, 0, sizeof(double) * c->E * 5 * c->n3, st);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int reps = 3;
+  auto timed = [&](auto&& launch) -> double {
+    launch();  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    count_launch(reps + 1);
+    return t / reps;
+  };
+  StageConfig best = c->cfg;
+  if (e == cudaSuccess) {
+    // inputs of the volume kernel: gradients and surface fluxes
+    if (c->prm.viscous) {
+      launch_side<N, T>(a, 256, st, true);
+      launch_lift<N, T, 0>(a, st);
+    }
+    launch_side<N, T>(a, 256, st, false);
+    count_launch(3);
+    if (c->prm.viscous) {
+      ms[0] = timed([&] { launch_lift<N, T, 0>(a, st); });
+      best.lift_epb = V::D;
+      if constexpr (V::lift2) {
+        ms[1] = timed([&] { launch_lift<N, T, 2 * V::D>(a, st); });
+        if (ms[1] < ms[0]) best.lift_epb = 2 * V::D;
+      }
+    }
+    double vbest = 1e30;
+    auto vol = [&](int slot, double t, int epb, int pairs) {
+      ms[slot] = t;
+      if (t < vbest) {
+        vbest = t;
+        best.vol_epb = epb;
+        best.vol_pairs = pairs;
+      }
+    };
+    const bool other = !c->tune_keep_mapping;  // also try the other thread mapping
+    vol(2, timed([&] { launch_vol<N, 1, T, 0, V::fp64>(a, st); }), V::D, V::fp64 ? 1 : 0);
+    if constexpr (V::fp64) {
+      if (other) vol(3, timed([&] { launch_vol<N, 1, T, 0, false>(a, st); }), V::D, 0);
+    }
+    if constexpr (V::vol2) {
+      vol(4, timed([&] { launch_vol<N, 1, T, 2 * V::D, V::fp64>(a, st); }), 2 * V::D, V::fp64 ? 1 : 0);
+      if constexpr (V::fp64) {
+        if (other) vol(5, timed([&] { launch_vol<N, 1, T, 2 * V::D, false>(a, st); }), 2 * V::D, 0);
+      }
+    }
+    ms[6] = timed([&] {
+      if (c->prm.viscous) launch_side<N, T>(a, 256, st, true);
+      launch_side<N, T>(a, 256, st, false);
+    });
+    ms[7] = timed([&] {
+      if (c->prm.viscous) launch_side<N, T>(a, 128, st, true);
+      launch_side<N, T>(a, 128, st, false);
+    });
+    best.side_block = ms[7] < ms[6] ? 128 : 256;
+    e = cudaGetLastError();
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e == cudaSuccess) {
+    c->cfg = best;
+    c->tuned = true;
+  }
+  return e;
+}
+
+// Entry points of one degree (each degree is its own translation unit)
+#define DG_STAGE_ENTRY_POINTS(K)                                                                  \
+  cudaError_t stage_attrs_n##K() {                                                                \
+    cudaError_t e = stage_set_attrs<K, double>();                                                 \
+    if (e == cudaSuccess) e = stage_set_attrs<K, float>();                                        \
+    return e;                                                                                     \
+  }                                                                                               \
+  cudaError_t stage_launch_n##K(dg_ctx* c, const double* U, int mode, double A, double B, int f) { \
+    return c->prm.precision == DG_FP32_BULK ? stage_launch<K, float>(c, U, mode, A, B, f)         \
+                                            : stage_launch<K, double>(c, U, mode, A, B, f);       \
+  }                                                                                               \
+  cudaError_t stage_autotune_n##K(dg_ctx* c, double* ms) {                                        \
+    return c->prm.precision == DG_FP32_BULK ? stage_autotune<K, float>(c, ms)                     \
+                                            : stage_autotune<K, double>(c, ms);                   \
+  }
 
 #define DG_DISPATCH(N_, CALL)                      \
   switch (N_) {                                    \

@@ -59,6 +59,14 @@ struct CaseData {
   float f_mu, f_lam, f_ref_p, f_ref_H, f_ref_T, f_pad;  // FP32 copies (FP32-bulk kernels)
 };
 
+// Launch configuration of the stage kernels (the autotuner's choice).
+struct StageConfig {
+  int lift_epb = 0;     // elements per block of the lifting kernel (0: default)
+  int vol_epb = 0;      // elements per block of the volume kernel (0: default)
+  int vol_pairs = -1;   // 1: line-pair two-point sums, 0: per node, -1: default
+  int side_block = 256; // threads per block of the side kernels (128 or 256)
+};
+
 // Per-stage launch parameters of the RHS kernels.
 struct StageArgs {
   int E, S;
@@ -152,6 +160,10 @@ struct dg_ctx {
   int* side_case = nullptr;
   dg::CaseData* cases = nullptr;
   int n_case_slots = 0;
+  dg::StageConfig cfg;       // launch configuration of the stage kernels
+  bool tuned = false;        // cfg chosen by the autotuner
+  bool tune_keep_mapping = false;  // autotune elements per block and side blocks only
+                                   // (results then do not depend on the tuning)
   int* elem_list = nullptr;  // occupied elements / sides of a serving pool (device)
   int* side_list = nullptr;
   int64_t n_elem_list = 0, n_side_list = 0;

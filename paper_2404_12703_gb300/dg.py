@@ -29,7 +29,8 @@ DEBUG_METRICS, DEBUG_MAPS, DEBUG_GRAD, DEBUG_FSTAR, DEBUG_ALPHA = 0, 1, 2, 3, 4
 SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "dg_poll", "dg_server_stats",
                  "dg_server_destroy")
 EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
-           "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
+           "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_autotune", "dg_set_config", "dg_get_config",
+           "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
            "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
 
 
@@ -85,6 +86,9 @@ def load(path: str | None = None):
             "dg_rhs": (C.c_int, [vp, vp, vp]),
             "dg_step": (C.c_int, [vp, C.c_int, C.c_double]),
             "dg_advance": (C.c_int, [vp, C.c_double, C.c_int64, dp, C.POINTER(C.c_int64)]),
+            "dg_autotune": (C.c_int, [vp, C.POINTER(C.c_int), dp]),
+            "dg_set_config": (C.c_int, [vp, C.POINTER(C.c_int)]),
+            "dg_get_config": (C.c_int, [vp, C.POINTER(C.c_int)]),
             "dg_profile_step": (C.c_int, [vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int64)]),
             "dg_time_step": (C.c_int, [vp, dp]),
             "dg_kinetic": (C.c_int, [vp, dp]),
@@ -256,6 +260,28 @@ class Solver:
         k = C.c_int64()
         _check(self._lib.dg_advance(self._h, float(t_end), int(max_steps), C.byref(t), C.byref(k)))
         return t.value, k.value
+
+    CONFIG_KEYS = ("lift_epb", "vol_epb", "vol_pairs", "side_block")
+    TUNE_KEYS = ("lift_D", "lift_2D", "vol_D", "vol_D_other_mapping", "vol_2D", "vol_2D_other_mapping",
+                 "side_256", "side_128")
+
+    def autotune(self):
+        """Times the stage kernels' launch variants on the current state and
+        keeps the fastest; returns (config, per-variant ms)."""
+        cfg = (C.c_int * 4)()
+        ms = (C.c_double * 8)()
+        _check(self._lib.dg_autotune(self._h, cfg, ms))
+        return dict(zip(self.CONFIG_KEYS, list(cfg))), {k: (v if v >= 0 else None)
+                                                        for k, v in zip(self.TUNE_KEYS, list(ms))}
+
+    def set_config(self, lift_epb=0, vol_epb=0, vol_pairs=-1, side_block=0):
+        cfg = (C.c_int * 4)(lift_epb, vol_epb, vol_pairs, side_block)
+        _check(self._lib.dg_set_config(self._h, cfg))
+
+    def config(self):
+        cfg = (C.c_int * 4)()
+        _check(self._lib.dg_get_config(self._h, cfg))
+        return dict(zip(self.CONFIG_KEYS, list(cfg)))
 
     #: kernel kinds reported by profile_step, in the library's order
     KERNELS = ("cfl", "surf_prims", "lift", "surf_flux", "volume")

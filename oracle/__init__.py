@@ -67,7 +67,8 @@ def _lib(quad: bool = False):
 
         api = {
             "ops": fn("ops", C.c_int, [C.c_int, dp, dp, dp, dp, dp, dp]),
-            "mesh_new": fn("mesh_new", C.c_void_p, [C.c_int, C.c_long, dp, dp, C.c_void_p, ip]),
+            "mesh_new": fn("mesh_new", C.c_void_p, [C.c_int, C.c_long, dp, dp, C.c_void_p, C.c_void_p, C.c_int,
+                                                    C.c_void_p, ip]),
             "mesh_free": fn("mesh_free", None, [C.c_void_p]),
             "connectivity": fn("connectivity", None, [C.c_void_p, ip, ip, ip, ip]),
             "metrics": fn("metrics", None, [C.c_void_p, dp, dp]),
@@ -157,10 +158,14 @@ def rk_coeffs():
 class Mesh:
     """Oracle view of one mesh: connectivity, metrics and the DG operator."""
 
-    def __init__(self, N, xyz, period, quad=False, metric_mask=None):
+    def __init__(self, N, xyz, period, quad=False, metric_mask=None, face_bc=None, bcs=None):
         """``metric_mask``: optional boolean mask over elements; metrics are then
         formed only for those elements and their face neighbours (use the same
-        mask as ``want`` in ``rhs``)."""
+        mask as ``want`` in ``rhs``).  ``face_bc``: [E, 6] boundary-condition row
+        per face (0: a face with a partner; k >= 1: row k - 1 of ``bcs``);
+        ``bcs``: rows of (type, 8 parameters), type 1 isothermal no-slip wall
+        (u_w, v_w, w_w, T_w), 2 adiabatic no-slip wall (u_w, v_w, w_w), 3 slip
+        wall, 4 prescribed state (5 conservative values)."""
         self.N = int(N)
         self.n = self.N + 1
         xyz = _f64(xyz)
@@ -171,8 +176,18 @@ class Mesh:
         mask = None
         if metric_mask is not None:
             mask = np.ascontiguousarray(np.asarray(metric_mask, dtype=np.uint8))
+        fb = bcv = None
+        nbc = 0
+        if face_bc is not None:
+            fb = np.ascontiguousarray(np.asarray(face_bc, dtype=np.int32).reshape(-1))
+            bcv = np.zeros((len(bcs), 9))
+            for k, row in enumerate(bcs):
+                bcv[k, :len(row)] = row
+            nbc = len(bcs)
         self._h = self._api["mesh_new"](self.N, self.E, _dp(xyz.reshape(-1)), _dp(_f64(period)),
-                                        mask.ctypes.data if mask is not None else None, C.byref(st))
+                                        mask.ctypes.data if mask is not None else None,
+                                        fb.ctypes.data if fb is not None else None, nbc,
+                                        bcv.ctypes.data if bcv is not None else None, C.byref(st))
         self.status = st.value
         if self.status != 0:
             self.close()

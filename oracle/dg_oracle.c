@@ -254,6 +254,11 @@ typedef struct {
   int* master;   /* [E*6] 1 if this element side owns the normal */
   int* nbr_node; /* [E*6][n2] partner face node, in partner frame */
   int status;
+  /* boundary conditions: face_bc[E*6] = 0 for a face with a partner, else
+     k in 1..nbc, the row of bcv (type, then 8 parameters) */
+  int* face_bc;
+  int nbc;
+  real bcv[17][9];
 } mesh_t;
 
 static inline long node_of(int n, int i, int j, int k) { return i + (long)n * (j + (long)n * k); }
@@ -349,8 +354,12 @@ static int build_connectivity(mesh_t* M) {
   }
   /* x-wrap: faces whose wrapped centroid sits within tol of 0 from below were
      moved to ~0 by wrap(); nothing else straddles.  Every face needs a partner. */
-  for (long a = 0; a < F && !err; ++a)
-    if (M->nbr_e[a] < 0) err = 2;
+  for (long a = 0; a < F && !err; ++a) {
+    const int bc = M->face_bc ? M->face_bc[a] : 0;
+    if (M->nbr_e[a] < 0 && bc <= 0) err = 2;       /* an open face without a boundary condition */
+    if (M->nbr_e[a] >= 0 && bc > 0) err = 2;       /* a boundary condition on an inner face */
+    if (M->nbr_e[a] < 0) M->master[a] = 1;         /* boundary faces own their normal */
+  }
   free(keys);
   if (err) return -2;
   /* node correspondence by coordinates */
@@ -359,6 +368,7 @@ static int build_connectivity(mesh_t* M) {
       long ef = e * 6 + f;
       long e2 = M->nbr_e[ef];
       int f2 = M->nbr_f[ef];
+      if (e2 < 0) continue;  /* boundary face */
       for (int q = 0; q < n; ++q)
         for (int p = 0; p < n; ++p) {
           const real* xa = &M->xyz[(e * M->n3 + face_node(n, f, p, q)) * 3];
@@ -638,6 +648,82 @@ static int work_alloc(const mesh_t* M, work_t* w) {
   return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Boundary conditions (the paper names wall, farfield and outflow      */
+/* conditions for its application case without formulas; these are the */
+/* readings): per boundary face node, the BR1 lifting value q* and the  */
+/* surface flux f*, from the inner state, its gradients and the outward */
+/* unit normal nu (s: surface element, nv = s nu).                      */
+/*   1 isothermal no-slip wall (u_w, T_w): q* = (u_w, T_w); convective  */
+/*     flux (0, p nu, p u_w.nu); viscous flux F_v at (u_w, T_w) with the */
+/*     inner gradients;                                                 */
+/*   2 adiabatic no-slip wall (u_w): q* = (u_w, T); convective as 1;    */
+/*     viscous F_v at (u_w, T) with no temperature gradient (q.n = 0);  */
+/*   3 slip wall: q* = (u - (u.nu) nu, T); convective (0, p nu, 0); no  */
+/*     viscous flux;                                                    */
+/*   4 prescribed state U_ext: q* = (q + q_ext) / 2; the Riemann flux   */
+/*     between U and U_ext; viscous (F_v(q, g) + F_v(q_ext, g)) / 2.    */
+/* ------------------------------------------------------------------ */
+enum { BC_WALL_ISOTHERMAL = 1, BC_WALL_ADIABATIC = 2, BC_SLIP = 3, BC_STATE = 4 };
+
+static void bc_lift_value(const mesh_t* M, const params_t* P, int bc, const real* q, const real* nu, real* qs) {
+  const real* b = M->bcv[bc];
+  switch ((int)b[0]) {
+    case BC_WALL_ISOTHERMAL:
+      qs[0] = b[1]; qs[1] = b[2]; qs[2] = b[3]; qs[3] = b[4];
+      break;
+    case BC_WALL_ADIABATIC:
+      qs[0] = b[1]; qs[1] = b[2]; qs[2] = b[3]; qs[3] = q[5];
+      break;
+    case BC_SLIP: {
+      real un = q[1] * nu[0] + q[2] * nu[1] + q[3] * nu[2];
+      for (int c = 0; c < 3; ++c) qs[c] = q[1 + c] - un * nu[c];
+      qs[3] = q[5];
+      break;
+    }
+    default: {
+      real qe[6];
+      cons_to_prim(P, &b[1], qe);
+      qs[0] = (q[1] + qe[1]) / 2; qs[1] = (q[2] + qe[2]) / 2;
+      qs[2] = (q[3] + qe[3]) / 2; qs[3] = (q[5] + qe[5]) / 2;
+    }
+  }
+}
+
+static void bc_flux(const mesh_t* M, const params_t* P, int bc, const real* U, const real* q, const real* g,
+                    const real* nu, real s, const real* nv, real* fs) {
+  const real* b = M->bcv[bc];
+  const int type = (int)b[0];
+  if (type == BC_STATE) {
+    real qe[6], fc[5];
+    cons_to_prim(P, &b[1], qe);
+    riemann(P, P->riemann, U, q, &b[1], qe, nu, fc);
+    for (int k = 0; k < 5; ++k) fs[k] = fc[k] * s;
+    if (P->viscous) {
+      real f1[5], f2[5];
+      visc_flux(P, q, g, nv, f1);
+      visc_flux(P, qe, g, nv, f2);
+      for (int k = 0; k < 5; ++k) fs[k] -= (f1[k] + f2[k]) / 2;
+    }
+    return;
+  }
+  const real p = q[4];
+  real uw[3] = {0, 0, 0};
+  if (type != BC_SLIP) { uw[0] = b[1]; uw[1] = b[2]; uw[2] = b[3]; }
+  fs[0] = 0;
+  for (int c = 0; c < 3; ++c) fs[1 + c] = p * nu[c] * s;
+  fs[4] = p * (uw[0] * nu[0] + uw[1] * nu[1] + uw[2] * nu[2]) * s;
+  if (P->viscous && type != BC_SLIP) {
+    real qw[6] = {q[0], uw[0], uw[1], uw[2], q[4], type == BC_WALL_ISOTHERMAL ? b[4] : q[5]};
+    real gw[12];
+    for (int k = 0; k < 12; ++k) gw[k] = g[k];
+    if (type == BC_WALL_ADIABATIC) gw[9] = gw[10] = gw[11] = 0;
+    real fv[5];
+    visc_flux(P, qw, gw, nv, fv);
+    for (int k = 0; k < 5; ++k) fs[k] -= fv[k];
+  }
+}
+
 /* J Ut = -[ V_conv + V_visc + S ], Eq. dgsem with the split-form volume term.
    want: NULL for every element, else a 0/1 mask of the elements whose Ut is
    wanted (their neighbours' gradients are formed as needed). */
@@ -651,7 +737,8 @@ static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
   for (long e = 0; e < E; ++e) {
     if (want && !want[e]) continue;
     needg[e] = 1;
-    for (int f = 0; f < 6; ++f) needg[M->nbr_e[e * 6 + f]] = 1;
+    for (int f = 0; f < 6; ++f)
+      if (M->nbr_e[e * 6 + f] >= 0) needg[M->nbr_e[e * 6 + f]] = 1;
   }
   /* ConsToPrim everywhere */
   for (long v = 0; v < E * n3; ++v) cons_to_prim(P, &U[v * 5], &w->q[v * 6]);
@@ -685,8 +772,25 @@ static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
         if (!M->master[ef]) continue;
         long e2 = M->nbr_e[ef];
         int f2 = M->nbr_f[ef];
-        if (!needg[e] && !needg[e2]) continue;
         real sgn = (f % 2) ? 1 : -1;
+        if (e2 < 0) {  /* boundary face: the condition's lifting value */
+          if (!needg[e]) continue;
+          for (int qq = 0; qq < n; ++qq)
+            for (int p = 0; p < n; ++p) {
+              long vM = face_node(n, f, p, qq);
+              const real* Jam = &M->Ja[((e * n3 + vM) * 3 + f / 2) * 3];
+              real nv[3] = {sgn * Jam[0], sgn * Jam[1], sgn * Jam[2]};
+              real s = RSQRT(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+              real nu[3] = {nv[0] / s, nv[1] / s, nv[2] / s};
+              real qs[4];
+              bc_lift_value(M, P, M->face_bc[ef], &w->q[(e * n3 + vM) * 6], nu, qs);
+              for (int qv = 0; qv < 4; ++qv)
+                for (int x = 0; x < 3; ++x)
+                  w->g[(e * n3 + vM) * 12 + qv * 3 + x] += qs[qv] * sgn * Jam[x] / o->w[(f % 2) ? n - 1 : 0];
+            }
+          continue;
+        }
+        if (!needg[e] && !needg[e2]) continue;
         for (int qq = 0; qq < n; ++qq)
           for (int p = 0; p < n; ++p) {
             long vM = face_node(n, f, p, qq);
@@ -793,8 +897,26 @@ static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
       if (!M->master[ef]) continue;
       long e2 = M->nbr_e[ef];
       int f2 = M->nbr_f[ef];
-      if (want && !want[e] && !want[e2]) continue;
       real sgn = (f % 2) ? 1 : -1;
+      if (e2 < 0) {  /* boundary face */
+        if (want && !want[e]) continue;
+        for (int qq = 0; qq < n; ++qq)
+          for (int p = 0; p < n; ++p) {
+            long vM = face_node(n, f, p, qq);
+            const real* Jam = &M->Ja[((e * n3 + vM) * 3 + f / 2) * 3];
+            real nv[3] = {sgn * Jam[0], sgn * Jam[1], sgn * Jam[2]};
+            real s = RSQRT(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+            real nu[3] = {nv[0] / s, nv[1] / s, nv[2] / s};
+            real fs[5];
+            bc_flux(M, P, M->face_bc[ef], &U[(e * n3 + vM) * 5], &w->q[(e * n3 + vM) * 6],
+                    &w->g[(e * n3 + vM) * 12], nu, s, nv, fs);
+            if (fstar_out)
+              for (int k = 0; k < 5; ++k) fstar_out[(ef * n2 + p + n * qq) * 5 + k] = fs[k];
+            for (int k = 0; k < 5; ++k) w->B[(e * n3 + vM) * 5 + k] += fs[k] / o->w[(f % 2) ? n - 1 : 0];
+          }
+        continue;
+      }
+      if (want && !want[e] && !want[e2]) continue;
       for (int qq = 0; qq < n; ++qq)
         for (int p = 0; p < n; ++p) {
           long vM = face_node(n, f, p, qq);
@@ -940,8 +1062,10 @@ int ORC(ops)(int N, double* x, double* w, double* D, double* Dhat, double* Dspli
 /* metric_mask: NULL, or a 0/1 mask over elements; metrics are then formed only
    for the masked elements and the two rings of face neighbours around them
    (enough for rhs() with the same mask as `want`). */
+/* face_bc (may be NULL: every face has a partner): [E*6] boundary-condition
+   row per face (0: inner face); bc: nbc rows of 9 doubles (type, 8 params) */
 void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, const unsigned char* metric_mask,
-                    int* status) {
+                    const int* face_bc, int nbc, const double* bc, int* status) {
   handle_t* h = (handle_t*)calloc(1, sizeof(handle_t));
   mesh_t* M = &h->M;
   *status = 0;
@@ -957,7 +1081,18 @@ void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, cons
   M->master = (int*)malloc(sizeof(int) * E * 6);
   M->nbr_node = (int*)malloc(sizeof(int) * E * 6 * M->n2);
   to_real(xyz, M->xyz, E * n3 * 3);
-  int st = build_connectivity(M);
+  if (nbc > 16) { *status = -6; nbc = 16; }
+  M->nbc = nbc;
+  for (int k = 0; k < nbc; ++k)
+    for (int c = 0; c < 9; ++c) M->bcv[k + 1][c] = bc[k * 9 + c];
+  if (face_bc) {
+    M->face_bc = (int*)malloc(sizeof(int) * E * 6);
+    for (long a = 0; a < E * 6; ++a) {
+      M->face_bc[a] = face_bc[a];
+      if (face_bc[a] < 0 || face_bc[a] > nbc) *status = -6;
+    }
+  }
+  int st = *status ? *status : build_connectivity(M);
   if (st) { *status = st; }
   unsigned char* need = NULL;
   if (metric_mask && !st) {
@@ -968,12 +1103,14 @@ void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, cons
     for (long e = 0; e < E; ++e) {
       if (!metric_mask[e]) continue;
       ring[e] = 1;
-      for (int f = 0; f < 6; ++f) ring[M->nbr_e[e * 6 + f]] = 1;
+      for (int f = 0; f < 6; ++f)
+        if (M->nbr_e[e * 6 + f] >= 0) ring[M->nbr_e[e * 6 + f]] = 1;
     }
     for (long e = 0; e < E; ++e) {
       if (!ring[e]) continue;
       need[e] = 1;
-      for (int f = 0; f < 6; ++f) need[M->nbr_e[e * 6 + f]] = 1;
+      for (int f = 0; f < 6; ++f)
+        if (M->nbr_e[e * 6 + f] >= 0) need[M->nbr_e[e * 6 + f]] = 1;
     }
     free(ring);
   }
@@ -989,6 +1126,7 @@ void ORC(mesh_free)(void* hv) {
   mesh_t* M = &h->M;
   free(M->xyz); free(M->Ja); free(M->J); free(M->nbr_e); free(M->nbr_f); free(M->master);
   free(M->nbr_node);
+  free(M->face_bc);
   work_free(&h->w);
   free(h);
 }

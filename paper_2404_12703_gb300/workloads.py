@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "lgl_points", "ROTATIONS", "box_mesh", "prim_to_cons", "tgv_state",
-    "density_wave_state", "sod_state", "isentropic_vortex_state",
+    "density_wave_state", "sod_state", "isentropic_vortex_state", "box_face_bc", "couette_state",
     "uniform_state", "random_perturbation",
 ]
 
@@ -66,8 +66,10 @@ assert len(ROTATIONS) == 24
 
 
 def box_mesh(N, nel, length=(2 * math.pi,) * 3, origin=(0.0, 0.0, 0.0),
-             curved=0.0, seed=None, rotate=None, permute=None):
-    """Triply periodic box of ``nel = (nx, ny, nz)`` hexahedra at degree ``N``.
+             curved=0.0, seed=None, rotate=None, permute=None, periodic=(True, True, True)):
+    """Box of ``nel = (nx, ny, nz)`` hexahedra at degree ``N``, periodic in the
+    directions ``periodic`` marks (all three by default); the other directions
+    end in boundary faces (``period`` is 0 there, see ``box_face_bc``).
 
     ``curved`` displaces every node by ``curved * h * s(x)`` in each Cartesian
     direction, with ``s = sin(2 pi x'/Lx) sin(2 pi y'/Ly) sin(2 pi z'/Lz)`` in
@@ -126,12 +128,14 @@ def box_mesh(N, nel, length=(2 * math.pi,) * 3, origin=(0.0, 0.0, 0.0),
 
     # canonical corner vertex ids
     cvid = np.empty((E, 8), dtype=np.int64)
+    px, py, pz = (bool(v) for v in periodic)
+    mx, my, mz = nx + 1, ny + 1, nz + 1  # vertex counts per direction
     for c in range(8):
         bi, bj, bk = c & 1, (c >> 1) & 1, (c >> 2) & 1
-        vx = (ex_all + bi) % nx
-        vy = (ey_all + bj) % ny
-        vz = (ez_all + bk) % nz
-        cvid[:, c] = vx + nx * (vy + ny * vz)
+        vx = (ex_all + bi) % nx if px else ex_all + bi
+        vy = (ey_all + bj) % ny if py else ey_all + bj
+        vz = (ez_all + bk) % nz if pz else ez_all + bk
+        cvid[:, c] = vx + mx * (vy + my * vz)
 
     if not do_rot:
         xyz, corner_vid = X, cvid
@@ -159,9 +163,54 @@ def box_mesh(N, nel, length=(2 * math.pi,) * 3, origin=(0.0, 0.0, 0.0),
     return {
         "N": N, "E": E, "xyz": np.ascontiguousarray(xyz),
         "corner_vid": np.ascontiguousarray(corner_vid),
-        "period": np.array([Lx, Ly, Lz]), "rot": rot, "canon": canon,
+        "period": np.array([Lx if px else 0.0, Ly if py else 0.0, Lz if pz else 0.0]), "rot": rot,
+        "canon": canon,
         "nel": (nx, ny, nz), "length": (Lx, Ly, Lz), "origin": (ox, oy, oz),
     }
+
+
+BOX_SIDES = ("x-", "x+", "y-", "y+", "z-", "z+")
+
+
+def box_face_bc(mesh, side_bc):
+    """Boundary-condition row per element face of a ``box_mesh`` box:
+    ``side_bc`` maps box sides ("x-", "x+", "y-", "y+", "z-", "z+") to a row
+    index k >= 1 (faces inside the box, or on periodic sides, get 0).  Faces
+    are found by their centroid (the local frames may be rotated).  Returns
+    int32 [E, 6]."""
+    N, E = mesh["N"], mesh["E"]
+    n = N + 1
+    X = mesh["xyz"].reshape(E, n, n, n, 3)  # [e, k, j, i, c]
+    faces = [X[:, :, :, 0], X[:, :, :, -1], X[:, :, 0, :], X[:, :, -1, :], X[:, 0], X[:, -1]]
+    out = np.zeros((E, 6), dtype=np.int32)
+    lo = np.asarray(mesh["origin"], dtype=float)
+    hi = lo + np.asarray(mesh["length"], dtype=float)
+    tol = 1e-9 * float(np.max(mesh["length"]))
+    for f, F in enumerate(faces):
+        c = F.reshape(E, -1, 3).mean(axis=1)
+        for d in range(3):
+            if mesh["period"][d] > 0:
+                continue
+            for end, name in ((lo[d], BOX_SIDES[2 * d]), (hi[d], BOX_SIDES[2 * d + 1])):
+                k = side_bc.get(name, 0)
+                if k:
+                    out[np.abs(c[:, d] - end) < tol, f] = k
+    return out
+
+
+def couette_state(xyz, U_wall=1.0, h=1.0, T_wall=1.0, p=1.0, mu=0.01, Pr=0.72, gamma=1.4, R=1.0):
+    """Compressible plane Couette flow between isothermal no-slip walls at
+    y = 0 (at rest) and y = h (moving with U_wall in x), both at T_wall: an
+    exact steady solution of the compressible Navier-Stokes equations with
+    constant mu and lambda = gamma R mu / ((gamma - 1) Pr): u = U_wall y / h,
+    v = w = 0, uniform pressure, T = T_wall + mu U_wall^2 y (h - y) / (2 lambda h^2),
+    rho = p / (R T)."""
+    y = xyz[..., 1]
+    lam = gamma * R * mu / ((gamma - 1.0) * Pr)
+    T = T_wall + mu * U_wall ** 2 * y * (h - y) / (2.0 * lam * h * h)
+    rho = p / (R * T)
+    z = np.zeros_like(y)
+    return prim_to_cons(rho, U_wall * y / h, z, z, np.full_like(y, p), gamma)
 
 
 def prim_to_cons(rho, u, v, w, p, gamma=1.4):

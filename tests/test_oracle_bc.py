@@ -1,0 +1,105 @@
+"""Pins of the oracle's boundary conditions (walls, slip walls, prescribed
+states), by states the discrete operator must hold exactly:
+
+* compressible plane Couette flow (linear velocity, quadratic temperature,
+  uniform pressure) between isothermal no-slip walls is an exact steady
+  solution of the Navier-Stokes equations whose fields the DG space holds
+  exactly for N >= 2, so the operator must vanish to round-off;
+* the same with an adiabatic moving upper wall (its own exact profile);
+* a uniform stream parallel to slip walls, and a uniform stream through
+  prescribed-state boundaries equal to it, on curved rotated meshes;
+* mass (all walls) and total energy (walls at rest, adiabatic) are conserved
+  by the discrete operator in a wall-bounded box."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2404_12703_gb300 import workloads as W
+
+GAM, R, PR = 1.4, 1.0, 0.72
+
+
+def _weights(N):
+    x, w, *_ = O.ops(N)
+    return np.einsum("i,j,k->kji", w, w, w).reshape(-1)
+
+
+def _channel(N, nel=(3, 4, 3), seed=7, curved=0.0):
+    return W.box_mesh(N, nel, length=(2.0, 1.0, 2.0), origin=(0.0, 0.0, 0.0),
+                      periodic=(True, False, True), seed=seed, curved=curved)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_couette_between_isothermal_walls_is_a_discrete_steady_state(N):
+    m = _channel(N)
+    fb = W.box_face_bc(m, {"y-": 1, "y+": 2})
+    mu, Uw, Tw = 0.02, 0.7, 1.3
+    bcs = [(1, 0.0, 0.0, 0.0, Tw), (1, Uw, 0.0, 0.0, Tw)]
+    M = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=bcs)
+    U = W.couette_state(m["xyz"], U_wall=Uw, T_wall=Tw, p=0.9, mu=mu).reshape(m["E"], -1, 5)
+    Ut = M.rhs(U, O.params(mu=mu))
+    # terms of size p / h ~ 3 and mu U / h^2 ~ 0.2 cancel to round-off
+    assert np.abs(Ut).max() < 1e-12, np.abs(Ut).max(axis=(0, 1))
+    # a wrong wall temperature is seen
+    bad = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(1, 0.0, 0.0, 0.0, Tw + 0.1), bcs[1]])
+    assert np.abs(bad.rhs(U, O.params(mu=mu))).max() > 1e-3
+
+
+def test_couette_with_an_adiabatic_moving_wall():
+    """Isothermal wall at rest at y = 0, adiabatic wall moving with U at y = h:
+    T = T_w + mu U^2 (h y - y^2 / 2) / (lambda h^2)."""
+    N = 3
+    m = _channel(N)
+    fb = W.box_face_bc(m, {"y-": 1, "y+": 2})
+    mu, Uw, Tw, p = 0.02, 0.7, 1.3, 0.9
+    lam = GAM * R * mu / ((GAM - 1) * PR)
+    y = m["xyz"][..., 1]
+    T = Tw + mu * Uw ** 2 * (y - 0.5 * y * y) / lam
+    z = np.zeros_like(y)
+    U = W.prim_to_cons(p / (R * T), Uw * y, z, z, np.full_like(y, p)).reshape(m["E"], -1, 5)
+    M = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(1, 0.0, 0.0, 0.0, Tw), (2, Uw, 0.0, 0.0)])
+    assert np.abs(M.rhs(U, O.params(mu=mu))).max() < 1e-12
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_uniform_stream_along_slip_walls_and_through_prescribed_states(N):
+    m = _channel(N, curved=0.1, seed=8)
+    shape = (m["E"], (N + 1) ** 3)
+    # along slip walls: the stream is parallel to them
+    U = W.uniform_state(shape, rho=1.1, vel=(0.4, 0.0, -0.3), p=2.0)
+    fb = W.box_face_bc(m, {"y-": 1, "y+": 1})
+    M = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(3,)])
+    for prm in (O.params(mu=0.01), O.params(viscous=False, riemann="lf")):
+        Ut = M.rhs(U, prm)
+        assert np.abs(Ut).max() < 1e-12 * 10, np.abs(Ut).max()
+    # through prescribed-state boundaries equal to the stream (any direction)
+    U2 = W.uniform_state(shape, rho=1.1, vel=(0.4, 0.5, -0.3), p=2.0)
+    M2 = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(4, *U2[0, 0])])
+    for prm in (O.params(mu=0.01), O.params(riemann="lf")):
+        assert np.abs(M2.rhs(U2, prm)).max() < 1e-12 * 10
+
+
+def test_mass_and_energy_conserved_in_a_walled_box():
+    N = 3
+    m = _channel(N, curved=0.1, seed=9)
+    fb = W.box_face_bc(m, {"y-": 1, "y+": 2})
+    M = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(2, 0.0, 0.0, 0.0), (3,)])
+    U = W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.5).reshape(m["E"], -1, 5), 1e-2, 3)
+    Ut = M.rhs(U, O.params(mu=0.01))
+    _, J = M.metrics()
+    wq = _weights(N)[None, :, None] * J[..., None]
+    tot = (wq * Ut).sum(axis=(0, 1))
+    scale = (wq * np.abs(Ut)).sum(axis=(0, 1))
+    assert abs(tot[0]) <= 1e-13 * scale[0] and abs(tot[4]) <= 1e-13 * scale[4], tot / scale
+    # momentum is not conserved: the walls exert forces
+    assert abs(tot[2]) > 1e-6 * scale[2]
+
+
+def test_open_faces_need_a_boundary_condition():
+    m = _channel(3)
+    with pytest.raises(ValueError):
+        O.Mesh(3, m["xyz"], m["period"])
+    fb = W.box_face_bc(m, {"y-": 1, "y+": 1})
+    fb[0, 0] = 1  # a condition on a face that has a partner
+    with pytest.raises(ValueError):
+        O.Mesh(3, m["xyz"], m["period"], face_bc=fb, bcs=[(3,)])

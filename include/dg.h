@@ -91,7 +91,29 @@ typedef struct {
   int64_t n_elems;             /* number of elements E >= 1      */
   const int64_t* corner_vid;   /* [E][8] host                    */
   const double* xyz;           /* [E][(N+1)^3][3] host            */
+  /* Boundary conditions (all optional: NULL / 0 for a mesh in which every
+     face has a partner).  face_bc: [E][6] host, 0 for a face with a partner,
+     k = 1..n_bc for a boundary face with condition row k - 1 of bc; bc:
+     [n_bc][9] host rows (type, 8 parameters):
+       DG_BC_WALL_ISOTHERMAL (u_w, v_w, w_w, T_w): no-slip wall moving with
+         the (tangential) velocity u_w at temperature T_w; lifting value
+         (u_w, T_w), convective flux (0, p n, p u_w.n), viscous flux at the
+         wall state with the inner gradients;
+       DG_BC_WALL_ADIABATIC (u_w, v_w, w_w): as above with the inner
+         temperature and no heat flux;
+       DG_BC_SLIP: lifting value with the normal velocity removed,
+         convective flux (0, p n, 0), no viscous flux;
+       DG_BC_STATE (rho, rho u, rho v, rho w, rho e): the Riemann flux and
+         BR1 means between the inner and the prescribed state (farfield).
+     The paper names wall and farfield conditions for its application
+     without stating them (Sec. 5.3); these are the library's.  Serving
+     (dg_submit) takes periodic meshes only. */
+  const int* face_bc;
+  int n_bc;
+  const double* bc;
 } dg_mesh_desc;
+
+enum { DG_BC_WALL_ISOTHERMAL = 1, DG_BC_WALL_ADIABATIC = 2, DG_BC_SLIP = 3, DG_BC_STATE = 4 };
 
 typedef struct dg_ctx dg_ctx;
 

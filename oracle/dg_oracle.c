@@ -359,6 +359,10 @@ static int build_connectivity(mesh_t* M) {
     if (M->nbr_e[a] < 0 && bc <= 0) err = 2;       /* an open face without a boundary condition */
     if (M->nbr_e[a] >= 0 && bc > 0) err = 2;       /* a boundary condition on an inner face */
     if (M->nbr_e[a] < 0) M->master[a] = 1;         /* boundary faces own their normal */
+    if (M->nbr_e[a] < 0) {
+      M->nbr_f[a] = -1;
+      for (int pq = 0; pq < n2; ++pq) M->nbr_node[a * n2 + pq] = -1;
+    }
   }
   free(keys);
   if (err) return -2;

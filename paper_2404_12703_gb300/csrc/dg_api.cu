@@ -205,6 +205,7 @@ int alloc_side_arrays(dg_ctx* c, std::string& msg) {
   if (e == cudaSuccess) e = dalloc(c, &c->fstar32, S * 5 * n2);
   if (e == cudaSuccess) e = dalloc(c, &c->side_e, S);
   if (e == cudaSuccess) e = dalloc(c, &c->side_f, S);
+  if (e == cudaSuccess) e = dalloc(c, &c->side_bc, S);
   if (e != cudaSuccess) {
     msg = std::string("side arrays: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
@@ -319,6 +320,8 @@ void dg_destroy(dg_ctx* c) {
   dfree(c, c->side_list);
   dfree(c, c->side_e);
   dfree(c, c->side_f);
+  dfree(c, c->side_bc);
+  dfree(c, c->bcdata);
   dfree(c, c->ops);
   dfree(c, c->scal);
   if (c->scal_host) cudaFreeHost(c->scal_host);
@@ -370,6 +373,7 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
   A(dalloc(c, &c->side_e, S));
   A(dalloc(c, &c->side_f, S));
   A(dalloc(c, &c->side_case, S));
+  A(dalloc(c, &c->side_bc, S));
   A(dalloc(c, &c->ops, 1));
   A(dalloc(c, &c->scal, 1));
   if (e == cudaSuccess) e = cudaMallocHost(&c->scal_host, sizeof(DevScalars));
@@ -394,6 +398,7 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
     A(cudaMemsetAsync(c->nrm32, 0, sizeof(float) * S * 7 * n2, stream));
     A(cudaMemsetAsync(c->elem_case, 0xff, sizeof(int) * E, stream));
     A(cudaMemsetAsync(c->side_case, 0xff, sizeof(int) * S, stream));
+    A(cudaMemsetAsync(c->side_bc, 0xff, sizeof(int) * S, stream));
     A(cudaStreamSynchronize(stream));
   }
   if (e != cudaSuccess) {
@@ -417,6 +422,18 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
   if (!mesh || !mesh->corner_vid || !mesh->xyz) return fail(DG_ERR_ARG, "mesh description incomplete");
   if (mesh->N < 1 || mesh->N > NMAX) return fail(DG_ERR_ARG, "N must be in [1, 7]");
   if (mesh->n_elems < 1 || mesh->n_elems > (int64_t)1 << 26) return fail(DG_ERR_ARG, "bad element count");
+  if (mesh->face_bc) {
+    if (mesh->n_bc < 1 || mesh->n_bc > 64 || !mesh->bc) return fail(DG_ERR_ARG, "face_bc needs 1..64 condition rows");
+    for (int k = 0; k < mesh->n_bc; ++k) {
+      const int type = (int)mesh->bc[k * 9];
+      if (type < DG_BC_WALL_ISOTHERMAL || type > DG_BC_STATE || (double)type != mesh->bc[k * 9])
+        return fail(DG_ERR_ARG, "unknown boundary-condition type");
+      if (type == DG_BC_WALL_ISOTHERMAL && !(mesh->bc[k * 9 + 4] > 0)) return fail(DG_ERR_ARG, "wall temperature must be > 0");
+      if (type == DG_BC_STATE && !(mesh->bc[k * 9 + 1] > 0)) return fail(DG_ERR_ARG, "prescribed density must be > 0");
+    }
+    for (int64_t a = 0; a < 6 * mesh->n_elems; ++a)
+      if (mesh->face_bc[a] < 0 || mesh->face_bc[a] > mesh->n_bc) return fail(DG_ERR_ARG, "face_bc out of range");
+  }
   int st = check_params(params);
   if (st != DG_OK) return st;
   dg_ctx* c = new dg_ctx();
@@ -467,7 +484,19 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
     return r;
   }
   std::string msg;
-  st = build_mesh(c, mesh->corner_vid, mesh->xyz, msg);
+  if (mesh->face_bc) {
+    c->n_bc = mesh->n_bc;
+    e = dalloc(c, &c->bcdata, (size_t)9 * mesh->n_bc);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->bcdata, mesh->bc, sizeof(double) * 9 * mesh->n_bc, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      int r = cuda_fail(e, "boundary conditions");
+      dg_destroy(c);
+      return r;
+    }
+  }
+  st = build_mesh(c, mesh->corner_vid, mesh->xyz, mesh->face_bc, msg);
   if (st != DG_OK) {
     dg_destroy(c);
     return fail(st, msg);

@@ -38,7 +38,8 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
                     std::string& msg);
 
 // device mesh set-up (dg_mesh.cu)
-int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::string& msg);
+// h_face_bc (may be null): [E][6] boundary-condition row + 1 of every face (0: inner)
+int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, const int* h_face_bc, std::string& msg);
 
 // one evaluation of the right-hand side (dg_rhs.cu).
 //   mode 0: write Ut (internal layout) into c->Ut for state U

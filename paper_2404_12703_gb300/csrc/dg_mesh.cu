@@ -82,12 +82,19 @@ __global__ void k_face_insert(int64_t F_total, const long long* cvid, int* table
   atomicOr(err, 4);  // table full (cannot happen with load factor <= 1/2)
 }
 
-__global__ void k_face_check(int64_t F_total, const int* partner, int* master_flag, int* err) {
+// face_bc (may be null): > 0 marks a boundary face (it has no partner and
+// forms a side of its own)
+__global__ void k_face_check(int64_t F_total, const int* partner, const int* face_bc, int* master_flag, int* err) {
   int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (F >= F_total) return;
-  int P = partner[F];
-  if (P < 0 || P >= F_total || partner[P] != (int)F || P == (int)F) {
-    atomicOr(err, 8);  // unmatched face (open boundary) or inconsistent pairing
+  const int P = partner[F];
+  const int bc = face_bc ? face_bc[F] : 0;
+  if (P == -1 && bc > 0) {
+    master_flag[F] = 1;  // boundary face
+    return;
+  }
+  if (P < 0 || P >= F_total || partner[P] != (int)F || P == (int)F || bc != 0) {
+    atomicOr(err, 8);  // open face without a condition, a condition on an inner face, or bad pairing
     master_flag[F] = 0;
     return;
   }
@@ -136,11 +143,20 @@ __global__ void __launch_bounds__(1024) k_scan_flags(int64_t n, const int* flag,
 }
 
 __global__ void k_fill_sides(int64_t F_total, const long long* cvid, const int* partner, const int* master_flag,
-                             const int* side_of, int* elem_side, int2* side_e, int* side_f, int* err) {
+                             const int* side_of, const int* face_bc, int* elem_side, int2* side_e, int* side_f,
+                             int* side_bc, int* err) {
   int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (F >= F_total || !master_flag[F]) return;
   const int P = partner[F];
   const int s = side_of[F];
+  if (P < 0) {  // boundary side: master only, condition row face_bc - 1
+    side_e[s] = make_int2((int)(F / 6), -1);
+    side_f[s] = (int)(F % 6) | (15 << 4);
+    elem_side[F] = s << 4;
+    side_bc[s] = face_bc[F] - 1;
+    return;
+  }
+  side_bc[s] = -1;
   const int eM = (int)(F / 6), fM = (int)(F % 6), eS = P / 6, fS = P % 6;
   long long vm[4], vs[4];
   for (int c = 0; c < 4; ++c) {
@@ -334,8 +350,9 @@ static cudaError_t launch_metrics(dg_ctx* c, const double* d_xyz) {
 }
 
 // Builds maps and geometry.  Returns a DG_* status and an error message.
-int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::string& msg) {
+int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, const int* h_face_bc, std::string& msg) {
   const int64_t E = c->E, F = 6 * E;
+  int* d_fbc = nullptr;
   const int n3 = c->n3;
   long long* d_cvid = nullptr;
   double* d_xyz = nullptr;
@@ -366,18 +383,21 @@ int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::strin
   tmp_alloc(&d_flag, sizeof(int) * F, "allocating flag");
   tmp_alloc(&d_sideof, sizeof(int) * F, "allocating sideof");
   tmp_alloc(&d_misc, sizeof(int) * 4, "allocating misc");
+  if (h_face_bc) tmp_alloc(&d_fbc, sizeof(int) * F, "allocating face_bc");
   if (status == DG_OK) {
     ck(cudaMemcpyAsync(d_cvid, h_cvid, sizeof(long long) * E * 8, cudaMemcpyHostToDevice, c->stream), "copy cvid");
     ck(cudaMemcpyAsync(d_xyz, h_xyz, sizeof(double) * E * n3 * 3, cudaMemcpyHostToDevice, c->stream), "copy xyz");
     ck(cudaMemsetAsync(d_table, 0xff, sizeof(int) * tsize, c->stream), "memset table");
     ck(cudaMemsetAsync(d_partner, 0xff, sizeof(int) * F, c->stream), "memset partner");
     ck(cudaMemsetAsync(d_misc, 0, sizeof(int) * 4, c->stream), "memset misc");
+    if (h_face_bc)
+      ck(cudaMemcpyAsync(d_fbc, h_face_bc, sizeof(int) * F, cudaMemcpyHostToDevice, c->stream), "copy face_bc");
   }
   const unsigned nb = (unsigned)((F + 255) / 256);
   int h_misc[4] = {0, 0, 0, 0};
   if (status == DG_OK) {
     k_face_insert<<<nb, 256, 0, c->stream>>>(F, d_cvid, d_table, tsize - 1, d_partner, d_misc);
-    k_face_check<<<nb, 256, 0, c->stream>>>(F, d_partner, d_flag, d_misc);
+    k_face_check<<<nb, 256, 0, c->stream>>>(F, d_partner, d_fbc, d_flag, d_misc);
     k_scan_flags<<<1, 1024, 0, c->stream>>>(F, d_flag, d_sideof, d_misc + 1);
     count_launch(3);
     ck(cudaGetLastError(), "map kernels");
@@ -386,11 +406,11 @@ int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::strin
   }
   if (status == DG_OK && h_misc[0] != 0) {
     msg = "mesh faces do not pair up (code " + std::to_string(h_misc[0]) +
-          "): every face needs exactly one partner with the same four distinct corner ids "
-          "(a periodic direction needs at least three elements)";
+          "): every face needs exactly one partner with the same four distinct corner ids, "
+          "or a boundary condition if it has none (a periodic direction needs at least three elements)";
     status = DG_ERR_MESH;
   }
-  if (status == DG_OK && h_misc[1] != 3 * E) {
+  if (status == DG_OK && ((!h_face_bc && h_misc[1] != 3 * E) || h_misc[1] < 3 * E)) {
     msg = "unexpected number of sides";
     status = DG_ERR_MESH;
   }
@@ -400,8 +420,8 @@ int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::strin
   }
   if (status == DG_OK) {
     ck(cudaMemsetAsync(d_misc, 0, sizeof(int) * 4, c->stream), "memset misc");
-    k_fill_sides<<<nb, 256, 0, c->stream>>>(F, d_cvid, d_partner, d_flag, d_sideof, c->elem_side, c->side_e,
-                                            c->side_f, d_misc);
+    k_fill_sides<<<nb, 256, 0, c->stream>>>(F, d_cvid, d_partner, d_flag, d_sideof, d_fbc, c->elem_side,
+                                            c->side_e, c->side_f, c->side_bc, d_misc);
     count_launch();
     ck(cudaGetLastError(), "fill sides");
     cudaError_t le = cudaSuccess;
@@ -430,6 +450,7 @@ int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, std::strin
   tmp_free(d_flag);
   tmp_free(d_sideof);
   tmp_free(d_misc);
+  tmp_free(d_fbc);
   return status;
 }
 

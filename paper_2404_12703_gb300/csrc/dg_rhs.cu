@@ -196,6 +196,11 @@ __global__ void k_debug_maps(int E, const int* __restrict__ elem_side, const int
   nbr[x * 3 + 1] = slave ? fM : fS;
   nbr[x * 3 + 2] = slave ? 0 : 1;
   (void)e;
+  if (!slave && ee.y < 0) {  // boundary face: no partner
+    nbr[x * 3 + 1] = -1;
+    for (int pq = 0; pq < n2; ++pq) nodes[x * n2 + pq] = -1;
+    return;
+  }
   for (int pq = 0; pq < n2; ++pq) {
     const int p = pq % n, q = pq / n;
     int a, b;

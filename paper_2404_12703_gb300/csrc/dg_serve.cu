@@ -1060,6 +1060,7 @@ int dg_submit(dg_server* s, const dg_case_desc* d, int64_t* ticket) {
   if (!(d->t_end > 0) || !(d->mu >= 0) || !(d->cfl > 0) ||
       (d->riemann != DG_RIEMANN_ROE && d->riemann != DG_RIEMANN_LF))
     return set_error(DG_ERR_ARG, "dg_submit: bad t_end, mu, cfl or riemann");
+  if (m.face_bc) return set_error(DG_ERR_ARG, "dg_submit: serving takes periodic meshes only");
   Request r;
   r.N = m.N;
   r.E = m.n_elems;

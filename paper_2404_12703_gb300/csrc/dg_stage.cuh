@@ -254,6 +254,82 @@ __device__ __forceinline__ void lf_flux_s(const SPrim<T>& L, const SPrim<T>& R, 
 }
 
 // ---------------------------------------------------------------------------
+// Boundary conditions (rows of include/dg.h's dg_mesh_desc.bc): the BR1
+// lifting value and the surface flux at a boundary side node, from the inner
+// state q (shifted primitives), its gradients g, the outward unit normal nu,
+// the surface element sA and sn = sA nu.  In the shifted variables the
+// momentum flux carries p' (the p_ref part cancels by the discrete metric
+// identities, as on inner sides); the energy flux is the full one, the mass
+// flux being zero at walls.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void bc_lift_value(const StageArgs& a, const CaseParams& cp, int row,
+                                              const SPrim<T>& q, const T nu[3], T qs[4]) {
+  const double* b = a.bcdata + (size_t)row * 9;
+  const int type = (int)b[0];
+  if (type == DG_BC_WALL_ISOTHERMAL) {
+    qs[0] = T(b[1]), qs[1] = T(b[2]), qs[2] = T(b[3]), qs[3] = T(b[4] - cp.Tr);
+  } else if (type == DG_BC_WALL_ADIABATIC) {
+    qs[0] = T(b[1]), qs[1] = T(b[2]), qs[2] = T(b[3]), qs[3] = q.Tt;
+  } else if (type == DG_BC_SLIP) {
+    const T un = q.u * nu[0] + q.v * nu[1] + q.w * nu[2];
+    qs[0] = q.u - un * nu[0], qs[1] = q.v - un * nu[1], qs[2] = q.w - un * nu[2], qs[3] = q.Tt;
+  } else {
+    const double Ue[5] = {b[1], b[2], b[3], b[4], b[5]};
+    const SPrim<T> qe = shifted_prim<T>(Ue, a.gm1, a.Rinv, cp);
+    qs[0] = (q.u + qe.u) / T(2), qs[1] = (q.v + qe.v) / T(2), qs[2] = (q.w + qe.w) / T(2);
+    qs[3] = (q.Tt + qe.Tt) / T(2);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void bc_flux(const StageArgs& a, const CaseParams& cp, int row, const SPrim<T>& q,
+                                        const T g[12], const T nu[3], T sA, const T sn[3], T f[5]) {
+  const double* b = a.bcdata + (size_t)row * 9;
+  const int type = (int)b[0];
+  if (type == DG_BC_STATE) {
+    const double Ue[5] = {b[1], b[2], b[3], b[4], b[5]};
+    const SPrim<T> qe = shifted_prim<T>(Ue, a.gm1, a.Rinv, cp);
+    if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(q, qe, nu, pick<T>(a.gm1, a.f_gm1), pick<T>(cp.Hr, cp.fHr), f);
+    else lf_flux_s(q, qe, nu, pick<T>(a.gamma, a.f_gamma), pick<T>(cp.pr, cp.fpr), f);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f[k] *= sA;
+    if (a.viscous) {
+      T tau[6], W[3], f1[4], f2[4], vmu, vlam;
+      visc_coeffs<T>(a, cp, q.Tt, vmu, vlam);
+      viscous_parts(g, q.u, q.v, q.w, vmu, vlam, tau, W);
+      viscous_flux_n(tau, W, sn, f1);
+      visc_coeffs<T>(a, cp, qe.Tt, vmu, vlam);
+      viscous_parts(g, qe.u, qe.v, qe.w, vmu, vlam, tau, W);
+      viscous_flux_n(tau, W, sn, f2);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f[1 + k] -= (f1[k] + f2[k]) / T(2);
+    }
+    return;
+  }
+  T uw[3] = {T(0), T(0), T(0)};
+  if (type != DG_BC_SLIP) uw[0] = T(b[1]), uw[1] = T(b[2]), uw[2] = T(b[3]);
+  f[0] = T(0);
+  f[1] = q.p * nu[0] * sA;
+  f[2] = q.p * nu[1] * sA;
+  f[3] = q.p * nu[2] * sA;
+  f[4] = (q.p + pick<T>(cp.pr, cp.fpr)) * (uw[0] * nu[0] + uw[1] * nu[1] + uw[2] * nu[2]) * sA;
+  if (a.viscous && type != DG_BC_SLIP) {
+    T gw[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) gw[k] = g[k];
+    if (type == DG_BC_WALL_ADIABATIC) gw[9] = gw[10] = gw[11] = T(0);
+    const T Tw = type == DG_BC_WALL_ISOTHERMAL ? T(b[4] - cp.Tr) : q.Tt;
+    T tau[6], W[3], fv[4], vmu, vlam;
+    visc_coeffs<T>(a, cp, Tw, vmu, vlam);
+    viscous_parts(gw, uw[0], uw[1], uw[2], vmu, vlam, tau, W);
+    viscous_flux_n(tau, W, sn, fv);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f[1 + k] -= fv[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // BR1 surface flux of the lifted primitives
 // ---------------------------------------------------------------------------
 template <int N, typename T>
@@ -271,24 +347,38 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   const int2 ee = a.side_e[s];
   const int sf = a.side_f[s];
   const int fM = sf & 15, fS = (sf >> 4) & 15, flip = sf >> 8;
-  int ps, qs;
-  flip_to_slave<n>(flip, p, q, ps, qs);
-  const int vM = face_vol_node<n>(fM, p, q), vS = face_vol_node<n>(fS, ps, qs);
-  double UM[5], US[5];
-  const double* uM = a.U + (size_t)ee.x * 5 * n3 + vM;
-  const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) { UM[k] = uM[k * n3]; US[k] = uS[k * n3]; }
-  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
-  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
-  const T qa[4] = {T(0.5) * (qM.u + qS.u), T(0.5) * (qM.v + qS.v), T(0.5) * (qM.w + qS.w), T(0.5) * (qM.Tt + qS.Tt)};
-  T sn[3];
+  T sn[3], nu[3];
   if constexpr (sizeof(T) == sizeof(float)) {
     const float* nr = a.nrm32 + (size_t)s * 7 * n2 + pq;
     sn[0] = nr[0], sn[1] = nr[n2], sn[2] = nr[2 * n2];
+    nu[0] = nr[3 * n2], nu[1] = nr[4 * n2], nu[2] = nr[5 * n2];
   } else {
     const double* nr = a.nrm + (size_t)s * 4 * n2 + pq;
     sn[0] = nr[0], sn[1] = nr[n2], sn[2] = nr[2 * n2];
+    const double invd = 1.0 / nr[3 * n2];
+    nu[0] = sn[0] * invd, nu[1] = sn[1] * invd, nu[2] = sn[2] * invd;
+  }
+  const int vM = face_vol_node<n>(fM, p, q);
+  double UM[5];
+  const double* uM = a.U + (size_t)ee.x * 5 * n3 + vM;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) UM[k] = uM[k * n3];
+  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
+  T qa[4];
+  const int brow = a.side_bc ? a.side_bc[s] : -1;
+  if (brow >= 0) {
+    bc_lift_value<T>(a, cp, brow, qM, nu, qa);  // boundary side: the condition's value
+  } else {
+    int ps, qs;
+    flip_to_slave<n>(flip, p, q, ps, qs);
+    const int vS = face_vol_node<n>(fS, ps, qs);
+    double US[5];
+    const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) US[k] = uS[k * n3];
+    const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
+    qa[0] = T(0.5) * (qM.u + qS.u), qa[1] = T(0.5) * (qM.v + qS.v), qa[2] = T(0.5) * (qM.w + qS.w);
+    qa[3] = T(0.5) * (qM.Tt + qS.Tt);
   }
   T* out = TBuf<T>::lflux(a) + (size_t)s * 12 * n2 + pq;
 #pragma unroll
@@ -449,16 +539,6 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   const int2 ee = a.side_e[s];
   const int sf = a.side_f[s];
   const int fM = sf & 15, fS = (sf >> 4) & 15, flip = sf >> 8;
-  int ps, qs;
-  flip_to_slave<n>(flip, p, q, ps, qs);
-  const int vM = face_vol_node<n>(fM, p, q), vS = face_vol_node<n>(fS, ps, qs);
-  double UM[5], US[5];
-  const double* uM = a.U + (size_t)ee.x * 5 * n3 + vM;
-  const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) { UM[k] = uM[k * n3]; US[k] = uS[k * n3]; }
-  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
-  const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
   T sn[3], nu[3], sA;
   if constexpr (sizeof(T) == sizeof(float)) {
     const float* nr = a.nrm32 + (size_t)s * 7 * n2 + pq;
@@ -473,27 +553,55 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
     sA = sAd;
     nu[0] = nr[0] * invd, nu[1] = nr[n2] * invd, nu[2] = nr[2 * n2] * invd;
   }
+  const int vM = face_vol_node<n>(fM, p, q);
+  double UM[5];
+  const double* uM = a.U + (size_t)ee.x * 5 * n3 + vM;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) UM[k] = uM[k * n3];
+  const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
+  const T* G = TBuf<T>::g(a);
   T f[5];
-  if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, pick<T>(a.gm1, a.f_gm1), pick<T>(cp.Hr, cp.fHr), f);
-  else lf_flux_s(qM, qS, nu, pick<T>(a.gamma, a.f_gamma), pick<T>(cp.pr, cp.fpr), f);
+  const int brow = a.side_bc ? a.side_bc[s] : -1;
+  if (brow >= 0) {  // boundary side
+    T gM[12];
+    if (a.viscous) {
+      const T* pgM = G + (size_t)ee.x * 12 * n3 + vM;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) f[k] *= sA;
-  if (a.viscous) {
-    T gM[12], gS[12];
-    const T* G = TBuf<T>::g(a);
-    const T* pgM = G + (size_t)ee.x * 12 * n3 + vM;
-    const T* pgS = G + (size_t)ee.y * 12 * n3 + vS;
+      for (int k = 0; k < 12; ++k) gM[k] = pgM[k * n3];
+    } else {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) { gM[k] = pgM[k * n3]; gS[k] = pgS[k * n3]; }
-    T tau[6], W[3], fvM[4], fvS[4], vmu, vlam;
-    visc_coeffs<T>(a, cp, qM.Tt, vmu, vlam);
-    viscous_parts(gM, qM.u, qM.v, qM.w, vmu, vlam, tau, W);
-    viscous_flux_n(tau, W, sn, fvM);
-    visc_coeffs<T>(a, cp, qS.Tt, vmu, vlam);
-    viscous_parts(gS, qS.u, qS.v, qS.w, vmu, vlam, tau, W);
-    viscous_flux_n(tau, W, sn, fvS);
+      for (int k = 0; k < 12; ++k) gM[k] = T(0);
+    }
+    bc_flux<T>(a, cp, brow, qM, gM, nu, sA, sn, f);
+  } else {
+    int ps, qs;
+    flip_to_slave<n>(flip, p, q, ps, qs);
+    const int vS = face_vol_node<n>(fS, ps, qs);
+    double US[5];
+    const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) f[1 + k] -= T(0.5) * (fvM[k] + fvS[k]);
+    for (int k = 0; k < 5; ++k) US[k] = uS[k * n3];
+    const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
+    if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, pick<T>(a.gm1, a.f_gm1), pick<T>(cp.Hr, cp.fHr), f);
+    else lf_flux_s(qM, qS, nu, pick<T>(a.gamma, a.f_gamma), pick<T>(cp.pr, cp.fpr), f);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f[k] *= sA;
+    if (a.viscous) {
+      T gM[12], gS[12];
+      const T* pgM = G + (size_t)ee.x * 12 * n3 + vM;
+      const T* pgS = G + (size_t)ee.y * 12 * n3 + vS;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) { gM[k] = pgM[k * n3]; gS[k] = pgS[k * n3]; }
+      T tau[6], W[3], fvM[4], fvS[4], vmu, vlam;
+      visc_coeffs<T>(a, cp, qM.Tt, vmu, vlam);
+      viscous_parts(gM, qM.u, qM.v, qM.w, vmu, vlam, tau, W);
+      viscous_flux_n(tau, W, sn, fvM);
+      visc_coeffs<T>(a, cp, qS.Tt, vmu, vlam);
+      viscous_parts(gS, qS.u, qS.v, qS.w, vmu, vlam, tau, W);
+      viscous_flux_n(tau, W, sn, fvS);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f[1 + k] -= T(0.5) * (fvM[k] + fvS[k]);
+    }
   }
   T* out = TBuf<T>::fstar(a) + (size_t)s * 5 * n2 + pq;
 #pragma unroll
@@ -1029,6 +1137,8 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.cases = c->cases;
   a.elem_list = c->elem_list;
   a.side_list = c->side_list;
+  a.side_bc = c->side_bc;
+  a.bcdata = c->bcdata;
   if (c->elem_list) {
     a.E = (int)c->n_elem_list;
     a.S = (int)c->n_side_list;

@@ -111,6 +111,9 @@ struct StageArgs {
   // these (E and S are then their counts), so freed ranges cost nothing
   const int* elem_list;
   const int* side_list;
+  // boundary conditions: row of every side (-1: inner side), rows [n][9]
+  const int* side_bc;
+  const double* bcdata;
 };
 
 }  // namespace dg
@@ -144,6 +147,9 @@ struct dg_ctx {
   int* elem_side = nullptr;  // [E][6]
   int2* side_e = nullptr;    // [S]
   int* side_f = nullptr;     // [S]
+  int* side_bc = nullptr;    // [S] boundary-condition row (-1: inner side)
+  double* bcdata = nullptr;  // [n_bc][9] boundary-condition rows (type, 8 parameters)
+  int n_bc = 0;
   dg::Ops* ops = nullptr;    // device copy of the operators of degree N
   dg::DevScalars* scal = nullptr;
   dg::DevScalars* scal_host = nullptr;  // pinned mirror

@@ -50,7 +50,24 @@ class Params(C.Structure):
 
 class MeshDesc(C.Structure):
     _fields_ = [("N", C.c_int), ("n_elems", C.c_int64), ("corner_vid", C.POINTER(C.c_int64)),
-                ("xyz", C.POINTER(C.c_double))]
+                ("xyz", C.POINTER(C.c_double)), ("face_bc", C.POINTER(C.c_int)), ("n_bc", C.c_int),
+                ("bc", C.POINTER(C.c_double))]
+
+
+BC_WALL_ISOTHERMAL, BC_WALL_ADIABATIC, BC_SLIP, BC_STATE = 1, 2, 3, 4
+
+
+def _bc_arrays(mesh):
+    """(face_bc int32 [E*6], bc float64 [n_bc*9]) of a mesh dict with optional
+    ``face_bc`` [E, 6] and ``bcs`` (rows of type + up to 8 parameters)."""
+    if mesh.get("face_bc") is None:
+        return None, None, 0
+    fb = np.ascontiguousarray(np.asarray(mesh["face_bc"], dtype=np.int32).reshape(-1))
+    rows = mesh.get("bcs") or []
+    bc = np.zeros((max(len(rows), 1), 9))
+    for k, r in enumerate(rows):
+        bc[k, :len(r)] = r
+    return fb, np.ascontiguousarray(bc.reshape(-1)), len(rows)
 
 
 class ServerConfig(C.Structure):
@@ -177,8 +194,12 @@ class Solver:
         cvid = np.ascontiguousarray(mesh["corner_vid"], dtype=np.int64)
         self.E = int(xyz.shape[0])
         self.params = params if params is not None else default_params(**kw)
+        fb, bc, nbc = _bc_arrays(mesh)
+        self._bc_keep = (fb, bc)
         desc = MeshDesc(self.N, self.E, cvid.ctypes.data_as(C.POINTER(C.c_int64)),
-                        xyz.ctypes.data_as(C.POINTER(C.c_double)))
+                        xyz.ctypes.data_as(C.POINTER(C.c_double)),
+                        fb.ctypes.data_as(C.POINTER(C.c_int)) if fb is not None else None, nbc,
+                        bc.ctypes.data_as(C.POINTER(C.c_double)) if bc is not None else None)
         h = C.c_void_p()
         _check(lib.dg_init_mesh(C.byref(h), C.byref(desc), C.byref(self.params), _stream_ptr(stream)))
         self._h = h
@@ -384,7 +405,10 @@ class Server:
         N, E = int(mesh["N"]), int(xyz.shape[0])
         assert U0.size == E * (N + 1) ** 3 * 5
         d = CaseDesc()
-        d.mesh = MeshDesc(N, E, cvid.ctypes.data_as(C.POINTER(C.c_int64)), xyz.ctypes.data_as(C.POINTER(C.c_double)))
+        fb, bc, nbc = _bc_arrays(mesh)
+        d.mesh = MeshDesc(N, E, cvid.ctypes.data_as(C.POINTER(C.c_int64)), xyz.ctypes.data_as(C.POINTER(C.c_double)),
+                          fb.ctypes.data_as(C.POINTER(C.c_int)) if fb is not None else None, nbc,
+                          bc.ctypes.data_as(C.POINTER(C.c_double)) if bc is not None else None)
         d.U0 = U0.ctypes.data_as(C.POINTER(C.c_double))
         d.t_end, d.mu, d.riemann, d.cfl = float(t_end), float(mu), int(riemann), float(cfl)
         t = C.c_int64()

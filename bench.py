@@ -386,6 +386,42 @@ def compressible_bench(dg, torch, stream):
                         "(the paper's 14-stage scheme is not printed in it), CFL 0.9 to t = 3", **out}
 
 
+def channel_bench(dg, torch, stream):
+    """Wall-bounded channel: 16 x 8 x 16 curved elements at N = 7 (1,048,576
+    DOF) on [0, 4] x [0, 1] x [0, 4], periodic in x and z, isothermal no-slip
+    walls at y = 0 (at rest) and y = 1 (moving), Couette flow plus a seeded
+    perturbation, 20 CFL steps in both precisions; the walls' lifting values
+    and fluxes run in the surface kernels."""
+    from paper_2404_12703_gb300 import workloads as W
+    N, mu = 7, 1e-3
+    m = W.box_mesh(N, (16, 8, 16), length=(4.0, 1.0, 4.0), origin=(0.0, 0.0, 0.0),
+                   periodic=(True, False, True), curved=0.1, seed=11)
+    m["face_bc"] = W.box_face_bc(m, {"y-": 1, "y+": 2})
+    m["bcs"] = [(1, 0.0, 0.0, 0.0, 1.0), (1, 1.0, 0.0, 0.0, 1.0)]
+    dof = m["E"] * (N + 1) ** 3
+    U0 = W.random_perturbation(W.couette_state(m["xyz"], U_wall=1.0, T_wall=1.0, p=10.0, mu=mu)
+                               .reshape(m["E"], -1, 5), 1e-3, 11)
+    out = {}
+    for name, prec in (("fp64", dg.FP64), ("fp32_bulk", dg.FP32_BULK)):
+        s = dg.Solver(m, stream=stream, mu=mu, precision=prec)
+        s.set_state(U0)
+        s.step(3)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(20)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        U, t = s.get_state()
+        out[name] = {"ms_per_step": ms, "dof_updates_per_s": dof * STAGES / (ms * 1e-3), "t": t,
+                     "finite": bool(np.isfinite(U).all())}
+        s.close()
+    return {"workload": f"channel 16x8x16 curved elements, N = 7 ({dof} DOF), isothermal no-slip walls "
+                        f"(one moving), Couette + perturbation, Re = 1000, 20 steps", **out}
+
+
 def run_long(args):
     """FP32-bulk against FP64 over a long Taylor-Green run: 32^3 Cartesian
     elements at N = 5 (7,077,888 DOF), Re 1600, Ma 0.1, both precisions from
@@ -623,9 +659,10 @@ def run_ours(args):
     if not args.no_shock and rank == 0:
         shock = shock_tube_bench(dg, torch, stream)
 
-    comp = None
+    comp = chan = None
     if not args.no_shock and rank == 0:
         comp = compressible_bench(dg, torch, stream)
+        chan = channel_bench(dg, torch, stream)
 
     serving = None
     if not args.no_serving and rank == 0:
@@ -652,6 +689,7 @@ def run_ours(args):
             "e2e": {"value": world * dof * STAGES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32, "shock_tube": shock, "compressible_tgv": comp,
+            "channel": chan,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

@@ -104,7 +104,9 @@ typedef struct {
        DG_BC_SLIP: lifting value with the normal velocity removed,
          convective flux (0, p n, 0), no viscous flux;
        DG_BC_STATE (rho, rho u, rho v, rho w, rho e): the Riemann flux and
-         BR1 means between the inner and the prescribed state (farfield).
+         BR1 means between the inner and the prescribed state (farfield);
+       DG_BC_OUTFLOW (p_out): as DG_BC_STATE with the outer state the inner
+         density and velocity at the pressure p_out (subsonic outflow).
      The paper names wall and farfield conditions for its application
      without stating them (Sec. 5.3); these are the library's.  Serving
      (dg_submit) takes periodic meshes only. */
@@ -113,7 +115,7 @@ typedef struct {
   const double* bc;
 } dg_mesh_desc;
 
-enum { DG_BC_WALL_ISOTHERMAL = 1, DG_BC_WALL_ADIABATIC = 2, DG_BC_SLIP = 3, DG_BC_STATE = 4 };
+enum { DG_BC_WALL_ISOTHERMAL = 1, DG_BC_WALL_ADIABATIC = 2, DG_BC_SLIP = 3, DG_BC_STATE = 4, DG_BC_OUTFLOW = 5 };
 
 typedef struct dg_ctx dg_ctx;
 
@@ -176,6 +178,14 @@ int dg_advance(dg_ctx* ctx, double t_end, int64_t max_steps, double* t_out, int6
    3 surface flux, 4 volume integral + SurfInt + ApplyJac + RK update.  Both
    arrays have 5 entries.  Synchronises after every step. */
 int dg_profile_step(dg_ctx* ctx, int n_steps, double dt, double* ms, int64_t* launches);
+
+/* Sponge zone (the paper's application damps outgoing waves in sponge
+   zones, Sec. 5.3): adds the source -sigma (U - U_base) to Ut at every node,
+   in FP64 in both precisions.  sigma: [E][node] host, >= 0; U_base:
+   [E][node][5] host (public layout); sigma NULL removes the sponge.  The
+   time-step rule does not see the source: keep sigma dt of order one or
+   below.  Copies the arrays (synchronises). */
+int dg_set_sponge(dg_ctx* ctx, const double* sigma, const double* U_base);
 
 /* Autotuner of the stage kernels' launch configuration (the paper plans
    launch-configuration tuning, Sec. 3.2; this is the library's own).  Times

@@ -70,6 +70,7 @@ def _lib(quad: bool = False):
             "mesh_new": fn("mesh_new", C.c_void_p, [C.c_int, C.c_long, dp, dp, C.c_void_p, C.c_void_p, C.c_int,
                                                     C.c_void_p, ip]),
             "mesh_free": fn("mesh_free", None, [C.c_void_p]),
+            "set_sponge": fn("set_sponge", None, [C.c_void_p, C.c_void_p, C.c_void_p]),
             "connectivity": fn("connectivity", None, [C.c_void_p, ip, ip, ip, ip]),
             "metrics": fn("metrics", None, [C.c_void_p, dp, dp]),
             "rhs": fn("rhs", C.c_int, [C.c_void_p, dp, dp, dp, C.c_void_p, dp, dp, dp]),
@@ -165,7 +166,7 @@ class Mesh:
         per face (0: a face with a partner; k >= 1: row k - 1 of ``bcs``);
         ``bcs``: rows of (type, 8 parameters), type 1 isothermal no-slip wall
         (u_w, v_w, w_w, T_w), 2 adiabatic no-slip wall (u_w, v_w, w_w), 3 slip
-        wall, 4 prescribed state (5 conservative values)."""
+        wall, 4 prescribed state (5 conservative values), 5 pressure outflow (p_out)."""
         self.N = int(N)
         self.n = self.N + 1
         xyz = _f64(xyz)
@@ -192,6 +193,16 @@ class Mesh:
         if self.status != 0:
             self.close()
             raise ValueError(f"oracle mesh construction failed ({self.status})")
+
+    def set_sponge(self, sigma=None, base=None):
+        """Sponge zone: the source -sigma (U - base) at every node (sigma
+        [E, n^3], base [E, n^3, 5]); None removes it."""
+        if sigma is None:
+            self._api["set_sponge"](self._h, None, None)
+            return
+        self._sg = np.ascontiguousarray(_f64(sigma).reshape(-1))
+        self._sb = np.ascontiguousarray(_f64(base).reshape(-1))
+        self._api["set_sponge"](self._h, self._sg.ctypes.data, self._sb.ctypes.data)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -259,6 +259,9 @@ typedef struct {
   int* face_bc;
   int nbc;
   real bcv[17][9];
+  /* sponge zone (may be NULL): source -sigma (U - U_base) at every node */
+  real* sponge_sigma;  /* [E][n3] */
+  real* sponge_base;   /* [E][n3][5] */
 } mesh_t;
 
 static inline long node_of(int n, int i, int j, int k) { return i + (long)n * (j + (long)n * k); }
@@ -666,11 +669,27 @@ static int work_alloc(const mesh_t* M, work_t* w) {
 /*   3 slip wall: q* = (u - (u.nu) nu, T); convective (0, p nu, 0); no  */
 /*     viscous flux;                                                    */
 /*   4 prescribed state U_ext: q* = (q + q_ext) / 2; the Riemann flux   */
-/*     between U and U_ext; viscous (F_v(q, g) + F_v(q_ext, g)) / 2.    */
+/*     between U and U_ext; viscous (F_v(q, g) + F_v(q_ext, g)) / 2;    */
+/*   5 pressure outflow (p_out): as 4 with U_ext the inner density and  */
+/*     velocity at the pressure p_out.                                  */
 /* ------------------------------------------------------------------ */
-enum { BC_WALL_ISOTHERMAL = 1, BC_WALL_ADIABATIC = 2, BC_SLIP = 3, BC_STATE = 4 };
+enum { BC_WALL_ISOTHERMAL = 1, BC_WALL_ADIABATIC = 2, BC_SLIP = 3, BC_STATE = 4, BC_OUTFLOW = 5 };
 
-static void bc_lift_value(const mesh_t* M, const params_t* P, int bc, const real* q, const real* nu, real* qs) {
+/* the outer state of a prescribed-state or outflow condition */
+static void bc_outer_state(const params_t* P, const real* b, const real* U, const real* q, real* Ue) {
+  if ((int)b[0] == BC_STATE) {
+    for (int k = 0; k < 5; ++k) Ue[k] = b[1 + k];
+    return;
+  }
+  Ue[0] = U[0];
+  Ue[1] = U[1];
+  Ue[2] = U[2];
+  Ue[3] = U[3];
+  Ue[4] = b[1] / (P->gamma - 1) + (real)0.5 * (U[1] * q[1] + U[2] * q[2] + U[3] * q[3]);
+}
+
+static void bc_lift_value(const mesh_t* M, const params_t* P, int bc, const real* U, const real* q, const real* nu,
+                          real* qs) {
   const real* b = M->bcv[bc];
   switch ((int)b[0]) {
     case BC_WALL_ISOTHERMAL:
@@ -686,8 +705,9 @@ static void bc_lift_value(const mesh_t* M, const params_t* P, int bc, const real
       break;
     }
     default: {
-      real qe[6];
-      cons_to_prim(P, &b[1], qe);
+      real Ue[5], qe[6];
+      bc_outer_state(P, b, U, q, Ue);
+      cons_to_prim(P, Ue, qe);
       qs[0] = (q[1] + qe[1]) / 2; qs[1] = (q[2] + qe[2]) / 2;
       qs[2] = (q[3] + qe[3]) / 2; qs[3] = (q[5] + qe[5]) / 2;
     }
@@ -698,10 +718,11 @@ static void bc_flux(const mesh_t* M, const params_t* P, int bc, const real* U, c
                     const real* nu, real s, const real* nv, real* fs) {
   const real* b = M->bcv[bc];
   const int type = (int)b[0];
-  if (type == BC_STATE) {
-    real qe[6], fc[5];
-    cons_to_prim(P, &b[1], qe);
-    riemann(P, P->riemann, U, q, &b[1], qe, nu, fc);
+  if (type == BC_STATE || type == BC_OUTFLOW) {
+    real Ue[5], qe[6], fc[5];
+    bc_outer_state(P, b, U, q, Ue);
+    cons_to_prim(P, Ue, qe);
+    riemann(P, P->riemann, U, q, Ue, qe, nu, fc);
     for (int k = 0; k < 5; ++k) fs[k] = fc[k] * s;
     if (P->viscous) {
       real f1[5], f2[5];
@@ -787,7 +808,7 @@ static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
               real s = RSQRT(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
               real nu[3] = {nv[0] / s, nv[1] / s, nv[2] / s};
               real qs[4];
-              bc_lift_value(M, P, M->face_bc[ef], &w->q[(e * n3 + vM) * 6], nu, qs);
+              bc_lift_value(M, P, M->face_bc[ef], &U[(e * n3 + vM) * 5], &w->q[(e * n3 + vM) * 6], nu, qs);
               for (int qv = 0; qv < 4; ++qv)
                 for (int x = 0; x < 3; ++x)
                   w->g[(e * n3 + vM) * 12 + qv * 3 + x] += qs[qv] * sgn * Jam[x] / o->w[(f % 2) ? n - 1 : 0];
@@ -952,13 +973,14 @@ static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
         }
     }
 
-  /* ---- ApplyJac ---- */
+  /* ---- ApplyJac; sponge source ---- */
   for (long e = 0; e < E; ++e) {
     if (want && !want[e]) continue;
     for (long v = 0; v < n3; ++v)
       for (int k = 0; k < 5; ++k) {
         long x = (e * n3 + v) * 5 + k;
         Ut[x] = -(w->Bc[x] + w->B[x]) / M->J[e * n3 + v];
+        if (M->sponge_sigma) Ut[x] -= M->sponge_sigma[e * n3 + v] * (U[x] - M->sponge_base[x]);
       }
   }
   if (alpha_out)
@@ -1124,6 +1146,21 @@ void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, cons
   return h;
 }
 
+/* sponge zone: sigma [E][n3] (NULL removes it), base state [E][n3][5] */
+void ORC(set_sponge)(void* hv, const double* sigma, const double* base) {
+  handle_t* h = (handle_t*)hv;
+  mesh_t* M = &h->M;
+  free(M->sponge_sigma);
+  free(M->sponge_base);
+  M->sponge_sigma = M->sponge_base = NULL;
+  if (!sigma) return;
+  long nn = M->E * M->n3;
+  M->sponge_sigma = (real*)malloc(sizeof(real) * nn);
+  M->sponge_base = (real*)malloc(sizeof(real) * nn * 5);
+  to_real(sigma, M->sponge_sigma, nn);
+  to_real(base, M->sponge_base, nn * 5);
+}
+
 void ORC(mesh_free)(void* hv) {
   handle_t* h = (handle_t*)hv;
   if (!h) return;
@@ -1131,6 +1168,8 @@ void ORC(mesh_free)(void* hv) {
   free(M->xyz); free(M->Ja); free(M->J); free(M->nbr_e); free(M->nbr_f); free(M->master);
   free(M->nbr_node);
   free(M->face_bc);
+  free(M->sponge_sigma);
+  free(M->sponge_base);
   work_free(&h->w);
   free(h);
 }

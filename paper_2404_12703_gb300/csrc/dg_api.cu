@@ -322,6 +322,8 @@ void dg_destroy(dg_ctx* c) {
   dfree(c, c->side_f);
   dfree(c, c->side_bc);
   dfree(c, c->bcdata);
+  dfree(c, c->sponge_sigma);
+  dfree(c, c->sponge_base);
   dfree(c, c->ops);
   dfree(c, c->scal);
   if (c->scal_host) cudaFreeHost(c->scal_host);
@@ -426,10 +428,11 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
     if (mesh->n_bc < 1 || mesh->n_bc > 64 || !mesh->bc) return fail(DG_ERR_ARG, "face_bc needs 1..64 condition rows");
     for (int k = 0; k < mesh->n_bc; ++k) {
       const int type = (int)mesh->bc[k * 9];
-      if (type < DG_BC_WALL_ISOTHERMAL || type > DG_BC_STATE || (double)type != mesh->bc[k * 9])
+      if (type < DG_BC_WALL_ISOTHERMAL || type > DG_BC_OUTFLOW || (double)type != mesh->bc[k * 9])
         return fail(DG_ERR_ARG, "unknown boundary-condition type");
       if (type == DG_BC_WALL_ISOTHERMAL && !(mesh->bc[k * 9 + 4] > 0)) return fail(DG_ERR_ARG, "wall temperature must be > 0");
       if (type == DG_BC_STATE && !(mesh->bc[k * 9 + 1] > 0)) return fail(DG_ERR_ARG, "prescribed density must be > 0");
+      if (type == DG_BC_OUTFLOW && !(mesh->bc[k * 9 + 1] > 0)) return fail(DG_ERR_ARG, "outflow pressure must be > 0");
     }
     for (int64_t a = 0; a < 6 * mesh->n_elems; ++a)
       if (mesh->face_bc[a] < 0 || mesh->face_bc[a] > mesh->n_bc) return fail(DG_ERR_ARG, "face_bc out of range");
@@ -737,6 +740,33 @@ int dg_profile_step(dg_ctx* c, int n_steps, double dt, double* ms, int64_t* laun
   }
   delete p;
   if (e != cudaSuccess) return cuda_fail(e, "dg_profile_step");
+  return DG_OK;
+}
+
+int dg_set_sponge(dg_ctx* c, const double* sigma, const double* U_base) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (!c->cap_stream) return fail(DG_ERR_STATE, "internal case context");
+  destroy_graph(c);  // the step graph captures the sponge arrays
+  if (!sigma) {
+    cudaStreamSynchronize(c->stream);
+    dfree(c, c->sponge_sigma);
+    dfree(c, c->sponge_base);
+    c->sponge_sigma = c->sponge_base = nullptr;
+    return DG_OK;
+  }
+  if (!U_base) return fail(DG_ERR_ARG, "U_base is NULL");
+  const int64_t nn = c->E * c->n3;
+  for (int64_t i = 0; i < nn; ++i)
+    if (!(sigma[i] >= 0) || !std::isfinite(sigma[i])) return fail(DG_ERR_ARG, "sigma must be finite and >= 0");
+  cudaError_t e = cudaSuccess;
+  if (!c->sponge_sigma) e = dalloc(c, &c->sponge_sigma, nn);
+  if (e == cudaSuccess && !c->sponge_base) e = dalloc(c, &c->sponge_base, nn * 5);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->sponge_sigma, sigma, sizeof(double) * nn, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->Upub, U_base, sizeof(double) * nn * 5, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = launch_to_internal(c, c->Upub, c->sponge_base);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_set_sponge");
   return DG_OK;
 }
 

@@ -262,8 +262,21 @@ __device__ __forceinline__ void lf_flux_s(const SPrim<T>& L, const SPrim<T>& R, 
 // identities, as on inner sides); the energy flux is the full one, the mass
 // flux being zero at walls.
 // ---------------------------------------------------------------------------
+// the outer state of a prescribed-state or outflow condition, in FP64
+__device__ __forceinline__ void bc_outer_state(const StageArgs& a, const double* b, const double U[5], double Ue[5]) {
+  if ((int)b[0] == DG_BC_STATE) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Ue[k] = b[1 + k];
+    return;
+  }
+  const double ri = 1.0 / U[0];
+  const double u = U[1] * ri, v = U[2] * ri, w = U[3] * ri;
+  Ue[0] = U[0], Ue[1] = U[1], Ue[2] = U[2], Ue[3] = U[3];
+  Ue[4] = b[1] / a.gm1 + 0.5 * (U[1] * u + U[2] * v + U[3] * w);
+}
+
 template <typename T>
-__device__ __forceinline__ void bc_lift_value(const StageArgs& a, const CaseParams& cp, int row,
+__device__ __forceinline__ void bc_lift_value(const StageArgs& a, const CaseParams& cp, int row, const double U[5],
                                               const SPrim<T>& q, const T nu[3], T qs[4]) {
   const double* b = a.bcdata + (size_t)row * 9;
   const int type = (int)b[0];
@@ -275,7 +288,8 @@ __device__ __forceinline__ void bc_lift_value(const StageArgs& a, const CasePara
     const T un = q.u * nu[0] + q.v * nu[1] + q.w * nu[2];
     qs[0] = q.u - un * nu[0], qs[1] = q.v - un * nu[1], qs[2] = q.w - un * nu[2], qs[3] = q.Tt;
   } else {
-    const double Ue[5] = {b[1], b[2], b[3], b[4], b[5]};
+    double Ue[5];
+    bc_outer_state(a, b, U, Ue);
     const SPrim<T> qe = shifted_prim<T>(Ue, a.gm1, a.Rinv, cp);
     qs[0] = (q.u + qe.u) / T(2), qs[1] = (q.v + qe.v) / T(2), qs[2] = (q.w + qe.w) / T(2);
     qs[3] = (q.Tt + qe.Tt) / T(2);
@@ -283,12 +297,14 @@ __device__ __forceinline__ void bc_lift_value(const StageArgs& a, const CasePara
 }
 
 template <typename T>
-__device__ __forceinline__ void bc_flux(const StageArgs& a, const CaseParams& cp, int row, const SPrim<T>& q,
-                                        const T g[12], const T nu[3], T sA, const T sn[3], T f[5]) {
+__device__ __forceinline__ void bc_flux(const StageArgs& a, const CaseParams& cp, int row, const double U[5],
+                                        const SPrim<T>& q, const T g[12], const T nu[3], T sA, const T sn[3],
+                                        T f[5]) {
   const double* b = a.bcdata + (size_t)row * 9;
   const int type = (int)b[0];
-  if (type == DG_BC_STATE) {
-    const double Ue[5] = {b[1], b[2], b[3], b[4], b[5]};
+  if (type == DG_BC_STATE || type == DG_BC_OUTFLOW) {
+    double Ue[5];
+    bc_outer_state(a, b, U, Ue);
     const SPrim<T> qe = shifted_prim<T>(Ue, a.gm1, a.Rinv, cp);
     if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(q, qe, nu, pick<T>(a.gm1, a.f_gm1), pick<T>(cp.Hr, cp.fHr), f);
     else lf_flux_s(q, qe, nu, pick<T>(a.gamma, a.f_gamma), pick<T>(cp.pr, cp.fpr), f);
@@ -367,7 +383,7 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   T qa[4];
   const int brow = a.side_bc ? a.side_bc[s] : -1;
   if (brow >= 0) {
-    bc_lift_value<T>(a, cp, brow, qM, nu, qa);  // boundary side: the condition's value
+    bc_lift_value<T>(a, cp, brow, UM, qM, nu, qa);  // boundary side: the condition's value
   } else {
     int ps, qs;
     flip_to_slave<n>(flip, p, q, ps, qs);
@@ -572,7 +588,7 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
 #pragma unroll
       for (int k = 0; k < 12; ++k) gM[k] = T(0);
     }
-    bc_flux<T>(a, cp, brow, qM, gM, nu, sA, sn, f);
+    bc_flux<T>(a, cp, brow, UM, qM, gM, nu, sA, sn, f);
   } else {
     int ps, qs;
     flip_to_slave<n>(flip, p, q, ps, qs);
@@ -1066,6 +1082,12 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
 #pragma unroll
   for (int k = 0; k < 5; ++k) Ut[k] = (double)(-(accC[k] + acc[k]) * Ji);
   Ut[4] += H_ref * Ut[0];
+  if (a.sponge_sigma) {  // sponge source -sigma (U - U_base), FP64
+    const double sg = a.sponge_sigma[(size_t)e * n3 + t];
+    const double* ub = a.sponge_base + (size_t)e * 5 * n3 + t;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Ut[k] -= sg * ((aos ? sUd[k * n3 + t] : U[k]) - ub[k * n3]);
+  }
   if (MODE == 0) {
     double* o = a.Ut + (size_t)e * 5 * n3 + t;
 #pragma unroll
@@ -1139,6 +1161,8 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.side_list = c->side_list;
   a.side_bc = c->side_bc;
   a.bcdata = c->bcdata;
+  a.sponge_sigma = c->sponge_sigma;
+  a.sponge_base = c->sponge_base;
   if (c->elem_list) {
     a.E = (int)c->n_elem_list;
     a.S = (int)c->n_side_list;

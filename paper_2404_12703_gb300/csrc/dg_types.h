@@ -114,6 +114,9 @@ struct StageArgs {
   // boundary conditions: row of every side (-1: inner side), rows [n][9]
   const int* side_bc;
   const double* bcdata;
+  // sponge zone (null: none): sigma [E][n3], base state [E][5][n3]
+  const double* sponge_sigma;
+  const double* sponge_base;
 };
 
 }  // namespace dg
@@ -150,6 +153,8 @@ struct dg_ctx {
   int* side_bc = nullptr;    // [S] boundary-condition row (-1: inner side)
   double* bcdata = nullptr;  // [n_bc][9] boundary-condition rows (type, 8 parameters)
   int n_bc = 0;
+  double* sponge_sigma = nullptr;  // [E][n3]
+  double* sponge_base = nullptr;   // [E][5][n3] internal layout
   dg::Ops* ops = nullptr;    // device copy of the operators of degree N
   dg::DevScalars* scal = nullptr;
   dg::DevScalars* scal_host = nullptr;  // pinned mirror

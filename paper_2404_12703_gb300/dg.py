@@ -30,6 +30,7 @@ SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "d
                  "dg_server_destroy")
 EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
            "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_autotune", "dg_set_config", "dg_get_config",
+           "dg_set_sponge",
            "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
            "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
 
@@ -54,7 +55,7 @@ class MeshDesc(C.Structure):
                 ("bc", C.POINTER(C.c_double))]
 
 
-BC_WALL_ISOTHERMAL, BC_WALL_ADIABATIC, BC_SLIP, BC_STATE = 1, 2, 3, 4
+BC_WALL_ISOTHERMAL, BC_WALL_ADIABATIC, BC_SLIP, BC_STATE, BC_OUTFLOW = 1, 2, 3, 4, 5
 
 
 def _bc_arrays(mesh):
@@ -104,6 +105,7 @@ def load(path: str | None = None):
             "dg_step": (C.c_int, [vp, C.c_int, C.c_double]),
             "dg_advance": (C.c_int, [vp, C.c_double, C.c_int64, dp, C.POINTER(C.c_int64)]),
             "dg_autotune": (C.c_int, [vp, C.POINTER(C.c_int), dp]),
+            "dg_set_sponge": (C.c_int, [vp, vp, vp]),
             "dg_set_config": (C.c_int, [vp, C.POINTER(C.c_int)]),
             "dg_get_config": (C.c_int, [vp, C.POINTER(C.c_int)]),
             "dg_profile_step": (C.c_int, [vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int64)]),
@@ -281,6 +283,17 @@ class Solver:
         k = C.c_int64()
         _check(self._lib.dg_advance(self._h, float(t_end), int(max_steps), C.byref(t), C.byref(k)))
         return t.value, k.value
+
+    def set_sponge(self, sigma=None, U_base=None):
+        """Sponge source -sigma (U - U_base): sigma [E, n^3] >= 0, U_base
+        [E, n^3, 5] (host arrays); None removes it."""
+        if sigma is None:
+            _check(self._lib.dg_set_sponge(self._h, None, None))
+            return
+        sg = np.ascontiguousarray(sigma, dtype=np.float64)
+        ub = np.ascontiguousarray(U_base, dtype=np.float64)
+        assert sg.size == self.E * self.n ** 3 and ub.size == 5 * sg.size
+        _check(self._lib.dg_set_sponge(self._h, C.c_void_p(sg.ctypes.data), C.c_void_p(ub.ctypes.data)))
 
     CONFIG_KEYS = ("lift_epb", "vol_epb", "vol_pairs", "side_block")
     TUNE_KEYS = ("lift_D", "lift_2D", "vol_D", "vol_D_other_mapping", "vol_2D", "vol_2D_other_mapping",

@@ -17,6 +17,7 @@ BCS = {
     "walls": [(1, 0.0, 0.0, 0.0, 1.2), (1, 0.6, 0.0, 0.1, 1.0)],
     "adiabatic+slip": [(2, 0.3, 0.0, 0.0), (3,)],
     "state": [(4, 1.1, 0.3, 0.2, -0.1, 6.0), (4, 0.9, 0.2, 0.1, 0.0, 5.5)],
+    "inflow+outflow": [(4, 1.1, 0.3, 0.2, -0.1, 6.0), (5, 2.2)],
 }
 
 
@@ -58,6 +59,8 @@ def test_maps_bit_exact():
     (5, "state", dict(riemann="lf")),
     (3, "adiabatic+slip", dict(viscous=0)),
     (3, "walls", dict(shock_capturing=1, alpha_force=0.3)),
+    (3, "inflow+outflow", dict()),
+    (5, "inflow+outflow", dict(riemann="lf", viscous=0)),
 ])
 def test_rhs_parity(N, bcs, kw):
     torch, dg = gpu_or_skip()
@@ -107,7 +110,7 @@ def test_ten_steps_parity():
 
 def test_fp32_bulk_against_oracle():
     torch, dg = gpu_or_skip()
-    for bcs in ("walls", "adiabatic+slip", "state"):
+    for bcs in ("walls", "adiabatic+slip", "state", "inflow+outflow"):
         m = _channel(4, bcs=bcs)
         s = dg.Solver(m, precision=dg.FP32_BULK)
         U = _state(m)
@@ -136,3 +139,33 @@ def test_boundary_errors():
     with pytest.raises(dg.DgError):
         srv.submit(m, _state(m), 0.01)
     srv.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sponge_parity(prec):
+    torch, dg = gpu_or_skip()
+    N = 4
+    m = _channel(N, bcs="inflow+outflow")
+    p = dg.FP64 if prec == "fp64" else dg.FP32_BULK
+    s = dg.Solver(m, precision=p)
+    U = _state(m)
+    y = m["xyz"].reshape(m["E"], -1, 3)[..., 1]
+    sigma = 5.0 * np.clip(y - 0.6, 0.0, None) ** 2           # a zone near the outflow
+    Ub = W.uniform_state(U.shape[:2], rho=1.0, vel=(0.0, 0.3, 0.0), p=2.0)
+    s.set_sponge(sigma, Ub)
+    Ut = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    prm = oracle_params(s.params)
+    Mq = _oracle(m, quad=True)
+    Mq.set_sponge(sigma, Ub)
+    ref = Mq.rhs(U, prm)
+    if p == dg.FP64:
+        M64 = _oracle(m)
+        M64.set_sponge(sigma, Ub)
+        bound, _ = parity_bound(M64.rhs(U, prm), ref)
+        assert np.all(rel_err(Ut, ref) <= bound)
+    else:
+        assert np.all(rel_err(Ut, ref) <= 2e-4)
+    # removing the sponge gives the plain operator back, bitwise
+    plain = dg.Solver(m, precision=p).rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    s.set_sponge(None)
+    np.testing.assert_array_equal(s.rhs(torch.from_numpy(U).cuda()).cpu().numpy(), plain)

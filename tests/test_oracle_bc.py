@@ -103,3 +103,42 @@ def test_open_faces_need_a_boundary_condition():
     fb[0, 0] = 1  # a condition on a face that has a partner
     with pytest.raises(ValueError):
         O.Mesh(3, m["xyz"], m["period"], face_bc=fb, bcs=[(3,)])
+
+
+def test_outflow_at_the_stream_pressure_keeps_a_uniform_stream():
+    """Prescribed state upstream, pressure outflow downstream at the stream's
+    own pressure: the outer states equal the inner ones, the stream stays."""
+    N = 3
+    m = _channel(N, curved=0.1, seed=12)
+    U = W.uniform_state((m["E"], (N + 1) ** 3), rho=1.2, vel=(0.1, 0.6, 0.2), p=3.0)
+    fb = W.box_face_bc(m, {"y-": 1, "y+": 2})
+    M = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(4, *U[0, 0]), (5, 3.0)])
+    for prm in (O.params(mu=0.01), O.params(riemann="lf", viscous=False)):
+        assert np.abs(M.rhs(U, prm)).max() < 1e-11
+    # another outflow pressure is seen at the outflow side only
+    M2 = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(4, *U[0, 0]), (5, 2.5)])
+    Ut = M2.rhs(U, O.params(mu=0.01))
+    assert np.abs(Ut).max() > 1e-2
+
+
+def test_sponge_source():
+    """A uniform state has no DG residual: the sponge alone sets Ut =
+    -sigma (U - U_base); over LSERK steps every node relaxes like
+    U_base + (U - U_base) exp(-sigma t) (fourth order in time)."""
+    N = 3
+    m = W.box_mesh(N, (3, 3, 3), curved=0.1, seed=13)
+    n3 = (N + 1) ** 3
+    U = W.uniform_state((m["E"], n3), rho=1.1, vel=(0.3, -0.2, 0.1), p=2.0)
+    Ub = W.uniform_state((m["E"], n3), rho=1.0, vel=(0.0, 0.0, 0.0), p=2.0)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    prm = O.params(mu=0.01)
+    sigma = np.full((m["E"], n3), 0.8)
+    M.set_sponge(sigma, Ub)
+    Ut = M.rhs(U, prm)
+    assert np.abs(Ut - (-sigma[..., None] * (U - Ub))).max() < 1e-13
+    dt, steps = 0.05, 20
+    Uk, t, _ = M.step(U, prm, steps, dt=dt)
+    exact = Ub + (U - Ub) * np.exp(-0.8 * t)
+    assert np.abs(Uk - exact).max() < 1e-8
+    M.set_sponge(None)
+    assert np.abs(M.rhs(U, prm)).max() < 1e-11

@@ -66,9 +66,10 @@ def _lib(quad: bool = False):
             return f
 
         api = {
-            "ops": fn("ops", C.c_int, [C.c_int, dp, dp, dp, dp, dp, dp]),
-            "mesh_new": fn("mesh_new", C.c_void_p, [C.c_int, C.c_long, dp, dp, C.c_void_p, C.c_void_p, C.c_int,
-                                                    C.c_void_p, ip]),
+            "ops": fn("ops", C.c_int, [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp]),
+            "mesh_new": fn("mesh_new", C.c_void_p, [C.c_int, C.c_int, C.c_long, dp, dp, C.c_void_p, C.c_void_p,
+                                                    C.c_int, C.c_void_p, ip]),
+            "node_xyz": fn("node_xyz", None, [C.c_void_p, dp]),
             "mesh_free": fn("mesh_free", None, [C.c_void_p]),
             "set_sponge": fn("set_sponge", None, [C.c_void_p, C.c_void_p, C.c_void_p]),
             "connectivity": fn("connectivity", None, [C.c_void_p, ip, ip, ip, ip]),
@@ -111,11 +112,21 @@ def params(gamma=1.4, R=1.0, Pr=0.72, mu=1.0 / 1600.0, riemann="roe", viscous=Tr
                     dtype=np.float64)
 
 
-def ops(N: int, quad: bool = False):
-    """LGL nodes x, weights w, D, Dhat, Dsplit and the inverse Legendre Vandermonde."""
+def ops(N: int, quad: bool = False, gauss: bool = False):
+    """Nodes x, weights w, D, Dhat, Dsplit and the inverse Legendre Vandermonde
+    of the LGL (default) or Gauss-Legendre (``gauss``) node set."""
+    return _ops_all(N, quad, gauss)[:6]
+
+
+def face_interp(N: int, gauss: bool = False, quad: bool = False):
+    """(l_i(+1), l_i(-1)): the Lagrange basis of the node set at the element ends."""
+    return _ops_all(N, quad, gauss)[6:]
+
+
+def _ops_all(N, quad, gauss):
     n = N + 1
-    out = [np.zeros(n), np.zeros(n)] + [np.zeros((n, n)) for _ in range(4)]
-    if _lib(quad)["ops"](N, *[_dp(a) for a in out]) != 0:
+    out = [np.zeros(n), np.zeros(n)] + [np.zeros((n, n)) for _ in range(4)] + [np.zeros(n), np.zeros(n)]
+    if _lib(quad)["ops"](N, int(bool(gauss)), *[_dp(a) for a in out]) != 0:
         raise ValueError("bad N")
     return tuple(out)
 
@@ -159,14 +170,17 @@ def rk_coeffs():
 class Mesh:
     """Oracle view of one mesh: connectivity, metrics and the DG operator."""
 
-    def __init__(self, N, xyz, period, quad=False, metric_mask=None, face_bc=None, bcs=None):
+    def __init__(self, N, xyz, period, quad=False, metric_mask=None, face_bc=None, bcs=None, gauss=False):
         """``metric_mask``: optional boolean mask over elements; metrics are then
         formed only for those elements and their face neighbours (use the same
         mask as ``want`` in ``rhs``).  ``face_bc``: [E, 6] boundary-condition row
         per face (0: a face with a partner; k >= 1: row k - 1 of ``bcs``);
         ``bcs``: rows of (type, 8 parameters), type 1 isothermal no-slip wall
         (u_w, v_w, w_w, T_w), 2 adiabatic no-slip wall (u_w, v_w, w_w), 3 slip
-        wall, 4 prescribed state (5 conservative values), 5 pressure outflow (p_out)."""
+        wall, 4 prescribed state (5 conservative values), 5 pressure outflow (p_out).
+        ``gauss``: the standard DGSEM on Gauss-Legendre nodes instead of the split
+        form on LGL nodes; ``xyz`` stays the LGL-node geometry and ``nodes()``
+        returns the solution-node coordinates."""
         self.N = int(N)
         self.n = self.N + 1
         xyz = _f64(xyz)
@@ -185,7 +199,8 @@ class Mesh:
             for k, row in enumerate(bcs):
                 bcv[k, :len(row)] = row
             nbc = len(bcs)
-        self._h = self._api["mesh_new"](self.N, self.E, _dp(xyz.reshape(-1)), _dp(_f64(period)),
+        self.gauss = bool(gauss)
+        self._h = self._api["mesh_new"](self.N, int(self.gauss), self.E, _dp(xyz.reshape(-1)), _dp(_f64(period)),
                                         mask.ctypes.data if mask is not None else None,
                                         fb.ctypes.data if fb is not None else None, nbc,
                                         bcv.ctypes.data if bcv is not None else None, C.byref(st))
@@ -224,6 +239,12 @@ class Mesh:
         node = np.zeros((E, 6, n2), np.int32)
         self._api["connectivity"](self._h, _ip(nbr_e), _ip(nbr_f), _ip(master), _ip(node))
         return nbr_e, nbr_f, master, node
+
+    def nodes(self):
+        """Coordinates of the solution nodes [E][n^3][3]."""
+        X = np.zeros((self.E, self.n ** 3, 3))
+        self._api["node_xyz"](self._h, _dp(X))
+        return X
 
     def metrics(self):
         Ja = np.zeros((self.E, self.n ** 3, 3, 3))

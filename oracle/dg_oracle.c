@@ -28,6 +28,12 @@
  *   - Carpenter-Kennedy five-stage 2N-storage RK4 (Sec. 2.2, Time integration)
  *     and a CFL time step (the paper gives no rule; see the reading in dg_dt).
  *   - kinetic energy E_k and its exact rate (Sec. 5.2).
+ *   - boundary conditions (walls, prescribed state, pressure outflow), a sponge
+ *     source, and Sutherland's law for mu(T) (Sec. 6 application, Sec. 2.1).
+ *   - the standard (non-split) DGSEM on Gauss-Legendre nodes (Sec. 2.2,
+ *     Eq. dgsem with lhat+-_i = l_i(+-1)/w_i; Sec. 5.1): nodes the roots of
+ *     P_{N+1}, ProlongToFace by interpolation with l(+-1), the collocated
+ *     flux divergence as volume term, SurfInt over every node of a line.
  *
  * Node index inside an element: node = i + n*(j + n*k), i along xi.
  * Public state layout: U[e][node][v], v = (rho, rho u, rho v, rho w, rho e).
@@ -151,6 +157,34 @@ static void lgl(int N, oreal* x, oreal* w) {
   }
 }
 
+/* Gauss-Legendre nodes: the N + 1 roots of P_{N+1}; weights
+   2 / ((1 - x^2) P_{N+1}'(x)^2). */
+static void gauss_legendre(int N, oreal* x, oreal* w) {
+  const int n = N + 1;
+  for (int j = 0; j < n; ++j) {
+    oreal t = -cosl(M_PI * ((long double)j + 0.75L) / ((long double)n + 0.5L));
+    for (int it = 0; it < 200; ++it) {
+      oreal P, dP;
+      legendre(n, t, &P, &dP);
+      oreal dt = P / dP;
+      t -= dt;
+      if (fabsl(dt) <= 4 * LDBL_EPSILON) break;
+    }
+    oreal P, dP;
+    legendre(n, t, &P, &dP);
+    x[j] = t;
+    w[j] = 2 / ((1 - t * t) * dP * dP);
+  }
+}
+
+/* l_j(y) for the nodes x (Lagrange basis) */
+static oreal lagrange(int n, const oreal* x, int j, oreal y) {
+  oreal v = 1;
+  for (int m = 0; m < n; ++m)
+    if (m != j) v *= (y - x[m]) / (x[j] - x[m]);
+  return v;
+}
+
 /* D[i][j] = l_j'(x_i) with l_j(x) = prod_{m != j} (x - x_m) / (x_j - x_m). */
 static void lagrange_derivative(int n, const oreal* x, oreal* D) {
   for (int i = 0; i < n; ++i)
@@ -206,15 +240,25 @@ typedef struct {
   real Dsplit[NMAX * NMAX]; /* 2 D[i][a] - d_iN d_aN / w_N + d_i0 d_a0 / w_0 */
   real Vinv[NMAX * NMAX];   /* inverse of V[i][m] = Ltilde_m(x_i)          */
   oreal Dl[NMAX * NMAX];    /* D in long double, for the metrics          */
+  int gauss;                /* 0: LGL nodes, 1: Gauss-Legendre nodes       */
+  real Lp[NMAX], Lm[NMAX];  /* l_i(+1), l_i(-1): interpolation to the faces */
+  oreal xl[NMAX];           /* the nodes in long double                   */
 } ops_t;
 
-static int build_ops(int N, ops_t* o) {
+static int build_ops(int N, int gauss, ops_t* o) {
   if (N < 1 || N + 1 > NMAX) return -1;
   int n = N + 1;
   o->N = N;
   o->n = n;
+  o->gauss = gauss;
   oreal x[NMAX], w[NMAX], V[NMAX * NMAX], Vi[NMAX * NMAX];
-  lgl(N, x, w);
+  if (gauss) gauss_legendre(N, x, w);
+  else lgl(N, x, w);
+  for (int i = 0; i < n; ++i) {
+    o->xl[i] = x[i];
+    o->Lp[i] = (real)lagrange(n, x, i, 1);
+    o->Lm[i] = (real)lagrange(n, x, i, -1);
+  }
   lagrange_derivative(n, x, o->Dl);
   for (int i = 0; i < n; ++i) { o->x[i] = (real)x[i]; o->w[i] = (real)w[i]; }
   for (int i = 0; i < n; ++i)
@@ -246,7 +290,8 @@ typedef struct {
   int N, n, n2, n3;
   long E;
   real period[3];
-  real* xyz;     /* [E][n3][3]                                   */
+  real* xyz;     /* [E][n3][3] at the LGL nodes (geometry input)  */
+  real* xyzs;    /* [E][n3][3] at the solution nodes (= xyz on LGL) */
   real* Ja;      /* [E][n3][3][3]  Ja[.][d][c] = (J a^d)_c       */
   real* J;       /* [E][n3]                                      */
   int* nbr_e;    /* [E*6]                                        */
@@ -414,15 +459,68 @@ static mreal mline(int n, const mreal* Dm, const mreal* fld, int stride, long v,
   return s;
 }
 
+/* one-dimensional interpolation along direction d of a field with ncomp
+   components per node: out[i] = sum_a I[i][a] in[a] on every line */
+static void interp_dir(int n, const mreal* I, const mreal* in, mreal* out, int ncomp, int d) {
+  long n3 = (long)n * n * n;
+  for (long v = 0; v < n3; ++v) {
+    int i = line_index(n, v, d);
+    for (int c = 0; c < ncomp; ++c) {
+      mreal s = 0;
+      for (int a = 0; a < n; ++a) s += I[i * n + a] * in[line_node(n, v, d, a) * ncomp + c];
+      out[v * ncomp + c] = s;
+    }
+  }
+}
+
+/* tensor-product interpolation I x I x I, applied one direction at a time */
+static void interp3(int n, const mreal* I, mreal* f, mreal* tmp, int ncomp) {
+  interp_dir(n, I, f, tmp, ncomp, 0);
+  interp_dir(n, I, tmp, f, ncomp, 1);
+  interp_dir(n, I, f, tmp, ncomp, 2);
+  memcpy(f, tmp, sizeof(mreal) * n * n * n * ncomp);
+}
+
+static mreal det3(const mreal* a) {
+  return a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+         a[2] * (a[3] * a[7] - a[4] * a[6]);
+}
+
 /* need: NULL for every element, else a 0/1 mask of the elements whose metrics
-   are formed (the others are left as NaN). */
+   are formed (the others are left as NaN).
+   The geometry is the degree-N polynomial through the given LGL node
+   coordinates.  The curl-form metrics are formed on the LGL nodes, where the
+   normal metric component on a face depends on that face's coordinates only
+   (so both elements of a face agree on it).  On Gauss-Legendre nodes the same
+   polynomials (J a^d and the Jacobian matrix dx/dxi) are evaluated at the GL
+   nodes by exact interpolation, and J = det(dx/dxi) there; the face normals
+   of the GL scheme are these metrics interpolated to the face (Sec. 2.2
+   reading), which then equal the LGL face values. */
 static void build_metrics(mesh_t* M, const unsigned char* need) {
   int n = M->n, n3 = M->n3;
-  const mreal* Dm = M->o.Dl;
+  ops_t lglops;
+  const ops_t* og = &M->o;
+  if (M->o.gauss) {
+    build_ops(M->N, 0, &lglops);
+    og = &lglops;
+  }
+  const mreal* Dm = og->Dl;
+  mreal Ig[NMAX * NMAX];   /* Ig[g][l] = l^LGL_l(x^GL_g) */
+  if (M->o.gauss)
+    for (int g = 0; g < n; ++g)
+      for (int l = 0; l < n; ++l) Ig[g * n + l] = lagrange(n, og->xl, l, M->o.xl[g]);
   mreal* dx = (mreal*)malloc(sizeof(mreal) * 9 * n3);   /* dx[v][c][d] = d x_c / d xi_d */
   mreal* V = (mreal*)malloc(sizeof(mreal) * 3 * n3);    /* V[v][d]                    */
   mreal* X = (mreal*)malloc(sizeof(mreal) * 3 * n3);
+  mreal* Ja = (mreal*)malloc(sizeof(mreal) * 9 * n3);   /* Ja[v][d][c]                */
+  mreal* tmp = (mreal*)malloc(sizeof(mreal) * 9 * n3);
   for (long e = 0; e < M->E; ++e) {
+    const real* Xa = &M->xyz[e * n3 * 3];
+    if (M->o.gauss) {
+      for (long v = 0; v < n3 * 3; ++v) X[v] = (mreal)Xa[v];
+      interp3(n, Ig, X, tmp, 3);
+      for (long v = 0; v < n3 * 3; ++v) M->xyzs[e * n3 * 3 + v] = (real)X[v];
+    }
     if (need && !need[e]) {
       for (long v = 0; v < n3; ++v) {
         M->J[e * n3 + v] = NAN;
@@ -434,17 +532,11 @@ static void build_metrics(mesh_t* M, const unsigned char* need) {
        coordinates relative to the element's first node so that the products
        x_l grad x_m carry rounding relative to the element size, not to the
        distance from the origin */
-    const real* Xa = &M->xyz[e * n3 * 3];
     for (long v = 0; v < n3; ++v)
       for (int c = 0; c < 3; ++c) X[v * 3 + c] = (mreal)Xa[v * 3 + c] - (mreal)Xa[c];
     for (long v = 0; v < n3; ++v)
       for (int c = 0; c < 3; ++c)
         for (int d = 0; d < 3; ++d) dx[v * 9 + c * 3 + d] = mline(n, Dm, X + c, 3, v, d);
-    for (long v = 0; v < n3; ++v) {
-      const mreal* a = &dx[v * 9];
-      M->J[e * n3 + v] = (real)(a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
-                                a[2] * (a[3] * a[7] - a[4] * a[6]));
-    }
     for (int nc = 0; nc < 3; ++nc) {
       int m = (nc + 1) % 3, l = (nc + 2) % 3;
       for (long v = 0; v < n3; ++v)
@@ -453,13 +545,23 @@ static void build_metrics(mesh_t* M, const unsigned char* need) {
         for (int i = 0; i < 3; ++i) {
           int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
           mreal curl = mline(n, Dm, V + i2, 3, v, i1) - mline(n, Dm, V + i1, 3, v, i2);
-          M->Ja[((e * n3 + v) * 3 + i) * 3 + nc] = (real)(-curl);
+          Ja[(v * 3 + i) * 3 + nc] = -curl;
         }
+    }
+    if (M->o.gauss) {
+      interp3(n, Ig, Ja, tmp, 9);
+      interp3(n, Ig, dx, tmp, 9);
+    }
+    for (long v = 0; v < n3; ++v) {
+      M->J[e * n3 + v] = (real)det3(&dx[v * 9]);
+      for (int k = 0; k < 9; ++k) M->Ja[(e * n3 + v) * 9 + k] = (real)Ja[v * 9 + k];
     }
   }
   free(dx);
   free(V);
   free(X);
+  free(Ja);
+  free(tmp);
 }
 
 /* ------------------------------------------------------------------ */
@@ -991,6 +1093,243 @@ static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
   return 0;
 }
 
+/* ---- standard DGSEM on Gauss-Legendre nodes (Eq. dgsem, Sec. 5.1) ----
+   The face values are interpolations along the lines normal to the face
+   (ProlongToFace with l(+-1)); ConsToPrim then runs on the face values; the
+   surface terms are spread over every node of the line with
+   lhat+-_i = l_i(+-1) / w_i (SurfInt); the convective volume term is the
+   collocated flux divergence sum_a Dhat[i][a] (J a^d . F(U))_a.  The lifting
+   and viscous terms are those of the LGL scheme with the same face
+   interpolation; the lifted gradients are interpolated to the faces for the
+   viscous surface flux. */
+
+/* value at face point (p, q) of face f: sum_a l_a(+-1) fld[line node a] */
+static void face_value(const mesh_t* M, const real* fld, int ncomp, long e, int f, int p, int q, real* out) {
+  int n = M->n;
+  long n3 = M->n3;
+  const real* L = (f % 2) ? M->o.Lp : M->o.Lm;
+  long v0 = face_node(n, f, p, q);
+  for (int c = 0; c < ncomp; ++c) out[c] = 0;
+  for (int a = 0; a < n; ++a) {
+    long va = line_node(n, v0, f / 2, a);
+    for (int c = 0; c < ncomp; ++c) out[c] += L[a] * fld[(e * n3 + va) * ncomp + c];
+  }
+}
+
+/* J a^d of the face's direction interpolated to face point (p, q), times the
+   outward sign of face f */
+static void face_normal(const mesh_t* M, long e, int f, int p, int q, real* nv) {
+  int n = M->n, d = f / 2;
+  long n3 = M->n3;
+  const real* L = (f % 2) ? M->o.Lp : M->o.Lm;
+  long v0 = face_node(n, f, p, q);
+  real sgn = (f % 2) ? 1 : -1;
+  for (int c = 0; c < 3; ++c) nv[c] = 0;
+  for (int a = 0; a < n; ++a) {
+    long va = line_node(n, v0, d, a);
+    for (int c = 0; c < 3; ++c) nv[c] += L[a] * M->Ja[((e * n3 + va) * 3 + d) * 3 + c];
+  }
+  for (int c = 0; c < 3; ++c) nv[c] *= sgn;
+}
+
+/* acc[line node a] += sgn_add * val * l_a(+-1) / w_a along the line of face point (p, q) */
+static void surf_spread(const mesh_t* M, real* acc, int ncomp, long e, int f, int p, int q, const real* val,
+                        real sgn_add) {
+  int n = M->n;
+  long n3 = M->n3;
+  const real* L = (f % 2) ? M->o.Lp : M->o.Lm;
+  long v0 = face_node(n, f, p, q);
+  for (int a = 0; a < n; ++a) {
+    long va = line_node(n, v0, f / 2, a);
+    for (int c = 0; c < ncomp; ++c) acc[(e * n3 + va) * ncomp + c] += sgn_add * val[c] * L[a] / M->o.w[a];
+  }
+}
+
+static int rhs_gauss(const mesh_t* M, const params_t* P, const real* U, real* Ut, const unsigned char* want,
+                     real* g_out, real* fstar_out, work_t* w) {
+  int n = M->n, n2 = M->n2, n3 = M->n3;
+  long E = M->E, F = E * 6;
+  const ops_t* o = &M->o;
+  if (P->shock) return -7;  /* shock capturing is an LGL (split-form) feature */
+  unsigned char* needg = (unsigned char*)calloc(E, 1);
+  for (long e = 0; e < E; ++e) {
+    if (want && !want[e]) continue;
+    needg[e] = 1;
+    for (int f = 0; f < 6; ++f)
+      if (M->nbr_e[e * 6 + f] >= 0) needg[M->nbr_e[e * 6 + f]] = 1;
+  }
+  /* ProlongToFace of U, then ConsToPrim on the faces */
+  real* Uf = (real*)malloc(sizeof(real) * F * n2 * 5);
+  real* qf = (real*)malloc(sizeof(real) * F * n2 * 6);
+  real* gf = (real*)calloc(F * n2 * 12, sizeof(real));
+  for (long e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f)
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          long x = (e * 6 + f) * n2 + p + n * q;
+          face_value(M, U, 5, e, f, p, q, &Uf[x * 5]);
+          cons_to_prim(P, &Uf[x * 5], &qf[x * 6]);
+        }
+  for (long v = 0; v < E * n3; ++v) cons_to_prim(P, &U[v * 5], &w->q[v * 6]);
+  memset(w->B, 0, sizeof(real) * E * n3 * 5);
+  memset(w->Bc, 0, sizeof(real) * E * n3 * 5);
+
+  /* ---- BR1 lifting ---- */
+  static const int lifted[4] = {1, 2, 3, 5};
+  if (P->viscous) {
+    memset(w->g, 0, sizeof(real) * E * n3 * 12);
+    for (long e = 0; e < E; ++e) {
+      if (!needg[e]) continue;
+      for (long v = 0; v < n3; ++v)
+        for (int d = 0; d < 3; ++d) {
+          int i = line_index(n, v, d);
+          for (int a = 0; a < n; ++a) {
+            long va = line_node(n, v, d, a);
+            const real* Jaa = &M->Ja[((e * n3 + va) * 3 + d) * 3];
+            for (int qv = 0; qv < 4; ++qv)
+              for (int x = 0; x < 3; ++x)
+                w->g[(e * n3 + v) * 12 + qv * 3 + x] +=
+                    o->Dhat[i * n + a] * Jaa[x] * w->q[(e * n3 + va) * 6 + lifted[qv]];
+          }
+        }
+    }
+    for (long e = 0; e < E; ++e)
+      for (int f = 0; f < 6; ++f) {
+        long ef = e * 6 + f;
+        if (!M->master[ef]) continue;
+        long e2 = M->nbr_e[ef];
+        int f2 = M->nbr_f[ef];
+        if (e2 < 0 ? !needg[e] : (!needg[e] && !needg[e2])) continue;
+        for (int qq = 0; qq < n; ++qq)
+          for (int p = 0; p < n; ++p) {
+            long xM = ef * n2 + p + n * qq;
+            real nv[3];
+            face_normal(M, e, f, p, qq, nv);
+            real qs[4];
+            if (e2 < 0) {
+              real s = RSQRT(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+              real nu[3] = {nv[0] / s, nv[1] / s, nv[2] / s};
+              bc_lift_value(M, P, M->face_bc[ef], &Uf[xM * 5], &qf[xM * 6], nu, qs);
+            } else {
+              long xS = ((long)e2 * 6 + f2) * n2 + M->nbr_node[xM];
+              for (int qv = 0; qv < 4; ++qv) qs[qv] = (qf[xM * 6 + lifted[qv]] + qf[xS * 6 + lifted[qv]]) / 2;
+            }
+            real fl[12];
+            for (int qv = 0; qv < 4; ++qv)
+              for (int x = 0; x < 3; ++x) fl[qv * 3 + x] = qs[qv] * nv[x];
+            surf_spread(M, w->g, 12, e, f, p, qq, fl, 1);
+            if (e2 >= 0) {
+              int a2 = M->nbr_node[xM];
+              surf_spread(M, w->g, 12, e2, f2, a2 % n, a2 / n, fl, -1);
+            }
+          }
+      }
+    for (long e = 0; e < E; ++e) {
+      if (!needg[e]) continue;
+      for (long v = 0; v < n3; ++v)
+        for (int k = 0; k < 12; ++k) w->g[(e * n3 + v) * 12 + k] /= M->J[e * n3 + v];
+    }
+    /* ProlongToFace of the lifted gradients */
+    for (long e = 0; e < E; ++e) {
+      if (!needg[e]) continue;
+      for (int f = 0; f < 6; ++f)
+        for (int q = 0; q < n; ++q)
+          for (int p = 0; p < n; ++p)
+            face_value(M, w->g, 12, e, f, p, q, &gf[((e * 6 + f) * n2 + p + n * q) * 12]);
+    }
+  }
+
+  /* ---- volume integral: collocated flux divergence (standard weak form) ---- */
+  for (long e = 0; e < E; ++e) {
+    if (want && !want[e]) continue;
+    for (long v = 0; v < n3; ++v)
+      for (int d = 0; d < 3; ++d) {
+        int i = line_index(n, v, d);
+        for (int a = 0; a < n; ++a) {
+          long va = line_node(n, v, d, a);
+          const real* Jaa = &M->Ja[((e * n3 + va) * 3 + d) * 3];
+          real fc[5];
+          euler_flux(&U[(e * n3 + va) * 5], &w->q[(e * n3 + va) * 6], Jaa, fc);
+          for (int k = 0; k < 5; ++k) w->Bc[(e * n3 + v) * 5 + k] += o->Dhat[i * n + a] * fc[k];
+          if (P->viscous) {
+            real fv[5];
+            visc_flux(P, &w->q[(e * n3 + va) * 6], &w->g[(e * n3 + va) * 12], Jaa, fv);
+            for (int k = 0; k < 5; ++k) w->B[(e * n3 + v) * 5 + k] -= o->Dhat[i * n + a] * fv[k];
+          }
+        }
+      }
+  }
+
+  /* ---- FillFlux + SurfInt over the faces ---- */
+  for (long e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      long ef = e * 6 + f;
+      if (!M->master[ef]) continue;
+      long e2 = M->nbr_e[ef];
+      int f2 = M->nbr_f[ef];
+      if (e2 < 0 ? (want && !want[e]) : (want && !want[e] && !want[e2])) continue;
+      for (int qq = 0; qq < n; ++qq)
+        for (int p = 0; p < n; ++p) {
+          long xM = ef * n2 + p + n * qq;
+          real nv[3];
+          face_normal(M, e, f, p, qq, nv);
+          real s = RSQRT(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+          real nu[3] = {nv[0] / s, nv[1] / s, nv[2] / s};
+          real fs[5];
+          if (e2 < 0) {
+            bc_flux(M, P, M->face_bc[ef], &Uf[xM * 5], &qf[xM * 6], &gf[xM * 12], nu, s, nv, fs);
+          } else {
+            long xS = ((long)e2 * 6 + f2) * n2 + M->nbr_node[xM];
+            real fc[5];
+            riemann(P, P->riemann, &Uf[xM * 5], &qf[xM * 6], &Uf[xS * 5], &qf[xS * 6], nu, fc);
+            for (int k = 0; k < 5; ++k) fs[k] = fc[k] * s;
+            if (P->viscous) {
+              real fvM[5], fvS[5];
+              visc_flux(P, &qf[xM * 6], &gf[xM * 12], nv, fvM);
+              visc_flux(P, &qf[xS * 6], &gf[xS * 12], nv, fvS);
+              for (int k = 0; k < 5; ++k) fs[k] -= (fvM[k] + fvS[k]) / 2;
+            }
+          }
+          if (fstar_out)
+            for (int k = 0; k < 5; ++k) fstar_out[xM * 5 + k] = fs[k];
+          surf_spread(M, w->B, 5, e, f, p, qq, fs, 1);
+          if (e2 >= 0) {
+            int a2 = M->nbr_node[xM];
+            surf_spread(M, w->B, 5, e2, f2, a2 % n, a2 / n, fs, -1);
+          }
+        }
+    }
+
+  /* ---- ApplyJac; sponge source ---- */
+  for (long e = 0; e < E; ++e) {
+    if (want && !want[e]) continue;
+    for (long v = 0; v < n3; ++v)
+      for (int k = 0; k < 5; ++k) {
+        long x = (e * n3 + v) * 5 + k;
+        Ut[x] = -(w->Bc[x] + w->B[x]) / M->J[e * n3 + v];
+        if (M->sponge_sigma) Ut[x] -= M->sponge_sigma[e * n3 + v] * (U[x] - M->sponge_base[x]);
+      }
+  }
+  if (g_out && P->viscous)
+    for (long x = 0; x < E * n3 * 12; ++x) g_out[x] = w->g[x];
+  free(Uf);
+  free(qf);
+  free(gf);
+  free(needg);
+  return 0;
+}
+
+/* the DG operator of the mesh's node set */
+static int rhs_any(const mesh_t* M, const params_t* P, const real* U, real* Ut, const unsigned char* want,
+                   real* alpha_out, real* g_out, real* fstar_out, work_t* w) {
+  if (M->o.gauss) {
+    if (alpha_out)
+      for (long e = 0; e < M->E; ++e) alpha_out[e] = 0;
+    return rhs_gauss(M, P, U, Ut, want, g_out, fstar_out, w);
+  }
+  return rhs_impl(M, P, U, Ut, want, alpha_out, g_out, fstar_out, w);
+}
+
 /* ------------------------------------------------------------------ */
 /* Time step and LSERK                                                 */
 /* ------------------------------------------------------------------ */
@@ -1072,9 +1411,12 @@ typedef struct {
 static void to_real(const double* a, real* b, long n) { for (long i = 0; i < n; ++i) b[i] = a[i]; }
 static void to_double(const real* a, double* b, long n) { for (long i = 0; i < n; ++i) b[i] = (double)a[i]; }
 
-int ORC(ops)(int N, double* x, double* w, double* D, double* Dhat, double* Dsplit, double* Vinv) {
+int ORC(ops)(int N, int gauss, double* x, double* w, double* D, double* Dhat, double* Dsplit, double* Vinv,
+             double* Lp, double* Lm) {
   ops_t o;
-  if (build_ops(N, &o)) return -1;
+  if (build_ops(N, gauss, &o)) return -1;
+  to_double(o.Lp, Lp, N + 1);
+  to_double(o.Lm, Lm, N + 1);
   int n = N + 1;
   to_double(o.x, x, n);
   to_double(o.w, w, n);
@@ -1090,12 +1432,14 @@ int ORC(ops)(int N, double* x, double* w, double* D, double* Dhat, double* Dspli
    (enough for rhs() with the same mask as `want`). */
 /* face_bc (may be NULL: every face has a partner): [E*6] boundary-condition
    row per face (0: inner face); bc: nbc rows of 9 doubles (type, 8 params) */
-void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, const unsigned char* metric_mask,
-                    const int* face_bc, int nbc, const double* bc, int* status) {
+/* gauss: 0 for the split-form scheme on LGL nodes, 1 for the standard scheme
+   on Gauss-Legendre nodes (xyz is still given at the LGL nodes: the geometry) */
+void* ORC(mesh_new)(int N, int gauss, long E, const double* xyz, const double* period,
+                    const unsigned char* metric_mask, const int* face_bc, int nbc, const double* bc, int* status) {
   handle_t* h = (handle_t*)calloc(1, sizeof(handle_t));
   mesh_t* M = &h->M;
   *status = 0;
-  if (build_ops(N, &M->o)) { *status = -1; free(h); return NULL; }
+  if (build_ops(N, gauss, &M->o)) { *status = -1; free(h); return NULL; }
   M->N = N; M->n = N + 1; M->n2 = M->n * M->n; M->n3 = M->n2 * M->n; M->E = E;
   for (int d = 0; d < 3; ++d) M->period[d] = period[d];
   long n3 = M->n3;
@@ -1107,6 +1451,8 @@ void* ORC(mesh_new)(int N, long E, const double* xyz, const double* period, cons
   M->master = (int*)malloc(sizeof(int) * E * 6);
   M->nbr_node = (int*)malloc(sizeof(int) * E * 6 * M->n2);
   to_real(xyz, M->xyz, E * n3 * 3);
+  M->xyzs = M->xyz;
+  if (gauss) M->xyzs = (real*)malloc(sizeof(real) * E * n3 * 3);
   if (nbc > 16) { *status = -6; nbc = 16; }
   M->nbc = nbc;
   for (int k = 0; k < nbc; ++k)
@@ -1165,6 +1511,7 @@ void ORC(mesh_free)(void* hv) {
   handle_t* h = (handle_t*)hv;
   if (!h) return;
   mesh_t* M = &h->M;
+  if (M->xyzs != M->xyz) free(M->xyzs);
   free(M->xyz); free(M->Ja); free(M->J); free(M->nbr_e); free(M->nbr_f); free(M->master);
   free(M->nbr_node);
   free(M->face_bc);
@@ -1181,6 +1528,12 @@ void ORC(connectivity)(void* hv, int* nbr_e, int* nbr_f, int* master, int* nbr_n
   memcpy(nbr_f, M->nbr_f, sizeof(int) * F);
   memcpy(master, M->master, sizeof(int) * F);
   memcpy(nbr_node, M->nbr_node, sizeof(int) * F * M->n2);
+}
+
+/* coordinates of the solution nodes [E][n3][3] */
+void ORC(node_xyz)(void* hv, double* xyz) {
+  mesh_t* M = &((handle_t*)hv)->M;
+  to_double(M->xyzs, xyz, M->E * M->n3 * 3);
 }
 
 void ORC(metrics)(void* hv, double* Ja, double* J) {
@@ -1207,7 +1560,7 @@ int ORC(rhs)(void* hv, const double* prm, const double* U, double* Ut, const uns
   real* al = alpha ? (real*)calloc(M->E, sizeof(real)) : NULL;
   real* gr = grad ? (real*)calloc(M->E * M->n3 * 12, sizeof(real)) : NULL;
   real* fr = fstar ? (real*)calloc(M->E * 6 * M->n2 * 5, sizeof(real)) : NULL;
-  int st = rhs_impl(M, &P, Ur, Utr, want, al, gr, fr, &h->w);
+  int st = rhs_any(M, &P, Ur, Utr, want, al, gr, fr, &h->w);
   if (fr) { to_double(fr, fstar, M->E * 6 * M->n2 * 5); free(fr); }
   for (long x = 0; x < len; ++x) Ut[x] = (double)Utr[x];
   if (al) { to_double(al, alpha, M->E); free(al); }
@@ -1221,7 +1574,7 @@ typedef struct { handle_t* h; params_t P; } dgctx_t;
 static void dg_rhs_cb(void* c, const real* U, real t, real* Ut) {
   dgctx_t* x = (dgctx_t*)c;
   (void)t;
-  rhs_impl(&x->h->M, &x->P, U, Ut, NULL, NULL, NULL, NULL, &x->h->w);
+  rhs_any(&x->h->M, &x->P, U, Ut, NULL, NULL, NULL, NULL, &x->h->w);
 }
 
 double ORC(dt)(void* hv, const double* prm, const double* U, int* nonfinite) {
@@ -1260,7 +1613,7 @@ int ORC(step)(void* hv, const double* prm, double* U, int n_steps, double dt_fix
 }
 
 /* E_k = 1/(2|Omega|) int rho |u|^2 and dE_k/dt = 1/|Omega| int (u.(rho u)_t - |u|^2 rho_t / 2)
-   by LGL quadrature (Sec. 5.2, with rho0 = U0 = 1) */
+   by the quadrature of the node set (Sec. 5.2, with rho0 = U0 = 1) */
 void ORC(kinetic)(void* hv, const double* U, const double* Ut, double* out) {
   mesh_t* M = &((handle_t*)hv)->M;
   int n = M->n;
@@ -1315,7 +1668,7 @@ void ORC(point_visc)(const double* prm, const double* U, const double* g, const 
 /* indicator of one element's state U[n3][5] at degree N */
 double ORC(indicator)(int N, const double* prm, const double* U, double* E_out) {
   static mesh_t M;
-  if (build_ops(N, &M.o)) return -1;
+  if (build_ops(N, 0, &M.o)) return -1;
   M.N = N; M.n = N + 1; M.n2 = M.n * M.n; M.n3 = M.n2 * M.n;
   params_t P = read_params(prm);
   real q[NMAX * NMAX * NMAX * 6], u[5];

@@ -422,6 +422,42 @@ def channel_bench(dg, torch, stream):
                         f"(one moving), Couette + perturbation, Re = 1000, 20 steps", **out}
 
 
+def gauss_bench(dg, torch, stream, nel=NEL, steps=20):
+    """The standard DGSEM on Gauss-Legendre nodes (Sec. 5.1's GL scheme) on the
+    main workload's mesh (curved, renumbered, rotated, N = 7), Taylor-Green
+    vortex at Ma = 0.1 sampled at the GL nodes, CFL steps in both precisions,
+    with each kernel kind's share of the step."""
+    from paper_2404_12703_gb300 import workloads as W
+    N = 7
+    m = W.box_mesh(N, (nel,) * 3, curved=0.1, seed=SEED)
+    dof = m["E"] * (N + 1) ** 3
+    out = {}
+    U0 = None
+    for name, prec in (("fp64", dg.FP64), ("fp32_bulk", dg.FP32_BULK)):
+        s = dg.Solver(m, stream=stream, precision=prec, nodes="gauss")
+        if U0 is None:
+            U0 = W.tgv_state(s.node_coords()).reshape(m["E"], -1, 5)
+        s.set_state(U0)
+        s.step(3)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        U, t = s.get_state()
+        prof = s.profile_step(3)
+        tot = sum(v[0] for v in prof.values())
+        out[name] = {"ms_per_step": ms, "dof_updates_per_s": dof * STAGES / (ms * 1e-3), "t": t,
+                     "finite": bool(np.isfinite(U).all()),
+                     "kernel_share": {k: v[0] / tot for k, v in prof.items()}}
+        s.close()
+    return {"workload": f"TGV Re 1600 Ma 0.1 on {nel}^3 curved elements, N = 7 ({dof} DOF), standard DGSEM "
+                        f"on Gauss-Legendre nodes, {steps} CFL steps", **out}
+
+
 def run_long(args):
     """FP32-bulk against FP64 over a long Taylor-Green run: 32^3 Cartesian
     elements at N = 5 (7,077,888 DOF), Re 1600, Ma 0.1, both precisions from
@@ -659,10 +695,11 @@ def run_ours(args):
     if not args.no_shock and rank == 0:
         shock = shock_tube_bench(dg, torch, stream)
 
-    comp = chan = None
+    comp = chan = gauss = None
     if not args.no_shock and rank == 0:
         comp = compressible_bench(dg, torch, stream)
         chan = channel_bench(dg, torch, stream)
+        gauss = gauss_bench(dg, torch, stream, nel=nel)
 
     serving = None
     if not args.no_serving and rank == 0:
@@ -689,7 +726,7 @@ def run_ours(args):
             "e2e": {"value": world * dof * STAGES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32, "shock_tube": shock, "compressible_tgv": comp,
-            "channel": chan,
+            "channel": chan, "gauss_nodes": gauss,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

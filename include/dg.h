@@ -85,7 +85,8 @@ void dg_default_params(dg_params* p);
    corner_vid[e][c]: vertex id of corner c = bi + 2 bj + 4 bk of element e,
      where bi = 0 for i = 0 and 1 for i = N (likewise j, k).  Faces are
      matched by their sets of corner ids; periodic images must share ids.
-   xyz[e][node][3]: physical coordinates of the LGL nodes (Eq. ansatz). */
+   xyz[e][node][3]: physical coordinates of the LGL nodes (Eq. ansatz): the
+     geometry, a polynomial of degree N per element, for both node sets. */
 typedef struct {
   int N;                       /* polynomial degree, 1 <= N <= 7 */
   int64_t n_elems;             /* number of elements E >= 1      */
@@ -113,7 +114,22 @@ typedef struct {
   const int* face_bc;
   int n_bc;
   const double* bc;
+  /* Node set of the solution (Sec. 2.2: GL or LGL interpolation points;
+     Sec. 5.1 runs the split form on LGL and the standard form on GL nodes):
+       DG_NODES_LGL (0): split-form DGSEM on Legendre-Gauss-Lobatto nodes;
+       DG_NODES_GAUSS (1): standard DGSEM on Legendre-Gauss nodes.  Its face
+         values are interpolations with l(+-1) (ProlongToFace), its volume
+         term the collocated flux divergence sum_a Dhat_ia (J a . F)_a, and
+         SurfInt reaches every node of a line with lhat+-_i = l_i(+-1)/w_i.
+         The metrics are the LGL curl-form polynomials evaluated at the GL
+         nodes (so both elements of a face agree on its normal and free
+         streams are preserved), J = det(dx/dxi) there.  No shock capturing
+         and no serving (dg_submit) on GL nodes; dg_node_coords gives the
+         solution nodes' coordinates. */
+  int nodes;
 } dg_mesh_desc;
+
+enum { DG_NODES_LGL = 0, DG_NODES_GAUSS = 1 };
 
 enum { DG_BC_WALL_ISOTHERMAL = 1, DG_BC_WALL_ADIABATIC = 2, DG_BC_SLIP = 3, DG_BC_STATE = 4, DG_BC_OUTFLOW = 5 };
 
@@ -131,10 +147,17 @@ typedef struct dg_ctx dg_ctx;
    On error *out is set to NULL. */
 int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params, void* stream);
 
+/* Coordinates of the solution nodes, [E][node][3] float64, on the host
+   (on_device = 0) or the device (1): the LGL nodes as given, or the
+   geometry polynomial evaluated at the Gauss-Legendre nodes.  Synchronises
+   the context's stream. */
+int dg_node_coords(dg_ctx* ctx, double* xyz, int on_device);
+
 /* Changes the stream later work is enqueued on. */
 int dg_set_stream(dg_ctx* ctx, void* stream);
 
-/* Replaces the parameters (same mesh).  The precision may be changed too. */
+/* Replaces the parameters (same mesh).  The precision may be changed too.
+   DG_ERR_ARG for shock capturing on Gauss-Legendre nodes. */
 int dg_set_params(dg_ctx* ctx, const dg_params* params);
 
 /* Copies a state into the context and sets the time t.
@@ -147,8 +170,9 @@ int dg_set_state(dg_ctx* ctx, const double* U, int on_device, double t);
    since the last dg_set_state met a non-finite value. */
 int dg_get_state(dg_ctx* ctx, double* U, int on_device, double* t);
 
-/* Ut = R(U), Eq. dgsem with the split-form volume integral, BR1 lifting and
-   (if enabled) sub-cell blending, for the state U_dev (device, public layout)
+/* Ut = R(U), Eq. dgsem with the split-form volume integral (LGL nodes) or
+   the standard one (GL nodes), BR1 lifting and (if enabled, LGL only)
+   sub-cell blending, for the state U_dev (device, public layout)
    or the context's own state when U_dev is NULL.  Ut_dev: caller-owned device
    buffer [E][node][5].  Stream-ordered (asynchronous). */
 int dg_rhs(dg_ctx* ctx, const double* U_dev, double* Ut_dev);
@@ -174,8 +198,9 @@ int dg_advance(dg_ctx* ctx, double t_end, int64_t max_steps, double* t_out, int6
 /* Same work as dg_step, launched kernel by kernel (no graph) with CUDA events
    recorded on the context's stream around every launch.  Accumulates, per
    kernel kind k, the summed device time ms[k] and the launch count
-   launches[k]: k = 0 CFL reduction, 1 BR1 surface prolongation, 2 lifting,
-   3 surface flux, 4 volume integral + SurfInt + ApplyJac + RK update.  Both
+   launches[k]: k = 0 CFL reduction, 1 BR1 surface prolongation (on GL
+   nodes also the ProlongToFace of the state), 2 lifting, 3 surface flux,
+   4 volume integral + SurfInt + ApplyJac + RK update.  Both
    arrays have 5 entries.  Synchronises after every step. */
 int dg_profile_step(dg_ctx* ctx, int n_steps, double dt, double* ms, int64_t* launches);
 
@@ -201,7 +226,9 @@ int dg_set_sponge(dg_ctx* ctx, const double* sigma, const double* U_base);
    lift D, lift 2D, volume D default mapping, volume D other mapping, volume
    2D default, volume 2D other, side kernels at 256, at 128.  Synchronises.
    Elements per block change no arithmetic; the volume mapping changes the
-   summation order of the split-form sums (both within the FP64 parity). */
+   summation order of the split-form sums (both within the FP64 parity).
+   DG_ERR_STATE on Gauss-Legendre nodes (their kernels have one launch
+   configuration). */
 int dg_autotune(dg_ctx* ctx, int* config, double* ms);
 
 /* Sets (config, 4 ints as above; 0 / -1 entries select the defaults) or

@@ -71,9 +71,8 @@ static ld legendreP(int N, ld x) {
   return b;
 }
 
-static void build_ops(int N, Ops& o) {
-  const int n = N + 1;
-  ld x[NPMAX], w[NPMAX], D[NPMAX * NPMAX], lam[NPMAX];
+// LGL nodes and weights of degree N
+static void lgl_nodes(int N, ld* x, ld* w) {
   x[0] = -1;
   x[N] = 1;
   const int m = N - 1;
@@ -90,10 +89,36 @@ static void build_ops(int N, Ops& o) {
     }
     x[j] = t;
   }
-  for (int j = 0; j < n; ++j) {
+  for (int j = 0; j <= N; ++j) {
     ld P = legendreP(N, x[j]);
     w[j] = 2 / ((ld)N * (N + 1) * P * P);
   }
+}
+
+// Gauss-Legendre nodes (the zeros of P_{N+1}) and weights
+// 2 / ((1 - x^2) P_{N+1}'(x)^2), with P_m' = m (P_{m-1} - x P_m) / (1 - x^2)
+static void gauss_nodes(int N, ld* x, ld* w) {
+  const int m = N + 1;
+  for (int j = 0; j < m; ++j) {
+    ld t = -std::cos((ld)M_PI * (j + 0.75L) / (m + 0.5L));
+    ld dP = 1;
+    for (int it = 0; it < 100; ++it) {
+      const ld P = legendreP(m, t), P1 = legendreP(m - 1, t);
+      dP = (ld)m * (P1 - t * P) / (1 - t * t);
+      const ld step = P / dP;
+      t -= step;
+      if (std::fabs(step) < 1e-30L) break;
+    }
+    const ld P1 = legendreP(m - 1, t), P = legendreP(m, t);
+    dP = (ld)m * (P1 - t * P) / (1 - t * t);
+    x[j] = t;
+    w[j] = 2 / ((1 - t * t) * dP * dP);
+  }
+}
+
+// D[i][j] = l_j'(x_i) from barycentric weights
+static void derivative_matrix(int n, const ld* x, ld* D) {
+  ld lam[NPMAX];
   for (int j = 0; j < n; ++j) {
     ld p = 1;
     for (int k = 0; k < n; ++k)
@@ -109,11 +134,36 @@ static void build_ops(int N, Ops& o) {
     }
     D[i * n + i] = -s;
   }
+}
+
+// Lagrange basis l_j(y) of the nodes x
+static ld lagrange(int n, const ld* x, int j, ld y) {
+  ld v = 1;
+  for (int k = 0; k < n; ++k)
+    if (k != j) v *= (y - x[k]) / (x[j] - x[k]);
+  return v;
+}
+
+static void build_ops(int N, int gauss, Ops& o) {
+  const int n = N + 1;
+  ld xl[NPMAX], wl[NPMAX], Dl[NPMAX * NPMAX];
+  ld x[NPMAX], w[NPMAX], D[NPMAX * NPMAX];
+  lgl_nodes(N, xl, wl);
+  derivative_matrix(n, xl, Dl);
+  if (gauss) {
+    gauss_nodes(N, x, w);
+    derivative_matrix(n, x, D);
+  } else {
+    for (int i = 0; i < n; ++i) x[i] = xl[i], w[i] = wl[i];
+    for (int i = 0; i < n * n; ++i) D[i] = Dl[i];
+  }
   memset(&o, 0, sizeof(o));
   for (int i = 0; i < n; ++i) {
     o.x[i] = (double)x[i];
     o.w[i] = (double)w[i];
     o.winv[i] = (double)(1 / w[i]);
+    o.Lp[i] = gauss ? (double)lagrange(n, x, i, 1) : (i == N ? 1.0 : 0.0);
+    o.Lm[i] = gauss ? (double)lagrange(n, x, i, -1) : (i == 0 ? 1.0 : 0.0);
   }
   for (int i = 0; i < n; ++i)
     for (int a = 0; a < n; ++a) {
@@ -122,14 +172,21 @@ static void build_ops(int N, Ops& o) {
       o.Dlo[i * n + a] = (double)(d - (ld)o.D[i * n + a]);
       // weak operator: Dhat_ia = -(w_a / w_i) D_ai
       o.Dhat[i * n + a] = (double)(-(w[a] / w[i]) * D[a * n + i]);
-      // split operator: 2 D plus the two surface corrections
+      // split operator (LGL): 2 D plus the two surface corrections
       ld ds = 2 * d;
       if (i == N && a == N) ds -= 1 / w[N];
       if (i == 0 && a == 0) ds += 1 / w[0];
-      o.Dsplit[i * n + a] = (double)ds;
+      o.Dsplit[i * n + a] = gauss ? 0.0 : (double)ds;
+      const ld dg = Dl[i * n + a];
+      o.Dg[i * n + a] = (double)dg;
+      o.Dg_lo[i * n + a] = (double)(dg - (ld)o.Dg[i * n + a]);
+      const ld ig = gauss ? lagrange(n, xl, a, x[i]) : (ld)(i == a ? 1 : 0);
+      o.Ig[i * n + a] = (double)ig;
+      o.Ig_lo[i * n + a] = (double)(ig - (ld)o.Ig[i * n + a]);
     }
   // inverse Vandermonde of the orthonormal Legendre basis by discrete
-  // orthogonality of the LGL quadrature: c_m = sum_i w_i L_m(x_i) u_i / gamma_m
+  // orthogonality of the quadrature (exact to degree 2N - 1 on LGL, 2N + 1 on
+  // GL): c_m = sum_i w_i L_m(x_i) u_i / gamma_m
   ld L[NPMAX * NPMAX];
   for (int mm = 0; mm < n; ++mm)
     for (int i = 0; i < n; ++i) L[mm * n + i] = std::sqrt((ld)(2 * mm + 1) / 2) * legendreP(mm, x[i]);
@@ -144,7 +201,7 @@ int set_error(int code, const std::string& msg) { return fail(code, msg); }
 
 void lgl_weights(int N, double* w) {
   Ops o;
-  build_ops(N, o);
+  build_ops(N, 0, o);
   for (int i = 0; i <= N; ++i) w[i] = o.w[i];
 }
 
@@ -206,6 +263,11 @@ int alloc_side_arrays(dg_ctx* c, std::string& msg) {
   if (e == cudaSuccess) e = dalloc(c, &c->side_e, S);
   if (e == cudaSuccess) e = dalloc(c, &c->side_f, S);
   if (e == cudaSuccess) e = dalloc(c, &c->side_bc, S);
+  if (c->gauss) {
+    if (e == cudaSuccess) e = dalloc(c, &c->Ufc, S * 2 * 5 * n2);
+    if (e == cudaSuccess) e = dalloc(c, &c->gfc, S * 2 * 12 * n2);
+    if (e == cudaSuccess) e = dalloc(c, &c->gfc32, S * 2 * 12 * n2);
+  }
   if (e != cudaSuccess) {
     msg = std::string("side arrays: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
@@ -324,6 +386,10 @@ void dg_destroy(dg_ctx* c) {
   dfree(c, c->bcdata);
   dfree(c, c->sponge_sigma);
   dfree(c, c->sponge_base);
+  dfree(c, c->xyzs);
+  dfree(c, c->Ufc);
+  dfree(c, c->gfc);
+  dfree(c, c->gfc32);
   dfree(c, c->ops);
   dfree(c, c->scal);
   if (c->scal_host) cudaFreeHost(c->scal_host);
@@ -383,7 +449,7 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
   if (e == cudaSuccess) e = init_kernel_attributes(N);
   if (e == cudaSuccess) {
     Ops ops;
-    build_ops(N, ops);
+    build_ops(N, 0, ops);
     A(cudaMemcpyAsync(c->ops, &ops, sizeof(Ops), cudaMemcpyHostToDevice, stream));
     A(cudaMemsetAsync(c->scal, 0, sizeof(DevScalars), stream));
     A(cudaMemsetAsync(c->U, 0, sizeof(double) * E * 5 * n3, stream));
@@ -437,12 +503,16 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
     for (int64_t a = 0; a < 6 * mesh->n_elems; ++a)
       if (mesh->face_bc[a] < 0 || mesh->face_bc[a] > mesh->n_bc) return fail(DG_ERR_ARG, "face_bc out of range");
   }
+  if (mesh->nodes != DG_NODES_LGL && mesh->nodes != DG_NODES_GAUSS) return fail(DG_ERR_ARG, "unknown node set");
   int st = check_params(params);
   if (st != DG_OK) return st;
+  if (mesh->nodes == DG_NODES_GAUSS && params->shock_capturing)
+    return fail(DG_ERR_ARG, "shock capturing needs LGL nodes (the sub-cell FV scheme lives on the LGL sub-cells)");
   dg_ctx* c = new dg_ctx();
   cudaGetDevice(&c->device);
   c->stream = stream;
   c->pool_stream = pool_stream;
+  c->gauss = mesh->nodes == DG_NODES_GAUSS;
   c->prm = *params;
   c->N = mesh->N;
   c->n = c->N + 1;
@@ -464,6 +534,7 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
   A(dalloc(c, &c->fvmetric, E * 3 * (c->n - 1) * 3 * c->n2));
   A(dalloc(c, &c->cflgeo, E * 4 * n3));
   A(dalloc(c, &c->elem_side, E * 6));
+  A(dalloc(c, &c->xyzs, E * n3 * 3));
   A(dalloc(c, &c->ops, 1));
   A(dalloc(c, &c->scal, 1));
   if (e == cudaSuccess && !pool_stream) e = cudaMallocHost(&c->scal_host, sizeof(DevScalars));
@@ -475,7 +546,7 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
   }
   if (e == cudaSuccess) e = init_kernel_attributes(c->N);
   Ops ops;
-  build_ops(c->N, ops);
+  build_ops(c->N, c->gauss, ops);
   A(cudaMemcpyAsync(c->ops, &ops, sizeof(Ops), cudaMemcpyHostToDevice, c->stream));
   A(cudaMemsetAsync(c->scal, 0, sizeof(DevScalars), c->stream));
   A(cudaMemsetAsync(c->alpha, 0, sizeof(double) * E, c->stream));
@@ -516,6 +587,16 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params
   return dg::init_mesh_impl(out, mesh, params, (cudaStream_t)stream, nullptr);
 }
 
+int dg_node_coords(dg_ctx* c, double* xyz, int on_device) {
+  if (!c || !xyz) return fail(DG_ERR_ARG, "ctx or xyz is NULL");
+  if (!c->xyzs) return fail(DG_ERR_STATE, "the context has no mesh of its own");
+  cudaError_t e = cudaMemcpyAsync(xyz, c->xyzs, sizeof(double) * c->E * c->n3 * 3,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_node_coords");
+  return DG_OK;
+}
+
 int dg_set_stream(dg_ctx* c, void* stream) {
   if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
   c->stream = (cudaStream_t)stream;
@@ -526,6 +607,8 @@ int dg_set_params(dg_ctx* c, const dg_params* p) {
   if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
   int st = check_params(p);
   if (st != DG_OK) return st;
+  if (c->gauss && p->shock_capturing)
+    return fail(DG_ERR_ARG, "shock capturing needs LGL nodes (the sub-cell FV scheme lives on the LGL sub-cells)");
   c->prm = *p;
   destroy_graph(c);
   if (c->state_set) {
@@ -780,6 +863,7 @@ static void variants_of(int N, int& D, bool& lift2, bool& vol2) {
 int dg_autotune(dg_ctx* c, int* config, double* ms) {
   if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
+  if (c->gauss) return fail(DG_ERR_STATE, "the Gauss-Legendre kernels have one launch configuration");
   double t[8];
   cudaError_t e = launch_autotune(c, t);
   if (e != cudaSuccess) return cuda_fail(e, "dg_autotune");

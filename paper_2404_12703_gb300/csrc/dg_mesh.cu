@@ -184,23 +184,31 @@ __global__ void k_fill_sides(int64_t F_total, const long long* cvid, const int* 
 }
 
 // ---------------------------------------------------------------------------
-// Metrics in double-double (curl form), rounded; 1/J; sub-cell interface
-// metrics by telescoping the discrete derivative.
+// Metrics in double-double (curl form) on the LGL nodes of the geometry; on
+// Gauss-Legendre nodes the same polynomials (J a^d and dx/dxi) evaluated at
+// the GL nodes by exact interpolation, J = det(dx/dxi) there.  1/J; the
+// solution nodes' coordinates; sub-cell interface metrics (LGL) by
+// telescoping the discrete derivative.
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1)) k_metrics(int E, const double* __restrict__ xyz,
-                                                                        const Ops* __restrict__ ops,
+                                                                        const Ops* __restrict__ ops, int gauss,
                                                                         double* __restrict__ metric,
-                                                                        double* __restrict__ fvm) {
+                                                                        double* __restrict__ fvm,
+                                                                        double* __restrict__ xyzs) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  dd* sD = reinterpret_cast<dd*>(smem_raw);      // [n2]
-  dd* sX = sD + n2;                              // [3][n3]
+  dd* sD = reinterpret_cast<dd*>(smem_raw);      // [n2] LGL D
+  dd* sI = sD + n2;                              // [n2] LGL -> solution nodes
+  dd* sX = sI + n2;                              // [3][n3]
   dd* sV = sX + 3 * n3;                          // [3][n3]
   const int e = blockIdx.x;
   const int t = threadIdx.x;
   if (e >= E) return;
-  for (int k = t; k < n2; k += n3) sD[k] = {ops->D[k], ops->Dlo[k]};
+  for (int k = t; k < n2; k += n3) {
+    sD[k] = {ops->Dg[k], ops->Dg_lo[k]};
+    sI[k] = {ops->Ig[k], ops->Ig_lo[k]};
+  }
   const double* X = xyz + (size_t)e * n3 * 3;
   for (int c = 0; c < 3; ++c) sX[c * n3 + t] = two_sum(X[t * 3 + c], -X[c]);
   __syncwarp();
@@ -218,14 +226,7 @@ __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1)) k_metrics(int E, 
       for (int a = 0; a < n; ++a) s = dd_add(s, dd_mul(sD[idx[d] * n + a], sX[c * n3 + base + a * str[d]]));
       dx[c][d] = s;
     }
-  // J = det(dx / dxi)
-  dd J = dd_sub(dd_mul(dx[1][1], dx[2][2]), dd_mul(dx[1][2], dx[2][1]));
-  J = dd_mul(dx[0][0], J);
-  J = dd_sub(J, dd_mul(dx[0][1], dd_sub(dd_mul(dx[1][0], dx[2][2]), dd_mul(dx[1][2], dx[2][0]))));
-  J = dd_add(J, dd_mul(dx[0][2], dd_sub(dd_mul(dx[1][0], dx[2][1]), dd_mul(dx[1][1], dx[2][0]))));
-  double* Me = metric + (size_t)e * 10 * n3;
-  const double Jd = dd_to_double(J);
-  Me[9 * n3 + t] = 1.0 / Jd;
+  dd Ja[3][3];  // Ja[d][c] = (J a^d)_c
   for (int nc = 0; nc < 3; ++nc) {
     const int m = (nc + 1) % 3, l = (nc + 2) % 3;
 #pragma unroll
@@ -241,10 +242,57 @@ __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1)) k_metrics(int E, 
         a1 = dd_add(a1, dd_mul(sD[idx[i1] * n + a], sV[i2 * n3 + b1 + a * str[i1]]));
         a2 = dd_add(a2, dd_mul(sD[idx[i2] * n + a], sV[i1 * n3 + b2 + a * str[i2]]));
       }
-      Me[(ii * 3 + nc) * n3 + t] = -dd_to_double(dd_sub(a1, a2));
+      Ja[ii][nc] = dd_neg(dd_sub(a1, a2));
     }
     __syncthreads();
   }
+  dd Xs[3];  // relative coordinates of the solution node
+#pragma unroll
+  for (int c = 0; c < 3; ++c) Xs[c] = sX[c * n3 + t];
+  if (gauss) {
+    // tensor-product interpolation to the GL nodes, one direction at a time
+    // (sV is free now); every thread takes every barrier
+    dd* B0 = sV;
+    dd* B1 = sV + n3;
+    auto interp = [&](dd v) -> dd {
+      B0[t] = v;
+      __syncthreads();
+#pragma unroll 1
+      for (int d = 0; d < 3; ++d) {
+        const dd* src = d == 1 ? B1 : B0;
+        dd* dst = d == 1 ? B0 : B1;
+        const int base = t - idx[d] * str[d];
+        dd s = dd_from(0.0);
+        for (int a = 0; a < n; ++a) s = dd_add(s, dd_mul(sI[idx[d] * n + a], src[base + a * str[d]]));
+        dst[t] = s;
+        __syncthreads();
+      }
+      const dd r = B1[t];
+      __syncthreads();
+      return r;
+    };
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d) {
+        dx[c][d] = interp(dx[c][d]);
+        Ja[c][d] = interp(Ja[c][d]);
+      }
+    for (int c = 0; c < 3; ++c) Xs[c] = interp(Xs[c]);
+  }
+  // J = det(dx / dxi)
+  dd J = dd_sub(dd_mul(dx[1][1], dx[2][2]), dd_mul(dx[1][2], dx[2][1]));
+  J = dd_mul(dx[0][0], J);
+  J = dd_sub(J, dd_mul(dx[0][1], dd_sub(dd_mul(dx[1][0], dx[2][2]), dd_mul(dx[1][2], dx[2][0]))));
+  J = dd_add(J, dd_mul(dx[0][2], dd_sub(dd_mul(dx[1][0], dx[2][1]), dd_mul(dx[1][1], dx[2][0]))));
+  double* Me = metric + (size_t)e * 10 * n3;
+  Me[9 * n3 + t] = 1.0 / dd_to_double(J);
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Me[(d * 3 + c) * n3 + t] = dd_to_double(Ja[d][c]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) xyzs[((size_t)e * n3 + t) * 3 + c] = dd_to_double(dd_add(Xs[c], dd_from(X[c])));
+  __syncthreads();
+  if (gauss) return;
   // sub-cell interface metrics (global writes above are visible after the barrier)
   for (int tt = t; tt < 3 * n2; tt += n3) {
     const int d = tt / n2, line = tt % n2;
@@ -267,9 +315,13 @@ __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1)) k_metrics(int E, 
   }
 }
 
+// surface normal s n (outward for the master) and surface element s of every
+// side node: J a^d of the master's face direction at the face node (LGL) or
+// interpolated to the face with l(+-1) (GL)
 template <int N>
 __global__ void k_side_geom(int S, const int2* __restrict__ side_e, const int* __restrict__ side_f,
-                            const double* __restrict__ metric, double* __restrict__ nrm) {
+                            const double* __restrict__ metric, const Ops* __restrict__ ops, int gauss,
+                            double* __restrict__ nrm) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= (int64_t)S * n2) return;
@@ -279,7 +331,18 @@ __global__ void k_side_geom(int S, const int2* __restrict__ side_e, const int* _
   const double sg = (fM & 1) ? 1.0 : -1.0;
   const double* Me = metric + (size_t)eM * 10 * n3 + (fM >> 1) * 3 * n3;
   double sn[3];
-  for (int c = 0; c < 3; ++c) sn[c] = sg * Me[c * n3 + v];
+  if (gauss) {
+    const int d = fM >> 1, st = d == 0 ? 1 : (d == 1 ? n : n2);
+    const int v0 = v - ((fM & 1) ? n - 1 : 0) * st;  // node 0 of the line
+    const double* L = (fM & 1) ? ops->Lp : ops->Lm;
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int a = 0; a < n; ++a) acc += L[a] * Me[c * n3 + v0 + a * st];
+      sn[c] = sg * acc;
+    }
+  } else {
+    for (int c = 0; c < 3; ++c) sn[c] = sg * Me[c * n3 + v];
+  }
   double* out = nrm + (size_t)s * 4 * n2;
   out[pq] = sn[0];
   out[n2 + pq] = sn[1];
@@ -332,13 +395,14 @@ __global__ void k_round_f32(int64_t n, const double* __restrict__ src, float* __
 template <int N>
 static cudaError_t launch_metrics(dg_ctx* c, const double* d_xyz) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-  const size_t sm = sizeof(dd) * (n2 + 6 * n3);
+  const size_t sm = sizeof(dd) * (2 * n2 + 6 * n3);
   cudaFuncSetAttribute(k_metrics<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_metrics<N><<<(unsigned)c->E, n3, sm, c->stream>>>((int)c->E, d_xyz, c->ops, c->metric, c->fvmetric);
+  k_metrics<N><<<(unsigned)c->E, n3, sm, c->stream>>>((int)c->E, d_xyz, c->ops, c->gauss, c->metric, c->fvmetric,
+                                                      c->xyzs);
   count_launch();
   const int64_t tot = c->S * n2;
   k_side_geom<N><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>((int)c->S, c->side_e, c->side_f, c->metric,
-                                                                       c->nrm);
+                                                                       c->ops, c->gauss, c->nrm);
   const int64_t nodes = c->E * n3;
   k_cfl_geo<N><<<(unsigned)((nodes + 255) / 256), 256, 0, c->stream>>>((int)c->E, c->metric, c->cflgeo);
   k_nrm32<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(tot, n2, c->nrm, c->nrm32);

@@ -1061,6 +1061,7 @@ int dg_submit(dg_server* s, const dg_case_desc* d, int64_t* ticket) {
       (d->riemann != DG_RIEMANN_ROE && d->riemann != DG_RIEMANN_LF))
     return set_error(DG_ERR_ARG, "dg_submit: bad t_end, mu, cfl or riemann");
   if (m.face_bc) return set_error(DG_ERR_ARG, "dg_submit: serving takes periodic meshes only");
+  if (m.nodes != DG_NODES_LGL) return set_error(DG_ERR_ARG, "dg_submit: serving takes LGL-node cases only");
   Request r;
   r.N = m.N;
   r.E = m.n_elems;

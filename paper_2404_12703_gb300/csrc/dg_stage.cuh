@@ -62,12 +62,14 @@ struct TBuf<double> {
   static __host__ __device__ double* g(const StageArgs& a) { return a.g; }
   static __host__ __device__ double* lflux(const StageArgs& a) { return a.lflux; }
   static __host__ __device__ double* fstar(const StageArgs& a) { return a.fstar; }
+  static __host__ __device__ double* gfc(const StageArgs& a) { return a.gfc; }
 };
 template <>
 struct TBuf<float> {
   static __host__ __device__ float* g(const StageArgs& a) { return a.g32; }
   static __host__ __device__ float* lflux(const StageArgs& a) { return a.lflux32; }
   static __host__ __device__ float* fstar(const StageArgs& a) { return a.fstar32; }
+  static __host__ __device__ float* gfc(const StageArgs& a) { return a.gfc32; }
 };
 
 // ---------------------------------------------------------------------------
@@ -348,7 +350,9 @@ __device__ __forceinline__ void bc_flux(const StageArgs& a, const CaseParams& cp
 // ---------------------------------------------------------------------------
 // BR1 surface flux of the lifted primitives
 // ---------------------------------------------------------------------------
-template <int N, typename T>
+// GL: the side's two face states come from the ProlongToFace array (master
+// face frame) instead of the face nodes of the elements
+template <int N, typename T, bool GL = false>
 __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   using S = Shape<N>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3;
@@ -376,9 +380,10 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   }
   const int vM = face_vol_node<n>(fM, p, q);
   double UM[5];
-  const double* uM = a.U + (size_t)ee.x * 5 * n3 + vM;
+  const double* uM = GL ? a.Ufc + (size_t)s * 10 * n2 + pq : a.U + (size_t)ee.x * 5 * n3 + vM;
+  constexpr int ust = GL ? n2 : n3;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) UM[k] = uM[k * n3];
+  for (int k = 0; k < 5; ++k) UM[k] = uM[k * ust];
   const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
   T qa[4];
   const int brow = a.side_bc ? a.side_bc[s] : -1;
@@ -389,9 +394,9 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
     flip_to_slave<n>(flip, p, q, ps, qs);
     const int vS = face_vol_node<n>(fS, ps, qs);
     double US[5];
-    const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
+    const double* uS = GL ? a.Ufc + (size_t)s * 10 * n2 + 5 * n2 + pq : a.U + (size_t)ee.y * 5 * n3 + vS;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) US[k] = uS[k * n3];
+    for (int k = 0; k < 5; ++k) US[k] = uS[k * ust];
     const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
     qa[0] = T(0.5) * (qM.u + qS.u), qa[1] = T(0.5) * (qM.v + qS.v), qa[2] = T(0.5) * (qM.w + qS.w);
     qa[3] = T(0.5) * (qM.Tt + qS.Tt);
@@ -540,7 +545,8 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS) k_lift(StageArgs a) {
 // ---------------------------------------------------------------------------
 // FillFlux: Riemann flux + BR1 viscous flux, times the surface element
 // ---------------------------------------------------------------------------
-template <int N, typename T>
+// GL: states and lifted gradients from the ProlongToFace arrays
+template <int N, typename T, bool GL = false>
 __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   using S = Shape<N>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3;
@@ -571,19 +577,21 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   }
   const int vM = face_vol_node<n>(fM, p, q);
   double UM[5];
-  const double* uM = a.U + (size_t)ee.x * 5 * n3 + vM;
+  const double* uM = GL ? a.Ufc + (size_t)s * 10 * n2 + pq : a.U + (size_t)ee.x * 5 * n3 + vM;
+  constexpr int ust = GL ? n2 : n3;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) UM[k] = uM[k * n3];
+  for (int k = 0; k < 5; ++k) UM[k] = uM[k * ust];
   const SPrim<T> qM = shifted_prim<T>(UM, a.gm1, a.Rinv, cp);
   const T* G = TBuf<T>::g(a);
+  const T* Gf = TBuf<T>::gfc(a);
   T f[5];
   const int brow = a.side_bc ? a.side_bc[s] : -1;
   if (brow >= 0) {  // boundary side
     T gM[12];
     if (a.viscous) {
-      const T* pgM = G + (size_t)ee.x * 12 * n3 + vM;
+      const T* pgM = GL ? Gf + (size_t)s * 24 * n2 + pq : G + (size_t)ee.x * 12 * n3 + vM;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) gM[k] = pgM[k * n3];
+      for (int k = 0; k < 12; ++k) gM[k] = pgM[k * ust];
     } else {
 #pragma unroll
       for (int k = 0; k < 12; ++k) gM[k] = T(0);
@@ -594,9 +602,9 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
     flip_to_slave<n>(flip, p, q, ps, qs);
     const int vS = face_vol_node<n>(fS, ps, qs);
     double US[5];
-    const double* uS = a.U + (size_t)ee.y * 5 * n3 + vS;
+    const double* uS = GL ? a.Ufc + (size_t)s * 10 * n2 + 5 * n2 + pq : a.U + (size_t)ee.y * 5 * n3 + vS;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) US[k] = uS[k * n3];
+    for (int k = 0; k < 5; ++k) US[k] = uS[k * ust];
     const SPrim<T> qS = shifted_prim<T>(US, a.gm1, a.Rinv, cp);
     if (cp.riemann == DG_RIEMANN_ROE) roe_flux_s(qM, qS, nu, pick<T>(a.gm1, a.f_gm1), pick<T>(cp.Hr, cp.fHr), f);
     else lf_flux_s(qM, qS, nu, pick<T>(a.gamma, a.f_gamma), pick<T>(cp.pr, cp.fpr), f);
@@ -604,10 +612,10 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
     for (int k = 0; k < 5; ++k) f[k] *= sA;
     if (a.viscous) {
       T gM[12], gS[12];
-      const T* pgM = G + (size_t)ee.x * 12 * n3 + vM;
-      const T* pgS = G + (size_t)ee.y * 12 * n3 + vS;
+      const T* pgM = GL ? Gf + (size_t)s * 24 * n2 + pq : G + (size_t)ee.x * 12 * n3 + vM;
+      const T* pgS = GL ? Gf + (size_t)s * 24 * n2 + 12 * n2 + pq : G + (size_t)ee.y * 12 * n3 + vS;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) { gM[k] = pgM[k * n3]; gS[k] = pgS[k * n3]; }
+      for (int k = 0; k < 12; ++k) { gM[k] = pgM[k * ust]; gS[k] = pgS[k * ust]; }
       T tau[6], W[3], fvM[4], fvS[4], vmu, vlam;
       visc_coeffs<T>(a, cp, qM.Tt, vmu, vlam);
       viscous_parts(gM, qM.u, qM.v, qM.w, vmu, vlam, tau, W);
@@ -1108,6 +1116,12 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
   }
 }
 
+}  // namespace dg
+
+#include "dg_stage_gl.cuh"
+
+namespace dg {
+
 // ---------------------------------------------------------------------------
 // host side: launch arguments, shared-memory sizes, one RHS evaluation
 // ---------------------------------------------------------------------------
@@ -1163,6 +1177,9 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.bcdata = c->bcdata;
   a.sponge_sigma = c->sponge_sigma;
   a.sponge_base = c->sponge_base;
+  a.Ufc = c->Ufc;
+  a.gfc = c->gfc;
+  a.gfc32 = c->gfc32;
   if (c->elem_list) {
     a.E = (int)c->n_elem_list;
     a.S = (int)c->n_side_list;
@@ -1199,13 +1216,13 @@ inline void launch_vol(const StageArgs& a, cudaStream_t st) {
   k_volume<N, MODE, T, E, PR>
       <<<(unsigned)((a.E + S::EPB - 1) / S::EPB), S::THREADS, VolumeSmem<N, T, E, PR>::bytes, st>>>(a);
 }
-template <int N, typename T>
+template <int N, typename T, bool GL = false>
 inline void launch_side(const StageArgs& a, int block, cudaStream_t st, bool prims) {
   const int64_t side_nodes = (int64_t)a.S * Shape<N>::n2;
   const int b = block == 128 ? 128 : 256;
   const unsigned g = (unsigned)((side_nodes + b - 1) / b);
-  if (prims) k_surf_prims<N, T><<<g, b, 0, st>>>(a);
-  else k_surf_flux<N, T><<<g, b, 0, st>>>(a);
+  if (prims) k_surf_prims<N, T, GL><<<g, b, 0, st>>>(a);
+  else k_surf_flux<N, T, GL><<<g, b, 0, st>>>(a);
 }
 
 template <int N, typename T>
@@ -1248,6 +1265,10 @@ cudaError_t stage_set_attrs() {
   };
   lift(k_lift<N, T, 0>, lift_smem_bytes<N, T, 0>());
   if constexpr (V::lift2) lift(k_lift<N, T, 2 * V::D>, lift_smem_bytes<N, T, 2 * V::D>());
+  lift(k_prolong_gl<N>, gl_prolong_smem<N>());
+  lift(k_lift_gl<N, T>, gl_lift_smem<N, T>());
+  lift(k_volume_gl<N, 0, T>, gl_volume_smem<N, T>());
+  lift(k_volume_gl<N, 1, T>, gl_volume_smem<N, T>());
   lift(k_volume<N, 0, T, 0, V::fp64>, VolumeSmem<N, T, 0, V::fp64>::bytes);
   lift(k_volume<N, 1, T, 0, V::fp64>, VolumeSmem<N, T, 0, V::fp64>::bytes);
   if constexpr (V::fp64) lift(k_volume<N, 1, T, 0, false>, VolumeSmem<N, T, 0, false>::bytes);
@@ -1258,8 +1279,45 @@ cudaError_t stage_set_attrs() {
   return cudaGetLastError();
 }
 
+// One stage of the standard DGSEM on Gauss-Legendre nodes: ProlongToFace,
+// (lifting,) surface flux, volume integral with SurfInt and ApplyJac
+template <int N, typename T>
+cudaError_t stage_launch_gl(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first) {
+  using S = Shape<N>;
+  StageArgs a = make_stage_args(c, U);
+  a.Ut = c->Ut;
+  a.Urk = c->U;
+  a.dU = c->dU;
+  a.rkA = rkA;
+  a.rkB = rkB;
+  a.first_stage = first;
+  if (a.E == 0) return cudaSuccess;
+  const unsigned nb = (unsigned)((a.E + S::EPB - 1) / S::EPB);
+  const int sb = c->cfg.side_block;
+  prof_begin(c, PK_SURF_PRIMS);
+  k_prolong_gl<N><<<nb, S::THREADS, gl_prolong_smem<N>(), c->stream>>>(a);
+  if (c->prm.viscous) launch_side<N, T, true>(a, sb, c->stream, true);
+  prof_end(c);
+  if (c->prm.viscous) {
+    prof_begin(c, PK_LIFT);
+    k_lift_gl<N, T><<<nb, S::THREADS, gl_lift_smem<N, T>(), c->stream>>>(a);
+    prof_end(c);
+    count_launch(2);
+  }
+  prof_begin(c, PK_SURF_FLUX);
+  launch_side<N, T, true>(a, sb, c->stream, false);
+  prof_end(c);
+  prof_begin(c, PK_VOLUME);
+  if (mode == 0) k_volume_gl<N, 0, T><<<nb, S::THREADS, gl_volume_smem<N, T>(), c->stream>>>(a);
+  else k_volume_gl<N, 1, T><<<nb, S::THREADS, gl_volume_smem<N, T>(), c->stream>>>(a);
+  prof_end(c);
+  count_launch(3);
+  return cudaGetLastError();
+}
+
 template <int N, typename T>
 cudaError_t stage_launch(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first) {
+  if (c->gauss) return stage_launch_gl<N, T>(c, U, mode, rkA, rkB, first);
   StageArgs a = make_stage_args(c, U);
   a.Ut = c->Ut;
   a.Urk = c->U;

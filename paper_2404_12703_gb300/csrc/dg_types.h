@@ -11,16 +11,22 @@ namespace dg {
 constexpr int NMAX = 7;
 constexpr int NPMAX = NMAX + 1;
 
-// 1D operators of one degree N, rounded to double from extended-precision
-// values (Sec. 2.2, Eq. dgsem and the operator definitions after it).
+// 1D operators of one degree N on the solution nodes (LGL or Gauss-Legendre),
+// rounded to double from extended-precision values (Sec. 2.2, Eq. dgsem and
+// the operator definitions after it), and the LGL operators of the geometry.
 struct Ops {
   double x[NPMAX], w[NPMAX], winv[NPMAX];
   double D[NPMAX * NPMAX];       // D[i][a] = l_a'(x_i)
   double Dhat[NPMAX * NPMAX];    // -(w_a / w_i) D[a][i]
-  double Dsplit[NPMAX * NPMAX];  // 2 D + corner corrections (diagonal zero)
+  double Dsplit[NPMAX * NPMAX];  // 2 D + corner corrections (diagonal zero), LGL
   double Dlo[NPMAX * NPMAX];     // D - (double)D (double-double tail)
   double Vinv[NPMAX * NPMAX];    // nodal -> orthonormal Legendre modes
-  double Dinv_w[NPMAX];          // unused padding / reserved
+  double Lp[NPMAX], Lm[NPMAX];   // l_i(+1), l_i(-1) (unit vectors on LGL)
+  // geometry: the LGL derivative matrix (double-double) and the
+  // interpolation from the LGL nodes to the solution nodes (double-double;
+  // the identity on LGL)
+  double Dg[NPMAX * NPMAX], Dg_lo[NPMAX * NPMAX];
+  double Ig[NPMAX * NPMAX], Ig_lo[NPMAX * NPMAX];
 };
 
 // Scalars kept on the device (one block, one per context).
@@ -117,6 +123,11 @@ struct StageArgs {
   // sponge zone (null: none): sigma [E][n3], base state [E][5][n3]
   const double* sponge_sigma;
   const double* sponge_base;
+  // Gauss-Legendre nodes: face values of the state [S][2][5][n2] and of the
+  // lifted gradients [S][2][12][n2] (master, slave; master face frame)
+  double* Ufc;
+  double* gfc;
+  float* gfc32;
 };
 
 }  // namespace dg
@@ -158,6 +169,11 @@ struct dg_ctx {
   dg::Ops* ops = nullptr;    // device copy of the operators of degree N
   dg::DevScalars* scal = nullptr;
   dg::DevScalars* scal_host = nullptr;  // pinned mirror
+  int gauss = 0;              // solution on Gauss-Legendre nodes (standard DGSEM)
+  double* xyzs = nullptr;     // [E][n3][3] coordinates of the solution nodes
+  double* Ufc = nullptr;      // GL: [S][2][5][n2] face values of the state
+  double* gfc = nullptr;      // GL: [S][2][12][n2] face values of the lifted gradients
+  float* gfc32 = nullptr;     // GL, FP32-bulk: the same in FP32
   int64_t bytes = 0;
   double t_host = 0.0;
   bool state_set = false;

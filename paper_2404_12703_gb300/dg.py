@@ -30,7 +30,7 @@ SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "d
                  "dg_server_destroy")
 EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
            "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_autotune", "dg_set_config", "dg_get_config",
-           "dg_set_sponge",
+           "dg_set_sponge", "dg_node_coords",
            "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
            "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
 
@@ -52,7 +52,10 @@ class Params(C.Structure):
 class MeshDesc(C.Structure):
     _fields_ = [("N", C.c_int), ("n_elems", C.c_int64), ("corner_vid", C.POINTER(C.c_int64)),
                 ("xyz", C.POINTER(C.c_double)), ("face_bc", C.POINTER(C.c_int)), ("n_bc", C.c_int),
-                ("bc", C.POINTER(C.c_double))]
+                ("bc", C.POINTER(C.c_double)), ("nodes", C.c_int)]
+
+
+NODES_LGL, NODES_GAUSS = 0, 1
 
 
 BC_WALL_ISOTHERMAL, BC_WALL_ADIABATIC, BC_SLIP, BC_STATE, BC_OUTFLOW = 1, 2, 3, 4, 5
@@ -98,6 +101,7 @@ def load(path: str | None = None):
             "dg_default_params": (None, [C.POINTER(Params)]),
             "dg_init_mesh": (C.c_int, [C.POINTER(vp), C.POINTER(MeshDesc), C.POINTER(Params), vp]),
             "dg_set_stream": (C.c_int, [vp, vp]),
+            "dg_node_coords": (C.c_int, [vp, vp, C.c_int]),
             "dg_set_params": (C.c_int, [vp, C.POINTER(Params)]),
             "dg_set_state": (C.c_int, [vp, vp, C.c_int, C.c_double]),
             "dg_get_state": (C.c_int, [vp, vp, C.c_int, dp]),
@@ -184,10 +188,13 @@ class Solver:
     """One mesh on the current CUDA device, with its state.
 
     ``mesh`` is a dict with ``N``, ``xyz`` [E][n][n][n][3] (or [E][n^3][3]) and
-    ``corner_vid`` [E][8] as produced by ``workloads.box_mesh``.
+    ``corner_vid`` [E][8] as produced by ``workloads.box_mesh``.  ``nodes``:
+    "lgl" (split-form DGSEM, the default) or "gauss" (standard DGSEM on
+    Gauss-Legendre nodes; ``xyz`` stays the LGL-node geometry and
+    ``node_coords()`` gives the solution nodes).
     """
 
-    def __init__(self, mesh, params: Params | None = None, stream=None, **kw):
+    def __init__(self, mesh, params: Params | None = None, stream=None, nodes="lgl", **kw):
         lib = load()
         self._lib = lib
         self.N = int(mesh["N"])
@@ -201,7 +208,9 @@ class Solver:
         desc = MeshDesc(self.N, self.E, cvid.ctypes.data_as(C.POINTER(C.c_int64)),
                         xyz.ctypes.data_as(C.POINTER(C.c_double)),
                         fb.ctypes.data_as(C.POINTER(C.c_int)) if fb is not None else None, nbc,
-                        bc.ctypes.data_as(C.POINTER(C.c_double)) if bc is not None else None)
+                        bc.ctypes.data_as(C.POINTER(C.c_double)) if bc is not None else None,
+                        {"lgl": NODES_LGL, "gauss": NODES_GAUSS}[nodes] if isinstance(nodes, str) else int(nodes))
+        self.nodes = desc.nodes
         h = C.c_void_p()
         _check(lib.dg_init_mesh(C.byref(h), C.byref(desc), C.byref(self.params), _stream_ptr(stream)))
         self._h = h
@@ -222,6 +231,12 @@ class Solver:
         N, E, S, b = C.c_int(), C.c_int64(), C.c_int64(), C.c_int64()
         _check(self._lib.dg_sizes(self._h, C.byref(N), C.byref(E), C.byref(S), C.byref(b)))
         return {"N": N.value, "E": E.value, "S": S.value, "bytes": b.value}
+
+    def node_coords(self):
+        """Coordinates of the solution nodes [E][n^3][3] (numpy, float64)."""
+        X = np.zeros((self.E, self.n ** 3, 3))
+        _check(self._lib.dg_node_coords(self._h, C.c_void_p(X.ctypes.data), 0))
+        return X
 
     def set_stream(self, stream=None):
         _check(self._lib.dg_set_stream(self._h, _stream_ptr(stream)))

@@ -46,13 +46,20 @@ BYTES_PER_DOF = 8 * (30 + 204 / (N_DEG + 1))
 # DRAM bytes per DOF of one k_volume<7,1> launch, from the ncu capture summarised
 # in profiles/k_volume_tgv12_N7_fp64.md (12^3 mesh; the traffic scales with
 # the DOF count).  Set to None whenever the kernel changes until re-measured.
-VOLUME_TRAFFIC_BYTES_PER_DOF = 332.05
+VOLUME_TRAFFIC_BYTES_PER_DOF = 332.63
 # FP32-bulk: algorithmic bytes per DOF of one volume-kernel launch (reads U 40,
 # FP32 metrics 40, FP32 lifted gradients 48, dU 40, surface fluxes ~8; writes
 # U 40, dU 40), and of a whole stage for the minimal two-phase method with the
 # RK register in FP64 and the face traces in FP32: 342 B at N = 7.
 VOLUME32_BYTES_PER_DOF = 40 + 40 + 48 + 40 + 8 + 40 + 40
 BYTES32_PER_DOF = 342.0
+# Standard DGSEM on Gauss-Legendre nodes, algorithmic flops per DOF and stage
+# (n = N + 1, FMA = 2 flops).  Lifting: D-hat line sums 72 n, metric products
+# 36, both faces of three lines 144, 1/J 12, ProlongToFace of the twelve
+# gradient components 144.  Volume: D-hat line sums 30 n, three contravariant
+# Euler and viscous fluxes 114, stress and heat flux 40, SurfInt 60,
+# ApplyJac and RK 25.
+GL_FLOPS_PER_DOF = {"lift": 72 * (N_DEG + 1) + 336, "volume": 30 * (N_DEG + 1) + 239}
 
 
 def workload_desc(nel=NEL):
@@ -453,6 +460,17 @@ def gauss_bench(dg, torch, stream, nel=NEL, steps=20):
         out[name] = {"ms_per_step": ms, "dof_updates_per_s": dof * STAGES / (ms * 1e-3), "t": t,
                      "finite": bool(np.isfinite(U).all()),
                      "kernel_share": {k: v[0] / tot for k, v in prof.items()}}
+        if prec == dg.FP64:
+            # the lifting kernel dominates: its algorithmic FLOP/s against the FP64 ALU peak
+            lift_ms = prof["lift"][0] / max(prof["lift"][1], 1)
+            ach = GL_FLOPS_PER_DOF["lift"] * dof / (lift_ms * 1e-3) / 1e12
+            vol_ms = prof["volume"][0] / max(prof["volume"][1], 1)
+            out[name]["roofline"] = {"kernel": "k_lift_gl<7,double>", "bound": "alu", "achieved": ach,
+                                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                                     "flops_per_dof": GL_FLOPS_PER_DOF["lift"], "ms_per_launch": lift_ms,
+                                     "volume_ms_per_launch": vol_ms,
+                                     "volume_frac": GL_FLOPS_PER_DOF["volume"] * dof / (vol_ms * 1e-3) / 1e12
+                                     / FP64_PEAK_TFLOPS}
         s.close()
     return {"workload": f"TGV Re 1600 Ma 0.1 on {nel}^3 curved elements, N = 7 ({dof} DOF), standard DGSEM "
                         f"on Gauss-Legendre nodes, {steps} CFL steps", **out}
@@ -752,7 +770,18 @@ def main():
     ap.add_argument("--long-run", type=float, default=0.0,
                     help="instead of the benchmark: FP32-bulk vs FP64 Taylor-Green run (32^3, N = 5) to this time")
     ap.add_argument("--long-every", type=float, default=0.25, help="output interval of --long-run")
+    ap.add_argument("--gauss-only", action="store_true",
+                    help="run only the Gauss-Legendre-node measurement (--nel, --steps) and print it")
     args = ap.parse_args()
+    if args.gauss_only:
+        import torch
+        from paper_2404_12703_gb300 import build as B
+        from paper_2404_12703_gb300 import dg
+        B.build()
+        dg.load()
+        stream = torch.cuda.Stream()
+        print(json.dumps(gauss_bench(dg, torch, stream, nel=args.nel, steps=max(args.steps, 1))), flush=True)
+        return 0
     if args.long_run > 0:
         return run_long(args)
     if args.warmup < 3:

@@ -476,6 +476,49 @@ def gauss_bench(dg, torch, stream, nel=NEL, steps=20):
                         f"on Gauss-Legendre nodes, {steps} CFL steps", **out}
 
 
+def mms_error(dg, torch, stream, N, nel, nodes, T=0.2, cfl=0.2, mu=0.01):
+    """L2 density error at time T of the manufactured solution of Sec. 5.1 on
+    [-1, 1]^3 (nel^3 curved elements, periodic), viscous, started from its
+    interpolant, CFL steps ending exactly on T."""
+    from paper_2404_12703_gb300 import workloads as W
+    m = W.box_mesh(N, (nel,) * 3, length=(2.0, 2.0, 2.0), origin=(-1.0, -1.0, -1.0), curved=0.05, seed=2)
+    s = dg.Solver(m, stream=stream, nodes=nodes, mu=mu, cfl=cfl, source=dg.SOURCE_MMS)
+    X = s.node_coords()
+    s.set_state(W.mms_state(X, 0.0))
+    t, steps = s.advance(T)
+    U, _ = s.get_state()
+    ex = W.mms_state(X, t)
+    Ja, J = s.debug("metrics")
+    w = s.quadrature_weights()
+    wq = np.einsum("i,j,k->kji", w, w, w).reshape(-1)[None, :] * J
+    err = float(np.sqrt((wq * (U[..., 0] - ex[..., 0]) ** 2).sum() / wq.sum()))
+    s.close()
+    return err, steps
+
+
+def convergence_study(dg, torch, stream, degrees=(2, 3, 4, 5, 6, 7), T=0.2):
+    """Sec. 5.1's convergence test on the GPU: the manufactured solution with
+    both schemes (split form on LGL nodes, standard form on GL nodes), L2
+    density errors on nested meshes and the experimental orders."""
+    out = {}
+    for nodes in ("lgl", "gauss"):
+        rows = {}
+        for N in degrees:
+            # a periodic direction needs three elements at least
+            levels = (4, 8, 16, 32) if N <= 3 else ((4, 8, 16) if N == 4 else (3, 6, 12))
+            cfl = 0.2 if N <= 4 else 0.1  # keeps the RK4 error below the spatial one
+            errs = []
+            for nel in levels:
+                e, steps = mms_error(dg, torch, stream, N, nel, nodes, T=T, cfl=cfl)
+                errs.append({"elements": nel ** 3, "l2_rho": e, "steps": steps})
+            for i in range(1, len(errs)):
+                errs[i]["eoc"] = float(np.log2(errs[i - 1]["l2_rho"] / errs[i]["l2_rho"]))
+            rows[str(N)] = errs
+        out[nodes] = rows
+    return {"workload": f"manufactured solution of Sec. 5.1 (A = 0.1, a = 1, mu = 0.01) on [-1,1]^3 curved "
+                        f"periodic meshes, to t = {T}, CFL 0.2 (N <= 4) or 0.1", **out}
+
+
 def run_long(args):
     """FP32-bulk against FP64 over a long Taylor-Green run: 32^3 Cartesian
     elements at N = 5 (7,077,888 DOF), Re 1600, Ma 0.1, both precisions from
@@ -772,7 +815,17 @@ def main():
     ap.add_argument("--long-every", type=float, default=0.25, help="output interval of --long-run")
     ap.add_argument("--gauss-only", action="store_true",
                     help="run only the Gauss-Legendre-node measurement (--nel, --steps) and print it")
+    ap.add_argument("--convergence", action="store_true",
+                    help="run only the manufactured-solution convergence study of Sec. 5.1 and print it")
     args = ap.parse_args()
+    if args.convergence:
+        import torch
+        from paper_2404_12703_gb300 import build as B
+        from paper_2404_12703_gb300 import dg
+        B.build()
+        dg.load()
+        print(json.dumps(convergence_study(dg, torch, torch.cuda.Stream())), flush=True)
+        return 0
     if args.gauss_only:
         import torch
         from paper_2404_12703_gb300 import build as B

@@ -75,7 +75,17 @@ typedef struct {
                             constant Pr; 0: constant mu.  Standalone contexts only:
                             the server's cases use a constant mu                 */
   double T_ref;          /* Sutherland reference temperature (> 0)                */
+  int source;            /* DG_SOURCE_NONE, or DG_SOURCE_MMS: the source of the
+                            manufactured solution of Sec. 5.1 (Eq. mms), added to
+                            Ut at every node in FP64 at the stage time: with
+                            phi = 2 pi (x + y + z - a t), density and momentum
+                            components 2 + A sin(phi), total energy their square;
+                            constant viscosity only (DG_ERR_ARG with sutherland) */
+  double source_A;       /* its amplitude A (Sec. 5.1: 0.1)                      */
+  double source_a;       /* its advection speed a (Sec. 5.1: 1)                  */
 } dg_params;
+
+enum { DG_SOURCE_NONE = 0, DG_SOURCE_MMS = 1 };
 
 /* Fills p with the defaults: gamma 1.4, R 1, Pr 0.72, mu 1/1600, Roe, viscous,
    no shock capturing, alpha in [1e-3, 0.5], CFL = DFL = 0.9, FP64. */
@@ -152,6 +162,10 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params
    geometry polynomial evaluated at the Gauss-Legendre nodes.  Synchronises
    the context's stream. */
 int dg_node_coords(dg_ctx* ctx, double* xyz, int on_device);
+
+/* The 1D quadrature weights of the solution nodes (N + 1 values: LGL or
+   Gauss-Legendre), for integrals of nodal data: sum_ijk w_i w_j w_k J_ijk f_ijk. */
+int dg_quadrature_weights(const dg_ctx* ctx, double* w);
 
 /* Changes the stream later work is enqueued on. */
 int dg_set_stream(dg_ctx* ctx, void* stream);

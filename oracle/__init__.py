@@ -25,7 +25,8 @@ _LIBS = {}
 
 #: parameter vector layout shared with dg_oracle.c's read_params()
 PARAM_KEYS = ("gamma", "R", "Pr", "mu", "riemann", "viscous", "shock",
-              "alpha_min", "alpha_max", "cfl", "dfl", "alpha_force")
+              "alpha_min", "alpha_max", "cfl", "dfl", "alpha_force", "sutherland", "T_ref",
+              "source", "source_A", "source_a")
 
 
 def build(quad: bool = True, force: bool = False) -> None:
@@ -74,7 +75,8 @@ def _lib(quad: bool = False):
             "set_sponge": fn("set_sponge", None, [C.c_void_p, C.c_void_p, C.c_void_p]),
             "connectivity": fn("connectivity", None, [C.c_void_p, ip, ip, ip, ip]),
             "metrics": fn("metrics", None, [C.c_void_p, dp, dp]),
-            "rhs": fn("rhs", C.c_int, [C.c_void_p, dp, dp, dp, C.c_void_p, dp, dp, dp]),
+            "rhs": fn("rhs", C.c_int, [C.c_void_p, dp, dp, C.c_double, dp, C.c_void_p, dp, dp, dp]),
+            "mms_source": fn("mms_source", None, [dp, C.c_long, dp, C.c_double, dp]),
             "dt": fn("dt", C.c_double, [C.c_void_p, dp, dp, ip]),
             "step": fn("step", C.c_int, [C.c_void_p, dp, dp, C.c_int, C.c_double, dp, dp]),
             "kinetic": fn("kinetic", None, [C.c_void_p, dp, dp, dp]),
@@ -102,14 +104,25 @@ def _f64(a):
 
 def params(gamma=1.4, R=1.0, Pr=0.72, mu=1.0 / 1600.0, riemann="roe", viscous=True,
            shock=False, alpha_min=1e-3, alpha_max=0.5, cfl=0.9, dfl=0.9,
-           alpha_force=-1.0, sutherland=False, T_ref=1.0) -> np.ndarray:
+           alpha_force=-1.0, sutherland=False, T_ref=1.0, source=0, source_A=0.1,
+           source_a=1.0) -> np.ndarray:
     """Flat parameter vector in the oracle's layout.  ``alpha_force >= 0`` makes
     every element blend with that alpha instead of the indicator's (tests).
-    ``sutherland``: mu(T) by Sutherland's law, ``mu`` being its value at T_ref."""
+    ``sutherland``: mu(T) by Sutherland's law, ``mu`` being its value at T_ref.
+    ``source = 1``: the manufactured-solution source of Sec. 5.1 with amplitude
+    ``source_A`` and advection speed ``source_a``."""
     r = {"roe": 0, "lf": 1}[riemann] if isinstance(riemann, str) else int(riemann)
     return np.array([gamma, R, Pr, mu, r, int(bool(viscous)), int(bool(shock)),
-                     alpha_min, alpha_max, cfl, dfl, alpha_force, int(bool(sutherland)), T_ref],
-                    dtype=np.float64)
+                     alpha_min, alpha_max, cfl, dfl, alpha_force, int(bool(sutherland)), T_ref,
+                     int(source), source_A, source_a], dtype=np.float64)
+
+
+def mms_source(x, t, prm):
+    """The manufactured-solution source Q(x, t) [n][5] at points x [n][3]."""
+    x = np.ascontiguousarray(np.reshape(x, (-1, 3)), dtype=np.float64)
+    Q = np.zeros((x.shape[0], 5))
+    _lib()["mms_source"](_dp(_f64(prm)), x.shape[0], _dp(x), float(t), _dp(Q))
+    return Q
 
 
 def ops(N: int, quad: bool = False, gauss: bool = False):
@@ -252,8 +265,8 @@ class Mesh:
         self._api["metrics"](self._h, _dp(Ja), _dp(J))
         return Ja, J
 
-    def rhs(self, U, prm, want=None, with_alpha=False, with_grad=False, with_fstar=False):
-        """Ut = R(U) in the public layout [E][n^3][5].  ``want`` is an optional
+    def rhs(self, U, prm, want=None, with_alpha=False, with_grad=False, with_fstar=False, t=0.0):
+        """Ut = R(U) (+ the source at time t) in the public layout [E][n^3][5].  ``want`` is an optional
         boolean mask over elements (other elements' Ut are returned as 0).
         Optional extras: alpha [E], lifted gradients [E][n^3][4][3] and the
         surface flux times s-hat on master faces [E][6][n^2][5] (zero on slave
@@ -267,7 +280,7 @@ class Mesh:
         alpha = np.zeros(self.E) if with_alpha else None
         grad = np.zeros((self.E, self.n ** 3, 4, 3)) if with_grad else None
         fstar = np.zeros((self.E, 6, self.n ** 2, 5)) if with_fstar else None
-        st = self._api["rhs"](self._h, _dp(_f64(prm)), _dp(U), _dp(Ut),
+        st = self._api["rhs"](self._h, _dp(_f64(prm)), _dp(U), float(t), _dp(Ut),
                               mask.ctypes.data if mask is not None else None,
                               _dp(alpha) if alpha is not None else None,
                               _dp(grad) if grad is not None else None,

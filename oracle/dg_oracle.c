@@ -56,6 +56,8 @@ typedef long double real;
 #define RLOG(x) logl(x)
 #define RPOW(x, y) powl(x, y)
 #define RFLOOR(x) floorl(x)
+#define RSIN(x) sinl(x)
+#define RCOS(x) cosl(x)
 #define REPS LDBL_EPSILON
 #define ORC(name) orcq_##name
 #else
@@ -66,6 +68,8 @@ typedef double real;
 #define RLOG(x) log(x)
 #define RPOW(x, y) pow(x, y)
 #define RFLOOR(x) floor(x)
+#define RSIN(x) sin(x)
+#define RCOS(x) cos(x)
 #define REPS DBL_EPSILON
 #define ORC(name) orc_##name
 #endif
@@ -77,7 +81,8 @@ typedef double real;
 /* ------------------------------------------------------------------ */
 enum {
   P_GAMMA = 0, P_R, P_PR, P_MU, P_RIEMANN, P_VISCOUS, P_SHOCK,
-  P_ALPHA_MIN, P_ALPHA_MAX, P_CFL, P_DFL, P_ALPHA_FORCE, P_SUTHERLAND, P_TREF, P_COUNT
+  P_ALPHA_MIN, P_ALPHA_MAX, P_CFL, P_DFL, P_ALPHA_FORCE, P_SUTHERLAND, P_TREF,
+  P_SOURCE, P_SRC_A, P_SRC_SPEED, P_COUNT
 };
 
 typedef struct {
@@ -89,6 +94,8 @@ typedef struct {
   real alpha_force;  /* >= 0: every element blends with this alpha (tests) */
   int sutherland;    /* 1: mu = mu(T) by Sutherland's law, mu being its value at T_ref */
   real T_ref;
+  int source;        /* 1: the manufactured-solution source of Sec. 5.1 */
+  real src_A, src_a; /* its amplitude A and advection speed a */
 } params_t;
 
 static params_t read_params(const double* p) {
@@ -107,6 +114,9 @@ static params_t read_params(const double* p) {
   P.alpha_force = p[P_ALPHA_FORCE];
   P.sutherland = (int)p[P_SUTHERLAND];
   P.T_ref = p[P_TREF];
+  P.source = (int)p[P_SOURCE];
+  P.src_A = p[P_SRC_A];
+  P.src_a = p[P_SRC_SPEED];
   return P;
 }
 
@@ -663,6 +673,31 @@ static real viscosity(const params_t* P, real T) {
   return P->mu * (real)1.4042 * th * RSQRT(th) / (th + (real)0.4042);
 }
 
+/* Manufactured solution of Sec. 5.1 (Eq. mms): with phi = 2 pi (x + y + z - a t),
+   rho = rho u = rho v = rho w = 2 + A sin(phi) and rho e = (2 + A sin(phi))^2
+   (the bold u of Eq. mms read as the momentum: with a velocity of that size
+   the pressure would be negative).  The velocity is (1, 1, 1), so tau = 0;
+   p = (gamma - 1)(rho^2 - 3 rho / 2), T = p / (rho R).  The source is
+   Q = U_t + div F_c - div F_v of that state, written out:
+     Q_rho = (3 - a) c,
+     Q_m   = (3 - a) c + (gamma - 1)(2 rho - 3/2) c           (each component),
+     Q_E   = -2 a rho c + 3 (2 rho + (gamma - 1)(2 rho - 3/2)) c
+             + 3 lambda (gamma - 1) / R (2 pi)^2 A sin(phi)      (viscous only),
+   with c = 2 pi A cos(phi); constant viscosity. */
+static void mms_source(const params_t* P, const real* x, real t, real* Q) {
+  const real w = 2 * (real)3.14159265358979323846264338327950288L;
+  const real phi = w * (x[0] + x[1] + x[2] - P->src_a * t);
+  const real sn = P->src_A * RSIN(phi), c = w * P->src_A * RCOS(phi);
+  const real rho = 2 + sn, g1 = P->gamma - 1;
+  Q[0] = (3 - P->src_a) * c;
+  for (int k = 1; k <= 3; ++k) Q[k] = (3 - P->src_a) * c + g1 * (2 * rho - (real)1.5) * c;
+  Q[4] = -2 * P->src_a * rho * c + 3 * (2 * rho + g1 * (2 * rho - (real)1.5)) * c;
+  if (P->viscous) {
+    const real lam = P->gamma * P->R * P->mu / (g1 * P->Pr);
+    Q[4] += 3 * lam * g1 / P->R * w * w * sn;
+  }
+}
+
 /* viscous flux F_v = (0, tau, tau.u - q) contracted with nv (Eq. nse, stress and
    Fourier law, heat conductivity lambda = gamma R mu / ((gamma - 1) Pr));
    g[qv][x] = d(u, v, w, T)_qv / dx_x */
@@ -854,7 +889,7 @@ static void bc_flux(const mesh_t* M, const params_t* P, int bc, const real* U, c
 /* J Ut = -[ V_conv + V_visc + S ], Eq. dgsem with the split-form volume term.
    want: NULL for every element, else a 0/1 mask of the elements whose Ut is
    wanted (their neighbours' gradients are formed as needed). */
-static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
+static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real t, real* Ut,
                     const unsigned char* want, real* alpha_out, real* g_out, real* fstar_out,
                     work_t* w) {
   int n = M->n, n2 = M->n2, n3 = M->n3;
@@ -1075,7 +1110,7 @@ static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
         }
     }
 
-  /* ---- ApplyJac; sponge source ---- */
+  /* ---- ApplyJac; sponge source; manufactured-solution source ---- */
   for (long e = 0; e < E; ++e) {
     if (want && !want[e]) continue;
     for (long v = 0; v < n3; ++v)
@@ -1083,6 +1118,12 @@ static int rhs_impl(const mesh_t* M, const params_t* P, const real* U, real* Ut,
         long x = (e * n3 + v) * 5 + k;
         Ut[x] = -(w->Bc[x] + w->B[x]) / M->J[e * n3 + v];
         if (M->sponge_sigma) Ut[x] -= M->sponge_sigma[e * n3 + v] * (U[x] - M->sponge_base[x]);
+      }
+    if (P->source)
+      for (long v = 0; v < n3; ++v) {
+        real Q[5];
+        mms_source(P, &M->xyzs[(e * n3 + v) * 3], t, Q);
+        for (int k = 0; k < 5; ++k) Ut[(e * n3 + v) * 5 + k] += Q[k];
       }
   }
   if (alpha_out)
@@ -1145,8 +1186,8 @@ static void surf_spread(const mesh_t* M, real* acc, int ncomp, long e, int f, in
   }
 }
 
-static int rhs_gauss(const mesh_t* M, const params_t* P, const real* U, real* Ut, const unsigned char* want,
-                     real* g_out, real* fstar_out, work_t* w) {
+static int rhs_gauss(const mesh_t* M, const params_t* P, const real* U, real t, real* Ut,
+                     const unsigned char* want, real* g_out, real* fstar_out, work_t* w) {
   int n = M->n, n2 = M->n2, n3 = M->n3;
   long E = M->E, F = E * 6;
   const ops_t* o = &M->o;
@@ -1300,7 +1341,7 @@ static int rhs_gauss(const mesh_t* M, const params_t* P, const real* U, real* Ut
         }
     }
 
-  /* ---- ApplyJac; sponge source ---- */
+  /* ---- ApplyJac; sponge source; manufactured-solution source ---- */
   for (long e = 0; e < E; ++e) {
     if (want && !want[e]) continue;
     for (long v = 0; v < n3; ++v)
@@ -1308,6 +1349,12 @@ static int rhs_gauss(const mesh_t* M, const params_t* P, const real* U, real* Ut
         long x = (e * n3 + v) * 5 + k;
         Ut[x] = -(w->Bc[x] + w->B[x]) / M->J[e * n3 + v];
         if (M->sponge_sigma) Ut[x] -= M->sponge_sigma[e * n3 + v] * (U[x] - M->sponge_base[x]);
+      }
+    if (P->source)
+      for (long v = 0; v < n3; ++v) {
+        real Q[5];
+        mms_source(P, &M->xyzs[(e * n3 + v) * 3], t, Q);
+        for (int k = 0; k < 5; ++k) Ut[(e * n3 + v) * 5 + k] += Q[k];
       }
   }
   if (g_out && P->viscous)
@@ -1320,14 +1367,15 @@ static int rhs_gauss(const mesh_t* M, const params_t* P, const real* U, real* Ut
 }
 
 /* the DG operator of the mesh's node set */
-static int rhs_any(const mesh_t* M, const params_t* P, const real* U, real* Ut, const unsigned char* want,
+static int rhs_any(const mesh_t* M, const params_t* P, const real* U, real t, real* Ut, const unsigned char* want,
                    real* alpha_out, real* g_out, real* fstar_out, work_t* w) {
+  if (P->source && P->sutherland) return -8;  /* the source is written for a constant viscosity */
   if (M->o.gauss) {
     if (alpha_out)
       for (long e = 0; e < M->E; ++e) alpha_out[e] = 0;
-    return rhs_gauss(M, P, U, Ut, want, g_out, fstar_out, w);
+    return rhs_gauss(M, P, U, t, Ut, want, g_out, fstar_out, w);
   }
-  return rhs_impl(M, P, U, Ut, want, alpha_out, g_out, fstar_out, w);
+  return rhs_impl(M, P, U, t, Ut, want, alpha_out, g_out, fstar_out, w);
 }
 
 /* ------------------------------------------------------------------ */
@@ -1549,7 +1597,7 @@ static real* conv_state(const mesh_t* M, const double* U) {
   return r;
 }
 
-int ORC(rhs)(void* hv, const double* prm, const double* U, double* Ut, const unsigned char* want,
+int ORC(rhs)(void* hv, const double* prm, const double* U, double t, double* Ut, const unsigned char* want,
              double* alpha, double* grad, double* fstar) {
   handle_t* h = (handle_t*)hv;
   mesh_t* M = &h->M;
@@ -1560,7 +1608,7 @@ int ORC(rhs)(void* hv, const double* prm, const double* U, double* Ut, const uns
   real* al = alpha ? (real*)calloc(M->E, sizeof(real)) : NULL;
   real* gr = grad ? (real*)calloc(M->E * M->n3 * 12, sizeof(real)) : NULL;
   real* fr = fstar ? (real*)calloc(M->E * 6 * M->n2 * 5, sizeof(real)) : NULL;
-  int st = rhs_any(M, &P, Ur, Utr, want, al, gr, fr, &h->w);
+  int st = rhs_any(M, &P, Ur, (real)t, Utr, want, al, gr, fr, &h->w);
   if (fr) { to_double(fr, fstar, M->E * 6 * M->n2 * 5); free(fr); }
   for (long x = 0; x < len; ++x) Ut[x] = (double)Utr[x];
   if (al) { to_double(al, alpha, M->E); free(al); }
@@ -1570,11 +1618,10 @@ int ORC(rhs)(void* hv, const double* prm, const double* U, double* Ut, const uns
   return st;
 }
 
-typedef struct { handle_t* h; params_t P; } dgctx_t;
+typedef struct { handle_t* h; params_t P; int status; } dgctx_t;
 static void dg_rhs_cb(void* c, const real* U, real t, real* Ut) {
   dgctx_t* x = (dgctx_t*)c;
-  (void)t;
-  rhs_any(&x->h->M, &x->P, U, Ut, NULL, NULL, NULL, NULL, &x->h->w);
+  x->status = rhs_any(&x->h->M, &x->P, U, t, Ut, NULL, NULL, NULL, NULL, &x->h->w);
 }
 
 double ORC(dt)(void* hv, const double* prm, const double* U, int* nonfinite) {
@@ -1591,7 +1638,7 @@ int ORC(step)(void* hv, const double* prm, double* U, int n_steps, double dt_fix
               double* dt_last) {
   handle_t* h = (handle_t*)hv;
   mesh_t* M = &h->M;
-  dgctx_t c = {h, read_params(prm)};
+  dgctx_t c = {h, read_params(prm), 0};
   long len = M->E * M->n3 * 5;
   real* Ur = conv_state(M, U);
   real* dU = (real*)calloc(len, sizeof(real));
@@ -1603,6 +1650,7 @@ int ORC(step)(void* hv, const double* prm, double* U, int n_steps, double dt_fix
     dt = dt_fixed > 0 ? (real)dt_fixed : time_step(M, &c.P, Ur, &bad);
     if (bad) { st = -5; break; }
     lserk_step(Ur, dU, Ut, len, t, dt, dg_rhs_cb, &c);
+    if (c.status) { st = c.status; break; }
     t += dt;
   }
   to_double(Ur, U, len);
@@ -1652,6 +1700,16 @@ void ORC(point_flux)(const double* prm, int kind, const double* UL, const double
   else if (kind == 2) kep_flux(uL, qL, uR, qR, n, fr);
   else euler_flux(uL, qL, n, fr);
   to_double(fr, f, 5);
+}
+
+/* the manufactured-solution source at points x [n][3], time t */
+void ORC(mms_source)(const double* prm, long npts, const double* x, double t, double* Q) {
+  params_t P = read_params(prm);
+  for (long i = 0; i < npts; ++i) {
+    real xr[3] = {x[i * 3], x[i * 3 + 1], x[i * 3 + 2]}, q[5];
+    mms_source(&P, xr, (real)t, q);
+    for (int k = 0; k < 5; ++k) Q[i * 5 + k] = (double)q[k];
+  }
 }
 
 void ORC(point_visc)(const double* prm, const double* U, const double* g, const double* nv, double* f) {

@@ -281,6 +281,9 @@ static const double RKA[5] = {0.0, -567301805773.0 / 1357537059087.0, -240426799
 static const double RKB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                               2277821191437.0 / 14882151754819.0};
+// stage times t_n + c_s dt
+static const double RKC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363218457.0,
+                              2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
 
 __global__ void k_set_scalars(DevScalars* s, double dt_fixed, int set_t, double t, int reset_flags,
                               double t_end = 0.0) {
@@ -307,6 +310,10 @@ static int check_params(const dg_params* p) {
   if (p->riemann != DG_RIEMANN_ROE && p->riemann != DG_RIEMANN_LF) return fail(DG_ERR_ARG, "unknown Riemann solver");
   if (p->precision != DG_FP64 && p->precision != DG_FP32_BULK) return fail(DG_ERR_ARG, "unknown precision");
   if (p->sutherland && !(p->T_ref > 0)) return fail(DG_ERR_ARG, "Sutherland's law needs T_ref > 0");
+  if (p->source != DG_SOURCE_NONE && p->source != DG_SOURCE_MMS) return fail(DG_ERR_ARG, "unknown source");
+  if (p->source && p->sutherland)
+    return fail(DG_ERR_ARG, "the manufactured-solution source is written for a constant viscosity");
+  if (p->source && !std::isfinite(p->source_A + p->source_a)) return fail(DG_ERR_ARG, "source parameters");
   return DG_OK;
 }
 
@@ -334,6 +341,9 @@ void dg_default_params(dg_params* p) {
   p->alpha_force = -1.0;
   p->sutherland = 0;
   p->T_ref = 1.0;
+  p->source = DG_SOURCE_NONE;
+  p->source_A = 0.1;
+  p->source_a = 1.0;
 }
 
 const char* dg_error_string(int code) {
@@ -587,6 +597,14 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params
   return dg::init_mesh_impl(out, mesh, params, (cudaStream_t)stream, nullptr);
 }
 
+int dg_quadrature_weights(const dg_ctx* c, double* w) {
+  if (!c || !w) return fail(DG_ERR_ARG, "ctx or w is NULL");
+  Ops o;
+  build_ops(c->N, c->gauss, o);
+  for (int i = 0; i <= c->N; ++i) w[i] = o.w[i];
+  return DG_OK;
+}
+
 int dg_node_coords(dg_ctx* c, double* xyz, int on_device) {
   if (!c || !xyz) return fail(DG_ERR_ARG, "ctx or xyz is NULL");
   if (!c->xyzs) return fail(DG_ERR_STATE, "the context has no mesh of its own");
@@ -693,7 +711,11 @@ int dg_rhs(dg_ctx* c, const double* U_dev, double* Ut_dev) {
 
 static cudaError_t enqueue_step(dg_ctx* c) {
   cudaError_t e = launch_cfl(c, false);
-  for (int s = 0; s < 5 && e == cudaSuccess; ++s) e = launch_rhs(c, c->U, 1, RKA[s], RKB[s], s == 0);
+  for (int s = 0; s < 5 && e == cudaSuccess; ++s) {
+    c->stage_c = RKC[s];
+    e = launch_rhs(c, c->U, 1, RKA[s], RKB[s], s == 0);
+  }
+  c->stage_c = 0.0;
   return e;
 }
 

@@ -136,6 +136,36 @@ __device__ __forceinline__ void visc_coeffs(const StageArgs& a, const CaseParams
   mu = mu0 * T(1.4042) * th * sqrt(th) / (th + T(0.4042));
   lam = mu * pick<T>(a.kappa, a.f_kappa);
 }
+// Manufactured-solution source of Sec. 5.1 (Eq. mms) at node coordinates x
+// and time ts, FP64: with phi = 2 pi (x + y + z - a t), rho = rho u = rho v =
+// rho w = 2 + A sin(phi) and rho e = rho^2 (velocity (1, 1, 1), no stress),
+// Q = U_t + div F_c - div F_v of that state:
+//   Q_rho = (3 - a) c,  Q_m = Q_rho + (gamma - 1)(2 rho - 3/2) c,
+//   Q_E = -2 a rho c + 3 (2 rho + (gamma - 1)(2 rho - 3/2)) c
+//         + 3 lambda (gamma - 1) / R (2 pi)^2 A sin(phi)   (viscous),
+// c = 2 pi A cos(phi).
+__device__ __forceinline__ void mms_source(const StageArgs& a, const double* x, double ts, double Q[5]) {
+  const double w = 2.0 * 3.141592653589793;
+  const double phi = w * (x[0] + x[1] + x[2] - a.src_a * ts);
+  double sn, cs;
+  sincos(phi, &sn, &cs);
+  sn *= a.src_A;
+  const double c = w * a.src_A * cs;
+  const double rho = 2.0 + sn, g1 = a.gm1;
+  Q[0] = (3.0 - a.src_a) * c;
+  const double qm = Q[0] + g1 * (2.0 * rho - 1.5) * c;
+  Q[1] = qm;
+  Q[2] = qm;
+  Q[3] = qm;
+  Q[4] = -2.0 * a.src_a * rho * c + 3.0 * (2.0 * rho + g1 * (2.0 * rho - 1.5)) * c;
+  if (a.viscous) Q[4] += 3.0 * a.lam * g1 * a.Rinv * w * w * sn;
+}
+// the time of the stage being evaluated: the state's time for a plain
+// right-hand side (mode 0); within a step the device time is already t_n + dt
+__device__ __forceinline__ double stage_time(const StageArgs& a, int mode) {
+  return mode == 0 ? a.scal->t : a.scal->t - (1.0 - a.rkC) * a.scal->dt;
+}
+
 __device__ __forceinline__ double case_dt(const StageArgs& a, int c) {
   return a.cases ? a.cases[c < 0 ? 0 : c].dt : a.scal->dt;
 }
@@ -1096,6 +1126,12 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
 #pragma unroll
     for (int k = 0; k < 5; ++k) Ut[k] -= sg * ((aos ? sUd[k * n3 + t] : U[k]) - ub[k * n3]);
   }
+  if (a.source) {  // manufactured-solution source, FP64
+    double Q[5];
+    mms_source(a, a.xyzs + ((size_t)e * n3 + t) * 3, stage_time(a, MODE), Q);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Ut[k] += Q[k];
+  }
   if (MODE == 0) {
     double* o = a.Ut + (size_t)e * 5 * n3 + t;
 #pragma unroll
@@ -1180,6 +1216,11 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.Ufc = c->Ufc;
   a.gfc = c->gfc;
   a.gfc32 = c->gfc32;
+  a.source = c->xyzs ? c->prm.source : 0;
+  a.src_A = c->prm.source_A;
+  a.src_a = c->prm.source_a;
+  a.xyzs = c->xyzs;
+  a.rkC = c->stage_c;
   if (c->elem_list) {
     a.E = (int)c->n_elem_list;
     a.S = (int)c->n_side_list;

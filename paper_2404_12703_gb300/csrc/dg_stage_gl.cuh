@@ -355,6 +355,12 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume_gl(StageArgs a) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) Ut[k] -= sg * (U[k] - ub[k * n3]);
   }
+  if (a.source) {  // manufactured-solution source, FP64
+    double Q[5];
+    mms_source(a, a.xyzs + ((size_t)e * n3 + t) * 3, stage_time(a, MODE), Q);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Ut[k] += Q[k];
+  }
   if (MODE == 0) {
     double* o = a.Ut + (size_t)e * 5 * n3 + t;
 #pragma unroll

@@ -128,6 +128,12 @@ struct StageArgs {
   double* Ufc;
   double* gfc;
   float* gfc32;
+  // manufactured-solution source (Sec. 5.1): on/off, amplitude, speed, the
+  // solution nodes' coordinates [E][n3][3] and the stage's RK c coefficient
+  int source;
+  double src_A, src_a;
+  const double* xyzs;
+  double rkC;
 };
 
 }  // namespace dg
@@ -170,6 +176,7 @@ struct dg_ctx {
   dg::DevScalars* scal = nullptr;
   dg::DevScalars* scal_host = nullptr;  // pinned mirror
   int gauss = 0;              // solution on Gauss-Legendre nodes (standard DGSEM)
+  double stage_c = 0.0;       // RK c coefficient of the stage being enqueued (stage time)
   double* xyzs = nullptr;     // [E][n3][3] coordinates of the solution nodes
   double* Ufc = nullptr;      // GL: [S][2][5][n2] face values of the state
   double* gfc = nullptr;      // GL: [S][2][12][n2] face values of the lifted gradients

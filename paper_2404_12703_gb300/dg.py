@@ -30,7 +30,7 @@ SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "d
                  "dg_server_destroy")
 EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
            "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_autotune", "dg_set_config", "dg_get_config",
-           "dg_set_sponge", "dg_node_coords",
+           "dg_set_sponge", "dg_node_coords", "dg_quadrature_weights",
            "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
            "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
 
@@ -46,7 +46,11 @@ class Params(C.Structure):
                 ("riemann", C.c_int), ("viscous", C.c_int), ("shock_capturing", C.c_int),
                 ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("cfl", C.c_double),
                 ("dfl", C.c_double), ("precision", C.c_int), ("alpha_force", C.c_double),
-                ("sutherland", C.c_int), ("T_ref", C.c_double)]
+                ("sutherland", C.c_int), ("T_ref", C.c_double), ("source", C.c_int), ("source_A", C.c_double),
+                ("source_a", C.c_double)]
+
+
+SOURCE_NONE, SOURCE_MMS = 0, 1
 
 
 class MeshDesc(C.Structure):
@@ -102,6 +106,7 @@ def load(path: str | None = None):
             "dg_init_mesh": (C.c_int, [C.POINTER(vp), C.POINTER(MeshDesc), C.POINTER(Params), vp]),
             "dg_set_stream": (C.c_int, [vp, vp]),
             "dg_node_coords": (C.c_int, [vp, vp, C.c_int]),
+            "dg_quadrature_weights": (C.c_int, [vp, dp]),
             "dg_set_params": (C.c_int, [vp, C.POINTER(Params)]),
             "dg_set_state": (C.c_int, [vp, vp, C.c_int, C.c_double]),
             "dg_get_state": (C.c_int, [vp, vp, C.c_int, dp]),
@@ -231,6 +236,12 @@ class Solver:
         N, E, S, b = C.c_int(), C.c_int64(), C.c_int64(), C.c_int64()
         _check(self._lib.dg_sizes(self._h, C.byref(N), C.byref(E), C.byref(S), C.byref(b)))
         return {"N": N.value, "E": E.value, "S": S.value, "bytes": b.value}
+
+    def quadrature_weights(self):
+        """1D quadrature weights of the solution nodes (LGL or Gauss-Legendre)."""
+        w = (C.c_double * 8)()
+        _check(self._lib.dg_quadrature_weights(self._h, w))
+        return np.array(list(w)[:self.n])
 
     def node_coords(self):
         """Coordinates of the solution nodes [E][n^3][3] (numpy, float64)."""

@@ -298,6 +298,17 @@ def isentropic_vortex_state(xyz, center, strength=5.0, mean=(1.0, 1.0, 0.0),
     return prim_to_cons(rho, u, v, w, p, gamma)
 
 
+def mms_state(xyz, t=0.0, A=0.1, a=1.0):
+    """The manufactured solution of Sec. 5.1 (Eq. mms) at the points xyz and
+    time t: with phi = 2 pi (x + y + z - a t), density and the three momentum
+    components 2 + A sin(phi), total energy (2 + A sin(phi))^2 (the bold u of
+    Eq. mms read as the momentum).  Period 1 in x, y and z."""
+    X = np.asarray(xyz, dtype=np.float64).reshape(-1, 3)
+    r = 2.0 + A * np.sin(2 * math.pi * (X[:, 0] + X[:, 1] + X[:, 2] - a * t))
+    U = np.stack([r, r, r, r, r * r], axis=-1)
+    return U.reshape(np.asarray(xyz).shape[:-1] + (5,))
+
+
 def uniform_state(shape, rho=1.2, vel=(0.3, -0.2, 0.1), p=2.0, gamma=1.4):
     """A constant state (free-stream) of the given leading shape."""
     ones = np.ones(shape)

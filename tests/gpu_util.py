@@ -28,7 +28,8 @@ def oracle_params(dgp):
     return O.params(gamma=dgp.gamma, R=dgp.R, Pr=dgp.Pr, mu=dgp.mu, riemann=dgp.riemann,
                     viscous=dgp.viscous, shock=dgp.shock_capturing, alpha_min=dgp.alpha_min,
                     alpha_max=dgp.alpha_max, cfl=dgp.cfl, dfl=dgp.dfl, alpha_force=dgp.alpha_force,
-                    sutherland=dgp.sutherland, T_ref=dgp.T_ref)
+                    sutherland=dgp.sutherland, T_ref=dgp.T_ref, source=dgp.source, source_A=dgp.source_A,
+                    source_a=dgp.source_a)
 
 
 def rel_err(a, ref):

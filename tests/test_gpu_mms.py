@@ -78,3 +78,28 @@ def test_source_refused_with_sutherland():
     with pytest.raises(dg.DgError) as ex:
         dg.Solver(_mesh(2), source=dg.SOURCE_MMS, sutherland=1)
     assert ex.value.code == dg.DG_ERR_ARG
+
+
+def _mms_l2(dg, N, nel, nodes, T=0.2, cfl=0.2):
+    m = W.box_mesh(N, (nel,) * 3, length=(2.0, 2.0, 2.0), origin=(-1.0, -1.0, -1.0), curved=0.05, seed=2)
+    s = dg.Solver(m, nodes=nodes, mu=0.01, cfl=cfl, source=dg.SOURCE_MMS)
+    X = s.node_coords()
+    s.set_state(W.mms_state(X, 0.0))
+    t, _ = s.advance(T)
+    U, _ = s.get_state()
+    _, J = s.debug("metrics")
+    w = s.quadrature_weights()
+    wq = np.einsum("i,j,k->kji", w, w, w).reshape(-1)[None, :] * J
+    return np.sqrt((wq * (U[..., 0] - W.mms_state(X, t)[..., 0]) ** 2).sum() / wq.sum())
+
+
+@pytest.mark.parametrize("nodes", ["lgl", "gauss"])
+@pytest.mark.parametrize("N,levels,cfl", [(3, (8, 16), 0.2), (5, (6, 12), 0.1)])
+def test_manufactured_solution_design_order(nodes, N, levels, cfl):
+    """Sec. 5.1's convergence test on the GPU (the split form on LGL nodes and
+    the standard form on GL nodes): the L2 density error at t = 0.2 on two
+    nested curved meshes falls at the design order N + 1 or faster."""
+    torch, dg = gpu_or_skip()
+    e = [_mms_l2(dg, N, nel, nodes, cfl=cfl) for nel in levels]
+    rate = np.log2(e[0] / e[1])
+    assert rate > N + 0.5, (e, rate)

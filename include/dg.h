@@ -295,6 +295,15 @@ typedef struct {
                               arrival order while the resident DOF stay within
                               this bound (a case is always admitted onto an
                               idle server)                                  */
+  int64_t priority_dof;    /* step policy: 0 = every resident case advances in
+                              every batched step; > 0 = each step advances
+                              the resident cases in submission order (first
+                              fit) while their DOF stay within this bound,
+                              the oldest always; the others sit out that
+                              step with their state unchanged (their blocks
+                              leave at once), so the oldest cases run at
+                              close to their own speed and small cases fill
+                              the rest of the GPU                           */
 } dg_server_config;
 
 typedef struct {

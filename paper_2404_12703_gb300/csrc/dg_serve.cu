@@ -47,8 +47,9 @@ __global__ void __launch_bounds__(128) k_cfl_cases(int64_t nlist, const int* __r
   if (blockIdx.x >= nlist) return;
   const int64_t e = elist[blockIdx.x];
   const int c = ecase[e];
-  // free slot, or a case at its end time: the whole block leaves together
-  if (c < 0 || !(cases[c].t < cases[c].t_end)) return;
+  // free slot, a case at its end time or one sitting out the step: the
+  // whole block leaves together
+  if (c < 0 || !(cases[c].t < cases[c].t_end) || cases[c].paused) return;
   const T kv = T(kvf * cases[c].mu);
   double lc = 0.0, lv = 0.0;
   int bad = 0;
@@ -105,6 +106,12 @@ __global__ void k_dt_cases(int nslots, CaseData* cases) {
   if (c >= nslots) return;
   CaseData& d = cases[c];
   if (!d.active) return;
+  if (d.paused) {  // sits out this step: time step 0, state unchanged
+    d.dt = 0.0;
+    d.lam_c = 0ull;
+    d.lam_v = 0ull;
+    return;
+  }
   const double np1 = d.N + 1.0;
   const double lc = __longlong_as_double((long long)d.lam_c);
   const double lv = __longlong_as_double((long long)d.lam_v);
@@ -118,6 +125,15 @@ __global__ void k_dt_cases(int nslots, CaseData* cases) {
   if (dt > 0) d.steps += 1;
   d.lam_c = 0ull;
   d.lam_v = 0ull;
+}
+
+// sit-out flags of the case slots (priority policy), one bit per slot
+struct PauseMask {
+  unsigned long long w[64];
+};
+__global__ void k_set_pause(CaseData* cases, int nslots, PauseMask m) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nslots) cases[c].paused = (int)((m.w[c >> 6] >> (c & 63)) & 1ull);
 }
 
 __global__ void k_fill_int(int* p, int64_t n, int v) {
@@ -295,6 +311,7 @@ struct dg_server {
   double stat_steps = 0, stat_finished = 0, stat_captures = 0, stat_dofstages = 0, stat_device_s = 0;
   double stat_capture_s = 0, stat_prepare_s = 0, stat_insert_s = 0;  // host time
   std::string worker_error;
+  dg::PauseMask pause{};  // sit-out flags last sent to the device (step thread only)
 };
 
 namespace dg {
@@ -773,6 +790,7 @@ static void worker_loop(dg_server* s) {
     for (auto& sl : s->slots) have = have || sl.used;
     // 2. launch step k+1 of every resident case
     if (have) {
+      const bool membership_changed = s->dirty;
       if (s->dirty) {
         // an executable graph still in flight is released when it completes
         const double tc0 = now_s();
@@ -807,6 +825,34 @@ static void worker_loop(dg_server* s) {
           break;
         }
         s->dirty = false;
+      }
+      if (s->cfg.priority_dof > 0) {
+        // priority policy: resident cases in submission order, first fit
+        // within the DOF bound, the oldest always; the rest sit this step out
+        std::vector<int> order;
+        for (int i = 0; i < (int)s->slots.size(); ++i)
+          if (s->slots[i].used) order.push_back(i);
+        std::sort(order.begin(), order.end(),
+                  [&](int x, int y) { return s->slots[x].ticket < s->slots[y].ticket; });
+        PauseMask m{};
+        int64_t run = 0;
+        bool first = true;
+        for (int i : order) {
+          const Slot& sl = s->slots[i];
+          const int64_t dof = sl.E * (sl.N + 1) * (sl.N + 1) * (sl.N + 1);
+          if (first || run + dof <= s->cfg.priority_dof) {
+            run += dof;
+            first = false;
+          } else {
+            m.w[i >> 6] |= 1ull << (i & 63);
+          }
+        }
+        if (membership_changed || memcmp(&m, &s->pause, sizeof(m)) != 0) {
+          const int ns = (int)s->slots.size();
+          k_set_pause<<<(ns + 127) / 128, 128, 0, s->stream>>>(s->d_cases, ns, m);
+          count_launch(1);
+          s->pause = m;
+        }
       }
       const int b = (int)(s->launched & 1);
       cudaEventRecord(s->step_t0[b], s->stream);
@@ -978,6 +1024,7 @@ int dg_server_create(dg_server** out, const dg_server_config* cfg) {
   *out = nullptr;
   if (cfg->max_cases < 1 || cfg->max_cases > 4096) return set_error(DG_ERR_ARG, "max_cases must be in [1, 4096]");
   if (cfg->max_resident_dof < 0) return set_error(DG_ERR_ARG, "max_resident_dof must be >= 0");
+  if (cfg->priority_dof < 0) return set_error(DG_ERR_ARG, "priority_dof must be >= 0");
   if (cfg->precision != DG_FP64 && cfg->precision != DG_FP32_BULK) return set_error(DG_ERR_ARG, "bad precision");
   dg_server* s = new dg_server();
   s->cfg = *cfg;

@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
   const int p = pq % n, q = pq / n;
   const int cs = a.side_case ? a.side_case[s] : 0;
   if (cs < 0) return;  // free side slot of a serving pool
+  if (a.cases && a.cases[cs].dt == 0.0) return;  // a case that finished or sits this step out
   const CaseParams cp = case_params(a, cs);
   const int2 ee = a.side_e[s];
   const int sf = a.side_f[s];
@@ -587,6 +588,7 @@ __global__ void __launch_bounds__(256) k_surf_flux(StageArgs a) {
   const int p = pq % n, q = pq / n;
   const int cs = a.side_case ? a.side_case[s] : 0;
   if (cs < 0) return;  // free side slot of a serving pool
+  if (a.cases && a.cases[cs].dt == 0.0) return;  // a case that finished or sits this step out
   const CaseParams cp = case_params(a, cs);
   const int2 ee = a.side_e[s];
   const int sf = a.side_f[s];
@@ -1093,6 +1095,9 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
   }
   if constexpr (aos) cp_async_wait<0>();
   if (!valid) return;
+  // a serving case that finished or sits this step out keeps its state (its
+  // surface fluxes were not formed this step)
+  if (MODE == 1 && a.cases && a.cases[ce].dt == 0.0) return;
 
   // ---- SurfInt: face nodes receive +-f* lhat ----
   const T* Fst = TBuf<T>::fstar(a);

@@ -61,7 +61,7 @@ struct CaseData {
   int nonfinite;  // sticky
   int steps;      // completed steps
   int N;          // polynomial degree of the case's pool
-  int pad;
+  int paused;     // 1: the case sits out the next step (priority policy)
   float f_mu, f_lam, f_ref_p, f_ref_H, f_ref_T, f_pad;  // FP32 copies (FP32-bulk kernels)
 };
 

@@ -81,7 +81,7 @@ def _bc_arrays(mesh):
 class ServerConfig(C.Structure):
     _fields_ = [("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double), ("dfl", C.c_double),
                 ("precision", C.c_int), ("max_cases", C.c_int), ("pool_elems", C.c_int64 * 8),
-                ("max_resident_dof", C.c_int64)]
+                ("max_resident_dof", C.c_int64), ("priority_dof", C.c_int64)]
 
 
 class CaseDesc(C.Structure):
@@ -405,7 +405,7 @@ class Server:
                  "nonfinite")
 
     def __init__(self, pool_elems=None, max_cases=64, precision=FP64, gamma=1.4, R=1.0, Pr=0.72, dfl=0.9,
-                 max_resident_dof=0):
+                 max_resident_dof=0, priority_dof=0):
         lib = load()
         self._lib = lib
         cfg = ServerConfig()
@@ -414,6 +414,7 @@ class Server:
         cfg.precision = precision
         cfg.max_cases = max_cases
         cfg.max_resident_dof = int(max_resident_dof)
+        cfg.priority_dof = int(priority_dof)
         if pool_elems is not None:
             for N in range(8):
                 cfg.pool_elems[N] = int(pool_elems.get(N, 0))

@@ -158,3 +158,33 @@ def test_fp32_bulk_alone_and_in_the_mix_are_bitwise_equal():
     for tk, Ua in zip(tickets, alone):
         np.testing.assert_array_equal(srv.wait(tk)[0], Ua)
     srv.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_priority_policy_keeps_results_and_serves_oldest_first(prec):
+    """With priority_dof of one DOF only the oldest resident case advances in
+    each batched step (the others sit it out with their state unchanged): the
+    results are bitwise those of the free-for-all mix, and the cases finish
+    one after another in submission order."""
+    torch, dg = gpu_or_skip()
+    precision = dg.FP64 if prec == "fp64" else dg.FP32_BULK
+    t_end = 0.04
+    built = [make(*c) for c in CASES[:4]]
+    free = dg.Server(POOLS, max_cases=8, precision=precision)
+    ref = [free.wait(tk)[0] for tk in [free.submit(m, U0, t_end, mu=mu) for m, U0, mu in built]]
+    free.close()
+    srv = dg.Server(POOLS, max_cases=8, precision=precision, priority_dof=1)
+    tickets = [srv.submit(m, U0, t_end, mu=mu) for m, U0, mu in built]
+    out = [srv.wait(tk) for tk in tickets]
+    stats = srv.stats()
+    srv.close()
+    for (U, st), Ur in zip(out, ref):
+        np.testing.assert_array_equal(U, Ur)
+        assert st["t_final"] == t_end and st["nonfinite"] == 0
+    # one case at a time: the batched steps add up to the cases' own steps
+    # (plus at most one step per case for the hand-over)
+    own = sum(st["steps"] for _, st in out)
+    assert own <= stats["steps"] <= own + 2 * len(out) + 2, (own, stats["steps"])
+    # and they finish in submission order
+    ends = [st["time_to_solution"] for _, st in out]
+    assert all(ends[i] < ends[i + 1] for i in range(len(ends) - 1)), ends

@@ -486,6 +486,31 @@ def gauss_bench(dg, torch, stream, nel=NEL, steps=20):
                         f"on Gauss-Legendre nodes, {steps} CFL steps", **out}
 
 
+# Measured device memory per DOF of the paper's solver (Sec. 4.2, Tab.
+# memory_requirements), KiB, for N = 1..7
+PAPER_KIB_PER_DOF = {1: 1.457, 2: 1.188, 3: 1.049, 4: 0.996, 5: 0.942, 6: 0.895, 7: 0.869}
+
+
+def memory_per_dof(dg, stream, nel=8):
+    """Device bytes per DOF of one context (state, RK register, scratch,
+    metrics in both precisions, lifted gradients, side arrays; LGL nodes,
+    FP64) for N = 1..7 on an nel^3 periodic mesh, against the paper's table,
+    and the largest N = 7 problem that would fit this GPU's memory."""
+    import torch
+    from paper_2404_12703_gb300 import workloads as W
+    out = {}
+    for N in range(1, 8):
+        m = W.box_mesh(N, (nel,) * 3, seed=3)
+        s = dg.Solver(m, stream=stream)
+        dof = m["E"] * (N + 1) ** 3
+        kib = s.sizes()["bytes"] / dof / 1024.0
+        out[str(N)] = {"kib_per_dof": kib, "paper_kib_per_dof": PAPER_KIB_PER_DOF[N]}
+        s.close()
+    total = torch.cuda.get_device_properties(0).total_memory
+    out["max_dof_N7_this_gpu"] = int(0.95 * total / (out["7"]["kib_per_dof"] * 1024.0))
+    return out
+
+
 def mms_error(dg, torch, stream, N, nel, nodes, T=0.2, cfl=0.2, mu=0.01):
     """L2 density error at time T of the manufactured solution of Sec. 5.1 on
     [-1, 1]^3 (nel^3 curved elements, periodic), viscous, started from its
@@ -766,11 +791,12 @@ def run_ours(args):
     if not args.no_shock and rank == 0:
         shock = shock_tube_bench(dg, torch, stream)
 
-    comp = chan = gauss = None
+    comp = chan = gauss = memory = None
     if not args.no_shock and rank == 0:
         comp = compressible_bench(dg, torch, stream)
         chan = channel_bench(dg, torch, stream)
         gauss = gauss_bench(dg, torch, stream, nel=nel)
+        memory = memory_per_dof(dg, stream)
 
     serving = None
     if not args.no_serving and rank == 0:
@@ -797,7 +823,7 @@ def run_ours(args):
             "e2e": {"value": world * dof * STAGES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32, "shock_tube": shock, "compressible_tgv": comp,
-            "channel": chan, "gauss_nodes": gauss,
+            "channel": chan, "gauss_nodes": gauss, "memory": memory,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

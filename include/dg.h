@@ -385,6 +385,13 @@ int dg_kinetic_noalloc(int N, int64_t n_elems, const double* U, const double* J,
                             p + n q in the master's face frame, last dg_rhs
    what = DG_DEBUG_ALPHA:   out0 = blending factor [E] of the last dg_rhs
    Synchronises. */
+/* Verification of the library's own binary64 -> binary32 (round to nearest,
+   ties to even) and binary32 -> binary64 conversions, which the FP32-bulk
+   kernels run on the integer pipe instead of the FP64 unit: out[i] =
+   binary32(in[i]), back[i] = binary64(out[i]); device buffers of n values,
+   stream-ordered on `stream`.  DG_ERR_ARG for NULL buffers or n < 0. */
+int dg_selftest_convert(const double* in, float* out, double* back, int64_t n, void* stream);
+
 enum { DG_DEBUG_METRICS = 0, DG_DEBUG_MAPS = 1, DG_DEBUG_GRAD = 2, DG_DEBUG_FSTAR = 3,
        DG_DEBUG_ALPHA = 4 };
 int dg_debug(dg_ctx* ctx, int what, void* out0, void* out1);

@@ -597,6 +597,13 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* params
   return dg::init_mesh_impl(out, mesh, params, (cudaStream_t)stream, nullptr);
 }
 
+int dg_selftest_convert(const double* in, float* out, double* back, int64_t n, void* stream) {
+  if (!in || !out || !back || n < 0 || n > ((int64_t)1 << 40)) return fail(DG_ERR_ARG, "bad buffers or size");
+  cudaError_t e = launch_convert_check(in, out, back, n, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_selftest_convert");
+  return DG_OK;
+}
+
 int dg_quadrature_weights(const dg_ctx* c, double* w) {
   if (!c || !w) return fail(DG_ERR_ARG, "ctx or w is NULL");
   Ops o;

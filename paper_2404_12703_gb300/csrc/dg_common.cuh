@@ -81,6 +81,72 @@ __device__ __forceinline__ dd dd_mul(dd a, dd b) {
 __device__ __forceinline__ double dd_to_double(dd a) { return __dadd_rn(a.hi, a.lo); }
 
 // ---------------------------------------------------------------------------
+// binary64 <-> binary32 conversions on the integer pipe.  The FP32-bulk
+// kernels convert FP64 state values to FP32 and their FP32 results back; a
+// GB300 runs FP64 at 1/64 of the FP32 rate and the hardware conversions
+// share that unit, where they used half or more of its cycles in those
+// kernels.  These do the same conversions with 32/64-bit integer operations,
+// written from the IEEE 754 formats: binary64 -> binary32 rounds to nearest,
+// ties to even (normal, subnormal, overflow to infinity, zero, NaN to the
+// quiet NaN 0x7fffffff); binary32 -> binary64 is exact.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;  // 52 fraction bits
+  if (e == 0x7ff) return __uint_as_float(m ? 0x7fffffffu : (sign | 0x7f800000u));
+  const int ef = e - 1023 + 127;  // biased binary32 exponent
+  if (ef >= 0xff) return __uint_as_float(sign | 0x7f800000u);
+  if (ef > 0) {
+    // keep 23 fraction bits; the 29 dropped bits decide the rounding; a carry
+    // out of the fraction increments the exponent (to infinity at the top)
+    unsigned q = ((unsigned)ef << 23) | (unsigned)(m >> 29);
+    const unsigned long long rem = m & 0x1FFFFFFFull, half = 0x10000000ull;
+    if (rem > half || (rem == half && (q & 1u))) ++q;
+    return __uint_as_float(sign | q);
+  }
+  if (ef < -24 || e == 0) return __uint_as_float(sign);  // below half the smallest subnormal (or a binary64 subnormal)
+  // binary32 subnormal: 53-bit significand shifted right by 30 - ef
+  const unsigned long long mm = m | (1ull << 52);
+  const int shift = 30 - ef;
+  unsigned long long q = mm >> shift;
+  const unsigned long long rem = mm & ((1ull << shift) - 1), half = 1ull << (shift - 1);
+  if (rem > half || (rem == half && (q & 1ull))) ++q;
+  return __uint_as_float(sign | (unsigned)q);
+}
+
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xff, m = u & 0x7fffffu;
+  if (e == 0xff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | ((unsigned long long)m << 29)));
+  if (e == 0) {
+    if (m == 0) return __longlong_as_double((long long)sign);
+    // subnormal: normalise the fraction (leading one moved to bit 23)
+    const int lz = __clz(m) - 8;  // zeros between bit 22 and the leading one, plus one
+    const unsigned mn = (m << lz) & 0x7fffffu;
+    const unsigned long long e64 = (unsigned long long)(1023 - 126 - lz);
+    return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)mn << 29)));
+  }
+  const unsigned long long e64 = (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)m << 29)));
+}
+
+// an FP64 value in the arithmetic type T (FP32: rounded on the integer pipe)
+template <typename T>
+__device__ __forceinline__ T from_f64(double v) {
+  if constexpr (sizeof(T) == sizeof(float)) return f32_rn(v);
+  else return v;
+}
+// a value of the arithmetic type T in FP64 (exact; FP32 on the integer pipe)
+template <typename T>
+__device__ __forceinline__ double to_f64(T v) {
+  if constexpr (sizeof(T) == sizeof(float)) return f64_of(v);
+  else return v;
+}
+
+// ---------------------------------------------------------------------------
 // Point-wise physics, templated on the arithmetic type T.
 // ---------------------------------------------------------------------------
 struct Gas {

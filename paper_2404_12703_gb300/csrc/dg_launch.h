@@ -81,6 +81,9 @@ cudaError_t launch_to_public(dg_ctx* c, const double* internal, double* pub);
 // kinetic energy reductions into c->scal->kin (U internal, Ut internal or null)
 cudaError_t launch_kinetic(dg_ctx* c, const double* U, const double* Ut);
 
+// the integer-pipe binary64 <-> binary32 conversions over n values (dg_rhs.cu)
+cudaError_t launch_convert_check(const double* in, float* out, double* back, int64_t n, cudaStream_t st);
+
 // verification copies
 cudaError_t launch_debug_metrics(dg_ctx* c, double* Ja, double* J);
 cudaError_t launch_debug_maps(dg_ctx* c, int* nbr, int* nodes);

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U
                                             int sutherland, double inv_Tref, DevScalars* scal) {
   constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
   constexpr bool f32 = sizeof(T) == sizeof(float);
-  double lc = 0.0, lv = 0.0;
+  T lcT = T(0), lvT = T(0);  // per-thread maxima in the arithmetic type
   int bad = 0;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < (int64_t)E * n3;
        x += (int64_t)gridDim.x * blockDim.x) {
@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U
     const T Ji = M(9);
     T aa = T(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) aa += fabs(u * M(d * 3) + v * M(d * 3 + 1) + w * M(d * 3 + 2)) + c * T(Gm[d * n3]);
+    for (int d = 0; d < 3; ++d)
+      aa += fabs(u * M(d * 3) + v * M(d * 3 + 1) + w * M(d * 3 + 2)) + c * T(Gm[d * n3]);
     aa *= Ji;
     T kvn = T(kv);
     if (sutherland) {  // mu(T) / mu_ref by Sutherland's law (Eq. sutherland)
@@ -47,9 +48,10 @@ __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U
     }
     const T bb = kvn * ri * T(Gm[3 * n3]) * Ji * Ji;
     if (!isfinite(aa) || !isfinite(bb)) bad = 1;
-    lc = fmax(lc, double(aa));
-    lv = fmax(lv, double(bb));
+    lcT = fmax(lcT, aa);
+    lvT = fmax(lvT, bb);
   }
+  double lc = to_f64<T>(lcT), lv = to_f64<T>(lvT);
   // block reduction
   __shared__ double rc[32], rv[32];
   __shared__ int rb;
@@ -70,6 +72,23 @@ __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U
     if (viscous) atomicMax(&scal->lam_v, (unsigned long long)__double_as_longlong(lv));
     if (rb) atomicOr(&scal->nonfinite, 1);
   }
+}
+
+// the integer-pipe conversions, for dg_selftest_convert
+__global__ void k_convert_check(const double* __restrict__ in, float* __restrict__ out, double* __restrict__ back,
+                                int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float f = f32_rn(in[i]);
+  out[i] = f;
+  back[i] = f64_of(f);
+}
+
+cudaError_t launch_convert_check(const double* in, float* out, double* back, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_convert_check<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, back, n);
+  count_launch();
+  return cudaGetLastError();
 }
 
 // the CFL rule from the reduced spectral radii

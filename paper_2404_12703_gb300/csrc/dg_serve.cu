@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(128) k_cfl_cases(int64_t nlist, const int* __r
   // whole block leaves together
   if (c < 0 || !(cases[c].t < cases[c].t_end) || cases[c].paused) return;
   const T kv = T(kvf * cases[c].mu);
-  double lc = 0.0, lv = 0.0;
+  T lcT = T(0), lvT = T(0);
   int bad = 0;
   for (int t = threadIdx.x; t < n3; t += 128) {
     const double* up = U + e * 5 * n3 + t;
@@ -65,13 +65,15 @@ __global__ void __launch_bounds__(128) k_cfl_cases(int64_t nlist, const int* __r
     const T Ji = M(9);
     T aa = T(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) aa += fabs(u * M(d * 3) + v * M(d * 3 + 1) + w * M(d * 3 + 2)) + cs * T(Gm[d * n3]);
+    for (int d = 0; d < 3; ++d)
+      aa += fabs(u * M(d * 3) + v * M(d * 3 + 1) + w * M(d * 3 + 2)) + cs * T(Gm[d * n3]);
     aa *= Ji;
     const T bb = kv * ri * T(Gm[3 * n3]) * Ji * Ji;
     if (!isfinite(aa) || !isfinite(bb)) bad = 1;
-    lc = fmax(lc, double(aa));
-    lv = fmax(lv, double(bb));
+    lcT = fmax(lcT, aa);
+    lvT = fmax(lvT, bb);
   }
+  double lc = to_f64<T>(lcT), lv = to_f64<T>(lvT);
   __shared__ double rc[4], rv[4];
   __shared__ int rb;
   if (threadIdx.x == 0) rb = 0;

@@ -170,37 +170,44 @@ __device__ __forceinline__ double case_dt(const StageArgs& a, int c) {
   return a.cases ? a.cases[c < 0 ? 0 : c].dt : a.scal->dt;
 }
 
-// ConsToPrim (Eqs. eos_p, eos_T) in FP64; the FP64 path has a zero reference
-template <typename T>
-__device__ __forceinline__ SPrim<T> shifted_prim(const double U[5], double gm1, double Rinv, const CaseParams& cp,
-                                                double* p_full = nullptr) {
-  const double ri = 1.0 / U[0];
-  const double u = U[1] * ri, v = U[2] * ri, w = U[3] * ri;
-  const double p = gm1 * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
-  const double H = (U[4] + p) * ri;
-  const double Tm = p * ri * Rinv;
-  if (p_full) *p_full = p;
-  return {T(U[0]), T(u), T(v), T(w), T(p - cp.pr), T(H - cp.Hr), T(Tm - cp.Tr)};
-}
-
+// ConsToPrim (Eqs. eos_p, eos_T).  FP64 path: in FP64 with a zero reference.
 // FP32-bulk: the shifted primitives from the two deviations that cancel,
 // d_rho = rho - rr and d_E = rho e - Er, taken in FP64; the rest in FP32.
 // With Er = pr / (gamma - 1) and Hr = (Er + pr) / rr, exactly
 //   p' = (gamma - 1)(d_E - |m|^2 / (2 rho)),
 //   H' = (d_E + p' - Hr d_rho) / rho,
 //   T' = (p' / R - Tr d_rho) / rho.
-template <>
-__device__ __forceinline__ SPrim<float> shifted_prim<float>(const double U[5], double gm1, double Rinv,
-                                                            const CaseParams& cp, double* p_full) {
-  const float drho = float(U[0] - cp.rr), dE = float(U[4] - cp.Er);
-  const float rho = float(U[0]), m0 = float(U[1]), m1 = float(U[2]), m2 = float(U[3]);
-  const float ri = 1.0f / rho;
-  const float u = m0 * ri, v = m1 * ri, w = m2 * ri;
-  const float pp = cp.fgm1 * (dE - 0.5f * (m0 * u + m1 * v + m2 * w));
-  const float Hp = (dE + pp - cp.fHr * drho) * ri;
-  const float Tp = (pp * cp.fRinv - cp.fTr * drho) * ri;
-  if (p_full) *p_full = cp.pr + double(pp);
-  return {rho, u, v, w, pp, Hp, Tp};
+// INTCVT: the FP32 conversions on the integer pipe (f32_rn / f64_of: the
+// same values as the hardware conversions, off the FP64 unit).  That pays
+// in the volume kernel, whose FP64 unit also carries the RK update; in the
+// lifting and surface kernels the extra integer instructions cost more than
+// the conversions they replace.
+template <typename T, bool INTCVT = false>
+__device__ __forceinline__ SPrim<T> shifted_prim(const double U[5], double gm1, double Rinv, const CaseParams& cp,
+                                                double* p_full = nullptr) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    auto cvt = [](double x) -> float {
+      if constexpr (INTCVT) return f32_rn(x);
+      else return float(x);
+    };
+    const float drho = cvt(U[0] - cp.rr), dE = cvt(U[4] - cp.Er);
+    const float rho = cvt(U[0]), m0 = cvt(U[1]), m1 = cvt(U[2]), m2 = cvt(U[3]);
+    const float ri = 1.0f / rho;
+    const float u = m0 * ri, v = m1 * ri, w = m2 * ri;
+    const float pp = cp.fgm1 * (dE - 0.5f * (m0 * u + m1 * v + m2 * w));
+    const float Hp = (dE + pp - cp.fHr * drho) * ri;
+    const float Tp = (pp * cp.fRinv - cp.fTr * drho) * ri;
+    if (p_full) *p_full = cp.pr + (INTCVT ? f64_of(pp) : double(pp));
+    return {rho, u, v, w, pp, Hp, Tp};
+  } else {
+    const double ri = 1.0 / U[0];
+    const double u = U[1] * ri, v = U[2] * ri, w = U[3] * ri;
+    const double p = gm1 * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
+    const double H = (U[4] + p) * ri;
+    const double Tm = p * ri * Rinv;
+    if (p_full) *p_full = p;
+    return {T(U[0]), T(u), T(v), T(w), T(p - cp.pr), T(H - cp.Hr), T(Tm - cp.Tr)};
+  }
 }
 
 // metric component c (0..8: J a^d_x at 3d + x; 9: 1/J) of node t of element e
@@ -839,7 +846,7 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
 #pragma unroll
       for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
     }
-    me = shifted_prim<T>(U, a.gm1, a.Rinv, cp, &p_full);
+    me = shifted_prim<T, true>(U, a.gm1, a.Rinv, cp, &p_full);
     // halved values: every arithmetic mean of the two-point flux is then one
     // addition, bit-identical to (a + b) / 2
     if constexpr (aos) {
@@ -1123,7 +1130,7 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
   const T Ji = metric_at<T>(a, e, 9, t, n3);
   double Ut[5];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) Ut[k] = (double)(-(accC[k] + acc[k]) * Ji);
+  for (int k = 0; k < 5; ++k) Ut[k] = to_f64<T>(-(accC[k] + acc[k]) * Ji);
   Ut[4] += H_ref * Ut[0];
   if (a.sponge_sigma) {  // sponge source -sigma (U - U_base), FP64
     const double sg = a.sponge_sigma[(size_t)e * n3 + t];

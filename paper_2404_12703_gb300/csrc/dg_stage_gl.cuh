@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume_gl(StageArgs a) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
   }
-  const SPrim<T> me = shifted_prim<T>(U, a.gm1, a.Rinv, cp);
+  const SPrim<T> me = shifted_prim<T, true>(U, a.gm1, a.Rinv, cp);
   T tau[6] = {0, 0, 0, 0, 0, 0}, W[3] = {0, 0, 0};
   if (a.viscous) {
     T g[12];
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_volume_gl(StageArgs a) {
   const T Ji = metric_at<T>(a, e, 9, t, n3);
   double Ut[5];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) Ut[k] = (double)(-acc[k] * Ji);
+  for (int k = 0; k < 5; ++k) Ut[k] = to_f64<T>(-acc[k] * Ji);
   Ut[4] += cp.Hr * Ut[0];
   if (a.sponge_sigma) {  // sponge source -sigma (U - U_base), FP64
     const double sg = a.sponge_sigma[(size_t)e * n3 + t];

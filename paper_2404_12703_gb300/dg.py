@@ -30,7 +30,7 @@ SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "d
                  "dg_server_destroy")
 EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
            "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_autotune", "dg_set_config", "dg_get_config",
-           "dg_set_sponge", "dg_node_coords", "dg_quadrature_weights",
+           "dg_set_sponge", "dg_node_coords", "dg_quadrature_weights", "dg_selftest_convert",
            "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
            "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
 
@@ -107,6 +107,7 @@ def load(path: str | None = None):
             "dg_set_stream": (C.c_int, [vp, vp]),
             "dg_node_coords": (C.c_int, [vp, vp, C.c_int]),
             "dg_quadrature_weights": (C.c_int, [vp, dp]),
+            "dg_selftest_convert": (C.c_int, [vp, vp, vp, C.c_int64, vp]),
             "dg_set_params": (C.c_int, [vp, C.POINTER(Params)]),
             "dg_set_state": (C.c_int, [vp, vp, C.c_int, C.c_double]),
             "dg_get_state": (C.c_int, [vp, vp, C.c_int, dp]),
@@ -176,6 +177,18 @@ def kinetic_noalloc(N, U, J, Ut=None, out=None, stream=None):
                                      C.c_void_p(Ut.data_ptr() if Ut is not None else 0),
                                      C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+def convert_check(x, stream=None):
+    """The library's integer-pipe conversions applied to a CUDA float64 tensor:
+    (binary32 values, those values back in binary64)."""
+    import torch
+    x = x.contiguous()
+    out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    back = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    _check(load().dg_selftest_convert(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                      C.c_void_p(back.data_ptr()), x.numel(), _stream_ptr(stream)))
+    return out, back
 
 
 def launch_count() -> int:

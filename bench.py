@@ -46,13 +46,16 @@ BYTES_PER_DOF = 8 * (30 + 204 / (N_DEG + 1))
 # DRAM bytes per DOF of one k_volume<7,1> launch, from the ncu capture summarised
 # in profiles/k_volume_tgv12_N7_fp64.md (12^3 mesh; the traffic scales with
 # the DOF count).  Set to None whenever the kernel changes until re-measured.
-VOLUME_TRAFFIC_BYTES_PER_DOF = 332.63
+VOLUME_TRAFFIC_BYTES_PER_DOF = 332.02
 # FP32-bulk: algorithmic bytes per DOF of one volume-kernel launch (reads U 40,
 # FP32 metrics 40, FP32 lifted gradients 48, dU 40, surface fluxes ~8; writes
 # U 40, dU 40), and of a whole stage for the minimal two-phase method with the
 # RK register in FP64 and the face traces in FP32: 342 B at N = 7.
 VOLUME32_BYTES_PER_DOF = 40 + 40 + 48 + 40 + 8 + 40 + 40
 BYTES32_PER_DOF = 342.0
+# DRAM bytes per DOF of one k_volume<7,1,float> launch (ncu, 12^3 mesh,
+# profiles/k_volume_tgv12_N7_fp32bulk.md); None whenever the kernel changes
+VOLUME32_TRAFFIC_BYTES_PER_DOF = 220.94
 # Standard DGSEM on Gauss-Legendre nodes, algorithmic flops per DOF and stage
 # (n = N + 1, FMA = 2 flops).  Lifting: D-hat line sums 72 n, metric products
 # 36, both faces of three lines 144, 1/J 12, ProlongToFace of the twelve
@@ -775,7 +778,9 @@ def run_ours(args):
                          "achieved": VOLUME32_BYTES_PER_DOF * dof / (vol32 * 1e-3) / 1e9,
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": VOLUME32_BYTES_PER_DOF * dof / (vol32 * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
-                         "traffic": None, "peak_source": peak_src,
+                         "traffic": (VOLUME32_TRAFFIC_BYTES_PER_DOF * dof if VOLUME32_TRAFFIC_BYTES_PER_DOF
+                                     else None),
+                         "peak_source": peak_src,
                          "algorithmic_bytes_per_dof": VOLUME32_BYTES_PER_DOF},
             "whole_step_hbm_frac": BYTES32_PER_DOF * dof * STAGES / (ms32 * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
             "accuracy_vs_fp64": {

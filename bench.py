@@ -135,7 +135,7 @@ class Clocks:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
@@ -147,13 +147,17 @@ class Clocks:
                     smax.append(float(parts[2]))
                 except ValueError:
                     continue
+                try:
+                    power.append(float(parts[3]))
+                except ValueError:
+                    pass
                 for nm, v in zip(names, parts[5:9]):
                     if v.lower() == "active":
                         reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w": statistics.median(power) if power else None}
 
 
 def measured_peaks():
@@ -818,6 +822,14 @@ def run_ours(args):
                          f"single-threaded FP64 C"}
 
     if rank == 0:
+        clocks = clk.summary()
+        # energy per DOF and stage (Sec. 4.1: EPID = P_rank PID), from the median
+        # board power sampled during the timed region (no cooling share)
+        pw = clocks.get("power_w")
+        epid = {"power_w": pw, "j_per_dof_stage": (pw / (value / world) if pw else None),
+                "paper_a100_j_per_dof_stage": 2.05e-6,
+                "note": "board power of this GPU; the paper's figure is Rotor 37 on A100 with 448 W per GPU "
+                        "including cooling"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -827,7 +839,7 @@ def run_ours(args):
             "autotune": {"config": tune64[0], "variant_ms": tune64[1]},
             "e2e": {"value": world * dof * STAGES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
-            "clocks": clk.summary(), "cpu_baseline": cpu, "fp32_bulk": fp32, "shock_tube": shock, "compressible_tgv": comp,
+            "clocks": clocks, "epid": epid, "cpu_baseline": cpu, "fp32_bulk": fp32, "shock_tube": shock, "compressible_tgv": comp,
             "channel": chan, "gauss_nodes": gauss, "memory": memory,
             "serving": serving,
         }

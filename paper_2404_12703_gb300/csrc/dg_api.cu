@@ -251,25 +251,59 @@ static void dfree(dg_ctx* c, void* p) {
   else cudaFree(p);
 }
 
+// side arrays common to both precisions (the working arrays of one
+// precision come from ensure_arrays)
 int alloc_side_arrays(dg_ctx* c, std::string& msg) {
   cudaError_t e = cudaSuccess;
   const int64_t S = c->S, n2 = c->n2;
   if (e == cudaSuccess) e = dalloc(c, &c->nrm, S * 4 * n2);
-  if (e == cudaSuccess) e = dalloc(c, &c->nrm32, S * 7 * n2);
-  if (e == cudaSuccess) e = dalloc(c, &c->lflux, S * 12 * n2);
-  if (e == cudaSuccess) e = dalloc(c, &c->fstar, S * 5 * n2);
-  if (e == cudaSuccess) e = dalloc(c, &c->lflux32, S * 12 * n2);
-  if (e == cudaSuccess) e = dalloc(c, &c->fstar32, S * 5 * n2);
   if (e == cudaSuccess) e = dalloc(c, &c->side_e, S);
   if (e == cudaSuccess) e = dalloc(c, &c->side_f, S);
   if (e == cudaSuccess) e = dalloc(c, &c->side_bc, S);
-  if (c->gauss) {
-    if (e == cudaSuccess) e = dalloc(c, &c->Ufc, S * 2 * 5 * n2);
-    if (e == cudaSuccess) e = dalloc(c, &c->gfc, S * 2 * 12 * n2);
-    if (e == cudaSuccess) e = dalloc(c, &c->gfc32, S * 2 * 12 * n2);
-  }
+  if (c->gauss && e == cudaSuccess) e = dalloc(c, &c->Ufc, S * 2 * 5 * n2);
   if (e != cudaSuccess) {
     msg = std::string("side arrays: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+  }
+  return DG_OK;
+}
+
+// The working arrays of the parameters' precision (FP64: lifted gradients,
+// lifting and surface fluxes; FP32-bulk: their FP32 twins and the FP32
+// metrics and side geometry, rounded from the FP64 ones) and, with shock
+// capturing, the sub-cell interface metrics.  Each set is allocated and
+// formed the first time a parameter set needs it, so a context holds only
+// what it uses.  E and S are the context's capacities (a serving pool's).
+int ensure_arrays(dg_ctx* c, const dg_params* p, std::string& msg) {
+  const int64_t E = c->cap_E, S = c->cap_S;
+  const int64_t n3 = c->n3, n2 = c->n2;
+  cudaStream_t st = c->pool_stream ? c->pool_stream : c->stream;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  if (p->precision == DG_FP64 && !c->g) {
+    A(dalloc(c, &c->g, E * 12 * n3));
+    A(dalloc(c, &c->lflux, S * 12 * n2));
+    A(dalloc(c, &c->fstar, S * 5 * n2));
+    if (c->gauss) A(dalloc(c, &c->gfc, S * 2 * 12 * n2));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->g, 0, sizeof(double) * E * 12 * n3, st);
+  }
+  if (p->precision == DG_FP32_BULK && !c->g32) {
+    A(dalloc(c, &c->g32, E * 12 * n3));
+    A(dalloc(c, &c->metric32, E * 10 * n3));
+    A(dalloc(c, &c->lflux32, S * 12 * n2));
+    A(dalloc(c, &c->fstar32, S * 5 * n2));
+    A(dalloc(c, &c->nrm32, S * 7 * n2));
+    if (c->gauss) A(dalloc(c, &c->gfc32, S * 2 * 12 * n2));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->g32, 0, sizeof(float) * E * 12 * n3, st);
+    if (e == cudaSuccess) e = launch_fp32_geometry(c, st);
+  }
+  if (p->shock_capturing && !c->fvmetric) {
+    A(dalloc(c, &c->fvmetric, E * 3 * (c->n - 1) * 3 * n2));
+    if (e == cudaSuccess) e = launch_fv_metrics(c, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    msg = std::string("working arrays: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
   }
   return DG_OK;
@@ -434,20 +468,11 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
   A(dalloc(c, &c->Ut, E * 5 * n3));
   A(dalloc(c, &c->Upub, E * 5 * n3));
   A(dalloc(c, &c->metric, E * 10 * n3));
-  A(dalloc(c, &c->metric32, E * 10 * n3));
-  A(dalloc(c, &c->g, E * 12 * n3));
-  A(dalloc(c, &c->g32, E * 12 * n3));
   A(dalloc(c, &c->alpha, E));
-  A(dalloc(c, &c->fvmetric, E * 3 * (c->n - 1) * 3 * n2));
   A(dalloc(c, &c->cflgeo, E * 4 * n3));
   A(dalloc(c, &c->elem_side, E * 6));
   A(dalloc(c, &c->elem_case, E));
   A(dalloc(c, &c->nrm, S * 4 * n2));
-  A(dalloc(c, &c->nrm32, S * 7 * n2));
-  A(dalloc(c, &c->lflux, S * 12 * n2));
-  A(dalloc(c, &c->fstar, S * 5 * n2));
-  A(dalloc(c, &c->lflux32, S * 12 * n2));
-  A(dalloc(c, &c->fstar32, S * 5 * n2));
   A(dalloc(c, &c->side_e, S));
   A(dalloc(c, &c->side_f, S));
   A(dalloc(c, &c->side_case, S));
@@ -465,19 +490,27 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
     A(cudaMemsetAsync(c->U, 0, sizeof(double) * E * 5 * n3, stream));
     A(cudaMemsetAsync(c->dU, 0, sizeof(double) * E * 5 * n3, stream));
     A(cudaMemsetAsync(c->metric, 0, sizeof(double) * E * 10 * n3, stream));
-    A(cudaMemsetAsync(c->metric32, 0, sizeof(float) * E * 10 * n3, stream));
     A(cudaMemsetAsync(c->cflgeo, 0, sizeof(double) * E * 4 * n3, stream));
-    A(cudaMemsetAsync(c->g, 0, sizeof(double) * E * 12 * n3, stream));
-    A(cudaMemsetAsync(c->g32, 0, sizeof(float) * E * 12 * n3, stream));
     A(cudaMemsetAsync(c->elem_side, 0, sizeof(int) * E * 6, stream));
     A(cudaMemsetAsync(c->side_e, 0, sizeof(int2) * S, stream));
     A(cudaMemsetAsync(c->side_f, 0, sizeof(int) * S, stream));
     A(cudaMemsetAsync(c->nrm, 0, sizeof(double) * S * 4 * n2, stream));
-    A(cudaMemsetAsync(c->nrm32, 0, sizeof(float) * S * 7 * n2, stream));
     A(cudaMemsetAsync(c->elem_case, 0xff, sizeof(int) * E, stream));
     A(cudaMemsetAsync(c->side_case, 0xff, sizeof(int) * S, stream));
     A(cudaMemsetAsync(c->side_bc, 0xff, sizeof(int) * S, stream));
     A(cudaStreamSynchronize(stream));
+  }
+  c->cap_E = E;
+  c->cap_S = S;
+  if (e == cudaSuccess) {
+    // the working arrays of the pool's precision (the geometry is all zero here)
+    std::string m2;
+    const int st = ensure_arrays(c, params, m2);
+    if (st != DG_OK) {
+      msg = "pool allocation: " + m2;
+      dg_destroy(c);
+      return st;
+    }
   }
   if (e != cudaSuccess) {
     msg = std::string("pool allocation: ") + cudaGetErrorString(e);
@@ -537,11 +570,7 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
   A(dalloc(c, &c->Ut, E * 5 * n3));
   A(dalloc(c, &c->Upub, E * 5 * n3));
   A(dalloc(c, &c->metric, E * 10 * n3));
-  A(dalloc(c, &c->metric32, E * 10 * n3));
-  A(dalloc(c, &c->g, E * 12 * n3));
-  A(dalloc(c, &c->g32, E * 12 * n3));
   A(dalloc(c, &c->alpha, E));
-  A(dalloc(c, &c->fvmetric, E * 3 * (c->n - 1) * 3 * c->n2));
   A(dalloc(c, &c->cflgeo, E * 4 * n3));
   A(dalloc(c, &c->elem_side, E * 6));
   A(dalloc(c, &c->xyzs, E * n3 * 3));
@@ -560,7 +589,6 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
   A(cudaMemcpyAsync(c->ops, &ops, sizeof(Ops), cudaMemcpyHostToDevice, c->stream));
   A(cudaMemsetAsync(c->scal, 0, sizeof(DevScalars), c->stream));
   A(cudaMemsetAsync(c->alpha, 0, sizeof(double) * E, c->stream));
-  A(cudaMemsetAsync(c->g, 0, sizeof(double) * E * 12 * n3, c->stream));
   A(cudaStreamSynchronize(c->stream));
   if (e != cudaSuccess) {
     int r = cuda_fail(e, "initialisation");
@@ -581,6 +609,11 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
     }
   }
   st = build_mesh(c, mesh->corner_vid, mesh->xyz, mesh->face_bc, msg);
+  if (st == DG_OK) {
+    c->cap_E = c->E;
+    c->cap_S = c->S;
+    st = ensure_arrays(c, &c->prm, msg);
+  }
   if (st != DG_OK) {
     dg_destroy(c);
     return fail(st, msg);
@@ -634,6 +667,11 @@ int dg_set_params(dg_ctx* c, const dg_params* p) {
   if (st != DG_OK) return st;
   if (c->gauss && p->shock_capturing)
     return fail(DG_ERR_ARG, "shock capturing needs LGL nodes (the sub-cell FV scheme lives on the LGL sub-cells)");
+  {
+    std::string msg;
+    const int sa = ensure_arrays(c, p, msg);  // a new precision's working arrays, or the FV metrics
+    if (sa != DG_OK) return fail(sa, msg);
+  }
   c->prm = *p;
   destroy_graph(c);
   if (c->state_set) {

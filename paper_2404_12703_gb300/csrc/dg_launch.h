@@ -37,6 +37,15 @@ int init_mesh_impl(dg_ctx** out, const dg_mesh_desc* mesh, const dg_params* para
 int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, cudaStream_t stream,
                     std::string& msg);
 
+// FP32 copies of the metrics and side geometry, and the sub-cell interface
+// metrics of the FV blending, from the FP64 geometry (dg_mesh.cu)
+cudaError_t launch_fp32_geometry(dg_ctx* c, cudaStream_t st);
+cudaError_t launch_fv_metrics(dg_ctx* c, cudaStream_t st);
+
+// the arrays a parameter set needs (FP64 or FP32 working arrays, FV
+// interface metrics), allocated and formed on first use (dg_api.cu)
+int ensure_arrays(dg_ctx* c, const dg_params* p, std::string& msg);
+
 // device mesh set-up (dg_mesh.cu)
 // h_face_bc (may be null): [E][6] boundary-condition row + 1 of every face (0: inner)
 int build_mesh(dg_ctx* c, const int64_t* h_cvid, const double* h_xyz, const int* h_face_bc, std::string& msg);

@@ -187,14 +187,12 @@ __global__ void k_fill_sides(int64_t F_total, const long long* cvid, const int* 
 // Metrics in double-double (curl form) on the LGL nodes of the geometry; on
 // Gauss-Legendre nodes the same polynomials (J a^d and dx/dxi) evaluated at
 // the GL nodes by exact interpolation, J = det(dx/dxi) there.  1/J; the
-// solution nodes' coordinates; sub-cell interface metrics (LGL) by
-// telescoping the discrete derivative.
+// solution nodes' coordinates.
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1)) k_metrics(int E, const double* __restrict__ xyz,
                                                                         const Ops* __restrict__ ops, int gauss,
                                                                         double* __restrict__ metric,
-                                                                        double* __restrict__ fvm,
                                                                         double* __restrict__ xyzs) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -291,26 +289,35 @@ __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1)) k_metrics(int E, 
     for (int c = 0; c < 3; ++c) Me[(d * 3 + c) * n3 + t] = dd_to_double(Ja[d][c]);
 #pragma unroll
   for (int c = 0; c < 3; ++c) xyzs[((size_t)e * n3 + t) * 3 + c] = dd_to_double(dd_add(Xs[c], dd_from(X[c])));
-  __syncthreads();
-  if (gauss) return;
-  // sub-cell interface metrics (global writes above are visible after the barrier)
-  for (int tt = t; tt < 3 * n2; tt += n3) {
-    const int d = tt / n2, line = tt % n2;
-    const int p = line % n, q = line / n;
-    int base, st;
-    if (d == 0) { base = n * (p + n * q); st = 1; }
-    else if (d == 1) { base = p + n2 * q; st = n; }
-    else { base = p + n * q; st = n2; }
-    double* F = fvm + (size_t)e * 3 * (n - 1) * 3 * n2;
-    for (int c = 0; c < 3; ++c) {
-      const double* Jd_c = Me + (d * 3 + c) * n3;
-      double Jh = Jd_c[base];
-      for (int i = 0; i < n - 1; ++i) {
-        double dj = 0.0;
-        for (int a = 0; a < n; ++a) dj += ops->D[i * n + a] * Jd_c[base + a * st];
-        Jh = Jh + ops->w[i] * dj;
-        F[((d * (n - 1) + i) * 3 + c) * n2 + line] = Jh;
-      }
+}
+
+// sub-cell interface metrics of the FV blending (LGL), by telescoping the
+// discrete derivative of J a^d along each line: one thread per line and
+// direction, formed when shock capturing is first enabled
+template <int N>
+__global__ void k_fv_metrics(int E, const double* __restrict__ metric, const Ops* __restrict__ ops,
+                             double* __restrict__ fvm) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)E * 3 * n2) return;
+  const int64_t e = tid / (3 * n2);
+  const int tt = (int)(tid % (3 * n2));
+  const int d = tt / n2, line = tt % n2;
+  const int p = line % n, q = line / n;
+  int base, st;
+  if (d == 0) { base = n * (p + n * q); st = 1; }
+  else if (d == 1) { base = p + n2 * q; st = n; }
+  else { base = p + n * q; st = n2; }
+  const double* Me = metric + (size_t)e * 10 * n3;
+  double* F = fvm + (size_t)e * 3 * (n - 1) * 3 * n2;
+  for (int c = 0; c < 3; ++c) {
+    const double* Jd_c = Me + (d * 3 + c) * n3;
+    double Jh = Jd_c[base];
+    for (int i = 0; i < n - 1; ++i) {
+      double dj = 0.0;
+      for (int a = 0; a < n; ++a) dj += ops->D[i * n + a] * Jd_c[base + a * st];
+      Jh = Jh + ops->w[i] * dj;
+      F[((d * (n - 1) + i) * 3 + c) * n2 + line] = Jh;
     }
   }
 }
@@ -397,19 +404,43 @@ static cudaError_t launch_metrics(dg_ctx* c, const double* d_xyz) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   const size_t sm = sizeof(dd) * (2 * n2 + 6 * n3);
   cudaFuncSetAttribute(k_metrics<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_metrics<N><<<(unsigned)c->E, n3, sm, c->stream>>>((int)c->E, d_xyz, c->ops, c->gauss, c->metric, c->fvmetric,
-                                                      c->xyzs);
+  k_metrics<N><<<(unsigned)c->E, n3, sm, c->stream>>>((int)c->E, d_xyz, c->ops, c->gauss, c->metric, c->xyzs);
   count_launch();
   const int64_t tot = c->S * n2;
   k_side_geom<N><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>((int)c->S, c->side_e, c->side_f, c->metric,
                                                                        c->ops, c->gauss, c->nrm);
   const int64_t nodes = c->E * n3;
   k_cfl_geo<N><<<(unsigned)((nodes + 255) / 256), 256, 0, c->stream>>>((int)c->E, c->metric, c->cflgeo);
-  k_nrm32<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(tot, n2, c->nrm, c->nrm32);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+// FP32 copies of the metrics and side geometry (FP32-bulk), from the FP64 ones
+cudaError_t launch_fp32_geometry(dg_ctx* c, cudaStream_t st) {
+  const int64_t tot = c->S * c->n2;
+  if (tot > 0) k_nrm32<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, c->n2, c->nrm, c->nrm32);
+  const int64_t mwords = c->E * 10 * c->n3;
+  if (mwords > 0) k_round_f32<<<(unsigned)((mwords + 255) / 256), 256, 0, st>>>(mwords, c->metric, c->metric32);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+// sub-cell interface metrics (shock capturing), from the FP64 metrics
+cudaError_t launch_fv_metrics(dg_ctx* c, cudaStream_t st) {
+  const int64_t tot = c->E * 3 * c->n2;
+  if (tot == 0) return cudaSuccess;
+  const unsigned nb = (unsigned)((tot + 127) / 128);
+  switch (c->N) {
+    case 1: k_fv_metrics<1><<<nb, 128, 0, st>>>((int)c->E, c->metric, c->ops, c->fvmetric); break;
+    case 2: k_fv_metrics<2><<<nb, 128, 0, st>>>((int)c->E, c->metric, c->ops, c->fvmetric); break;
+    case 3: k_fv_metrics<3><<<nb, 128, 0, st>>>((int)c->E, c->metric, c->ops, c->fvmetric); break;
+    case 4: k_fv_metrics<4><<<nb, 128, 0, st>>>((int)c->E, c->metric, c->ops, c->fvmetric); break;
+    case 5: k_fv_metrics<5><<<nb, 128, 0, st>>>((int)c->E, c->metric, c->ops, c->fvmetric); break;
+    case 6: k_fv_metrics<6><<<nb, 128, 0, st>>>((int)c->E, c->metric, c->ops, c->fvmetric); break;
+    case 7: k_fv_metrics<7><<<nb, 128, 0, st>>>((int)c->E, c->metric, c->ops, c->fvmetric); break;
+    default: return cudaErrorInvalidValue;
+  }
   count_launch();
-  const int64_t mwords = c->E * 10 * n3;
-  k_round_f32<<<(unsigned)((mwords + 255) / 256), 256, 0, c->stream>>>(mwords, c->metric, c->metric32);
-  count_launch(3);
   return cudaGetLastError();
 }
 

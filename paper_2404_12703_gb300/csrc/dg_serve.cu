@@ -536,11 +536,12 @@ static bool admit(dg_server* s, Request& r, std::string& err) {
   };
   cp(p->U + e0 * 5 * n3, tmp->U, sizeof(double) * E * 5 * n3);
   cp(p->metric + e0 * 10 * n3, tmp->metric, sizeof(double) * E * 10 * n3);
-  cp(p->metric32 + e0 * 10 * n3, tmp->metric32, sizeof(float) * E * 10 * n3);
+  if (p->metric32 && tmp->metric32) cp(p->metric32 + e0 * 10 * n3, tmp->metric32, sizeof(float) * E * 10 * n3);
   cp(p->cflgeo + e0 * 4 * n3, tmp->cflgeo, sizeof(double) * E * 4 * n3);
-  cp(p->fvmetric + e0 * 3 * (p->n - 1) * 3 * n2, tmp->fvmetric, sizeof(double) * E * 3 * (p->n - 1) * 3 * n2);
+  if (p->fvmetric && tmp->fvmetric)
+    cp(p->fvmetric + e0 * 3 * (p->n - 1) * 3 * n2, tmp->fvmetric, sizeof(double) * E * 3 * (p->n - 1) * 3 * n2);
   cp(p->nrm + s0 * 4 * n2, tmp->nrm, sizeof(double) * S * 4 * n2);
-  cp(p->nrm32 + s0 * 7 * n2, tmp->nrm32, sizeof(float) * S * 7 * n2);
+  if (p->nrm32 && tmp->nrm32) cp(p->nrm32 + s0 * 7 * n2, tmp->nrm32, sizeof(float) * S * 7 * n2);
   cp(p->side_f + s0, tmp->side_f, sizeof(int) * S);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->dU + e0 * 5 * n3, 0, sizeof(double) * E * 5 * n3, q);
   if (e == cudaSuccess) {

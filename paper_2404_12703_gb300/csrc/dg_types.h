@@ -175,6 +175,7 @@ struct dg_ctx {
   dg::Ops* ops = nullptr;    // device copy of the operators of degree N
   dg::DevScalars* scal = nullptr;
   dg::DevScalars* scal_host = nullptr;  // pinned mirror
+  int64_t cap_E = 0, cap_S = 0;  // allocated element and side capacity (a pool's, or E and S)
   int gauss = 0;              // solution on Gauss-Legendre nodes (standard DGSEM)
   double stage_c = 0.0;       // RK c coefficient of the stage being enqueued (stage time)
   double* xyzs = nullptr;     // [E][n3][3] coordinates of the solution nodes

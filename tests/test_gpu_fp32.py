@@ -92,3 +92,28 @@ def test_precision_switch_keeps_state():
     c = s.rhs().cpu().numpy()
     np.testing.assert_array_equal(a, c)
     assert rel_err(b, a).max() < 2e-4
+
+
+def test_arrays_follow_the_parameters():
+    """A context holds the working arrays of its own precision only; switching
+    the precision (or turning shock capturing on) with dg_set_params forms
+    the missing ones, and the results equal those of a context created with
+    those parameters, bit for bit."""
+    torch, dg = gpu_or_skip()
+    N = 4
+    m = mesh(N, (3, 3, 4))
+    U = torch.from_numpy(W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5), 1e-3, 4)).cuda()
+    s = dg.Solver(m)
+    b64 = s.sizes()["bytes"]
+    r64 = s.rhs(U).cpu().numpy()
+    s.set_params(precision=dg.FP32_BULK)
+    assert s.sizes()["bytes"] > b64
+    r32 = s.rhs(U).cpu().numpy()
+    f32 = dg.Solver(m, precision=dg.FP32_BULK)
+    assert f32.sizes()["bytes"] < s.sizes()["bytes"]
+    np.testing.assert_array_equal(r32, f32.rhs(U).cpu().numpy())
+    s.set_params(precision=dg.FP64)
+    np.testing.assert_array_equal(s.rhs(U).cpu().numpy(), r64)
+    s.set_params(shock_capturing=1, alpha_force=0.3, riemann="lf")
+    ref = dg.Solver(m, shock_capturing=1, alpha_force=0.3, riemann="lf")
+    np.testing.assert_array_equal(s.rhs(U).cpu().numpy(), ref.rhs(U).cpu().numpy())

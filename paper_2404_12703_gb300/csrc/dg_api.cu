@@ -690,14 +690,31 @@ int dg_sizes(const dg_ctx* c, int* N, int64_t* E, int64_t* S, int64_t* bytes) {
   return DG_OK;
 }
 
+// the device address of pinned (page-locked) host memory, or null for
+// other memory: pinned host arrays are read and written by the layout
+// conversion kernels directly over the host link, without a staging copy
+static void* pinned_device_address(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int dg_set_state(dg_ctx* c, const double* U, int on_device, double t) {
   if (!c || !U) return fail(DG_ERR_ARG, "ctx or U is NULL");
   const size_t bytes = sizeof(double) * c->E * 5 * c->n3;
   cudaError_t e = cudaSuccess;
   const double* src = U;
   if (!on_device) {
-    e = cudaMemcpyAsync(c->Upub, U, bytes, cudaMemcpyHostToDevice, c->stream);
-    src = c->Upub;
+    const double* mapped = static_cast<const double*>(pinned_device_address(U));
+    if (mapped) {
+      src = mapped;
+    } else {
+      e = cudaMemcpyAsync(c->Upub, U, bytes, cudaMemcpyHostToDevice, c->stream);
+      src = c->Upub;
+    }
   }
   if (e == cudaSuccess) e = launch_to_internal(c, src, c->U);
   if (e == cudaSuccess) e = launch_refs(c);
@@ -719,8 +736,13 @@ int dg_get_state(dg_ctx* c, double* U, int on_device, double* t) {
   const size_t bytes = sizeof(double) * c->E * 5 * c->n3;
   cudaError_t e = cudaSuccess;
   if (U) {
-    e = launch_to_public(c, c->U, on_device ? U : c->Upub);
-    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(U, c->Upub, bytes, cudaMemcpyDeviceToHost, c->stream);
+    double* mapped = on_device ? nullptr : static_cast<double*>(pinned_device_address(U));
+    if (on_device || mapped) {
+      e = launch_to_public(c, c->U, on_device ? U : mapped);
+    } else {
+      e = launch_to_public(c, c->U, c->Upub);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(U, c->Upub, bytes, cudaMemcpyDeviceToHost, c->stream);
+    }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->scal_host, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

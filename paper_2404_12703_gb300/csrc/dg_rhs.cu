@@ -134,21 +134,32 @@ __global__ void k_dt(DevScalars* scal, double cfl, double dfl, int N, int viscou
 // ---------------------------------------------------------------------------
 // layout conversion and reductions
 // ---------------------------------------------------------------------------
-__global__ void k_to_internal(int64_t E, int n3, const double* __restrict__ pub, double* __restrict__ in) {
-  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (x >= E * n3 * 5) return;
-  const int64_t e = x / (5 * n3);
-  const int r = (int)(x % (5 * n3));
-  const int v = r / n3, t = r % n3;
-  in[x] = pub[(e * n3 + t) * 5 + v];
+// layout conversion, one element per block through shared memory, so that
+// both the reads and the writes are contiguous (the source may be pinned
+// host memory read over the host link)
+__global__ void __launch_bounds__(256) k_to_internal(int n3, const double* __restrict__ pub, double* __restrict__ in) {
+  extern __shared__ double sbuf[];  // [n3][5]
+  const int64_t e = blockIdx.x;
+  const double* src = pub + e * 5 * n3;
+  double* dst = in + e * 5 * n3;
+  for (int i = threadIdx.x; i < 5 * n3; i += blockDim.x) sbuf[i] = src[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < 5 * n3; i += blockDim.x) {
+    const int v = i / n3, t = i % n3;
+    dst[i] = sbuf[t * 5 + v];
+  }
 }
-__global__ void k_to_public(int64_t E, int n3, const double* __restrict__ in, double* __restrict__ pub) {
-  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (x >= E * n3 * 5) return;
-  const int64_t e = x / (5 * n3);
-  const int r = (int)(x % (5 * n3));
-  const int t = r / 5, v = r % 5;
-  pub[x] = in[e * 5 * n3 + (int64_t)v * n3 + t];
+__global__ void __launch_bounds__(256) k_to_public(int n3, const double* __restrict__ in, double* __restrict__ pub) {
+  extern __shared__ double sbuf[];  // [5][n3]
+  const int64_t e = blockIdx.x;
+  const double* src = in + e * 5 * n3;
+  double* dst = pub + e * 5 * n3;
+  for (int i = threadIdx.x; i < 5 * n3; i += blockDim.x) sbuf[i] = src[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < 5 * n3; i += blockDim.x) {
+    const int t = i / 5, v = i % 5;
+    dst[i] = sbuf[v * n3 + t];
+  }
 }
 
 template <int N>
@@ -355,14 +366,14 @@ cudaError_t launch_cfl(dg_ctx* c, bool report_only) {
 }
 
 cudaError_t launch_to_internal(dg_ctx* c, const double* pub, double* internal) {
-  const int64_t tot = c->E * c->n3 * 5;
-  k_to_internal<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->E, c->n3, pub, internal);
+  if (c->E == 0) return cudaSuccess;
+  k_to_internal<<<(unsigned)c->E, 256, sizeof(double) * 5 * c->n3, c->stream>>>(c->n3, pub, internal);
   count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_to_public(dg_ctx* c, const double* internal, double* pub) {
-  const int64_t tot = c->E * c->n3 * 5;
-  k_to_public<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->E, c->n3, internal, pub);
+  if (c->E == 0) return cudaSuccess;
+  k_to_public<<<(unsigned)c->E, 256, sizeof(double) * 5 * c->n3, c->stream>>>(c->n3, internal, pub);
   count_launch();
   return cudaGetLastError();
 }

@@ -264,3 +264,29 @@ def test_full_size_sampled_elements():
     err = rel_err(Ut[want], ref[want])
     assert np.all(err <= bound), (err, bound, floor)
     assert np.isfinite(Ut).all()
+
+
+def test_state_transfer_through_pinned_and_pageable_host_memory():
+    """dg_set_state / dg_get_state convert the layout straight from and into
+    pinned host buffers (no staging copy) and through a device staging copy
+    for pageable ones: both give the same state, bit for bit."""
+    torch, dg = gpu_or_skip()
+    N = 3
+    m = mesh(N, (3, 4, 3))
+    U = W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5), 1e-3, 9)
+    pinned_in = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+    pinned_out = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+    pinned_in.numpy()[...] = U
+    s = dg.Solver(m)
+    s.set_state(pinned_in.numpy(), t=0.5)
+    Up, t = s.get_state(pinned_out.numpy())
+    assert t == 0.5
+    np.testing.assert_array_equal(pinned_out.numpy(), U)
+    s.step(2, dt=1e-3)
+    A, _ = s.get_state(pinned_out.numpy())
+    B, _ = s.get_state()  # pageable
+    np.testing.assert_array_equal(A, B)
+    s2 = dg.Solver(m)
+    s2.set_state(U.copy(), t=0.5)  # pageable
+    s2.step(2, dt=1e-3)
+    np.testing.assert_array_equal(s2.get_state()[0], B)

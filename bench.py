@@ -561,6 +561,39 @@ def convergence_study(dg, torch, stream, degrees=(2, 3, 4, 5, 6, 7), T=0.2):
                         f"periodic meshes, to t = {T}, CFL 0.2 (N <= 4) or 0.1", **out}
 
 
+def tgv_validation(dg, torch, t_end=10.0, every=0.5, levels=(16, 24)):
+    """The Taylor-Green vortex of Sec. 5.2 (Re 1600, Ma 0.1, version II) on
+    curved, permuted meshes at N = 7, FP32-bulk, CFL steps to t_end: the
+    kinetic energy and its exact dissipation rate at every output time, and
+    the peak of -dE_k/dt.  (The paper compares with reference data that is
+    not part of this repository; the curves here are reported as computed.)"""
+    from paper_2404_12703_gb300 import workloads as W
+    out = {}
+    stream = torch.cuda.Stream()
+    for nel in levels:
+        m = W.box_mesh(N_DEG, (nel,) * 3, curved=0.1, seed=SEED)
+        s = dg.Solver(m, stream=stream, precision=dg.FP32_BULK)
+        s.set_state(W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5))
+        rows = []
+        k = s.kinetic()
+        rows.append({"t": 0.0, "E_k": k[0], "minus_dEk_dt": -k[1], "steps": 0})
+        steps = 0
+        t0 = time.perf_counter()
+        for i in range(1, int(round(t_end / every)) + 1):
+            t, ns = s.advance(i * every)
+            steps += ns
+            k = s.kinetic()
+            rows.append({"t": t, "E_k": k[0], "minus_dEk_dt": -k[1], "steps": steps})
+        wall = time.perf_counter() - t0
+        U, _ = s.get_state()
+        peak = max(rows, key=lambda r: r["minus_dEk_dt"])
+        out[f"{nel}^3"] = {"dof": m["E"] * (N_DEG + 1) ** 3, "wall_s": wall, "finite": bool(np.isfinite(U).all()),
+                           "peak_minus_dEk_dt": peak["minus_dEk_dt"], "peak_t": peak["t"], "history": rows}
+        s.close()
+    return {"workload": f"TGV Re 1600 Ma 0.1 (version II), curved permuted meshes, N = 7, FP32-bulk, to t = {t_end}",
+            **out}
+
+
 def run_long(args):
     """FP32-bulk against FP64 over a long Taylor-Green run: 32^3 Cartesian
     elements at N = 5 (7,077,888 DOF), Re 1600, Ma 0.1, both precisions from
@@ -868,9 +901,19 @@ def main():
     ap.add_argument("--long-every", type=float, default=0.25, help="output interval of --long-run")
     ap.add_argument("--gauss-only", action="store_true",
                     help="run only the Gauss-Legendre-node measurement (--nel, --steps) and print it")
+    ap.add_argument("--tgv-validation", type=float, default=0.0,
+                    help="run only the Taylor-Green validation (16^3 and 24^3, N = 7, FP32-bulk) to this time")
     ap.add_argument("--convergence", action="store_true",
                     help="run only the manufactured-solution convergence study of Sec. 5.1 and print it")
     args = ap.parse_args()
+    if args.tgv_validation > 0:
+        import torch
+        from paper_2404_12703_gb300 import build as B
+        from paper_2404_12703_gb300 import dg
+        B.build()
+        dg.load()
+        print(json.dumps(tgv_validation(dg, torch, t_end=args.tgv_validation)), flush=True)
+        return 0
     if args.convergence:
         import torch
         from paper_2404_12703_gb300 import build as B

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "dg_common.cuh"
 #include "dg_launch.h"
@@ -278,27 +279,54 @@ int ensure_arrays(dg_ctx* c, const dg_params* p, std::string& msg) {
   const int64_t E = c->cap_E, S = c->cap_S;
   const int64_t n3 = c->n3, n2 = c->n2;
   cudaStream_t st = c->pool_stream ? c->pool_stream : c->stream;
+  // one set of arrays, all or nothing: on any failure the set's arrays are
+  // freed again and its pointers stay null, so a later call starts afresh
+  struct Want {
+    void** slot;
+    size_t bytes;
+  };
+  auto take = [&](const std::vector<Want>& set) -> cudaError_t {
+    std::vector<void*> got;
+    cudaError_t e = cudaSuccess;
+    for (const Want& w : set) {
+      void* q = nullptr;
+      e = c->pool_stream ? pool_alloc(&q, w.bytes, c->pool_stream) : cudaMalloc(&q, w.bytes);
+      if (e != cudaSuccess) break;
+      got.push_back(q);
+    }
+    if (e != cudaSuccess) {
+      for (void* q : got) dfree(c, q);
+      return e;
+    }
+    size_t i = 0;
+    for (const Want& w : set) {
+      *w.slot = got[i++];
+      c->bytes += (int64_t)w.bytes;
+    }
+    return cudaSuccess;
+  };
   cudaError_t e = cudaSuccess;
-  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   if (p->precision == DG_FP64 && !c->g) {
-    A(dalloc(c, &c->g, E * 12 * n3));
-    A(dalloc(c, &c->lflux, S * 12 * n2));
-    A(dalloc(c, &c->fstar, S * 5 * n2));
-    if (c->gauss) A(dalloc(c, &c->gfc, S * 2 * 12 * n2));
+    std::vector<Want> set = {{(void**)&c->g, sizeof(double) * E * 12 * n3},
+                             {(void**)&c->lflux, sizeof(double) * S * 12 * n2},
+                             {(void**)&c->fstar, sizeof(double) * S * 5 * n2}};
+    if (c->gauss) set.push_back({(void**)&c->gfc, sizeof(double) * S * 2 * 12 * n2});
+    e = take(set);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->g, 0, sizeof(double) * E * 12 * n3, st);
   }
-  if (p->precision == DG_FP32_BULK && !c->g32) {
-    A(dalloc(c, &c->g32, E * 12 * n3));
-    A(dalloc(c, &c->metric32, E * 10 * n3));
-    A(dalloc(c, &c->lflux32, S * 12 * n2));
-    A(dalloc(c, &c->fstar32, S * 5 * n2));
-    A(dalloc(c, &c->nrm32, S * 7 * n2));
-    if (c->gauss) A(dalloc(c, &c->gfc32, S * 2 * 12 * n2));
+  if (e == cudaSuccess && p->precision == DG_FP32_BULK && !c->g32) {
+    std::vector<Want> set = {{(void**)&c->g32, sizeof(float) * E * 12 * n3},
+                             {(void**)&c->metric32, sizeof(float) * E * 10 * n3},
+                             {(void**)&c->lflux32, sizeof(float) * S * 12 * n2},
+                             {(void**)&c->fstar32, sizeof(float) * S * 5 * n2},
+                             {(void**)&c->nrm32, sizeof(float) * S * 7 * n2}};
+    if (c->gauss) set.push_back({(void**)&c->gfc32, sizeof(float) * S * 2 * 12 * n2});
+    e = take(set);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->g32, 0, sizeof(float) * E * 12 * n3, st);
     if (e == cudaSuccess) e = launch_fp32_geometry(c, st);
   }
-  if (p->shock_capturing && !c->fvmetric) {
-    A(dalloc(c, &c->fvmetric, E * 3 * (c->n - 1) * 3 * n2));
+  if (e == cudaSuccess && p->shock_capturing && !c->fvmetric) {
+    e = take({{(void**)&c->fvmetric, sizeof(double) * E * 3 * (c->n - 1) * 3 * n2}});  // one array
     if (e == cudaSuccess) e = launch_fv_metrics(c, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

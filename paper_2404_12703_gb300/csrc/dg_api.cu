@@ -966,7 +966,14 @@ int dg_set_sponge(dg_ctx* c, const double* sigma, const double* U_base) {
     e = cudaMemcpyAsync(c->Upub, U_base, sizeof(double) * nn * 5, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = launch_to_internal(c, c->Upub, c->sponge_base);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "dg_set_sponge");
+  if (e != cudaSuccess) {
+    // no half-set sponge: the kernels read the base state whenever sigma is set
+    cudaStreamSynchronize(c->stream);
+    dfree(c, c->sponge_sigma);
+    dfree(c, c->sponge_base);
+    c->sponge_sigma = c->sponge_base = nullptr;
+    return cuda_fail(e, "dg_set_sponge");
+  }
   return DG_OK;
 }
 

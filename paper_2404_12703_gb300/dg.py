@@ -266,11 +266,16 @@ class Solver:
         _check(self._lib.dg_set_stream(self._h, _stream_ptr(stream)))
 
     def set_params(self, params: Params | None = None, **kw):
+        """Replaces the parameters (a Params, or keyword changes to the current
+        ones); on an error the solver keeps its current parameters."""
         if params is None:
-            params = self.params
+            params = Params()
+            C.pointer(params)[0] = self.params  # a copy of the current parameters
             for k, v in kw.items():
                 if k == "riemann" and isinstance(v, str):
                     v = {"roe": ROE, "lf": LF}[v]
+                if k == "precision" and isinstance(v, str):
+                    v = {"fp64": FP64, "fp32": FP32_BULK}[v]
                 setattr(params, k, v)
         _check(self._lib.dg_set_params(self._h, C.byref(params)))
         self.params = params

@@ -209,6 +209,18 @@ int dg_step(dg_ctx* ctx, int n_steps, double dt);
    stop is this library's.) */
 int dg_advance(dg_ctx* ctx, double t_end, int64_t max_steps, double* t_out, int64_t* steps_out);
 
+/* The low-storage Runge-Kutta scheme of dg_step and dg_advance (Sec. 2.2:
+   GALAEXI offers several explicit low-storage schemes; its validation uses
+   the five-stage fourth-order scheme of Carpenter and Kennedy, the default
+   here, and its application a 14-stage one).  n_stages (1..32) stages of
+   the 2N-storage form dU <- A_s dU + dt R(U, t + c_s dt), U <- U + B_s dU;
+   A[0] must be 0 (the first stage starts the register), c gives the stage
+   times (used by the manufactured-solution source).  A = NULL restores the
+   default.  The CFL rule is unchanged: scale cfl and dfl to the scheme's
+   stability region.  DG_ERR_ARG for a bad size or non-finite coefficients.
+   Serving keeps the default scheme. */
+int dg_set_rk(dg_ctx* ctx, int n_stages, const double* A, const double* B, const double* c);
+
 /* Same work as dg_step, launched kernel by kernel (no graph) with CUDA events
    recorded on the context's stream around every launch.  Accumulates, per
    kernel kind k, the summed device time ms[k] and the launch count

@@ -78,12 +78,14 @@ def _lib(quad: bool = False):
             "rhs": fn("rhs", C.c_int, [C.c_void_p, dp, dp, C.c_double, dp, C.c_void_p, dp, dp, dp]),
             "mms_source": fn("mms_source", None, [dp, C.c_long, dp, C.c_double, dp]),
             "dt": fn("dt", C.c_double, [C.c_void_p, dp, dp, ip]),
-            "step": fn("step", C.c_int, [C.c_void_p, dp, dp, C.c_int, C.c_double, dp, dp]),
+            "step": fn("step", C.c_int, [C.c_void_p, dp, dp, C.c_int, C.c_double, dp, dp, C.c_int, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
             "kinetic": fn("kinetic", None, [C.c_void_p, dp, dp, dp]),
             "point_flux": fn("point_flux", None, [dp, C.c_int, dp, dp, dp, dp]),
             "point_visc": fn("point_visc", None, [dp, dp, dp, dp, dp]),
             "indicator": fn("indicator", C.c_double, [C.c_int, dp, dp, dp]),
-            "lserk_ode": fn("lserk_ode", C.c_double, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int]),
+            "lserk_ode": fn("lserk_ode", C.c_double, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                                                      C.c_void_p, C.c_void_p, C.c_void_p]),
             "rk_coeffs": fn("rk_coeffs", None, [dp, dp, dp]),
         }
         _LIBS[key] = api
@@ -169,9 +171,20 @@ def indicator(N, Uelem, prm=None):
     return a, float(Ev[0])
 
 
-def lserk_ode(kind: int, lam: float, y0: float, dt: float, n_steps: int) -> float:
-    """Integrate y' = lam y (kind 0) or y' = -y^2 + cos t (kind 1) with the LSERK scheme."""
-    return _lib()["lserk_ode"](kind, lam, y0, dt, n_steps)
+def _rk_args(rk):
+    """(ns, A, B, C pointers) of an optional 2N-storage scheme (A, B, C)."""
+    if rk is None:
+        return 0, None, None, None, None
+    A, B, Cc = (np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in rk)
+    keep = (A, B, Cc)
+    return len(A), A.ctypes.data, B.ctypes.data, Cc.ctypes.data, keep
+
+
+def lserk_ode(kind: int, lam: float, y0: float, dt: float, n_steps: int, rk=None) -> float:
+    """Integrate y' = lam y (kind 0) or y' = -y^2 + cos t (kind 1) with the
+    five-stage LSERK scheme, or the 2N-storage scheme rk = (A, B, c)."""
+    ns, a, b, c, keep = _rk_args(rk)
+    return _lib()["lserk_ode"](kind, lam, y0, dt, n_steps, ns, a, b, c)
 
 
 def rk_coeffs():
@@ -301,12 +314,15 @@ class Mesh:
         d = self._api["dt"](self._h, _dp(_f64(prm)), _dp(self._state(U)), C.byref(bad))
         return d, bool(bad.value)
 
-    def step(self, U, prm, n_steps, dt=0.0, t=0.0):
-        """Advance n_steps LSERK steps; returns (U, t, last dt)."""
+    def step(self, U, prm, n_steps, dt=0.0, t=0.0, rk=None):
+        """Advance n_steps LSERK steps (the five-stage scheme, or the 2N-storage
+        scheme rk = (A, B, c)); returns (U, t, last dt)."""
         U = self._state(U).copy()
         tt = np.array([t], dtype=np.float64)
         dl = np.zeros(1)
-        st = self._api["step"](self._h, _dp(_f64(prm)), _dp(U), int(n_steps), float(dt), _dp(tt), _dp(dl))
+        ns, a, b, c, keep = _rk_args(rk)
+        st = self._api["step"](self._h, _dp(_f64(prm)), _dp(U), int(n_steps), float(dt), _dp(tt), _dp(dl),
+                               ns, a, b, c)
         if st != 0:
             raise RuntimeError(f"oracle step failed ({st})")
         return U, float(tt[0]), float(dl[0])

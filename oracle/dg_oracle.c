@@ -1400,14 +1400,43 @@ static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0,
 typedef void (*rhs_fn)(void* ctx, const real* U, real t, real* Ut);
 
 /* one 2N-storage step: dU = A_s dU + dt R(U); U = U + B_s dU */
-static void lserk_step(real* U, real* dU, real* Ut, long len, real t, real dt, rhs_fn f, void* ctx) {
-  for (int s = 0; s < 5; ++s) {
-    f(ctx, U, t + (real)RK_C[s] * dt, Ut);
+/* a 2N-storage low-storage RK scheme (Sec. 2.2 names several): ns stages,
+   dU <- A_s dU + dt R(U, t + c_s dt), U <- U + B_s dU (A_1 is not used) */
+typedef struct {
+  int ns;
+  real A[32], B[32], C[32];
+} rk_t;
+
+static rk_t rk_default(void) {
+  rk_t r;
+  r.ns = 5;
+  for (int s = 0; s < 5; ++s) { r.A[s] = RK_A[s]; r.B[s] = RK_B[s]; r.C[s] = RK_C[s]; }
+  return r;
+}
+
+static void lserk_step_rk(const rk_t* rk, real* U, real* dU, real* Ut, long len, real t, real dt, rhs_fn f,
+                          void* ctx) {
+  for (int s = 0; s < rk->ns; ++s) {
+    f(ctx, U, t + rk->C[s] * dt, Ut);
     for (long x = 0; x < len; ++x) {
-      dU[x] = (s == 0 ? 0 : (real)RK_A[s] * dU[x]) + dt * Ut[x];
-      U[x] = U[x] + (real)RK_B[s] * dU[x];
+      dU[x] = (s == 0 ? 0 : rk->A[s] * dU[x]) + dt * Ut[x];
+      U[x] = U[x] + rk->B[s] * dU[x];
     }
   }
+}
+
+static void lserk_step(real* U, real* dU, real* Ut, long len, real t, real dt, rhs_fn f, void* ctx) {
+  const rk_t rk = rk_default();
+  lserk_step_rk(&rk, U, dU, Ut, len, t, dt, f, ctx);
+}
+
+/* a scheme from its coefficient arrays (NULL: the default five-stage one) */
+static rk_t rk_from(int ns, const double* A, const double* B, const double* C) {
+  if (!A || ns < 1 || ns > 32) return rk_default();
+  rk_t r;
+  r.ns = ns;
+  for (int s = 0; s < ns; ++s) { r.A[s] = A[s]; r.B[s] = B[s]; r.C[s] = C[s]; }
+  return r;
 }
 
 /* Time step (the paper gives no rule; reading):
@@ -1635,7 +1664,8 @@ double ORC(dt)(void* hv, const double* prm, const double* U, int* nonfinite) {
 
 /* n_steps LSERK steps; dt_fixed > 0 uses that step, else the CFL rule each step */
 int ORC(step)(void* hv, const double* prm, double* U, int n_steps, double dt_fixed, double* t_io,
-              double* dt_last) {
+              double* dt_last, int rk_ns, const double* rk_A, const double* rk_B, const double* rk_C) {
+  const rk_t rk = rk_from(rk_ns, rk_A, rk_B, rk_C);
   handle_t* h = (handle_t*)hv;
   mesh_t* M = &h->M;
   dgctx_t c = {h, read_params(prm), 0};
@@ -1649,7 +1679,7 @@ int ORC(step)(void* hv, const double* prm, double* U, int n_steps, double dt_fix
     int bad = 0;
     dt = dt_fixed > 0 ? (real)dt_fixed : time_step(M, &c.P, Ur, &bad);
     if (bad) { st = -5; break; }
-    lserk_step(Ur, dU, Ut, len, t, dt, dg_rhs_cb, &c);
+    lserk_step_rk(&rk, Ur, dU, Ut, len, t, dt, dg_rhs_cb, &c);
     if (c.status) { st = c.status; break; }
     t += dt;
   }
@@ -1748,11 +1778,13 @@ static void ode_cb(void* c, const real* y, real t, real* yt) {
   if (o->kind == 0) yt[0] = o->lam * y[0];
   else yt[0] = -y[0] * y[0] + (real)cos((double)t);
 }
-double ORC(lserk_ode)(int kind, double lam, double y0, double dt, int n_steps) {
+double ORC(lserk_ode)(int kind, double lam, double y0, double dt, int n_steps, int rk_ns, const double* rk_A,
+                      const double* rk_B, const double* rk_C) {
+  const rk_t rk = rk_from(rk_ns, rk_A, rk_B, rk_C);
   odectx_t c = {kind, (real)lam};
   real y = y0, dy = 0, yt = 0, t = 0;
   for (int s = 0; s < n_steps; ++s) {
-    lserk_step(&y, &dy, &yt, 1, t, (real)dt, ode_cb, &c);
+    lserk_step_rk(&rk, &y, &dy, &yt, 1, t, (real)dt, ode_cb, &c);
     t += dt;
   }
   return (double)y;

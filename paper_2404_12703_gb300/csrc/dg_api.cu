@@ -806,9 +806,11 @@ int dg_rhs(dg_ctx* c, const double* U_dev, double* Ut_dev) {
 
 static cudaError_t enqueue_step(dg_ctx* c) {
   cudaError_t e = launch_cfl(c, false);
-  for (int s = 0; s < 5 && e == cudaSuccess; ++s) {
-    c->stage_c = RKC[s];
-    e = launch_rhs(c, c->U, 1, RKA[s], RKB[s], s == 0);
+  const bool own = c->rk_ns > 0;
+  const int ns = own ? c->rk_ns : 5;
+  for (int s = 0; s < ns && e == cudaSuccess; ++s) {
+    c->stage_c = own ? c->rk_c[s] : RKC[s];
+    e = launch_rhs(c, c->U, 1, own ? c->rk_a[s] : RKA[s], own ? c->rk_b[s] : RKB[s], s == 0);
   }
   c->stage_c = 0.0;
   return e;
@@ -940,6 +942,28 @@ int dg_profile_step(dg_ctx* c, int n_steps, double dt, double* ms, int64_t* laun
   }
   delete p;
   if (e != cudaSuccess) return cuda_fail(e, "dg_profile_step");
+  return DG_OK;
+}
+
+int dg_set_rk(dg_ctx* c, int n_stages, const double* A, const double* B, const double* cc) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (!A) {
+    c->rk_ns = 0;
+    destroy_graph(c);
+    return DG_OK;
+  }
+  if (!B || !cc || n_stages < 1 || n_stages > 32) return fail(DG_ERR_ARG, "1..32 stages with A, B and c");
+  if (A[0] != 0.0) return fail(DG_ERR_ARG, "A[0] must be 0");
+  for (int s = 0; s < n_stages; ++s)
+    if (!std::isfinite(A[s]) || !std::isfinite(B[s]) || !std::isfinite(cc[s]))
+      return fail(DG_ERR_ARG, "non-finite coefficient");
+  for (int s = 0; s < n_stages; ++s) {
+    c->rk_a[s] = A[s];
+    c->rk_b[s] = B[s];
+    c->rk_c[s] = cc[s];
+  }
+  c->rk_ns = n_stages;
+  destroy_graph(c);  // the step graph holds the stages
   return DG_OK;
 }
 

@@ -178,6 +178,8 @@ struct dg_ctx {
   int64_t cap_E = 0, cap_S = 0;  // allocated element and side capacity (a pool's, or E and S)
   int gauss = 0;              // solution on Gauss-Legendre nodes (standard DGSEM)
   double stage_c = 0.0;       // RK c coefficient of the stage being enqueued (stage time)
+  int rk_ns = 0;              // low-storage RK scheme of dg_step (0: the default five-stage one)
+  double rk_a[32] = {}, rk_b[32] = {}, rk_c[32] = {};
   double* xyzs = nullptr;     // [E][n3][3] coordinates of the solution nodes
   double* Ufc = nullptr;      // GL: [S][2][5][n2] face values of the state
   double* gfc = nullptr;      // GL: [S][2][12][n2] face values of the lifted gradients

@@ -31,6 +31,7 @@ SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "d
 EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
            "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_autotune", "dg_set_config", "dg_get_config",
            "dg_set_sponge", "dg_node_coords", "dg_quadrature_weights", "dg_selftest_convert",
+           "dg_set_rk",
            "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
            "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
 
@@ -108,6 +109,7 @@ def load(path: str | None = None):
             "dg_node_coords": (C.c_int, [vp, vp, C.c_int]),
             "dg_quadrature_weights": (C.c_int, [vp, dp]),
             "dg_selftest_convert": (C.c_int, [vp, vp, vp, C.c_int64, vp]),
+            "dg_set_rk": (C.c_int, [vp, C.c_int, dp, dp, dp]),
             "dg_set_params": (C.c_int, [vp, C.POINTER(Params)]),
             "dg_set_state": (C.c_int, [vp, vp, C.c_int, C.c_double]),
             "dg_get_state": (C.c_int, [vp, vp, C.c_int, dp]),
@@ -327,6 +329,18 @@ class Solver:
         k = C.c_int64()
         _check(self._lib.dg_advance(self._h, float(t_end), int(max_steps), C.byref(t), C.byref(k)))
         return t.value, k.value
+
+    def set_rk(self, A=None, B=None, c=None):
+        """The 2N-storage low-storage RK scheme of step / advance (A[0] = 0);
+        no arguments restore the default five-stage scheme."""
+        if A is None:
+            _check(self._lib.dg_set_rk(self._h, 0, None, None, None))
+            return
+        A, B, c = (np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in (A, B, c))
+        assert A.size == B.size == c.size
+        dpt = C.POINTER(C.c_double)
+        _check(self._lib.dg_set_rk(self._h, A.size, A.ctypes.data_as(dpt), B.ctypes.data_as(dpt),
+                                   c.ctypes.data_as(dpt)))
 
     def set_sponge(self, sigma=None, U_base=None):
         """Sponge source -sigma (U - U_base): sigma [E, n^3] >= 0, U_base

@@ -290,3 +290,38 @@ def test_state_transfer_through_pinned_and_pageable_host_memory():
     s2.set_state(U.copy(), t=0.5)  # pageable
     s2.step(2, dt=1e-3)
     np.testing.assert_array_equal(s2.get_state()[0], B)
+
+
+def test_other_low_storage_schemes():
+    """dg_set_rk: the five-stage table passed explicitly reproduces the default
+    bit for bit; a three-stage scheme (Williamson's RK3) over ten CFL steps
+    matches the oracle with the same scheme; bad tables are refused."""
+    torch, dg = gpu_or_skip()
+    from test_oracle_dg import RK3_WILLIAMSON
+    N = 3
+    m = W.box_mesh(N, (4, 4, 4), curved=0.1, seed=3)
+    U0 = W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5)
+    a = _solver(dg, m)
+    a.set_state(U0)
+    a.step(3)
+    b = _solver(dg, m)
+    b.set_rk(*O.rk_coeffs())
+    b.set_state(U0)
+    b.step(3)
+    np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])
+    s = _solver(dg, m, cfl=0.5)
+    s.set_rk(*RK3_WILLIAMSON)
+    s.set_state(U0)
+    s.step(10)
+    U, t = s.get_state()
+    prm = oracle_params(s.params)
+    Uo, to, _ = O.Mesh(N, m["xyz"], m["period"]).step(U0, prm, 10, rk=RK3_WILLIAMSON)
+    assert abs(t - to) <= 1e-13 * to
+    assert np.abs(U - Uo).max() / np.abs(Uo).max() <= 1e-10
+    with pytest.raises(dg.DgError) as ex:  # A[0] must be 0
+        s.set_rk([0.1, -0.5], [0.5, 0.5], [0.0, 0.5])
+    assert ex.value.code == dg.DG_ERR_ARG
+    z = np.zeros(1)
+    with pytest.raises(dg.DgError) as ex:  # no stages
+        dg._check(dg.load().dg_set_rk(s._h, 0, O._dp(z), O._dp(z), O._dp(z)))
+    assert ex.value.code == dg.DG_ERR_ARG

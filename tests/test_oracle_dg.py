@@ -192,6 +192,34 @@ def test_lserk_order_and_stability_polynomial():
     assert abs(O.lserk_ode(0, 0, 1.0, 1.0, 1) - 1.0) < 1e-15
 
 
+# Williamson's three-stage, third-order 2N-storage scheme (J. Comput. Phys.
+# 35, 1980): A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15), c = (0, 1/3, 3/4)
+RK3_WILLIAMSON = ([0.0, -5.0 / 9.0, -153.0 / 128.0], [1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0], [0.0, 1.0 / 3.0, 0.75])
+
+
+def test_other_low_storage_schemes():
+    """The integrator takes any 2N-storage scheme (Sec. 2.2: GALAEXI offers
+    several; Sec. 5.3 uses a 14-stage one): the five-stage table passed
+    explicitly reproduces the built-in scheme bit for bit; a three-stage
+    scheme has the stability polynomial 1 + z + z^2/2 + z^3/6 and third order,
+    its abscissae exercised by a non-autonomous ODE."""
+    ck = O.rk_coeffs()
+    for kind, lam in ((0, -0.7), (1, 0.0)):
+        assert O.lserk_ode(kind, lam, 0.5, 0.1, 7, rk=ck) == O.lserk_ode(kind, lam, 0.5, 0.1, 7)
+    zs = np.linspace(-1.0, 1.0, 9)
+    R = np.array([O.lserk_ode(0, z, 1.0, 1.0, 1, rk=RK3_WILLIAMSON) for z in zs])
+    np.testing.assert_allclose(np.polynomial.polynomial.polyfit(zs, R, 4), [1, 1, 0.5, 1 / 6, 0], atol=1e-12)
+    ref = O.lserk_ode(1, 0, 0.5, 1.0 / 4096, 4096)
+    e1 = abs(O.lserk_ode(1, 0, 0.5, 1.0 / 32, 32, rk=RK3_WILLIAMSON) - ref)
+    e2 = abs(O.lserk_ode(1, 0, 0.5, 1.0 / 64, 64, rk=RK3_WILLIAMSON) - ref)
+    assert 2.7 < math.log2(e1 / e2) < 3.5, math.log2(e1 / e2)
+    # a wrong abscissa breaks the order on the non-autonomous ODE
+    bad = (RK3_WILLIAMSON[0], RK3_WILLIAMSON[1], [0.0, 0.5, 0.75])
+    b1 = abs(O.lserk_ode(1, 0, 0.5, 1.0 / 32, 32, rk=bad) - ref)
+    b2 = abs(O.lserk_ode(1, 0, 0.5, 1.0 / 64, 64, rk=bad) - ref)
+    assert math.log2(b1 / b2) < 2.5
+
+
 def test_time_step_closed_form():
     """Cartesian element of size h, uniform state: lambda_c = sum_d (|u_d| + c) 2/h."""
     N = 4

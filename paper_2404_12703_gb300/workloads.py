@@ -169,6 +169,83 @@ def box_mesh(N, nel, length=(2 * math.pi,) * 3, origin=(0.0, 0.0, 0.0),
     }
 
 
+def ogrid_mesh(N, m=3, k=2, nz=3, length=(1.0, 1.0, 1.0), inner=0.3, curved=0.0, seed=None):
+    """An unstructured hexahedral mesh, periodic in x, y and z: the unit square
+    split into five blocks (a centre square [a, 1 - a]^2 of m x m cells and
+    four trapezoids of m x k cells between it and the square's sides),
+    extruded in z over nz layers, scaled to ``length``.  The centre square's
+    corners are vertices of three quadrilaterals (edges of three hexahedra),
+    and the square's corner, identified periodically, of eight; the cells
+    are straight-sided (bilinear), LGL nodes of degree N.  ``curved``
+    displaces every node like ``box_mesh`` (sine products that vanish on the
+    box faces); with ``seed`` the element ids are shuffled.
+
+    Returns a dict with ``N``, ``E``, ``xyz`` (E, n, n, n, 3), ``corner_vid``
+    (E, 8) and ``period``."""
+    Lx, Ly, Lz = (float(v) for v in length)
+    a = float(inner)
+    n = N + 1
+    xi = lgl_points(N)
+    ref = (xi + 1.0) / 2.0
+    g = np.linspace(0.0, 1.0, m + 1)
+    rr = np.linspace(0.0, 1.0, k + 1)
+    quads = []
+
+    def block(P, ns, nr, us, vs):
+        for i in range(ns):
+            for j in range(nr):
+                quads.append((P(us[i], vs[j]), P(us[i + 1], vs[j]), P(us[i], vs[j + 1]), P(us[i + 1], vs[j + 1])))
+
+    w = 1.0 - 2.0 * a
+    block(lambda u, v: (a + w * u, a + w * v), m, m, g, g)                        # centre
+    block(lambda s, r: ((1 - r) * s + r * (a + w * s), r * a), m, k, g, rr)        # bottom
+    block(lambda s, r: ((1 - r) * s + r * (a + w * s), 1 - r * a), m, k, g, rr)    # top
+    block(lambda s, r: (r * a, (1 - r) * s + r * (a + w * s)), m, k, g, rr)        # left
+    block(lambda s, r: (1 - r * a, (1 - r) * s + r * (a + w * s)), m, k, g, rr)    # right
+    # counter-clockwise corners (positive Jacobian): swap the two local axes otherwise
+    fixed = []
+    for p00, p10, p01, p11 in quads:
+        cross = (p10[0] - p00[0]) * (p01[1] - p00[1]) - (p10[1] - p00[1]) * (p01[0] - p00[0])
+        fixed.append((p00, p10, p01, p11) if cross > 0 else (p00, p01, p10, p11))
+    Q = len(fixed)
+    E = Q * nz
+    hz = Lz / nz
+    vid2d = {}
+
+    def vid(p):
+        key = (round(p[0] % 1.0, 9) % 1.0, round(p[1] % 1.0, 9) % 1.0)
+        return vid2d.setdefault(key, len(vid2d))
+
+    X = np.empty((E, n, n, n, 3))
+    cvid = np.empty((E, 8), dtype=np.int64)
+    for q, (p00, p10, p01, p11) in enumerate(fixed):
+        c = np.array([p00, p10, p01, p11], dtype=np.float64)
+        ids = [vid(p) for p in (p00, p10, p01, p11)]
+        # bilinear map at the LGL nodes: x[j, i] for xi (i) and eta (j)
+        U, V = np.meshgrid(ref, ref, indexing="xy")
+        xy = ((1 - U) * (1 - V))[..., None] * c[0] + (U * (1 - V))[..., None] * c[1] \
+            + ((1 - U) * V)[..., None] * c[2] + (U * V)[..., None] * c[3]
+        for lz in range(nz):
+            e = q * nz + lz
+            X[e, :, :, :, 0] = Lx * xy[None, :, :, 0]
+            X[e, :, :, :, 1] = Ly * xy[None, :, :, 1]
+            X[e, :, :, :, 2] = (lz + ref)[:, None, None] * hz
+            for cc in range(8):
+                bi, bj, bk = cc & 1, (cc >> 1) & 1, (cc >> 2) & 1
+                cvid[e, cc] = ids[bi + 2 * bj] + len(fixed) * 4 * ((lz + bk) % nz)
+    if curved != 0.0:
+        h = min(Lx, Ly) * min(a / k, w / m, (1.0 - a) / max(m, k)) if k > 0 else min(Lx, Ly) / m
+        h = min(h, hz)
+        s = (np.sin(2 * math.pi * X[..., 0] / Lx) * np.sin(2 * math.pi * X[..., 1] / Ly)
+             * np.sin(2 * math.pi * X[..., 2] / Lz))
+        X = X + (curved * h * s)[..., None]
+    if seed is not None:
+        perm = np.random.Generator(np.random.PCG64(seed)).permutation(E)
+        X, cvid = X[perm], cvid[perm]
+    return {"N": N, "E": E, "xyz": np.ascontiguousarray(X), "corner_vid": np.ascontiguousarray(cvid),
+            "period": np.array([Lx, Ly, Lz])}
+
+
 BOX_SIDES = ("x-", "x+", "y-", "y+", "z-", "z+")
 
 

@@ -325,3 +325,31 @@ def test_other_low_storage_schemes():
     with pytest.raises(dg.DgError) as ex:  # no stages
         dg._check(dg.load().dg_set_rk(s._h, 0, O._dp(z), O._dp(z), O._dp(z)))
     assert ex.value.code == dg.DG_ERR_ARG
+
+
+@pytest.mark.parametrize("nodes", ["lgl", "gauss"])
+def test_unstructured_ogrid_mesh(nodes):
+    """The five-block O-grid mesh (edges with three, four and eight elements
+    around them): maps bit-exact against the oracle's coordinate matching,
+    the right-hand side within the parity bound, FP32-bulk within 2e-4."""
+    torch, dg = gpu_or_skip()
+    N = 4
+    m = W.ogrid_mesh(N, m=3, k=2, nz=3, length=(2 * np.pi,) * 3, curved=0.1, seed=5)
+    gauss = nodes == "gauss"
+    s = _solver(dg, m, nodes=nodes)
+    nbr, nodemap = s.debug("maps")
+    on, of, om, onode = O.Mesh(N, m["xyz"], m["period"]).connectivity()
+    np.testing.assert_array_equal(nbr[..., 0], on)
+    np.testing.assert_array_equal(nbr[..., 1], of)
+    np.testing.assert_array_equal(nbr[..., 2], om)
+    np.testing.assert_array_equal(nodemap, onode)
+    M = O.Mesh(N, m["xyz"], m["period"], gauss=gauss)
+    U = W.random_perturbation(W.tgv_state(M.nodes(), Ma=0.5).reshape(m["E"], -1, 5), 1e-3, 2)
+    Ut = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    prm = oracle_params(s.params)
+    ref = O.Mesh(N, m["xyz"], m["period"], quad=True, gauss=gauss).rhs(U, prm)
+    bound, floor = parity_bound(M.rhs(U, prm), ref)
+    err = rel_err(Ut, ref)
+    assert np.all(err <= bound), (err, bound, floor)
+    s32 = _solver(dg, m, nodes=nodes, precision=dg.FP32_BULK)
+    assert np.all(rel_err(s32.rhs(torch.from_numpy(U).cuda()).cpu().numpy(), ref) <= 2e-4)

@@ -150,3 +150,34 @@ def test_rejects_unmatched_mesh():
     m = W.box_mesh(2, (2, 2, 2))
     with pytest.raises(ValueError):
         O.Mesh(2, m["xyz"], np.array([0.0, 0.0, 0.0]))  # no periodicity -> open faces
+
+
+def test_unstructured_ogrid_mesh():
+    """The five-block O-grid mesh (centre square and four trapezoids, periodic
+    in x, y and z): every face pairs up, edges have three, four or eight
+    elements around them (not only the four of a box), and the operator keeps
+    free streams to round-off and conserves on it, with both node sets."""
+    from collections import Counter
+    N = 3
+    m = W.ogrid_mesh(N, m=3, k=2, nz=3, curved=0.1, seed=5)
+    cnt = Counter()
+    for cv in m["corner_vid"]:
+        for c in range(4):
+            cnt[tuple(sorted((cv[c], cv[c + 4])))] += 1
+    valences = set(cnt.values())
+    assert {3, 4, 8} <= valences, valences
+    for gauss in (False, True):
+        M = O.Mesh(N, m["xyz"], m["period"], gauss=gauss)
+        nbr_e, _, _, _ = M.connectivity()
+        assert (nbr_e >= 0).all()
+        U = W.uniform_state((m["E"], (N + 1) ** 3), rho=1.1, vel=(0.4, -0.3, 0.25), p=3.0)
+        Ut = M.rhs(U, O.params(mu=0.01))
+        _, J = M.metrics()
+        assert np.abs(Ut).max() < 1e-14 * 300.0 / J.min(), np.abs(Ut).max()
+        x, w, *_ = O.ops(N, gauss=gauss)
+        wq = np.einsum("i,j,k->kji", w, w, w).reshape(-1)[None, :, None] * J[..., None]
+        U2 = W.random_perturbation(W.tgv_state(M.nodes() * 2 * np.pi, Ma=0.3).reshape(m["E"], -1, 5), 1e-2, 3)
+        Ut2 = M.rhs(U2, O.params(mu=0.01))
+        tot = (wq * Ut2).sum(axis=(0, 1))
+        scale = (wq * np.abs(Ut2)).sum(axis=(0, 1))
+        assert np.all(np.abs(tot) <= 1e-13 * scale), tot / scale

@@ -194,6 +194,62 @@ def cpu_oracle_sample(steps, nel=6, seed=SEED):
     return dof, times
 
 
+def _oracle_replica(args):
+    """One process of the all-cores oracle measurement: builds its sample,
+    waits at the barrier, then steps it (returns the stepping time)."""
+    steps, nel, seed, barrier = args
+    import oracle as O
+    from paper_2404_12703_gb300 import workloads as W
+    m = W.box_mesh(N_DEG, (nel,) * 3, curved=0.1, seed=seed)
+    M = O.Mesh(N_DEG, m["xyz"], m["period"])
+    U = W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5)
+    prm = O.params()
+    barrier.wait()
+    t0 = time.perf_counter()
+    M.step(U, prm, steps)
+    return time.perf_counter() - t0
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_oracle_all_cores(steps=2, nel=4, seed=SEED):
+    """The oracle as it stands on every usable host core: one independent
+    replica of the sample per core (spawned processes, so nothing is forked
+    from a process that holds a CUDA context), all released together by a
+    barrier; aggregate DOF-updates/s over the slowest replica's time."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        barrier = man.Barrier(cores)
+        with ctx.Pool(cores) as pool:
+            times = pool.map(_oracle_replica, [(steps, nel, seed, barrier)] * cores, chunksize=1)
+    dof = nel ** 3 * (N_DEG + 1) ** 3
+    value = cores * dof * STAGES * steps / max(times)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"{cores} independent replicas (one process per core) of {nel}^3 elements of the same "
+                      f"curved N=7 TGV workload ({dof} DOF each), {steps} LSERK steps each, single-threaded "
+                      f"FP64 C per process; the oracle is not parallelised within a mesh"}
+
+
 SERVING_SIZES = (4, 8, 12, 16)
 SERVING_T_END = 0.02
 
@@ -851,9 +907,13 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         cdof, ctimes = cpu_oracle_sample(2, nel=4)
         cval = cdof * STAGES * len(ctimes) / sum(ctimes)
-        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"4^3 elements of the same curved N=7 TGV workload ({cdof} DOF), 2 LSERK steps, "
                          f"single-threaded FP64 C"}
+        try:
+            cpu["all_cores"] = cpu_oracle_all_cores()
+        except (OSError, RuntimeError) as ex:
+            cpu["all_cores"] = {"unavailable": f"{type(ex).__name__}: {ex}"}
 
     if rank == 0:
         clocks = clk.summary()

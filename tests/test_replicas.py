@@ -73,3 +73,23 @@ sys.exit(bench.run_reference(A()))
     p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_oracle_on_all_host_cores():
+    """The CPU baseline's all-cores figure: one spawned replica of the sample
+    per usable core, aggregate rate over the slowest replica, the CPU model
+    named."""
+    code = r"""
+import os, sys, json
+sys.path.insert(0, os.environ["ROOT"])
+import bench
+print(json.dumps(bench.cpu_oracle_all_cores(steps=1, nel=3)))
+"""
+    env = dict(os.environ, ROOT=ROOT)
+    p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr
+    import json
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    assert r["cores"] == len(os.sched_getaffinity(0))
+    assert r["value"] > 0 and r["kind"] == "oracle" and r["cpu_model"]
+    assert f"{r['cores']} independent replicas" in r["sample"]

@@ -204,7 +204,7 @@ def _oracle_replica(args):
     M = O.Mesh(N_DEG, m["xyz"], m["period"])
     U = W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5)
     prm = O.params()
-    barrier.wait()
+    barrier.wait(timeout=300)
     t0 = time.perf_counter()
     M.step(U, prm, steps)
     return time.perf_counter() - t0
@@ -241,7 +241,7 @@ def cpu_oracle_all_cores(steps=2, nel=4, seed=SEED):
     with ctx.Manager() as man:
         barrier = man.Barrier(cores)
         with ctx.Pool(cores) as pool:
-            times = pool.map(_oracle_replica, [(steps, nel, seed, barrier)] * cores, chunksize=1)
+            times = pool.map_async(_oracle_replica, [(steps, nel, seed, barrier)] * cores, chunksize=1).get(timeout=900)
     dof = nel ** 3 * (N_DEG + 1) ** 3
     value = cores * dof * STAGES * steps / max(times)
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
@@ -912,7 +912,7 @@ def run_ours(args):
                          f"single-threaded FP64 C"}
         try:
             cpu["all_cores"] = cpu_oracle_all_cores()
-        except (OSError, RuntimeError) as ex:
+        except Exception as ex:  # an auxiliary figure: its failure is reported, not fatal
             cpu["all_cores"] = {"unavailable": f"{type(ex).__name__}: {ex}"}
 
     if rank == 0:

@@ -18,8 +18,11 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "dg_oracle.c")
-_OUT = os.path.join(_HERE, "_build")
+# DG_ORACLE_SOURCE / DG_ORACLE_BUILD point the loader at another copy of the
+# source and build folder: the test that plants mistakes in a copy of the
+# oracle and checks that its pins catch each one uses them
+_SRC = os.environ.get("DG_ORACLE_SOURCE") or os.path.join(_HERE, "dg_oracle.c")
+_OUT = os.environ.get("DG_ORACLE_BUILD") or os.path.join(_HERE, "_build")
 _LOCK = threading.Lock()
 _LIBS = {}
 

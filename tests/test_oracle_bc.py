@@ -29,20 +29,22 @@ def _channel(N, nel=(3, 4, 3), seed=7, curved=0.0):
                       periodic=(True, False, True), seed=seed, curved=curved)
 
 
-@pytest.mark.parametrize("N", [2, 3, 5])
-def test_couette_between_isothermal_walls_is_a_discrete_steady_state(N):
+@pytest.mark.parametrize("N,Rg", [(2, R), (3, R), (5, R), (3, 2.5)])
+def test_couette_between_isothermal_walls_is_a_discrete_steady_state(N, Rg):
+    """With a gas constant other than 1 the wall temperatures are consistent
+    with the inner state only through T = p / (rho R)."""
     m = _channel(N)
     fb = W.box_face_bc(m, {"y-": 1, "y+": 2})
-    mu, Uw, Tw = 0.02, 0.7, 1.3
+    mu, Uw, Tw = 0.02, 0.7, 1.3 / Rg
     bcs = [(1, 0.0, 0.0, 0.0, Tw), (1, Uw, 0.0, 0.0, Tw)]
     M = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=bcs)
-    U = W.couette_state(m["xyz"], U_wall=Uw, T_wall=Tw, p=0.9, mu=mu).reshape(m["E"], -1, 5)
-    Ut = M.rhs(U, O.params(mu=mu))
+    U = W.couette_state(m["xyz"], U_wall=Uw, T_wall=Tw, p=0.9, mu=mu, R=Rg).reshape(m["E"], -1, 5)
+    Ut = M.rhs(U, O.params(mu=mu, R=Rg))
     # terms of size p / h ~ 3 and mu U / h^2 ~ 0.2 cancel to round-off
     assert np.abs(Ut).max() < 1e-12, np.abs(Ut).max(axis=(0, 1))
     # a wrong wall temperature is seen
-    bad = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(1, 0.0, 0.0, 0.0, Tw + 0.1), bcs[1]])
-    assert np.abs(bad.rhs(U, O.params(mu=mu))).max() > 1e-3
+    bad = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(1, 0.0, 0.0, 0.0, Tw + 0.1 / Rg), bcs[1]])
+    assert np.abs(bad.rhs(U, O.params(mu=mu, R=Rg))).max() > 1e-3
 
 
 def test_couette_with_an_adiabatic_moving_wall():

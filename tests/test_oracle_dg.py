@@ -289,6 +289,42 @@ def test_indicator_limits():
     assert abs(E - 1.0 / 33.0) < 1e-12
 
 
+@pytest.mark.parametrize("N", [3, 5, 7])
+def test_indicator_sigmoid_at_known_modal_energy(N):
+    """The indicator's map from the modal energy E to the blending factor, on
+    states whose E is known in closed form: rho p = 2 + b Ltilde_m(x) has the
+    3D modal coefficients c_000 = 4 sqrt(2) and c_m00 = 2 b, so the energy
+    fraction of mode m is 4 b^2 / (32 + 4 b^2).  With m = N it enters through
+    the top mode, with m = N - 1 through the second-highest one (Hennemann's
+    indicator takes the larger of the two).  The map is the reading of the
+    Hennemann indicator: threshold T(N) = 0.5 10^(-1.8 (N + 1)^(1/4)), sharpness
+    s = ln((1 - 1e-4) / 1e-4), alpha = 1 / (1 + exp(-s (E - T) / T)), set to 0
+    below alpha_min; alpha = 1/2 exactly at E = T."""
+    n = N + 1
+    x = W.lgl_points(N)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    T = 0.5 * 10.0 ** (-1.8 * (N + 1) ** 0.25)
+    s = math.log((1 - 1e-4) / 1e-4)
+    prm = O.params(shock=True, alpha_min=1e-3, alpha_max=1.0)
+    for m in (N, N - 1):
+        c = np.zeros(n)
+        c[m] = 1.0
+        Lm = np.polynomial.legendre.legval(X, c) * math.sqrt((2 * m + 1) / 2)
+        for target in (0.5 * T, 0.9 * T, T, 1.2 * T, 2.0 * T):
+            b = math.sqrt(8 * target / (1 - target))
+            U = W.prim_to_cons(np.ones_like(X), 0 * X, 0 * X, 0 * X, 2 + b * Lm)
+            a, E = O.indicator(N, np.transpose(U, (2, 1, 0, 3)).reshape(-1, 5), prm)
+            assert abs(E - target) < 1e-12 * target + 1e-15, (m, target, E)
+            want = 1 / (1 + math.exp(-s * (target - T) / T))
+            want = 0.0 if want < 1e-3 else want
+            assert abs(a - want) < 1e-9, (m, target, a, want)
+        # exactly at the threshold: one half
+        b = math.sqrt(8 * T / (1 - T))
+        U = W.prim_to_cons(np.ones_like(X), 0 * X, 0 * X, 0 * X, 2 + b * Lm)
+        a, _ = O.indicator(N, np.transpose(U, (2, 1, 0, 3)).reshape(-1, 5), prm)
+        assert abs(a - 0.5) < 1e-9
+
+
 def test_sod_tube_with_blending_converges_to_exact():
     """FV sub-cell blending with LF fluxes on the Sod tube (inviscid): the density
     approaches the exact Riemann solution as the mesh is refined, and the

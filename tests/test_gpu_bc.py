@@ -76,14 +76,14 @@ def test_rhs_parity(N, bcs, kw):
     assert np.all(err <= bound), (err, bound, floor)
 
 
-@pytest.mark.parametrize("N", [2, 3, 5])
-def test_couette_is_a_discrete_steady_state(N):
+@pytest.mark.parametrize("N,Rg", [(2, 1.0), (3, 1.0), (5, 1.0), (3, 2.5)])
+def test_couette_is_a_discrete_steady_state(N, Rg):
     torch, dg = gpu_or_skip()
-    mu, Uw, Tw = 0.02, 0.7, 1.3
+    mu, Uw, Tw = 0.02, 0.7, 1.3 / Rg
     m = _channel(N, curved=0.0)
     m["bcs"] = [(1, 0.0, 0.0, 0.0, Tw), (1, Uw, 0.0, 0.0, Tw)]
-    s = dg.Solver(m, mu=mu)
-    U = W.couette_state(m["xyz"], U_wall=Uw, T_wall=Tw, p=0.9, mu=mu).reshape(m["E"], -1, 5)
+    s = dg.Solver(m, mu=mu, R=Rg)
+    U = W.couette_state(m["xyz"], U_wall=Uw, T_wall=Tw, p=0.9, mu=mu, R=Rg).reshape(m["E"], -1, 5)
     Ut = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
     assert np.abs(Ut).max() < 1e-12, np.abs(Ut).max(axis=(0, 1))
     # and stays put over steps

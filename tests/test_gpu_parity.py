@@ -353,3 +353,36 @@ def test_unstructured_ogrid_mesh(nodes):
     assert np.all(err <= bound), (err, bound, floor)
     s32 = _solver(dg, m, nodes=nodes, precision=dg.FP32_BULK)
     assert np.all(rel_err(s32.rhs(torch.from_numpy(U).cuda()).cpu().numpy(), ref) <= 2e-4)
+
+
+@pytest.mark.parametrize("kw", [dict(R=2.5, gamma=1.3, Pr=0.7, mu=0.01),
+                                dict(R=287.0, gamma=1.4, Pr=0.71, mu=0.01, sutherland=1, T_ref=1.0 / 287.0),
+                                dict(R=2.5, gamma=1.3, viscous=0, riemann="lf")])
+def test_gas_constants_other_than_the_defaults(kw):
+    """A gas constant R != 1 (temperature T = p / (rho R), Sutherland's law
+    in T, the heat conductivity gamma R mu / ((gamma - 1) Pr)), another
+    gamma and Prandtl number: the right-hand side within the parity bound,
+    the CFL time step within 1e-14, ten steps within 1e-10, FP32-bulk within
+    2e-4."""
+    torch, dg = gpu_or_skip()
+    N = 4
+    m = mesh(N, (3, 3, 4))
+    s = _solver(dg, m, **kw)
+    U = W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.5, gamma=kw["gamma"], R=kw["R"]).reshape(m["E"], -1, 5),
+                              1e-3, 6)
+    Ut = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    prm = oracle_params(s.params)
+    ref = O.Mesh(N, m["xyz"], m["period"], quad=True).rhs(U, prm)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    bound, floor = parity_bound(M.rhs(U, prm), ref)
+    err = rel_err(Ut, ref)
+    assert np.all(err <= bound), (err, bound, floor)
+    s.set_state(U)
+    odt, _ = M.dt(U, prm)
+    assert abs(s.time_step() - odt) <= 1e-14 * odt
+    s.step(10)
+    U10, _ = s.get_state()
+    Uo, _, _ = M.step(U, prm, 10)
+    assert np.abs(U10 - Uo).max() / np.abs(Uo).max() <= 1e-10
+    s32 = _solver(dg, m, precision=dg.FP32_BULK, **kw)
+    assert np.all(rel_err(s32.rhs(torch.from_numpy(U).cuda()).cpu().numpy(), ref) <= 2e-4)

@@ -9,7 +9,10 @@ states), by states the discrete operator must hold exactly:
 * a uniform stream parallel to slip walls, and a uniform stream through
   prescribed-state boundaries equal to it, on curved rotated meshes;
 * mass (all walls) and total energy (walls at rest, adiabatic) are conserved
-  by the discrete operator in a wall-bounded box."""
+  by the discrete operator in a wall-bounded box;
+* closed forms of the boundary terms on affine elements: the residual of a
+  uniform state against another prescribed state, and the lifted gradients
+  at slip walls crossed by a normal velocity."""
 import numpy as np
 import pytest
 
@@ -79,6 +82,66 @@ def test_uniform_stream_along_slip_walls_and_through_prescribed_states(N):
     M2 = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(4, *U2[0, 0])])
     for prm in (O.params(mu=0.01), O.params(riemann="lf")):
         assert np.abs(M2.rhs(U2, prm)).max() < 1e-12 * 10
+
+
+def _euler_flux_y(U):
+    rho, mx, my, mz, E = U
+    v = my / rho
+    p = (GAM - 1) * (E - 0.5 * (mx * mx + my * my + mz * mz) / rho)
+    return np.array([my, mx * v, my * v + p, mz * v, (E + p) * v])
+
+
+@pytest.mark.parametrize("N,kind", [(3, "roe"), (4, "lf")])
+def test_boundary_residual_of_a_uniform_state_against_a_prescribed_state(N, kind):
+    """Uniform inner stream U_in, prescribed state U_ext != U_in at y = 0 and
+    U_in at y = 1, inviscid, affine elements.  Every volume term and inner
+    face cancels, so only the nodes on y = 0 move, by the weak form's surface
+    term: J Ut = -(s / w_0) (f*(U_in, U_ext; n) - F(U_in) . n), n = -y the
+    outward normal; on a box element of height h_y, s / J = 2 / h_y.  f* is
+    the point Riemann flux pinned by the hand-computed values."""
+    m = _channel(N)
+    shape = (m["E"], (N + 1) ** 3)
+    U = W.uniform_state(shape, rho=1.1, vel=(0.4, 0.3, -0.2), p=2.0)
+    Ue = W.uniform_state((1, 1), rho=1.3, vel=(0.1, 0.6, 0.25), p=2.4)[0, 0]
+    fb = W.box_face_bc(m, {"y-": 1, "y+": 2})
+    M = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(4, *Ue), (4, *U[0, 0])])
+    prm = O.params(viscous=False, riemann=kind)
+    Ut = M.rhs(U, prm)
+    w0 = O.ops(N)[1][0]
+    hy = 1.0 / 4
+    fs = O.point_flux(kind, U[0, 0], Ue, np.array([0.0, -1.0, 0.0]), prm)
+    want = -(2 / hy) / w0 * (fs + _euler_flux_y(U[0, 0]))
+    y = m["xyz"].reshape(m["E"], -1, 3)[..., 1]
+    on = np.abs(y) < 1e-12
+    assert on.sum() == 3 * 3 * (N + 1) ** 2
+    scale = np.abs(want).max()
+    assert np.abs(Ut[on] - want).max() < 1e-12 * scale, (Ut[on][:2], want)
+    assert np.abs(Ut[~on]).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_slip_wall_lifting_value_is_the_tangential_velocity(N):
+    """A uniform stream with a normal velocity v at slip walls y = 0 and y = 1:
+    the lifting value there is the tangential velocity, so the lifted
+    gradients of the constant field are zero except dv/dy at the wall nodes,
+    which is (q* - q) . n s / (J w_0) = +v 2 / (h_y w_0) at y = 0 and the
+    opposite at y = 1."""
+    m = _channel(N)
+    shape = (m["E"], (N + 1) ** 3)
+    v = 0.3
+    U = W.uniform_state(shape, rho=1.1, vel=(0.4, v, -0.2), p=2.0)
+    fb = W.box_face_bc(m, {"y-": 1, "y+": 1})
+    M = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(3,)])
+    _, g = M.rhs(U, O.params(mu=0.01), with_grad=True)
+    w0 = O.ops(N)[1][0]
+    want = v * 2 / (1.0 / 4) / w0
+    y = m["xyz"].reshape(m["E"], -1, 3)[..., 1]
+    lo, hi = np.abs(y) < 1e-12, np.abs(y - 1) < 1e-12
+    assert np.abs(g[lo][:, 1, 1] - want).max() < 1e-12 * want
+    assert np.abs(g[hi][:, 1, 1] + want).max() < 1e-12 * want
+    rest = g.copy()
+    rest[lo | hi, 1, 1] = 0
+    assert np.abs(rest).max() < 1e-12 * want
 
 
 def test_mass_and_energy_conserved_in_a_walled_box():

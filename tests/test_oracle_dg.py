@@ -259,6 +259,14 @@ def test_kinetic_energy_tgv_version1_and_rate():
     Ep, _, _ = M.kinetic(U + d * Ut)
     Em, _, _ = M.kinetic(U - d * Ut)
     assert abs(rate - (Ep - Em) / (2 * d)) < 1e-8 * max(1.0, abs(rate)) + 1e-7
+    # the rate along any direction V is the derivative of E_k along V (a
+    # direction with a density part, which the Taylor-Green Ut hardly has)
+    V = np.random.default_rng(5).normal(size=U.shape)
+    _, rv, _ = M.kinetic(U, V)
+    d = 1e-5
+    Ep, _, _ = M.kinetic(U + d * V)
+    Em, _, _ = M.kinetic(U - d * V)
+    assert abs(rv - (Ep - Em) / (2 * d)) < 1e-7 * abs(rv)
 
 
 def test_indicator_limits():

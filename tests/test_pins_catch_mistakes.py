@@ -100,6 +100,41 @@ MUTANTS = [
     ("stage update without the register", "U[x] = U[x] + rk->B[s] * dU[x];", "U[x] = U[x] + rk->B[s] * dt * Ut[x];", 0),
     ("CFL step without (N+1)^2", "real dt = P->cfl * 2 / (np1 * np1 * lc);", "real dt = P->cfl * 2 / (np1 * lc);", 0),
     ("CFL sound speed times |Ja|^2", "+ c * RSQRT(nj2);", "+ c * nj2;", 0),
+    ("viscous step factor fixed at 4/3", "real kv = (real)4 / 3 > P->gamma / P->Pr ? (real)4 / 3 : P->gamma / P->Pr;",
+     "real kv = (real)4 / 3;", 0),
+    ("viscous step with (N+1)^2", "real dv = P->dfl * 4 / (np1 * np1 * np1 * np1 * lv);",
+     "real dv = P->dfl * 4 / (np1 * np1 * lv);", 0),
+    ("second stage register index", "dU[x] = (s == 0 ? 0 : rk->A[s] * dU[x]) + dt * Ut[x];",
+     "dU[x] = (s == 0 ? 0 : rk->A[s - 1] * dU[x]) + dt * Ut[x];", 0),
+    # nodes, weights and the Lagrange basis
+    ("Legendre recurrence coefficient", "oreal p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;",
+     "oreal p2 = ((2 * k + 1) * x * p1 - (k - 1) * p0) / k;", 0),
+    ("LGL weights with N^2", "w[j] = 2 / ((oreal)N * (N + 1) * P * P);", "w[j] = 2 / ((oreal)N * N * P * P);", 0),
+    ("GL weights without 1 - x^2", "w[j] = 2 / ((1 - t * t) * dP * dP);", "w[j] = 2 / (dP * dP);", 0),
+    ("derivative matrix transposed", "D[i * n + j] = s;", "D[j * n + i] = s;", 0),
+    ("modal basis not normalised", "V[i * n + m] = sqrtl((oreal)(2 * m + 1) / 2) * P;", "V[i * n + m] = P;", 0),
+    # connectivity and the Gauss-node face terms
+    ("partner face node transposed", "M->nbr_node[ef * n2 + p + n * q] = found;",
+     "M->nbr_node[ef * n2 + q + n * p] = found;", 0),
+    ("GL face normal sign", "real sgn = (f % 2) ? 1 : -1;", "real sgn = (f % 2) ? -1 : 1;", 2),
+    ("GL face value weights", "for (int c = 0; c < ncomp; ++c) out[c] += L[a] * fld[(e * n3 + va) * ncomp + c];",
+     "for (int c = 0; c < ncomp; ++c) out[c] += fld[(e * n3 + va) * ncomp + c] / M->n;", 0),
+    ("GL metric Jacobian at the LGL nodes", "interp3(n, Ig, dx, tmp, 9);", "", 0),
+    ("GL lifting slave sign", "surf_spread(M, w->g, 12, e2, f2, a2 % n, a2 / n, fl, -1);",
+     "surf_spread(M, w->g, 12, e2, f2, a2 % n, a2 / n, fl, 1);", 0),
+    ("GL surface slave sign", "surf_spread(M, w->B, 5, e2, f2, a2 % n, a2 / n, fs, -1);",
+     "surf_spread(M, w->B, 5, e2, f2, a2 % n, a2 / n, fs, 1);", 0),
+    # boundary states
+    ("prescribed state ignored", "for (int k = 0; k < 5; ++k) Ue[k] = b[1 + k];", "for (int k = 0; k < 5; ++k) Ue[k] = U[k];", 0),
+    ("slip wall lifts the full velocity", "for (int c = 0; c < 3; ++c) qs[c] = q[1 + c] - un * nu[c];",
+     "for (int c = 0; c < 3; ++c) qs[c] = q[1 + c];", 0),
+    # physics details
+    ("Sutherland constant", "(th + (real)0.4042)", "(th + (real)1.4042)", 0),
+    ("MMS momentum source without pressure", "Q[k] = (3 - P->src_a) * c + g1 * (2 * rho - (real)1.5) * c;",
+     "Q[k] = (3 - P->src_a) * c;", 0),
+    # diagnostics
+    ("kinetic energy without 1/2", "ek += wq * r * v2 / 2;", "ek += wq * r * v2;", 0),
+    ("kinetic energy rate mass-term sign", "- v2 * ut[0] / 2", "+ v2 * ut[0] / 2", 0),
 ]
 
 

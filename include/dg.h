@@ -26,9 +26,9 @@
  *  - "Device pointer" means memory on the device the context was created on.
  *    Work is enqueued on the context's stream (see dg_init_mesh); calls that
  *    return data to the host synchronise that stream.
- *  - Only closed (e.g. triply periodic) meshes are supported: every face must
- *    have exactly one partner face with the same four distinct corner ids.
- *    A periodic direction therefore needs at least three elements: with two,
+ *  - Every face either has exactly one partner face with the same four
+ *    distinct corner ids or carries a boundary condition (dg_mesh_desc
+ *    face_bc).  A periodic direction needs at least three elements: with two,
  *    the faces across the other directions of both layers share all corner ids.
  */
 #ifndef DG_H
@@ -43,7 +43,7 @@ extern "C" {
 enum {
   DG_OK = 0,
   DG_ERR_ARG = -1,        /* invalid argument (null pointer, N out of range, ...) */
-  DG_ERR_MESH = -2,       /* mesh is not a closed, consistent hex mesh          */
+  DG_ERR_MESH = -2,       /* faces do not pair up (nor carry a condition)       */
   DG_ERR_OOM = -3,        /* device allocation failed                           */
   DG_ERR_CUDA = -4,       /* a CUDA runtime call failed                         */
   DG_ERR_NONFINITE = -5,  /* the time-step reduction met a NaN / Inf            */

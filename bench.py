@@ -293,6 +293,17 @@ SERVING_CAP_DOF = 16 ** 3 * 8 ** 3
 SERVING_PRIORITY_DOF = 3_000_000
 
 
+def fifo_latencies(arrivals, service):
+    """One server, first in first out (Lindley's recursion): case k starts at
+    max(its arrival, the previous case's end).  Returns each case's time to
+    solution (end - arrival) and the makespan (the last end)."""
+    free_at, lat = 0.0, []
+    for a, s in zip(arrivals, service):
+        free_at = max(float(a), free_at) + float(s)
+        lat.append(free_at - float(a))
+    return lat, free_at
+
+
 def serve_all(dg, cases, precision, arrivals, max_resident_dof=0, priority_dof=0):
     """Submits the cases at the given arrival times (s after the start) to one
     server; returns time-to-solution per case, makespan and server stats."""
@@ -339,12 +350,7 @@ def serving_bench(dg, n_cases, precision):
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(cases)))
     arrivals -= arrivals[0]
     # the one-by-one queue: same arrivals, FIFO, measured service times
-    free_at, seq_lat = 0.0, []
-    for a, sv_t in zip(arrivals, service):
-        start = max(a, free_at)
-        free_at = start + sv_t
-        seq_lat.append(free_at - a)
-    seq_makespan = free_at
+    seq_lat, seq_makespan = fifo_latencies(arrivals, service)
     lat, makespan, sstats = serve_all(dg, cases, precision, arrivals)
     lat_c, makespan_c, sstats_c = serve_all(dg, cases, precision, arrivals, SERVING_CAP_DOF)
     lat_p, makespan_p, sstats_p = serve_all(dg, cases, precision, arrivals, 0, SERVING_PRIORITY_DOF)

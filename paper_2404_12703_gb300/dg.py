@@ -172,9 +172,17 @@ def kinetic_noalloc(N, U, J, Ut=None, out=None, stream=None):
     J: CUDA float64 [E, n^3]; Ut: like U or None; out: CUDA float64 [3] or None
     (then a tensor is allocated here, by PyTorch, not by the library)."""
     import torch
+    if not 1 <= int(N) <= 7:
+        raise DgError(DG_ERR_ARG, "N must be in 1..7")
+    E = J.shape[0]
+    n3 = (int(N) + 1) ** 3
+    _device_buf(J, E * n3, "J")
+    _device_buf(U, E * n3 * 5, "U")
+    if Ut is not None:
+        _device_buf(Ut, E * n3 * 5, "Ut")
     if out is None:
         out = torch.empty(3, dtype=torch.float64, device=U.device)
-    E = J.shape[0]
+    _device_buf(out, 3, "out")
     _check(load().dg_kinetic_noalloc(int(N), int(E), C.c_void_p(U.data_ptr()), C.c_void_p(J.data_ptr()),
                                      C.c_void_p(Ut.data_ptr() if Ut is not None else 0),
                                      C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
@@ -185,6 +193,8 @@ def convert_check(x, stream=None):
     """The library's integer-pipe conversions applied to a CUDA float64 tensor:
     (binary32 values, those values back in binary64)."""
     import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64:
+        raise DgError(DG_ERR_ARG, "x: a CUDA float64 tensor is required")
     x = x.contiguous()
     out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
     back = torch.empty(x.shape, dtype=torch.float64, device=x.device)
@@ -202,6 +212,41 @@ def _stream_ptr(stream):
         import torch
         stream = torch.cuda.current_stream()
     return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _device_buf(t, numel, name, dtype="float64"):
+    """Checks a tensor handed to the C ABI as a raw device pointer: a CUDA
+    tensor of the given dtype, C-contiguous, with exactly numel values (the
+    library reads and writes that many).  Raises DgError (DG_ERR_ARG)
+    otherwise, like the library's own size checks."""
+    import torch
+    want = getattr(torch, dtype)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != want:
+        raise DgError(DG_ERR_ARG, f"{name}: a CUDA {dtype} tensor is required")
+    if not t.is_contiguous():
+        raise DgError(DG_ERR_ARG, f"{name}: the tensor must be contiguous")
+    if t.numel() != numel:
+        raise DgError(DG_ERR_ARG, f"{name}: {t.numel()} values, expected {numel}")
+    return t
+
+
+def _mesh_arrays(xyz, cvid, N):
+    """Checks the sizes of a mesh's node coordinates [E][(N+1)^3][3] and
+    corner ids [E][8] before the library reads them."""
+    E = int(xyz.shape[0]) if xyz.ndim else 0
+    if xyz.size != E * (N + 1) ** 3 * 3:
+        raise DgError(DG_ERR_ARG, f"xyz: {xyz.size} values, expected E (N+1)^3 3 = {E * (N + 1) ** 3 * 3}")
+    if cvid.size != E * 8:
+        raise DgError(DG_ERR_ARG, f"corner_vid: {cvid.size} values, expected 8 E = {8 * E}")
+
+
+def _host_buf(a, numel, name):
+    """Checks a host array handed to the C ABI: float64, C-contiguous, numel values."""
+    if a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise DgError(DG_ERR_ARG, f"{name}: a C-contiguous float64 array is required")
+    if a.size != numel:
+        raise DgError(DG_ERR_ARG, f"{name}: {a.size} values, expected {numel}")
+    return a
 
 
 class Solver:
@@ -222,6 +267,7 @@ class Solver:
         xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
         cvid = np.ascontiguousarray(mesh["corner_vid"], dtype=np.int64)
         self.E = int(xyz.shape[0])
+        _mesh_arrays(xyz, cvid, self.N)
         self.params = params if params is not None else default_params(**kw)
         fb, bc, nbc = _bc_arrays(mesh)
         self._bc_keep = (fb, bc)
@@ -285,14 +331,12 @@ class Solver:
     # -- state ----------------------------------------------------------------
     def set_state(self, U, t=0.0):
         """U: torch CUDA tensor or numpy array, float64, shape [E, n^3, 5] (any view)."""
+        size = self.E * self.n ** 3 * 5
         if isinstance(U, np.ndarray):
-            Uh = np.ascontiguousarray(U, dtype=np.float64)
-            assert Uh.size == self.E * self.n ** 3 * 5
+            Uh = _host_buf(np.ascontiguousarray(U, dtype=np.float64), size, "U")
             _check(self._lib.dg_set_state(self._h, C.c_void_p(Uh.ctypes.data), 0, float(t)))
         else:
-            import torch
-            assert U.is_cuda and U.dtype == torch.float64 and U.is_contiguous()
-            assert U.numel() == self.E * self.n ** 3 * 5
+            _device_buf(U, size, "U")
             _check(self._lib.dg_set_state(self._h, C.c_void_p(U.data_ptr()), 1, float(t)))
 
     def get_state(self, out=None):
@@ -300,11 +344,12 @@ class Solver:
         numpy array of E * n^3 * 5 float64 (e.g. backed by pinned memory), or
         None (a new numpy array)."""
         t = C.c_double()
+        size = self.E * self.n ** 3 * 5
         if out is None or isinstance(out, np.ndarray):
-            U = np.empty((self.E, self.n ** 3, 5)) if out is None else out
-            assert U.dtype == np.float64 and U.flags.c_contiguous and U.size == self.E * self.n ** 3 * 5
+            U = np.empty((self.E, self.n ** 3, 5)) if out is None else _host_buf(out, size, "out")
             _check(self._lib.dg_get_state(self._h, C.c_void_p(U.ctypes.data), 0, C.byref(t)))
             return U, t.value
+        _device_buf(out, size, "out")
         _check(self._lib.dg_get_state(self._h, C.c_void_p(out.data_ptr()), 1, C.byref(t)))
         return out, t.value
 
@@ -313,8 +358,12 @@ class Solver:
         """Ut = R(U) on the device.  U: CUDA float64 tensor [E, n^3, 5] or None
         (the solver's own state).  Returns a CUDA tensor."""
         import torch
+        size = self.E * self.n ** 3 * 5
+        if U is not None:
+            _device_buf(U, size, "U")
         if out is None:
             out = torch.empty((self.E, self.n ** 3, 5), dtype=torch.float64, device="cuda")
+        _device_buf(out, size, "out")
         up = C.c_void_p(U.data_ptr()) if U is not None else C.c_void_p(0)
         _check(self._lib.dg_rhs(self._h, up, C.c_void_p(out.data_ptr())))
         return out
@@ -336,8 +385,9 @@ class Solver:
         if A is None:
             _check(self._lib.dg_set_rk(self._h, 0, None, None, None))
             return
-        A, B, c = (np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in (A, B, c))
-        assert A.size == B.size == c.size
+        A, B, c = (np.ascontiguousarray(np.asarray(v, dtype=np.float64)).reshape(-1) for v in (A, B, c))
+        if not A.size == B.size == c.size:
+            raise DgError(DG_ERR_ARG, "A, B and c need one entry per stage each")
         dpt = C.POINTER(C.c_double)
         _check(self._lib.dg_set_rk(self._h, A.size, A.ctypes.data_as(dpt), B.ctypes.data_as(dpt),
                                    c.ctypes.data_as(dpt)))
@@ -348,9 +398,8 @@ class Solver:
         if sigma is None:
             _check(self._lib.dg_set_sponge(self._h, None, None))
             return
-        sg = np.ascontiguousarray(sigma, dtype=np.float64)
-        ub = np.ascontiguousarray(U_base, dtype=np.float64)
-        assert sg.size == self.E * self.n ** 3 and ub.size == 5 * sg.size
+        sg = _host_buf(np.ascontiguousarray(sigma, dtype=np.float64), self.E * self.n ** 3, "sigma")
+        ub = _host_buf(np.ascontiguousarray(U_base, dtype=np.float64), 5 * sg.size, "U_base")
         _check(self._lib.dg_set_sponge(self._h, C.c_void_p(sg.ctypes.data), C.c_void_p(ub.ctypes.data)))
 
     CONFIG_KEYS = ("lift_epb", "vol_epb", "vol_pairs", "side_block")
@@ -473,9 +522,9 @@ class Server:
             riemann = {"roe": ROE, "lf": LF}[riemann]
         xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
         cvid = np.ascontiguousarray(mesh["corner_vid"], dtype=np.int64)
-        U0 = np.ascontiguousarray(U0, dtype=np.float64)
         N, E = int(mesh["N"]), int(xyz.shape[0])
-        assert U0.size == E * (N + 1) ** 3 * 5
+        _mesh_arrays(xyz, cvid, N)
+        U0 = _host_buf(np.ascontiguousarray(U0, dtype=np.float64), E * (N + 1) ** 3 * 5, "U0")
         d = CaseDesc()
         fb, bc, nbc = _bc_arrays(mesh)
         d.mesh = MeshDesc(N, E, cvid.ctypes.data_as(C.POINTER(C.c_int64)), xyz.ctypes.data_as(C.POINTER(C.c_double)),

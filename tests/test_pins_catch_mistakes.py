@@ -180,8 +180,8 @@ def test_planted_text_is_unique_where_it_must_be():
 
 def test_every_planted_mistake_fails_a_pin():
     pytest.importorskip("numpy")
-    workers = min(len(MUTANTS), max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
-                                    else (os.cpu_count() or 1)))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    workers = max(1, min(len(MUTANTS), cores, 16))   # each worker is a pytest process of ~150 MB
     with tempfile.TemporaryDirectory() as tmp:
         with cf.ThreadPoolExecutor(workers) as ex:
             results = list(ex.map(lambda c: _run(c, tmp), MUTANTS))

@@ -624,6 +624,43 @@ def convergence_study(dg, torch, stream, degrees=(2, 3, 4, 5, 6, 7), T=0.2):
                         f"periodic meshes, to t = {T}, CFL 0.2 (N <= 4) or 0.1", **out}
 
 
+def eps_from_gradients(g, wq, mu_ratio, mu0):
+    """Sec. 5.2's solenoidal and dilatational dissipation rates, with rho_0 =
+    U_0 = L = 1 (Re = 1 / mu_0), from velocity gradients g[..., a, b] =
+    d u_a / d x_b at the nodes, the quadrature weights times J (wq) and the
+    viscosity ratio mu(T) / mu_0 at the nodes."""
+    d = np.asarray(g)[..., :3, :]
+    wx = d[..., 2, 1] - d[..., 1, 2]
+    wy = d[..., 0, 2] - d[..., 2, 0]
+    wz = d[..., 1, 0] - d[..., 0, 1]
+    div = d[..., 0, 0] + d[..., 1, 1] + d[..., 2, 2]
+    vol = wq.sum()
+    eps_s = mu0 * (wq * mu_ratio * (wx * wx + wy * wy + wz * wz)).sum() / vol
+    eps_d = 4.0 / 3.0 * mu0 * (wq * mu_ratio * div * div).sum() / vol
+    return float(eps_s), float(eps_d)
+
+
+def dissipation_rates(s, torch):
+    """eps_S and eps_D of a solver's current state from the library's BR1
+    lifted velocity gradients (one dg_rhs of the state, then the gradient
+    copy); the viscosity ratio follows Sutherland's law when it is on."""
+    torch.cuda.synchronize()
+    s.rhs()
+    g = s.debug("grad")
+    _, J = s.debug("metrics")
+    w = s.quadrature_weights()
+    wq = np.einsum("i,j,k->kji", w, w, w).reshape(-1)[None, :] * J
+    prm = s.params
+    ratio = np.ones_like(J)
+    if prm.sutherland:
+        U, _ = s.get_state()
+        rho = U[..., 0]
+        p = (prm.gamma - 1) * (U[..., 4] - 0.5 * (U[..., 1] ** 2 + U[..., 2] ** 2 + U[..., 3] ** 2) / rho)
+        th = p / (rho * prm.R) / prm.T_ref
+        ratio = 1.4042 * th ** 1.5 / (th + 0.4042)
+    return eps_from_gradients(g, wq, ratio, prm.mu)
+
+
 def tgv_validation(dg, torch, t_end=10.0, every=0.5, levels=(16, 24)):
     """The Taylor-Green vortex of Sec. 5.2 (Re 1600, Ma 0.1, version II) on
     curved, permuted meshes at N = 7, FP32-bulk, CFL steps to t_end: the
@@ -639,15 +676,19 @@ def tgv_validation(dg, torch, t_end=10.0, every=0.5, levels=(16, 24)):
         s.set_state(W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5))
         rows = []
         k = s.kinetic()
-        rows.append({"t": 0.0, "E_k": k[0], "minus_dEk_dt": -k[1], "steps": 0})
+        eps = dissipation_rates(s, torch)
+        rows.append({"t": 0.0, "E_k": k[0], "minus_dEk_dt": -k[1], "eps_S": eps[0], "eps_D": eps[1], "steps": 0})
         steps = 0
-        t0 = time.perf_counter()
+        wall = 0.0
         for i in range(1, int(round(t_end / every)) + 1):
+            t0 = time.perf_counter()
             t, ns = s.advance(i * every)
+            wall += time.perf_counter() - t0
             steps += ns
             k = s.kinetic()
-            rows.append({"t": t, "E_k": k[0], "minus_dEk_dt": -k[1], "steps": steps})
-        wall = time.perf_counter() - t0
+            eps = dissipation_rates(s, torch)
+            rows.append({"t": t, "E_k": k[0], "minus_dEk_dt": -k[1], "eps_S": eps[0], "eps_D": eps[1],
+                         "steps": steps})
         U, _ = s.get_state()
         peak = max(rows, key=lambda r: r["minus_dEk_dt"])
         out[f"{nel}^3"] = {"dof": m["E"] * (N_DEG + 1) ** 3, "wall_s": wall, "finite": bool(np.isfinite(U).all()),
@@ -696,9 +737,12 @@ def run_long(args):
             ms[name] += e0.elapsed_time(e1)
         t = k * every
         k64, k32 = s64.kinetic(), s32.kinetic()
+        e64, e32 = dissipation_rates(s64, torch), dissipation_rates(s32, torch)
         rows.append({"t": t, "ek_fp64": k64[0], "ek_fp32": k32[0], "rate_fp64": -k64[1], "rate_fp32": -k32[1],
                      "rate_rel_err": abs(k32[1] - k64[1]) / abs(k64[1]),
-                     "ek_rel_err": abs(k32[0] - k64[0]) / abs(k64[0])})
+                     "ek_rel_err": abs(k32[0] - k64[0]) / abs(k64[0]),
+                     "eps_S_fp64": e64[0], "eps_S_fp32": e32[0], "eps_S_rel_err": abs(e32[0] - e64[0]) / abs(e64[0]),
+                     "eps_D_fp64": e64[1], "eps_D_fp32": e32[1]})
         print(json.dumps({"progress": rows[-1]}), flush=True)
     U64, _ = s64.get_state()
     U32, _ = s32.get_state()
@@ -706,6 +750,7 @@ def run_long(args):
     line = {"workload": f"Taylor-Green vortex Re 1600 Ma 0.1, {nel}^3 Cartesian elements, N = {N} ({dof} DOF), "
                         f"FP32-bulk vs FP64 from the same state, fixed dt = {dt:.6g} ({steps} steps) to t = {t}",
             "rows": rows, "max_rate_rel_err": max(r["rate_rel_err"] for r in rows),
+            "max_eps_S_rel_err": max(r["eps_S_rel_err"] for r in rows),
             "l2_state_rel_err": float(np.sqrt(((U32 - U64) ** 2).sum() / (U64 ** 2).sum())),
             "finite": bool(np.isfinite(U32).all() and np.isfinite(U64).all()),
             "ms_per_step": {k: v / steps for k, v in ms.items()},

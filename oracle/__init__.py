@@ -84,6 +84,7 @@ def _lib(quad: bool = False):
             "step": fn("step", C.c_int, [C.c_void_p, dp, dp, C.c_int, C.c_double, dp, dp, C.c_int, C.c_void_p,
                                           C.c_void_p, C.c_void_p]),
             "kinetic": fn("kinetic", None, [C.c_void_p, dp, dp, dp]),
+            "dissipation": fn("dissipation", C.c_int, [C.c_void_p, dp, dp, dp]),
             "point_flux": fn("point_flux", None, [dp, C.c_int, dp, dp, dp, dp]),
             "point_visc": fn("point_visc", None, [dp, dp, dp, dp, dp]),
             "indicator": fn("indicator", C.c_double, [C.c_int, dp, dp, dp]),
@@ -329,6 +330,16 @@ class Mesh:
         if st != 0:
             raise RuntimeError(f"oracle step failed ({st})")
         return U, float(tt[0]), float(dl[0])
+
+    def dissipation(self, U, prm):
+        """(eps_S, eps_D): the solenoidal and dilatational dissipation rates of
+        Sec. 5.2 from the lifted velocity gradients (rho_0 = U_0 = L = 1,
+        Re = 1 / mu); viscous parameters only."""
+        out = np.zeros(2)
+        st = self._api["dissipation"](self._h, _dp(_f64(prm)), _dp(self._state(U)), _dp(out))
+        if st != 0:
+            raise RuntimeError(f"oracle dissipation failed ({st})")
+        return tuple(out)
 
     def kinetic(self, U, Ut=None):
         """(E_k, dE_k/dt, |Omega|)."""

@@ -1715,6 +1715,44 @@ void ORC(kinetic)(void* hv, const double* U, const double* Ut, double* out) {
   out[2] = (double)vol;
 }
 
+/* Solenoidal and dilatational dissipation rates of Sec. 5.2,
+     eps_S = 1 / (Re |Omega|) int (mu(T) / mu_0) omega . omega,
+     eps_D = 4 / (3 Re |Omega|) int (mu(T) / mu_0) (div u)^2,
+   with rho_0 = U_0 = L = 1, so Re = 1 / mu_0 (mu_0 the parameter mu); omega
+   and div u from the BR1 lifted velocity gradients of the state, integrated
+   by the quadrature of the node set.  out[0] = eps_S, out[1] = eps_D. */
+int ORC(dissipation)(void* hv, const double* prm, const double* U, double* out) {
+  handle_t* h = (handle_t*)hv;
+  mesh_t* M = &h->M;
+  params_t P = read_params(prm);
+  if (!P.viscous) return -1;
+  long len = M->E * M->n3 * 5;
+  real* Ur = conv_state(M, U);
+  real* Utr = (real*)calloc(len, sizeof(real));
+  real* g = (real*)calloc(M->E * M->n3 * 12, sizeof(real));
+  int st = rhs_any(M, &P, Ur, 0, Utr, NULL, NULL, g, NULL, &h->w);
+  int n = M->n;
+  real vol = 0, es = 0, ed = 0;
+  for (long e = 0; e < M->E && !st; ++e)
+    for (long v = 0; v < M->n3; ++v) {
+      int i = (int)(v % n), j = (int)((v / n) % n), k = (int)(v / ((long)n * n));
+      real wq = M->o.w[i] * M->o.w[j] * M->o.w[k] * M->J[e * M->n3 + v];
+      const real* d = &g[(e * M->n3 + v) * 12];   /* d[3 a + b] = d u_a / d x_b */
+      real q[6];
+      cons_to_prim(&P, &Ur[(e * M->n3 + v) * 5], q);
+      real r = viscosity(&P, q[5]) / P.mu;
+      real wx = d[7] - d[5], wy = d[2] - d[6], wz = d[3] - d[1];
+      real dv = d[0] + d[4] + d[8];
+      vol += wq;
+      es += wq * r * (wx * wx + wy * wy + wz * wz);
+      ed += wq * r * dv * dv;
+    }
+  out[0] = (double)(P.mu * es / vol);
+  out[1] = (double)(4 * P.mu * ed / (3 * vol));
+  free(Ur); free(Utr); free(g);
+  return st;
+}
+
 /* ---- point-wise hooks for the pin tests ---- */
 void ORC(point_flux)(const double* prm, int kind, const double* UL, const double* UR,
                      const double* nv, double* f) {

@@ -48,3 +48,25 @@ def test_serving_stream_is_seeded_and_in_range():
         assert x["t_end"] == bench.SERVING_T_END
         assert x["U0"].shape == (x["nel"] ** 3, (x["N"] + 1) ** 3, 5)
         assert (x["mu"] > 0) == (x["kind"] == "tgv")
+
+
+def test_dissipation_rates_from_gradients_match_the_oracle():
+    """The benchmark's eps_S / eps_D arithmetic (applied to the library's
+    lifted gradients on the GPU) against the oracle's, fed the oracle's own
+    gradients: equal to round-off, on a state with vorticity and dilatation."""
+    import oracle as O
+    from paper_2404_12703_gb300 import workloads as W
+    N, mu = 5, 0.01
+    m = W.box_mesh(N, (3, 3, 3), curved=0.1, seed=3)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    X = m["xyz"].reshape(m["E"], -1, 3)
+    ph = np.sin(X @ np.ones(3))
+    U = W.prim_to_cons(1 + 0.1 * ph, ph, 0.5 * np.cos(X[..., 0]), -0.3 * ph, np.full_like(ph, 5.0))
+    prm = O.params(mu=mu)
+    _, g = M.rhs(U, prm, with_grad=True)
+    _, J = M.metrics()
+    w = O.ops(N)[1]
+    wq = np.einsum("i,j,k->kji", w, w, w).reshape(-1)[None, :] * J
+    got = bench.eps_from_gradients(g, wq, np.ones_like(J), mu)
+    want = M.dissipation(U, prm)
+    assert abs(got[0] - want[0]) < 1e-13 * want[0] and abs(got[1] - want[1]) < 1e-13 * want[1], (got, want)

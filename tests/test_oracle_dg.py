@@ -333,6 +333,75 @@ def test_indicator_sigmoid_at_known_modal_energy(N):
         assert abs(a - 0.5) < 1e-9
 
 
+def test_dissipation_rates_of_the_taylor_green_vortex():
+    """Sec. 5.2's eps_S and eps_D at the Version I initial field, whose
+    velocity is divergence-free with vorticity (-cos x sin y sin z,
+    -sin x cos y sin z, 2 sin x sin y cos z): |omega|^2 averages to 3/4, so
+    eps_S = 0.75 mu exactly and eps_D = 0.  The discrete rates converge to
+    them spectrally, and -dE_k/dt from the right-hand side equals eps_S to
+    the same accuracy (incompressible limit, Ma = 0.1)."""
+    prm = O.params()
+    mu = 1.0 / 1600.0
+    errs, dil = [], []
+    for N in (3, 5, 7):
+        m = W.box_mesh(N, (4, 4, 4), curved=0.05, seed=4)
+        M = O.Mesh(N, m["xyz"], m["period"])
+        U = W.tgv_state(m["xyz"], version=1).reshape(m["E"], -1, 5)
+        eS, eD = M.dissipation(U, prm)
+        errs.append(abs(eS / (0.75 * mu) - 1))
+        dil.append(eD / (0.75 * mu))
+        _, rate, _ = M.kinetic(U, M.rhs(U, prm))
+        assert abs(-rate - eS) < 1e-3 * eS
+    assert errs[0] < 1e-4 and errs[1] < 1e-6 and errs[2] < 1e-9, errs
+    assert errs[0] > errs[1] > errs[2]
+    assert dil[0] < 1e-3 and dil[2] < 1e-10 and dil[0] > dil[1] > dil[2], dil
+
+
+def test_dissipation_rates_of_a_plane_wave():
+    """u = a sin(k . x) with k = (1, 1, 1) and a = (1, 0.5, -0.3) on the
+    2 pi-periodic box: omega = (k x a) cos(k . x) and div u = (k . a) cos(k . x),
+    so eps_S = mu |k x a|^2 / 2 and eps_D = (4/3) mu (k . a)^2 / 2 (density 1,
+    uniform pressure)."""
+    N, mu = 7, 0.01
+    m = W.box_mesh(N, (4, 4, 4), curved=0.05, seed=11)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    X = m["xyz"].reshape(m["E"], -1, 3)
+    k, a = np.ones(3), np.array([1.0, 0.5, -0.3])
+    ph = np.sin(X @ k)
+    U = W.prim_to_cons(np.ones_like(ph), a[0] * ph, a[1] * ph, a[2] * ph, np.full_like(ph, 5.0))
+    eS, eD = M.dissipation(U, O.params(mu=mu))
+    wantS = mu * np.dot(np.cross(k, a), np.cross(k, a)) / 2
+    wantD = 4 / 3 * mu * np.dot(k, a) ** 2 / 2
+    assert abs(eS - wantS) < 1e-7 * wantS, (eS, wantS)
+    assert abs(eD - wantD) < 1e-7 * wantD, (eD, wantD)
+
+
+def test_dissipation_rates_of_couette_flow():
+    """Couette flow between isothermal walls, u = U y / h: omega = (0, 0, -U/h)
+    and div u = 0, so eps_S = mu (U/h)^2 exactly (the lifted gradients of the
+    discrete steady state are exact) and eps_D = 0.  With Sutherland's law the
+    weight mu(T)/mu_0 makes eps_S = mu_0 (U/h)^2 times the mean of mu(T(y))/mu_0
+    across the channel, a smooth integral the quadrature resolves."""
+    from scipy.integrate import quad
+    N = 5
+    m = W.box_mesh(N, (3, 4, 3), length=(2.0, 1.0, 2.0), origin=(0.0, 0.0, 0.0),
+                   periodic=(True, False, True), seed=7)
+    fb = W.box_face_bc(m, {"y-": 1, "y+": 2})
+    mu, Uw, Tw = 0.02, 0.7, 1.3
+    M = O.Mesh(N, m["xyz"], m["period"], face_bc=fb, bcs=[(1, 0.0, 0.0, 0.0, Tw), (1, Uw, 0.0, 0.0, Tw)])
+    U = W.couette_state(m["xyz"], U_wall=Uw, T_wall=Tw, p=0.9, mu=mu).reshape(m["E"], -1, 5)
+    eS, eD = M.dissipation(U, O.params(mu=mu))
+    assert abs(eS - mu * Uw ** 2) < 1e-12 * mu * Uw ** 2, eS
+    assert eD < 1e-24
+    Tref = 0.9
+    lam = 1.4 * mu / (0.4 * 0.72)
+    T = lambda y: Tw + mu * Uw ** 2 * y * (1 - y) / (2 * lam)
+    suth = lambda y: 1.4042 * (T(y) / Tref) ** 1.5 / (T(y) / Tref + 0.4042)
+    want = mu * Uw ** 2 * quad(suth, 0.0, 1.0, epsabs=0, epsrel=1e-13)[0]
+    eS2, _ = M.dissipation(U, O.params(mu=mu, sutherland=True, T_ref=Tref))
+    assert abs(eS2 - want) < 1e-10 * want, (eS2, want)
+
+
 def test_sod_tube_with_blending_converges_to_exact():
     """FV sub-cell blending with LF fluxes on the Sod tube (inviscid): the density
     approaches the exact Riemann solution as the mesh is refined, and the

@@ -135,6 +135,11 @@ MUTANTS = [
     # diagnostics
     ("kinetic energy without 1/2", "ek += wq * r * v2 / 2;", "ek += wq * r * v2;", 0),
     ("kinetic energy rate mass-term sign", "- v2 * ut[0] / 2", "+ v2 * ut[0] / 2", 0),
+    ("vorticity component sign", "real wx = d[7] - d[5]", "real wx = d[7] + d[5]", 0),
+    ("vorticity from the wrong gradient", "wz = d[3] - d[1];", "wz = d[3] - d[2];", 0),
+    ("dilatational rate without 4/3", "out[1] = (double)(4 * P.mu * ed / (3 * vol));",
+     "out[1] = (double)(P.mu * ed / vol);", 0),
+    ("dissipation without the viscosity weight", "real r = viscosity(&P, q[5]) / P.mu;", "real r = 1;", 0),
 ]
 
 

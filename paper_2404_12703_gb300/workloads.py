@@ -66,7 +66,8 @@ assert len(ROTATIONS) == 24
 
 
 def box_mesh(N, nel, length=(2 * math.pi,) * 3, origin=(0.0, 0.0, 0.0),
-             curved=0.0, seed=None, rotate=None, permute=None, periodic=(True, True, True)):
+             curved=0.0, seed=None, rotate=None, permute=None, periodic=(True, True, True),
+             rotations=None):
     """Box of ``nel = (nx, ny, nz)`` hexahedra at degree ``N``, periodic in the
     directions ``periodic`` marks (all three by default); the other directions
     end in boundary faces (``period`` is 0 there, see ``box_face_bc``).
@@ -79,7 +80,8 @@ def box_mesh(N, nel, length=(2 * math.pi,) * 3, origin=(0.0, 0.0, 0.0),
     With ``seed`` given, every element's local frame is turned by one of the 24
     proper cube rotations and the element ids are shuffled, both drawn from
     ``numpy.random.Generator(PCG64(seed))``; ``rotate``/``permute`` override the
-    two choices separately.
+    two choices separately.  ``rotations`` (E,) sets every element's rotation
+    index (into ``ROTATIONS``) explicitly instead.
 
     Returns a dict with ``N``, ``E``, ``xyz`` (E, n, n, n, 3), ``corner_vid``
     (E, 8), ``period`` (3,), ``rot`` (E,) rotation index, ``canon`` (E,) the
@@ -101,7 +103,12 @@ def box_mesh(N, nel, length=(2 * math.pi,) * 3, origin=(0.0, 0.0, 0.0),
     do_rot = (seed is not None) if rotate is None else bool(rotate)
     do_perm = (seed is not None) if permute is None else bool(permute)
     rot = np.zeros(E, dtype=np.int64)
-    if do_rot:
+    if rotations is not None:
+        rot = np.asarray(rotations, dtype=np.int64).reshape(E)
+        if rot.min() < 0 or rot.max() > 23:
+            raise ValueError("rotation indices are 0..23")
+        do_rot = True
+    elif do_rot:
         r = rng if rng is not None else np.random.Generator(np.random.PCG64(0))
         rot = r.integers(0, 24, size=E)
     if do_perm:
@@ -396,3 +403,19 @@ def random_perturbation(U, scale, seed):
     """``U`` times ``1 + scale * r`` with ``r`` uniform in [-1, 1] from ``PCG64(seed)``."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return U * (1.0 + scale * rng.uniform(-1.0, 1.0, size=U.shape))
+
+
+def rotation_pair_meshes(N, curved=0.1):
+    """Meshes that put every ordered pair of the 24 cube rotations across a
+    face: 3^3 periodic boxes whose centre element (canonical index 13) is
+    turned by rotation a and its six face neighbours by 6 k .. 6 k + 5
+    (k = 0..3), for a = 0..23 (96 meshes).  The other elements take a fixed
+    spread of rotations.  Yields (a, neighbour rotations, mesh)."""
+    nbrs = (12, 14, 10, 16, 4, 22)
+    for a in range(24):
+        for k in range(4):
+            rot = (np.arange(27) * 7 + a) % 24
+            rot[13] = a
+            for j, e in enumerate(nbrs):
+                rot[e] = 6 * k + j
+            yield a, tuple(6 * k + j for j in range(6)), box_mesh(N, (3, 3, 3), curved=curved, rotations=rot)

@@ -386,3 +386,21 @@ def test_gas_constants_other_than_the_defaults(kw):
     assert np.abs(U10 - Uo).max() / np.abs(Uo).max() <= 1e-10
     s32 = _solver(dg, m, precision=dg.FP32_BULK, **kw)
     assert np.all(rel_err(s32.rhs(torch.from_numpy(U).cuda()).cpu().numpy(), ref) <= 2e-4)
+
+
+def test_maps_for_every_rotation_pair():
+    """All 24 x 24 ordered pairs of element rotations across a face (96 meshes
+    of 3^3 elements, the centre element against its six neighbours): the
+    device maps, built from corner ids, equal the oracle's coordinate
+    matching bit for bit."""
+    torch, dg = gpu_or_skip()
+    N = 2
+    for a, bs, m in W.rotation_pair_meshes(N):
+        s = _solver(dg, m)
+        nbr, nodes = s.debug("maps")
+        on, of, om, onode = O.Mesh(N, m["xyz"], m["period"]).connectivity()
+        np.testing.assert_array_equal(nbr[..., 0], on, err_msg=str((a, bs)))
+        np.testing.assert_array_equal(nbr[..., 1], of, err_msg=str((a, bs)))
+        np.testing.assert_array_equal(nbr[..., 2], om, err_msg=str((a, bs)))
+        np.testing.assert_array_equal(nodes, onode, err_msg=str((a, bs)))
+        s.close()

@@ -181,3 +181,44 @@ def test_unstructured_ogrid_mesh():
         tot = (wq * Ut2).sum(axis=(0, 1))
         scale = (wq * np.abs(Ut2)).sum(axis=(0, 1))
         assert np.all(np.abs(tot) <= 1e-13 * scale), tot / scale
+
+
+def test_every_rotation_pair_across_a_face():
+    """All 24 x 24 ordered pairs of element rotations meet across a face (the
+    centre element of a 3^3 box against its six neighbours, 96 meshes): the
+    coordinate matching pairs every face node with the node at the same
+    point, and the operator equals the unrotated one mapped back."""
+    N = 2
+    n = N + 1
+    base = W.box_mesh(N, (3, 3, 3), curved=0.1)
+    prm = O.params(mu=0.01)
+    Ub = W.tgv_state(base["xyz"], Ma=0.5).reshape(base["E"], -1, 5)
+    Ut_b = O.Mesh(N, base["xyz"], base["period"]).rhs(Ub, prm).reshape(base["E"], n, n, n, 5)
+    scale = np.abs(Ut_b).max(axis=(0, 1, 2, 3))
+    idx = np.arange(n)
+    I, Jj, K = np.meshgrid(idx, idx, idx, indexing="ij")
+    loc = np.stack([2 * I - N, 2 * Jj - N, 2 * K - N], axis=-1)
+    seen = set()
+    for a, bs, m in W.rotation_pair_meshes(N):
+        seen.update((a, b) for b in bs)
+        M = O.Mesh(N, m["xyz"], m["period"])
+        nbr_e, nbr_f, master, node = M.connectivity()
+        X = m["xyz"].reshape(m["E"], n, n, n, 3)
+        e = 13
+        for f in range(6):
+            e2, f2 = nbr_e[e, f], nbr_f[e, f]
+            fa, fb = face_nodes(n, f), face_nodes(n, f2)
+            for pq in range(n * n):
+                i, j, k = fa[pq]
+                i2, j2, k2 = fb[node[e, f, pq]]
+                d = X[e, k, j, i] - X[e2, k2, j2, i2]
+                d = d - m["period"] * np.round(d / m["period"])
+                assert np.abs(d).max() < 1e-10, (a, bs, f)
+        Ut = M.rhs(W.tgv_state(m["xyz"], Ma=0.5).reshape(m["E"], -1, 5), prm).reshape(m["E"], n, n, n, 5)
+        for el in (13, 12, 14, 10, 16, 4, 22):
+            R = W.ROTATIONS[m["rot"][el]]
+            can = (loc @ R.T + N) // 2
+            mapped = Ut_b[m["canon"][el]][can[..., 2], can[..., 1], can[..., 0]]
+            got = np.transpose(Ut[el], (2, 1, 0, 3))
+            assert np.all(np.abs(got - mapped).max(axis=(0, 1, 2)) <= 1e-12 * scale), (a, bs, el)
+    assert len(seen) == 24 * 24

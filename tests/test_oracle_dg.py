@@ -402,6 +402,34 @@ def test_dissipation_rates_of_couette_flow():
     assert abs(eS2 - want) < 1e-10 * want, (eS2, want)
 
 
+@pytest.mark.parametrize("N", [3, 5])
+def test_isentropic_vortex_converges_to_the_translated_vortex(N):
+    """The inviscid isentropic vortex (strength 5, mean flow (1, 1, 0)) is an
+    exact solution that translates with the mean flow.  After t = 0.1 on
+    curved, rotated meshes of 4 x 4 x 3 and 8 x 8 x 3 elements over the 10^3
+    box, the L2 density error against the translated vortex falls at more
+    than N - 1/2 (pre-asymptotic at these sizes; the design order is N + 1)."""
+    L, T = 10.0, 0.1
+
+    def err(nel):
+        m = W.box_mesh(N, (nel, nel, 3), length=(L, L, L), curved=0.05, seed=2)
+        M = O.Mesh(N, m["xyz"], m["period"])
+        U0 = W.isentropic_vortex_state(m["xyz"], center=(L / 2, L / 2), period=m["period"]).reshape(m["E"], -1, 5)
+        prm = O.params(viscous=False)
+        dt0, _ = M.dt(U0, prm)
+        n = int(np.ceil(T / dt0))
+        U, t, _ = M.step(U0, prm, n, dt=T / n)
+        Ue = W.isentropic_vortex_state(m["xyz"], center=(L / 2 + t, L / 2 + t),
+                                       period=m["period"]).reshape(m["E"], -1, 5)
+        _, J = M.metrics()
+        w = O.ops(N)[1]
+        wq = np.einsum("i,j,k->kji", w, w, w).reshape(-1)[None, :] * J
+        return math.sqrt((wq * (U[..., 0] - Ue[..., 0]) ** 2).sum() / wq.sum())
+
+    e4, e8 = err(4), err(8)
+    assert e4 < 1e-2 and math.log2(e4 / e8) > N - 0.5, (e4, e8)
+
+
 def test_sod_tube_with_blending_converges_to_exact():
     """FV sub-cell blending with LF fluxes on the Sod tube (inviscid): the density
     approaches the exact Riemann solution as the mesh is refined, and the

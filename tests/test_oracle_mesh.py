@@ -222,3 +222,45 @@ def test_every_rotation_pair_across_a_face():
             got = np.transpose(Ut[el], (2, 1, 0, 3))
             assert np.all(np.abs(got - mapped).max(axis=(0, 1, 2)) <= 1e-12 * scale), (a, bs, el)
     assert len(seen) == 24 * 24
+
+
+def _corner_xyz(m):
+    n = m["N"] + 1
+    X = m["xyz"].reshape(m["E"], n, n, n, 3)   # [e, k, j, i]
+    out = np.empty((m["E"], 8, 3))
+    for c in range(8):
+        i, j, k = (c & 1) * (n - 1), ((c >> 1) & 1) * (n - 1), ((c >> 2) & 1) * (n - 1)
+        out[:, c] = X[:, k, j, i]
+    return out
+
+
+@pytest.mark.parametrize("make", ["rotation_pairs", "random", "ogrid"])
+def test_corner_ids_agree_with_corner_coordinates(make):
+    """The corner ids the library pairs faces by name the same point wherever
+    they occur (up to the periodic shifts), and distinct ids distinct points:
+    the generated meshes (explicit rotations, random rotations and
+    renumbering, the O-grid) give the device and the oracle's coordinate
+    matching the same topology."""
+    if make == "rotation_pairs":
+        meshes = [m for _, _, m in W.rotation_pair_meshes(2)][::7]
+    elif make == "random":
+        meshes = [W.box_mesh(3, (3, 4, 5), curved=0.1, seed=s) for s in (1, 2, 3)]
+    else:
+        meshes = [W.ogrid_mesh(3, m=3, k=2, nz=3, curved=0.1, seed=5)]
+    for m in meshes:
+        P = np.asarray(m["period"], dtype=float)
+        C = _corner_xyz(m).reshape(-1, 3)
+        ids = m["corner_vid"].reshape(-1)
+        first = {}
+        for v, x in zip(ids, C):
+            if v in first:
+                d = x - first[v]
+                d = np.where(P > 0, d - P * np.round(d / np.where(P > 0, P, 1)), d)
+                assert np.abs(d).max() < 1e-9
+            else:
+                first[v] = x
+        pts = np.array(list(first.values()))
+        key = np.where(P > 0, np.mod(pts, np.where(P > 0, P, 1)), pts)
+        key = np.round(key * 1e6).astype(np.int64)
+        key = np.where(P > 0, np.mod(key, np.round(np.where(P > 0, P, 1) * 1e6).astype(np.int64)), key)
+        assert len({tuple(r) for r in key}) == len(first)

@@ -333,7 +333,8 @@ def test_indicator_sigmoid_at_known_modal_energy(N):
         assert abs(a - 0.5) < 1e-9
 
 
-def test_dissipation_rates_of_the_taylor_green_vortex():
+@pytest.mark.parametrize("gauss", [False, True])
+def test_dissipation_rates_of_the_taylor_green_vortex(gauss):
     """Sec. 5.2's eps_S and eps_D at the Version I initial field, whose
     velocity is divergence-free with vorticity (-cos x sin y sin z,
     -sin x cos y sin z, 2 sin x sin y cos z): |omega|^2 averages to 3/4, so
@@ -345,14 +346,14 @@ def test_dissipation_rates_of_the_taylor_green_vortex():
     errs, dil = [], []
     for N in (3, 5, 7):
         m = W.box_mesh(N, (4, 4, 4), curved=0.05, seed=4)
-        M = O.Mesh(N, m["xyz"], m["period"])
-        U = W.tgv_state(m["xyz"], version=1).reshape(m["E"], -1, 5)
+        M = O.Mesh(N, m["xyz"], m["period"], gauss=gauss)
+        U = W.tgv_state(M.nodes(), version=1).reshape(m["E"], -1, 5)
         eS, eD = M.dissipation(U, prm)
         errs.append(abs(eS / (0.75 * mu) - 1))
         dil.append(eD / (0.75 * mu))
         _, rate, _ = M.kinetic(U, M.rhs(U, prm))
         assert abs(-rate - eS) < 1e-3 * eS
-    assert errs[0] < 1e-4 and errs[1] < 1e-6 and errs[2] < 1e-9, errs
+    assert errs[0] < 2e-4 and errs[1] < 1e-6 and errs[2] < 1e-9, errs
     assert errs[0] > errs[1] > errs[2]
     assert dil[0] < 1e-3 and dil[2] < 1e-10 and dil[0] > dil[1] > dil[2], dil
 

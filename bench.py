@@ -556,7 +556,7 @@ def gauss_bench(dg, torch, stream, nel=NEL, steps=20):
                         f"on Gauss-Legendre nodes, {steps} CFL steps", **out}
 
 
-# Measured device memory per DOF of the paper's solver (Sec. 4.2, Tab.
+# Measured device memory per DOF of the paper's solver (Sec. 4.3, Tab.
 # memory_requirements), KiB, for N = 1..7
 PAPER_KIB_PER_DOF = {1: 1.457, 2: 1.188, 3: 1.049, 4: 0.996, 5: 0.942, 6: 0.895, 7: 0.869}
 
@@ -968,7 +968,7 @@ def run_ours(args):
 
     if rank == 0:
         clocks = clk.summary()
-        # energy per DOF and stage (Sec. 4.1: EPID = P_rank PID), from the median
+        # energy per DOF and stage (Sec. 4.2: EPID = P_rank PID), from the median
         # board power sampled during the timed region (no cooling share)
         pw = clocks.get("power_w")
         epid = {"power_w": pw, "j_per_dof_stage": (pw / (value / world) if pw else None),

@@ -119,7 +119,7 @@ typedef struct {
        DG_BC_OUTFLOW (p_out): as DG_BC_STATE with the outer state the inner
          density and velocity at the pressure p_out (subsonic outflow).
      The paper names wall and farfield conditions for its application
-     without stating them (Sec. 5.3); these are the library's.  Serving
+     without stating them (Sec. 6); these are the library's.  Serving
      (dg_submit) takes periodic meshes only. */
   const int* face_bc;
   int n_bc;
@@ -231,7 +231,7 @@ int dg_set_rk(dg_ctx* ctx, int n_stages, const double* A, const double* B, const
 int dg_profile_step(dg_ctx* ctx, int n_steps, double dt, double* ms, int64_t* launches);
 
 /* Sponge zone (the paper's application damps outgoing waves in sponge
-   zones, Sec. 5.3): adds the source -sigma (U - U_base) to Ut at every node,
+   zones, Sec. 6): adds the source -sigma (U - U_base) to Ut at every node,
    in FP64 in both precisions.  sigma: [E][node] host, >= 0; U_base:
    [E][node][5] host (public layout); sigma NULL removes the sponge.  The
    time-step rule does not see the source: keep sigma dt of order one or
@@ -239,7 +239,7 @@ int dg_profile_step(dg_ctx* ctx, int n_steps, double dt, double* ms, int64_t* la
 int dg_set_sponge(dg_ctx* ctx, const double* sigma, const double* U_base);
 
 /* Autotuner of the stage kernels' launch configuration (the paper plans
-   launch-configuration tuning, Sec. 3.2; this is the library's own).  Times
+   launch-configuration tuning, Sec. 3.3; this is the library's own).  Times
    every launch variant on the context's current state and keeps the fastest:
    elements per thread block of the lifting and volume kernels (the default,
    about 256 threads, or twice as many elements), the volume kernel's thread

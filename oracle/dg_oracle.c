@@ -27,7 +27,11 @@
  *     (Sec. 2.3, Eq. of the blended operator).
  *   - Carpenter-Kennedy five-stage 2N-storage RK4 (Sec. 2.2, Time integration)
  *     and a CFL time step (the paper gives no rule; see the reading in dg_dt).
- *   - kinetic energy E_k and its exact rate (Sec. 5.2).
+ *   - kinetic energy E_k and its exact rate, and the solenoidal and
+ *     dilatational dissipation rates eps_S, eps_D from the lifted velocity
+ *     gradients (Sec. 5.2).
+ *   - the manufactured-solution source of Sec. 5.1 (Eq. mms) and any
+ *     2N-storage low-storage RK scheme given by its coefficients.
  *   - boundary conditions (walls, prescribed state, pressure outflow), a sponge
  *     source, and Sutherland's law for mu(T) (Sec. 6 application, Sec. 2.1).
  *   - the standard (non-split) DGSEM on Gauss-Legendre nodes (Sec. 2.2,

@@ -199,7 +199,7 @@ RK3_WILLIAMSON = ([0.0, -5.0 / 9.0, -153.0 / 128.0], [1.0 / 3.0, 15.0 / 16.0, 8.
 
 def test_other_low_storage_schemes():
     """The integrator takes any 2N-storage scheme (Sec. 2.2: GALAEXI offers
-    several; Sec. 5.3 uses a 14-stage one): the five-stage table passed
+    several; Sec. 6 uses a 14-stage one): the five-stage table passed
     explicitly reproduces the built-in scheme bit for bit; a three-stage
     scheme has the stability polynomial 1 + z + z^2/2 + z^3/6 and third order,
     its abscissae exercised by a non-autonomous ODE."""

@@ -194,8 +194,12 @@ int dg_rhs(dg_ctx* ctx, const double* U_dev, double* Ut_dev);
 /* Advances the context's state by n_steps steps of the five-stage
    low-storage RK4 (Sec. 2.2, Time integration).  dt > 0: fixed step;
    dt <= 0: each step uses the CFL rule evaluated on the device from the
-   step's initial state.  Stream-ordered (asynchronous, graph-launched). */
-int dg_step(dg_ctx* ctx, int n_steps, double dt);
+   step's initial state.  t_out NULL: stream-ordered (asynchronous,
+   graph-launched); the time stays on the device (dg_get_state reads it).
+   t_out non-NULL: the call then synchronises the context's stream and
+   stores the time reached in *t_out, returning DG_ERR_NONFINITE if a step
+   since the last dg_set_state met a non-finite value. */
+int dg_step(dg_ctx* ctx, int n_steps, double dt, double* t_out);
 
 /* Advances the context's state with CFL time steps (as dg_step with dt <= 0)
    to exactly t_end: the device clips a step that would pass t_end to end on
@@ -370,19 +374,27 @@ void dg_server_destroy(dg_server* srv);
    implicit device synchronisation a cudaMalloc / cudaFree can cause.
    Inputs (device, caller-owned): U [E][node][5] (public layout), J [E][node]
    (Jacobians, e.g. from dg_debug DG_DEBUG_METRICS), Ut [E][node][5] or NULL.
+   nodes: the node set the state lives on, DG_NODES_LGL or DG_NODES_GAUSS
+   (the quadrature weights of E_k and |Omega| are those of that set, as in
+   dg_kinetic for a context of that set); anything else gives DG_ERR_ARG.
    Output (device, caller-owned, 3 doubles): out[0] = E_k, out[1] = dE_k/dt
    (0 when Ut is NULL), out[2] = |Omega|, with the definitions of dg_kinetic.
    N in [1, 7]; n_elems at most 262144 (its built-in scratch holds one partial
    sum triple per element), else DG_ERR_ARG.  Stream-ordered on `stream`; no
-   synchronisation.  The scratch is a single file-scope device array (6 MiB,
-   held by every GPU that loads the library until the process exits), shared
-   by all calls on a device: calls whose work overlaps on the GPU (for
-   example on two streams) race on it.  Each call overwrites every scratch
-   entry it reads, so nothing needs clearing.  The first call on a device
-   looks up the array's device address (cudaGetSymbolAddress) and caches it:
-   make that first call before any stream capture. */
-int dg_kinetic_noalloc(int N, int64_t n_elems, const double* U, const double* J, const double* Ut, double* out,
-                       void* stream);
+   synchronisation.  U, J, Ut, out and the stream must belong to the current
+   device: the scratch used is the current device's.  The scratch is a single
+   file-scope device array (6 MiB, held by every GPU that loads the library
+   until the process exits), shared by all calls on a device: calls whose
+   work overlaps on the GPU (for example on two streams) race on it.  Each
+   call overwrites every scratch entry it reads, so nothing needs clearing.
+   The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress) and caches it for the life of the process: make
+   that first call before any stream capture.  The cached address belongs to
+   the device's primary context; after cudaDeviceReset (or anything else that
+   destroys and recreates that context) it is stale, so do not call this
+   entry point again in that process. */
+int dg_kinetic_noalloc(int N, int nodes, int64_t n_elems, const double* U, const double* J, const double* Ut,
+                       double* out, void* stream);
 
 /* Verification access to intermediate arrays (device buffers, caller-owned).
    what = DG_DEBUG_METRICS: out0 = Ja [E][node][3][3] ((J a^d)_c at [d][c]),

@@ -200,9 +200,9 @@ static void build_ops(int N, int gauss, Ops& o) {
 
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
 
-void lgl_weights(int N, double* w) {
+void quadrature_weights(int N, int gauss, double* w) {
   Ops o;
-  build_ops(N, 0, o);
+  build_ops(N, gauss, o);
   for (int i = 0; i <= N; ++i) w[i] = o.w[i];
 }
 
@@ -847,17 +847,29 @@ static cudaError_t launch_steps(dg_ctx* c, int64_t n_steps) {
   return e;
 }
 
-int dg_step(dg_ctx* c, int n_steps, double dt) {
+int dg_step(dg_ctx* c, int n_steps, double dt, double* t_out) {
   if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
   if (!c->cap_stream) return fail(DG_ERR_STATE, "internal case context: no capture stream");
   if (n_steps < 0) return fail(DG_ERR_ARG, "n_steps < 0");
-  if (n_steps == 0) return DG_OK;
-  k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, dt > 0 ? dt : 0.0, 0, 0.0, 0);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_steps(c, n_steps);
+  cudaError_t e = cudaSuccess;
+  if (n_steps > 0) {
+    k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, dt > 0 ? dt : 0.0, 0, 0.0, 0);
+    count_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_steps(c, n_steps);
+  }
+  if (e == cudaSuccess && t_out) {
+    // the time reached, read back through the pinned mirror
+    e = cudaMemcpyAsync(c->scal_host, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "dg_step");
+  if (t_out) {
+    c->t_host = c->scal_host->t;
+    *t_out = c->t_host;
+    if (c->scal_host->nonfinite) return fail(DG_ERR_NONFINITE, "a time step met a non-finite value");
+  }
   return DG_OK;
 }
 

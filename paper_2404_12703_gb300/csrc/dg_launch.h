@@ -18,8 +18,9 @@ void prof_end(dg_ctx* c);
 // records the thread's last error message and returns code
 int set_error(int code, const std::string& msg);
 
-// LGL quadrature weights of degree N (n = N + 1 entries)
-void lgl_weights(int N, double* w);
+// quadrature weights of degree N (n = N + 1 entries) on the LGL nodes
+// (gauss = 0) or the Gauss-Legendre nodes (gauss = 1)
+void quadrature_weights(int N, int gauss, double* w);
 
 // allocation of the side arrays once the number of sides is known
 int alloc_side_arrays(dg_ctx* c, std::string& msg);

@@ -127,9 +127,11 @@ static cudaError_t scratch_address(double** out) {
 
 using namespace dg;
 
-extern "C" int dg_kinetic_noalloc(int N, int64_t n_elems, const double* U, const double* J, const double* Ut,
-                                  double* out, void* stream) {
+extern "C" int dg_kinetic_noalloc(int N, int nodes, int64_t n_elems, const double* U, const double* J,
+                                  const double* Ut, double* out, void* stream) {
   if (N < 1 || N > NMAX) return set_error(DG_ERR_ARG, "dg_kinetic_noalloc: N must be in [1, 7]");
+  if (nodes != DG_NODES_LGL && nodes != DG_NODES_GAUSS)
+    return set_error(DG_ERR_ARG, "dg_kinetic_noalloc: nodes must be DG_NODES_LGL or DG_NODES_GAUSS");
   if (n_elems < 1) return set_error(DG_ERR_ARG, "dg_kinetic_noalloc: n_elems must be positive");
   if (n_elems > KIN_NOALLOC_MAX_ELEMS)
     return set_error(DG_ERR_ARG, "dg_kinetic_noalloc: n_elems exceeds the maximum of 262144 elements "
@@ -141,7 +143,7 @@ extern "C" int dg_kinetic_noalloc(int N, int64_t n_elems, const double* U, const
     return set_error(DG_ERR_CUDA, std::string("dg_kinetic_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   QuadWeights qw;
   for (int i = 0; i < NPMAX; ++i) qw.w[i] = 0.0;
-  lgl_weights(N, qw.w);
+  quadrature_weights(N, nodes == DG_NODES_GAUSS ? 1 : 0, qw.w);  // the weights of the state's node set
   cudaStream_t st = (cudaStream_t)stream;
   switch (N) {
     case 1: k_kin_noalloc_elem<1><<<(unsigned)n_elems, KIN_THREADS, 0, st>>>(U, J, Ut, qw, part); break;

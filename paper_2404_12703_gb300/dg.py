@@ -114,7 +114,7 @@ def load(path: str | None = None):
             "dg_set_state": (C.c_int, [vp, vp, C.c_int, C.c_double]),
             "dg_get_state": (C.c_int, [vp, vp, C.c_int, dp]),
             "dg_rhs": (C.c_int, [vp, vp, vp]),
-            "dg_step": (C.c_int, [vp, C.c_int, C.c_double]),
+            "dg_step": (C.c_int, [vp, C.c_int, C.c_double, dp]),
             "dg_advance": (C.c_int, [vp, C.c_double, C.c_int64, dp, C.POINTER(C.c_int64)]),
             "dg_autotune": (C.c_int, [vp, C.POINTER(C.c_int), dp]),
             "dg_set_sponge": (C.c_int, [vp, vp, vp]),
@@ -130,7 +130,7 @@ def load(path: str | None = None):
             "dg_error_string": (C.c_char_p, [C.c_int]),
             "dg_last_error": (C.c_char_p, []),
             "dg_launch_count": (C.c_int64, []),
-            "dg_kinetic_noalloc": (C.c_int, [C.c_int, C.c_int64, vp, vp, vp, vp, vp]),
+            "dg_kinetic_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int64, vp, vp, vp, vp, vp]),
             "dg_server_default_config": (None, [C.POINTER(ServerConfig)]),
             "dg_server_create": (C.c_int, [C.POINTER(vp), C.POINTER(ServerConfig)]),
             "dg_submit": (C.c_int, [vp, C.POINTER(CaseDesc), C.POINTER(C.c_int64)]),
@@ -165,15 +165,19 @@ def default_params(**kw) -> Params:
     return p
 
 
-def kinetic_noalloc(N, U, J, Ut=None, out=None, stream=None):
+def kinetic_noalloc(N, U, J, Ut=None, out=None, stream=None, nodes=0):
     """E_k, dE_k/dt and |Omega| of a caller-owned device state without any device
     allocation inside the library (for callers that cannot allocate: see
     dg_kinetic_noalloc in include/dg.h).  U: CUDA float64 [E, n^3, 5];
     J: CUDA float64 [E, n^3]; Ut: like U or None; out: CUDA float64 [3] or None
-    (then a tensor is allocated here, by PyTorch, not by the library)."""
+    (then a tensor is allocated here, by PyTorch, not by the library); nodes:
+    NODES_LGL or NODES_GAUSS, the node set of the state.  Every buffer must sit
+    on the current CUDA device, whose scratch the library uses."""
     import torch
     if not 1 <= int(N) <= 7:
         raise DgError(DG_ERR_ARG, "N must be in 1..7")
+    if int(nodes) not in (NODES_LGL, NODES_GAUSS):
+        raise DgError(DG_ERR_ARG, "nodes must be NODES_LGL or NODES_GAUSS")
     E = J.shape[0]
     n3 = (int(N) + 1) ** 3
     _device_buf(J, E * n3, "J")
@@ -183,8 +187,12 @@ def kinetic_noalloc(N, U, J, Ut=None, out=None, stream=None):
     if out is None:
         out = torch.empty(3, dtype=torch.float64, device=U.device)
     _device_buf(out, 3, "out")
-    _check(load().dg_kinetic_noalloc(int(N), int(E), C.c_void_p(U.data_ptr()), C.c_void_p(J.data_ptr()),
-                                     C.c_void_p(Ut.data_ptr() if Ut is not None else 0),
+    cur = torch.cuda.current_device()
+    for name, t in (("U", U), ("J", J), ("Ut", Ut), ("out", out)):
+        if t is not None and t.device.index != cur:
+            raise DgError(DG_ERR_ARG, f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+    _check(load().dg_kinetic_noalloc(int(N), int(nodes), int(E), C.c_void_p(U.data_ptr()),
+                                     C.c_void_p(J.data_ptr()), C.c_void_p(Ut.data_ptr() if Ut is not None else 0),
                                      C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
 
@@ -368,8 +376,15 @@ class Solver:
         _check(self._lib.dg_rhs(self._h, up, C.c_void_p(out.data_ptr())))
         return out
 
-    def step(self, n_steps=1, dt=0.0):
-        _check(self._lib.dg_step(self._h, int(n_steps), float(dt)))
+    def step(self, n_steps=1, dt=0.0, sync=False):
+        """n_steps LSERK steps (dt <= 0: CFL steps).  Asynchronous and returns
+        None; with sync=True the call waits and returns the time reached."""
+        if not sync:
+            _check(self._lib.dg_step(self._h, int(n_steps), float(dt), None))
+            return None
+        t = C.c_double()
+        _check(self._lib.dg_step(self._h, int(n_steps), float(dt), C.byref(t)))
+        return t.value
 
     def advance(self, t_end, max_steps=1 << 62):
         """CFL steps to exactly t_end (the last one clipped on the device);

@@ -67,8 +67,23 @@ def test_state_errors():
     s.set_state(bad)
     s.step(1)
     assert _code(dg, s.get_state) == dg.DG_ERR_NONFINITE
+    s.set_state(bad)
+    assert _code(dg, s.step, 1, sync=True) == dg.DG_ERR_NONFINITE   # dg_step with t_out reports it too
     # a finite state clears the flag
     s.set_state(U)
     s.step(1)
     Ug, t = s.get_state()
     assert np.isfinite(Ug).all() and t > 0
+
+
+def test_step_reports_the_time_reached():
+    """dg_step with t_out synchronises and returns the time dg_get_state reads;
+    zero steps return the current time."""
+    torch, dg = gpu_or_skip()
+    m = W.box_mesh(3, (3, 3, 3))
+    s = dg.Solver(m)
+    s.set_state(W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5), t=0.25)
+    assert s.step(0, sync=True) == 0.25
+    t1 = s.step(3, sync=True)
+    assert t1 > 0.25 and s.get_state()[1] == t1
+    assert s.step(2, dt=1e-3, sync=True) == t1 + 1e-3 + 1e-3

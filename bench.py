@@ -48,15 +48,28 @@ BYTES_PER_DOF = 8 * (30 + 204 / (N_DEG + 1))
 # in profiles/k_volume_tgv12_N7_fp64.md (12^3 mesh; the traffic scales with
 # the DOF count).  Set to None whenever the kernel changes until re-measured.
 VOLUME_TRAFFIC_BYTES_PER_DOF = 332.02
-# FP32-bulk: algorithmic bytes per DOF of one volume-kernel launch (reads U 40,
-# FP32 metrics 40, FP32 lifted gradients 48, dU 40, surface fluxes ~8; writes
-# U 40, dU 40), and of a whole stage for the minimal two-phase method with the
-# RK register in FP64 and the face traces in FP32: 342 B at N = 7.
+# FP32-bulk, four-kernel stage: algorithmic bytes per DOF of one volume-kernel
+# launch (reads U 40, FP32 metrics 40, FP32 lifted gradients 48, dU 40, surface
+# fluxes ~8; writes U 40, dU 40)
 VOLUME32_BYTES_PER_DOF = 40 + 40 + 48 + 40 + 8 + 40 + 40
+# FP32-bulk, two-kernel stage (the default on periodic meshes), per DOF at
+# N = 7, with 6 / (N + 1) = 0.75 element face nodes and 0.375 side nodes per
+# DOF.  Element kernel: reads U 40, dU 40, FP32 metrics 40, q* 0.75 x 16,
+# side normals 0.75 x 12, f* 0.75 x 20; writes U 40, dU 40, face traces
+# 0.75 x 32 and partial viscous fluxes 0.75 x 16.  Side kernel, per side
+# node: reads two traces 64, two partial viscous fluxes 32, side geometry 28;
+# writes f* 20 and q* 16 (the edge and corner nodes' re-reads of neighbouring
+# traces are not counted).
+FACE_NODES_PER_DOF = 6 / (N_DEG + 1)
+FELEM32_BYTES_PER_DOF = 40 + 40 + 40 + FACE_NODES_PER_DOF * (16 + 12 + 20) + 40 + 40 + FACE_NODES_PER_DOF * (32 + 16)
+FFLUX32_BYTES_PER_DOF = FACE_NODES_PER_DOF / 2 * (64 + 32 + 28 + 20 + 16)
+# a whole stage of the minimal two-phase method with the RK register and the
+# metrics in FP64 and the face traces in FP32: 342 B at N = 7 (the budget the
+# whole-step HBM fraction is quoted against)
 BYTES32_PER_DOF = 342.0
-# DRAM bytes per DOF of one k_volume<7,1,float> launch (ncu, 12^3 mesh,
-# profiles/k_volume_tgv12_N7_fp32bulk.md); None whenever the kernel changes
-VOLUME32_TRAFFIC_BYTES_PER_DOF = 220.94
+# DRAM bytes per DOF of one launch of the FP32-bulk dominant kernel (ncu); None
+# whenever the kernel changes until re-measured
+VOLUME32_TRAFFIC_BYTES_PER_DOF = None
 # Standard DGSEM on Gauss-Legendre nodes, algorithmic flops per DOF and stage
 # (n = N + 1, FMA = 2 flops).  Lifting: D-hat line sums 72 n, metric products
 # 36, both faces of three lines 144, 1/J 12, ProlongToFace of the twelve
@@ -361,8 +374,10 @@ def serving_bench(dg, n_cases, precision):
         "workload": f"{len(cases)} cases (seeded PCG64(5)): n^3 meshes n in {{{','.join(map(str, SERVING_SIZES))}}}, "
                     f"N in {{3,5,7}}, "
                     f"half TGV (Re 1600, Ma 0.1), half isentropic vortex (inviscid), each to t = {SERVING_T_END}; "
-                    f"Poisson arrivals at 0.9 x the one-by-one service rate ({rate:.2f}/s); shortened from "
-                    f"the 200-case, t = 1 configuration",
+                    f"Poisson arrivals at 0.9 x the one-by-one service rate ({rate:.2f}/s); "
+                    + ("the 200 cases of the serving configuration, " if len(cases) == 200 else
+                       f"the first {len(cases)} of the serving configuration's 200 cases, ")
+                    + "each run to t = 0.02 instead of t = 1 (shortened)",
         "precision": "FP64" if precision == dg.FP64 else "FP32-bulk",
         "p50_s": p(lat, 50), "p99_s": p(lat, 99),
         "dof_updates_per_s": sstats["dof_stage_updates"] / makespan, "makespan_s": makespan,
@@ -857,6 +872,19 @@ def run_ours(args):
                         "achieved_gbs": BYTES_PER_DOF * dof * STAGES / (ms_step * 1e-3) / 1e9,
                         "peak_gbs": peaks.get("hbm_gbs"), "peak_source": peak_src}}
     roofline["hbm"]["frac"] = roofline["hbm"]["achieved_gbs"] / roofline["hbm"]["peak_gbs"]
+    # the FP64 rates this GPU reaches in the library's own probes (dg_peak_probe):
+    # independent FMA chains, DMMA (mma.sync m8n8k4) chains, and both from the
+    # same warps; FP32 FMA for the FP32-bulk path's ALU ceiling
+    with Clocks(local) as pclk:
+        probe = {name: dg.peak_probe(kind, iters)[0] / 1e12
+                 for name, kind, iters in (("fp64_fma", dg.PEAK_FP64_FMA, 16384),
+                                           ("fp64_mma", dg.PEAK_FP64_MMA, 4096),
+                                           ("fp64_fma_and_mma", dg.PEAK_FP64_BOTH, 4096),
+                                           ("fp32_fma", dg.PEAK_FP32_FMA, 131072))}
+    probe["clocks"] = pclk.summary()
+    probe["unit"] = "TFLOP/s"
+    roofline["probe"] = probe
+    roofline["frac_of_probe"] = achieved_tf / probe["fp64_fma"]
     total_flops = sum(FLOPS_PER_DOF.values()) * dof * STAGES
     roofline["whole_step_fp64_frac"] = total_flops / (ms_step * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
 
@@ -903,6 +931,28 @@ def run_ours(args):
         k32 = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1],
                    "share": (v[0] / tot32 if tot32 else None)} for k, v in prof32.items()}
         vol32 = k32["volume"]["ms_per_launch"]
+        form32 = s32.stage_form()
+        if form32 == 2:
+            kname = "k_felem<7,1> (two-kernel FP32-bulk stage: lifting, KEP volume, viscous volume, SurfInt, " \
+                    "ApplyJac, RK update, next stage's face data)"
+            vbytes = FELEM32_BYTES_PER_DOF
+            k32["surf_flux"]["algorithmic_bytes_per_dof"] = FFLUX32_BYTES_PER_DOF
+            sf = k32["surf_flux"]["ms_per_launch"]
+            k32["surf_flux"]["hbm_frac"] = FFLUX32_BYTES_PER_DOF * dof / (sf * 1e-3) / 1e9 / peaks.get("hbm_gbs")
+        else:
+            kname, vbytes = "k_volume<7,1,float>", VOLUME32_BYTES_PER_DOF
+        k32["volume"]["algorithmic_bytes_per_dof"] = vbytes
+        # the four-kernel stage on the same workload, for comparison
+        s32.set_config(**dict(s32.config(), stage_form=1))
+        s32.set_state(U0)
+        s32.step(args.warmup)
+        barrier()
+        e0.record(stream)
+        s32.step(args.steps)
+        e1.record(stream)
+        barrier()
+        ms32_four = e0.elapsed_time(e1) / args.steps
+        s32.set_config(**dict(s32.config(), stage_form=0))
         # accuracy against the FP64 path: same initial state, same fixed dt,
         # `steps` steps each; kinetic-energy dissipation rate and L2 state error
         solver.set_state(U0)
@@ -919,14 +969,16 @@ def run_ours(args):
             "speedup_vs_fp64": ms_step / ms32, "dtype": "f32 arithmetic, f64 state/RK/metrics/reductions",
             "autotune": {"config": tune32[0], "variant_ms": tune32[1]},
             "kernels": k32,
-            "roofline": {"bound": "hbm", "kernel": "k_volume<7,1,float>",
-                         "achieved": VOLUME32_BYTES_PER_DOF * dof / (vol32 * 1e-3) / 1e9,
+            "stage_form": form32,
+            "four_kernel_stage_ms_per_step": ms32_four,
+            "roofline": {"bound": "hbm", "kernel": kname,
+                         "achieved": vbytes * dof / (vol32 * 1e-3) / 1e9,
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                         "frac": VOLUME32_BYTES_PER_DOF * dof / (vol32 * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+                         "frac": vbytes * dof / (vol32 * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
                          "traffic": (VOLUME32_TRAFFIC_BYTES_PER_DOF * dof if VOLUME32_TRAFFIC_BYTES_PER_DOF
                                      else None),
                          "peak_source": peak_src,
-                         "algorithmic_bytes_per_dof": VOLUME32_BYTES_PER_DOF},
+                         "algorithmic_bytes_per_dof": vbytes},
             "whole_step_hbm_frac": BYTES32_PER_DOF * dof * STAGES / (ms32 * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
             "accuracy_vs_fp64": {
                 "steps": args.steps, "dt": dt_fix,
@@ -952,19 +1004,21 @@ def run_ours(args):
     if not args.no_serving and rank == 0:
         serving = {"fp64": serving_bench(dg, args.serving_cases, dg.FP64)}
         if not args.no_fp32:
-            serving["fp32_bulk"] = serving_bench(dg, args.serving_cases, dg.FP32_BULK)
+            serving["fp32_bulk"] = serving_bench(dg, args.serving_cases_fp32, dg.FP32_BULK)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
+        # the oracle on the host's cores: one independent replica per usable
+        # core (the headline cpu_baseline), and one replica alone
         cdof, ctimes = cpu_oracle_sample(2, nel=4)
-        cval = cdof * STAGES * len(ctimes) / sum(ctimes)
-        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
-               "sample": f"4^3 elements of the same curved N=7 TGV workload ({cdof} DOF), 2 LSERK steps, "
-                         f"single-threaded FP64 C"}
+        single = {"value": cdof * STAGES * len(ctimes) / sum(ctimes), "unit": UNIT, "cores": 1, "kind": "oracle",
+                  "sample": f"4^3 elements of the same curved N=7 TGV workload ({cdof} DOF), 2 LSERK steps, "
+                            f"single-threaded FP64 C"}
         try:
-            cpu["all_cores"] = cpu_oracle_all_cores()
-        except Exception as ex:  # an auxiliary figure: its failure is reported, not fatal
-            cpu["all_cores"] = {"unavailable": f"{type(ex).__name__}: {ex}"}
+            cpu = cpu_oracle_all_cores()
+            cpu["single_core"] = single
+        except Exception as ex:  # all cores unavailable: the single-core figure, with the reason
+            cpu = dict(single, cpu_model=cpu_model(), all_cores={"unavailable": f"{type(ex).__name__}: {ex}"})
 
     if rank == 0:
         clocks = clk.summary()
@@ -1003,6 +1057,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurement")
+    ap.add_argument("--serving-cases-fp32", type=int, default=200,
+                    help="cases of the FP32-bulk serving stream (the configuration's 200 by default)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-cases", type=int, default=48)
     ap.add_argument("--no-shock", action="store_true", help="skip the shock-tube measurement")

@@ -225,6 +225,17 @@ int dg_advance(dg_ctx* ctx, double t_end, int64_t max_steps, double* t_out, int6
    Serving keeps the default scheme. */
 int dg_set_rk(dg_ctx* ctx, int n_stages, const double* A, const double* B, const double* c);
 
+/* The library's built-in schemes, as dg_set_rk would set them:
+   DG_RK_CK5: the five-stage fourth-order scheme of Carpenter and Kennedy
+   (the default);  DG_RK_NDB14: the fourteen-stage fourth-order scheme of
+   Niegemann, Diehl and Busch (Sec. 2.2 cites it, Sec. 6 runs the
+   application with it).  Its stability region reaches about 18.5 along the
+   negative real axis and 6.1 along the imaginary axis (the five-stage
+   scheme: 4.7 and 3.3), so it takes a larger cfl and dfl.  DG_ERR_ARG for
+   another value. */
+enum { DG_RK_CK5 = 0, DG_RK_NDB14 = 1 };
+int dg_set_rk_scheme(dg_ctx* ctx, int scheme);
+
 /* Same work as dg_step, launched kernel by kernel (no graph) with CUDA events
    recorded on the context's stream around every launch.  Accumulates, per
    kernel kind k, the summed device time ms[k] and the launch count
@@ -248,24 +259,36 @@ int dg_set_sponge(dg_ctx* ctx, const double* sigma, const double* U_base);
    elements per thread block of the lifting and volume kernels (the default,
    about 256 threads, or twice as many elements), the volume kernel's thread
    mapping for the split-form sums (FP64: one task per line pair, or one per
-   node) and the side kernels' block size (128 or 256 threads).  Only scratch
-   arrays are written; the state is unchanged.  config (may be NULL, 4 ints):
-   lift elements per block, volume elements per block, line pairs (1) or per
-   node (0), side block size.  ms (may be NULL, 8 doubles): mean time per
-   launch of each variant (-1 where a variant does not exist), in the order
-   lift D, lift 2D, volume D default mapping, volume D other mapping, volume
-   2D default, volume 2D other, side kernels at 256, at 128.  Synchronises.
+   node) and the side kernels' block size (128 or 256 threads).  In the
+   two-kernel FP32-bulk stage (see dg_stage_form) the volume entries apply to
+   its element kernel and the side entry to its side kernel.  Only scratch
+   arrays are written; the state is unchanged.  config (may be NULL, 6 ints,
+   as in dg_set_config).  ms (may be NULL, 8 doubles): mean time per launch
+   of each variant (-1 where a variant does not exist), in the order lift D,
+   lift 2D, volume D default mapping, volume D other mapping, volume 2D
+   default, volume 2D other, side kernels at 256, at 128.  Synchronises.
    Elements per block change no arithmetic; the volume mapping changes the
    summation order of the split-form sums (both within the FP64 parity).
    DG_ERR_STATE on Gauss-Legendre nodes (their kernels have one launch
    configuration). */
 int dg_autotune(dg_ctx* ctx, int* config, double* ms);
 
-/* Sets (config, 4 ints as above; 0 / -1 entries select the defaults) or
-   reads back the launch configuration.  DG_ERR_ARG for a value that is not
-   one of the variants. */
+/* Sets or reads back the launch configuration, 6 ints: lift elements per
+   block, volume elements per block, line pairs (1) or per node (0), side
+   block size (0 / -1 entries select the defaults), the FP32-bulk stage form
+   (0: the two-kernel stage where it applies, else four kernels; 1: always
+   the four-kernel stage) and the two-kernel stage's L2 prefetch of the next
+   wave's element data (1 on, the default; 0 off).  DG_ERR_ARG for a value
+   that is not one of the variants. */
 int dg_set_config(dg_ctx* ctx, const int* config);
 int dg_get_config(const dg_ctx* ctx, int* config);
+
+/* The stage form the context's steps use: 2 for the two-kernel FP32-bulk
+   stage (FillFlux per side node, then everything else per element; periodic
+   LGL meshes of a single context in FP32-bulk), 4 for the four-kernel stage
+   (surface prolongation, lifting, surface flux, volume), the form of FP64,
+   Gauss-Legendre nodes, boundary conditions and serving pools. */
+int dg_stage_form(const dg_ctx* ctx);
 
 /* Time step the CFL rule gives for the context's state (synchronises). */
 int dg_time_step(dg_ctx* ctx, double* dt);
@@ -395,6 +418,19 @@ void dg_server_destroy(dg_server* srv);
    entry point again in that process. */
 int dg_kinetic_noalloc(int N, int nodes, int64_t n_elems, const double* U, const double* J, const double* Ut,
                        double* out, void* stream);
+
+/* Arithmetic peak probe for the roofline denominators of the benchmark (a
+   measurement aid; the paper reports no peaks).  kind 0: FP64 FMA rate (the
+   bound of the FP64 path, Sec. 4 measures against its own hardware); 1: FP64
+   tensor rate (mma.sync m8n8k4 DMMA); 2: both issued from the same warps, in
+   equal numbers per iteration (a rate near the sum of kinds 0 and 1 shows
+   separate pipes, one near either alone a shared one); 3: FP32 FMA rate.
+   One launch of iters iterations over eight 256-thread blocks per SM on the
+   current device, timed with CUDA events after a warm-up launch; an FMA
+   counts 2 flops, one m8n8k4 MMA 512 per warp.  *flops_per_s: the rate;
+   *ms (may be NULL): the timed launch.  Allocates and frees a small output
+   buffer; synchronises `stream`.  DG_ERR_ARG for a bad kind or iters < 1. */
+int dg_peak_probe(int kind, int iters, double* flops_per_s, double* ms, void* stream);
 
 /* Verification access to intermediate arrays (device buffers, caller-owned).
    what = DG_DEBUG_METRICS: out0 = Ja [E][node][3][3] ((J a^d)_c at [d][c]),

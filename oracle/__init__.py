@@ -91,6 +91,7 @@ def _lib(quad: bool = False):
             "lserk_ode": fn("lserk_ode", C.c_double, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
                                                       C.c_void_p, C.c_void_p, C.c_void_p]),
             "rk_coeffs": fn("rk_coeffs", None, [dp, dp, dp]),
+            "rk14_coeffs": fn("rk14_coeffs", None, [dp, dp, dp]),
         }
         _LIBS[key] = api
         return api
@@ -194,6 +195,15 @@ def lserk_ode(kind: int, lam: float, y0: float, dt: float, n_steps: int, rk=None
 def rk_coeffs():
     A, B, Cc = np.zeros(5), np.zeros(5), np.zeros(5)
     _lib()["rk_coeffs"](_dp(A), _dp(B), _dp(Cc))
+    return A, B, Cc
+
+
+def rk14_coeffs():
+    """(A, B, c) of the fourteen-stage fourth-order 2N-storage scheme of
+    Niegemann, Diehl and Busch (the scheme of the paper's application run);
+    pass it as rk= to Mesh.step and lserk_ode."""
+    A, B, Cc = np.zeros(14), np.zeros(14), np.zeros(14)
+    _lib()["rk14_coeffs"](_dp(A), _dp(B), _dp(Cc))
     return A, B, Cc
 
 

@@ -1401,6 +1401,25 @@ static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0,
                                2006345519317.0 / 3224310063776.0,
                                2802321613138.0 / 2924317926251.0};
 
+/* Niegemann, Diehl and Busch's fourteen-stage fourth-order 2N-storage
+   scheme (J. Comput. Phys. 231, 2012; Sec. 2.2 cites it, Sec. 6 runs the
+   application with it): A, B and the abscissae c as published, 16 digits */
+static const double RK14_A[14] = {0.0, -0.7188012108672410, -0.7785331173421570, -0.0053282796654044,
+                                  -0.8552979934029281, -3.9564138245774565, -1.5780575380587385,
+                                  -2.0837094552574054, -0.7483334182761610, -0.7032861106563359,
+                                  0.0013917096117681, -0.0932075369637460, -0.9514200470875948,
+                                  -7.1151571693922548};
+static const double RK14_B[14] = {0.0367762454319673, 0.3136296607553959, 0.1531848691869027,
+                                  0.0030097086818182, 0.3326293790646110, 0.2440251405350864,
+                                  0.3718879239592277, 0.6204126221582444, 0.1524043173028741,
+                                  0.0760894927419266, 0.0077604214040978, 0.0024647284755382,
+                                  0.0780348340049386, 5.5059777270269628};
+static const double RK14_C[14] = {0.0, 0.0367762454319673, 0.1249685262725025, 0.2446177702277698,
+                                  0.2476149531070420, 0.2969311120382472, 0.3978149645802642,
+                                  0.5270854589440328, 0.6981269994175695, 0.8190890835352128,
+                                  0.8527059887098624, 0.8604711817462826, 0.8627060376969976,
+                                  0.8734213127600976};
+
 typedef void (*rhs_fn)(void* ctx, const real* U, real t, real* Ut);
 
 /* one 2N-storage step: dU = A_s dU + dt R(U); U = U + B_s dU */
@@ -1834,4 +1853,9 @@ double ORC(lserk_ode)(int kind, double lam, double y0, double dt, int n_steps, i
 
 void ORC(rk_coeffs)(double* A, double* B, double* C) {
   for (int s = 0; s < 5; ++s) { A[s] = RK_A[s]; B[s] = RK_B[s]; C[s] = RK_C[s]; }
+}
+
+/* the fourteen-stage table (14 entries each) */
+void ORC(rk14_coeffs)(double* A, double* B, double* C) {
+  for (int s = 0; s < 14; ++s) { A[s] = RK14_A[s]; B[s] = RK14_B[s]; C[s] = RK14_C[s]; }
 }

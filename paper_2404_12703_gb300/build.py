@@ -48,6 +48,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
              "-I", os.path.join(ROOT, "include"), *ARCH]
     if ptxas_info:
         flags += ["-Xptxas", "-v"]
+    if os.environ.get("DG_BUILD_CHECK") == "1":
+        # debug build: bounds checks in the kernels that have them (DG_CHECK)
+        flags += ["-DDG_CHECK"]
     procs = []
     objs = []
     for s in srcs:

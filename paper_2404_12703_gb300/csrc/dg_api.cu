@@ -321,6 +321,12 @@ int ensure_arrays(dg_ctx* c, const dg_params* p, std::string& msg) {
                              {(void**)&c->fstar32, sizeof(float) * S * 5 * n2},
                              {(void**)&c->nrm32, sizeof(float) * S * 7 * n2}};
     if (c->gauss) set.push_back({(void**)&c->gfc32, sizeof(float) * S * 2 * 12 * n2});
+    // face data of the two-kernel stage: periodic LGL meshes of a single context
+    if (fused_eligible(c)) {
+      set.push_back({(void**)&c->tr32, sizeof(float) * S * 2 * n2 * 8});
+      set.push_back({(void**)&c->pfv32, sizeof(float) * S * 2 * n2 * 4});
+      set.push_back({(void**)&c->qs32, sizeof(float) * S * n2 * 4});
+    }
     e = take(set);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->g32, 0, sizeof(float) * E * 12 * n3, st);
     if (e == cudaSuccess) e = launch_fp32_geometry(c, st);
@@ -353,6 +359,20 @@ __global__ void k_set_scalars(DevScalars* s, double dt_fixed, int set_t, double 
   s->t_end = t_end;
   if (set_t) s->t = t;
   if (reset_flags) s->nonfinite = 0;
+}
+// saves (restore = 0) or restores (restore = 1) the reference state of the
+// shifted primitives around a dg_rhs of another state
+__global__ void k_keep_refs(DevScalars* s, int restore) {
+  double* r[5] = {&s->ref_p, &s->ref_H, &s->ref_T, &s->ref_rho, &s->ref_E};
+  float* f[3] = {&s->f_ref_p, &s->f_ref_H, &s->f_ref_T};
+  for (int k = 0; k < 5; ++k) {
+    if (restore) *r[k] = s->keep_ref[k];
+    else s->keep_ref[k] = *r[k];
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (restore) *f[k] = s->keep_f_ref[k];
+    else s->keep_f_ref[k] = *f[k];
+  }
 }
 __global__ void k_zero_kin(DevScalars* s) {
   s->kin[0] = s->kin[1] = s->kin[2] = s->kin[3] = 0.0;
@@ -462,6 +482,9 @@ void dg_destroy(dg_ctx* c) {
   dfree(c, c->Ufc);
   dfree(c, c->gfc);
   dfree(c, c->gfc32);
+  dfree(c, c->tr32);
+  dfree(c, c->pfv32);
+  dfree(c, c->qs32);
   dfree(c, c->ops);
   dfree(c, c->scal);
   if (c->scal_host) cudaFreeHost(c->scal_host);
@@ -702,6 +725,7 @@ int dg_set_params(dg_ctx* c, const dg_params* p) {
   }
   c->prm = *p;
   destroy_graph(c);
+  c->traces_valid = false;
   if (c->state_set) {
     cudaError_t e = launch_refs(c);
     if (e != cudaSuccess) return cuda_fail(e, "dg_set_params");
@@ -752,6 +776,7 @@ int dg_set_state(dg_ctx* c, const double* U, int on_device, double t) {
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
+  c->traces_valid = false;
   if (e != cudaSuccess) return cuda_fail(e, "dg_set_state");
   c->t_host = t;
   c->state_set = true;
@@ -792,14 +817,27 @@ int dg_rhs(dg_ctx* c, const double* U_dev, double* Ut_dev) {
     Uin = c->dU;
   }
   // reference state of the shifted primitives taken from the evaluated state
-  // (any constant is exact; this one keeps the FP32-bulk rounding small)
-  double* Ukeep = c->U;
-  c->U = const_cast<double*>(Uin);
-  if (e == cudaSuccess) e = launch_refs(c);
-  c->U = Ukeep;
+  // (any constant is exact; this one keeps the FP32-bulk rounding small); the
+  // context's own is kept and put back, so later steps are unchanged
+  if (e == cudaSuccess && U_dev && c->state_set) {
+    k_keep_refs<<<1, 1, 0, c->stream>>>(c->scal, 0);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (U_dev) {  // the context's own state keeps the reference it was set with
+    double* Ukeep = c->U;
+    c->U = const_cast<double*>(Uin);
+    if (e == cudaSuccess) e = launch_refs(c);
+    c->U = Ukeep;
+  }
   if (e == cudaSuccess) e = launch_rhs(c, Uin, 0, 0.0, 0.0, 0);
   if (e == cudaSuccess) e = launch_to_public(c, c->Ut, Ut_dev);
-  if (e == cudaSuccess && U_dev && c->state_set) e = launch_refs(c);
+  if (e == cudaSuccess && U_dev && c->state_set) {
+    k_keep_refs<<<1, 1, 0, c->stream>>>(c->scal, 1);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  c->traces_valid = false;
   if (e != cudaSuccess) return cuda_fail(e, "dg_rhs");
   return DG_OK;
 }
@@ -837,12 +875,23 @@ static cudaError_t ensure_step_graph(dg_ctx* c) {
   return e;
 }
 
+// the two-kernel FP32-bulk stage reads the face data of the step's state:
+// formed here when no step left them behind
+static cudaError_t ensure_face_data(dg_ctx* c) {
+  if (!fused_active(c) || c->traces_valid) return cudaSuccess;
+  cudaError_t e = launch_fprep(c, c->U);
+  if (e == cudaSuccess) c->traces_valid = true;
+  return e;
+}
+
 static cudaError_t launch_steps(dg_ctx* c, int64_t n_steps) {
   cudaError_t e = ensure_step_graph(c);
+  if (e == cudaSuccess) e = ensure_face_data(c);
   if (e != cudaSuccess) return e;
   for (int64_t i = 0; i < n_steps && e == cudaSuccess; ++i) {
     e = cudaGraphLaunch(c->step_graph, c->stream);
-    count_launch(2 + 5 * (c->prm.viscous ? 4 : 2));
+    const int per_stage = fused_active(c) ? 2 : (c->prm.viscous ? 4 : 2);
+    count_launch(2 + (c->rk_ns > 0 ? c->rk_ns : 5) * per_stage);
   }
   return e;
 }
@@ -930,6 +979,7 @@ int dg_profile_step(dg_ctx* c, int n_steps, double dt, double* ms, int64_t* laun
   if (e == cudaSuccess) {
     k_set_scalars<<<1, 1, 0, c->stream>>>(c->scal, dt > 0 ? dt : 0.0, 0, 0.0, 0);
     count_launch();
+    e = ensure_face_data(c);
     c->prof = p;
     for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
       p->used = 0;
@@ -979,6 +1029,31 @@ int dg_set_rk(dg_ctx* c, int n_stages, const double* A, const double* B, const d
   return DG_OK;
 }
 
+// Niegemann, Diehl and Busch's fourteen-stage fourth-order 2N-storage scheme
+// (Sec. 2.2 cites it; Sec. 6 runs the application with it), as published
+static const double NDB14_A[14] = {0.0, -0.7188012108672410, -0.7785331173421570, -0.0053282796654044,
+                                   -0.8552979934029281, -3.9564138245774565, -1.5780575380587385,
+                                   -2.0837094552574054, -0.7483334182761610, -0.7032861106563359,
+                                   0.0013917096117681, -0.0932075369637460, -0.9514200470875948,
+                                   -7.1151571693922548};
+static const double NDB14_B[14] = {0.0367762454319673, 0.3136296607553959, 0.1531848691869027,
+                                   0.0030097086818182, 0.3326293790646110, 0.2440251405350864,
+                                   0.3718879239592277, 0.6204126221582444, 0.1524043173028741,
+                                   0.0760894927419266, 0.0077604214040978, 0.0024647284755382,
+                                   0.0780348340049386, 5.5059777270269628};
+static const double NDB14_C[14] = {0.0, 0.0367762454319673, 0.1249685262725025, 0.2446177702277698,
+                                   0.2476149531070420, 0.2969311120382472, 0.3978149645802642,
+                                   0.5270854589440328, 0.6981269994175695, 0.8190890835352128,
+                                   0.8527059887098624, 0.8604711817462826, 0.8627060376969976,
+                                   0.8734213127600976};
+
+int dg_set_rk_scheme(dg_ctx* c, int scheme) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (scheme == DG_RK_CK5) return dg_set_rk(c, 0, nullptr, nullptr, nullptr);
+  if (scheme == DG_RK_NDB14) return dg_set_rk(c, 14, NDB14_A, NDB14_B, NDB14_C);
+  return fail(DG_ERR_ARG, "unknown scheme (DG_RK_CK5 or DG_RK_NDB14)");
+}
+
 int dg_set_sponge(dg_ctx* c, const double* sigma, const double* U_base) {
   if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
   if (!c->cap_stream) return fail(DG_ERR_STATE, "internal case context");
@@ -1026,6 +1101,7 @@ int dg_autotune(dg_ctx* c, int* config, double* ms) {
   if (c->gauss) return fail(DG_ERR_STATE, "the Gauss-Legendre kernels have one launch configuration");
   double t[8];
   cudaError_t e = launch_autotune(c, t);
+  c->traces_valid = false;  // the tuner's runs write the face arrays
   if (e != cudaSuccess) return cuda_fail(e, "dg_autotune");
   destroy_graph(c);  // the next step captures the chosen variants
   if (config) dg_get_config(c, config);
@@ -1038,17 +1114,22 @@ int dg_set_config(dg_ctx* c, const int* config) {
   int D;
   bool lift2, vol2;
   variants_of(c->N, D, lift2, vol2);
-  const int le = config[0], ve = config[1], pr = config[2], sb = config[3];
+  const int le = config[0], ve = config[1], pr = config[2], sb = config[3], sf = config[4], pf = config[5];
   if (!(le == 0 || le == D || (lift2 && le == 2 * D))) return fail(DG_ERR_ARG, "lift elements per block");
   if (!(ve == 0 || ve == D || (vol2 && ve == 2 * D))) return fail(DG_ERR_ARG, "volume elements per block");
   if (!(pr == -1 || pr == 0 || pr == 1)) return fail(DG_ERR_ARG, "volume mapping");
   if (pr == 1 && c->prm.precision == DG_FP32_BULK) return fail(DG_ERR_ARG, "line pairs are an FP64 mapping");
   if (!(sb == 0 || sb == 128 || sb == 256)) return fail(DG_ERR_ARG, "side block size");
+  if (!(sf == 0 || sf == 1)) return fail(DG_ERR_ARG, "stage form (0: default, 1: four kernels)");
+  if (!(pf == 0 || pf == 1)) return fail(DG_ERR_ARG, "prefetch (0 or 1)");
   c->cfg.lift_epb = le;
   c->cfg.vol_epb = ve;
   c->cfg.vol_pairs = pr;
   c->cfg.side_block = sb == 0 ? 256 : sb;
+  c->cfg.stage_form = sf;
+  c->cfg.prefetch = pf;
   destroy_graph(c);
+  c->traces_valid = false;  // the other stage form does not keep the face data
   return DG_OK;
 }
 
@@ -1061,7 +1142,14 @@ int dg_get_config(const dg_ctx* c, int* config) {
   config[1] = c->cfg.vol_epb > 0 ? c->cfg.vol_epb : D;
   config[2] = c->cfg.vol_pairs >= 0 ? c->cfg.vol_pairs : (c->prm.precision == DG_FP32_BULK ? 0 : 1);
   config[3] = c->cfg.side_block;
+  config[4] = c->cfg.stage_form;
+  config[5] = c->cfg.prefetch;
   return DG_OK;
+}
+
+int dg_stage_form(const dg_ctx* c) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  return fused_active(c) ? 2 : 4;
 }
 
 int dg_time_step(dg_ctx* c, double* dt) {
@@ -1083,6 +1171,7 @@ int dg_kinetic(dg_ctx* c, double* out) {
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
   if (!c->scal_host) return fail(DG_ERR_STATE, "internal case context: no host mirror");
   cudaError_t e = launch_rhs(c, c->U, 0, 0.0, 0.0, 0);
+  c->traces_valid = false;
   if (e == cudaSuccess) {
     k_zero_kin<<<1, 1, 0, c->stream>>>(c->scal);
     count_launch();

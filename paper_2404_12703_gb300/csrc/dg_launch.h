@@ -43,6 +43,21 @@ int create_pool_ctx(dg_ctx** out, int N, int64_t capE, const dg_params* params, 
 cudaError_t launch_fp32_geometry(dg_ctx* c, cudaStream_t st);
 cudaError_t launch_fv_metrics(dg_ctx* c, cudaStream_t st);
 
+// the two-kernel FP32-bulk stage serves periodic LGL meshes (no boundary
+// sides): single contexts and serving pools, not the server's temporary
+// per-case contexts; its face arrays exist only there
+inline bool fused_eligible(const dg_ctx* c) {
+  return !c->gauss && !c->pool_stream && c->n_bc == 0;
+}
+// the stage launches of c use the two-kernel FP32-bulk form
+inline bool fused_active(const dg_ctx* c) {
+  return c->prm.precision == DG_FP32_BULK && c->tr32 && fused_eligible(c) && c->cfg.stage_form != 1;
+}
+// face data of the context's state for the two-kernel stage (dg_rhs.cu):
+// every element (a pool's occupied ones), or with E >= 0 the elements
+// e0 .. e0 + E - 1, on stream st (null: the context's stream)
+cudaError_t launch_fprep(dg_ctx* c, const double* U, int64_t e0 = 0, int64_t E = -1, cudaStream_t st = nullptr);
+
 // the arrays a parameter set needs (FP64 or FP32 working arrays, FV
 // interface metrics), allocated and formed on first use (dg_api.cu)
 int ensure_arrays(dg_ctx* c, const dg_params* p, std::string& msg);
@@ -67,7 +82,8 @@ cudaError_t init_kernel_attributes(int N);
 #define DG_DECLARE_STAGE_N(K)                                                                    \
   cudaError_t stage_attrs_n##K();                                                                \
   cudaError_t stage_launch_n##K(dg_ctx* c, const double* U, int mode, double A, double B, int f); \
-  cudaError_t stage_autotune_n##K(dg_ctx* c, double* ms);
+  cudaError_t stage_autotune_n##K(dg_ctx* c, double* ms);                                        \
+  cudaError_t fprep_n##K(dg_ctx* c, const double* U, int64_t e0, int64_t E, cudaStream_t st);
 DG_DECLARE_STAGE_N(1)
 DG_DECLARE_STAGE_N(2)
 DG_DECLARE_STAGE_N(3)

@@ -292,6 +292,19 @@ cudaError_t launch_rhs(dg_ctx* c, const double* U, int mode, double rkA, double 
   }
 }
 
+cudaError_t launch_fprep(dg_ctx* c, const double* U, int64_t e0, int64_t E, cudaStream_t st) {
+  switch (c->N) {
+    case 1: return fprep_n1(c, U, e0, E, st);
+    case 2: return fprep_n2(c, U, e0, E, st);
+    case 3: return fprep_n3(c, U, e0, E, st);
+    case 4: return fprep_n4(c, U, e0, E, st);
+    case 5: return fprep_n5(c, U, e0, E, st);
+    case 6: return fprep_n6(c, U, e0, E, st);
+    case 7: return fprep_n7(c, U, e0, E, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_autotune(dg_ctx* c, double* ms) {
   switch (c->N) {
     case 1: return stage_autotune_n1(c, ms);

@@ -583,6 +583,8 @@ static bool admit(dg_server* s, Request& r, std::string& err) {
     d.f_ref_T = (float)d.ref_T;
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_cases + slot, &d, sizeof(CaseData), cudaMemcpyHostToDevice, q);
+  // the two-kernel FP32-bulk stage: the face data of the case's initial state
+  if (e == cudaSuccess && fused_active(p)) e = launch_fprep(p, p->U, e0, E, q);
   cudaEvent_t ev = nullptr;
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(ev, q);

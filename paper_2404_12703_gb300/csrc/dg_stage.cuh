@@ -1167,6 +1167,7 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
 }  // namespace dg
 
 #include "dg_stage_gl.cuh"
+#include "dg_fused32.cuh"
 
 namespace dg {
 
@@ -1233,6 +1234,12 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.src_a = c->prm.source_a;
   a.xyzs = c->xyzs;
   a.rkC = c->stage_c;
+  a.tr32 = c->tr32;
+  a.pfv32 = c->pfv32;
+  a.qs32 = c->qs32;
+  a.epilogue = 0;
+  a.prefetch = 0;
+  a.elem_off = 0;
   if (c->elem_list) {
     a.E = (int)c->n_elem_list;
     a.S = (int)c->n_side_list;
@@ -1309,6 +1316,9 @@ inline void vol_variant(const StageArgs& a, int epb, int pairs, cudaStream_t st)
   }
 }
 
+template <int N, int E>
+inline int felem_wave();
+
 template <int N, typename T>
 cudaError_t stage_set_attrs() {
   using V = Variants<N, T>;
@@ -1329,6 +1339,109 @@ cudaError_t stage_set_attrs() {
     lift(k_volume<N, 1, T, 2 * V::D, V::fp64>, VolumeSmem<N, T, 2 * V::D, V::fp64>::bytes);
     if constexpr (V::fp64) lift(k_volume<N, 1, T, 2 * V::D, false>, VolumeSmem<N, T, 2 * V::D, false>::bytes);
   }
+  if constexpr (!V::fp64) {
+    lift(k_fprep<N>, FusedSmem<N>::bytes);
+    lift(k_felem<N, 0, 0>, FusedSmem<N, 0>::bytes);
+    lift(k_felem<N, 1, 0>, FusedSmem<N, 0>::bytes);
+    if constexpr (V::vol2) lift(k_felem<N, 1, 2 * V::D>, FusedSmem<N, 2 * V::D>::bytes);
+    // the prefetch distances, queried here (context set-up) and not during
+    // the capture of a step graph
+    felem_wave<N, 0>();
+    if constexpr (V::vol2) felem_wave<N, 2 * V::D>();
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The two-kernel FP32-bulk stage (dg_fused32.cuh)
+// ---------------------------------------------------------------------------
+// blocks of k_felem<N, 1, E> resident per SM times the SM count: the L2
+// prefetch distance (one wave ahead)
+template <int N, int E>
+inline int felem_wave() {
+  static int wave = 0;
+  if (wave == 0) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_felem<N, 1, E>, Shape<N, E>::THREADS,
+                                                      FusedSmem<N, E>::bytes) == cudaSuccess &&
+        sms > 0 && per > 0)
+      wave = sms * per;
+    else
+      wave = -1;  // unknown: no prefetch
+  }
+  return wave;
+}
+template <int N, int MODE, int E>
+inline void launch_felem(StageArgs a, int prefetch, cudaStream_t st) {
+  using S = Shape<N, E>;
+  a.prefetch = prefetch ? std::max(0, felem_wave<N, E>()) : 0;
+  k_felem<N, MODE, E><<<(unsigned)((a.E + S::EPB - 1) / S::EPB), S::THREADS, FusedSmem<N, E>::bytes, st>>>(a);
+}
+template <int N>
+inline void launch_fflux(const StageArgs& a, int block, cudaStream_t st) {
+  const int64_t side_nodes = (int64_t)a.S * Shape<N>::n2;
+  const int b = block == 128 ? 128 : 256;
+  k_fflux<N><<<(unsigned)((side_nodes + b - 1) / b), b, 0, st>>>(a);
+}
+// face data of state U: every element of the context (a serving pool: its
+// occupied elements), or, with E_range >= 0, the elements e0 .. e0 + E_range - 1
+template <int N>
+inline cudaError_t fprep_launch(dg_ctx* c, const double* U, int64_t e0 = 0, int64_t E_range = -1,
+                                cudaStream_t st = nullptr) {
+  using S = Shape<N>;
+  StageArgs a = make_stage_args(c, U);
+  if (E_range >= 0) {
+    a.elem_list = nullptr;
+    a.elem_off = (int)e0;
+    a.E = (int)E_range;
+  }
+  if (a.E == 0) return cudaSuccess;
+  k_fprep<N><<<(unsigned)((a.E + S::EPB - 1) / S::EPB), S::THREADS, FusedSmem<N>::bytes, st ? st : c->stream>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+template <int N>
+inline void felem_variant(const StageArgs& a, int mode, int epb, int prefetch, cudaStream_t st) {
+  using V = Variants<N, float>;
+  if (mode == 0) return launch_felem<N, 0, 0>(a, 0, st);
+  if constexpr (V::vol2) {
+    if (epb == 2 * V::D) return launch_felem<N, 1, 2 * V::D>(a, prefetch, st);
+  }
+  launch_felem<N, 1, 0>(a, prefetch, st);
+}
+
+// One stage in the two-kernel form.  Mode 0 (dg_rhs) first forms the face
+// data of U; mode 1 expects them from the previous stage (or k_fprep, run by
+// the stepping loop before the first step) and leaves those of the updated
+// state behind.
+template <int N>
+cudaError_t stage_launch_fused(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first) {
+  StageArgs a = make_stage_args(c, U);
+  a.Ut = c->Ut;
+  a.Urk = c->U;
+  a.dU = c->dU;
+  a.rkA = rkA;
+  a.rkB = rkB;
+  a.first_stage = first;
+  a.epilogue = mode == 1;
+  if (a.E == 0) return cudaSuccess;
+  const StageConfig& g = c->cfg;
+  if (mode == 0) {
+    prof_begin(c, PK_SURF_PRIMS);
+    cudaError_t e = fprep_launch<N>(c, U);
+    prof_end(c);
+    if (e != cudaSuccess) return e;
+    c->traces_valid = false;  // they now describe U, not necessarily the context's state
+  }
+  prof_begin(c, PK_SURF_FLUX);
+  launch_fflux<N>(a, g.side_block, c->stream);
+  prof_end(c);
+  prof_begin(c, PK_VOLUME);
+  felem_variant<N>(a, mode, g.vol_epb, g.prefetch, c->stream);
+  prof_end(c);
+  count_launch(2);
   return cudaGetLastError();
 }
 
@@ -1371,6 +1484,9 @@ cudaError_t stage_launch_gl(dg_ctx* c, const double* U, int mode, double rkA, do
 template <int N, typename T>
 cudaError_t stage_launch(dg_ctx* c, const double* U, int mode, double rkA, double rkB, int first) {
   if (c->gauss) return stage_launch_gl<N, T>(c, U, mode, rkA, rkB, first);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (fused_active(c)) return stage_launch_fused<N>(c, U, mode, rkA, rkB, first);
+  }
   StageArgs a = make_stage_args(c, U);
   a.Ut = c->Ut;
   a.Urk = c->U;
@@ -1408,9 +1524,74 @@ cudaError_t stage_launch(dg_ctx* c, const double* U, int mode, double rkA, doubl
 // repetitions, in the order lift D, lift 2D, volume (D, default mapping),
 // volume (D, other mapping), volume (2D, default), volume (2D, other), side
 // 256, side 128 (-1 where a variant does not exist).
+// Autotuner of the two-kernel FP32-bulk stage: the element kernel at D and
+// 2D elements per block (ms[2], ms[4]) and the side kernel at 256 and 128
+// threads (ms[6], ms[7]); the runs read the face data of the state (formed
+// first) and write the RK update and the epilogue's face data to scratch.
+template <int N>
+cudaError_t stage_autotune_fused(dg_ctx* c, double* ms) {
+  using V = Variants<N, float>;
+  StageArgs a = make_stage_args(c, c->U);
+  a.Ut = c->Ut;
+  a.Urk = c->Ut;
+  a.dU = c->Upub;
+  a.rkA = 0.5;
+  a.rkB = 0.5;
+  a.first_stage = 0;
+  a.epilogue = 1;
+  for (int i = 0; i < 8; ++i) ms[i] = -1.0;
+  if (a.E == 0) return cudaSuccess;
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaMemsetAsync(c->Upub, 0, sizeof(double) * c->E * 5 * c->n3, st);
+  if (e == cudaSuccess) e = fprep_launch<N>(c, c->U);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int reps = 3;
+  auto timed = [&](auto&& launch) -> double {
+    launch();  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    count_launch(reps + 1);
+    return t / reps;
+  };
+  StageConfig best = c->cfg;
+  if (e == cudaSuccess) {
+    const int pf = c->cfg.prefetch;
+    ms[6] = timed([&] { launch_fflux<N>(a, 256, st); });
+    ms[7] = timed([&] { launch_fflux<N>(a, 128, st); });
+    best.side_block = ms[7] < ms[6] ? 128 : 256;
+    ms[2] = timed([&] { launch_felem<N, 1, 0>(a, pf, st); });
+    best.vol_epb = V::D;
+    if constexpr (V::vol2) {
+      ms[4] = timed([&] { launch_felem<N, 1, 2 * V::D>(a, pf, st); });
+      if (ms[4] < ms[2]) best.vol_epb = 2 * V::D;
+    }
+    e = cudaGetLastError();
+    // the runs' epilogues wrote the face data of a scratch state: form the
+    // state's own again (a serving pool steps on without re-forming them)
+    if (e == cudaSuccess) e = fprep_launch<N>(c, c->U);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e == cudaSuccess) {
+    c->cfg = best;
+    c->tuned = true;
+  }
+  return e;
+}
+
 template <int N, typename T>
 cudaError_t stage_autotune(dg_ctx* c, double* ms) {
   using V = Variants<N, T>;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (fused_active(c)) return stage_autotune_fused<N>(c, ms);
+  }
   StageArgs a = make_stage_args(c, c->U);
   a.Ut = c->Ut;
   a.Urk = c->Ut;
@@ -1509,6 +1690,9 @@ cudaError_t stage_autotune(dg_ctx* c, double* ms) {
   cudaError_t stage_autotune_n##K(dg_ctx* c, double* ms) {                                        \
     return c->prm.precision == DG_FP32_BULK ? stage_autotune<K, float>(c, ms)                     \
                                             : stage_autotune<K, double>(c, ms);                   \
+  }                                                                                               \
+  cudaError_t fprep_n##K(dg_ctx* c, const double* U, int64_t e0, int64_t E, cudaStream_t st) {    \
+    return fprep_launch<K>(c, U, e0, E, st);                                                      \
   }
 
 #define DG_DISPATCH(N_, CALL)                      \

@@ -46,6 +46,9 @@ struct DevScalars {
   double dt_cfl;             // CFL time step of the current state (dg_time_step)
   double ref_rho, ref_E;     // reference density and total energy (state at rest)
   float f_ref_p, f_ref_H, f_ref_T, f_pad;  // FP32 copies for the FP32-bulk kernels
+  // the context's reference state, kept while dg_rhs evaluates another state
+  double keep_ref[5];
+  float keep_f_ref[4];
 };
 
 // Per-case data of a serving pool (device, one entry per case slot).
@@ -71,6 +74,11 @@ struct StageConfig {
   int vol_epb = 0;      // elements per block of the volume kernel (0: default)
   int vol_pairs = -1;   // 1: line-pair two-point sums, 0: per node, -1: default
   int side_block = 256; // threads per block of the side kernels (128 or 256)
+  // FP32-bulk stage: 0 the two-kernel stage where it applies (periodic LGL
+  // meshes of a single context), else the four-kernel one; 1 always the
+  // four-kernel stage
+  int stage_form = 0;
+  int prefetch = 1;     // two-kernel stage: L2 prefetch of the next wave's element data (0: off)
 };
 
 // Per-stage launch parameters of the RHS kernels.
@@ -134,6 +142,15 @@ struct StageArgs {
   double src_A, src_a;
   const double* xyzs;
   double rkC;
+  // two-kernel FP32-bulk stage (dg_fused32.cuh): face traces [S][2][n2][8],
+  // partial viscous fluxes [S][2][n2][4], BR1 means q* [S][n2][4]; the
+  // element kernel's epilogue on / off; L2 prefetch distance in blocks (0: off)
+  float* tr32;
+  float* pfv32;
+  float* qs32;
+  int epilogue;
+  int prefetch;
+  int elem_off;  // k_fprep without an element list: elements elem_off .. elem_off + E - 1
 };
 
 }  // namespace dg
@@ -184,6 +201,13 @@ struct dg_ctx {
   double* Ufc = nullptr;      // GL: [S][2][5][n2] face values of the state
   double* gfc = nullptr;      // GL: [S][2][12][n2] face values of the lifted gradients
   float* gfc32 = nullptr;     // GL, FP32-bulk: the same in FP32
+  // two-kernel FP32-bulk stage: face data (see StageArgs); traces_valid: the
+  // face data hold the current state's (set by a step's last stage, cleared by
+  // anything else that writes the state or the face arrays)
+  float* tr32 = nullptr;
+  float* pfv32 = nullptr;
+  float* qs32 = nullptr;
+  bool traces_valid = false;
   int64_t bytes = 0;
   double t_host = 0.0;
   bool state_set = false;

@@ -31,9 +31,10 @@ SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "d
 EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
            "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_autotune", "dg_set_config", "dg_get_config",
            "dg_set_sponge", "dg_node_coords", "dg_quadrature_weights", "dg_selftest_convert",
-           "dg_set_rk",
+           "dg_set_rk", "dg_set_rk_scheme", "dg_stage_form",
            "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
-           "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc")
+           "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc",
+           "dg_peak_probe")
 
 
 class DgError(RuntimeError):
@@ -52,6 +53,7 @@ class Params(C.Structure):
 
 
 SOURCE_NONE, SOURCE_MMS = 0, 1
+RK_CK5, RK_NDB14 = 0, 1
 
 
 class MeshDesc(C.Structure):
@@ -110,6 +112,7 @@ def load(path: str | None = None):
             "dg_quadrature_weights": (C.c_int, [vp, dp]),
             "dg_selftest_convert": (C.c_int, [vp, vp, vp, C.c_int64, vp]),
             "dg_set_rk": (C.c_int, [vp, C.c_int, dp, dp, dp]),
+            "dg_set_rk_scheme": (C.c_int, [vp, C.c_int]),
             "dg_set_params": (C.c_int, [vp, C.POINTER(Params)]),
             "dg_set_state": (C.c_int, [vp, vp, C.c_int, C.c_double]),
             "dg_get_state": (C.c_int, [vp, vp, C.c_int, dp]),
@@ -120,6 +123,7 @@ def load(path: str | None = None):
             "dg_set_sponge": (C.c_int, [vp, vp, vp]),
             "dg_set_config": (C.c_int, [vp, C.POINTER(C.c_int)]),
             "dg_get_config": (C.c_int, [vp, C.POINTER(C.c_int)]),
+            "dg_stage_form": (C.c_int, [vp]),
             "dg_profile_step": (C.c_int, [vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int64)]),
             "dg_time_step": (C.c_int, [vp, dp]),
             "dg_kinetic": (C.c_int, [vp, dp]),
@@ -131,6 +135,7 @@ def load(path: str | None = None):
             "dg_last_error": (C.c_char_p, []),
             "dg_launch_count": (C.c_int64, []),
             "dg_kinetic_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int64, vp, vp, vp, vp, vp]),
+            "dg_peak_probe": (C.c_int, [C.c_int, C.c_int, dp, dp, vp]),
             "dg_server_default_config": (None, [C.POINTER(ServerConfig)]),
             "dg_server_create": (C.c_int, [C.POINTER(vp), C.POINTER(ServerConfig)]),
             "dg_submit": (C.c_int, [vp, C.POINTER(CaseDesc), C.POINTER(C.c_int64)]),
@@ -195,6 +200,16 @@ def kinetic_noalloc(N, U, J, Ut=None, out=None, stream=None, nodes=0):
                                      C.c_void_p(J.data_ptr()), C.c_void_p(Ut.data_ptr() if Ut is not None else 0),
                                      C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+PEAK_FP64_FMA, PEAK_FP64_MMA, PEAK_FP64_BOTH, PEAK_FP32_FMA = 0, 1, 2, 3
+
+
+def peak_probe(kind, iters=4096, stream=None):
+    """(FLOP/s, ms) of the arithmetic peak probe `kind` (see dg_peak_probe)."""
+    r, t = C.c_double(), C.c_double()
+    _check(load().dg_peak_probe(int(kind), int(iters), C.byref(r), C.byref(t), _stream_ptr(stream)))
+    return r.value, t.value
 
 
 def convert_check(x, stream=None):
@@ -407,6 +422,13 @@ class Solver:
         _check(self._lib.dg_set_rk(self._h, A.size, A.ctypes.data_as(dpt), B.ctypes.data_as(dpt),
                                    c.ctypes.data_as(dpt)))
 
+    def set_rk_scheme(self, scheme):
+        """A built-in scheme: RK_CK5 (the default five-stage one) or RK_NDB14
+        (the fourteen-stage one of the paper's application run)."""
+        if isinstance(scheme, str):
+            scheme = {"ck5": RK_CK5, "ndb14": RK_NDB14}[scheme]
+        _check(self._lib.dg_set_rk_scheme(self._h, int(scheme)))
+
     def set_sponge(self, sigma=None, U_base=None):
         """Sponge source -sigma (U - U_base): sigma [E, n^3] >= 0, U_base
         [E, n^3, 5] (host arrays); None removes it."""
@@ -417,25 +439,32 @@ class Solver:
         ub = _host_buf(np.ascontiguousarray(U_base, dtype=np.float64), 5 * sg.size, "U_base")
         _check(self._lib.dg_set_sponge(self._h, C.c_void_p(sg.ctypes.data), C.c_void_p(ub.ctypes.data)))
 
-    CONFIG_KEYS = ("lift_epb", "vol_epb", "vol_pairs", "side_block")
+    CONFIG_KEYS = ("lift_epb", "vol_epb", "vol_pairs", "side_block", "stage_form", "prefetch")
     TUNE_KEYS = ("lift_D", "lift_2D", "vol_D", "vol_D_other_mapping", "vol_2D", "vol_2D_other_mapping",
                  "side_256", "side_128")
 
     def autotune(self):
         """Times the stage kernels' launch variants on the current state and
         keeps the fastest; returns (config, per-variant ms)."""
-        cfg = (C.c_int * 4)()
+        cfg = (C.c_int * 6)()
         ms = (C.c_double * 8)()
         _check(self._lib.dg_autotune(self._h, cfg, ms))
         return dict(zip(self.CONFIG_KEYS, list(cfg))), {k: (v if v >= 0 else None)
                                                         for k, v in zip(self.TUNE_KEYS, list(ms))}
 
-    def set_config(self, lift_epb=0, vol_epb=0, vol_pairs=-1, side_block=0):
-        cfg = (C.c_int * 4)(lift_epb, vol_epb, vol_pairs, side_block)
+    def set_config(self, lift_epb=0, vol_epb=0, vol_pairs=-1, side_block=0, stage_form=0, prefetch=1):
+        cfg = (C.c_int * 6)(lift_epb, vol_epb, vol_pairs, side_block, stage_form, prefetch)
         _check(self._lib.dg_set_config(self._h, cfg))
 
+    def stage_form(self):
+        """2: the two-kernel FP32-bulk stage; 4: the four-kernel stage."""
+        r = self._lib.dg_stage_form(self._h)
+        if r < 0:
+            _check(r)
+        return r
+
     def config(self):
-        cfg = (C.c_int * 4)()
+        cfg = (C.c_int * 6)()
         _check(self._lib.dg_get_config(self._h, cfg))
         return dict(zip(self.CONFIG_KEYS, list(cfg)))
 

@@ -327,6 +327,33 @@ def test_other_low_storage_schemes():
     assert ex.value.code == dg.DG_ERR_ARG
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fourteen_stage_scheme(prec):
+    """The library's built-in fourteen-stage scheme (its own copy of the
+    published table) over ten CFL steps against the oracle stepping with the
+    oracle's copy, on the compressible Taylor-Green set-up of Sec. 5.2
+    (Ma 1.25, Sutherland's law); FP64 within 1e-10 of the oracle, FP32-bulk
+    within 1e-5 (a state moved by ten steps of FP32-rounded fluxes)."""
+    torch, dg = gpu_or_skip()
+    N = 3
+    m = W.box_mesh(N, (4, 4, 4), curved=0.1, seed=14, length=(2 * np.pi,) * 3)
+    U0 = W.tgv_state(m["xyz"], Ma=1.25).reshape(m["E"], -1, 5)
+    p0 = 1.0 / (1.4 * 1.25 ** 2)
+    s = _solver(dg, m, precision=dg.FP64 if prec == "fp64" else dg.FP32_BULK, sutherland=1, T_ref=p0,
+                cfl=1.5, dfl=3.0)
+    s.set_rk_scheme(dg.RK_NDB14)
+    s.set_state(U0)
+    s.step(10)
+    U, t = s.get_state()
+    Uo, to, _ = O.Mesh(N, m["xyz"], m["period"]).step(U0, oracle_params(s.params), 10, rk=O.rk14_coeffs())
+    assert abs(t - to) <= (1e-13 if prec == "fp64" else 1e-6) * to
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert np.abs(U - Uo).max() / np.abs(Uo).max() <= tol
+    with pytest.raises(dg.DgError) as ex:
+        s.set_rk_scheme(7)
+    assert ex.value.code == dg.DG_ERR_ARG
+
+
 @pytest.mark.parametrize("nodes", ["lgl", "gauss"])
 def test_unstructured_ogrid_mesh(nodes):
     """The five-block O-grid mesh (edges with three, four and eight elements

@@ -188,3 +188,33 @@ def test_priority_policy_keeps_results_and_serves_oldest_first(prec):
     # and they finish in submission order
     ends = [st["time_to_solution"] for _, st in out]
     assert all(ends[i] < ends[i + 1] for i in range(len(ends) - 1)), ends
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_a_nonfinite_case_is_isolated(prec):
+    """Fault isolation, made on the host: a NaN planted in one submitted case's
+    initial state.  The CFL reduction flags that case only; it retires at
+    once with the non-finite flag, and the three other cases of the mix end
+    bitwise equal to their runs alone."""
+    torch, dg = gpu_or_skip()
+    precision = dg.FP64 if prec == "fp64" else dg.FP32_BULK
+    t_end = 0.04
+    built = [make(*c) for c in CASES[:4]]
+    alone = []
+    for m, U0, mu in built:
+        srv = dg.Server(POOLS, max_cases=8, precision=precision)
+        alone.append(srv.wait(srv.submit(m, U0, t_end, mu=mu))[0])
+        srv.close()
+    bad = 1
+    mix = [(m, U0.copy(), mu) for m, U0, mu in built]
+    mix[bad][1][2, 5, 0] = np.nan
+    srv = dg.Server(POOLS, max_cases=8, precision=precision)
+    tickets = [srv.submit(m, U0, t_end, mu=mu) for m, U0, mu in mix]
+    for i, tk in enumerate(tickets):
+        U, st = srv.wait(tk)
+        if i == bad:
+            assert st["nonfinite"] == 1 and st["t_final"] < t_end
+        else:
+            assert st["nonfinite"] == 0 and st["t_final"] == t_end
+            np.testing.assert_array_equal(U, alone[i])
+    srv.close()

@@ -220,6 +220,60 @@ def test_other_low_storage_schemes():
     assert math.log2(b1 / b2) < 2.5
 
 
+def _butcher(A, B):
+    """Butcher matrix and weights of the 2N-storage scheme (A, B).  With
+    k_s = R(U_{s-1}), dU_s = A_s dU_{s-1} + dt k_s and U_s = U_{s-1} + B_s dU_s,
+    U_s = U_0 + dt sum_{j<=s} (sum_{i=j..s} B_i prod_{l=j+1..i} A_l) k_j."""
+    m = len(A)
+    a = np.zeros((m + 1, m))
+    for s in range(1, m + 1):
+        for j in range(1, s + 1):
+            tot = 0.0
+            for i in range(j, s + 1):
+                p = 1.0
+                for l in range(j + 1, i + 1):
+                    p *= A[l - 1]
+                tot += B[i - 1] * p
+            a[s, j - 1] = tot
+    return a[:m], a[m]
+
+
+def test_fourteen_stage_scheme():
+    """The fourteen-stage fourth-order 2N-storage scheme of Niegemann, Diehl and
+    Busch (Sec. 2.2 cites it; Sec. 6 runs the application with it), entered
+    from the publication's 16-digit table.  Its Butcher form satisfies the
+    eight order conditions of order four to round-off (a mistyped digit in
+    the k-th place leaves a residual of about 10^-k), its abscissae are the
+    Butcher row sums, it is not of order five, one oracle step of y' = z y is
+    the scheme's stability polynomial, and the oracle integrator shows fourth
+    order on a nonlinear, non-autonomous ODE."""
+    A, B, c = O.rk14_coeffs()
+    assert len(A) == 14 and A[0] == 0.0
+    a, b = _butcher(A, B)
+    np.testing.assert_allclose(a.sum(axis=1), c, rtol=0, atol=1e-14)
+    one = np.ones(14)
+    conds = [b @ one - 1, b @ c - 1 / 2, b @ c ** 2 - 1 / 3, b @ (a @ c) - 1 / 6, b @ c ** 3 - 1 / 4,
+             b @ (c * (a @ c)) - 1 / 8, b @ (a @ c ** 2) - 1 / 12, b @ (a @ (a @ c)) - 1 / 24]
+    assert max(abs(x) for x in conds) < 2e-14, conds
+    assert abs(b @ c ** 4 - 1 / 5) > 1e-4
+    gam = [1.0]
+    v = one
+    for _ in range(14):
+        gam.append(b @ v)
+        v = a @ v
+    np.testing.assert_allclose(gam[:5], [1, 1, 1 / 2, 1 / 6, 1 / 24], rtol=0, atol=1e-13)
+    for z in (-0.9, -0.4, 0.3, 0.7):
+        R = np.polynomial.polynomial.polyval(z, gam)
+        assert abs(O.lserk_ode(0, z, 1.0, 1.0, 1, rk=(A, B, c)) - R) < 1e-13 * abs(R)
+    # its fourth-order error constant is small (the scheme is optimised), so
+    # the observed order approaches 4 from above only at fine steps: 5.2, 4.9,
+    # 4.7 and 4.5 between dt = 1/4 ... 1/64
+    ref = O.lserk_ode(1, 0, 0.5, 1.0 / 2048, 2048, rk=(A, B, c))
+    e1 = abs(O.lserk_ode(1, 0, 0.5, 1.0 / 32, 32, rk=(A, B, c)) - ref)
+    e2 = abs(O.lserk_ode(1, 0, 0.5, 1.0 / 64, 64, rk=(A, B, c)) - ref)
+    assert 3.7 < math.log2(e1 / e2) < 4.8, math.log2(e1 / e2)
+
+
 def test_time_step_closed_form():
     """Cartesian element of size h, uniform state: lambda_c = sum_d (|u_d| + c) 2/h."""
     N = 4

@@ -97,6 +97,10 @@ MUTANTS = [
      "w->Bc[(e * n3 + v) * 5 + k] += o->Dhat[a * n + i] * fc[k];", 0),
     # time integration and time step (Sec. 2.2)
     ("stage time dropped", "f(ctx, U, t + rk->C[s] * dt, Ut);", "f(ctx, U, t, Ut);", 0),
+    # the fourteen-stage table: one digit mistyped in A, B and c
+    ("fourteen-stage A digit", "-2.0837094552574054", "-2.0837094562574054", 0),
+    ("fourteen-stage B digit", "0.1524043173028741", "0.1524043173029741", 0),
+    ("fourteen-stage c digit", "0.8190890835352128", "0.8190890835352728", 0),
     ("stage update without the register", "U[x] = U[x] + rk->B[s] * dU[x];", "U[x] = U[x] + rk->B[s] * dt * Ut[x];", 0),
     ("CFL step without (N+1)^2", "real dt = P->cfl * 2 / (np1 * np1 * lc);", "real dt = P->cfl * 2 / (np1 * lc);", 0),
     ("CFL sound speed times |Ja|^2", "+ c * RSQRT(nj2);", "+ c * nj2;", 0),

@@ -74,13 +74,29 @@ struct FusedSmem {
   using S = Shape<N, EPB_>;
   static constexpr int n2d = (S::n2 + 1) & ~1;  // Vinv (FP64), even count: 16-byte aligned after it
   static constexpr int n2p = (S::n2 + 3) & ~3;  // Dsplit / Dhat (FP32)
-  // per element: P (2 float4 per node), J (3 float4 per node), W (12 floats
-  // per node: lifting products, viscous / FV fluxes, FP64 indicator scratch),
+  static constexpr int n4 = (S::n + 3) & ~3;    // a row of Dhat padded to whole float4s
+  // a node plane with one pad word after every line of n nodes (pad_idx):
+  // lines along any direction then fall in distinct banks
+  static constexpr int Pn = S::n3 + S::n2;
+  // per element: P (2 float4 per node: (rho, u, v, w) / 2 and (p', H') / 2, T'),
+  // J (3 float4 planes, (Ja^d) / 2), q (4 planes: u, v, w, T'), W (12 planes:
+  // lifting sums; also viscous / FV fluxes and the FP64 indicator scratch),
   // face normals (6 faces x n2 float4: s n and the SurfInt sign)
-  static constexpr int per_elem_f = 8 * S::n3 + 12 * S::n3 + 12 * S::n3 + 24 * S::n2;
-  static constexpr size_t bytes = sizeof(double) * n2d + sizeof(float) * (2 * n2p + S::EPB * per_elem_f);
-  static_assert(2 * S::n3 + 4 * S::n2 <= 6 * S::n3, "the indicator scratch fits the W workspace");
+  static constexpr int offJ = 8 * S::n3, offQ = offJ + 12 * Pn, offW = offQ + 4 * Pn, offN = offW + 12 * Pn;
+  static constexpr int per_elem_f = offN + 24 * S::n2;
+  static constexpr size_t bytes =
+      sizeof(double) * n2d + sizeof(float) * (2 * n2p + S::n * n4 + S::EPB * per_elem_f);
+  static_assert(2 * S::n3 + 4 * S::n2 <= 6 * Pn, "the indicator scratch fits the W workspace");
+  static_assert((2 * n2p + S::n * n4) % 4 == 0 && per_elem_f % 4 == 0 && offQ % 4 == 0 && offW % 4 == 0 &&
+                    offN % 4 == 0,
+                "16-byte alignment of the float4 planes");
 };
+
+// padded plane index of node t: one pad word after each line of n nodes
+template <int n>
+__device__ __forceinline__ int pad_idx(int t) {
+  return t + t / n;
+}
 
 // the side record of element e's face f at its face-frame node (p, q):
 // side s, half (0: e is the master, 1: the slave), node index in the master frame
@@ -135,51 +151,70 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, const v
 // ---------------------------------------------------------------------------
 // The weak-form volume part of the lifting (Eq. lifting) at node t:
 //   acc[qv * 3 + x] = sum_d sum_al Dhat[id_d][al] (Ja^d_x q_qv)_al
-// q: the node's (u, v, w, T'); J4: the element's halved metrics, one float4
-// per direction and node; F2: the element's workspace (6 float2 planes).
-// Every thread of the block calls it (it holds barriers).
+// Register-blocked: per direction, one task per (line, variable) loads the
+// line's q_qv and Ja^d once, forms the three products in registers and applies
+// the n x n matrix Dhat (rows read as broadcast float4s) to them; the three
+// sums of each node go to the W planes (written for the first direction,
+// added for the others).  Qs: the element's q planes (u, v, w, T'); J4: its
+// halved metrics; W: its 12 workspace planes; sDr: Dhat with rows padded to
+// n4 floats.  Every thread of the block calls it (it holds barriers); W may
+// be reused after the caller's next barrier.
 // ---------------------------------------------------------------------------
-template <int n>
-__device__ __forceinline__ void lift_volume(const float q[4], const float4* J4, float2* F2, const float* sDh, int t,
+// FACES: only the sums at the element's face nodes are needed (the
+// epilogue): a line inside the element in both other directions computes its
+// two end nodes only; every face node lies on a line that computes it for
+// each direction.
+template <int n, int n4, bool FACES = false>
+__device__ __forceinline__ void lift_volume(const float* Qs, const float4* J4, float* W, const float* sDr, int t,
                                             float acc[12]) {
-  constexpr int n2 = n * n, n3 = n2 * n;
-#pragma unroll
-  for (int c = 0; c < 12; ++c) acc[c] = 0.0f;
+  constexpr int n2 = n * n, n3 = n2 * n, Pn = n3 + n2;
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
-    {
-      const float4 jj = J4[d * n3 + t];
-      const float J0 = 2.0f * jj.x, J1 = 2.0f * jj.y, J2 = 2.0f * jj.z;  // exact: the halving undone
-      float pr[12];
-#pragma unroll
-      for (int qv = 0; qv < 4; ++qv) {
-        pr[qv * 3 + 0] = J0 * q[qv];
-        pr[qv * 3 + 1] = J1 * q[qv];
-        pr[qv * 3 + 2] = J2 * q[qv];
-      }
-#pragma unroll
-      for (int k = 0; k < 6; ++k) F2[k * n3 + t] = make_float2(pr[2 * k], pr[2 * k + 1]);
-    }
-    __syncwarp();
-    __syncthreads();
-    {
-      const int id = dir_index<n>(t, d), sd = dir_stride<n>(d), base = t - id * sd;
+    const int sd = dir_stride<n>(d);
+    for (int task = t; task < 4 * n2; task += n3) {
+      const int qv = task / n2, l = task % n2, lp = l % n, lq = l / n;
+      const int base = d == 0 ? n * (lp + n * lq) : (d == 1 ? lp + n2 * lq : lp + n * lq);
+      float P0[n], P1[n], P2[n];
 #pragma unroll
       for (int al = 0; al < n; ++al) {
-        const float c = sDh[id * n + al];
-        const int nb = base + al * sd;
-        if (!DG_CHK(nb >= 0 && nb < n3, nb)) continue;
+        const int v = pad_idx<n>(base + al * sd);
+        const float q = Qs[qv * Pn + v];
+        const float4 j = J4[d * Pn + v];
+        P0[al] = (2.0f * j.x) * q;  // exact: the halving undone
+        P1[al] = (2.0f * j.y) * q;
+        P2[al] = (2.0f * j.z) * q;
+      }
+      const bool inner = FACES && lp > 0 && lp < n - 1 && lq > 0 && lq < n - 1;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          const float2 v = F2[k * n3 + nb];
-          acc[2 * k] += c * v.x;
-          acc[2 * k + 1] += c * v.y;
+      for (int i = 0; i < n; ++i) {
+        if (inner && i > 0 && i < n - 1) continue;
+        float r[n4];
+#pragma unroll
+        for (int c = 0; c < n4; c += 4) {
+          const float4 v4 = *reinterpret_cast<const float4*>(sDr + i * n4 + c);
+          r[c] = v4.x, r[c + 1] = v4.y, r[c + 2] = v4.z, r[c + 3] = v4.w;
+        }
+        float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
+#pragma unroll
+        for (int al = 0; al < n; ++al) {
+          o0 += r[al] * P0[al];
+          o1 += r[al] * P1[al];
+          o2 += r[al] * P2[al];
+        }
+        float* w = W + (qv * 3) * Pn + pad_idx<n>(base + i * sd);
+        if (d == 0) {
+          w[0] = o0, w[Pn] = o1, w[2 * Pn] = o2;
+        } else {
+          w[0] += o0, w[Pn] += o1, w[2 * Pn] += o2;
         }
       }
     }
     __syncwarp();
     __syncthreads();
   }
+  const int v = pad_idx<n>(t);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = W[k * Pn + v];
 }
 
 // Loads the element's face normals into shared memory: sSn[f][pq] = (s n of
@@ -207,13 +242,21 @@ __device__ __forceinline__ void load_face_normals(const StageArgs& a, int e, int
 // ---------------------------------------------------------------------------
 template <int N>
 __device__ __forceinline__ void face_epilogue(const StageArgs& a, const CaseParams& cp, int e, int t, bool valid,
-                                              const SPrim<float>& me, float Jinv, const float4* J4, float2* F2,
-                                              const float* sDh, const float4* sSn) {
-  constexpr int n = N + 1, n2 = n * n;
+                                              const SPrim<float>& me, float Jinv, const float4* J4, float* Qs,
+                                              float* Wk, const float* sDr, const float4* sSn) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  constexpr int Pn = n3 + n2, n4 = (n + 3) & ~3;
   const int idx[3] = {t % n, (t / n) % n, t / n2};
   const float q[4] = {me.u, me.v, me.w, me.Tt};
   float acc[12];
-  if (a.viscous) lift_volume<n>(q, J4, F2, sDh, t, acc);  // block-uniform condition
+  if (a.viscous) {  // block-uniform condition
+    const int v = pad_idx<n>(t);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Qs[k * Pn + v] = q[k];
+    __syncwarp();
+    __syncthreads();
+    lift_volume<n, n4, true>(Qs, J4, Wk, sDr, t, acc);
+  }
   if (!valid) return;
   bool on[3];
   int sd[3], hd[3], pqd[3];
@@ -279,12 +322,14 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_fprep(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* sDs = reinterpret_cast<float*>(reinterpret_cast<double*>(smraw) + L::n2d);
   float* sDh = sDs + L::n2p;
-  float* base = sDh + L::n2p;
+  float* sDr = sDh + L::n2p;  // [n][n4] Dhat, rows padded
+  float* base = sDr + n * L::n4;
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
   float* mine = base + (size_t)le * L::per_elem_f;
-  float4* J4 = reinterpret_cast<float4*>(mine + 8 * n3);
-  float2* F2 = reinterpret_cast<float2*>(mine + 20 * n3);
-  float4* sSn = reinterpret_cast<float4*>(mine + 32 * n3);
+  float4* J4 = reinterpret_cast<float4*>(mine + L::offJ);
+  float* Qs = mine + L::offQ;
+  float* Wk = mine + L::offW;
+  float4* sSn = reinterpret_cast<float4*>(mine + L::offN);
   // the element: a.elem_off + the block's slot, or an entry of the element
   // list (a serving pool's occupied elements); slots past the end redo the
   // last element and store nothing
@@ -294,21 +339,26 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_fprep(StageArgs a) {
   const bool valid = blockIdx.x * EPB + le < a.E && ce >= 0;
   const int e = DG_CHK(el >= 0 && t < n3 && le < EPB, el) ? el : 0;
   const CaseParams cp = case_params(a, ce);
-  for (int k = threadIdx.x; k < n2; k += blockDim.x) sDh[k] = (float)a.ops->Dhat[k];
+  for (int k = threadIdx.x; k < n * L::n4; k += blockDim.x) {
+    const int i = k / L::n4, al = k % L::n4;
+    sDr[k] = al < n ? (float)a.ops->Dhat[i * n + al] : 0.0f;
+  }
   load_face_normals<n>(a, e, t, sSn);
   double U[5];
   const double* u = a.U + (size_t)e * 5 * n3 + t;
 #pragma unroll
   for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
   const SPrim<float> me = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp);
+  const int vp = pad_idx<n>(t);
 #pragma unroll
   for (int d = 0; d < 3; ++d)
-    J4[d * n3 + t] = make_float4(0.5f * metric_at<float>(a, e, 3 * d, t, n3), 0.5f * metric_at<float>(a, e, 3 * d + 1, t, n3),
-                                 0.5f * metric_at<float>(a, e, 3 * d + 2, t, n3), 0.0f);
+    J4[d * L::Pn + vp] = make_float4(0.5f * metric_at<float>(a, e, 3 * d, t, n3),
+                                     0.5f * metric_at<float>(a, e, 3 * d + 1, t, n3),
+                                     0.5f * metric_at<float>(a, e, 3 * d + 2, t, n3), 0.0f);
   const float Jinv = metric_at<float>(a, e, 9, t, n3);
   __syncwarp();
   __syncthreads();
-  face_epilogue<N>(a, cp, e, t, valid, me, Jinv, J4, F2, sDh, sSn);
+  face_epilogue<N>(a, cp, e, t, valid, me, Jinv, J4, Qs, Wk, sDr, sSn);
 }
 
 // ---------------------------------------------------------------------------
@@ -449,16 +499,18 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
   double* sVi = reinterpret_cast<double*>(smraw);  // [n2] Vinv (FP64)
   float* sDs = reinterpret_cast<float*>(sVi + L::n2d);
   float* sDh = sDs + L::n2p;
-  float* base = sDh + L::n2p;
+  float* sDr = sDh + L::n2p;  // [n][n4] Dhat, rows padded
+  float* base = sDr + n * L::n4;
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
   float* mine = base + (size_t)le * L::per_elem_f;
-  float4* P4 = reinterpret_cast<float4*>(mine);             // [n3] (rho, u, v, w) / 2
-  float4* Q4 = P4 + n3;                                     // [n3] (p' / 2, H' / 2, T', 0)
-  float4* J4 = reinterpret_cast<float4*>(mine + 8 * n3);    // [3][n3] (Ja^d) / 2
-  float* Wk = mine + 20 * n3;                               // [12 n3] workspace
-  float2* F2 = reinterpret_cast<float2*>(Wk);
+  float4* P4 = reinterpret_cast<float4*>(mine);                   // [n3] (rho, u, v, w) / 2
+  float4* Q4 = P4 + n3;                                           // [n3] (p' / 2, H' / 2, T', 0)
+  float4* J4 = reinterpret_cast<float4*>(mine + L::offJ);         // [3][Pn] (Ja^d) / 2, padded index
+  float* Qs = mine + L::offQ;                                     // [4][Pn] u, v, w, T', padded index
+  float* Wk = mine + L::offW;                                     // [12][Pn] workspace
   float4* G4 = reinterpret_cast<float4*>(Wk);
-  float4* sSn = reinterpret_cast<float4*>(mine + 32 * n3);  // [6][n2] face normals and signs
+  float4* sSn = reinterpret_cast<float4*>(mine + L::offN);        // [6][n2] face normals and signs
+  constexpr int Pn = L::Pn;
   // slots past the last element redo the last element, free slots of a
   // serving pool compute on what they hold; neither stores
   const int ei = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
@@ -481,10 +533,26 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
                   a.metric32 + (size_t)a.E * 10 * n3);
     }
   }
+  // this element's later gathers, asked of L2 now: its six sides' q* and f*
+  // records (read after the lifting and in SurfInt) and its RK register (read
+  // by the update), so that those reads do not each wait on HBM
+  if (t < 6) {
+    const int sf = es_side(a.elem_side[(size_t)e * 6 + t]);
+    if (a.viscous)
+      prefetch_l2(a.qs32 + (size_t)sf * n2 * 4, sizeof(float) * 4 * n2, a.qs32, a.qs32 + (size_t)a.S * n2 * 4);
+    prefetch_l2(a.fstar32 + (size_t)sf * 5 * n2, sizeof(float) * 5 * n2, a.fstar32, a.fstar32 + (size_t)a.S * 5 * n2);
+  } else if (t == 6 && MODE == 1 && !a.first_stage) {
+    const float* d32 = reinterpret_cast<const float*>(a.dU);
+    prefetch_l2(d32 + (size_t)e * 5 * n3, sizeof(float) * 5 * n3, d32, d32 + (size_t)a.E * 5 * n3);
+  }
   for (int k = threadIdx.x; k < n2; k += blockDim.x) {
     sDs[k] = (float)a.ops->Dsplit[k];
     sDh[k] = (float)a.ops->Dhat[k];
     sVi[k] = a.ops->Vinv[k];
+  }
+  for (int k = threadIdx.x; k < n * L::n4; k += blockDim.x) {
+    const int i = k / L::n4, al = k % L::n4;
+    sDr[k] = al < n ? (float)a.ops->Dhat[i * n + al] : 0.0f;
   }
   load_face_normals<n>(a, e, t, sSn);
   double U[5];
@@ -494,14 +562,18 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
 #pragma unroll
     for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
   }
-  const SPrim<float> me = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp, &p_full);
+  // the FP64 pressure only for the indicator (one FP64 addition less otherwise)
+  const SPrim<float> me = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp, a.shock ? &p_full : nullptr);
   // halved values: every arithmetic mean of the two-point flux is one addition
   P4[t] = make_float4(0.5f * me.rho, 0.5f * me.u, 0.5f * me.v, 0.5f * me.w);
   Q4[t] = make_float4(0.5f * me.p, 0.5f * me.H, me.Tt, 0.0f);
+  const int vp = pad_idx<n>(t);
+  Qs[vp] = me.u, Qs[Pn + vp] = me.v, Qs[2 * Pn + vp] = me.w, Qs[3 * Pn + vp] = me.Tt;
 #pragma unroll
   for (int d = 0; d < 3; ++d)
-    J4[d * n3 + t] = make_float4(0.5f * metric_at<float>(a, e, 3 * d, t, n3), 0.5f * metric_at<float>(a, e, 3 * d + 1, t, n3),
-                                 0.5f * metric_at<float>(a, e, 3 * d + 2, t, n3), 0.0f);
+    J4[d * Pn + vp] = make_float4(0.5f * metric_at<float>(a, e, 3 * d, t, n3),
+                                  0.5f * metric_at<float>(a, e, 3 * d + 1, t, n3),
+                                  0.5f * metric_at<float>(a, e, 3 * d + 2, t, n3), 0.0f);
   const float Jinv = metric_at<float>(a, e, 9, t, n3);
   __syncwarp();
   __syncthreads();
@@ -509,9 +581,8 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
   float tau[6] = {0, 0, 0, 0, 0, 0}, W[3] = {0, 0, 0};
   // ---- BR1 lifting of the stage's state: volume part, then q* of the six faces ----
   if (a.viscous) {
-    const float q[4] = {me.u, me.v, me.w, me.Tt};
     float g[12];
-    lift_volume<n>(q, J4, F2, sDh, t, g);
+    lift_volume<n, L::n4>(Qs, J4, Wk, sDr, t, g);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int id = idx[d];
@@ -548,7 +619,7 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
     const int id = dir_index<n>(t, d), sd = dir_stride<n>(d), bse = t - id * sd;
     const float4 ai = P4[t];
     const float4 bi = Q4[t];
-    const float4 ji = J4[d * n3 + t];
+    const float4 ji = J4[d * Pn + vp];
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
 #pragma unroll
     for (int al = 0; al < n; ++al) {
@@ -557,7 +628,7 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
       if (!DG_CHK(va >= 0 && va < n3, va)) continue;
       const float4 aa = P4[va];
       const float4 ba = Q4[va];
-      const float4 ja = J4[d * n3 + va];
+      const float4 ja = J4[d * Pn + pad_idx<n>(va)];
       const float m0 = ji.x + ja.x, m1 = ji.y + ja.y, m2 = ji.z + ja.z;
       const float rho = ai.x + aa.x;
       const float u0 = ai.y + aa.y, u1 = ai.z + aa.z, u2 = ai.w + aa.w;
@@ -582,7 +653,7 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
       {
-        const float4 jj = J4[d * n3 + t];
+        const float4 jj = J4[d * Pn + vp];
         const float nv[3] = {2.0f * jj.x, 2.0f * jj.y, 2.0f * jj.z};
         float fv[4];
         viscous_flux_n(tau, W, nv, fv);
@@ -680,22 +751,29 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
 #pragma unroll
     for (int k = 0; k < 5; ++k) acc[k] += sg * Fs[k * n2];
   }
-  // ---- ApplyJac; the energy equation gets H_ref times the mass equation back (FP64) ----
+  // ---- ApplyJac; the energy equation gets H_ref times the mass equation back ----
+  float ut32[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) ut32[k] = -(accC[k] + acc[k]) * Jinv;
+  // the FP64 tendency: for dg_rhs, and in a stage with sources
+  const bool sources = a.sponge_sigma || a.source;
   double Ut[5];
+  if (MODE == 0 || sources) {
 #pragma unroll
-  for (int k = 0; k < 5; ++k) Ut[k] = f64_of(-(accC[k] + acc[k]) * Jinv);
-  Ut[4] += cp.Hr * Ut[0];
-  if (a.sponge_sigma) {  // sponge source -sigma (U - U_base), FP64
-    const double sg = a.sponge_sigma[(size_t)e * n3 + t];
-    const double* ub = a.sponge_base + (size_t)e * 5 * n3 + t;
+    for (int k = 0; k < 5; ++k) Ut[k] = f64_of(ut32[k]);
+    Ut[4] += cp.Hr * Ut[0];
+    if (a.sponge_sigma) {  // sponge source -sigma (U - U_base), FP64
+      const double sg = a.sponge_sigma[(size_t)e * n3 + t];
+      const double* ub = a.sponge_base + (size_t)e * 5 * n3 + t;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) Ut[k] -= sg * (U[k] - ub[k * n3]);
-  }
-  if (a.source) {  // manufactured-solution source, FP64
-    double Q[5];
-    mms_source(a, a.xyzs + ((size_t)e * n3 + t) * 3, stage_time(a, MODE), Q);
+      for (int k = 0; k < 5; ++k) Ut[k] -= sg * (U[k] - ub[k * n3]);
+    }
+    if (a.source) {  // manufactured-solution source, FP64
+      double Q[5];
+      mms_source(a, a.xyzs + ((size_t)e * n3 + t) * 3, stage_time(a, MODE), Q);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) Ut[k] += Q[k];
+      for (int k = 0; k < 5; ++k) Ut[k] += Q[k];
+    }
   }
   if constexpr (MODE == 0) {
     if (valid) {
@@ -704,13 +782,27 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
       for (int k = 0; k < 5; ++k) o[k * n3] = Ut[k];
     }
   } else {
-    const double dt = case_dt(a, ce);
-    double* du = a.dU + (size_t)e * 5 * n3 + t;
+    // RK update.  This stage form keeps the RK register in FP32 (the state
+    // stays FP64): dU = A dU + dt Ut in FP32, U += B dU in FP64.  The
+    // register is O(dt |Ut|) and rounds at the level of the FP32 fluxes
+    // already in Ut; the energy tendency's H_ref part is added in FP32, its
+    // rounding far below the FP32 error that Ut_rho already carries times H_ref.
+    float utf[5];
+    if (sources) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) utf[k] = f32_rn(Ut[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) utf[k] = ut32[k];
+      utf[4] = ut32[4] + cp.fHr * ut32[0];
+    }
+    const float dtf = f32_rn(case_dt(a, ce));
+    float* du = reinterpret_cast<float*>(a.dU) + (size_t)e * 5 * n3 + t;
     double* uo = a.Urk + (size_t)e * 5 * n3 + t;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      const double r = a.first_stage ? dt * Ut[k] : a.rkA * du[k * n3] + dt * Ut[k];
-      U[k] += a.rkB * r;  // the updated state
+      const float r = a.first_stage ? dtf * utf[k] : fmaf(a.f_rkA, du[k * n3], dtf * utf[k]);
+      U[k] += a.rkB * f64_of(r);  // the updated state
       if (valid) {
         du[k * n3] = r;
         uo[k * n3] = U[k];
@@ -721,7 +813,7 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
       const SPrim<float> mn = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp);
       __syncwarp();
       __syncthreads();  // the workspace is read by no thread any more
-      face_epilogue<N>(a, cp, e, t, valid, mn, Jinv, J4, F2, sDh, sSn);
+      face_epilogue<N>(a, cp, e, t, valid, mn, Jinv, J4, Qs, Wk, sDr, sSn);
     }
   }
 }

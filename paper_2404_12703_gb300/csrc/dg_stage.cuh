@@ -1424,6 +1424,7 @@ cudaError_t stage_launch_fused(dg_ctx* c, const double* U, int mode, double rkA,
   a.dU = c->dU;
   a.rkA = rkA;
   a.rkB = rkB;
+  a.f_rkA = (float)rkA;
   a.first_stage = first;
   a.epilogue = mode == 1;
   if (a.E == 0) return cudaSuccess;
@@ -1537,6 +1538,7 @@ cudaError_t stage_autotune_fused(dg_ctx* c, double* ms) {
   a.dU = c->Upub;
   a.rkA = 0.5;
   a.rkB = 0.5;
+  a.f_rkA = 0.5f;
   a.first_stage = 0;
   a.epilogue = 1;
   for (int i = 0; i < 8; ++i) ms[i] = -1.0;

@@ -115,6 +115,7 @@ struct StageArgs {
   double* dU;       // RK register
   const DevScalars* scal;
   double rkA, rkB;
+  float f_rkA;  // rkA in FP32 (the two-kernel FP32-bulk stage's register update)
   int first_stage;
   // serving pools: case of every element / side (-1: free slot) and the
   // per-case data; null for a single-mesh context

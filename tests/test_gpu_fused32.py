@@ -8,8 +8,9 @@ the oracle, as for the four-kernel stage; the two forms differ only in FP32
 rounding order (the BR1 face gradient is completed from a partial viscous
 flux and the neighbours' halves of q*), so their right-hand sides agree
 within 2e-5, and after 10 steps their states differ by no more than either
-differs from the FP64 oracle (and below 1e-7 of the state; the state and
-the RK update stay FP64); the face data that a step leaves behind equal
+differs from the FP64 oracle (and below 1e-7 of the state; the state stays
+FP64, the two-kernel stage keeps its RK register in FP32); the face data
+that a step leaves behind equal
 those formed from scratch, so interrupted and uninterrupted step sequences
 are bitwise equal.
 """

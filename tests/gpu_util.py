@@ -49,5 +49,25 @@ def parity_bound(oracle_fp64, oracle_ld, floor_factor=4.0, base=1e-12):
     return np.maximum(base, floor_factor * floor), floor
 
 
+def parity_check(err, bound, floor):
+    """Asserts err <= bound per variable with a message that gives the ratio
+    of the GPU error to the FP64 floor (the FP64 oracle's own error against
+    the long-double one); with DG_PARITY_LOG set, appends that ratio, the
+    error and the floor of the calling test as one JSON line to that file."""
+    import inspect
+    import json
+    import os
+    floor = np.asarray(floor, dtype=float)
+    err = np.asarray(err, dtype=float)
+    ratio = np.where(floor > 0, err / np.where(floor > 0, floor, 1.0), 0.0)
+    path = os.environ.get("DG_PARITY_LOG")
+    if path:
+        test = os.environ.get("PYTEST_CURRENT_TEST", inspect.stack()[1].function).split(" ")[0]
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": test, "ratio_max": float(ratio.max()), "err": err.tolist(),
+                                "floor": floor.tolist()}) + "\n")
+    assert np.all(err <= bound), {"err": err, "bound": bound, "floor": floor, "gpu_to_floor": ratio}
+
+
 def mesh(N, nel, curved=0.1, seed=20240419, **kw):
     return W.box_mesh(N, nel, curved=curved, seed=seed, **kw)

@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from paper_2404_12703_gb300 import workloads as W
 
-from gpu_util import gpu_or_skip, oracle_params, parity_bound, rel_err
+from gpu_util import parity_check, gpu_or_skip, oracle_params, parity_bound, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -73,7 +73,7 @@ def test_rhs_parity(N, bcs, kw):
     o64 = _oracle(m).rhs(U, prm)
     bound, floor = parity_bound(o64, ref)
     err = rel_err(Ut, ref)
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
 
 
 @pytest.mark.parametrize("N,Rg", [(2, 1.0), (3, 1.0), (5, 1.0), (3, 2.5)])

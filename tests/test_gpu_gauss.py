@@ -17,7 +17,7 @@ import pytest
 import oracle as O
 from paper_2404_12703_gb300 import workloads as W
 
-from gpu_util import gpu_or_skip, mesh, oracle_params, parity_bound, rel_err
+from gpu_util import parity_check, gpu_or_skip, mesh, oracle_params, parity_bound, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -73,7 +73,7 @@ def test_rhs_parity(N, nel, Ma, kw):
     o64 = _oracle(m).rhs(U, prm)
     bound, floor = parity_bound(o64, ref)
     err = rel_err(Ut, ref)
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
 
 
 def test_gradients_and_face_fluxes():
@@ -122,7 +122,7 @@ def test_boundary_conditions(N, bcs, kw):
     ref = _oracle(m, quad=True).rhs(U, prm)
     bound, floor = parity_bound(_oracle(m).rhs(U, prm), ref)
     err = rel_err(Ut, ref)
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -237,7 +237,7 @@ def test_full_size_sampled_elements():
     o64 = _oracle(m, metric_mask=want).rhs(U, prm, want=want)
     bound, floor = parity_bound(o64[want], ref[want])
     err = rel_err(Ut[want], ref[want])
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
     assert np.isfinite(Ut).all()
 
 

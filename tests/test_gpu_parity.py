@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 from paper_2404_12703_gb300 import workloads as W
 
-from gpu_util import gpu_or_skip, mesh, oracle_params, parity_bound, rel_err
+from gpu_util import parity_check, gpu_or_skip, mesh, oracle_params, parity_bound, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -71,7 +71,7 @@ def test_rhs_parity(N, nel, Ma, kw):
     o64 = O.Mesh(N, m["xyz"], m["period"]).rhs(U, prm)
     bound, floor = parity_bound(o64, ref)
     err = rel_err(Ut, ref)
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
     if Ma >= 0.5:
         assert np.all(err <= 1e-12), err
 
@@ -92,7 +92,7 @@ def test_partial_last_block(N, nel, kw):
     o64 = O.Mesh(N, m["xyz"], m["period"]).rhs(U, prm)
     bound, floor = parity_bound(o64, ref)
     err = rel_err(Ut, ref)
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
     if s.params.shock_capturing:
         al = s.debug("alpha")
         assert np.abs(al - oal).max() <= 1e-12
@@ -240,7 +240,7 @@ def test_shock_capturing_parity(alpha_force):
         assert np.abs(al - oal).max() <= 1e-12
     bound, floor = parity_bound(o64, ref)
     err = rel_err(Ut, ref)
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
 
 
 def test_full_size_sampled_elements():
@@ -262,7 +262,7 @@ def test_full_size_sampled_elements():
     o64 = O.Mesh(N, m["xyz"], m["period"], metric_mask=want).rhs(U, prm, want=want)
     bound, floor = parity_bound(o64[want], ref[want])
     err = rel_err(Ut[want], ref[want])
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
     assert np.isfinite(Ut).all()
 
 
@@ -377,7 +377,7 @@ def test_unstructured_ogrid_mesh(nodes):
     ref = O.Mesh(N, m["xyz"], m["period"], quad=True, gauss=gauss).rhs(U, prm)
     bound, floor = parity_bound(M.rhs(U, prm), ref)
     err = rel_err(Ut, ref)
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
     s32 = _solver(dg, m, nodes=nodes, precision=dg.FP32_BULK)
     assert np.all(rel_err(s32.rhs(torch.from_numpy(U).cuda()).cpu().numpy(), ref) <= 2e-4)
 
@@ -403,7 +403,7 @@ def test_gas_constants_other_than_the_defaults(kw):
     M = O.Mesh(N, m["xyz"], m["period"])
     bound, floor = parity_bound(M.rhs(U, prm), ref)
     err = rel_err(Ut, ref)
-    assert np.all(err <= bound), (err, bound, floor)
+    parity_check(err, bound, floor)
     s.set_state(U)
     odt, _ = M.dt(U, prm)
     assert abs(s.time_step() - odt) <= 1e-14 * odt

@@ -324,11 +324,11 @@ def fifo_latencies(arrivals, service):
     return lat, free_at
 
 
-def serve_all(dg, cases, precision, arrivals, max_resident_dof=0, priority_dof=0):
+def serve_all(dg, cases, precision, arrivals, max_resident_dof=0, priority_dof=0, persistent=0):
     """Submits the cases at the given arrival times (s after the start) to one
     server; returns time-to-solution per case, makespan and server stats."""
     srv = dg.Server(SERVING_POOLS, max_cases=64, precision=precision, max_resident_dof=max_resident_dof,
-                    priority_dof=priority_dof)
+                    priority_dof=priority_dof, persistent=persistent)
     t0 = time.perf_counter()
     tickets = []
     for a, c in zip(arrivals, cases):
@@ -376,6 +376,12 @@ def serving_bench(dg, n_cases, precision):
     lat_p, makespan_p, sstats_p = serve_all(dg, cases, precision, arrivals, 0, SERVING_PRIORITY_DOF)
     # closed system: every case submitted at once (capacity, not arrivals)
     _, sat_makespan, sat_stats = serve_all(dg, cases, precision, np.zeros(len(cases)))
+    persist = None
+    if precision == dg.FP32_BULK:
+        # the same with each pool's stages in one persistent launch per step
+        _, pm, pst = serve_all(dg, cases, precision, np.zeros(len(cases)), persistent=1)
+        persist = {"makespan_s": pm, "dof_updates_per_s": pst["dof_stage_updates"] / pm,
+                   "step_device_s": pst["step_device_s"]}
     p = lambda v, q: float(np.percentile(np.asarray(v), q))
     return {
         "workload": f"{len(cases)} cases (seeded PCG64(5)): n^3 meshes n in {{{','.join(map(str, SERVING_SIZES))}}}, "
@@ -401,6 +407,7 @@ def serving_bench(dg, n_cases, precision):
                         "vs_one_by_one_busy": sum(service) / sat_makespan,
                         "step_device_s": sat_stats["step_device_s"],
                         "host_s": {k: sat_stats[k] for k in ("capture_host_s", "setup_host_s", "insert_host_s")}},
+        "all_at_once_persistent": persist,
         "batched_steps": sstats["steps"], "graph_captures": sstats["captures"],
     }
 

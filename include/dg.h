@@ -273,13 +273,17 @@ int dg_set_sponge(dg_ctx* ctx, const double* sigma, const double* U_base);
    configuration). */
 int dg_autotune(dg_ctx* ctx, int* config, double* ms);
 
-/* Sets or reads back the launch configuration, 6 ints: lift elements per
+/* Sets or reads back the launch configuration, 7 ints: lift elements per
    block, volume elements per block, line pairs (1) or per node (0), side
    block size (0 / -1 entries select the defaults), the FP32-bulk stage form
    (0: the two-kernel stage where it applies, else four kernels; 1: always
-   the four-kernel stage) and the two-kernel stage's L2 prefetch of the next
-   wave's element data (1 on, the default; 0 off).  DG_ERR_ARG for a value
-   that is not one of the variants. */
+   the four-kernel stage), the two-kernel stage's L2 prefetch of the next
+   wave's element data (1 on, the default; 0 off) and its launch form (0:
+   one launch per kernel and stage, the default; 1: one persistent launch
+   per step running every stage, its phases separated by grid-wide barriers
+   whose waits give up after about a second: a step that loses a
+   participant ends with DG_ERR_TIMEOUT from dg_get_state instead of a
+   hang).  DG_ERR_ARG for a value that is not one of the variants. */
 int dg_set_config(dg_ctx* ctx, const int* config);
 int dg_get_config(const dg_ctx* ctx, int* config);
 
@@ -343,6 +347,11 @@ typedef struct {
                               leave at once), so the oldest cases run at
                               close to their own speed and small cases fill
                               the rest of the GPU                           */
+  int persistent;          /* FP32-bulk pools: 1 = each pool runs a step's
+                              stages in one persistent launch (grid-wide
+                              barriers with bounded waits) instead of one
+                              launch per kernel and stage; 0 (default) = the
+                              per-kernel launches                           */
 } dg_server_config;
 
 typedef struct {
@@ -451,6 +460,18 @@ int dg_peak_probe(int kind, int iters, double* flops_per_s, double* ms, void* st
    binary32(in[i]), back[i] = binary64(out[i]); device buffers of n values,
    stream-ordered on `stream`.  DG_ERR_ARG for NULL buffers or n < 0. */
 int dg_selftest_convert(const double* in, float* out, double* back, int64_t n, void* stream);
+
+/* Verification of the persistent launch's bounded waits: runs one persistent
+   step launch of the context (two-kernel FP32-bulk stage) whose grid-wide
+   barriers wait for one participant more than the grid holds, with waits of
+   about spin_polls x 200 ns.  The first barrier cannot complete: every block
+   gives up and leaves, the launch ends, the timeout flag is read back and
+   cleared.  Returns DG_ERR_TIMEOUT when the waits ran out as they must
+   (DG_OK would mean a barrier passed without its missing participant);
+   the context's state is unchanged (the element phase never ran).
+   DG_ERR_STATE if the context does not use the two-kernel stage.
+   Synchronises. */
+int dg_selftest_wait_timeout(dg_ctx* ctx, unsigned spin_polls);
 
 enum { DG_DEBUG_METRICS = 0, DG_DEBUG_MAPS = 1, DG_DEBUG_GRAD = 2, DG_DEBUG_FSTAR = 3,
        DG_DEBUG_ALPHA = 4 };

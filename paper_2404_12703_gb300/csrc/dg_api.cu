@@ -358,7 +358,7 @@ __global__ void k_set_scalars(DevScalars* s, double dt_fixed, int set_t, double 
   s->dt_fixed = dt_fixed;
   s->t_end = t_end;
   if (set_t) s->t = t;
-  if (reset_flags) s->nonfinite = 0;
+  if (reset_flags) s->nonfinite = 0, s->timeout = 0;
 }
 // saves (restore = 0) or restores (restore = 1) the reference state of the
 // shifted primitives around a dg_rhs of another state
@@ -374,6 +374,7 @@ __global__ void k_keep_refs(DevScalars* s, int restore) {
     else s->keep_f_ref[k] = *f[k];
   }
 }
+__global__ void k_clear_timeout(DevScalars* s) { s->timeout = 0; }
 __global__ void k_zero_kin(DevScalars* s) {
   s->kin[0] = s->kin[1] = s->kin[2] = s->kin[3] = 0.0;
   s->lam_c = 0ull;
@@ -802,6 +803,7 @@ int dg_get_state(dg_ctx* c, double* U, int on_device, double* t) {
   if (e != cudaSuccess) return cuda_fail(e, "dg_get_state");
   c->t_host = c->scal_host->t;
   if (t) *t = c->t_host;
+  if (c->scal_host->timeout) return fail(DG_ERR_TIMEOUT, "a persistent step's grid-wide wait ran out");
   if (c->scal_host->nonfinite) return fail(DG_ERR_NONFINITE, "a time step met a non-finite value");
   return DG_OK;
 }
@@ -846,6 +848,10 @@ static cudaError_t enqueue_step(dg_ctx* c) {
   cudaError_t e = launch_cfl(c, false);
   const bool own = c->rk_ns > 0;
   const int ns = own ? c->rk_ns : 5;
+  if (e == cudaSuccess && persist_active(c)) {
+    // every stage in one persistent launch
+    return launch_persist(c, ns, own ? c->rk_a : RKA, own ? c->rk_b : RKB, own ? c->rk_c : RKC);
+  }
   for (int s = 0; s < ns && e == cudaSuccess; ++s) {
     c->stage_c = own ? c->rk_c[s] : RKC[s];
     e = launch_rhs(c, c->U, 1, own ? c->rk_a[s] : RKA[s], own ? c->rk_b[s] : RKB[s], s == 0);
@@ -891,7 +897,7 @@ static cudaError_t launch_steps(dg_ctx* c, int64_t n_steps) {
   for (int64_t i = 0; i < n_steps && e == cudaSuccess; ++i) {
     e = cudaGraphLaunch(c->step_graph, c->stream);
     const int per_stage = fused_active(c) ? 2 : (c->prm.viscous ? 4 : 2);
-    count_launch(2 + (c->rk_ns > 0 ? c->rk_ns : 5) * per_stage);
+    count_launch(persist_active(c) ? 3 : 2 + (c->rk_ns > 0 ? c->rk_ns : 5) * per_stage);
   }
   return e;
 }
@@ -917,6 +923,7 @@ int dg_step(dg_ctx* c, int n_steps, double dt, double* t_out) {
   if (t_out) {
     c->t_host = c->scal_host->t;
     *t_out = c->t_host;
+    if (c->scal_host->timeout) return fail(DG_ERR_TIMEOUT, "a persistent step's grid-wide wait ran out");
     if (c->scal_host->nonfinite) return fail(DG_ERR_NONFINITE, "a time step met a non-finite value");
   }
   return DG_OK;
@@ -941,7 +948,7 @@ int dg_advance(dg_ctx* c, double t_end, int64_t max_steps, double* t_out, int64_
   const long long steps0 = h->steps;
   int64_t launched = 0;
   double dt_last = 0.0;
-  while (e == cudaSuccess && h->t < t_end && launched < max_steps && !h->nonfinite) {
+  while (e == cudaSuccess && h->t < t_end && launched < max_steps && !h->nonfinite && !h->timeout) {
     // a batch that ends just short of t_end at the last step's size; the
     // last few steps go one at a time
     int64_t K = 1;
@@ -962,6 +969,7 @@ int dg_advance(dg_ctx* c, double t_end, int64_t max_steps, double* t_out, int64_
   c->t_host = h->t;
   if (t_out) *t_out = h->t;
   if (steps_out) *steps_out = (int64_t)(h->steps - steps0);
+  if (h->timeout) return fail(DG_ERR_TIMEOUT, "a persistent step's grid-wide wait ran out");
   if (h->nonfinite) return fail(DG_ERR_NONFINITE, "a time step met a non-finite value");
   return DG_OK;
 }
@@ -1115,6 +1123,7 @@ int dg_set_config(dg_ctx* c, const int* config) {
   bool lift2, vol2;
   variants_of(c->N, D, lift2, vol2);
   const int le = config[0], ve = config[1], pr = config[2], sb = config[3], sf = config[4], pf = config[5];
+  const int ps = config[6];
   if (!(le == 0 || le == D || (lift2 && le == 2 * D))) return fail(DG_ERR_ARG, "lift elements per block");
   if (!(ve == 0 || ve == D || (vol2 && ve == 2 * D))) return fail(DG_ERR_ARG, "volume elements per block");
   if (!(pr == -1 || pr == 0 || pr == 1)) return fail(DG_ERR_ARG, "volume mapping");
@@ -1122,12 +1131,14 @@ int dg_set_config(dg_ctx* c, const int* config) {
   if (!(sb == 0 || sb == 128 || sb == 256)) return fail(DG_ERR_ARG, "side block size");
   if (!(sf == 0 || sf == 1)) return fail(DG_ERR_ARG, "stage form (0: default, 1: four kernels)");
   if (!(pf == 0 || pf == 1)) return fail(DG_ERR_ARG, "prefetch (0 or 1)");
+  if (!(ps == 0 || ps == 1)) return fail(DG_ERR_ARG, "launch form (0: per kernel, 1: persistent)");
   c->cfg.lift_epb = le;
   c->cfg.vol_epb = ve;
   c->cfg.vol_pairs = pr;
   c->cfg.side_block = sb == 0 ? 256 : sb;
   c->cfg.stage_form = sf;
   c->cfg.prefetch = pf;
+  c->cfg.persistent = ps;
   destroy_graph(c);
   c->traces_valid = false;  // the other stage form does not keep the face data
   return DG_OK;
@@ -1144,6 +1155,27 @@ int dg_get_config(const dg_ctx* c, int* config) {
   config[3] = c->cfg.side_block;
   config[4] = c->cfg.stage_form;
   config[5] = c->cfg.prefetch;
+  config[6] = c->cfg.persistent;
+  return DG_OK;
+}
+
+int dg_selftest_wait_timeout(dg_ctx* c, unsigned spin_polls) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (!fused_active(c)) return fail(DG_ERR_STATE, "the context does not use the two-kernel stage");
+  if (!c->scal_host) return fail(DG_ERR_STATE, "internal case context: no host mirror");
+  // one persistent step launch whose barriers wait for a participant that
+  // does not exist; the element phase never runs, so the state is unchanged
+  cudaError_t e = launch_persist(c, 5, RKA, RKB, RKC, 1u, spin_polls);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->scal_host, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_selftest_wait_timeout");
+  const int ran_out = c->scal_host->timeout;
+  k_clear_timeout<<<1, 1, 0, c->stream>>>(c->scal);
+  count_launch();
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_selftest_wait_timeout");
+  if (ran_out) return fail(DG_ERR_TIMEOUT, "the barrier waits ran out (expected)");
   return DG_OK;
 }
 

@@ -419,10 +419,10 @@ __device__ __forceinline__ void nbr_lift_part(const StageArgs& a, int s, int h, 
   for (int k = 0; k < 12; ++k) gc[k] *= Jinv;
 }
 
+// the work of side node tid (side list entry tid / n2, node tid % n2)
 template <int N>
-__global__ void __launch_bounds__(256) k_fflux(StageArgs a) {
+__device__ __forceinline__ void fflux_body(const StageArgs& a, int64_t tid) {
   constexpr int n = N + 1, n2 = n * n;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= (int64_t)a.S * n2) return;
   const int si = (int)(tid / n2), pq = (int)(tid % n2);
   const int s = a.side_list ? a.side_list[si] : si;
@@ -482,6 +482,11 @@ __global__ void __launch_bounds__(256) k_fflux(StageArgs a) {
   for (int k = 0; k < 5; ++k) out[k * n2] = f[k];
 }
 
+template <int N>
+__global__ void __launch_bounds__(256) k_fflux(StageArgs a) {
+  fflux_body<N>(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // k_felem: one stage of one element (FP32-bulk arithmetic, FP64 state)
 // ---------------------------------------------------------------------------
@@ -489,13 +494,20 @@ __global__ void __launch_bounds__(256) k_fflux(StageArgs a) {
 // of the updated state.  a.prefetch > 0: each block first asks L2 for the
 // state, RK register and metrics of the element a.prefetch blocks further on
 // (the next wave on the GPU), so that wave's loads find them in L2.
-template <int N, int MODE, int EPB_ = 0>
-__global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::template vol_min_blocks<float>())
-    k_felem(StageArgs a) {
+// the coefficients of one low-storage RK stage
+struct StageCoef {
+  double A, B, C;  // dU = A dU + dt Ut, U += B dU; stage time t + C dt
+  float fA;        // A in FP32 (the FP32 register update)
+  int first;       // the first stage (A is not used)
+};
+
+// the work of element block blk (elements blk * EPB ... of the element list)
+template <int N, int MODE, int EPB_>
+__device__ __forceinline__ void felem_body(const StageArgs& a, const StageCoef& sc, unsigned blk,
+                                           unsigned char* smraw) {
   using S = Shape<N, EPB_>;
   using L = FusedSmem<N, EPB_>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
-  extern __shared__ __align__(16) unsigned char smraw[];
   double* sVi = reinterpret_cast<double*>(smraw);  // [n2] Vinv (FP64)
   float* sDs = reinterpret_cast<float*>(sVi + L::n2d);
   float* sDh = sDs + L::n2p;
@@ -513,22 +525,25 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
   constexpr int Pn = L::Pn;
   // slots past the last element redo the last element, free slots of a
   // serving pool compute on what they hold; neither stores
-  const int ei = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
+  const int ei = (int)blk * EPB + le < a.E ? (int)blk * EPB + le : a.E - 1;
   const int el = a.elem_list ? a.elem_list[ei] : ei;
   const int ce = a.elem_case ? a.elem_case[el] : 0;
   // elements of cases that finished or sit this step out (time step 0) keep
   // their state and face data; a block made only of such slots leaves at once
-  const bool valid = blockIdx.x * EPB + le < a.E && ce >= 0 && !(a.cases && a.cases[ce].dt == 0.0);
+  const bool valid = (int)blk * EPB + le < a.E && ce >= 0 && !(a.cases && a.cases[ce].dt == 0.0);
   if (a.elem_case && __syncthreads_and(!valid)) return;
   const int e = DG_CHK(el >= 0 && t < n3 && le < EPB, el) ? el : 0;
   const CaseParams cp = case_params(a, ce);
   if (a.prefetch > 0 && threadIdx.x == 0 && !a.elem_list) {
-    const int64_t e2 = (int64_t)(blockIdx.x + a.prefetch) * EPB;
+    const int64_t e2 = (int64_t)(blk + a.prefetch) * EPB;
     if (e2 < a.E) {
       const int64_t ne = min((int64_t)EPB, (int64_t)a.E - e2);
       const size_t ub = sizeof(double) * 5 * n3;
       prefetch_l2(a.U + e2 * 5 * n3, ub * ne, a.U, a.U + (size_t)a.E * 5 * n3);
-      if (MODE == 1 && !a.first_stage) prefetch_l2(a.dU + e2 * 5 * n3, ub * ne, a.dU, a.dU + (size_t)a.E * 5 * n3);
+      if (MODE == 1 && !sc.first) {
+        const float* d32 = reinterpret_cast<const float*>(a.dU);
+        prefetch_l2(d32 + e2 * 5 * n3, sizeof(float) * 5 * n3 * ne, d32, d32 + (size_t)a.E * 5 * n3);
+      }
       prefetch_l2(a.metric32 + e2 * 10 * n3, sizeof(float) * 10 * n3 * ne, a.metric32,
                   a.metric32 + (size_t)a.E * 10 * n3);
     }
@@ -541,7 +556,7 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
     if (a.viscous)
       prefetch_l2(a.qs32 + (size_t)sf * n2 * 4, sizeof(float) * 4 * n2, a.qs32, a.qs32 + (size_t)a.S * n2 * 4);
     prefetch_l2(a.fstar32 + (size_t)sf * 5 * n2, sizeof(float) * 5 * n2, a.fstar32, a.fstar32 + (size_t)a.S * 5 * n2);
-  } else if (t == 6 && MODE == 1 && !a.first_stage) {
+  } else if (t == 6 && MODE == 1 && !sc.first) {
     const float* d32 = reinterpret_cast<const float*>(a.dU);
     prefetch_l2(d32 + (size_t)e * 5 * n3, sizeof(float) * 5 * n3, d32, d32 + (size_t)a.E * 5 * n3);
   }
@@ -770,7 +785,8 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
     }
     if (a.source) {  // manufactured-solution source, FP64
       double Q[5];
-      mms_source(a, a.xyzs + ((size_t)e * n3 + t) * 3, stage_time(a, MODE), Q);
+      const double ts = MODE == 0 ? a.scal->t : a.scal->t - (1.0 - sc.C) * a.scal->dt;
+      mms_source(a, a.xyzs + ((size_t)e * n3 + t) * 3, ts, Q);
 #pragma unroll
       for (int k = 0; k < 5; ++k) Ut[k] += Q[k];
     }
@@ -801,8 +817,8 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
     double* uo = a.Urk + (size_t)e * 5 * n3 + t;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      const float r = a.first_stage ? dtf * utf[k] : fmaf(a.f_rkA, du[k * n3], dtf * utf[k]);
-      U[k] += a.rkB * f64_of(r);  // the updated state
+      const float r = sc.first ? dtf * utf[k] : fmaf(sc.fA, du[k * n3], dtf * utf[k]);
+      U[k] += sc.B * f64_of(r);  // the updated state
       if (valid) {
         du[k * n3] = r;
         uo[k * n3] = U[k];
@@ -815,6 +831,88 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
       __syncthreads();  // the workspace is read by no thread any more
       face_epilogue<N>(a, cp, e, t, valid, mn, Jinv, J4, Qs, Wk, sDr, sSn);
     }
+  }
+}
+
+template <int N, int MODE, int EPB_ = 0>
+__global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::template vol_min_blocks<float>())
+    k_felem(StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const StageCoef sc{a.rkA, a.rkB, a.rkC, a.f_rkA, a.first_stage};
+  felem_body<N, MODE, EPB_>(a, sc, blockIdx.x, smraw);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form: one launch runs every stage of a step.  Each stage is a
+// side phase (FillFlux over all side nodes, grid-stride) and an element phase
+// (the element blocks, grid-stride), separated by grid-wide barriers.  The
+// grid is at most the number of blocks the GPU holds at once (a cooperative
+// launch), and every barrier wait gives up after a bounded spin: it then sets
+// the context's timeout flag and every block leaves, so a missing
+// participant ends the launch with an error the host reads
+// (DG_ERR_TIMEOUT) instead of a hang.
+// ---------------------------------------------------------------------------
+struct PersistArgs {
+  int ns;                           // stages
+  double A[32], B[32], C[32];       // the low-storage scheme
+  unsigned* bar;                    // [2]: arrivals, generation (zero at launch)
+  int* timeout;                     // sticky flag
+  unsigned expect_extra;            // arrivals beyond the grid the barriers wait for (0; a test raises it)
+  unsigned spin_limit;              // polls of 200 ns before a barrier wait gives up
+  int nblk;                         // element blocks of the element phase
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, int* flag, unsigned limit) {
+  __shared__ int ok;
+  __syncwarp();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    volatile int* vflag = flag;
+    const unsigned g = *gen;
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(bar, 1u) + 1u == expected) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned it = 0;
+      while (*gen == g) {
+        if (*vflag || ++it > limit) {
+          atomicExch(flag, 1);
+          good = 0;
+          break;
+        }
+        __nanosleep(200);
+      }
+    }
+    __threadfence();
+    ok = good && !*vflag;
+  }
+  __syncwarp();
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int N>
+__global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_blocks<float>())
+    k_fpersist(StageArgs a, PersistArgs p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const unsigned expected = gridDim.x + p.expect_extra;
+  const int64_t side_work = (int64_t)a.S * Shape<N>::n2;
+  for (int st = 0; st < p.ns; ++st) {
+    for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < side_work;
+         tid += (int64_t)gridDim.x * blockDim.x)
+      fflux_body<N>(a, tid);
+    if (!grid_barrier(p.bar, expected, p.timeout, p.spin_limit)) return;
+    const StageCoef sc{p.A[st], p.B[st], p.C[st], (float)p.A[st], st == 0};
+    for (unsigned blk = blockIdx.x; blk < (unsigned)p.nblk; blk += gridDim.x) {
+      felem_body<N, 1, 0>(a, sc, blk, smraw);
+      __syncwarp();
+      __syncthreads();  // the next element reuses the shared memory
+    }
+    if (st + 1 < p.ns && !grid_barrier(p.bar, expected, p.timeout, p.spin_limit)) return;
   }
 }
 

@@ -58,6 +58,14 @@ inline bool fused_active(const dg_ctx* c) {
 // e0 .. e0 + E - 1, on stream st (null: the context's stream)
 cudaError_t launch_fprep(dg_ctx* c, const double* U, int64_t e0 = 0, int64_t E = -1, cudaStream_t st = nullptr);
 
+// the steps of a two-kernel FP32-bulk context run as one persistent launch
+inline bool persist_active(const dg_ctx* c) { return fused_active(c) && c->cfg.persistent == 1; }
+// one persistent launch of every stage of a step (dg_rhs.cu); spin: polls of
+// a barrier wait before it gives up; extra: the barrier test hook (0)
+constexpr unsigned PERSIST_SPIN = 5000000u;  // about a second of 200 ns polls
+cudaError_t launch_persist(dg_ctx* c, int ns, const double* A, const double* B, const double* C, unsigned extra = 0,
+                           unsigned spin = PERSIST_SPIN);
+
 // the arrays a parameter set needs (FP64 or FP32 working arrays, FV
 // interface metrics), allocated and formed on first use (dg_api.cu)
 int ensure_arrays(dg_ctx* c, const dg_params* p, std::string& msg);
@@ -83,7 +91,9 @@ cudaError_t init_kernel_attributes(int N);
   cudaError_t stage_attrs_n##K();                                                                \
   cudaError_t stage_launch_n##K(dg_ctx* c, const double* U, int mode, double A, double B, int f); \
   cudaError_t stage_autotune_n##K(dg_ctx* c, double* ms);                                        \
-  cudaError_t fprep_n##K(dg_ctx* c, const double* U, int64_t e0, int64_t E, cudaStream_t st);
+  cudaError_t fprep_n##K(dg_ctx* c, const double* U, int64_t e0, int64_t E, cudaStream_t st);           \
+  cudaError_t persist_n##K(dg_ctx* c, int ns, const double* A, const double* B, const double* C, unsigned extra, \
+                           unsigned spin);
 DG_DECLARE_STAGE_N(1)
 DG_DECLARE_STAGE_N(2)
 DG_DECLARE_STAGE_N(3)

@@ -305,6 +305,20 @@ cudaError_t launch_fprep(dg_ctx* c, const double* U, int64_t e0, int64_t E, cuda
   }
 }
 
+cudaError_t launch_persist(dg_ctx* c, int ns, const double* A, const double* B, const double* C, unsigned extra,
+                           unsigned spin) {
+  switch (c->N) {
+    case 1: return persist_n1(c, ns, A, B, C, extra, spin);
+    case 2: return persist_n2(c, ns, A, B, C, extra, spin);
+    case 3: return persist_n3(c, ns, A, B, C, extra, spin);
+    case 4: return persist_n4(c, ns, A, B, C, extra, spin);
+    case 5: return persist_n5(c, ns, A, B, C, extra, spin);
+    case 6: return persist_n6(c, ns, A, B, C, extra, spin);
+    case 7: return persist_n7(c, ns, A, B, C, extra, spin);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_autotune(dg_ctx* c, double* ms) {
   switch (c->N) {
     case 1: return stage_autotune_n1(c, ms);

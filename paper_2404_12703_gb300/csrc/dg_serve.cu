@@ -229,6 +229,7 @@ struct Pool {
   int* h_elist[2] = {nullptr, nullptr};  // pinned staging of the occupied-element / side lists,
   int* h_slist[2] = {nullptr, nullptr};  // alternating between rebuilds
   int list_buf = 0;
+  int* h_timeout = nullptr;  // pinned [2]: the pool's persistent-launch timeout flag after step k
 };
 
 struct Request {
@@ -359,6 +360,8 @@ static cudaError_t capture_step(dg_server* s) {
   static const double RKB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
                                 1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                                 2277821191437.0 / 14882151754819.0};
+  static const double RKC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363218457.0,
+                                2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
   const double kvf = std::max(4.0 / 3.0, s->prm.gamma / s->prm.Pr);
   // The graph forks into one branch per pool, so that the kernels of
   // different pools (degrees) can run side by side:
@@ -404,7 +407,15 @@ static cudaError_t capture_step(dg_server* s) {
     if (P.ctx->n_elem_list == 0) continue;
     cudaStream_t keep = P.ctx->stream;
     P.ctx->stream = P.branch;
-    for (int st = 0; st < 5 && le == cudaSuccess; ++st) le = launch_rhs(P.ctx, P.ctx->U, 1, RKA[st], RKB[st], st == 0);
+    if (persist_active(P.ctx)) {
+      // every stage in one persistent launch; the pools' persistent launches
+      // follow one another on the main capture stream (each grid fills the
+      // GPU, and its blocks must all be resident at once)
+      P.ctx->stream = s->cap_stream;
+      le = launch_persist(P.ctx, 5, RKA, RKB, RKC);
+    } else {
+      for (int st = 0; st < 5 && le == cudaSuccess; ++st) le = launch_rhs(P.ctx, P.ctx->U, 1, RKA[st], RKB[st], st == 0);
+    }
     P.ctx->stream = keep;
   }
   join();
@@ -865,6 +876,10 @@ static void worker_loop(dg_server* s) {
       count_launch(1);
       cudaMemcpyAsync(s->h_cases + b * s->cfg.max_cases, s->d_cases, sizeof(CaseData) * s->cfg.max_cases,
                       cudaMemcpyDeviceToHost, s->stream);
+      for (auto& kv : s->pools)
+        if (kv.second.h_timeout)
+          cudaMemcpyAsync(kv.second.h_timeout + b, &kv.second.ctx->scal->timeout, sizeof(int), cudaMemcpyDeviceToHost,
+                          s->stream);
       cudaEventRecord(s->step_ev[b], s->stream);
       s->launched += 1;
     }
@@ -884,6 +899,14 @@ static void worker_loop(dg_server* s) {
       break;
     }
     inflight = have;
+    bool timed_out = false;
+    for (auto& kv : s->pools) timed_out = timed_out || (kv.second.h_timeout && kv.second.h_timeout[b]);
+    if (timed_out) {
+      std::lock_guard<std::mutex> lk(s->m);
+      s->worker_error = "batched step: a persistent launch's grid-wide wait ran out";
+      s->stop = true;
+      break;
+    }
     const CaseData* rec = s->h_cases + b * s->cfg.max_cases;
     float step_ms = 0.0f;
     cudaEventElapsedTime(&step_ms, s->step_t0[b], s->step_ev[b]);
@@ -1007,6 +1030,7 @@ void dg_server_destroy(dg_server* s) {
       if (kv.second.h_elist[b]) cudaFreeHost(kv.second.h_elist[b]);
       if (kv.second.h_slist[b]) cudaFreeHost(kv.second.h_slist[b]);
     }
+    if (kv.second.h_timeout) cudaFreeHost(kv.second.h_timeout);
     if (kv.second.fork) cudaEventDestroy(kv.second.fork);
     if (kv.second.join) cudaEventDestroy(kv.second.join);
   }
@@ -1076,12 +1100,17 @@ int dg_server_create(dg_server** out, const dg_server_config* cfg) {
     }
     P.ctx->cases = s->d_cases;
     P.ctx->n_case_slots = cfg->max_cases;
+    P.ctx->cfg.persistent = cfg->persistent ? 1 : 0;
     cudaError_t pe = cudaStreamCreateWithFlags(&P.branch, cudaStreamNonBlocking);
     if (pe == cudaSuccess) pe = cudaMalloc(&P.ctx->elem_list, sizeof(int) * cfg->pool_elems[N]);
     if (pe == cudaSuccess) pe = cudaMalloc(&P.ctx->side_list, sizeof(int) * 3 * cfg->pool_elems[N]);
     for (int b = 0; b < 2 && pe == cudaSuccess; ++b) {
       pe = cudaMallocHost(&P.h_elist[b], sizeof(int) * cfg->pool_elems[N]);
       if (pe == cudaSuccess) pe = cudaMallocHost(&P.h_slist[b], sizeof(int) * 3 * cfg->pool_elems[N]);
+    }
+    if (pe == cudaSuccess && cfg->persistent) {
+      pe = cudaMallocHost(&P.h_timeout, 2 * sizeof(int));
+      if (pe == cudaSuccess) P.h_timeout[0] = P.h_timeout[1] = 0;
     }
     if (pe == cudaSuccess) pe = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
     if (pe == cudaSuccess) pe = cudaEventCreateWithFlags(&P.join, cudaEventDisableTiming);

@@ -1318,6 +1318,8 @@ inline void vol_variant(const StageArgs& a, int epb, int pairs, cudaStream_t st)
 
 template <int N, int E>
 inline int felem_wave();
+template <int N>
+inline int persist_grid();
 
 template <int N, typename T>
 cudaError_t stage_set_attrs() {
@@ -1348,6 +1350,8 @@ cudaError_t stage_set_attrs() {
     // the capture of a step graph
     felem_wave<N, 0>();
     if constexpr (V::vol2) felem_wave<N, 2 * V::D>();
+    lift(k_fpersist<N>, FusedSmem<N>::bytes);
+    persist_grid<N>();
   }
   return cudaGetLastError();
 }
@@ -1373,6 +1377,68 @@ inline int felem_wave() {
   }
   return wave;
 }
+// blocks of the persistent kernel the GPU holds at once (its grid)
+template <int N>
+inline int persist_grid() {
+  static int grid = 0;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fpersist<N>, Shape<N>::THREADS,
+                                                      FusedSmem<N>::bytes) == cudaSuccess &&
+        sms > 0 && per > 0)
+      grid = sms * per;
+    else
+      grid = -1;
+  }
+  return grid;
+}
+
+// One persistent launch for all stages of a step (two-kernel FP32-bulk
+// stage); extra / spin: the barrier test hook and the wait limit in polls.
+template <int N>
+cudaError_t persist_launch(dg_ctx* c, int ns, const double* A, const double* B, const double* C, unsigned extra,
+                           unsigned spin) {
+  using S = Shape<N>;
+  StageArgs a = make_stage_args(c, c->U);
+  if (a.E == 0) return cudaSuccess;
+  a.Ut = c->Ut;
+  a.Urk = c->U;
+  a.dU = c->dU;
+  a.epilogue = 1;
+  const int nblk = (a.E + S::EPB - 1) / S::EPB;
+  const int cap = persist_grid<N>();
+  if (cap <= 0) return cudaErrorInvalidConfiguration;
+  const int grid = std::min(nblk, cap);
+  a.prefetch = c->cfg.prefetch ? grid : 0;  // the element this block takes next
+  PersistArgs p{};
+  p.ns = ns;
+  for (int s = 0; s < ns; ++s) p.A[s] = A[s], p.B[s] = B[s], p.C[s] = C[s];
+  p.bar = c->scal->bar;
+  p.timeout = &c->scal->timeout;
+  p.expect_extra = extra;
+  p.spin_limit = spin;
+  p.nblk = nblk;
+  cudaError_t e = cudaMemsetAsync(p.bar, 0, sizeof(unsigned) * 2, c->stream);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(S::THREADS);
+  cfg.dynamicSmemBytes = FusedSmem<N>::bytes;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;  // every block resident at once
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  prof_begin(c, PK_VOLUME);
+  e = cudaLaunchKernelEx(&cfg, k_fpersist<N>, a, p);
+  prof_end(c);
+  count_launch();
+  return e;
+}
+
 template <int N, int MODE, int E>
 inline void launch_felem(StageArgs a, int prefetch, cudaStream_t st) {
   using S = Shape<N, E>;
@@ -1695,6 +1761,10 @@ cudaError_t stage_autotune(dg_ctx* c, double* ms) {
   }                                                                                               \
   cudaError_t fprep_n##K(dg_ctx* c, const double* U, int64_t e0, int64_t E, cudaStream_t st) {    \
     return fprep_launch<K>(c, U, e0, E, st);                                                      \
+  }                                                                                               \
+  cudaError_t persist_n##K(dg_ctx* c, int ns, const double* A, const double* B, const double* C,    \
+                           unsigned extra, unsigned spin) {                                       \
+    return persist_launch<K>(c, ns, A, B, C, extra, spin);                                        \
   }
 
 #define DG_DISPATCH(N_, CALL)                      \

@@ -49,6 +49,11 @@ struct DevScalars {
   // the context's reference state, kept while dg_rhs evaluates another state
   double keep_ref[5];
   float keep_f_ref[4];
+  // grid-wide barrier of the persistent stage kernel (arrivals, generation;
+  // zeroed before each launch) and its sticky timeout flag
+  unsigned bar[2];
+  int timeout;
+  int pad2;
 };
 
 // Per-case data of a serving pool (device, one entry per case slot).
@@ -79,6 +84,7 @@ struct StageConfig {
   // four-kernel stage
   int stage_form = 0;
   int prefetch = 1;     // two-kernel stage: L2 prefetch of the next wave's element data (0: off)
+  int persistent = 0;   // two-kernel stage: one persistent launch per step for all stages (1)
 };
 
 // Per-stage launch parameters of the RHS kernels.

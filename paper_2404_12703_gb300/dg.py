@@ -31,7 +31,7 @@ SERVE_EXPORTS = ("dg_server_default_config", "dg_server_create", "dg_submit", "d
 EXPORTS = SERVE_EXPORTS + ("dg_default_params", "dg_init_mesh", "dg_set_stream", "dg_set_params", "dg_set_state",
            "dg_get_state", "dg_rhs", "dg_step", "dg_advance", "dg_autotune", "dg_set_config", "dg_get_config",
            "dg_set_sponge", "dg_node_coords", "dg_quadrature_weights", "dg_selftest_convert",
-           "dg_set_rk", "dg_set_rk_scheme", "dg_stage_form",
+           "dg_set_rk", "dg_set_rk_scheme", "dg_stage_form", "dg_selftest_wait_timeout",
            "dg_profile_step", "dg_time_step", "dg_kinetic", "dg_debug", "dg_sizes",
            "dg_destroy", "dg_error_string", "dg_last_error", "dg_launch_count", "dg_kinetic_noalloc",
            "dg_peak_probe")
@@ -84,7 +84,7 @@ def _bc_arrays(mesh):
 class ServerConfig(C.Structure):
     _fields_ = [("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double), ("dfl", C.c_double),
                 ("precision", C.c_int), ("max_cases", C.c_int), ("pool_elems", C.c_int64 * 8),
-                ("max_resident_dof", C.c_int64), ("priority_dof", C.c_int64)]
+                ("max_resident_dof", C.c_int64), ("priority_dof", C.c_int64), ("persistent", C.c_int)]
 
 
 class CaseDesc(C.Structure):
@@ -124,6 +124,7 @@ def load(path: str | None = None):
             "dg_set_config": (C.c_int, [vp, C.POINTER(C.c_int)]),
             "dg_get_config": (C.c_int, [vp, C.POINTER(C.c_int)]),
             "dg_stage_form": (C.c_int, [vp]),
+            "dg_selftest_wait_timeout": (C.c_int, [vp, C.c_uint]),
             "dg_profile_step": (C.c_int, [vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int64)]),
             "dg_time_step": (C.c_int, [vp, dp]),
             "dg_kinetic": (C.c_int, [vp, dp]),
@@ -439,22 +440,28 @@ class Solver:
         ub = _host_buf(np.ascontiguousarray(U_base, dtype=np.float64), 5 * sg.size, "U_base")
         _check(self._lib.dg_set_sponge(self._h, C.c_void_p(sg.ctypes.data), C.c_void_p(ub.ctypes.data)))
 
-    CONFIG_KEYS = ("lift_epb", "vol_epb", "vol_pairs", "side_block", "stage_form", "prefetch")
+    CONFIG_KEYS = ("lift_epb", "vol_epb", "vol_pairs", "side_block", "stage_form", "prefetch", "persistent")
     TUNE_KEYS = ("lift_D", "lift_2D", "vol_D", "vol_D_other_mapping", "vol_2D", "vol_2D_other_mapping",
                  "side_256", "side_128")
 
     def autotune(self):
         """Times the stage kernels' launch variants on the current state and
         keeps the fastest; returns (config, per-variant ms)."""
-        cfg = (C.c_int * 6)()
+        cfg = (C.c_int * 7)()
         ms = (C.c_double * 8)()
         _check(self._lib.dg_autotune(self._h, cfg, ms))
         return dict(zip(self.CONFIG_KEYS, list(cfg))), {k: (v if v >= 0 else None)
                                                         for k, v in zip(self.TUNE_KEYS, list(ms))}
 
-    def set_config(self, lift_epb=0, vol_epb=0, vol_pairs=-1, side_block=0, stage_form=0, prefetch=1):
-        cfg = (C.c_int * 6)(lift_epb, vol_epb, vol_pairs, side_block, stage_form, prefetch)
+    def set_config(self, lift_epb=0, vol_epb=0, vol_pairs=-1, side_block=0, stage_form=0, prefetch=1, persistent=0):
+        cfg = (C.c_int * 7)(lift_epb, vol_epb, vol_pairs, side_block, stage_form, prefetch, persistent)
         _check(self._lib.dg_set_config(self._h, cfg))
+
+    def selftest_wait_timeout(self, spin_polls=5000):
+        """Runs one persistent step launch whose grid-wide barriers wait for a
+        participant that does not exist (see dg_selftest_wait_timeout); returns
+        the library's status code (DG_ERR_TIMEOUT when the waits ran out)."""
+        return self._lib.dg_selftest_wait_timeout(self._h, int(spin_polls))
 
     def stage_form(self):
         """2: the two-kernel FP32-bulk stage; 4: the four-kernel stage."""
@@ -464,7 +471,7 @@ class Solver:
         return r
 
     def config(self):
-        cfg = (C.c_int * 6)()
+        cfg = (C.c_int * 7)()
         _check(self._lib.dg_get_config(self._h, cfg))
         return dict(zip(self.CONFIG_KEYS, list(cfg)))
 
@@ -530,7 +537,7 @@ class Server:
                  "nonfinite")
 
     def __init__(self, pool_elems=None, max_cases=64, precision=FP64, gamma=1.4, R=1.0, Pr=0.72, dfl=0.9,
-                 max_resident_dof=0, priority_dof=0):
+                 max_resident_dof=0, priority_dof=0, persistent=0):
         lib = load()
         self._lib = lib
         cfg = ServerConfig()
@@ -540,6 +547,7 @@ class Server:
         cfg.max_cases = max_cases
         cfg.max_resident_dof = int(max_resident_dof)
         cfg.priority_dof = int(priority_dof)
+        cfg.persistent = int(persistent)
         if pool_elems is not None:
             for N in range(8):
                 cfg.pool_elems[N] = int(pool_elems.get(N, 0))

@@ -153,3 +153,48 @@ def test_stage_form_selection():
     assert s.stage_form() == 2
     s.set_config(stage_form=1)
     assert s.stage_form() == 4
+
+
+@pytest.mark.parametrize("N", [3, 7])
+def test_persistent_launch_equals_per_kernel_launches(N):
+    """One persistent launch per step (side and element phases of every stage
+    separated by grid-wide barriers) runs the same per-side and per-element
+    arithmetic as one launch per kernel and stage: bitwise equal steps, with
+    the default scheme and with the 14-stage one."""
+    torch, dg = gpu_or_skip()
+    m = mesh(N, (4, 3, 5), seed=70 + N)
+    U0 = W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5), 1e-3, N)
+    for scheme in ("ck5", "ndb14"):
+        out = []
+        for persistent in (0, 1):
+            s = dg.Solver(m, precision=dg.FP32_BULK)
+            s.set_config(persistent=persistent)
+            s.set_rk_scheme(scheme)
+            s.set_state(U0)
+            s.step(4)
+            out.append(s.get_state())
+            s.close()
+        assert out[0][1] == out[1][1]
+        np.testing.assert_array_equal(out[0][0], out[1][0])
+
+
+def test_persistent_waits_give_up():
+    """Failure detection without a GPU fault: a persistent step launch whose
+    grid-wide barriers wait for a participant that never comes gives up after
+    its bounded wait and reports DG_ERR_TIMEOUT; the state is untouched and
+    the context steps on as if nothing happened."""
+    torch, dg = gpu_or_skip()
+    N = 3
+    m = mesh(N, (4, 4, 4), seed=5)
+    U0 = W.tgv_state(m["xyz"]).reshape(m["E"], -1, 5)
+    a = dg.Solver(m, precision=dg.FP32_BULK)
+    a.set_config(persistent=1)
+    a.set_state(U0)
+    assert a.selftest_wait_timeout(2000) == dg.DG_ERR_TIMEOUT
+    U, t = a.get_state()                       # no timeout left behind
+    np.testing.assert_array_equal(U, U0.reshape(U.shape))
+    a.step(3)
+    b = dg.Solver(m, precision=dg.FP32_BULK)
+    b.set_state(U0)
+    b.step(3)
+    np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])

@@ -218,3 +218,19 @@ def test_a_nonfinite_case_is_isolated(prec):
             assert st["nonfinite"] == 0 and st["t_final"] == t_end
             np.testing.assert_array_equal(U, alone[i])
     srv.close()
+
+
+def test_fp32_bulk_persistent_pools_match_per_kernel_pools():
+    """Serving pools that run each step's stages as one persistent launch give
+    the per-kernel pools' results bit for bit."""
+    torch, dg = gpu_or_skip()
+    t_end = 0.05
+    built = [make(*c) for c in CASES]
+    out = []
+    for persistent in (0, 1):
+        srv = dg.Server(POOLS, max_cases=8, precision=dg.FP32_BULK, persistent=persistent)
+        tickets = [srv.submit(m, U0, t_end, mu=mu) for m, U0, mu in built]
+        out.append([srv.wait(tk)[0] for tk in tickets])
+        srv.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)

@@ -448,7 +448,9 @@ int dg_peak_probe(int kind, int iters, double* flops_per_s, double* ms, void* st
                             neighbour face, 1 if this side is the master),
                             out1 = int32 [E][6][n^2] partner face node
    what = DG_DEBUG_GRAD:    out0 = lifted gradients [E][node][4][3] of the
-                            last dg_rhs / stage (d(u,v,w,T)/dx_c)
+                            last dg_rhs / stage (d(u,v,w,T)/dx_c); in the
+                            two-kernel FP32-bulk stage (dg_stage_form 2),
+                            of the last dg_rhs only
    what = DG_DEBUG_FSTAR:   out0 = surface flux times s-hat [E][6][n^2][5]
                             on master faces (zero on slave faces), face node
                             p + n q in the master's face frame, last dg_rhs

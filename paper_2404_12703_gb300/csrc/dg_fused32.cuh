@@ -156,16 +156,17 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, const v
 // the n x n matrix Dhat (rows read as broadcast float4s) to them; the three
 // sums of each node go to the W planes (written for the first direction,
 // added for the others).  Qs: the element's q planes (u, v, w, T'); J4: its
-// halved metrics; W: its 12 workspace planes; sDr: Dhat with rows padded to
-// n4 floats.  Every thread of the block calls it (it holds barriers); W may
-// be reused after the caller's next barrier.
+// halved metrics; W: its 12 workspace planes; sDr2: 2 Dhat with rows padded
+// to n4 floats (the factor 2 undoes the halving of the metrics, exactly:
+// (2 Dhat) (J/2 q) rounds as Dhat (J q)).  Every thread of the block calls it
+// (it holds barriers); W may be reused after the caller's next barrier.
 // ---------------------------------------------------------------------------
 // FACES: only the sums at the element's face nodes are needed (the
 // epilogue): a line inside the element in both other directions computes its
 // two end nodes only; every face node lies on a line that computes it for
 // each direction.
 template <int n, int n4, bool FACES = false>
-__device__ __forceinline__ void lift_volume(const float* Qs, const float4* J4, float* W, const float* sDr, int t,
+__device__ __forceinline__ void lift_volume(const float* Qs, const float4* J4, float* W, const float* sDr2, int t,
                                             float acc[12]) {
   constexpr int n2 = n * n, n3 = n2 * n, Pn = n3 + n2;
 #pragma unroll 1
@@ -180,9 +181,9 @@ __device__ __forceinline__ void lift_volume(const float* Qs, const float4* J4, f
         const int v = pad_idx<n>(base + al * sd);
         const float q = Qs[qv * Pn + v];
         const float4 j = J4[d * Pn + v];
-        P0[al] = (2.0f * j.x) * q;  // exact: the halving undone
-        P1[al] = (2.0f * j.y) * q;
-        P2[al] = (2.0f * j.z) * q;
+        P0[al] = j.x * q;
+        P1[al] = j.y * q;
+        P2[al] = j.z * q;
       }
       const bool inner = FACES && lp > 0 && lp < n - 1 && lq > 0 && lq < n - 1;
 #pragma unroll
@@ -191,7 +192,7 @@ __device__ __forceinline__ void lift_volume(const float* Qs, const float4* J4, f
         float r[n4];
 #pragma unroll
         for (int c = 0; c < n4; c += 4) {
-          const float4 v4 = *reinterpret_cast<const float4*>(sDr + i * n4 + c);
+          const float4 v4 = *reinterpret_cast<const float4*>(sDr2 + i * n4 + c);
           r[c] = v4.x, r[c + 1] = v4.y, r[c + 2] = v4.z, r[c + 3] = v4.w;
         }
         float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
@@ -318,11 +319,11 @@ template <int N>
 __global__ void __launch_bounds__(Shape<N>::THREADS) k_fprep(StageArgs a) {
   using S = Shape<N>;
   using L = FusedSmem<N>;
-  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  constexpr int n = S::n, n3 = S::n3, EPB = S::EPB;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* sDs = reinterpret_cast<float*>(reinterpret_cast<double*>(smraw) + L::n2d);
   float* sDh = sDs + L::n2p;
-  float* sDr = sDh + L::n2p;  // [n][n4] Dhat, rows padded
+  float* sDr = sDh + L::n2p;  // [n][n4] 2 Dhat, rows padded (lift_volume)
   float* base = sDr + n * L::n4;
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
   float* mine = base + (size_t)le * L::per_elem_f;
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_fprep(StageArgs a) {
   const CaseParams cp = case_params(a, ce);
   for (int k = threadIdx.x; k < n * L::n4; k += blockDim.x) {
     const int i = k / L::n4, al = k % L::n4;
-    sDr[k] = al < n ? (float)a.ops->Dhat[i * n + al] : 0.0f;
+    sDr[k] = al < n ? 2.0f * (float)a.ops->Dhat[i * n + al] : 0.0f;
   }
   load_face_normals<n>(a, e, t, sSn);
   double U[5];
@@ -488,358 +489,28 @@ __global__ void __launch_bounds__(256) k_fflux(StageArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// k_felem: one stage of one element (FP32-bulk arithmetic, FP64 state)
+// k_felem: one stage of one element block (the work is in dg_felem_body.cuh)
 // ---------------------------------------------------------------------------
-// MODE 0: writes Ut; MODE 1: the RK update, then (a.epilogue) the face data
-// of the updated state.  a.prefetch > 0: each block first asks L2 for the
-// state, RK register and metrics of the element a.prefetch blocks further on
-// (the next wave on the GPU), so that wave's loads find them in L2.
-// the coefficients of one low-storage RK stage
-struct StageCoef {
-  double A, B, C;  // dU = A dU + dt Ut, U += B dU; stage time t + C dt
-  float fA;        // A in FP32 (the FP32 register update)
-  int first;       // the first stage (A is not used)
+// the coefficients of one low-storage RK stage, read where they are used
+// (dU = A dU + dt Ut, U += B dU; stage time t + C dt; fA: A in FP32; first:
+// the first stage, whose A is not used): from the launch arguments of a
+// per-stage launch, or from the scheme of a persistent launch
+struct CoefOfStage {
+  const StageArgs& a;
+  __device__ __forceinline__ double A() const { return a.rkA; }
+  __device__ __forceinline__ double B() const { return a.rkB; }
+  __device__ __forceinline__ double C() const { return a.rkC; }
+  __device__ __forceinline__ float fA() const { return a.f_rkA; }
+  __device__ __forceinline__ bool first() const { return a.first_stage != 0; }
 };
-
-// the work of element block blk (elements blk * EPB ... of the element list)
-template <int N, int MODE, int EPB_>
-__device__ __forceinline__ void felem_body(const StageArgs& a, const StageCoef& sc, unsigned blk,
-                                           unsigned char* smraw) {
-  using S = Shape<N, EPB_>;
-  using L = FusedSmem<N, EPB_>;
-  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
-  double* sVi = reinterpret_cast<double*>(smraw);  // [n2] Vinv (FP64)
-  float* sDs = reinterpret_cast<float*>(sVi + L::n2d);
-  float* sDh = sDs + L::n2p;
-  float* sDr = sDh + L::n2p;  // [n][n4] Dhat, rows padded
-  float* base = sDr + n * L::n4;
-  const int le = threadIdx.x / n3, t = threadIdx.x % n3;
-  float* mine = base + (size_t)le * L::per_elem_f;
-  float4* P4 = reinterpret_cast<float4*>(mine);                   // [n3] (rho, u, v, w) / 2
-  float4* Q4 = P4 + n3;                                           // [n3] (p' / 2, H' / 2, T', 0)
-  float4* J4 = reinterpret_cast<float4*>(mine + L::offJ);         // [3][Pn] (Ja^d) / 2, padded index
-  float* Qs = mine + L::offQ;                                     // [4][Pn] u, v, w, T', padded index
-  float* Wk = mine + L::offW;                                     // [12][Pn] workspace
-  float4* G4 = reinterpret_cast<float4*>(Wk);
-  float4* sSn = reinterpret_cast<float4*>(mine + L::offN);        // [6][n2] face normals and signs
-  constexpr int Pn = L::Pn;
-  // slots past the last element redo the last element, free slots of a
-  // serving pool compute on what they hold; neither stores
-  const int ei = (int)blk * EPB + le < a.E ? (int)blk * EPB + le : a.E - 1;
-  const int el = a.elem_list ? a.elem_list[ei] : ei;
-  const int ce = a.elem_case ? a.elem_case[el] : 0;
-  // elements of cases that finished or sit this step out (time step 0) keep
-  // their state and face data; a block made only of such slots leaves at once
-  const bool valid = (int)blk * EPB + le < a.E && ce >= 0 && !(a.cases && a.cases[ce].dt == 0.0);
-  if (a.elem_case && __syncthreads_and(!valid)) return;
-  const int e = DG_CHK(el >= 0 && t < n3 && le < EPB, el) ? el : 0;
-  const CaseParams cp = case_params(a, ce);
-  if (a.prefetch > 0 && threadIdx.x == 0 && !a.elem_list) {
-    const int64_t e2 = (int64_t)(blk + a.prefetch) * EPB;
-    if (e2 < a.E) {
-      const int64_t ne = min((int64_t)EPB, (int64_t)a.E - e2);
-      const size_t ub = sizeof(double) * 5 * n3;
-      prefetch_l2(a.U + e2 * 5 * n3, ub * ne, a.U, a.U + (size_t)a.E * 5 * n3);
-      if (MODE == 1 && !sc.first) {
-        const float* d32 = reinterpret_cast<const float*>(a.dU);
-        prefetch_l2(d32 + e2 * 5 * n3, sizeof(float) * 5 * n3 * ne, d32, d32 + (size_t)a.E * 5 * n3);
-      }
-      prefetch_l2(a.metric32 + e2 * 10 * n3, sizeof(float) * 10 * n3 * ne, a.metric32,
-                  a.metric32 + (size_t)a.E * 10 * n3);
-    }
-  }
-  // this element's later gathers, asked of L2 now: its six sides' q* and f*
-  // records (read after the lifting and in SurfInt) and its RK register (read
-  // by the update), so that those reads do not each wait on HBM
-  if (t < 6) {
-    const int sf = es_side(a.elem_side[(size_t)e * 6 + t]);
-    if (a.viscous)
-      prefetch_l2(a.qs32 + (size_t)sf * n2 * 4, sizeof(float) * 4 * n2, a.qs32, a.qs32 + (size_t)a.S * n2 * 4);
-    prefetch_l2(a.fstar32 + (size_t)sf * 5 * n2, sizeof(float) * 5 * n2, a.fstar32, a.fstar32 + (size_t)a.S * 5 * n2);
-  } else if (t == 6 && MODE == 1 && !sc.first) {
-    const float* d32 = reinterpret_cast<const float*>(a.dU);
-    prefetch_l2(d32 + (size_t)e * 5 * n3, sizeof(float) * 5 * n3, d32, d32 + (size_t)a.E * 5 * n3);
-  }
-  for (int k = threadIdx.x; k < n2; k += blockDim.x) {
-    sDs[k] = (float)a.ops->Dsplit[k];
-    sDh[k] = (float)a.ops->Dhat[k];
-    sVi[k] = a.ops->Vinv[k];
-  }
-  for (int k = threadIdx.x; k < n * L::n4; k += blockDim.x) {
-    const int i = k / L::n4, al = k % L::n4;
-    sDr[k] = al < n ? (float)a.ops->Dhat[i * n + al] : 0.0f;
-  }
-  load_face_normals<n>(a, e, t, sSn);
-  double U[5];
-  double p_full;
-  {
-    const double* u = a.U + (size_t)e * 5 * n3 + t;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
-  }
-  // the FP64 pressure only for the indicator (one FP64 addition less otherwise)
-  const SPrim<float> me = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp, a.shock ? &p_full : nullptr);
-  // halved values: every arithmetic mean of the two-point flux is one addition
-  P4[t] = make_float4(0.5f * me.rho, 0.5f * me.u, 0.5f * me.v, 0.5f * me.w);
-  Q4[t] = make_float4(0.5f * me.p, 0.5f * me.H, me.Tt, 0.0f);
-  const int vp = pad_idx<n>(t);
-  Qs[vp] = me.u, Qs[Pn + vp] = me.v, Qs[2 * Pn + vp] = me.w, Qs[3 * Pn + vp] = me.Tt;
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-    J4[d * Pn + vp] = make_float4(0.5f * metric_at<float>(a, e, 3 * d, t, n3),
-                                  0.5f * metric_at<float>(a, e, 3 * d + 1, t, n3),
-                                  0.5f * metric_at<float>(a, e, 3 * d + 2, t, n3), 0.0f);
-  const float Jinv = metric_at<float>(a, e, 9, t, n3);
-  __syncwarp();
-  __syncthreads();
-  const int idx[3] = {t % n, (t / n) % n, t / n2};  // indexed by unrolled (constant) d only
-  float tau[6] = {0, 0, 0, 0, 0, 0}, W[3] = {0, 0, 0};
-  // ---- BR1 lifting of the stage's state: volume part, then q* of the six faces ----
-  if (a.viscous) {
-    float g[12];
-    lift_volume<n, L::n4>(Qs, J4, Wk, sDr, t, g);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int id = idx[d];
-      if (id != 0 && id != n - 1) continue;
-      const int f = 2 * d + (id == n - 1 ? 1 : 0);
-      int p, qq;
-      face_pq(d, idx, p, qq);
-      const int es = a.elem_side[(size_t)e * 6 + f];
-      int pm = p, qm = qq;
-      if (es_slave(es)) flip_to_master<n>(es_flip(es), p, qq, pm, qm);
-      if (!DG_CHK(es_side(es) >= 0 && es_side(es) < a.S && pm >= 0 && pm < n && qm >= 0 && qm < n, es_side(es)))
-        continue;
-      const float4 qs = ld4(a.qs32 + ((size_t)es_side(es) * n2 + pm + n * qm) * 4);
-      const float4 sn = sSn[f * n2 + p + n * qq];
-      const float qa[4] = {qs.x, qs.y, qs.z, qs.w};
-#pragma unroll
-      for (int qv = 0; qv < 4; ++qv) {
-        g[qv * 3 + 0] += sn.w * (qa[qv] * sn.x);
-        g[qv * 3 + 1] += sn.w * (qa[qv] * sn.y);
-        g[qv * 3 + 2] += sn.w * (qa[qv] * sn.z);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 12; ++k) g[k] *= Jinv;
-    float vmu, vlam;
-    visc_coeffs<float>(a, cp, me.Tt, vmu, vlam);
-    viscous_parts(g, me.u, me.v, me.w, vmu, vlam, tau, W);
-  }
-  // ---- split-form KEP volume integral, one node per thread over its partners ----
-  float accC[5] = {0, 0, 0, 0, 0};  // convective DG volume term
-  float acc[5] = {0, 0, 0, 0, 0};   // viscous volume + surface terms
-#pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    const int id = dir_index<n>(t, d), sd = dir_stride<n>(d), bse = t - id * sd;
-    const float4 ai = P4[t];
-    const float4 bi = Q4[t];
-    const float4 ji = J4[d * Pn + vp];
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
-#pragma unroll
-    for (int al = 0; al < n; ++al) {
-      if (al == id) continue;
-      const int va = bse + al * sd;
-      if (!DG_CHK(va >= 0 && va < n3, va)) continue;
-      const float4 aa = P4[va];
-      const float4 ba = Q4[va];
-      const float4 ja = J4[d * Pn + pad_idx<n>(va)];
-      const float m0 = ji.x + ja.x, m1 = ji.y + ja.y, m2 = ji.z + ja.z;
-      const float rho = ai.x + aa.x;
-      const float u0 = ai.y + aa.y, u1 = ai.z + aa.z, u2 = ai.w + aa.w;
-      const float pp = bi.x + ba.x;
-      const float H = bi.y + ba.y;
-      const float fr = rho * (u0 * m0 + u1 * m1 + u2 * m2);
-      const float dv = sDs[id * n + al];
-      s0 += dv * fr;
-      s1 += dv * (fr * u0 + pp * m0);
-      s2 += dv * (fr * u1 + pp * m1);
-      s3 += dv * (fr * u2 + pp * m2);
-      s4 += dv * (fr * H);
-    }
-    if (d == 0) {
-      accC[0] = s0, accC[1] = s1, accC[2] = s2, accC[3] = s3, accC[4] = s4;
-    } else {
-      accC[0] += s0, accC[1] += s1, accC[2] += s2, accC[3] += s3, accC[4] += s4;
-    }
-  }
-  // ---- viscous volume term: collocated weak form, per direction ----
-  if (a.viscous) {
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-      {
-        const float4 jj = J4[d * Pn + vp];
-        const float nv[3] = {2.0f * jj.x, 2.0f * jj.y, 2.0f * jj.z};
-        float fv[4];
-        viscous_flux_n(tau, W, nv, fv);
-        G4[t] = make_float4(fv[0], fv[1], fv[2], fv[3]);
-      }
-      __syncwarp();
-      __syncthreads();
-      {
-        const int id = dir_index<n>(t, d), sd = dir_stride<n>(d), bse = t - id * sd;
-#pragma unroll
-        for (int al = 0; al < n; ++al) {
-          const float c = sDh[id * n + al];
-          const float4 gv = G4[bse + al * sd];
-          acc[1] -= c * gv.x;
-          acc[2] -= c * gv.y;
-          acc[3] -= c * gv.z;
-          acc[4] -= c * gv.w;
-        }
-      }
-      __syncwarp();
-      __syncthreads();
-    }
-  }
-  // ---- shock capturing: indicator and FV sub-cell blending (Sec. 2.3) ----
-  if (a.shock) {
-    double al;
-    if (a.alpha_force >= 0) {
-      al = a.alpha_force;
-    } else {
-      double* X1 = reinterpret_cast<double*>(Wk);  // the workspace is free here
-      al = element_alpha<n>(U[0] * p_full, X1, X1 + n3, X1 + 2 * n3, sVi, t, a.alpha_min, a.alpha_max);
-    }
-    if (valid && t == 0) a.alpha[e] = al;
-    if (__syncthreads_or(al > 0)) {
-      float vfv[5] = {0, 0, 0, 0, 0};
-      float* G = Wk;
-      const double* FVm = a.fvmetric + (size_t)e * 3 * (n - 1) * 3 * n2;
-#pragma unroll 1
-      for (int d = 0; d < 3; ++d) {
-        const int id = dir_index<n>(t, d), sd = dir_stride<n>(d);
-        const bool right = id < n - 1;
-        const int line = d == 0 ? idx[1] + n * idx[2] : (d == 1 ? idx[0] + n * idx[2] : idx[0] + n * idx[1]);
-        const double* fm = FVm + (size_t)(d * (n - 1) + (right ? id : n - 2)) * 3 * n2 + line;
-        const double mv[3] = {fm[0], fm[n2], fm[2 * n2]};
-        const double sAd = sqrt(mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2]);
-        const float nu[3] = {float(mv[0] / sAd), float(mv[1] / sAd), float(mv[2] / sAd)};
-        const int nb = right ? t + sd : t;
-        double UR[5];
-        const double* ur = a.U + (size_t)e * 5 * n3 + nb;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) UR[k] = ur[k * n3];
-        const SPrim<float> qR = shifted_prim<float>(UR, a.gm1, a.Rinv, cp);
-        float fb[5];
-        lf_flux_s(me, qR, nu, a.f_gamma, cp.fpr, fb);
-        if (right) {
-#pragma unroll
-          for (int k = 0; k < 5; ++k) G[k * n3 + t] = fb[k] * float(sAd);
-        }
-        __syncwarp();
-        __syncthreads();
-        if (right) {
-#pragma unroll
-          for (int k = 0; k < 5; ++k) vfv[k] += G[k * n3 + t] / float(a.ops->w[id]);
-        }
-        if (id > 0) {
-          const int nl = t - sd;
-#pragma unroll
-          for (int k = 0; k < 5; ++k) vfv[k] -= G[k * n3 + nl] / float(a.ops->w[id]);
-        }
-        __syncwarp();
-        __syncthreads();
-      }
-      if (al > 0) {
-        const float alt = float(al);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) accC[k] = (1 - alt) * accC[k] + alt * vfv[k];
-      }
-    }
-  }
-  // ---- SurfInt: face nodes receive +-f* lhat ----
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int id = idx[d];
-    if (id != 0 && id != n - 1) continue;
-    const int f = 2 * d + (id == n - 1 ? 1 : 0);
-    int p, qq;
-    face_pq(d, idx, p, qq);
-    const int es = a.elem_side[(size_t)e * 6 + f];
-    int pm = p, qm = qq;
-    if (es_slave(es)) flip_to_master<n>(es_flip(es), p, qq, pm, qm);
-    if (!DG_CHK(es_side(es) >= 0 && es_side(es) < a.S && pm >= 0 && pm < n && qm >= 0 && qm < n, es_side(es)))
-      continue;
-    const float sg = sSn[f * n2 + p + n * qq].w;
-    const float* Fs = a.fstar32 + (size_t)es_side(es) * 5 * n2 + pm + n * qm;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) acc[k] += sg * Fs[k * n2];
-  }
-  // ---- ApplyJac; the energy equation gets H_ref times the mass equation back ----
-  float ut32[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) ut32[k] = -(accC[k] + acc[k]) * Jinv;
-  // the FP64 tendency: for dg_rhs, and in a stage with sources
-  const bool sources = a.sponge_sigma || a.source;
-  double Ut[5];
-  if (MODE == 0 || sources) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) Ut[k] = f64_of(ut32[k]);
-    Ut[4] += cp.Hr * Ut[0];
-    if (a.sponge_sigma) {  // sponge source -sigma (U - U_base), FP64
-      const double sg = a.sponge_sigma[(size_t)e * n3 + t];
-      const double* ub = a.sponge_base + (size_t)e * 5 * n3 + t;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) Ut[k] -= sg * (U[k] - ub[k * n3]);
-    }
-    if (a.source) {  // manufactured-solution source, FP64
-      double Q[5];
-      const double ts = MODE == 0 ? a.scal->t : a.scal->t - (1.0 - sc.C) * a.scal->dt;
-      mms_source(a, a.xyzs + ((size_t)e * n3 + t) * 3, ts, Q);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) Ut[k] += Q[k];
-    }
-  }
-  if constexpr (MODE == 0) {
-    if (valid) {
-      double* o = a.Ut + (size_t)e * 5 * n3 + t;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) o[k * n3] = Ut[k];
-    }
-  } else {
-    // RK update.  This stage form keeps the RK register in FP32 (the state
-    // stays FP64): dU = A dU + dt Ut in FP32, U += B dU in FP64.  The
-    // register is O(dt |Ut|) and rounds at the level of the FP32 fluxes
-    // already in Ut; the energy tendency's H_ref part is added in FP32, its
-    // rounding far below the FP32 error that Ut_rho already carries times H_ref.
-    float utf[5];
-    if (sources) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) utf[k] = f32_rn(Ut[k]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) utf[k] = ut32[k];
-      utf[4] = ut32[4] + cp.fHr * ut32[0];
-    }
-    const float dtf = f32_rn(case_dt(a, ce));
-    float* du = reinterpret_cast<float*>(a.dU) + (size_t)e * 5 * n3 + t;
-    double* uo = a.Urk + (size_t)e * 5 * n3 + t;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      const float r = sc.first ? dtf * utf[k] : fmaf(sc.fA, du[k * n3], dtf * utf[k]);
-      U[k] += sc.B * f64_of(r);  // the updated state
-      if (valid) {
-        du[k * n3] = r;
-        uo[k * n3] = U[k];
-      }
-    }
-    if (a.epilogue) {
-      // ---- the face data of the updated state for the next stage ----
-      const SPrim<float> mn = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp);
-      __syncwarp();
-      __syncthreads();  // the workspace is read by no thread any more
-      face_epilogue<N>(a, cp, e, t, valid, mn, Jinv, J4, Qs, Wk, sDr, sSn);
-    }
-  }
-}
 
 template <int N, int MODE, int EPB_ = 0>
 __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::template vol_min_blocks<float>())
     k_felem(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const StageCoef sc{a.rkA, a.rkB, a.rkC, a.f_rkA, a.first_stage};
-  felem_body<N, MODE, EPB_>(a, sc, blockIdx.x, smraw);
+  const unsigned blk = blockIdx.x;
+  const CoefOfStage sc{a};
+#include "dg_felem_body.cuh"
 }
 
 // ---------------------------------------------------------------------------
@@ -852,6 +523,18 @@ __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS, Shape<N, EPB_>::templ
 // participant ends the launch with an error the host reads
 // (DG_ERR_TIMEOUT) instead of a hang.
 // ---------------------------------------------------------------------------
+struct PersistArgs;
+// the coefficients of stage st of a persistent launch's scheme
+struct CoefOfScheme {
+  const PersistArgs& p;
+  int st;
+  __device__ __forceinline__ double A() const;
+  __device__ __forceinline__ double B() const;
+  __device__ __forceinline__ double C() const;
+  __device__ __forceinline__ float fA() const { return (float)A(); }
+  __device__ __forceinline__ bool first() const { return st == 0; }
+};
+
 struct PersistArgs {
   int ns;                           // stages
   double A[32], B[32], C[32];       // the low-storage scheme
@@ -861,6 +544,10 @@ struct PersistArgs {
   unsigned spin_limit;              // polls of 200 ns before a barrier wait gives up
   int nblk;                         // element blocks of the element phase
 };
+
+__device__ __forceinline__ double CoefOfScheme::A() const { return p.A[st]; }
+__device__ __forceinline__ double CoefOfScheme::B() const { return p.B[st]; }
+__device__ __forceinline__ double CoefOfScheme::C() const { return p.C[st]; }
 
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, int* flag, unsigned limit) {
   __shared__ int ok;
@@ -906,9 +593,10 @@ __global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::template vol_min_
          tid += (int64_t)gridDim.x * blockDim.x)
       fflux_body<N>(a, tid);
     if (!grid_barrier(p.bar, expected, p.timeout, p.spin_limit)) return;
-    const StageCoef sc{p.A[st], p.B[st], p.C[st], (float)p.A[st], st == 0};
     for (unsigned blk = blockIdx.x; blk < (unsigned)p.nblk; blk += gridDim.x) {
-      felem_body<N, 1, 0>(a, sc, blk, smraw);
+      constexpr int MODE = 1, EPB_ = 0;
+      const CoefOfScheme sc{p, st};
+#include "dg_felem_body.cuh"
       __syncwarp();
       __syncthreads();  // the next element reuses the shared memory
     }

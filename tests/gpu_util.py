@@ -69,5 +69,16 @@ def parity_check(err, bound, floor):
     assert np.all(err <= bound), {"err": err, "bound": bound, "floor": floor, "gpu_to_floor": ratio}
 
 
+def rk_stage_weight_sum(A, B):
+    """sum_i |b_i| over the Butcher weights of a 2N-storage scheme
+    (dU_j = A_j dU_{j-1} + dt L_j, U_j = U_{j-1} + B_j dU_j): stage i's
+    right-hand side enters the step with b_i = sum_{j >= i} B_j prod_{k=i+1..j} A_k,
+    so a rounding error in each stage's right-hand side reaches the state
+    amplified by up to this sum (1 when every b_i >= 0)."""
+    s = len(A)
+    b = [sum(B[j] * float(np.prod(A[i + 1:j + 1])) for j in range(i, s)) for i in range(s)]
+    return float(np.sum(np.abs(b)))
+
+
 def mesh(N, nel, curved=0.1, seed=20240419, **kw):
     return W.box_mesh(N, nel, curved=curved, seed=seed, **kw)

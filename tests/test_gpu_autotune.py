@@ -20,17 +20,19 @@ pytestmark = pytest.mark.gpu
 
 def _variants(N, fp64, form=0):
     """Launch configurations (lift and volume elements per block, mapping, side
-    block, stage form, prefetch).  FP32-bulk form 0 is the two-kernel stage on
-    these periodic meshes (elements per block of its element kernel, side
-    block, L2 prefetch on or off); form 1 the four-kernel stage."""
+    block, stage form, prefetch, launch form).  FP32-bulk form 0 is the
+    two-kernel stage on these periodic meshes (elements per block of its
+    element kernel, side block, L2 prefetch on or off); form 1 the
+    four-kernel stage; the launch form stays per kernel (the persistent form
+    has its own tests)."""
     n3 = (N + 1) ** 3
     D = 1 if n3 >= 256 else 256 // n3
     lifts = [D] + ([2 * D] if 2 * D * n3 <= 1024 else [])
     vols = [D] + ([2 * D] if 2 * D * n3 <= 512 else [])
     maps = [1, 0] if fp64 else [0]
     if not fp64 and form == 0:
-        return [(D, ve, 0, sb, 0, pf) for ve in vols for sb in (256, 128) for pf in (1, 0)]
-    return [(le, ve, pr, sb, form, 1) for le in lifts for ve in vols for pr in maps for sb in (256, 128)]
+        return [(D, ve, 0, sb, 0, pf, 0) for ve in vols for sb in (256, 128) for pf in (1, 0)]
+    return [(le, ve, pr, sb, form, 1, 0) for le in lifts for ve in vols for pr in maps for sb in (256, 128)]
 
 
 def _two_steps(s, U0, dt):
@@ -105,7 +107,8 @@ def test_invalid_configurations_are_refused():
     torch, dg = gpu_or_skip()
     m = mesh(7, (3, 3, 3))
     s = dg.Solver(m)
-    for cfg in [(3, 0, -1, 0), (0, 2, -1, 0), (0, 0, 2, 0), (0, 0, -1, 64), (0, 0, -1, 0, 2), (0, 0, -1, 0, 0, 3)]:
+    for cfg in [(3, 0, -1, 0), (0, 2, -1, 0), (0, 0, 2, 0), (0, 0, -1, 64), (0, 0, -1, 0, 2), (0, 0, -1, 0, 0, 3),
+                (0, 0, -1, 0, 0, 1, 2)]:
         with pytest.raises(dg.DgError) as ei:
             s.set_config(*cfg)
         assert ei.value.code == dg.DG_ERR_ARG

@@ -57,9 +57,13 @@ def test_rhs_against_oracle_and_four_kernel_stage(N, nel, Ma, kw):
     ref = O.Mesh(N, m["xyz"], m["period"]).rhs(U, oracle_params(a.params))
     assert np.all(rel_err(Ua, ref) <= 2e-4), rel_err(Ua, ref)
     assert np.all(rel_err(Ua, Ub) <= 2e-5), rel_err(Ua, Ub)
-    # the face fluxes, face by face
+    # the face fluxes, face by face, and the lifted gradients node by node
     np.testing.assert_allclose(a.debug("fstar"), b.debug("fstar"), rtol=0,
                                atol=2e-5 * np.abs(b.debug("fstar")).max())
+    if a.params.viscous:
+        ga, gb = a.debug("grad"), b.debug("grad")
+        assert np.abs(ga).max() > 0
+        np.testing.assert_allclose(ga, gb, rtol=0, atol=2e-5 * np.abs(gb).max())
 
 
 def test_free_stream():

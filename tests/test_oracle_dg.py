@@ -274,6 +274,24 @@ def test_fourteen_stage_scheme():
     assert 3.7 < math.log2(e1 / e2) < 4.8, math.log2(e1 / e2)
 
 
+def test_stage_weight_sums():
+    """The amplification of stage rounding errors by the schemes' Butcher
+    weights (gpu_util.rk_stage_weight_sum, which bounds the FP32-bulk
+    fourteen-stage parity test) against the Butcher weights formed as a
+    matrix product: 1 for the five-stage scheme (all weights positive),
+    98.6 for the fourteen-stage one, whose weights b_12, b_13, b_14 =
+    37.2, -39.1, 5.5 cancel on stage derivatives taken at nearly equal times
+    (c = 0.8605, 0.8627, 0.8734)."""
+    from gpu_util import rk_stage_weight_sum
+    for coeffs, lo, hi in ((O.rk_coeffs(), 1.0 - 1e-14, 1.0 + 1e-14), (O.rk14_coeffs(), 98.0, 99.0)):
+        A, B, c = coeffs
+        _, b = _butcher(A, B)
+        assert abs(rk_stage_weight_sum(A, B) - np.abs(b).sum()) < 1e-12
+        assert lo < np.abs(b).sum() < hi
+    _, b = _butcher(*O.rk14_coeffs()[:2])
+    np.testing.assert_allclose(b[11:], [37.2, -39.1, 5.5], rtol=0, atol=0.05)
+
+
 def test_time_step_closed_form():
     """Cartesian element of size h, uniform state: lambda_c = sum_d (|u_d| + c) 2/h."""
     N = 4

@@ -34,6 +34,9 @@ do {
     float* Wk = mine + L::offW;                                     // [12][Pn] workspace
     float4* G4 = reinterpret_cast<float4*>(Wk);
     float4* sSn = reinterpret_cast<float4*>(mine + L::offN);        // [6][n2] face normals and signs
+    float4* sQst = reinterpret_cast<float4*>(mine + L::offQS);      // [6][n2] q* of the six sides
+    float* sFst = mine + L::offFS;                                  // [5][6 n2] f* of the six sides
+    float* sDU = mine + L::offDU;                                   // [5][n3] the RK register
     constexpr int Pn = L::Pn;
     // slots past the last element redo the last element, free slots of a
     // serving pool compute on what they hold; neither stores
@@ -46,31 +49,24 @@ do {
     if (a.elem_case && __syncthreads_and(!valid)) break;
     const int e = DG_CHK(el >= 0 && t < n3 && le < EPB, el) ? el : 0;
     const CaseParams cp = case_params(a, ce);
-    if (a.prefetch > 0 && threadIdx.x == 0 && !a.elem_list) {
-      const int64_t e2 = (int64_t)(blk + a.prefetch) * EPB;
-      if (e2 < a.E) {
-        const int64_t ne = min((int64_t)EPB, (int64_t)a.E - e2);
-        const size_t ub = sizeof(double) * 5 * n3;
-        prefetch_l2(a.U + e2 * 5 * n3, ub * ne, a.U, a.U + (size_t)a.E * 5 * n3);
-        if (MODE == 1 && !sc.first()) {
-          const float* d32 = reinterpret_cast<const float*>(a.dU);
-          prefetch_l2(d32 + e2 * 5 * n3, sizeof(float) * 5 * n3 * ne, d32, d32 + (size_t)a.E * 5 * n3);
+    if (a.prefetch > 0 && threadIdx.x == 0) {
+      // the elements of the block a.prefetch blocks further on, when they are
+      // one contiguous range (always without an element list; in a serving
+      // pool, unless the block spans two cases' ranges)
+      const int64_t i2 = (int64_t)(blk + a.prefetch) * EPB;
+      if (i2 < a.E) {
+        const int64_t ne = min((int64_t)EPB, (int64_t)a.E - i2);
+        const int64_t e2 = a.elem_list ? a.elem_list[i2] : i2;
+        if (!a.elem_list || a.elem_list[i2 + ne - 1] == e2 + ne - 1) {
+          const size_t ub = sizeof(double) * 5 * n3, Ea = (size_t)a.E_all;
+          prefetch_l2(a.U + e2 * 5 * n3, ub * ne, a.U, a.U + Ea * 5 * n3);
+          if (MODE == 1 && !sc.first()) {
+            const float* d32 = reinterpret_cast<const float*>(a.dU);
+            prefetch_l2(d32 + e2 * 5 * n3, sizeof(float) * 5 * n3 * ne, d32, d32 + Ea * 5 * n3);
+          }
+          prefetch_l2(a.metric32 + e2 * 10 * n3, sizeof(float) * 10 * n3 * ne, a.metric32, a.metric32 + Ea * 10 * n3);
         }
-        prefetch_l2(a.metric32 + e2 * 10 * n3, sizeof(float) * 10 * n3 * ne, a.metric32,
-                    a.metric32 + (size_t)a.E * 10 * n3);
       }
-    }
-    // this element's later gathers, asked of L2 now: its six sides' q* and f*
-    // records (read after the lifting and in SurfInt) and its RK register (read
-    // by the update), so that those reads do not each wait on HBM
-    if (t < 6) {
-      const int sf = es_side(a.elem_side[(size_t)e * 6 + t]);
-      if (a.viscous)
-        prefetch_l2(a.qs32 + (size_t)sf * n2 * 4, sizeof(float) * 4 * n2, a.qs32, a.qs32 + (size_t)a.S * n2 * 4);
-      prefetch_l2(a.fstar32 + (size_t)sf * 5 * n2, sizeof(float) * 5 * n2, a.fstar32, a.fstar32 + (size_t)a.S * 5 * n2);
-    } else if (t == 6 && MODE == 1 && !sc.first()) {
-      const float* d32 = reinterpret_cast<const float*>(a.dU);
-      prefetch_l2(d32 + (size_t)e * 5 * n3, sizeof(float) * 5 * n3, d32, d32 + (size_t)a.E * 5 * n3);
     }
     for (int k = threadIdx.x; k < n2; k += blockDim.x) {
       sDs[k] = (float)a.ops->Dsplit[k];
@@ -81,7 +77,10 @@ do {
       const int i = k / L::n4, al = k % L::n4;
       sDr[k] = al < n ? 2.0f * (float)a.ops->Dhat[i * n + al] : 0.0f;
     }
-    load_face_normals<n>(a, e, t, sSn);
+    // the element's state and metrics first, then its face data (normals;
+    // q*, f* and the RK register by asynchronous copies), so that the side
+    // map's round trip overlaps those loads and nothing later in the element
+    // waits on global memory
     double U[5];
     double p_full;
     {
@@ -89,6 +88,16 @@ do {
   #pragma unroll
       for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
     }
+    float mt[10];
+  #pragma unroll
+    for (int c = 0; c < 10; ++c) mt[c] = metric_at<float>(a, e, c, t, n3);
+    load_face_data<n>(a, e, t, sSn, sQst, sFst, a.viscous != 0);
+    if (MODE == 1 && !sc.first()) {
+      const float* d32 = reinterpret_cast<const float*>(a.dU) + (size_t)e * 5 * n3 + t;
+  #pragma unroll
+      for (int k = 0; k < 5; ++k) cp_async4(sDU + k * n3 + t, d32 + k * n3);
+    }
+    cp_async_commit();
     // the FP64 pressure only for the indicator (one FP64 addition less otherwise)
     const SPrim<float> me = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp, a.shock ? &p_full : nullptr);
     // halved values: every arithmetic mean of the two-point flux is one addition
@@ -98,10 +107,9 @@ do {
     Qs[vp] = me.u, Qs[Pn + vp] = me.v, Qs[2 * Pn + vp] = me.w, Qs[3 * Pn + vp] = me.Tt;
   #pragma unroll
     for (int d = 0; d < 3; ++d)
-      J4[d * Pn + vp] = make_float4(0.5f * metric_at<float>(a, e, 3 * d, t, n3),
-                                    0.5f * metric_at<float>(a, e, 3 * d + 1, t, n3),
-                                    0.5f * metric_at<float>(a, e, 3 * d + 2, t, n3), 0.0f);
-    const float Jinv = metric_at<float>(a, e, 9, t, n3);
+      J4[d * Pn + vp] = make_float4(0.5f * mt[3 * d], 0.5f * mt[3 * d + 1], 0.5f * mt[3 * d + 2], 0.0f);
+    const float Jinv = mt[9];
+    cp_async_wait<0>();  // this thread's copies; the barrier makes every thread's visible
     __syncwarp();
     __syncthreads();
     const int idx[3] = {t % n, (t / n) % n, t / n2};  // indexed by unrolled (constant) d only
@@ -117,12 +125,7 @@ do {
         const int f = 2 * d + (id == n - 1 ? 1 : 0);
         int p, qq;
         face_pq(d, idx, p, qq);
-        const int es = a.elem_side[(size_t)e * 6 + f];
-        int pm = p, qm = qq;
-        if (es_slave(es)) flip_to_master<n>(es_flip(es), p, qq, pm, qm);
-        if (!DG_CHK(es_side(es) >= 0 && es_side(es) < a.S && pm >= 0 && pm < n && qm >= 0 && qm < n, es_side(es)))
-          continue;
-        const float4 qs = ld4(a.qs32 + ((size_t)es_side(es) * n2 + pm + n * qm) * 4);
+        const float4 qs = sQst[f * n2 + p + n * qq];
         const float4 sn = sSn[f * n2 + p + n * qq];
         const float qa[4] = {qs.x, qs.y, qs.z, qs.w};
   #pragma unroll
@@ -147,7 +150,9 @@ do {
     // ---- split-form KEP volume integral, one node per thread over its partners ----
     float accC[5] = {0, 0, 0, 0, 0};  // convective DG volume term
     float acc[5] = {0, 0, 0, 0, 0};   // viscous volume + surface terms
-  #pragma unroll 1
+    // unrolled over the directions: each partner's shared-memory offsets,
+    // padding included, are then compile-time constants
+  #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int id = dir_index<n>(t, d), sd = dir_stride<n>(d), bse = t - id * sd;
       const float4 ai = P4[t];
@@ -274,15 +279,10 @@ do {
       const int f = 2 * d + (id == n - 1 ? 1 : 0);
       int p, qq;
       face_pq(d, idx, p, qq);
-      const int es = a.elem_side[(size_t)e * 6 + f];
-      int pm = p, qm = qq;
-      if (es_slave(es)) flip_to_master<n>(es_flip(es), p, qq, pm, qm);
-      if (!DG_CHK(es_side(es) >= 0 && es_side(es) < a.S && pm >= 0 && pm < n && qm >= 0 && qm < n, es_side(es)))
-        continue;
-      const float sg = sSn[f * n2 + p + n * qq].w;
-      const float* Fs = a.fstar32 + (size_t)es_side(es) * 5 * n2 + pm + n * qm;
+      const int slot = f * n2 + p + n * qq;
+      const float sg = sSn[slot].w;
   #pragma unroll
-      for (int k = 0; k < 5; ++k) acc[k] += sg * Fs[k * n2];
+      for (int k = 0; k < 5; ++k) acc[k] += sg * sFst[k * 6 * n2 + slot];
     }
     // ---- ApplyJac; the energy equation gets H_ref times the mass equation back ----
     float ut32[5];
@@ -335,7 +335,7 @@ do {
       double* uo = a.Urk + (size_t)e * 5 * n3 + t;
   #pragma unroll
       for (int k = 0; k < 5; ++k) {
-        const float r = sc.first() ? dtf * utf[k] : fmaf(sc.fA(), du[k * n3], dtf * utf[k]);
+        const float r = sc.first() ? dtf * utf[k] : fmaf(sc.fA(), sDU[k * n3 + t], dtf * utf[k]);
         U[k] += sc.B() * f64_of(r);  // the updated state
         if (valid) {
           du[k * n3] = r;
@@ -347,7 +347,7 @@ do {
         const SPrim<float> mn = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp);
         __syncwarp();
         __syncthreads();  // the workspace is read by no thread any more
-        face_epilogue<N>(a, cp, e, t, valid, mn, Jinv, J4, Qs, Wk, sDr, sSn);
+        face_epilogue<N>(a, cp, e, t, valid, mn, Jinv, J4, Qs, P4, Wk, sDr, sSn);  // P4, Q4 are free after the KEP sums
       }
     }
 } while (0);

@@ -81,15 +81,21 @@ struct FusedSmem {
   // per element: P (2 float4 per node: (rho, u, v, w) / 2 and (p', H') / 2, T'),
   // J (3 float4 planes, (Ja^d) / 2), q (4 planes: u, v, w, T'), W (12 planes:
   // lifting sums; also viscous / FV fluxes and the FP64 indicator scratch),
-  // face normals (6 faces x n2 float4: s n and the SurfInt sign)
+  // face normals (6 faces x n2 float4: s n and the SurfInt sign), and the
+  // element's gathered face and RK data: q* of its six sides (6 x n2 float4),
+  // their f* (5 planes of 6 n2) and its FP32 RK register (5 planes of n3)
   static constexpr int offJ = 8 * S::n3, offQ = offJ + 12 * Pn, offW = offQ + 4 * Pn, offN = offW + 12 * Pn;
-  static constexpr int per_elem_f = offN + 24 * S::n2;
+  static constexpr int offQS = offN + 24 * S::n2, offFS = offQS + 24 * S::n2;
+  static constexpr int offDU = (offFS + 30 * S::n2 + 3) & ~3;  // (rounded to whole float4s)
+  static constexpr int per_elem_f = (offDU + 5 * S::n3 + 3) & ~3;
   static constexpr size_t bytes =
       sizeof(double) * n2d + sizeof(float) * (2 * n2p + S::n * n4 + S::EPB * per_elem_f);
   static_assert(2 * S::n3 + 4 * S::n2 <= 6 * Pn, "the indicator scratch fits the W workspace");
+  static_assert(Pn <= 2 * S::n3, "a padded float4 node plane fits the P planes (the epilogue's R4)");
   static_assert((2 * n2p + S::n * n4) % 4 == 0 && per_elem_f % 4 == 0 && offQ % 4 == 0 && offW % 4 == 0 &&
-                    offN % 4 == 0,
+                    offN % 4 == 0 && offQS % 4 == 0 && offFS % 4 == 0 && offDU % 4 == 0,
                 "16-byte alignment of the float4 planes");
+  static_assert(EPB_ != 0 || bytes <= 113 * 1024, "two blocks per SM at the default elements per block");
 };
 
 // padded plane index of node t: one pad word after each line of n nodes
@@ -158,14 +164,12 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, const v
 // added for the others).  Qs: the element's q planes (u, v, w, T'); J4: its
 // halved metrics; W: its 12 workspace planes; sDr2: 2 Dhat with rows padded
 // to n4 floats (the factor 2 undoes the halving of the metrics, exactly:
-// (2 Dhat) (J/2 q) rounds as Dhat (J q)).  Every thread of the block calls it
-// (it holds barriers); W may be reused after the caller's next barrier.
+// (2 Dhat) (J/2 q) rounds as Dhat (J q)).  READ: node t's twelve sums are
+// read back into acc (else they stay in W only).  Every thread of the block
+// calls it (it holds barriers); W may be reused after the caller's next
+// barrier.
 // ---------------------------------------------------------------------------
-// FACES: only the sums at the element's face nodes are needed (the
-// epilogue): a line inside the element in both other directions computes its
-// two end nodes only; every face node lies on a line that computes it for
-// each direction.
-template <int n, int n4, bool FACES = false>
+template <int n, int n4, bool READ = true>
 __device__ __forceinline__ void lift_volume(const float* Qs, const float4* J4, float* W, const float* sDr2, int t,
                                             float acc[12]) {
   constexpr int n2 = n * n, n3 = n2 * n, Pn = n3 + n2;
@@ -185,10 +189,8 @@ __device__ __forceinline__ void lift_volume(const float* Qs, const float4* J4, f
         P1[al] = j.y * q;
         P2[al] = j.z * q;
       }
-      const bool inner = FACES && lp > 0 && lp < n - 1 && lq > 0 && lq < n - 1;
 #pragma unroll
       for (int i = 0; i < n; ++i) {
-        if (inner && i > 0 && i < n - 1) continue;
         float r[n4];
 #pragma unroll
         for (int c = 0; c < n4; c += 4) {
@@ -213,9 +215,11 @@ __device__ __forceinline__ void lift_volume(const float* Qs, const float4* J4, f
     __syncwarp();
     __syncthreads();
   }
-  const int v = pad_idx<n>(t);
+  if constexpr (READ) {
+    const int v = pad_idx<n>(t);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = W[k * Pn + v];
+    for (int k = 0; k < 12; ++k) acc[k] = W[k * Pn + v];
+  }
 }
 
 // Loads the element's face normals into shared memory: sSn[f][pq] = (s n of
@@ -235,76 +239,113 @@ __device__ __forceinline__ void load_face_normals(const StageArgs& a, int e, int
   }
 }
 
+// The element's face data for a stage: the side normals as load_face_normals
+// stores them, and, by asynchronous copies (cp.async, one group with the
+// caller's), for each face f and face-frame node pq: the side's q* record
+// (sQs[f n2 + pq], when `lift`) and its f* (sFs[k][f n2 + pq]).  The copies
+// are issued as soon as the side record is known, so that their latency
+// overlaps the loads of the element's state and metrics; the caller commits
+// the group and waits before its block-wide barrier.
+template <int n>
+__device__ __forceinline__ void load_face_data(const StageArgs& a, int e, int t, float4* sSn, float4* sQs,
+                                               float* sFs, bool lift) {
+  constexpr int n2 = n * n;
+  const float w0 = (float)a.ops->winv[0];
+  for (int k = t; k < 6 * n2; k += n2 * n) {
+    const int f = k / n2, pq = k % n2;
+    int s, half, pm;
+    face_record<n>(a.elem_side, e, f, pq % n, pq / n, s, half, pm);
+    if (!DG_CHK(s >= 0 && s < a.S && pm >= 0 && pm < n2, s)) continue;
+    if (lift) cp_async16(sQs + k, a.qs32 + ((size_t)s * n2 + pm) * 4);
+    const float* fs = a.fstar32 + (size_t)s * 5 * n2 + pm;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) cp_async4(sFs + c * 6 * n2 + k, fs + c * n2);
+    const float* nr = a.nrm32 + (size_t)s * 7 * n2 + pm;
+    sSn[k] = make_float4(nr[0], nr[n2], nr[2 * n2], half ? -w0 : w0);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Epilogue: the face data of a state for the next k_fflux.  me: the node's
-// shifted primitives; Jinv its 1/J; sSn the element's face normals.  All
-// threads of the block call it (the lifting holds barriers); `valid` masks
-// the stores.
+// shifted primitives; Jinv its 1/J; sSn the element's face normals; R4 a
+// free float4 plane of the element (n3 + n2 entries, padded node index).  All threads of the block
+// call it (the lifting holds barriers); `valid` masks the stores.
+// The node values go to shared memory (q in the Qs planes, (rho, p', H', 1/J)
+// in R4), the lifting leaves its volume sums in the W planes, and
+// then one thread per (face, face node) slot forms that record: the node's
+// own halves of q* on every face through it, g_part, the viscous parts and
+// the partial viscous flux through the slot's face (edge and corner nodes
+// form g_part once per face they lie on, in the same order of operations).
 // ---------------------------------------------------------------------------
 template <int N>
 __device__ __forceinline__ void face_epilogue(const StageArgs& a, const CaseParams& cp, int e, int t, bool valid,
                                               const SPrim<float>& me, float Jinv, const float4* J4, float* Qs,
-                                              float* Wk, const float* sDr, const float4* sSn) {
+                                              float4* R4, float* Wk, const float* sDr, const float4* sSn) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   constexpr int Pn = n3 + n2, n4 = (n + 3) & ~3;
-  const int idx[3] = {t % n, (t / n) % n, t / n2};
-  const float q[4] = {me.u, me.v, me.w, me.Tt};
-  float acc[12];
-  if (a.viscous) {  // block-uniform condition
+  {
     const int v = pad_idx<n>(t);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) Qs[k * Pn + v] = q[k];
-    __syncwarp();
-    __syncthreads();
-    lift_volume<n, n4, true>(Qs, J4, Wk, sDr, t, acc);
+    Qs[v] = me.u, Qs[Pn + v] = me.v, Qs[2 * Pn + v] = me.w, Qs[3 * Pn + v] = me.Tt;
+    R4[v] = make_float4(me.rho, me.p, me.H, Jinv);  // padded: face slots read it with a node stride of n
+  }
+  __syncwarp();
+  __syncthreads();
+  if (a.viscous) {  // block-uniform condition
+    // the volume sums at every node, left in the W planes: computing only the
+    // face nodes' sums saves no time (a warp's lines mix both kinds, and
+    // warp-uniform task orders for them meet shared-memory bank conflicts)
+    float unused[12];
+    lift_volume<n, n4, false>(Qs, J4, Wk, sDr, t, unused);
   }
   if (!valid) return;
-  bool on[3];
-  int sd[3], hd[3], pqd[3];
-  float4 nd[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    on[d] = idx[d] == 0 || idx[d] == n - 1;
-    if (!on[d]) continue;
-    const int f = 2 * d + (idx[d] == n - 1 ? 1 : 0);
-    int p, qq;
-    face_pq(d, idx, p, qq);
-    face_record<n>(a.elem_side, e, f, p, qq, sd[d], hd[d], pqd[d]);
-    nd[d] = DG_CHK(f * n2 + p + n * qq < 6 * n2, f * n2 + p + n * qq) ? sSn[f * n2 + p + n * qq] : make_float4(0, 0, 0, 0);
-  }
-  if (!(on[0] || on[1] || on[2])) return;
-  // own halves of q* on every face through the node
-  float tau[6], W[3];
-  if (a.viscous) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (!on[d]) continue;
-      const float4 sn = nd[d];
-#pragma unroll
-      for (int qv = 0; qv < 4; ++qv) {
-        const float h = sn.w * (0.5f * q[qv]);
-        acc[qv * 3 + 0] += h * sn.x;
-        acc[qv * 3 + 1] += h * sn.y;
-        acc[qv * 3 + 2] += h * sn.z;
-      }
-    }
-    float g[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) g[k] = acc[k] * Jinv;
-    float vmu, vlam;
-    visc_coeffs<float>(a, cp, me.Tt, vmu, vlam);
-    viscous_parts(g, me.u, me.v, me.w, vmu, vlam, tau, W);
-  }
-  const float4 r0 = make_float4(me.u, me.v, me.w, me.Tt), r1 = make_float4(me.rho, me.p, me.H, Jinv);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    if (!on[d]) continue;
-    const size_t rec = ((size_t)sd[d] * 2 + hd[d]) * n2 + pqd[d];
-    if (!DG_CHK(sd[d] >= 0 && sd[d] < a.S && pqd[d] >= 0 && pqd[d] < n2 && (hd[d] == 0 || hd[d] == 1), rec)) continue;
-    st4(a.tr32 + rec * 8, r0);
-    st4(a.tr32 + rec * 8 + 4, r1);
+  for (int slot = t; slot < 6 * n2; slot += n3) {
+    const int f = slot / n2, pq = slot % n2, p = pq % n, qq = pq / n, df = f >> 1;
+    const int side = (f & 1) ? n - 1 : 0;
+    // the node of the slot: face-frame (p, q) is (j, k) on x-faces, (i, k) on
+    // y-faces, (i, j) on z-faces
+    const int i0 = df == 0 ? side : p, i1 = df == 0 ? p : (df == 1 ? side : qq), i2 = df == 2 ? side : qq;
+    const int idx[3] = {i0, i1, i2};  // indexed by unrolled (constant) d only
+    const int node = i0 + n * (i1 + n * i2), vn = pad_idx<n>(node);
+    if (!DG_CHK(node >= 0 && node < n3, node)) continue;
+    const float q[4] = {Qs[vn], Qs[Pn + vn], Qs[2 * Pn + vn], Qs[3 * Pn + vn]};
+    float tau[6], W[3];
     if (a.viscous) {
-      const float snv[3] = {nd[d].x, nd[d].y, nd[d].z};
+      float acc[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = Wk[k * Pn + vn];
+      // own halves of q* on every face through the node
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (idx[d] != 0 && idx[d] != n - 1) continue;
+        const int fd = 2 * d + (idx[d] == n - 1 ? 1 : 0);
+        int pd, qd;
+        face_pq(d, idx, pd, qd);
+        const float4 sn = sSn[fd * n2 + pd + n * qd];
+#pragma unroll
+        for (int qv = 0; qv < 4; ++qv) {
+          const float h = sn.w * (0.5f * q[qv]);
+          acc[qv * 3 + 0] += h * sn.x;
+          acc[qv * 3 + 1] += h * sn.y;
+          acc[qv * 3 + 2] += h * sn.z;
+        }
+      }
+      const float Jn = R4[vn].w;
+      float g[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) g[k] = acc[k] * Jn;
+      float vmu, vlam;
+      visc_coeffs<float>(a, cp, q[3], vmu, vlam);
+      viscous_parts(g, q[0], q[1], q[2], vmu, vlam, tau, W);
+    }
+    int sd, hd, pqd;
+    face_record<n>(a.elem_side, e, f, p, qq, sd, hd, pqd);
+    const size_t rec = ((size_t)sd * 2 + hd) * n2 + pqd;
+    if (!DG_CHK(sd >= 0 && sd < a.S && pqd >= 0 && pqd < n2 && (hd == 0 || hd == 1), rec)) continue;
+    st4(a.tr32 + rec * 8, make_float4(q[0], q[1], q[2], q[3]));
+    st4(a.tr32 + rec * 8 + 4, R4[vn]);
+    if (a.viscous) {
+      const float4 sn = sSn[slot];
+      const float snv[3] = {sn.x, sn.y, sn.z};
       float fv[4];
       viscous_flux_n(tau, W, snv, fv);
       st4(a.pfv32 + rec * 4, make_float4(fv[0], fv[1], fv[2], fv[3]));
@@ -327,6 +368,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_fprep(StageArgs a) {
   float* base = sDr + n * L::n4;
   const int le = threadIdx.x / n3, t = threadIdx.x % n3;
   float* mine = base + (size_t)le * L::per_elem_f;
+  float4* R4 = reinterpret_cast<float4*>(mine);  // the P planes, free here
   float4* J4 = reinterpret_cast<float4*>(mine + L::offJ);
   float* Qs = mine + L::offQ;
   float* Wk = mine + L::offW;
@@ -359,7 +401,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_fprep(StageArgs a) {
   const float Jinv = metric_at<float>(a, e, 9, t, n3);
   __syncwarp();
   __syncthreads();
-  face_epilogue<N>(a, cp, e, t, valid, me, Jinv, J4, Qs, Wk, sDr, sSn);
+  face_epilogue<N>(a, cp, e, t, valid, me, Jinv, J4, Qs, R4, Wk, sDr, sSn);
 }
 
 // ---------------------------------------------------------------------------

@@ -73,11 +73,20 @@ struct TBuf<float> {
 };
 
 // ---------------------------------------------------------------------------
-// Asynchronous global -> shared copies (cp.async, 8 bytes per thread and call)
+// Asynchronous global -> shared copies (cp.async, 4, 8 or 16 bytes per thread and call)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// 16 bytes, both addresses 16-byte aligned (bypasses L1)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // waits until at most K of this thread's committed groups are still in flight
@@ -1240,6 +1249,7 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.epilogue = 0;
   a.prefetch = 0;
   a.elem_off = 0;
+  a.E_all = (int)c->E;
   if (c->elem_list) {
     a.E = (int)c->n_elem_list;
     a.S = (int)c->n_side_list;

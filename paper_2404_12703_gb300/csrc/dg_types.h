@@ -158,6 +158,7 @@ struct StageArgs {
   int epilogue;
   int prefetch;
   int elem_off;  // k_fprep without an element list: elements elem_off .. elem_off + E - 1
+  int E_all;     // elements of the context's arrays (E, or a serving pool's capacity)
 };
 
 }  // namespace dg

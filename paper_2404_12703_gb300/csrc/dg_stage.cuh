@@ -458,8 +458,165 @@ __global__ void __launch_bounds__(256) k_surf_prims(StageArgs a) {
 // ---------------------------------------------------------------------------
 // Lifted gradients (weak form, Eq. lifting)
 // ---------------------------------------------------------------------------
+// FP64 shared-memory layout of k_lift (line tasks): the tables (Dhat, then
+// for even n its even and odd half matrices), then per element the q planes
+// (4), the metric planes (9) and the sums (12), each a padded node plane of
+// n^3 + n^2 doubles (one pad after every line of n nodes: the tasks' 64-bit
+// loads along any direction then fall in distinct banks)
+template <int N, int EPB_ = 0>
+struct Lift64Smem {
+  using S = Shape<N, EPB_>;
+  static constexpr int h = S::n / 2, Pn = S::n3 + S::n2;
+  static constexpr int ntab = (S::n2 + 2 * h * h + 1) & ~1;
+  static constexpr size_t bytes = sizeof(double) * (ntab + (size_t)S::EPB * 25 * Pn);
+};
+
+// The FP64 lifting (Eq. lifting, volume part, then the surface part and
+// 1/J) by line tasks: per direction d, one task per (line, variable) loads
+// the line's q and Ja^d once, forms the three products and applies Dhat;
+// for even n through its even and odd half matrices (Dhat is
+// centro-antisymmetric on LGL nodes: with e_j = P_j + P_(n-1-j) and
+// o_j = P_j - P_(n-1-j), y_i = (De e)_i / 2 + (Do o)_i / 2 and
+// y_(n-1-i) = (Do o)_i / 2 - (De e)_i / 2, with De_ij = Dhat_ij +
+// Dhat_i(n-1-j) and Do_ij = Dhat_ij - Dhat_i(n-1-j)): 6 n + 3 n / 2 FP64
+// operations per line and product column instead of n^2, where the lifting
+// is bound by the FP64 unit.  The sums collect in shared memory (written for
+// the first direction, added for the others).
+template <int N, int EPB_>
+__device__ __forceinline__ void lift_lines64(const StageArgs& a) {
+  using S = Shape<N, EPB_>;
+  using L = Lift64Smem<N, EPB_>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB, Pn = L::Pn, h = L::h;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sD = reinterpret_cast<double*>(smraw);  // [n][n] Dhat
+  double* sDe = sD + n2;                          // [h][h] even half
+  double* sDo = sDe + h * h;                      // [h][h] odd half, each halved
+  const int le = threadIdx.x / n3, t = threadIdx.x % n3;
+  double* q = sD + L::ntab + (size_t)le * 25 * Pn;  // [4][Pn] u, v, w, T'
+  double* J = q + 4 * Pn;                           // [9][Pn] Ja^d_c
+  double* W = J + 9 * Pn;                           // [12][Pn] the sums
+  const int ei = blockIdx.x * EPB + le < a.E ? blockIdx.x * EPB + le : a.E - 1;
+  const int e = a.elem_list ? a.elem_list[ei] : ei;
+  const int ce = a.elem_case ? a.elem_case[e] : 0;
+  const bool valid = blockIdx.x * EPB + le < a.E && ce >= 0;
+  const bool busy = valid && !(a.cases && a.cases[ce].dt == 0.0);
+  if (a.elem_case && __syncthreads_and(!busy)) return;
+  const CaseParams cp = case_params(a, ce);
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) sD[k] = a.ops->Dhat[k];
+  for (int k = threadIdx.x; k < h * h; k += blockDim.x) {
+    const int i = k / h, j = k % h;
+    const double* D = a.ops->Dhat + i * n;
+    sDe[k] = 0.5 * (D[j] + D[n - 1 - j]);
+    sDo[k] = 0.5 * (D[j] - D[n - 1 - j]);
+  }
+  const int vp = t + t / n;  // padded index of node t
+  {
+    double U[5];
+    const double* u = a.U + (size_t)e * 5 * n3 + t;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) U[k] = u[k * n3];
+    const SPrim<double> pr = shifted_prim<double>(U, a.gm1, a.Rinv, cp);
+    q[vp] = pr.u, q[Pn + vp] = pr.v, q[2 * Pn + vp] = pr.w, q[3 * Pn + vp] = pr.Tt;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) J[c * Pn + vp] = metric_at<double>(a, e, c, t, n3);
+  }
+  const double Ji = metric_at<double>(a, e, 9, t, n3);
+  __syncwarp();
+  __syncthreads();
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    const int sd = d == 0 ? 1 : (d == 1 ? n : n2);
+    for (int task = t; task < 4 * n2; task += n3) {
+      const int qv = task / n2, l = task % n2, lp = l % n, lq = l / n;
+      const int bl = d == 0 ? n * (lp + n * lq) : (d == 1 ? lp + n2 * lq : lp + n * lq);
+      double P0[n], P1[n], P2[n];
+#pragma unroll
+      for (int al = 0; al < n; ++al) {
+        const int v = bl + al * sd, pv = v + v / n;
+        const double qq = q[qv * Pn + pv];
+        P0[al] = J[(3 * d) * Pn + pv] * qq;
+        P1[al] = J[(3 * d + 1) * Pn + pv] * qq;
+        P2[al] = J[(3 * d + 2) * Pn + pv] * qq;
+      }
+      auto put = [&](int i, double y0, double y1, double y2) {
+        const int v = bl + i * sd;
+        double* w = W + (qv * 3) * Pn + v + v / n;
+        if (d == 0) {
+          w[0] = y0, w[Pn] = y1, w[2 * Pn] = y2;
+        } else {
+          w[0] += y0, w[Pn] += y1, w[2 * Pn] += y2;
+        }
+      };
+      if constexpr (n % 2 == 0) {
+        double E0[h], E1[h], E2[h], O0[h], O1[h], O2[h];
+#pragma unroll
+        for (int j = 0; j < h; ++j) {
+          E0[j] = P0[j] + P0[n - 1 - j], O0[j] = P0[j] - P0[n - 1 - j];
+          E1[j] = P1[j] + P1[n - 1 - j], O1[j] = P1[j] - P1[n - 1 - j];
+          E2[j] = P2[j] + P2[n - 1 - j], O2[j] = P2[j] - P2[n - 1 - j];
+        }
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+          double e0 = 0.0, e1 = 0.0, e2 = 0.0, p0 = 0.0, p1 = 0.0, p2 = 0.0;
+#pragma unroll
+          for (int j = 0; j < h; ++j) {
+            const double ce = sDe[i * h + j], co = sDo[i * h + j];
+            e0 += ce * E0[j], e1 += ce * E1[j], e2 += ce * E2[j];
+            p0 += co * O0[j], p1 += co * O1[j], p2 += co * O2[j];
+          }
+          put(i, p0 + e0, p1 + e1, p2 + e2);
+          put(n - 1 - i, p0 - e0, p1 - e1, p2 - e2);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+#pragma unroll
+          for (int al = 0; al < n; ++al) {
+            const double c = sD[i * n + al];
+            y0 += c * P0[al], y1 += c * P1[al], y2 += c * P2[al];
+          }
+          put(i, y0, y1, y2);
+        }
+      }
+    }
+    __syncwarp();
+    __syncthreads();
+  }
+  if (!valid) return;
+  double acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = W[k * Pn + vp];
+  // surface part: on LGL nodes only face nodes receive it
+  const int idx[3] = {t % n, (t / n) % n, t / n2};
+  const double* Lf = a.lflux;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int id = idx[d];
+    if (id != 0 && id != n - 1) continue;
+    const int f = 2 * d + (id == n - 1 ? 1 : 0);
+    const int es = a.elem_side[(size_t)e * 6 + f];
+    const int s = es_side(es);
+    const int p = d == 0 ? idx[1] : idx[0];
+    const int qq = d == 2 ? idx[1] : idx[2];
+    int pm = p, qm = qq;
+    if (es_slave(es)) flip_to_master<n>(es_flip(es), p, qq, pm, qm);
+    const double sg = es_slave(es) ? -a.ops->winv[id] : a.ops->winv[id];
+    const double* Lr = Lf + (size_t)s * 12 * n2 + pm + n * qm;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] += sg * Lr[k * n2];
+  }
+  double* g = a.g + (size_t)e * 12 * n3 + t;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) g[k * n3] = acc[k] * Ji;
+}
+
 template <int N, typename T, int EPB_ = 0>
 __global__ void __launch_bounds__(Shape<N, EPB_>::THREADS) k_lift(StageArgs a) {
+  if constexpr (sizeof(T) == sizeof(double)) {
+    lift_lines64<N, EPB_>(a);
+    return;
+  }
   using S = Shape<N, EPB_>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   constexpr int n2p = (n2 + 3) & ~3;  // keeps the arrays below 16-byte aligned
@@ -1260,6 +1417,7 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
 template <int N, typename T, int E = 0>
 inline size_t lift_smem_bytes() {
   using S = Shape<N, E>;
+  if constexpr (sizeof(T) == sizeof(double)) return Lift64Smem<N, E>::bytes;
   return sizeof(T) * (((S::n2 + 3) & ~3) + S::EPB * 16 * S::n3);
 }
 

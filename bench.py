@@ -55,14 +55,17 @@ VOLUME32_BYTES_PER_DOF = 40 + 40 + 48 + 40 + 8 + 40 + 40
 # FP32-bulk, two-kernel stage (the default on periodic meshes), per DOF at
 # N = 7, with 6 / (N + 1) = 0.75 element face nodes and 0.375 side nodes per
 # DOF.  Element kernel: reads U 40, the FP32 RK register 20, FP32 metrics
-# 40, q* 0.75 x 16, side normals 0.75 x 12, f* 0.75 x 20; writes U 40, the
-# register 20, face traces 0.75 x 32 and partial viscous fluxes 0.75 x 16.
+# 40, the lifting's volume sums 48, q* 0.75 x 16, side normals 0.75 x 12,
+# f* 0.75 x 20; writes U 40, the register 20, the lifting's volume sums of
+# the updated state 48, face traces 0.75 x 32 and partial viscous fluxes
+# 0.75 x 16 (the sums, 96 B, in viscous runs such as the benchmark's TGV).
 # Side kernel, per side
 # node: reads two traces 64, two partial viscous fluxes 32, side geometry 28;
 # writes f* 20 and q* 16 (the edge and corner nodes' re-reads of neighbouring
 # traces are not counted).
 FACE_NODES_PER_DOF = 6 / (N_DEG + 1)
-FELEM32_BYTES_PER_DOF = 40 + 20 + 40 + FACE_NODES_PER_DOF * (16 + 12 + 20) + 40 + 20 + FACE_NODES_PER_DOF * (32 + 16)
+FELEM32_BYTES_PER_DOF = (40 + 20 + 40 + 48 + FACE_NODES_PER_DOF * (16 + 12 + 20) + 40 + 20 + 48
+                         + FACE_NODES_PER_DOF * (32 + 16))
 FFLUX32_BYTES_PER_DOF = FACE_NODES_PER_DOF / 2 * (64 + 32 + 28 + 20 + 16)
 # a whole stage of the minimal two-phase method with the RK register and the
 # metrics in FP64 and the face traces in FP32: 342 B at N = 7 (the budget the

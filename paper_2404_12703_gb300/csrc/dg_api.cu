@@ -326,6 +326,7 @@ int ensure_arrays(dg_ctx* c, const dg_params* p, std::string& msg) {
       set.push_back({(void**)&c->tr32, sizeof(float) * S * 2 * n2 * 8});
       set.push_back({(void**)&c->pfv32, sizeof(float) * S * 2 * n2 * 4});
       set.push_back({(void**)&c->qs32, sizeof(float) * S * n2 * 4});
+      set.push_back({(void**)&c->wv32, sizeof(float) * E * 12 * n3});
     }
     e = take(set);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->g32, 0, sizeof(float) * E * 12 * n3, st);
@@ -486,6 +487,7 @@ void dg_destroy(dg_ctx* c) {
   dfree(c, c->tr32);
   dfree(c, c->pfv32);
   dfree(c, c->qs32);
+  dfree(c, c->wv32);
   dfree(c, c->ops);
   dfree(c, c->scal);
   if (c->scal_host) cudaFreeHost(c->scal_host);

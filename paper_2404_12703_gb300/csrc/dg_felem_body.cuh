@@ -65,6 +65,8 @@ do {
             prefetch_l2(d32 + e2 * 5 * n3, sizeof(float) * 5 * n3 * ne, d32, d32 + Ea * 5 * n3);
           }
           prefetch_l2(a.metric32 + e2 * 10 * n3, sizeof(float) * 10 * n3 * ne, a.metric32, a.metric32 + Ea * 10 * n3);
+          if (a.viscous)
+            prefetch_l2(a.wv32 + e2 * 12 * n3, sizeof(float) * 12 * n3 * ne, a.wv32, a.wv32 + Ea * 12 * n3);
         }
       }
     }
@@ -92,6 +94,11 @@ do {
   #pragma unroll
     for (int c = 0; c < 10; ++c) mt[c] = metric_at<float>(a, e, c, t, n3);
     load_face_data<n>(a, e, t, sSn, sQst, sFst, a.viscous != 0);
+    if (a.viscous) {  // the lifting's volume sums of this state, formed by the face-data pass
+      const float* ws = a.wv32 + (size_t)e * 12 * n3 + t;
+  #pragma unroll
+      for (int k = 0; k < 12; ++k) cp_async4(Wk + k * Pn + pad_idx<n>(t), ws + k * n3);
+    }
     if (MODE == 1 && !sc.first()) {
       const float* d32 = reinterpret_cast<const float*>(a.dU) + (size_t)e * 5 * n3 + t;
   #pragma unroll
@@ -104,7 +111,6 @@ do {
     P4[t] = make_float4(0.5f * me.rho, 0.5f * me.u, 0.5f * me.v, 0.5f * me.w);
     Q4[t] = make_float4(0.5f * me.p, 0.5f * me.H, me.Tt, 0.0f);
     const int vp = pad_idx<n>(t);
-    Qs[vp] = me.u, Qs[Pn + vp] = me.v, Qs[2 * Pn + vp] = me.w, Qs[3 * Pn + vp] = me.Tt;
   #pragma unroll
     for (int d = 0; d < 3; ++d)
       J4[d * Pn + vp] = make_float4(0.5f * mt[3 * d], 0.5f * mt[3 * d + 1], 0.5f * mt[3 * d + 2], 0.0f);
@@ -114,10 +120,11 @@ do {
     __syncthreads();
     const int idx[3] = {t % n, (t / n) % n, t / n2};  // indexed by unrolled (constant) d only
     float tau[6] = {0, 0, 0, 0, 0, 0}, W[3] = {0, 0, 0};
-    // ---- BR1 lifting of the stage's state: volume part, then q* of the six faces ----
+    // ---- BR1 lifting of the stage's state: volume part (read), then q* of the six faces ----
     if (a.viscous) {
       float g[12];
-      lift_volume<n, L::n4>(Qs, J4, Wk, sDr, t, g);
+  #pragma unroll
+      for (int k = 0; k < 12; ++k) g[k] = Wk[k * Pn + vp];  // this thread's own copies (waited for above)
   #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const int id = idx[d];
@@ -188,6 +195,9 @@ do {
     }
     // ---- viscous volume term: collocated weak form, per direction ----
     if (a.viscous) {
+      // its flux planes overlay the W planes whose sums every thread has read
+      __syncwarp();
+      __syncthreads();
   #pragma unroll 1
       for (int d = 0; d < 3; ++d) {
         {

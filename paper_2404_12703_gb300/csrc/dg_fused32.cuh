@@ -30,6 +30,11 @@
 //         halves of q*:  g_part = (1/J) [ sum_d Dhat (Ja^d q) +
 //         sum_{faces f through the node} +-lhat (q_own / 2) (s n)_f ]
 //   qs32  [S][n2] float4: q* = (q_master + q_slave) / 2 of (u, v, w, T')
+// and per element, at every node:
+//   wv32  [E][12][n3] floats: the volume part of the lifting,
+//         sum_d Dhat (Ja^d q), before 1/J.  The epilogue forms it for the
+//         updated state anyway (for g_part); the next stage's element kernel
+//         reads it instead of forming the same sums again.
 //
 // Why the split is exact: BR1's face gradient is
 //   g = g_part + (1/J) sum_{f through the node} +-lhat (q_nbr(f) / 2) (s n)_f
@@ -296,6 +301,14 @@ __device__ __forceinline__ void face_epilogue(const StageArgs& a, const CasePara
     // warp-uniform task orders for them meet shared-memory bank conflicts)
     float unused[12];
     lift_volume<n, n4, false>(Qs, J4, Wk, sDr, t, unused);
+    // the node's twelve sums for the next stage's lifting, which would form
+    // them again from the same state and metrics
+    if (valid) {
+      const int v = pad_idx<n>(t);
+      float* ws = a.wv32 + (size_t)e * 12 * n3 + t;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) ws[k * n3] = Wk[k * Pn + v];
+    }
   }
   if (!valid) return;
   for (int slot = t; slot < 6 * n2; slot += n3) {

@@ -1403,6 +1403,7 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.tr32 = c->tr32;
   a.pfv32 = c->pfv32;
   a.qs32 = c->qs32;
+  a.wv32 = c->wv32;
   a.epilogue = 0;
   a.prefetch = 0;
   a.elem_off = 0;

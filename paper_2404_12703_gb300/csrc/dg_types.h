@@ -155,6 +155,7 @@ struct StageArgs {
   float* tr32;
   float* pfv32;
   float* qs32;
+  float* wv32;  // the lifting's volume sums of the state [E][12][n3] (Eq. lifting, before 1/J)
   int epilogue;
   int prefetch;
   int elem_off;  // k_fprep without an element list: elements elem_off .. elem_off + E - 1
@@ -215,6 +216,7 @@ struct dg_ctx {
   float* tr32 = nullptr;
   float* pfv32 = nullptr;
   float* qs32 = nullptr;
+  float* wv32 = nullptr;  // the lifting's volume sums of the face data's state
   bool traces_valid = false;
   int64_t bytes = 0;
   double t_host = 0.0;

@@ -93,6 +93,17 @@ __device__ __forceinline__ double dd_to_double(dd a) { return __dadd_rn(a.hi, a.
 __device__ __forceinline__ float f32_rn(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  // the common case, a binary32 normal (biased binary64 exponent 897..1150):
+  // adding half an ulp minus one, plus the kept last bit, to the magnitude
+  // rounds to nearest, ties to even, at the 29th bit; a carry runs into the
+  // exponent field (up to infinity from the top binade), and the exponent
+  // bias changes from 1023 to 127 by one subtraction (modulo 2^32, the
+  // result fits 31 bits)
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  if (mag >= (897ull << 52) && mag < (1151ull << 52)) {
+    const unsigned long long r = mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull);
+    return __uint_as_float(sign | ((unsigned)(r >> 29) - (896u << 23)));
+  }
   const int e = (int)((b >> 52) & 0x7ff);
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;  // 52 fraction bits
   if (e == 0x7ff) return __uint_as_float(m ? 0x7fffffffu : (sign | 0x7f800000u));
@@ -118,6 +129,11 @@ __device__ __forceinline__ float f32_rn(double x) {
 
 __device__ __forceinline__ double f64_of(float f) {
   const unsigned u = __float_as_uint(f);
+  // the common case, a binary32 normal: the fraction moves up by 29 bits and
+  // the biased exponent grows by 1023 - 127 = 896, in the high word
+  const unsigned mag = u & 0x7fffffffu;
+  if (mag >= 0x00800000u && mag < 0x7f800000u)
+    return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(mag << 29));
   const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
   const unsigned e = (u >> 23) & 0xff, m = u & 0x7fffffu;
   if (e == 0xff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | ((unsigned long long)m << 29)));

@@ -59,6 +59,9 @@ VOLUME32_BYTES_PER_DOF = 40 + 40 + 48 + 40 + 8 + 40 + 40
 # f* 0.75 x 20; writes U 40, the register 20, the lifting's volume sums of
 # the updated state 48, face traces 0.75 x 32 and partial viscous fluxes
 # 0.75 x 16 (the sums, 96 B, in viscous runs such as the benchmark's TGV).
+# The last stage of a step also reduces the next time step's spectral radii
+# from the state and metrics it holds (no further bytes), so the CFL
+# reduction kernel does not read the state again.
 # Side kernel, per side
 # node: reads two traces 64, two partial viscous fluxes 32, side geometry 28;
 # writes f* 20 and q* 16 (the edge and corner nodes' re-reads of neighbouring

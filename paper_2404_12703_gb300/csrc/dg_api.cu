@@ -847,7 +847,11 @@ int dg_rhs(dg_ctx* c, const double* U_dev, double* Ut_dev) {
 }
 
 static cudaError_t enqueue_step(dg_ctx* c) {
-  cudaError_t e = launch_cfl(c, false);
+  // two-kernel FP32-bulk steps take the radii of their state from the
+  // previous step's last stage, whose epilogue reduces those of the state
+  // it writes; otherwise the CFL reduction reads the state
+  const bool fcfl = cfl_fused(c);
+  cudaError_t e = fcfl ? launch_dt_next(c) : launch_cfl(c, false);
   const bool own = c->rk_ns > 0;
   const int ns = own ? c->rk_ns : 5;
   if (e == cudaSuccess && persist_active(c)) {
@@ -856,9 +860,11 @@ static cudaError_t enqueue_step(dg_ctx* c) {
   }
   for (int s = 0; s < ns && e == cudaSuccess; ++s) {
     c->stage_c = own ? c->rk_c[s] : RKC[s];
+    c->stage_cfl = fcfl && s == ns - 1;
     e = launch_rhs(c, c->U, 1, own ? c->rk_a[s] : RKA[s], own ? c->rk_b[s] : RKB[s], s == 0);
   }
   c->stage_c = 0.0;
+  c->stage_cfl = 0;
   return e;
 }
 
@@ -885,10 +891,20 @@ static cudaError_t ensure_step_graph(dg_ctx* c) {
 
 // the two-kernel FP32-bulk stage reads the face data of the step's state:
 // formed here when no step left them behind
+// (and, when the steps take their time step from the previous step's last
+// stage, the CFL radii of the state: the face-data pass reduces them too)
 static cudaError_t ensure_face_data(dg_ctx* c) {
-  if (!fused_active(c) || c->traces_valid) return cudaSuccess;
-  cudaError_t e = launch_fprep(c, c->U);
-  if (e == cudaSuccess) c->traces_valid = true;
+  if (!fused_active(c)) return cudaSuccess;
+  const bool fcfl = cfl_fused(c);
+  if (c->traces_valid && (!fcfl || c->lam_next_valid)) return cudaSuccess;
+  cudaError_t e = fcfl ? launch_clear_next(c) : cudaSuccess;
+  c->stage_cfl = fcfl;
+  if (e == cudaSuccess) e = launch_fprep(c, c->U);
+  c->stage_cfl = 0;
+  if (e == cudaSuccess) {
+    c->traces_valid = true;
+    c->lam_next_valid = fcfl;
+  }
   return e;
 }
 
@@ -899,8 +915,10 @@ static cudaError_t launch_steps(dg_ctx* c, int64_t n_steps) {
   for (int64_t i = 0; i < n_steps && e == cudaSuccess; ++i) {
     e = cudaGraphLaunch(c->step_graph, c->stream);
     const int per_stage = fused_active(c) ? 2 : (c->prm.viscous ? 4 : 2);
-    count_launch(persist_active(c) ? 3 : 2 + (c->rk_ns > 0 ? c->rk_ns : 5) * per_stage);
+    count_launch(persist_active(c) ? 3 : (cfl_fused(c) ? 1 : 2) + (c->rk_ns > 0 ? c->rk_ns : 5) * per_stage);
   }
+  // a persistent step leaves the face data of its state but not its radii
+  if (!cfl_fused(c)) c->lam_next_valid = false;
   return e;
 }
 

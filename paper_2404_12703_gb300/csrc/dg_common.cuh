@@ -276,6 +276,61 @@ __device__ __forceinline__ void viscous_parts(const T g[12], T u, T v, T w, T mu
   W[2] = tau[4] * u + tau[5] * v + tau[2] * w + lam * g[11];
 }
 
+// The spectral radii of the CFL rule at one node (dg_time_step in dg.h):
+// convective aa = sum_d (|u . Ja^d| + c |Ja^d|) / J and viscous
+// bb = kv(T) |Ja|^2 / (rho J^2), from the node's conservative state Uv, its
+// metrics M (Ja^d_c at 3 d + c, 1/J at 9), its geometry factors G (|Ja^d| for
+// d = 0, 1, 2, then sum_d |Ja^d|^2) and kv = max(4/3, gamma / Pr) mu (times
+// Sutherland's mu(T) / mu_ref).  FP32: every product and sum is a separately
+// rounded operation written out, so the CFL reduction kernel and the
+// two-kernel stage's epilogue, which both call this, form bitwise the same
+// radii whatever the compiler fuses around them.  FP64:
+__device__ __forceinline__ void cfl_radii(const double Uv[5], const double M[10], const double G[4], double gamma,
+                                          double gm1, double Rinv, double kv, int sutherland, double inv_Tref,
+                                          double& aa, double& bb) {
+  const double ri = 1.0 / Uv[0];
+  const double u = Uv[1] * ri, v = Uv[2] * ri, w = Uv[3] * ri;
+  const double p = gm1 * (Uv[4] - 0.5 * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
+  const double c = sqrt(gamma * p * ri);
+  double a = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) a += fabs(u * M[d * 3] + v * M[d * 3 + 1] + w * M[d * 3 + 2]) + c * G[d];
+  aa = a * M[9];
+  double kvn = kv;
+  if (sutherland) {  // mu(T) / mu_ref by Sutherland's law (Eq. sutherland)
+    const double th = p * ri * Rinv * inv_Tref;
+    kvn = kvn * 1.4042 * th * sqrt(th) / (th + 0.4042);
+  }
+  bb = kvn * ri * G[3] * M[9] * M[9];
+}
+// FP32: the geometry factors |Ja^d| and sum_d |Ja^d|^2 are formed here from
+// the FP32 metrics (the FP64 path reads them, formed once from the FP64
+// metrics), so the radii need nothing beyond the state and the metrics.
+__device__ __forceinline__ void cfl_radii(const float Uv[5], const float M[10], float gamma, float gm1, float Rinv,
+                                          float kv, int sutherland, float inv_Tref, float& aa, float& bb) {
+  const float ri = 1.0f / Uv[0];
+  const float u = __fmul_rn(Uv[1], ri), v = __fmul_rn(Uv[2], ri), w = __fmul_rn(Uv[3], ri);
+  const float m2 = __fmaf_rn(Uv[3], w, __fmaf_rn(Uv[2], v, __fmul_rn(Uv[1], u)));
+  const float p = __fmul_rn(gm1, __fsub_rn(Uv[4], __fmul_rn(0.5f, m2)));
+  const float c = sqrtf(__fmul_rn(__fmul_rn(gamma, p), ri));
+  float a = 0.0f, g2 = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float j0 = M[d * 3], j1 = M[d * 3 + 1], j2 = M[d * 3 + 2];
+    const float nj2 = __fmaf_rn(j2, j2, __fmaf_rn(j1, j1, __fmul_rn(j0, j0)));
+    g2 = __fadd_rn(g2, nj2);
+    const float un = __fmaf_rn(w, j2, __fmaf_rn(v, j1, __fmul_rn(u, j0)));
+    a = __fadd_rn(a, __fmaf_rn(c, sqrtf(nj2), fabsf(un)));
+  }
+  aa = __fmul_rn(a, M[9]);
+  float kvn = kv;
+  if (sutherland) {  // mu(T) / mu_ref by Sutherland's law (Eq. sutherland)
+    const float th = __fmul_rn(__fmul_rn(__fmul_rn(p, ri), Rinv), inv_Tref);
+    kvn = __fmul_rn(__fmul_rn(__fmul_rn(kvn, 1.4042f), th), sqrtf(th)) / __fadd_rn(th, 0.4042f);
+  }
+  bb = __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(kvn, ri), g2), M[9]), M[9]);
+}
+
 // F_v . nv  (4 non-zero components: momentum x, y, z and energy)
 template <typename T>
 __device__ __forceinline__ void viscous_flux_n(const T tau[6], const T W[3], const T nv[3], T f[4]) {

@@ -355,9 +355,15 @@ do {
       if (a.epilogue) {
         // ---- the face data of the updated state for the next stage ----
         const SPrim<float> mn = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp);
+        // the last stage of a step: the CFL radii of the updated state, for
+        // the next step's time step (element 0's q* records hold the warps'
+        // maxima: every thread read its q* in the lifting)
+        float* red = base + L::offQS;
+        if (a.cfl_out) cfl_block_radii<n>(a, valid, U, J4, vp, Jinv, red);
         __syncwarp();
         __syncthreads();  // the workspace is read by no thread any more
         face_epilogue<N>(a, cp, e, t, valid, mn, Jinv, J4, Qs, P4, Wk, sDr, sSn);  // P4, Q4 are free after the KEP sums
+        if (a.cfl_out && threadIdx.x == 0) cfl_block_finish(a, red, (int)(blockDim.x >> 5));
       }
     }
 } while (0);

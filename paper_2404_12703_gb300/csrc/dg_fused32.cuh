@@ -366,6 +366,60 @@ __device__ __forceinline__ void face_epilogue(const StageArgs& a, const CasePara
   }
 }
 
+// The CFL spectral radii of the state an element block prepares, for the
+// next step's time step (two-kernel FP32-bulk steps; the CFL reduction
+// kernel then does not read the state again).  Each thread forms its node's
+// radii with cfl_radii from the same FP32 values k_cfl<N, float> uses (the
+// state rounded to FP32 and the FP32 metrics, which J4 holds halved), so the
+// radii are bitwise k_cfl's and need no load beyond the element's own; the
+// lanes of a warp take their maxima, and lane 0 leaves them in red[2 w]
+// (convective), red[2 w + 1] (viscous) and red[64 + w] (1: a non-finite
+// radius) for warp w.  Every thread of the block calls it; after the
+// block's next barrier thread 0 calls cfl_block_finish.
+template <int n>
+__device__ __forceinline__ void cfl_block_radii(const StageArgs& a, bool valid, const double U[5], const float4* J4,
+                                                int vp, float Jinv, float* red) {
+  constexpr int n3 = n * n * n, Pn = n3 + n * n;
+  float Uv[5], M[10];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) Uv[k] = f32_rn(U[k]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float4 j = J4[d * Pn + vp];
+    M[3 * d] = 2.0f * j.x, M[3 * d + 1] = 2.0f * j.y, M[3 * d + 2] = 2.0f * j.z;
+  }
+  M[9] = Jinv;
+  float aa, bb;
+  cfl_radii(Uv, M, a.f_gamma, a.f_gm1, a.f_Rinv, a.f_cflkv, a.sutherland, a.f_inv_Tref, aa, bb);
+  const bool bad = valid && !(isfinite(aa) && isfinite(bb));
+  if (!valid) aa = bb = 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    aa = fmaxf(aa, __shfl_xor_sync(0xffffffffu, aa, o));
+    bb = fmaxf(bb, __shfl_xor_sync(0xffffffffu, bb, o));
+  }
+  const bool wbad = __any_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    const int w = threadIdx.x >> 5;
+    red[2 * w] = aa;
+    red[2 * w + 1] = bb;
+    red[64 + w] = wbad ? 1.0f : 0.0f;
+  }
+}
+// thread 0: the block's maxima into the step scalars (as k_cfl adds its blocks')
+__device__ __forceinline__ void cfl_block_finish(const StageArgs& a, const float* red, int nwarps) {
+  float lc = 0.0f, lv = 0.0f;
+  bool bad = false;
+  for (int w = 0; w < nwarps; ++w) {
+    lc = fmaxf(lc, red[2 * w]);
+    lv = fmaxf(lv, red[2 * w + 1]);
+    bad = bad || red[64 + w] != 0.0f;
+  }
+  atomicMax(&a.scal_cfl->lam_c_next, (unsigned long long)__double_as_longlong(f64_of(lc)));
+  if (a.viscous) atomicMax(&a.scal_cfl->lam_v_next, (unsigned long long)__double_as_longlong(f64_of(lv)));
+  if (bad) atomicOr(&a.scal_cfl->nonfinite, 1);
+}
+
 // ---------------------------------------------------------------------------
 // k_fprep: face data of the state a.U
 // ---------------------------------------------------------------------------
@@ -412,9 +466,12 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_fprep(StageArgs a) {
                                      0.5f * metric_at<float>(a, e, 3 * d + 1, t, n3),
                                      0.5f * metric_at<float>(a, e, 3 * d + 2, t, n3), 0.0f);
   const float Jinv = metric_at<float>(a, e, 9, t, n3);
+  float* red = base + L::offQS;  // element 0's q* records (unused here)
+  if (a.cfl_out) cfl_block_radii<n>(a, valid, U, J4, vp, Jinv, red);
   __syncwarp();
   __syncthreads();
   face_epilogue<N>(a, cp, e, t, valid, me, Jinv, J4, Qs, R4, Wk, sDr, sSn);
+  if (a.cfl_out && threadIdx.x == 0) cfl_block_finish(a, red, (int)(blockDim.x >> 5));
 }
 
 // ---------------------------------------------------------------------------

@@ -60,6 +60,11 @@ cudaError_t launch_fprep(dg_ctx* c, const double* U, int64_t e0 = 0, int64_t E =
 
 // the steps of a two-kernel FP32-bulk context run as one persistent launch
 inline bool persist_active(const dg_ctx* c) { return fused_active(c) && c->cfg.persistent == 1; }
+// the CFL reduction of a step is part of the previous step's last stage: the
+// two-kernel FP32-bulk steps of a single context launched per kernel (not
+// serving pools, whose cases each take their own time step, and not the
+// persistent launch)
+inline bool cfl_fused(const dg_ctx* c) { return fused_active(c) && !persist_active(c) && !c->elem_case; }
 // one persistent launch of every stage of a step (dg_rhs.cu); spin: polls of
 // a barrier wait before it gives up; extra: the barrier test hook (0)
 constexpr unsigned PERSIST_SPIN = 5000000u;  // about a second of 200 ns polls
@@ -82,6 +87,12 @@ cudaError_t launch_rhs(dg_ctx* c, const double* U, int mode, double rkA, double 
 // CFL reduction: writes dt (and advances nothing); fixed dt if dt_fixed > 0
 // report_only: writes the CFL time step to dt_cfl instead of taking the step
 cudaError_t launch_cfl(dg_ctx* c, bool report_only);
+// two-kernel FP32-bulk steps: the time step from the radii that the previous
+// step's last stage (or the face-data pass of a new state) reduced into
+// lam_*_next, which it clears for the step's own last stage
+cudaError_t launch_dt_next(dg_ctx* c);
+// clears lam_*_next before a face-data pass reduces a new state's radii
+cudaError_t launch_clear_next(dg_ctx* c);
 
 // raises the dynamic shared-memory limits of the kernels of degree N
 cudaError_t init_kernel_attributes(int N);

@@ -11,7 +11,7 @@ namespace dg {
 // ---------------------------------------------------------------------------
 // CFL reduction (the paper gives no rule; see dg_time_step in dg.h)
 // ---------------------------------------------------------------------------
-// T = float (FP32-bulk): the spectral radii in FP32, from the FP32 metrics
+// T = float (FP32-bulk): the spectral radii in FP32, from the FP32 metrics alone
 template <int N, typename T>
 __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U, const double* __restrict__ metric,
                                             const float* __restrict__ metric32, const double* __restrict__ geo,
@@ -25,28 +25,22 @@ __global__ void __launch_bounds__(256) k_cfl(int E, const double* __restrict__ U
        x += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = x / n3;
     const int t = (int)(x % n3);
-    T Uv[5];
+    T Uv[5], M[10];
     const double* up = U + e * 5 * n3 + t;
 #pragma unroll
     for (int k = 0; k < 5; ++k) Uv[k] = T(up[k * n3]);
-    const T ri = T(1) / Uv[0];
-    const T u = Uv[1] * ri, v = Uv[2] * ri, w = Uv[3] * ri;
-    const T p = T(gm1) * (Uv[4] - T(0.5) * (Uv[1] * u + Uv[2] * v + Uv[3] * w));
-    const T c = sqrt(T(gamma) * p * ri);
-    auto M = [&](int k) { return f32 ? T(metric32[(e * 10 + k) * n3 + t]) : T(metric[(e * 10 + k) * n3 + t]); };
-    const double* Gm = geo + e * 4 * n3 + t;
-    const T Ji = M(9);
-    T aa = T(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-      aa += fabs(u * M(d * 3) + v * M(d * 3 + 1) + w * M(d * 3 + 2)) + c * T(Gm[d * n3]);
-    aa *= Ji;
-    T kvn = T(kv);
-    if (sutherland) {  // mu(T) / mu_ref by Sutherland's law (Eq. sutherland)
-      const T th = p * ri * T(Rinv) * T(inv_Tref);
-      kvn = kvn * T(1.4042) * th * sqrt(th) / (th + T(0.4042));
+    for (int k = 0; k < 10; ++k) M[k] = f32 ? T(metric32[(e * 10 + k) * n3 + t]) : T(metric[(e * 10 + k) * n3 + t]);
+    T aa, bb;
+    if constexpr (f32) {
+      cfl_radii(Uv, M, T(gamma), T(gm1), T(Rinv), T(kv), sutherland, T(inv_Tref), aa, bb);
+    } else {
+      T G[4];
+      const double* Gm = geo + e * 4 * n3 + t;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) G[k] = Gm[k * n3];
+      cfl_radii(Uv, M, G, gamma, gm1, Rinv, kv, sutherland, inv_Tref, aa, bb);
     }
-    const T bb = kvn * ri * T(Gm[3 * n3]) * Ji * Ji;
     if (!isfinite(aa) || !isfinite(bb)) bad = 1;
     lcT = fmax(lcT, aa);
     lvT = fmax(lvT, bb);
@@ -111,7 +105,14 @@ __global__ void k_dt_report(DevScalars* scal, double cfl, double dfl, int N, int
   scal->lam_v = 0ull;
 }
 
-__global__ void k_dt(DevScalars* scal, double cfl, double dfl, int N, int viscous) {
+// next: the radii come from the previous step's last stage (lam_*_next)
+__global__ void k_dt(DevScalars* scal, double cfl, double dfl, int N, int viscous, int next = 0) {
+  if (next) {
+    scal->lam_c = scal->lam_c_next;
+    scal->lam_v = scal->lam_v_next;
+    scal->lam_c_next = 0ull;
+    scal->lam_v_next = 0ull;
+  }
   double dt = scal->dt_fixed > 0 ? scal->dt_fixed : cfl_dt(scal, cfl, dfl, N, viscous);
   double tn = scal->t + dt;
   if (scal->t_end > 0) {
@@ -389,6 +390,24 @@ cudaError_t launch_cfl(dg_ctx* c, bool report_only) {
     k_dt<<<1, 1, 0, c->stream>>>(c->scal, c->prm.cfl, c->prm.dfl, c->N, c->prm.viscous);
   prof_end(c);
   count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt_next(dg_ctx* c) {
+  prof_begin(c, PK_CFL);
+  k_dt<<<1, 1, 0, c->stream>>>(c->scal, c->prm.cfl, c->prm.dfl, c->N, c->prm.viscous, 1);
+  prof_end(c);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_clear_next(DevScalars* scal) {
+  scal->lam_c_next = 0ull;
+  scal->lam_v_next = 0ull;
+}
+cudaError_t launch_clear_next(dg_ctx* c) {
+  k_clear_next<<<1, 1, 0, c->stream>>>(c->scal);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -1404,6 +1404,9 @@ inline StageArgs make_stage_args(dg_ctx* c, const double* U) {
   a.pfv32 = c->pfv32;
   a.qs32 = c->qs32;
   a.wv32 = c->wv32;
+  a.cfl_out = c->stage_cfl;
+  a.scal_cfl = c->scal;
+  a.f_cflkv = (float)(std::max(4.0 / 3.0, c->prm.gamma / c->prm.Pr) * c->prm.mu);
   a.epilogue = 0;
   a.prefetch = 0;
   a.elem_off = 0;

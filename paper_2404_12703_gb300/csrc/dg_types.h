@@ -54,6 +54,10 @@ struct DevScalars {
   unsigned bar[2];
   int timeout;
   int pad2;
+  // two-kernel FP32-bulk steps: the spectral radii of the state a step ends
+  // with, reduced by its last stage (or by the face-data pass of a new
+  // state) for the next step's time step (bits of positive doubles)
+  unsigned long long lam_c_next, lam_v_next;
 };
 
 // Per-case data of a serving pool (device, one entry per case slot).
@@ -157,6 +161,12 @@ struct StageArgs {
   float* qs32;
   float* wv32;  // the lifting's volume sums of the state [E][12][n3] (Eq. lifting, before 1/J)
   int epilogue;
+  // the element kernel's epilogue (and k_fprep) also reduces the CFL radii
+  // of the state it prepares into scal->lam_*_next (f_cflkv: max(4/3,
+  // gamma / Pr) mu in FP32)
+  int cfl_out;
+  float f_cflkv;
+  DevScalars* scal_cfl;  // the step scalars the reduction writes (scal, writable)
   int prefetch;
   int elem_off;  // k_fprep without an element list: elements elem_off .. elem_off + E - 1
   int E_all;     // elements of the context's arrays (E, or a serving pool's capacity)
@@ -204,6 +214,8 @@ struct dg_ctx {
   int64_t cap_E = 0, cap_S = 0;  // allocated element and side capacity (a pool's, or E and S)
   int gauss = 0;              // solution on Gauss-Legendre nodes (standard DGSEM)
   double stage_c = 0.0;       // RK c coefficient of the stage being enqueued (stage time)
+  int stage_cfl = 0;          // the stage (or face-data pass) being enqueued reduces the next CFL radii
+  bool lam_next_valid = false;  // scal->lam_*_next hold the radii of the current state
   int rk_ns = 0;              // low-storage RK scheme of dg_step (0: the default five-stage one)
   double rk_a[32] = {}, rk_b[32] = {}, rk_c[32] = {};
   double* xyzs = nullptr;     // [E][n3][3] coordinates of the solution nodes

@@ -131,6 +131,54 @@ def test_interrupted_steps_equal_uninterrupted_ones():
     np.testing.assert_array_equal(b.get_state()[0], ref)
 
 
+@pytest.mark.parametrize("N", [2, 7])
+def test_cfl_steps_take_the_radii_of_the_last_stage(N):
+    """Two-kernel CFL steps take their time step from the radii that the
+    previous step's last stage reduced for the state it wrote (the face-data
+    pass reduces them for a new state): each step's dt equals, bit for bit,
+    the CFL time step that the reduction kernel forms from the state in
+    memory (dg_time_step); CFL step sequences broken by dg_time_step,
+    dg_rhs of another state, dg_kinetic and a configuration change continue
+    bitwise as if nothing happened; a non-finite state is reported."""
+    torch, dg = gpu_or_skip()
+    m = mesh(N, (3, 4, 3), seed=40 + N)
+    U0 = W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5), 1e-3, N)
+    a = dg.Solver(m, precision=dg.FP32_BULK)
+    assert a.stage_form() == 2
+    a.set_state(U0)
+    t = 0.0
+    for _ in range(4):
+        dt = a.time_step()
+        a.step(1)
+        t_new = a.get_state()[1]
+        assert t_new == t + dt
+        t = t_new
+    ref, t_ref = a.get_state()
+    other = torch.from_numpy(W.random_perturbation(U0, 1e-2, 9)).cuda()
+    b = dg.Solver(m, precision=dg.FP32_BULK)
+    b.set_state(U0)
+    b.step(1)
+    b.time_step()
+    b.step(1)
+    b.rhs(other)
+    b.kinetic()
+    b.step(1)
+    b.set_config(**dict(b.config(), side_block=128))
+    b.step(1)
+    U, tb = b.get_state()
+    assert tb == t_ref
+    np.testing.assert_array_equal(U, ref)
+    bad = U0.copy()
+    bad[1, 3, 4] = np.nan
+    b.set_state(bad)
+    with pytest.raises(dg.DgError) as err:
+        b.step(1, sync=True)
+    assert err.value.code == dg.DG_ERR_NONFINITE
+    b.set_state(U0)
+    b.step(1)
+    assert np.isfinite(b.get_state()[0]).all()
+
+
 def test_profile_step_matches_graph_steps():
     torch, dg = gpu_or_skip()
     N = 5

@@ -490,6 +490,7 @@ void dg_destroy(dg_ctx* c) {
   dfree(c, c->wv32);
   dfree(c, c->ops);
   dfree(c, c->scal);
+  dfree(c, c->kin_part);
   if (c->scal_host) cudaFreeHost(c->scal_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
@@ -1222,6 +1223,15 @@ int dg_kinetic(dg_ctx* c, double* out) {
   if (!c || !out) return fail(DG_ERR_ARG, "ctx or out is NULL");
   if (!c->state_set) return fail(DG_ERR_STATE, "no state set");
   if (!c->scal_host) return fail(DG_ERR_STATE, "internal case context: no host mirror");
+  const int nb = kinetic_blocks(c);
+  if (c->kin_part_blocks < nb) {
+    dfree(c, c->kin_part);
+    c->kin_part = nullptr;
+    c->kin_part_blocks = 0;
+    cudaError_t ea = dalloc(c, &c->kin_part, (int64_t)nb * 3);
+    if (ea != cudaSuccess) return cuda_fail(ea, "dg_kinetic");
+    c->kin_part_blocks = nb;
+  }
   cudaError_t e = launch_rhs(c, c->U, 0, 0.0, 0.0, 0);
   c->traces_valid = false;
   if (e == cudaSuccess) {

@@ -126,6 +126,8 @@ cudaError_t launch_to_internal(dg_ctx* c, const double* pub, double* internal);
 cudaError_t launch_to_public(dg_ctx* c, const double* internal, double* pub);
 
 // kinetic energy reductions into c->scal->kin (U internal, Ut internal or null)
+// the grid of the kinetic-energy reduction (its per-block sums need that many [3] entries)
+int kinetic_blocks(dg_ctx* c);
 cudaError_t launch_kinetic(dg_ctx* c, const double* U, const double* Ut);
 
 // the integer-pipe binary64 <-> binary32 conversions over n values (dg_rhs.cu)

@@ -163,10 +163,14 @@ __global__ void __launch_bounds__(256) k_to_public(int n3, const double* __restr
   }
 }
 
+// E_k, its rate and the volume (Sec. 5.2), in a fixed order of summation, so
+// that dg_kinetic gives bitwise the same values on every call: a fixed grid
+// walks the nodes, each block adds its threads' sums in a fixed tree and
+// writes them to part[block][3]; k_kinetic_sum adds the blocks in order
 template <int N>
 __global__ void __launch_bounds__(256) k_kinetic(int E, const double* __restrict__ U, const double* __restrict__ Ut,
                                                  const double* __restrict__ metric, const Ops* __restrict__ ops,
-                                                 DevScalars* scal) {
+                                                 double* __restrict__ part) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   double vol = 0, ek = 0, rate = 0;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < (int64_t)E * n3;
@@ -184,15 +188,58 @@ __global__ void __launch_bounds__(256) k_kinetic(int E, const double* __restrict
       rate += wq * (vx * ut[n3] + vy * ut[2 * n3] + vz * ut[3 * n3] - v2 * ut[0] / 2);
     }
   }
+  // butterfly over the warp: every lane ends with the same sums
   for (int o = 16; o > 0; o >>= 1) {
     vol += __shfl_xor_sync(0xffffffffu, vol, o);
     ek += __shfl_xor_sync(0xffffffffu, ek, o);
     rate += __shfl_xor_sync(0xffffffffu, rate, o);
   }
+  __shared__ double red[3][8];
+  const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&scal->kin[0], ek);
-    atomicAdd(&scal->kin[1], rate);
-    atomicAdd(&scal->kin[2], vol);
+    red[0][w] = ek;
+    red[1][w] = rate;
+    red[2][w] = vol;
+  }
+  __syncwarp();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double a = red[k][0];
+      for (int j = 1; j < nw; ++j) a += red[k][j];
+      part[(size_t)blockIdx.x * 3 + k] = a;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_kinetic_sum(int nb, const double* __restrict__ part, DevScalars* scal) {
+  __shared__ double s[3][256];
+  double a = 0, b = 0, c = 0;
+  for (int i = threadIdx.x; i < nb; i += 256) {
+    a += part[(size_t)i * 3 + 0];
+    b += part[(size_t)i * 3 + 1];
+    c += part[(size_t)i * 3 + 2];
+  }
+  s[0][threadIdx.x] = a;
+  s[1][threadIdx.x] = b;
+  s[2][threadIdx.x] = c;
+  __syncwarp();
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + h];
+      s[1][threadIdx.x] += s[1][threadIdx.x + h];
+      s[2][threadIdx.x] += s[2][threadIdx.x + h];
+    }
+    __syncwarp();
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    scal->kin[0] = s[0][0];
+    scal->kin[1] = s[1][0];
+    scal->kin[2] = s[2][0];
   }
 }
 
@@ -424,10 +471,14 @@ cudaError_t launch_to_public(dg_ctx* c, const double* internal, double* pub) {
   return cudaGetLastError();
 }
 
+int kinetic_blocks(dg_ctx* c) { return cfl_blocks(c); }
+
 cudaError_t launch_kinetic(dg_ctx* c, const double* U, const double* Ut) {
   const int nb = cfl_blocks(c);
-  DG_DISPATCH(c->N, (k_kinetic<NN><<<nb, 256, 0, c->stream>>>((int)c->E, U, Ut, c->metric, c->ops, c->scal)));
-  count_launch();
+  if (!c->kin_part || c->kin_part_blocks < nb) return cudaErrorInvalidValue;
+  DG_DISPATCH(c->N, (k_kinetic<NN><<<nb, 256, 0, c->stream>>>((int)c->E, U, Ut, c->metric, c->ops, c->kin_part)));
+  k_kinetic_sum<<<1, 256, 0, c->stream>>>(nb, c->kin_part, c->scal);
+  count_launch(2);
   return cudaGetLastError();
 }
 

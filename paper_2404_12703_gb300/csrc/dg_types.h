@@ -210,6 +210,8 @@ struct dg_ctx {
   double* sponge_base = nullptr;   // [E][5][n3] internal layout
   dg::Ops* ops = nullptr;    // device copy of the operators of degree N
   dg::DevScalars* scal = nullptr;
+  double* kin_part = nullptr;  // [blocks][3] per-block kinetic-energy sums (dg_kinetic)
+  int kin_part_blocks = 0;
   dg::DevScalars* scal_host = nullptr;  // pinned mirror
   int64_t cap_E = 0, cap_S = 0;  // allocated element and side capacity (a pool's, or E and S)
   int gauss = 0;              // solution on Gauss-Legendre nodes (standard DGSEM)

@@ -435,3 +435,30 @@ def test_maps_for_every_rotation_pair():
         np.testing.assert_array_equal(nbr[..., 2], om, err_msg=str((a, bs)))
         np.testing.assert_array_equal(nodes, onode, err_msg=str((a, bs)))
         s.close()
+
+
+def test_kinetic_energy_against_oracle_and_reproducible():
+    """dg_kinetic (Sec. 5.2: E_k, its exact rate from the right-hand side, the
+    volume) against the oracle on LGL nodes, and bitwise the same on repeated
+    calls and in a second context of the same state (a fixed grid and a
+    fixed order of summation)."""
+    torch, dg = gpu_or_skip()
+    N = 5
+    m = mesh(N, (4, 3, 3), seed=12)
+    U0 = W.random_perturbation(W.tgv_state(m["xyz"], Ma=0.3).reshape(m["E"], -1, 5), 1e-3, 4)
+    a = _solver(dg, m)
+    a.set_state(U0)
+    k1 = a.kinetic()
+    k2 = a.kinetic()
+    b = _solver(dg, m)
+    b.set_state(U0)
+    k3 = b.kinetic()
+    assert tuple(k1) == tuple(k2) == tuple(k3)
+    M = O.Mesh(N, m["xyz"], m["period"])
+    prm = oracle_params(a.params)
+    ok = M.kinetic(U0, M.rhs(U0, prm))
+    assert abs(k1[0] - ok[0]) <= 1e-12 * abs(ok[0])
+    assert abs(k1[2] - ok[2]) <= 1e-12 * abs(ok[2])
+    # the rate is a small difference of O(1) terms: against the magnitude of its terms
+    scale = abs(ok[0]) * np.abs(M.rhs(U0, prm)).max() / np.abs(U0).max()
+    assert abs(k1[1] - ok[1]) <= 1e-9 * scale

@@ -41,7 +41,7 @@ def rel_err(a, ref):
     return np.abs(a - ref).max(axis=0) / scale
 
 
-def parity_bound(oracle_fp64, oracle_ld, floor_factor=4.0, base=1e-12):
+def parity_bound(oracle_fp64, oracle_ld, floor_factor=3.0, base=1e-12):
     """Per-variable bound: 1e-12, or floor_factor times the FP64 oracle's own
     rounding error against the long-double oracle when that floor is higher
     (the stated 1e-12 sits below FP64's floor at low Mach number and high N)."""

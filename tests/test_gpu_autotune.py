@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 from paper_2404_12703_gb300 import workloads as W
 
-from gpu_util import gpu_or_skip, mesh, oracle_params, parity_bound, rel_err
+from gpu_util import parity_check, gpu_or_skip, mesh, oracle_params, parity_bound, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -63,8 +63,8 @@ def test_every_variant_gives_the_same_steps(N):
                 prm = oracle_params(s.params)
                 q = O.Mesh(N, m["xyz"], m["period"], quad=True).step(U0, prm, 2, dt=dt)[0]
                 o64 = O.Mesh(N, m["xyz"], m["period"]).step(U0, prm, 2, dt=dt)[0]
-                bound, _ = parity_bound(o64, q)
-                assert np.all(rel_err(U, q) <= bound), (cfg, rel_err(U, q), bound)
+                bound, floor = parity_bound(o64, q)
+                parity_check(rel_err(U, q), bound, floor)
         s.close()
 
 
@@ -94,7 +94,8 @@ def test_autotune_keeps_the_state_and_picks_a_variant():
         q = O.Mesh(N, m["xyz"], m["period"], quad=True).step(U0, prm, 2, dt=dt)[0]
         if prec == dg.FP64:
             o64 = O.Mesh(N, m["xyz"], m["period"]).step(U0, prm, 2, dt=dt)[0]
-            assert np.all(rel_err(U2, q) <= parity_bound(o64, q)[0])
+            bound, floor = parity_bound(o64, q)
+            parity_check(rel_err(U2, q), bound, floor)
         else:
             # FP32-bulk steps: the state changes by O(dt |Ut|) per step, with
             # FP32-rounded fluxes (the near-zero z-momentum sets the largest

@@ -8,7 +8,7 @@ combinations, and sampled elements of the 24^3-element N = 7 mesh.
 
 Bounds as for the LGL path: coordinates and metrics within a few ulp of the
 extended-precision oracle; floating point against the long-double oracle
-within max(1e-12, 4 x the FP64 oracle's own error) per conservative
+within max(1e-12, 3 x the FP64 oracle's own error) per conservative
 variable; FP32-bulk within 2e-4 of max |Ut|.
 """
 import numpy as np

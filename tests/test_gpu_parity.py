@@ -2,7 +2,7 @@
 against the CPU oracle on the same seeded inputs.
 
 Bounds: integer maps bit-exact; floating point against the long-double oracle
-within max(1e-12, 4 x the FP64 oracle's own error), per conservative variable
+within max(1e-12, 3 x the FP64 oracle's own error), per conservative variable
 (the FP64 rounding floor of the operator exceeds 1e-12 at Ma = 0.1 and
 N >= 3, so an FP64 implementation is held to the floor FP64 allows);
 10 LSERK steps within 1e-10 relative of the oracle's 10 steps.

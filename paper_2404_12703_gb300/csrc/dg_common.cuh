@@ -279,12 +279,10 @@ __device__ __forceinline__ void viscous_parts(const T g[12], T u, T v, T w, T mu
 // The spectral radii of the CFL rule at one node (dg_time_step in dg.h):
 // convective aa = sum_d (|u . Ja^d| + c |Ja^d|) / J and viscous
 // bb = kv(T) |Ja|^2 / (rho J^2), from the node's conservative state Uv, its
-// metrics M (Ja^d_c at 3 d + c, 1/J at 9), its geometry factors G (|Ja^d| for
-// d = 0, 1, 2, then sum_d |Ja^d|^2) and kv = max(4/3, gamma / Pr) mu (times
-// Sutherland's mu(T) / mu_ref).  FP32: every product and sum is a separately
-// rounded operation written out, so the CFL reduction kernel and the
-// two-kernel stage's epilogue, which both call this, form bitwise the same
-// radii whatever the compiler fuses around them.  FP64:
+// metrics M (Ja^d_c at 3 d + c, 1/J at 9) and kv = max(4/3, gamma / Pr) mu
+// (times Sutherland's mu(T) / mu_ref).  FP64: the geometry factors G (|Ja^d|
+// for d = 0, 1, 2, then sum_d |Ja^d|^2) are read, formed once from the FP64
+// metrics.
 __device__ __forceinline__ void cfl_radii(const double Uv[5], const double M[10], const double G[4], double gamma,
                                           double gm1, double Rinv, double kv, int sutherland, double inv_Tref,
                                           double& aa, double& bb) {
@@ -303,9 +301,11 @@ __device__ __forceinline__ void cfl_radii(const double Uv[5], const double M[10]
   }
   bb = kvn * ri * G[3] * M[9] * M[9];
 }
-// FP32: the geometry factors |Ja^d| and sum_d |Ja^d|^2 are formed here from
-// the FP32 metrics (the FP64 path reads them, formed once from the FP64
-// metrics), so the radii need nothing beyond the state and the metrics.
+// FP32: the geometry factors are formed here from the FP32 metrics, so the
+// radii need nothing beyond the state and the metrics; every product and sum
+// is a separately rounded operation written out, so the CFL reduction kernel
+// and the two-kernel stage's epilogue, which both call this, form bitwise
+// the same radii whatever the compiler fuses around them.
 __device__ __forceinline__ void cfl_radii(const float Uv[5], const float M[10], float gamma, float gm1, float Rinv,
                                           float kv, int sutherland, float inv_Tref, float& aa, float& bb) {
   const float ri = 1.0f / Uv[0];

@@ -194,7 +194,10 @@ int dg_rhs(dg_ctx* ctx, const double* U_dev, double* Ut_dev);
 /* Advances the context's state by n_steps steps of the five-stage
    low-storage RK4 (Sec. 2.2, Time integration).  dt > 0: fixed step;
    dt <= 0: each step uses the CFL rule evaluated on the device from the
-   step's initial state.  t_out NULL: stream-ordered (asynchronous,
+   step's initial state (in the two-kernel FP32-bulk stage form the spectral
+   radii of that state are reduced by the previous step's last stage, or by
+   the face-data pass of a state no step wrote; the time step is bitwise the
+   one dg_time_step gives for the same state).  t_out NULL: stream-ordered (asynchronous,
    graph-launched); the time stays on the device (dg_get_state reads it).
    t_out non-NULL: the call then synchronises the context's stream and
    stores the time reached in *t_out, returning DG_ERR_NONFINITE if a step
@@ -300,7 +303,10 @@ int dg_time_step(dg_ctx* ctx, double* dt);
 /* Kinetic energy E_k = 1/(2|Omega|) int rho |u|^2 and its exact rate from the
    right-hand side, dE_k/dt = 1/|Omega| int (u.(rho u)_t - |u|^2 rho_t / 2)
    (Sec. 5.2), of the context's state; out[0] = E_k, out[1] = dE_k/dt,
-   out[2] = |Omega|.  FP64 reductions on the device; synchronises. */
+   out[2] = |Omega|.  FP64 reductions on the device in a fixed order of
+   summation, so repeated calls on the same state return bitwise the same
+   values; the first call allocates a small per-context array of partial
+   sums (a few tens of KB); synchronises. */
 int dg_kinetic(dg_ctx* ctx, double* out);
 
 /* ------------------------------------------------------------------------

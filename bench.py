@@ -76,7 +76,7 @@ FFLUX32_BYTES_PER_DOF = FACE_NODES_PER_DOF / 2 * (64 + 32 + 28 + 20 + 16)
 BYTES32_PER_DOF = 342.0
 # DRAM bytes per DOF of one launch of the FP32-bulk dominant kernel (ncu); None
 # whenever the kernel changes until re-measured
-VOLUME32_TRAFFIC_BYTES_PER_DOF = 282.9
+VOLUME32_TRAFFIC_BYTES_PER_DOF = 284.5
 # Standard DGSEM on Gauss-Legendre nodes, algorithmic flops per DOF and stage
 # (n = N + 1, FMA = 2 flops).  Lifting: D-hat line sums 72 n, metric products
 # 36, both faces of three lines 144, 1/J 12, ProlongToFace of the twelve

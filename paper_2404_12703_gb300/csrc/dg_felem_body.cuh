@@ -27,12 +27,12 @@ do {
     float* base = sDr + n * L::n4;
     const int le = threadIdx.x / n3, t = threadIdx.x % n3;
     float* mine = base + (size_t)le * L::per_elem_f;
-    float4* P4 = reinterpret_cast<float4*>(mine);                   // [n3] (rho, u, v, w) / 2
-    float4* Q4 = P4 + n3;                                           // [n3] (p' / 2, H' / 2, T', 0)
+    float4* P4 = reinterpret_cast<float4*>(mine);                   // [Pn] (rho, u, v, w) / 2, padded index
+    float4* Q4 = P4 + L::Pn;                                        // [Pn] (p' / 2, H' / 2, T', 0), padded index
     float4* J4 = reinterpret_cast<float4*>(mine + L::offJ);         // [3][Pn] (Ja^d) / 2, padded index
     float* Qs = mine + L::offQ;                                     // [4][Pn] u, v, w, T', padded index
     float* Wk = mine + L::offW;                                     // [12][Pn] workspace
-    float4* G4 = reinterpret_cast<float4*>(Wk);
+    float4* G4 = reinterpret_cast<float4*>(Wk);                     // [Pn] viscous fluxes, padded index
     float4* sSn = reinterpret_cast<float4*>(mine + L::offN);        // [6][n2] face normals and signs
     float4* sQst = reinterpret_cast<float4*>(mine + L::offQS);      // [6][n2] q* of the six sides
     float* sFst = mine + L::offFS;                                  // [5][6 n2] f* of the six sides
@@ -108,9 +108,9 @@ do {
     // the FP64 pressure only for the indicator (one FP64 addition less otherwise)
     const SPrim<float> me = shifted_prim<float, true>(U, a.gm1, a.Rinv, cp, a.shock ? &p_full : nullptr);
     // halved values: every arithmetic mean of the two-point flux is one addition
-    P4[t] = make_float4(0.5f * me.rho, 0.5f * me.u, 0.5f * me.v, 0.5f * me.w);
-    Q4[t] = make_float4(0.5f * me.p, 0.5f * me.H, me.Tt, 0.0f);
     const int vp = pad_idx<n>(t);
+    P4[vp] = make_float4(0.5f * me.rho, 0.5f * me.u, 0.5f * me.v, 0.5f * me.w);
+    Q4[vp] = make_float4(0.5f * me.p, 0.5f * me.H, me.Tt, 0.0f);
   #pragma unroll
     for (int d = 0; d < 3; ++d)
       J4[d * Pn + vp] = make_float4(0.5f * mt[3 * d], 0.5f * mt[3 * d + 1], 0.5f * mt[3 * d + 2], 0.0f);
@@ -162,8 +162,8 @@ do {
   #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int id = dir_index<n>(t, d), sd = dir_stride<n>(d), bse = t - id * sd;
-      const float4 ai = P4[t];
-      const float4 bi = Q4[t];
+      const float4 ai = P4[vp];
+      const float4 bi = Q4[vp];
       const float4 ji = J4[d * Pn + vp];
       float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
   #pragma unroll
@@ -171,9 +171,10 @@ do {
         if (al == id) continue;
         const int va = bse + al * sd;
         if (!DG_CHK(va >= 0 && va < n3, va)) continue;
-        const float4 aa = P4[va];
-        const float4 ba = Q4[va];
-        const float4 ja = J4[d * Pn + pad_idx<n>(va)];
+        const int pva = pad_idx<n>(va);
+        const float4 aa = P4[pva];
+        const float4 ba = Q4[pva];
+        const float4 ja = J4[d * Pn + pva];
         const float m0 = ji.x + ja.x, m1 = ji.y + ja.y, m2 = ji.z + ja.z;
         const float rho = ai.x + aa.x;
         const float u0 = ai.y + aa.y, u1 = ai.z + aa.z, u2 = ai.w + aa.w;
@@ -205,7 +206,7 @@ do {
           const float nv[3] = {2.0f * jj.x, 2.0f * jj.y, 2.0f * jj.z};
           float fv[4];
           viscous_flux_n(tau, W, nv, fv);
-          G4[t] = make_float4(fv[0], fv[1], fv[2], fv[3]);
+          G4[vp] = make_float4(fv[0], fv[1], fv[2], fv[3]);
         }
         __syncwarp();
         __syncthreads();
@@ -214,7 +215,7 @@ do {
   #pragma unroll
           for (int al = 0; al < n; ++al) {
             const float c = sDh[id * n + al];
-            const float4 gv = G4[bse + al * sd];
+            const float4 gv = G4[pad_idx<n>(bse + al * sd)];
             acc[1] -= c * gv.x;
             acc[2] -= c * gv.y;
             acc[3] -= c * gv.z;

@@ -83,13 +83,15 @@ struct FusedSmem {
   // a node plane with one pad word after every line of n nodes (pad_idx):
   // lines along any direction then fall in distinct banks
   static constexpr int Pn = S::n3 + S::n2;
-  // per element: P (2 float4 per node: (rho, u, v, w) / 2 and (p', H') / 2, T'),
-  // J (3 float4 planes, (Ja^d) / 2), q (4 planes: u, v, w, T'), W (12 planes:
+  // per element: P (2 float4 planes, padded index: (rho, u, v, w) / 2 and
+  // (p', H') / 2, T'; padded like every plane the line sums read, so that the
+  // four lines of eight nodes a warp holds along the first direction fall in
+  // distinct banks), J (3 float4 planes, (Ja^d) / 2), q (4 planes: u, v, w, T'), W (12 planes:
   // lifting sums; also viscous / FV fluxes and the FP64 indicator scratch),
   // face normals (6 faces x n2 float4: s n and the SurfInt sign), and the
   // element's gathered face and RK data: q* of its six sides (6 x n2 float4),
   // their f* (5 planes of 6 n2) and its FP32 RK register (5 planes of n3)
-  static constexpr int offJ = 8 * S::n3, offQ = offJ + 12 * Pn, offW = offQ + 4 * Pn, offN = offW + 12 * Pn;
+  static constexpr int offJ = 8 * Pn, offQ = offJ + 12 * Pn, offW = offQ + 4 * Pn, offN = offW + 12 * Pn;
   static constexpr int offQS = offN + 24 * S::n2, offFS = offQS + 24 * S::n2;
   static constexpr int offDU = (offFS + 30 * S::n2 + 3) & ~3;  // (rounded to whole float4s)
   static constexpr int per_elem_f = (offDU + 5 * S::n3 + 3) & ~3;
